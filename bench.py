@@ -1,0 +1,297 @@
+"""Throughput of the FP64 WENO5-HLLC-SSP-RK3 step on one GB300 (or N independent replicas).
+
+One "step" = one pass of the whole hot path over the grid: CFL reduction for dt, then three
+Runge-Kutta stages, each = immersed-boundary ghost fill + domain halo fill + fused stage
+kernel (WENO5, HLLC, viscous fluxes, divergence, stage combination).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload riemann2d|shock_cylinder]
+    python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
+
+Prints ONE JSON line (rank 0).  `value` is cell-updates/s with the state resident in HBM;
+`e2e` is the same metric through the C ABI with the state copied from pinned host memory
+and back every step; `roofline` divides the algorithmic FP64 operation count of the stage
+kernel by its CUDA-event time and by the FP64 peak.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+# Algorithmic FP64 operations (add/sub, mul, div, sqrt; each face once) per cell and RHS
+# evaluation, counted by oracle/count_flops.py on a seeded perturbation of each workload.
+FLOPS_PER_CELL_STAGE = {"riemann2d": 1281.0, "shock_cylinder": 1357.0}
+# FP64 peak of one GB300: 152 SMs x 2070 MHz boost, NVIDIA's 1.25 TFLOP/s FP64 figure.
+FP64_PEAK_TFLOPS = 1.25
+L2_FLUSH_BYTES = 256 << 20
+METRIC = "FP64 cell-updates/s per RK step on 1 GB300 (% roofline); adjoint/forward time ratio"
+
+
+def workload(name):
+    from paper_2601_04400_gb300 import workloads as W
+    if name == "riemann2d":
+        p = W.riemann2d(1024)
+        desc = "2D four-quadrant Riemann problem, Euler, 1024x1024, WENO5+HLLC+SSP-RK3, CFL 0.5, transmissive"
+    elif name == "shock_cylinder":
+        p = W.shock_cylinder()
+        desc = ("viscous Mach-2 shock over an immersed cylinder, Navier-Stokes Re=1000 Pr=0.72, 2048x1024, "
+                "WENO5+HLLC+IB+SSP-RK3, CFL 0.5")
+    else:
+        raise SystemExit("unknown workload %s" % name)
+    return p, desc
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi SM clock / throttle-reason sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(prob, budget_s=12.0):
+    """The oracle, as it stands, on the host cores: full-grid SSP-RK3 steps for ~budget_s."""
+    import oracle as O
+    U = O.prim_to_cons(prob, prob.W0)
+    dt = O.max_dt(prob, U, prob.cfl)
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        U = O.step(prob, U, [dt])
+        steps += 1
+        el = time.perf_counter() - t0
+        if el > budget_s or steps >= 200:
+            break
+    return {"value": prob.cells * steps / el, "unit": "cell-updates/s", "cores": O.threads(), "kind": "oracle",
+            "sample": "%d SSP-RK3 steps of the full %dx%d grid from the initial state, fixed dt, %.1f s"
+                      % (steps, prob.nx, prob.ny, el)}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle timed on the host cores (rank 0 only)."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle as O
+    from oracle import build as ob
+    ob.build()
+    prob, desc = workload(args.workload)
+    U = O.prim_to_cons(prob, prob.W0)
+    dt = O.max_dt(prob, U, prob.cfl)
+    t0 = time.perf_counter()
+    U1 = O.step(prob, U, [dt])
+    t1 = time.perf_counter() - t0
+    # bound the whole run to about two and a half minutes: a band of rows around the
+    # quadrant split when the full grid would take longer
+    budget = 150.0
+    rows = prob.ny
+    if (args.steps + args.warmup) * t1 > budget:
+        rows = max(16, int(prob.ny * budget / ((args.steps + args.warmup) * t1)))
+    sub = prob
+    if rows < prob.ny:
+        j0 = max(0, min(prob.ny - rows, int(0.8 * prob.ny) - rows // 2))
+        sub = prob.with_(ny=rows, y0=prob.y0 + j0 * prob.dy, W0=np.array(prob.W0[:, j0:j0 + rows]),
+                         sdf=None if prob.sdf is None else np.array(prob.sdf[:, j0:j0 + rows]))
+    Us = O.prim_to_cons(sub, sub.W0)
+    for _ in range(args.warmup):
+        Us = O.step(sub, Us, [dt])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        Us = O.step(sub, Us, [dt])
+    el = time.perf_counter() - t0
+    value = sub.cells * args.steps / el
+    sample = ("%d SSP-RK3 steps of a %dx%d %s of the workload, fixed dt" %
+              (args.steps, sub.nx, sub.ny, "band" if rows < prob.ny else "grid"))
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": desc, "nx": sub.nx, "ny": sub.ny},
+        "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": O.threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2601_04400_gb300 import binding as B
+    B.lib()
+    prob, desc = workload(args.workload)
+    stream = torch.cuda.current_stream()
+    solver = B.Solver.from_problem(prob, stream=stream)
+    W0 = torch.tensor(prob.W0, dtype=torch.float64, device="cuda")
+    U = solver.prim_to_cons(W0)
+    U0 = U.clone()
+    flush = torch.empty(L2_FLUSH_BYTES // 8, dtype=torch.float64, device="cuda")
+    cfl = prob.cfl
+
+    def one_step(Ud):
+        dt = solver.max_dt(Ud, cfl)
+        solver.step(Ud, dt, 1)
+
+    for _ in range(args.warmup):
+        one_step(U)
+    solver.check()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-resident timing -------------------------------------------------------
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    barrier()
+    with sampler:
+        B.js_profile_begin(solver.ctx, 3 * args.steps + 8)
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            one_step(U)
+            ev[k][1].record(stream)
+        stage_ms, stage_launches, launches = B.js_profile_end(solver.ctx)
+        barrier()
+    step_ms = sum(a.elapsed_time(b) for a, b in ev)
+    solver.check()
+    # ---- end to end through the C ABI with host buffers -------------------------------
+    Uh = torch.empty(U.shape, dtype=torch.float64).pin_memory()
+    Uh.copy_(U0.cpu())
+    Ud = torch.empty_like(U)
+    ee = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    for k in range(args.steps):
+        flush.zero_()
+        ee[k][0].record(stream)
+        Ud.copy_(Uh, non_blocking=True)
+        one_step(Ud)
+        Uh.copy_(Ud, non_blocking=True)
+        ee[k][1].record(stream)
+    barrier()
+    e2e_ms = sum(a.elapsed_time(b) for a, b in ee)
+    solver.check()
+
+    if dist is not None:
+        t = torch.tensor([step_ms, e2e_ms, stage_ms / max(stage_launches, 1)], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms, e2e_ms, stage_avg = t.tolist()
+    else:
+        stage_avg = stage_ms / max(stage_launches, 1)
+    cells = prob.cells
+    value = world * cells * args.steps / (step_ms * 1e-3)
+    e2e_value = world * cells * args.steps / (e2e_ms * 1e-3)
+    flop_launch = FLOPS_PER_CELL_STAGE[args.workload] * cells
+    achieved = flop_launch / (stage_avg * 1e-3) / 1e12
+    state_bytes = 4 * cells * 8
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "nx": prob.nx, "ny": prob.ny, "cells": cells,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "flushed between steps (256 MiB write)",
+                       "step": "CFL reduction + 3 x (IB fill, halo fill, fused stage kernel)"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                         "kernel": "stage2d (fused WENO5-HLLC stage)", "stage_ms_avg": stage_avg,
+                         "flops_per_launch": flop_launch},
+            "e2e": {"value": e2e_value, "unit": "cell-updates/s", "h2d_bytes_per_step": state_bytes,
+                    "d2h_bytes_per_step": state_bytes},
+            "gpu_launches": launches,
+            "clocks": sampler.summary(),
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(prob)
+        print(json.dumps(out), flush=True)
+    solver.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="riemann2d", choices=["riemann2d", "shock_cylinder"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,135 @@
+/*
+ * jaxshock.h -- C ABI of libjaxshock.so, a GB300 (sm_103a) FP64 implementation of the
+ * explicit finite-volume right-hand side of the 2D compressible Euler / Navier-Stokes
+ * equations of JAX-Shock (arXiv 2601.04400, Sec. 2) and its SSP-RK3 time step.
+ *
+ * Conventions (all entry points):
+ *   - State arrays are FP64, conserved variables stacked as [4][ny][nx], x fastest:
+ *     rho, rho*u, rho*v, E (Sec. 2, Eq. 1).  Device pointers unless a name says "host".
+ *     The caller owns every array it passes; the library owns its own workspace.
+ *   - ny == 1 is a one-dimensional problem: no y fluxes are evaluated.
+ *   - Work is enqueued on the context's CUDA stream and is asynchronous, except where an
+ *     entry point says it synchronises.  Nothing in js_step/js_rhs/js_*_vjp allocates or
+ *     synchronises, so a sequence of these calls can be captured into a CUDA graph.
+ *   - Return value: JS_OK (0) or a negative JS_ERR_* code.  Device-side failures (a
+ *     non-physical state, a barrier that timed out) are recorded in a device flag and
+ *     reported by js_sync_status, which synchronises the stream.
+ *   - A context is not thread-safe; use one context per host thread / stream.
+ */
+#ifndef JAXSHOCK_H
+#define JAXSHOCK_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  JS_OK = 0,
+  JS_ERR_ARG = -1,          /* invalid argument (sizes, null pointers, kinds)            */
+  JS_ERR_CUDA = -2,         /* a CUDA runtime call failed                                 */
+  JS_ERR_NONPHYSICAL = -3,  /* a fluid cell had rho <= 0, p <= 0 or a NaN                 */
+  JS_ERR_TIMEOUT = -4,      /* a bounded device-side wait gave up                         */
+  JS_ERR_IB = -5,           /* immersed boundary: an image point has no fluid neighbour   */
+  JS_ERR_NOMEM = -6         /* device allocation failed                                   */
+};
+
+/* Domain boundary kinds (Sec. 3: inflow, outflow, reflective walls; periodic for tests). */
+enum { JS_BC_TRANSMISSIVE = 0, JS_BC_REFLECTIVE = 1, JS_BC_PERIODIC = 2, JS_BC_INFLOW = 3 };
+
+/* Uniform Cartesian grid of nx*ny cells, lower-left corner (x0, y0), spacing (dx, dy). */
+typedef struct { int nx, ny; double x0, y0, dx, dy; } js_grid;
+
+/* Boundary kinds of the x-low, x-high, y-low and y-high sides, and for JS_BC_INFLOW the
+ * primitive state (rho, u, v, p) held in the three ghost layers of that side. */
+typedef struct { int kind[4]; double inflow[4][4]; } js_boundary;
+
+/* gamma: ratio of specific heats (Sec. 2, EOS).  mu, Pr: constant dynamic viscosity and
+ * Prandtl number of the Navier-Stokes terms (mu = 0: Euler).  nu: coefficient of the
+ * Laplacian artificial viscosity nu*lap(U) of the update equation in Sec. 2.  wall: the
+ * immersed wall condition, 0 = slip (the paper), 1 = no-slip. */
+typedef struct { double gamma, mu, Pr, nu; int wall; } js_params;
+
+/* Parameter-gradient layout used by the vjp entry points (20 doubles):
+ * [0] gamma, [1] mu, [2] Pr, [3] nu, [4 + 4*side + k] inflow state k (rho,u,v,p) of side. */
+#define JS_NPARAM 20
+
+typedef struct js_ctx js_ctx;
+
+/* Create a solver context (Sec. 2 problem statement).
+ *   grid, params, bc : problem description (copied).
+ *   sdf_host         : optional host array [ny][nx] of signed distances to the immersed
+ *                      solid (< 0 inside; Sec. 2, Fig. 1(c)); NULL = no immersed body.
+ *                      Ghost cells, image points and interpolation weights are
+ *                      precomputed here.
+ *   stream           : cudaStream_t to enqueue on (NULL = legacy default stream).
+ * Allocates the padded state buffers and IB tables on the current device.
+ * Errors: JS_ERR_ARG, JS_ERR_IB (image point outside the domain or without fluid
+ * neighbour), JS_ERR_NOMEM, JS_ERR_CUDA. */
+int js_create(const js_grid* grid, const js_params* params, const js_boundary* bc,
+              const double* sdf_host, void* stream, js_ctx** out);
+
+/* Release a context and its device memory (synchronises its stream). NULL is a no-op. */
+void js_destroy(js_ctx* ctx);
+
+/* Replace the physical parameters and boundary states (geometry stays). */
+int js_set_params(js_ctx* ctx, const js_params* params, const js_boundary* bc);
+
+/* Change the stream later work is enqueued on. */
+int js_set_stream(js_ctx* ctx, void* stream);
+
+/* Primitive (rho, u, v, p) -> conserved state with the context's gamma (Sec. 2, EOS).
+ * W, U: device [4][ny][nx]; may alias. */
+int js_prim_to_cons(js_ctx* ctx, const double* W, double* U);
+
+/* dUdt = L(U): boundary halos and immersed-boundary ghost states are filled from U, then
+ * WENO5 face states of the primitive variables (Sec. 2), HLLC fluxes, viscous fluxes,
+ * flux divergence and nu*lap(U).  Solid and ghost cells get dUdt = 0.
+ * U, dUdt: device [4][ny][nx], must not alias.  Asynchronous. */
+int js_rhs(js_ctx* ctx, const double* U, double* dUdt);
+
+/* Largest stable time step of U: dt = cfl / max over fluid cells of
+ * (|u| + a)/dx + (|v| + a)/dy, capped by the explicit viscous limit when mu > 0.
+ * U: device [4][ny][nx].  dt_out: host.  Synchronises the stream. */
+int js_max_dt(js_ctx* ctx, const double* U, double cfl, double* dt_out);
+
+/* Advance U in place by n_steps three-stage SSP-RK3 steps of size dt (the solver step
+ * S(U, theta) of Sec. 2 applied n_steps times).  U: device [4][ny][nx].  Asynchronous. */
+int js_step(js_ctx* ctx, double* U, double dt, int n_steps);
+
+/* Vector-Jacobian product of the RHS (reverse mode of js_rhs, Sec. 2 gradient chain rule):
+ *   U_bar  = (dL/dU)^T lam          (overwritten), device [4][ny][nx]
+ *   p_bar += (dL/dtheta)^T lam      (accumulated), device double[JS_NPARAM] or NULL
+ * lam: device [4][ny][nx].  Asynchronous. */
+int js_rhs_vjp(js_ctx* ctx, const double* U, const double* lam, double* U_bar, double* p_bar);
+
+/* Vector-Jacobian product of ONE SSP-RK3 step of size dt taken from U_n:
+ *   lam_n  = (dU_{n+1}/dU_n)^T lam_np1     (overwritten), device [4][ny][nx]
+ *   p_bar += (dU_{n+1}/dtheta)^T lam_np1   (accumulated), device double[JS_NPARAM] or NULL
+ * The three stage states are recomputed from U_n inside the call.  lam_n may alias
+ * lam_np1.  Asynchronous. */
+int js_step_vjp(js_ctx* ctx, const double* U_n, double dt, const double* lam_np1, double* lam_n,
+                double* p_bar);
+
+/* Read and clear the device error flag; synchronises the stream.  Returns JS_OK,
+ * JS_ERR_NONPHYSICAL or JS_ERR_TIMEOUT (or JS_ERR_CUDA if the stream itself failed). */
+int js_sync_status(js_ctx* ctx);
+
+/* Number of immersed-boundary ghost cells and, if tag_host != NULL, the cell tags
+ * (0 fluid, 1 solid, 2 ghost) as host uint8 [ny][nx]. */
+int js_ib_info(js_ctx* ctx, int* n_ghost, unsigned char* tag_host);
+
+/* Instrumentation.  js_profile_begin(ctx, capacity) starts timing every launch of the fused
+ * stage kernel (up to `capacity` launches) with CUDA events recorded on the context's stream,
+ * and counting every kernel the context launches.  js_profile_end synchronises the stream,
+ * stops recording and returns the summed stage-kernel time in ms, the number of stage
+ * launches timed and the number of kernels launched in between (any pointer may be NULL). */
+int js_profile_begin(js_ctx* ctx, int capacity);
+int js_profile_end(js_ctx* ctx, double* stage_ms, int* stage_launches, long long* kernel_launches);
+
+/* Human-readable text of a JS_* code (static storage). */
+const char* js_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* JAXSHOCK_H */

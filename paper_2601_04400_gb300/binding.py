@@ -1,0 +1,286 @@
+"""Thin ctypes binding of libjaxshock.so (include/jaxshock.h): argument marshalling only.
+
+Every step of the solver runs in the library's CUDA kernels; PyTorch only provides device
+memory and the stream.  Functions keep the C names (js_create, js_rhs, js_step, ...) and
+take torch tensors: float64, CUDA, contiguous, conserved variables shaped [4, ny, nx].
+The library is loaded on first use; if it is missing and cannot be built, loading raises --
+there is no CPU fallback.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+JS_OK, JS_ERR_ARG, JS_ERR_CUDA, JS_ERR_NONPHYSICAL, JS_ERR_TIMEOUT, JS_ERR_IB, JS_ERR_NOMEM = 0, -1, -2, -3, -4, -5, -6
+JS_NPARAM = 20
+
+_lib = None
+
+
+class JsGrid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("x0", C.c_double), ("y0", C.c_double),
+                ("dx", C.c_double), ("dy", C.c_double)]
+
+
+class JsBoundary(C.Structure):
+    _fields_ = [("kind", C.c_int * 4), ("inflow", (C.c_double * 4) * 4)]
+
+
+class JsParams(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("mu", C.c_double), ("Pr", C.c_double), ("nu", C.c_double),
+                ("wall", C.c_int)]
+
+
+class JsError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__("%s: %s (%d)" % (what, strerror(code), code))
+        self.code = code
+
+
+_P = C.c_void_p
+_D = C.c_double
+_I = C.c_int
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "js_create": (_I, [C.POINTER(JsGrid), C.POINTER(JsParams), C.POINTER(JsBoundary), _P, _P, C.POINTER(_P)]),
+    "js_destroy": (None, [_P]),
+    "js_set_params": (_I, [_P, C.POINTER(JsParams), C.POINTER(JsBoundary)]),
+    "js_set_stream": (_I, [_P, _P]),
+    "js_prim_to_cons": (_I, [_P, _P, _P]),
+    "js_rhs": (_I, [_P, _P, _P]),
+    "js_max_dt": (_I, [_P, _P, _D, C.POINTER(_D)]),
+    "js_step": (_I, [_P, _P, _D, _I]),
+    "js_rhs_vjp": (_I, [_P, _P, _P, _P, _P]),
+    "js_step_vjp": (_I, [_P, _P, _D, _P, _P, _P]),
+    "js_sync_status": (_I, [_P]),
+    "js_ib_info": (_I, [_P, C.POINTER(_I), _P]),
+    "js_profile_begin": (_I, [_P, _I]),
+    "js_profile_end": (_I, [_P, C.POINTER(_D), C.POINTER(_I), C.POINTER(C.c_longlong)]),
+    "js_strerror": (C.c_char_p, [_I]),
+}
+
+
+def library_path():
+    return _build.LIB
+
+
+def lib():
+    """Load libjaxshock.so (building it in-tree if it is absent)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            _build.build()
+        L = C.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def strerror(code):
+    return lib().js_strerror(int(code)).decode()
+
+
+def _check(rc, what):
+    if rc != JS_OK:
+        raise JsError(rc, what)
+
+
+def _ptr(t):
+    """Device pointer of a float64 CUDA tensor (must be contiguous)."""
+    import torch
+    if t is None:
+        return None
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream=None):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def make_structs(nx, ny, x0, y0, dx, dy, bc, gamma, mu, Pr, nu, inflow, wall=0):
+    g = JsGrid(int(nx), int(ny), float(x0), float(y0), float(dx), float(dy))
+    p = JsParams(float(gamma), float(mu), float(Pr), float(nu), int(wall))
+    b = JsBoundary()
+    inflow = np.asarray(inflow, dtype=np.float64).reshape(4, 4)
+    for s in range(4):
+        b.kind[s] = int(bc[s])
+        for k in range(4):
+            b.inflow[s][k] = float(inflow[s, k])
+    return g, p, b
+
+
+# ---------------------------------------------------------------------------------------
+# C-named wrappers
+# ---------------------------------------------------------------------------------------
+def js_create(grid, params, boundary, sdf=None, stream=None):
+    sdf_p = None
+    if sdf is not None:
+        sdf = np.ascontiguousarray(sdf, dtype=np.float64)
+        sdf_p = sdf.ctypes.data_as(C.c_void_p)
+    out = C.c_void_p()
+    _check(lib().js_create(C.byref(grid), C.byref(params), C.byref(boundary), sdf_p, _stream_ptr(stream),
+                           C.byref(out)), "js_create")
+    return out
+
+
+def js_destroy(ctx):
+    lib().js_destroy(ctx)
+
+
+def js_set_params(ctx, params, boundary):
+    _check(lib().js_set_params(ctx, C.byref(params), C.byref(boundary)), "js_set_params")
+
+
+def js_set_stream(ctx, stream=None):
+    _check(lib().js_set_stream(ctx, _stream_ptr(stream)), "js_set_stream")
+
+
+def js_prim_to_cons(ctx, W, U):
+    _check(lib().js_prim_to_cons(ctx, _ptr(W), _ptr(U)), "js_prim_to_cons")
+
+
+def js_rhs(ctx, U, dUdt):
+    _check(lib().js_rhs(ctx, _ptr(U), _ptr(dUdt)), "js_rhs")
+
+
+def js_max_dt(ctx, U, cfl):
+    dt = C.c_double(0.0)
+    _check(lib().js_max_dt(ctx, _ptr(U), float(cfl), C.byref(dt)), "js_max_dt")
+    return dt.value
+
+
+def js_step(ctx, U, dt, n_steps):
+    _check(lib().js_step(ctx, _ptr(U), float(dt), int(n_steps)), "js_step")
+
+
+def js_rhs_vjp(ctx, U, lam, U_bar, p_bar=None):
+    _check(lib().js_rhs_vjp(ctx, _ptr(U), _ptr(lam), _ptr(U_bar), _ptr(p_bar)), "js_rhs_vjp")
+
+
+def js_step_vjp(ctx, U_n, dt, lam_np1, lam_n, p_bar=None):
+    _check(lib().js_step_vjp(ctx, _ptr(U_n), float(dt), _ptr(lam_np1), _ptr(lam_n), _ptr(p_bar)), "js_step_vjp")
+
+
+def js_profile_begin(ctx, capacity):
+    _check(lib().js_profile_begin(ctx, int(capacity)), "js_profile_begin")
+
+
+def js_profile_end(ctx):
+    """Returns (summed stage-kernel ms, stage launches timed, kernels launched)."""
+    ms, n, k = C.c_double(0.0), C.c_int(0), C.c_longlong(0)
+    _check(lib().js_profile_end(ctx, C.byref(ms), C.byref(n), C.byref(k)), "js_profile_end")
+    return ms.value, n.value, k.value
+
+
+def js_sync_status(ctx):
+    return lib().js_sync_status(ctx)
+
+
+def js_ib_info(ctx, nx, ny):
+    n = C.c_int(0)
+    tag = np.zeros((ny, nx), dtype=np.uint8)
+    _check(lib().js_ib_info(ctx, C.byref(n), tag.ctypes.data_as(C.c_void_p)), "js_ib_info")
+    return n.value, tag
+
+
+# ---------------------------------------------------------------------------------------
+# convenience object owning a context
+# ---------------------------------------------------------------------------------------
+class Solver:
+    """One solver context: a grid, its parameters, boundaries and optional immersed body."""
+
+    def __init__(self, nx, ny, x0, y0, dx, dy, bc=(0, 0, 0, 0), gamma=1.4, mu=0.0, Pr=0.72, nu=0.0,
+                 inflow=None, wall=0, sdf=None, stream=None):
+        if inflow is None:
+            inflow = np.tile([1.0, 0.0, 0.0, 1.0], (4, 1))
+        self.nx, self.ny = int(nx), int(ny)
+        self.dx, self.dy = float(dx), float(dy)
+        self._spec = dict(nx=nx, ny=ny, x0=x0, y0=y0, dx=dx, dy=dy, bc=tuple(bc), gamma=gamma, mu=mu, Pr=Pr,
+                          nu=nu, inflow=np.asarray(inflow, dtype=np.float64).reshape(4, 4), wall=wall)
+        self._g, self._p, self._b = make_structs(**self._spec)
+        self.ctx = js_create(self._g, self._p, self._b, sdf, stream)
+
+    @classmethod
+    def from_problem(cls, prob, stream=None):
+        return cls(prob.nx, prob.ny, prob.x0, prob.y0, prob.dx, prob.dy, prob.bc, prob.gamma, prob.mu, prob.Pr,
+                   prob.nu, prob.inflow, getattr(prob, "wall", 0), prob.sdf, stream)
+
+    @property
+    def shape(self):
+        return (4, self.ny, self.nx)
+
+    def set_params(self, gamma=None, mu=None, Pr=None, nu=None, inflow=None):
+        for k, v in (("gamma", gamma), ("mu", mu), ("Pr", Pr), ("nu", nu)):
+            if v is not None:
+                self._spec[k] = float(v)
+        if inflow is not None:
+            self._spec["inflow"] = np.asarray(inflow, dtype=np.float64).reshape(4, 4)
+        self._g, self._p, self._b = make_structs(**self._spec)
+        js_set_params(self.ctx, self._p, self._b)
+
+    def set_stream(self, stream=None):
+        js_set_stream(self.ctx, stream)
+
+    def prim_to_cons(self, W):
+        import torch
+        U = torch.empty_like(W)
+        js_prim_to_cons(self.ctx, W, U)
+        return U
+
+    def rhs(self, U, out=None):
+        import torch
+        out = torch.empty_like(U) if out is None else out
+        js_rhs(self.ctx, U, out)
+        return out
+
+    def max_dt(self, U, cfl):
+        return js_max_dt(self.ctx, U, cfl)
+
+    def step(self, U, dt, n_steps=1):
+        js_step(self.ctx, U, dt, n_steps)
+        return U
+
+    def rhs_vjp(self, U, lam, U_bar=None, p_bar=None):
+        import torch
+        U_bar = torch.empty_like(U) if U_bar is None else U_bar
+        p_bar = torch.zeros(JS_NPARAM, dtype=torch.float64, device=U.device) if p_bar is None else p_bar
+        js_rhs_vjp(self.ctx, U, lam, U_bar, p_bar)
+        return U_bar, p_bar
+
+    def step_vjp(self, U_n, dt, lam_np1, lam_n=None, p_bar=None):
+        import torch
+        lam_n = torch.empty_like(U_n) if lam_n is None else lam_n
+        p_bar = torch.zeros(JS_NPARAM, dtype=torch.float64, device=U_n.device) if p_bar is None else p_bar
+        js_step_vjp(self.ctx, U_n, dt, lam_np1, lam_n, p_bar)
+        return lam_n, p_bar
+
+    def status(self):
+        return js_sync_status(self.ctx)
+
+    def check(self):
+        _check(self.status(), "device status")
+
+    def ib_info(self):
+        return js_ib_info(self.ctx, self.nx, self.ny)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            js_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

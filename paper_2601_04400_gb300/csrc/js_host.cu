@@ -1,0 +1,438 @@
+// Host side of libjaxshock.so: solver contexts, immersed-boundary precomputation and the
+// C ABI declared in include/jaxshock.h.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "jaxshock.h"
+#include "js_internal.h"
+
+using js::BcArgs;
+using js::IbArgs;
+using js::Lay;
+using js::StageArgs;
+
+struct js_ctx {
+  js_grid g;
+  js_params p;
+  js_boundary b;
+  Lay lay;
+  cudaStream_t stream = nullptr;
+  double* N = nullptr;  // padded U^n / step output
+  double* A = nullptr;  // padded stage buffers
+  double* B = nullptr;
+  unsigned char* tag = nullptr;       // device [ny][nx] or null (no immersed body)
+  std::vector<unsigned char> tag_host;
+  int n_ghost = 0;
+  long long* ib_dst = nullptr;
+  long long* ib_src = nullptr;
+  double* ib_w = nullptr;
+  double* ib_nrm = nullptr;
+  int* err = nullptr;
+  unsigned long long* red = nullptr;
+  BcArgs bc;
+  // instrumentation
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev;  // 2 per timed stage launch
+  int ev_used = 0;
+  long long launches = 0;
+};
+
+namespace {
+
+#define JS_CUDA(call)                                       \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return JS_ERR_CUDA;              \
+  } while (0)
+
+bool grid_valid(const js_grid* g) {
+  if (!g || g->nx < 6 || g->ny < 1 || (g->ny > 1 && g->ny < 6)) return false;
+  if (!(g->dx > 0.0) || !(g->dy > 0.0)) return false;
+  if ((long long)g->nx * g->ny > (1LL << 31)) return false;
+  return true;
+}
+
+bool params_valid(const js_params* p, const js_boundary* b) {
+  if (!p || !b) return false;
+  if (!(p->gamma > 1.0) || !(p->mu >= 0.0) || !(p->nu >= 0.0)) return false;
+  if (p->mu > 0.0 && !(p->Pr > 0.0)) return false;
+  if (p->wall != 0 && p->wall != 1) return false;
+  for (int s = 0; s < 4; ++s)
+    if (b->kind[s] < JS_BC_TRANSMISSIVE || b->kind[s] > JS_BC_INFLOW) return false;
+  return true;
+}
+
+void set_bc(js_ctx* c) {
+  for (int s = 0; s < 4; ++s) {
+    c->bc.kind[s] = c->b.kind[s];
+    const double r = c->b.inflow[s][0], u = c->b.inflow[s][1], v = c->b.inflow[s][2], pr = c->b.inflow[s][3];
+    c->bc.inflow_cons[s][0] = r;
+    c->bc.inflow_cons[s][1] = r * u;
+    c->bc.inflow_cons[s][2] = r * v;
+    c->bc.inflow_cons[s][3] = pr / (c->p.gamma - 1.0) + 0.5 * r * (u * u + v * v);
+  }
+}
+
+// Ghost-cell IB tables (Sec. 2, Fig. 1(c)): solid = sdf < 0; ghost = solid cell with a fluid
+// cell in its 7x7 box; normal = normalised gradient of sdf (central differences, one-sided
+// at grid edges); image point = ghost centre - 2 sdf n; bilinear weights over the 2x2 block
+// of cell centres around it (clamped into the grid), restricted to fluid cells and
+// renormalised.
+int build_ib(js_ctx* c, const double* sdf) {
+  const int nx = c->g.nx, ny = c->g.ny;
+  const double dx = c->g.dx, dy = c->g.dy, x0 = c->g.x0, y0 = c->g.y0;
+  std::vector<unsigned char>& tag = c->tag_host;
+  tag.assign((size_t)nx * ny, 0);
+  auto S = [&](int i, int j) { return sdf[(size_t)j * nx + i]; };
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) tag[(size_t)j * nx + i] = (S(i, j) < 0.0) ? 1 : 0;
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      if (tag[(size_t)j * nx + i] == 0) continue;
+      bool fluid_near = false;
+      for (int jj = j - 3; jj <= j + 3 && !fluid_near; ++jj)
+        for (int ii = i - 3; ii <= i + 3; ++ii) {
+          if (ii < 0 || jj < 0 || ii >= nx || jj >= ny) continue;
+          if (!(S(ii, jj) < 0.0)) { fluid_near = true; break; }
+        }
+      if (fluid_near) tag[(size_t)j * nx + i] = 2;
+    }
+  std::vector<long long> dst, src;
+  std::vector<double> w, nrm;
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      if (tag[(size_t)j * nx + i] != 2) continue;
+      const int il = i > 0 ? i - 1 : i, ir = i < nx - 1 ? i + 1 : i;
+      const int jl = j > 0 ? j - 1 : j, jr = j < ny - 1 ? j + 1 : j;
+      const double gx = (S(ir, j) - S(il, j)) / ((ir - il) * dx);
+      const double gy = (S(i, jr) - S(i, jl)) / ((jr - jl) * dy);
+      const double gn = std::sqrt(gx * gx + gy * gy);
+      if (!(gn > 0.0)) return JS_ERR_IB;
+      const double nxv = gx / gn, nyv = gy / gn;
+      const double phi = S(i, j);
+      const double xg = x0 + (i + 0.5) * dx, yg = y0 + (j + 0.5) * dy;
+      const double xi = xg - 2.0 * phi * nxv, yi = yg - 2.0 * phi * nyv;
+      const double fx = (xi - x0) / dx - 0.5, fy = (yi - y0) / dy - 0.5;
+      if (!(fx >= -0.5 && fy >= -0.5 && fx <= nx - 0.5 && fy <= ny - 0.5)) return JS_ERR_IB;
+      int i0 = (int)std::floor(fx), j0 = (int)std::floor(fy);
+      i0 = i0 < 0 ? 0 : (i0 > nx - 2 ? nx - 2 : i0);
+      j0 = j0 < 0 ? 0 : (j0 > ny - 2 ? ny - 2 : j0);
+      const double tx = fx - i0, ty = fy - j0;
+      const int ci[4] = {i0, i0 + 1, i0, i0 + 1}, cj[4] = {j0, j0, j0 + 1, j0 + 1};
+      double wk[4] = {(1.0 - tx) * (1.0 - ty), tx * (1.0 - ty), (1.0 - tx) * ty, tx * ty};
+      double sum = 0.0;
+      for (int m = 0; m < 4; ++m) {
+        if (tag[(size_t)cj[m] * nx + ci[m]] != 0) wk[m] = 0.0;
+        sum = sum + wk[m];
+      }
+      if (!(sum > 0.0)) return JS_ERR_IB;
+      dst.push_back(c->lay.idx(i, j));
+      for (int m = 0; m < 4; ++m) {
+        src.push_back(c->lay.idx(ci[m], cj[m]));
+        w.push_back(wk[m] / sum);
+      }
+      nrm.push_back(nxv);
+      nrm.push_back(nyv);
+    }
+  c->n_ghost = (int)dst.size();
+  if (cudaMalloc(&c->tag, tag.size()) != cudaSuccess) return JS_ERR_NOMEM;
+  JS_CUDA(cudaMemcpy(c->tag, tag.data(), tag.size(), cudaMemcpyHostToDevice));
+  if (c->n_ghost > 0) {
+    const size_t ng = (size_t)c->n_ghost;
+    if (cudaMalloc(&c->ib_dst, ng * sizeof(long long)) != cudaSuccess ||
+        cudaMalloc(&c->ib_src, 4 * ng * sizeof(long long)) != cudaSuccess ||
+        cudaMalloc(&c->ib_w, 4 * ng * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->ib_nrm, 2 * ng * sizeof(double)) != cudaSuccess)
+      return JS_ERR_NOMEM;
+    JS_CUDA(cudaMemcpy(c->ib_dst, dst.data(), ng * sizeof(long long), cudaMemcpyHostToDevice));
+    JS_CUDA(cudaMemcpy(c->ib_src, src.data(), 4 * ng * sizeof(long long), cudaMemcpyHostToDevice));
+    JS_CUDA(cudaMemcpy(c->ib_w, w.data(), 4 * ng * sizeof(double), cudaMemcpyHostToDevice));
+    JS_CUDA(cudaMemcpy(c->ib_nrm, nrm.data(), 2 * ng * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  return JS_OK;
+}
+
+IbArgs ib_args(const js_ctx* c) {
+  IbArgs a;
+  a.n = c->n_ghost;
+  a.dst = c->ib_dst;
+  a.src = c->ib_src;
+  a.w = c->ib_w;
+  a.nrm = c->ib_nrm;
+  return a;
+}
+
+// stage arguments common to js_rhs and js_step; cx, cy, av* and rk_* set by the caller
+StageArgs base_args(const js_ctx* c) {
+  StageArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.tag = c->tag;
+  a.err = c->err;
+  a.lay = c->lay;
+  a.gamma = c->p.gamma;
+  a.gm1 = c->p.gamma - 1.0;
+  a.g1 = 1.0 / (c->p.gamma - 1.0);
+  const double mu = c->p.mu, dx = c->g.dx, dy = c->g.dy;
+  const double kappa = (mu > 0.0) ? mu * c->p.gamma / ((c->p.gamma - 1.0) * c->p.Pr) : 0.0;
+  a.vx = js::ViscC{(4.0 / 3.0) * mu / dx, (2.0 / 3.0) * mu / (4.0 * dy), mu / dx, mu / (4.0 * dy), kappa / dx};
+  a.vy = js::ViscC{(4.0 / 3.0) * mu / dy, (2.0 / 3.0) * mu / (4.0 * dx), mu / dy, mu / (4.0 * dx), kappa / dy};
+  a.has_av = c->p.nu > 0.0 ? 1 : 0;
+  return a;
+}
+
+int fill_halos(js_ctx* c, double* X) {
+  JS_CUDA(js::launch_ib_fill(X, c->lay, ib_args(c), c->p.gamma, c->p.wall, c->stream));
+  JS_CUDA(js::launch_bc_fill(X, c->lay, c->bc, c->stream));
+  c->launches += (c->n_ghost > 0) ? 2 : 1;
+  return JS_OK;
+}
+
+// fused stage kernel, bracketed by events while profiling
+int stage(js_ctx* c, const StageArgs& a, bool visc, bool rhs) {
+  const bool timed = c->profiling && c->ev_used + 2 <= (int)c->ev.size();
+  if (timed) JS_CUDA(cudaEventRecord(c->ev[c->ev_used], c->stream));
+  JS_CUDA(js::launch_stage(a, visc, rhs, c->stream));
+  if (timed) {
+    JS_CUDA(cudaEventRecord(c->ev[c->ev_used + 1], c->stream));
+    c->ev_used += 2;
+  }
+  ++c->launches;
+  return JS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* js_strerror(int code) {
+  switch (code) {
+    case JS_OK: return "ok";
+    case JS_ERR_ARG: return "invalid argument";
+    case JS_ERR_CUDA: return "CUDA runtime error";
+    case JS_ERR_NONPHYSICAL: return "non-physical state (rho <= 0, p <= 0 or NaN in a fluid cell)";
+    case JS_ERR_TIMEOUT: return "bounded device wait timed out";
+    case JS_ERR_IB: return "immersed boundary: image point outside the domain or without fluid neighbour";
+    case JS_ERR_NOMEM: return "device allocation failed";
+    default: return "unknown error";
+  }
+}
+
+void js_destroy(js_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
+  cudaFree(c->N); cudaFree(c->A); cudaFree(c->B);
+  cudaFree(c->tag);
+  cudaFree(c->ib_dst); cudaFree(c->ib_src); cudaFree(c->ib_w); cudaFree(c->ib_nrm);
+  cudaFree(c->err); cudaFree(c->red);
+  for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+  delete c;
+}
+
+int js_create(const js_grid* grid, const js_params* params, const js_boundary* bc, const double* sdf_host,
+              void* stream, js_ctx** out) {
+  if (!out) return JS_ERR_ARG;
+  *out = nullptr;
+  if (!grid_valid(grid) || !params_valid(params, bc)) return JS_ERR_ARG;
+  if (sdf_host && grid->ny == 1) return JS_ERR_ARG;
+  js_ctx* c = new (std::nothrow) js_ctx();
+  if (!c) return JS_ERR_NOMEM;
+  c->g = *grid;
+  c->p = *params;
+  c->b = *bc;
+  c->stream = (cudaStream_t)stream;
+  Lay& L = c->lay;
+  L.nx = grid->nx;
+  L.ny = grid->ny;
+  L.gy = (grid->ny == 1) ? 0 : 3;
+  L.pitch = ((grid->nx + 6) + 3) / 4 * 4;  // 32-byte aligned rows
+  L.H = grid->ny + 2 * L.gy;
+  L.plane = ((long long)L.pitch * L.H + 31) / 32 * 32;
+  const size_t bytes = sizeof(double) * 4 * (size_t)L.plane;
+  if (cudaMalloc(&c->N, bytes) != cudaSuccess || cudaMalloc(&c->A, bytes) != cudaSuccess ||
+      cudaMalloc(&c->B, bytes) != cudaSuccess || cudaMalloc(&c->err, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&c->red, 4 * sizeof(unsigned long long)) != cudaSuccess) {
+    js_destroy(c);
+    return JS_ERR_NOMEM;
+  }
+  // padding never holds NaN garbage
+  if (cudaMemset(c->N, 0, bytes) != cudaSuccess || cudaMemset(c->A, 0, bytes) != cudaSuccess ||
+      cudaMemset(c->B, 0, bytes) != cudaSuccess || cudaMemset(c->err, 0, sizeof(int)) != cudaSuccess) {
+    js_destroy(c);
+    return JS_ERR_CUDA;
+  }
+  set_bc(c);
+  if (sdf_host) {
+    const int rc = build_ib(c, sdf_host);
+    if (rc != JS_OK) {
+      js_destroy(c);
+      return rc;
+    }
+  }
+  *out = c;
+  return JS_OK;
+}
+
+int js_set_params(js_ctx* c, const js_params* params, const js_boundary* bc) {
+  if (!c || !params_valid(params, bc)) return JS_ERR_ARG;
+  c->p = *params;
+  c->b = *bc;
+  set_bc(c);
+  return JS_OK;
+}
+
+int js_set_stream(js_ctx* c, void* stream) {
+  if (!c) return JS_ERR_ARG;
+  c->stream = (cudaStream_t)stream;
+  return JS_OK;
+}
+
+int js_prim_to_cons(js_ctx* c, const double* W, double* U) {
+  if (!c || !W || !U) return JS_ERR_ARG;
+  JS_CUDA(js::launch_prim_to_cons(W, U, (long long)c->g.nx * c->g.ny, c->p.gamma, c->stream));
+  return JS_OK;
+}
+
+int js_rhs(js_ctx* c, const double* U, double* dUdt) {
+  if (!c || !U || !dUdt || U == dUdt) return JS_ERR_ARG;
+  JS_CUDA(js::launch_pack(U, c->N, c->lay, c->stream));
+  ++c->launches;
+  int rc = fill_halos(c, c->N);
+  if (rc) return rc;
+  StageArgs a = base_args(c);
+  a.Uin = c->N;
+  a.Un = nullptr;
+  a.Uout = dUdt;
+  a.cx = 1.0 / c->g.dx;
+  a.cy = 1.0 / c->g.dy;
+  a.avx = c->p.nu / (c->g.dx * c->g.dx);
+  a.avy = c->p.nu / (c->g.dy * c->g.dy);
+  a.rk_a = 0.0;
+  a.rk_b = 1.0;
+  a.use_un = 0;
+  return stage(c, a, c->p.mu > 0.0, true);
+}
+
+int js_max_dt(js_ctx* c, const double* U, double cfl, double* dt_out) {
+  if (!c || !U || !dt_out || !(cfl > 0.0)) return JS_ERR_ARG;
+  JS_CUDA(js::launch_cfl(U, c->lay, c->tag, c->p.gamma, c->g.dx, c->g.dy, c->red, c->stream));
+  c->launches += 2;
+  unsigned long long h[2];
+  JS_CUDA(cudaMemcpyAsync(h, c->red, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  JS_CUDA(cudaStreamSynchronize(c->stream));
+  double rate, rmin;
+  std::memcpy(&rate, &h[0], sizeof(double));
+  std::memcpy(&rmin, &h[1], sizeof(double));
+  double dt = cfl / rate;
+  if (c->p.mu > 0.0) {
+    const double h2 = (c->g.ny > 1) ? (c->g.dx < c->g.dy ? c->g.dx : c->g.dy) : c->g.dx;
+    const double lim = (4.0 / 3.0 < c->p.gamma / c->p.Pr) ? c->p.gamma / c->p.Pr : 4.0 / 3.0;
+    const double dtv = cfl * h2 * h2 * rmin / (2.0 * c->p.mu * lim);
+    dt = (dtv < dt) ? dtv : dt;
+  }
+  *dt_out = dt;
+  if (!std::isfinite(dt) || !(dt > 0.0)) return JS_ERR_NONPHYSICAL;
+  return JS_OK;
+}
+
+int js_step(js_ctx* c, double* U, double dt, int n_steps) {
+  if (!c || !U || n_steps < 0 || !(dt > 0.0)) return JS_ERR_ARG;
+  if (n_steps == 0) return JS_OK;
+  JS_CUDA(js::launch_pack(U, c->N, c->lay, c->stream));
+  StageArgs a = base_args(c);
+  a.cx = dt / c->g.dx;
+  a.cy = dt / c->g.dy;
+  a.avx = dt * c->p.nu / (c->g.dx * c->g.dx);
+  a.avy = dt * c->p.nu / (c->g.dy * c->g.dy);
+  const bool visc = c->p.mu > 0.0;
+  double* in[3] = {c->N, c->A, c->B};
+  double* outp[3] = {c->A, c->B, c->N};
+  const double ra[3] = {0.0, 0.75, 1.0 / 3.0};
+  const double rb[3] = {1.0, 0.25, 2.0 / 3.0};
+  for (int k = 0; k < n_steps; ++k) {
+    for (int s = 0; s < 3; ++s) {
+      int rc = fill_halos(c, in[s]);
+      if (rc) return rc;
+      a.Uin = in[s];
+      a.Un = c->N;
+      a.Uout = outp[s];
+      a.rk_a = ra[s];
+      a.rk_b = rb[s];
+      a.use_un = (s > 0) ? 1 : 0;
+      rc = stage(c, a, visc, false);
+      if (rc) return rc;
+    }
+  }
+  JS_CUDA(js::launch_unpack(c->N, U, c->lay, c->stream));
+  c->launches += 2;  // pack + unpack
+  return JS_OK;
+}
+
+int js_rhs_vjp(js_ctx* c, const double* U, const double* lam, double* U_bar, double* p_bar) {
+  (void)c; (void)U; (void)lam; (void)U_bar; (void)p_bar;
+  return JS_ERR_ARG;
+}
+
+int js_step_vjp(js_ctx* c, const double* U_n, double dt, const double* lam_np1, double* lam_n, double* p_bar) {
+  (void)c; (void)U_n; (void)dt; (void)lam_np1; (void)lam_n; (void)p_bar;
+  return JS_ERR_ARG;
+}
+
+int js_sync_status(js_ctx* c) {
+  if (!c) return JS_ERR_ARG;
+  int h = 0;
+  JS_CUDA(cudaMemcpyAsync(&h, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  JS_CUDA(cudaStreamSynchronize(c->stream));
+  JS_CUDA(cudaMemsetAsync(c->err, 0, sizeof(int), c->stream));
+  JS_CUDA(cudaStreamSynchronize(c->stream));
+  if (h & js::ERR_TIMEOUT_BIT) return JS_ERR_TIMEOUT;
+  if (h & js::ERR_NONPHYSICAL_BIT) return JS_ERR_NONPHYSICAL;
+  return JS_OK;
+}
+
+int js_profile_begin(js_ctx* c, int capacity) {
+  if (!c || capacity < 0) return JS_ERR_ARG;
+  while ((int)c->ev.size() < 2 * capacity) {
+    cudaEvent_t e;
+    JS_CUDA(cudaEventCreate(&e));
+    c->ev.push_back(e);
+  }
+  c->ev_used = 0;
+  c->launches = 0;
+  c->profiling = true;
+  return JS_OK;
+}
+
+int js_profile_end(js_ctx* c, double* stage_ms, int* stage_launches, long long* kernel_launches) {
+  if (!c) return JS_ERR_ARG;
+  JS_CUDA(cudaStreamSynchronize(c->stream));
+  double total = 0.0;
+  for (int k = 0; k + 1 < c->ev_used; k += 2) {
+    float ms = 0.0f;
+    JS_CUDA(cudaEventElapsedTime(&ms, c->ev[k], c->ev[k + 1]));
+    total += ms;
+  }
+  if (stage_ms) *stage_ms = total;
+  if (stage_launches) *stage_launches = c->ev_used / 2;
+  if (kernel_launches) *kernel_launches = c->launches;
+  c->profiling = false;
+  c->ev_used = 0;
+  return JS_OK;
+}
+
+int js_ib_info(js_ctx* c, int* n_ghost, unsigned char* tag_host) {
+  if (!c || !n_ghost) return JS_ERR_ARG;
+  *n_ghost = c->n_ghost;
+  if (tag_host) {
+    const size_t n = (size_t)c->g.nx * c->g.ny;
+    if (c->tag_host.empty()) std::memset(tag_host, 0, n);
+    else std::memcpy(tag_host, c->tag_host.data(), n);
+  }
+  return JS_OK;
+}
+
+}  // extern "C"

@@ -113,11 +113,13 @@ def sod(n=200, t_end=0.2, cfl=0.5):
                    meta=dict(left=(1.0, 0.0, 1.0), right=(0.125, 0.0, 0.1), x_disc=0.5))
 
 
-def riemann2d(n=1024, t_end=0.8, cfl=0.5, split=0.8):
-    """2D four-quadrant Riemann problem on [0,1]^2, transmissive boundaries."""
-    dx = 1.0 / n
-    X, Y = cell_centres(n, n, 0.0, 0.0, dx, dx)
-    W = np.zeros((4, n, n))
+def riemann2d(n=1024, t_end=0.8, cfl=0.5, split=0.8, ny=None):
+    """2D four-quadrant Riemann problem on [0,1]^2, transmissive boundaries (n x ny cells)."""
+    nx = n
+    ny = n if ny is None else ny
+    dx, dy = 1.0 / nx, 1.0 / ny
+    X, Y = cell_centres(nx, ny, 0.0, 0.0, dx, dy)
+    W = np.zeros((4, ny, nx))
     ne = (X >= split) & (Y >= split)
     nw = (X < split) & (Y >= split)
     sw = (X < split) & (Y < split)
@@ -126,7 +128,7 @@ def riemann2d(n=1024, t_end=0.8, cfl=0.5, split=0.8):
                      (sw, (0.138, 1.206, 1.206, 0.029)), (se, (0.5323, 0.0, 1.206, 0.3))):
         for c in range(4):
             W[c][mask] = st[c]
-    return Problem("riemann2d", n, n, 0.0, 0.0, dx, dx, bc=(0, 0, 0, 0), W0=W, cfl=cfl, t_end=t_end)
+    return Problem("riemann2d", nx, ny, 0.0, 0.0, dx, dy, bc=(0, 0, 0, 0), W0=W, cfl=cfl, t_end=t_end)
 
 
 def shock_cylinder(nx=2048, ny=1024, mach=2.0, Re=1000.0, Pr=0.72, gamma=1.4, D=1.0,
