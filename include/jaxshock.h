@@ -126,6 +126,24 @@ int js_ib_info(js_ctx* ctx, int* n_ghost, unsigned char* tag_host);
 int js_profile_begin(js_ctx* ctx, int capacity);
 int js_profile_end(js_ctx* ctx, double* stage_ms, int* stage_launches, long long* kernel_launches);
 
+/* Allocation-free CFL time step -- the paper has no counterpart.  It serves callers that
+ * cannot allocate device memory, such as a host application or plugin that owns every
+ * device allocation through its own pool and forbids libraries to call cudaMalloc.  Same
+ * result as js_max_dt (the same IEEE operation order), without a context:
+ *   grid, params : the problem (only nx, ny, dx, dy, gamma, mu, Pr are used)
+ *   U            : device [4][ny][nx];  tag: optional device uint8 [ny][nx], 0 = fluid
+ *                  cell (only fluid cells count), or NULL for all cells
+ *   dt_out       : host; the stream is synchronised before returning.
+ * The reduction's scratch is one 64 KiB file-scope device array per GPU, kept until the
+ * process exits: grids above JS_NOALLOC_MAX_CELLS cells return JS_ERR_ARG.  All calls on a
+ * device share the array and it keeps the last call's partial results, so calls whose
+ * kernels overlap on the GPU race -- serialise them.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  Calls no allocating routine. */
+#define JS_NOALLOC_MAX_CELLS 8388608
+int js_max_dt_noalloc(const js_grid* grid, const js_params* params, const double* U,
+                      const unsigned char* tag, double cfl, void* stream, double* dt_out);
+
 /* Human-readable text of a JS_* code (static storage). */
 const char* js_strerror(int code);
 

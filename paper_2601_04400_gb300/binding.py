@@ -59,6 +59,7 @@ SIGNATURES = {
     "js_ib_info": (_I, [_P, C.POINTER(_I), _P]),
     "js_profile_begin": (_I, [_P, _I]),
     "js_profile_end": (_I, [_P, C.POINTER(_D), C.POINTER(_I), C.POINTER(C.c_longlong)]),
+    "js_max_dt_noalloc": (_I, [C.POINTER(JsGrid), C.POINTER(JsParams), _P, _P, _D, _P, C.POINTER(_D)]),
     "js_strerror": (C.c_char_p, [_I]),
 }
 
@@ -181,6 +182,21 @@ def js_profile_end(ctx):
     ms, n, k = C.c_double(0.0), C.c_int(0), C.c_longlong(0)
     _check(lib().js_profile_end(ctx, C.byref(ms), C.byref(n), C.byref(k)), "js_profile_end")
     return ms.value, n.value, k.value
+
+
+def js_max_dt_noalloc(grid, params, U, tag=None, cfl=0.5, stream=None):
+    """Context-free CFL step whose scratch is a static device array (no device allocation).
+    tag: optional uint8 CUDA tensor [ny, nx] (0 = fluid)."""
+    import torch
+    tp = None
+    if tag is not None:
+        if not (tag.is_cuda and tag.dtype == torch.uint8 and tag.is_contiguous()):
+            raise ValueError("tag must be a contiguous uint8 CUDA tensor")
+        tp = C.c_void_p(tag.data_ptr())
+    dt = C.c_double(0.0)
+    _check(lib().js_max_dt_noalloc(C.byref(grid), C.byref(params), _ptr(U), tp, float(cfl), _stream_ptr(stream),
+                                   C.byref(dt)), "js_max_dt_noalloc")
+    return dt.value
 
 
 def js_sync_status(ctx):
