@@ -1,0 +1,102 @@
+"""Differentiable rollouts of the SSP-RK3 solver step (Sec. 2: U^{n+k} = S(U^{n+k-1}, theta),
+gradients by the chain rule through the unrolled steps, Fig. 1(d)).
+
+Forward steps run js_step; the backward pass walks the steps in reverse with js_step_vjp.
+Only every `checkpoint_every`-th state is kept (default ceil(sqrt(n))); each segment is
+recomputed from its checkpoint during the backward pass, so a rollout of n steps holds about
+2 sqrt(n) states instead of n.
+
+theta is the 20-entry parameter vector of the library (gamma, mu, Pr, nu, then the inflow
+state rho, u, v, p of the x-low, x-high, y-low and y-high sides); its gradient is returned
+for gamma, for mu and Pr when mu > 0, for nu when nu > 0 and for the inflow states of inflow
+sides (the other entries receive zero).
+"""
+import math
+
+import torch
+
+from . import binding as B
+
+
+def theta_of(solver):
+    """Current parameter vector of a Solver as a float64 CPU tensor."""
+    sp = solver._spec
+    t = torch.zeros(B.JS_NPARAM, dtype=torch.float64)
+    t[0], t[1], t[2], t[3] = sp["gamma"], sp["mu"], sp["Pr"], sp["nu"]
+    t[4:] = torch.as_tensor(sp["inflow"].reshape(16))
+    return t
+
+
+def _apply_theta(solver, theta):
+    th = theta.detach().to("cpu", torch.float64)
+    solver.set_params(gamma=float(th[0]), mu=float(th[1]), Pr=float(th[2]), nu=float(th[3]),
+                      inflow=th[4:].numpy().reshape(4, 4))
+
+
+class _Rollout(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, U0, theta, solver, dts, outputs, every):
+        _apply_theta(solver, theta)
+        n = len(dts)
+        want = {k: i for i, k in enumerate(outputs)}
+        U = U0.detach().clone().contiguous()
+        ckpts = []
+        outs = [None] * len(outputs)
+        if 0 in want:
+            outs[want[0]] = U.clone()
+        for k in range(n):
+            if k % every == 0:
+                ckpts.append(U.clone())
+            solver.step(U, dts[k], 1)
+            if k + 1 in want:
+                outs[want[k + 1]] = U.clone()
+        ctx.solver, ctx.dts, ctx.outputs, ctx.every = solver, list(dts), list(outputs), every
+        ctx.ckpts = ckpts
+        ctx.theta = theta.detach().clone()
+        return torch.stack(outs)
+
+    @staticmethod
+    def backward(ctx, g):
+        solver, dts, every = ctx.solver, ctx.dts, ctx.every
+        _apply_theta(solver, ctx.theta)
+        n = len(dts)
+        inject = {}
+        for i, k in enumerate(ctx.outputs):
+            inject[k] = g[i] if k not in inject else inject[k] + g[i]
+        lam = torch.zeros_like(g[0])
+        if n in inject:
+            lam += inject[n]
+        pbar = torch.zeros(B.JS_NPARAM, dtype=torch.float64, device=g.device)
+        scratch = torch.empty_like(lam)
+        for seg in reversed(range(len(ctx.ckpts))):
+            start = seg * every
+            stop = min(start + every, n)
+            states = [ctx.ckpts[seg]]
+            U = ctx.ckpts[seg].clone()
+            for k in range(start, stop - 1):
+                solver.step(U, dts[k], 1)
+                states.append(U.clone())
+            for k in reversed(range(start, stop)):
+                solver.step_vjp(states[k - start], dts[k], lam, lam_n=scratch, p_bar=pbar)
+                lam, scratch = scratch, lam
+                if k in inject:
+                    lam = lam + inject[k]
+        st = solver.status()
+        if st != 0:
+            raise B.JsError(st, "rollout backward")
+        return lam, pbar.to(ctx.theta.device), None, None, None, None
+
+
+def rollout(solver, U0, theta, dts, outputs=None, checkpoint_every=None):
+    """Differentiable rollout.
+
+    solver: binding.Solver; U0: float64 CUDA tensor [4, ny, nx]; theta: float64 tensor [20]
+    (see module docstring); dts: list of step sizes (one per step).  outputs: step indices
+    whose states are returned stacked (default: only the final state, index len(dts)).
+    Returns a tensor [len(outputs), 4, ny, nx] (or [4, ny, nx] for the default)."""
+    n = len(dts)
+    default = outputs is None
+    outputs = [n] if default else list(outputs)
+    every = checkpoint_every or max(1, int(math.ceil(math.sqrt(max(n, 1)))))
+    out = _Rollout.apply(U0, theta, solver, list(dts), outputs, every)
+    return out[0] if default else out

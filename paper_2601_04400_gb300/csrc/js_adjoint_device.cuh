@@ -1,0 +1,270 @@
+// Reverse-mode building blocks of the FP64 right-hand side (gradient chain rule of Sec. 2,
+// applied to the discrete operator).  Each routine differentiates exactly the forward
+// formulation used by the stage kernel (js_device.cuh): cell-centred WENO5 with product
+// weights, HLLC on the upwind side with the standard star-state energy, the viscous face flux
+// and the cons -> prim map.  Non-smooth points follow the oracle's convention: min/max pass
+// the derivative to their first argument on ties, sign(s*) = 0 averages both branches.
+#pragma once
+#include "js_device.cuh"
+
+namespace js {
+
+// quotient a/b with the refined reciprocal it used (r ~ 1/b to ~2^-44, enough for a derivative)
+__device__ __forceinline__ double quot_r(double a, double b, double& r) {
+  r = rcp_seed(b);
+  const double e = fma(-b, r, 1.0);
+  r = fma(r, e, r);
+  const double q = a * r;
+  const double res = fma(-b, q, a);
+  return fma(r, res, q);
+}
+
+// ---------------------------------------------------------------------------------------
+// WENO5, cell-centred: forward with the internals the reverse pass needs
+// ---------------------------------------------------------------------------------------
+// saved per cell and variable: s0, s1, s2 (4 beta_k + 4 eps), qL, rL, qR, rR where
+// q = num/den of the face state (state = q_i + q/6) and r ~ 1/den.
+constexpr int WENO_SAVE = 7;
+
+struct Dl {  // first differences d_{i-3/2}, d_{i-1/2}, d_{i+1/2}, d_{i+3/2}
+  double m2, m1, p1, p2;
+};
+
+__device__ __forceinline__ void weno_cell_fwd(double q0, const Dl& d, double& Lf, double& Rf, double sv[WENO_SAVE]) {
+  const double D0 = d.m1 - d.m2, D1 = d.p1 - d.m1, D2 = d.p2 - d.p1;
+  const double t0 = fma(2.0, d.m1, D0), t1 = d.m1 + d.p1, t2 = fma(-2.0, d.p1, D2);
+  const double s0 = fma(K13 * D0, D0, fma(t0, t0, EPS4));
+  const double s1 = fma(K13 * D1, D1, fma(t1, t1, EPS4));
+  const double s2 = fma(K13 * D2, D2, fma(t2, t2, EPS4));
+  const double p01 = s0 * s1, p02 = s0 * s2, p12 = s1 * s2;
+  const double w0 = p12 * p12, w1 = p02 * p02, w2 = p01 * p01;
+  const double w1_6 = 6.0 * w1;
+  double rL, rR;
+  const double w2_3 = 3.0 * w2;
+  const double e0L = fma(-2.0, d.m2, 5.0 * d.m1), e1L = fma(2.0, d.p1, d.m1), e2L = fma(4.0, d.p1, -d.p2);
+  const double qL = quot_r(fma(w0, e0L, fma(w1_6, e1L, w2_3 * e2L)), w0 + w1_6 + w2_3, rL);
+  const double w0_3 = 3.0 * w0;
+  const double e0R = fma(-4.0, d.m1, d.m2), e1R = fma(-2.0, d.m1, -d.p1), e2R = fma(2.0, d.p2, -5.0 * d.p1);
+  const double qR = quot_r(fma(w0_3, e0R, fma(w1_6, e1R, w2 * e2R)), w0_3 + w1_6 + w2, rR);
+  Lf = fma(qL, SIXTH, q0);
+  Rf = fma(qR, SIXTH, q0);
+  sv[0] = s0; sv[1] = s1; sv[2] = s2;
+  sv[3] = qL; sv[4] = rL; sv[5] = qR; sv[6] = rR;
+}
+
+// Reverse of weno_cell_fwd: given the adjoints Lb (state at i+1/2) and Rb (state at i-1/2),
+// returns the adjoints of q_{i-2..i+2} in g[0..4] (overwritten).
+__device__ __forceinline__ void weno_cell_vjp(const Dl& d, const double sv[WENO_SAVE], double Lb, double Rb,
+                                              double g[5]) {
+  const double D0 = d.m1 - d.m2, D1 = d.p1 - d.m1, D2 = d.p2 - d.p1;
+  const double t0 = fma(2.0, d.m1, D0), t1 = d.m1 + d.p1, t2 = fma(-2.0, d.p1, D2);
+  const double s0 = sv[0], s1 = sv[1], s2 = sv[2];
+  const double p01 = s0 * s1, p02 = s0 * s2, p12 = s1 * s2;
+  const double w0 = p12 * p12, w1 = p02 * p02, w2 = p01 * p01;
+  const double w1_6 = 6.0 * w1, w2_3 = 3.0 * w2, w0_3 = 3.0 * w0;
+  const double e0L = fma(-2.0, d.m2, 5.0 * d.m1), e1L = fma(2.0, d.p1, d.m1), e2L = fma(4.0, d.p1, -d.p2);
+  const double e0R = fma(-4.0, d.m1, d.m2), e1R = fma(-2.0, d.m1, -d.p1), e2R = fma(2.0, d.p2, -5.0 * d.p1);
+  // state = q_i + q/6, q = num/den
+  const double nL = (SIXTH * Lb) * sv[4], dL = -nL * sv[3];
+  const double nR = (SIXTH * Rb) * sv[6], dR = -nR * sv[5];
+  // left-biased: num = w0 e0 + 6w1 e1 + 3w2 e2, den = w0 + 6w1 + 3w2
+  // right-biased: num = 3w0 e0 + 6w1 e1 + w2 e2, den = 3w0 + 6w1 + w2
+  const double bw0 = fma(nL, e0L, dL) + 3.0 * fma(nR, e0R, dR);
+  const double bw1 = 6.0 * (fma(nL, e1L, dL) + fma(nR, e1R, dR));
+  const double bw2 = fma(3.0, fma(nL, e2L, dL), fma(nR, e2R, dR));
+  const double be0L = nL * w0, be1L = nL * w1_6, be2L = nL * w2_3;
+  const double be0R = nR * w0_3, be1R = nR * w1_6, be2R = nR * w2;
+  // w0 = p12^2, w1 = p02^2, w2 = p01^2
+  const double bp12 = 2.0 * p12 * bw0, bp02 = 2.0 * p02 * bw1, bp01 = 2.0 * p01 * bw2;
+  const double bs0 = fma(bp01, s1, bp02 * s2);
+  const double bs1 = fma(bp01, s0, bp12 * s2);
+  const double bs2 = fma(bp02, s0, bp12 * s1);
+  // s_k = 13/3 D_k^2 + t_k^2 + 4 eps
+  double bD0 = (2.0 * K13) * D0 * bs0, bD1 = (2.0 * K13) * D1 * bs1, bD2 = (2.0 * K13) * D2 * bs2;
+  const double bt0 = 2.0 * t0 * bs0, bt1 = 2.0 * t1 * bs1, bt2 = 2.0 * t2 * bs2;
+  double bm2 = 0.0, bm1 = 0.0, bp1 = 0.0, bp2 = 0.0;
+  // t0 = D0 + 2 d_m1, t1 = d_m1 + d_p1, t2 = D2 - 2 d_p1
+  bD0 += bt0;
+  bm1 += 2.0 * bt0 + bt1;
+  bp1 += bt1 - 2.0 * bt2;
+  bD2 += bt2;
+  // candidate corrections
+  bm2 += -2.0 * be0L + be0R;
+  bm1 += 5.0 * be0L + be1L - 4.0 * be0R - 2.0 * be1R;
+  bp1 += 2.0 * be1L + 4.0 * be2L - be1R - 5.0 * be2R;
+  bp2 += -be2L + 2.0 * be2R;
+  // D0 = d_m1 - d_m2, D1 = d_p1 - d_m1, D2 = d_p2 - d_p1
+  bm1 += bD0 - bD1;
+  bm2 -= bD0;
+  bp1 += bD1 - bD2;
+  bp2 += bD2;
+  // d's of q_{i-2..i+2}; the centre value also enters both states directly
+  g[0] = -bm2;
+  g[1] = bm2 - bm1;
+  g[2] = (bm1 - bp1) + (Lb + Rb);
+  g[3] = bp1 - bp2;
+  g[4] = bp2;
+}
+
+// ---------------------------------------------------------------------------------------
+// HLLC forward + reverse (face-normal frame)
+// ---------------------------------------------------------------------------------------
+struct Face4 {
+  double r, un, ut, p;
+};
+
+// reverse of hllc_branch for one side; adds to the side adjoints and returns the adjoints
+// of s, d, m, spm, ss; gb accumulates d/dgamma.
+__device__ __forceinline__ void hllc_branch_vjp(double r, double un, double ut, double p, double s, double d, double m,
+                                                double spm, double ss, const Gas& g, const double Fb[4], double& br,
+                                                double& bun, double& but, double& bp, double& bs, double& bd,
+                                                double& bm, double& bspm, double& bss, double& gb) {
+  const double ke = fma(un, un, ut * ut);
+  const double E = fma(0.5 * r, ke, p * g.g1);
+  const double inv = recip(s - ss);
+  const double rs = m * inv, fac = d * inv;
+  const double Us1 = rs * ss, Us2 = rs * ut;
+  const double X = fma(p, inv, Us1);
+  const double Es = fma(ss - un, X, fac * E);
+  const double mom = r * un;
+  // F0 = mom + spm (rs - r); F1 = mom un + p + spm (Us1 - mom);
+  // F2 = mom ut + spm (Us2 - r ut); F3 = (E + p) un + spm (Es - E)
+  bspm = Fb[0] * (rs - r) + Fb[1] * (Us1 - mom) + Fb[2] * (Us2 - r * ut) + Fb[3] * (Es - E);
+  double bmom = Fb[0] + Fb[1] * (un - spm) + Fb[2] * ut;
+  double brs = Fb[0] * spm;
+  br = -spm * (Fb[0] + Fb[2] * ut);
+  bun = Fb[1] * mom + Fb[3] * (E + p);
+  but = Fb[2] * (mom - spm * r);
+  bp = Fb[1] + Fb[3] * un;
+  double bUs1 = Fb[1] * spm;
+  const double bUs2 = Fb[2] * spm;
+  double bE = Fb[3] * (un - spm);
+  const double bEs = Fb[3] * spm;
+  // Es = fac E + (ss - un) X
+  const double bfac = bEs * E;
+  bE += bEs * fac;
+  const double bX = bEs * (ss - un);
+  bss = bEs * X;
+  bun -= bEs * X;
+  // X = p inv + Us1
+  bp += bX * inv;
+  double binv = bX * p;
+  bUs1 += bX;
+  // Us2 = rs ut, Us1 = rs ss
+  brs += bUs2 * ut + bUs1 * ss;
+  but += bUs2 * rs;
+  bss += bUs1 * rs;
+  // fac = d inv, rs = m inv
+  bd = bfac * inv;
+  bm = brs * inv;
+  binv += bfac * d + brs * m;
+  // inv = 1/(s - ss)
+  const double t = binv * inv * inv;
+  bs = -t;
+  bss += t;
+  // mom = r un
+  br += bmom * un;
+  bun += bmom * r;
+  // E = 0.5 r ke + p/(gamma - 1)
+  br += bE * 0.5 * ke;
+  const double bke = bE * 0.5 * r;
+  bp += bE * g.g1;
+  gb -= bE * p * g.g1 * g.g1;
+  bun += 2.0 * un * bke;
+  but += 2.0 * ut * bke;
+}
+
+// Reverse of hllc(): F adjoint Fb (normal frame) -> adjoints of both face states (added).
+__device__ __forceinline__ void hllc_vjp(const Face4& L, const Face4& R, const Gas& g, const double Fb[4], Face4& bL,
+                                         Face4& bR, double& gb) {
+  const double gpL = g.gamma * L.p, gpR = g.gamma * R.p;
+  const double yL = rsqrt_nr(gpL * L.r), yR = rsqrt_nr(gpR * R.r);
+  const double aL = gpL * yL, aR = gpR * yR;
+  const double xL = L.un - aL, xR = R.un - aR;  // candidates of sL
+  const double zL = L.un + aL, zR = R.un + aR;  // candidates of sR
+  const bool sL_right = xR < xL;                // min ties go to the first argument
+  const bool sR_right = zL < zR;                // max ties go to the first argument
+  const double sL = sL_right ? xR : xL, sR = sR_right ? zR : zL;
+  const double dL = sL - L.un, dR = sR - R.un;
+  const double mL = L.r * dL, mR = R.r * dR;
+  const double num = fma(-R.un, mR, fma(L.un, mL, R.p - L.p));
+  const double den = mL - mR;
+  double rden;
+  const double ss = quot_r(num, den, rden);
+  double bsL = 0.0, bsR = 0.0, bdL = 0.0, bdR = 0.0, bmL = 0.0, bmR = 0.0, bss = 0.0;
+  auto side = [&](bool left, double scale) {
+    double Fs[4] = {scale * Fb[0], scale * Fb[1], scale * Fb[2], scale * Fb[3]};
+    double br, bun, but, bp, bs, bd, bm, bspm, bs2;
+    if (left) {
+      const double spm = fmin(0.0, sL);
+      hllc_branch_vjp(L.r, L.un, L.ut, L.p, sL, dL, mL, spm, ss, g, Fs, br, bun, but, bp, bs, bd, bm, bspm, bs2, gb);
+      bL.r += br; bL.un += bun; bL.ut += but; bL.p += bp;
+      bsL += bs + ((sL < 0.0) ? bspm : 0.0);
+      bdL += bd;
+      bmL += bm;
+    } else {
+      const double spm = fmax(0.0, sR);
+      hllc_branch_vjp(R.r, R.un, R.ut, R.p, sR, dR, mR, spm, ss, g, Fs, br, bun, but, bp, bs, bd, bm, bspm, bs2, gb);
+      bR.r += br; bR.un += bun; bR.ut += but; bR.p += bp;
+      bsR += bs + ((sR > 0.0) ? bspm : 0.0);
+      bdR += bd;
+      bmR += bm;
+    }
+    bss += bs2;
+  };
+  if (ss == 0.0) {
+    side(true, 0.5);
+    side(false, 0.5);
+  } else {
+    side(ss > 0.0, 1.0);
+  }
+  // ss = num/den, den = mL - mR, num = (pR - pL) + uL mL - uR mR
+  const double bnum = bss * rden, bden = -bss * ss * rden;
+  bmL += bden + bnum * L.un;
+  bmR += -bden - bnum * R.un;
+  bR.p += bnum;
+  bL.p -= bnum;
+  double buL = bnum * mL, buR = -bnum * mR;
+  // m = r d, d = s - u
+  bL.r += bmL * dL;
+  bR.r += bmR * dR;
+  bdL += bmL * L.r;
+  bdR += bmR * R.r;
+  bsL += bdL;
+  bsR += bdR;
+  buL -= bdL;
+  buR -= bdR;
+  // sL = min(uL - aL, uR - aR), sR = max(uL + aL, uR + aR)
+  double baL = 0.0, baR = 0.0;
+  if (sL_right) { buR += bsL; baR -= bsL; } else { buL += bsL; baL -= bsL; }
+  if (sR_right) { buR += bsR; baR += bsR; } else { buL += bsR; baL += bsR; }
+  bL.un += buL;
+  bR.un += buR;
+  // a = sqrt(gamma p / rho) = gp y with y = 1/sqrt(gp rho):
+  // da/dp = gamma y / 2, da/drho = -a gp y^2 / 2, da/dgamma = a p rho y^2 / 2
+  bL.p += baL * 0.5 * g.gamma * yL;
+  bR.p += baR * 0.5 * g.gamma * yR;
+  bL.r -= baL * 0.5 * aL * gpL * yL * yL;
+  bR.r -= baR * 0.5 * aR * gpR * yR * yR;
+  gb += 0.5 * (baL * aL * L.p * L.r * yL * yL + baR * aR * R.p * R.r * yR * yR);
+}
+
+// ---------------------------------------------------------------------------------------
+// cons -> prim reverse: prim adjoints (rho, u, v, p, T) -> conserved adjoints; gb += d/dgamma
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ void prim_vjp(double r, double mx, double my, double E, const Gas& g, const double qb[5],
+                                         double ub[4], double& gb) {
+  const double ir = recip(r);
+  const double u = mx * ir, v = my * ir;
+  const double p = g.gm1 * fma(-0.5, fma(mx, u, my * v), E);
+  const double T = p * ir;
+  const double bp = fma(qb[4], ir, qb[3]);
+  const double brq = fma(-qb[4], T * ir, qb[0]);
+  ub[3] = g.gm1 * bp;
+  ub[1] = fma(qb[1], ir, -g.gm1 * u * bp);
+  ub[2] = fma(qb[2], ir, -g.gm1 * v * bp);
+  ub[0] = brq - fma(u, qb[1], v * qb[2]) * ir + 0.5 * g.gm1 * fma(u, u, v * v) * bp;
+  gb += bp * p * g.g1;
+}
+
+}  // namespace js

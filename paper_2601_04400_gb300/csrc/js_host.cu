@@ -5,7 +5,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "jaxshock.h"
@@ -35,6 +37,25 @@ struct js_ctx {
   int* err = nullptr;
   unsigned long long* red = nullptr;
   BcArgs bc;
+  // transposed IB tables
+  int n_src = 0;
+  long long* ibt_cell = nullptr;
+  int* ibt_ptr = nullptr;
+  int* ibt_ghost = nullptr;
+  double* ibt_w = nullptr;
+  // adjoint workspace (allocated by the first vjp call)
+  bool adj_ready = false;
+  double* Q = nullptr;       // 5 planes
+  double* Qb = nullptr;      // 5 planes
+  double* lam = nullptr;     // 4 planes
+  double* P0 = nullptr;      // 4 planes (stage adjoint ping)
+  double* P1 = nullptr;      // 4 planes (pong)
+  double* Uacc = nullptr;    // 4 planes
+  double* wsave = nullptr;   // 56 planes
+  double* fadj = nullptr;    // 16 planes
+  double* inflow_acc = nullptr;   // 16
+  double* inflow_prim = nullptr;  // 16
+  double* qIb = nullptr;     // 4 per ghost
   // instrumentation
   bool profiling = false;
   std::vector<cudaEvent_t> ev;  // 2 per timed stage launch
@@ -140,6 +161,39 @@ int build_ib(js_ctx* c, const double* sdf) {
       nrm.push_back(nyv);
     }
   c->n_ghost = (int)dst.size();
+  // transposed tables: fluid source cell -> (ghost, weight), grouped by cell
+  {
+    std::vector<std::pair<long long, std::pair<int, double>>> ent;
+    for (int k = 0; k < c->n_ghost; ++k)
+      for (int m = 0; m < 4; ++m)
+        if (w[4 * k + m] != 0.0) ent.push_back({src[4 * k + m], {k, w[4 * k + m]}});
+    std::stable_sort(ent.begin(), ent.end(),
+                     [](const auto& x, const auto& y) { return x.first < y.first; });
+    std::vector<long long> cell;
+    std::vector<int> ptr, gh;
+    std::vector<double> ww;
+    for (size_t e = 0; e < ent.size(); ++e) {
+      if (e == 0 || ent[e].first != ent[e - 1].first) {
+        cell.push_back(ent[e].first);
+        ptr.push_back((int)e);
+      }
+      gh.push_back(ent[e].second.first);
+      ww.push_back(ent[e].second.second);
+    }
+    ptr.push_back((int)ent.size());
+    c->n_src = (int)cell.size();
+    if (c->n_src > 0) {
+      if (cudaMalloc(&c->ibt_cell, cell.size() * sizeof(long long)) != cudaSuccess ||
+          cudaMalloc(&c->ibt_ptr, ptr.size() * sizeof(int)) != cudaSuccess ||
+          cudaMalloc(&c->ibt_ghost, gh.size() * sizeof(int)) != cudaSuccess ||
+          cudaMalloc(&c->ibt_w, ww.size() * sizeof(double)) != cudaSuccess)
+        return JS_ERR_NOMEM;
+      JS_CUDA(cudaMemcpy(c->ibt_cell, cell.data(), cell.size() * sizeof(long long), cudaMemcpyHostToDevice));
+      JS_CUDA(cudaMemcpy(c->ibt_ptr, ptr.data(), ptr.size() * sizeof(int), cudaMemcpyHostToDevice));
+      JS_CUDA(cudaMemcpy(c->ibt_ghost, gh.data(), gh.size() * sizeof(int), cudaMemcpyHostToDevice));
+      JS_CUDA(cudaMemcpy(c->ibt_w, ww.data(), ww.size() * sizeof(double), cudaMemcpyHostToDevice));
+    }
+  }
   if (cudaMalloc(&c->tag, tag.size()) != cudaSuccess) return JS_ERR_NOMEM;
   JS_CUDA(cudaMemcpy(c->tag, tag.data(), tag.size(), cudaMemcpyHostToDevice));
   if (c->n_ghost > 0) {
@@ -229,6 +283,9 @@ void js_destroy(js_ctx* c) {
   cudaFree(c->tag);
   cudaFree(c->ib_dst); cudaFree(c->ib_src); cudaFree(c->ib_w); cudaFree(c->ib_nrm);
   cudaFree(c->err); cudaFree(c->red);
+  cudaFree(c->ibt_cell); cudaFree(c->ibt_ptr); cudaFree(c->ibt_ghost); cudaFree(c->ibt_w);
+  cudaFree(c->Q); cudaFree(c->Qb); cudaFree(c->lam); cudaFree(c->P0); cudaFree(c->P1); cudaFree(c->Uacc);
+  cudaFree(c->wsave); cudaFree(c->fadj); cudaFree(c->inflow_acc); cudaFree(c->inflow_prim); cudaFree(c->qIb);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   delete c;
 }
@@ -372,14 +429,146 @@ int js_step(js_ctx* c, double* U, double dt, int n_steps) {
   return JS_OK;
 }
 
+namespace {
+
+int adj_reserve(js_ctx* c) {
+  if (c->adj_ready) return JS_OK;
+  const size_t pl = sizeof(double) * (size_t)c->lay.plane;
+  struct { double** p; size_t planes; } bufs[] = {
+      {&c->Q, 5}, {&c->Qb, 5}, {&c->lam, 4}, {&c->P0, 4}, {&c->P1, 4}, {&c->Uacc, 4},
+      {&c->wsave, 2 * 4 * 7 /* js::WENO_SAVE */}, {&c->fadj, 16}};
+  for (auto& b : bufs) {
+    if (cudaMalloc(b.p, b.planes * pl) != cudaSuccess) return JS_ERR_NOMEM;
+    JS_CUDA(cudaMemset(*b.p, 0, b.planes * pl));
+  }
+  if (cudaMalloc(&c->inflow_acc, 16 * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&c->inflow_prim, 16 * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&c->qIb, sizeof(double) * 4 * (size_t)(c->n_ghost > 0 ? c->n_ghost : 1)) != cudaSuccess)
+    return JS_ERR_NOMEM;
+  c->adj_ready = true;
+  return JS_OK;
+}
+
+js::AdjArgs adj_args(js_ctx* c, const double* X, double* Ub, double* p_bar) {
+  js::AdjArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.lay = c->lay;
+  a.X = X;
+  a.Q = c->Q;
+  a.lam = c->lam;
+  a.Qb = c->Qb;
+  a.Ub = Ub;
+  a.wsave = c->wsave;
+  a.fadj = c->fadj;
+  a.pbar = p_bar;
+  a.tag = c->tag;
+  const double g = c->p.gamma;
+  a.gas = js::Gas{g, g - 1.0, 1.0 / (g - 1.0)};
+  a.inv_dx = 1.0 / c->g.dx;
+  a.inv_dy = 1.0 / c->g.dy;
+  a.nu_x1 = 1.0 / (c->g.dx * c->g.dx);
+  a.nu_y1 = 1.0 / (c->g.dy * c->g.dy);
+  a.nu_x = c->p.nu * a.nu_x1;
+  a.nu_y = c->p.nu * a.nu_y1;
+  const StageArgs s = base_args(c);
+  a.vx = s.vx;
+  a.vy = s.vy;
+  a.visc = c->p.mu > 0.0 ? 1 : 0;
+  a.inv_mu = a.visc ? 1.0 / c->p.mu : 0.0;
+  a.kg = -1.0 / (g * (g - 1.0));
+  a.kp = a.visc ? -1.0 / c->p.Pr : 0.0;
+  a.has_av = c->p.nu > 0.0 ? 1 : 0;
+  a.two_d = c->g.ny > 1 ? 1 : 0;
+  return a;
+}
+
+js::IbTArgs ibt_args(const js_ctx* c) {
+  js::IbTArgs t;
+  t.nsrc = c->n_src;
+  t.cell = c->ibt_cell;
+  t.ptr = c->ibt_ptr;
+  t.ghost = c->ibt_ghost;
+  t.w = c->ibt_w;
+  return t;
+}
+
+int adj_stage(js_ctx* c, const double* X, const double* Unext, double* Ub, double ra, double rb, double dt,
+              bool rhs_mode, double* p_bar) {
+  const js::AdjArgs a = adj_args(c, X, Ub, p_bar);
+  JS_CUDA(js::launch_adj_stage(a, c->bc, ib_args(c), ibt_args(c), c->p.wall, Unext, c->Uacc, ra, rb, dt, rhs_mode,
+                               c->inflow_acc, c->inflow_prim, c->qIb, c->stream, &c->launches));
+  return JS_OK;
+}
+
+int upload_inflow(js_ctx* c) {
+  double h[16];
+  for (int s = 0; s < 4; ++s)
+    for (int k = 0; k < 4; ++k) h[4 * s + k] = c->b.inflow[s][k];
+  JS_CUDA(cudaMemcpyAsync(c->inflow_prim, h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
+  return JS_OK;
+}
+
+}  // namespace
+
 int js_rhs_vjp(js_ctx* c, const double* U, const double* lam, double* U_bar, double* p_bar) {
-  (void)c; (void)U; (void)lam; (void)U_bar; (void)p_bar;
-  return JS_ERR_ARG;
+  if (!c || !U || !lam || !U_bar) return JS_ERR_ARG;
+  int rc = adj_reserve(c);
+  if (rc) return rc;
+  if ((rc = upload_inflow(c))) return rc;
+  JS_CUDA(js::launch_pack(U, c->N, c->lay, c->stream));
+  JS_CUDA(js::launch_pack(lam, c->P0, c->lay, c->stream));
+  c->launches += 2;
+  if ((rc = fill_halos(c, c->N))) return rc;
+  if ((rc = adj_stage(c, c->N, c->P0, c->P1, 0.0, 1.0, 1.0, true, p_bar))) return rc;
+  JS_CUDA(js::launch_adj_unpack(c->P1, nullptr, U_bar, c->lay, c->stream));
+  ++c->launches;
+  return JS_OK;
 }
 
 int js_step_vjp(js_ctx* c, const double* U_n, double dt, const double* lam_np1, double* lam_n, double* p_bar) {
-  (void)c; (void)U_n; (void)dt; (void)lam_np1; (void)lam_n; (void)p_bar;
-  return JS_ERR_ARG;
+  if (!c || !U_n || !lam_np1 || !lam_n || !(dt > 0.0)) return JS_ERR_ARG;
+  int rc = adj_reserve(c);
+  if (rc) return rc;
+  if ((rc = upload_inflow(c))) return rc;
+  // recompute and keep the three filled stage states X0 = N, X1 = A, X2 = B
+  JS_CUDA(js::launch_pack(U_n, c->N, c->lay, c->stream));
+  JS_CUDA(js::launch_pack(lam_np1, c->P0, c->lay, c->stream));
+  c->launches += 2;
+  StageArgs a = base_args(c);
+  a.cx = dt / c->g.dx;
+  a.cy = dt / c->g.dy;
+  a.avx = dt * c->p.nu / (c->g.dx * c->g.dx);
+  a.avy = dt * c->p.nu / (c->g.dy * c->g.dy);
+  const bool visc = c->p.mu > 0.0;
+  double* in[2] = {c->N, c->A};
+  double* outp[2] = {c->A, c->B};
+  const double ra[3] = {0.0, 0.75, 1.0 / 3.0};
+  const double rb[3] = {1.0, 0.25, 2.0 / 3.0};
+  for (int s = 0; s < 2; ++s) {
+    if ((rc = fill_halos(c, in[s]))) return rc;
+    a.Uin = in[s];
+    a.Un = c->N;
+    a.Uout = outp[s];
+    a.rk_a = ra[s];
+    a.rk_b = rb[s];
+    a.use_un = (s > 0) ? 1 : 0;
+    if ((rc = stage(c, a, visc, false))) return rc;
+  }
+  if ((rc = fill_halos(c, c->B))) return rc;
+  // reverse through the stages: P0 -> P1 -> P0 -> P1
+  JS_CUDA(cudaMemsetAsync(c->Uacc, 0, sizeof(double) * 4 * (size_t)c->lay.plane, c->stream));
+  double* X[3] = {c->N, c->A, c->B};
+  double* src = c->P0;
+  double* dst = c->P1;
+  for (int s = 2; s >= 0; --s) {
+    if ((rc = adj_stage(c, X[s], src, dst, ra[s], rb[s], dt, false, p_bar))) return rc;
+    double* t = src;
+    src = dst;
+    dst = t;
+  }
+  JS_CUDA(js::launch_adj_unpack(src, c->Uacc, lam_n, c->lay, c->stream));
+  ++c->launches;
+  return JS_OK;
 }
 
 int js_sync_status(js_ctx* c) {

@@ -34,6 +34,42 @@ struct IbArgs {
   const double* nrm;         // unit normal (2)
 };
 
+// transposed IB fill: for each fluid source cell, the ghosts that interpolate from it
+struct IbTArgs {
+  int nsrc;
+  const long long* cell;     // padded index of each source cell
+  const int* ptr;            // nsrc + 1 offsets into ghost / w
+  const int* ghost;          // ghost number
+  const double* w;           // its weight
+};
+
+// reverse-mode launch arguments (js_adjoint.cu)
+struct AdjArgs {
+  Lay lay;
+  const double* X;           // padded filled stage state (4 planes)
+  double* Q;                 // padded primitives rho, u, v, p, T (5 planes)
+  double* lam;               // padded lambda' (4 planes), zero outside fluid cells
+  double* Qb;                // padded primitive adjoints (5 planes)
+  double* Ub;                // padded conserved adjoints of X (4 planes)
+  double* wsave;             // WENO internals [dir][var][7] planes
+  double* fadj;              // face-state adjoints [dir][left/right][var] planes
+  double* pbar;              // parameter gradient (JS_NPARAM) or nullptr
+  const unsigned char* tag;
+  Gas gas;
+  double inv_dx, inv_dy;     // 1/dx, 1/dy
+  double nu_x, nu_y;         // nu/dx^2, nu/dy^2
+  double nu_x1, nu_y1;       // 1/dx^2, 1/dy^2
+  ViscC vx, vy;
+  double inv_mu, kg, kp;     // 1/mu, -1/(gamma (gamma-1)), -1/Pr
+  int visc, has_av, two_d;
+};
+
+cudaError_t launch_adj_stage(const AdjArgs& a, const BcArgs& bc, const IbArgs& ib, const IbTArgs& ibt, int wall,
+                             const double* Unext, double* Uacc, double ra, double rb, double dt, bool rhs_mode,
+                             double* inflow_acc, const double* inflow_prim, double* qIb, cudaStream_t s,
+                             long long* launches);
+cudaError_t launch_adj_unpack(const double* P, const double* P2, double* U, const Lay& lay, cudaStream_t s);
+
 cudaError_t launch_stage(const StageArgs& a, bool visc, bool rhs, cudaStream_t s);
 cudaError_t launch_bc_fill(double* U, const Lay& lay, const BcArgs& bc, cudaStream_t s);
 cudaError_t launch_ib_fill(double* U, const Lay& lay, const IbArgs& ib, double gamma, int wall, cudaStream_t s);

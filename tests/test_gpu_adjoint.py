@@ -1,0 +1,145 @@
+"""The hand-written reverse mode (js_rhs_vjp, js_step_vjp) against the oracle's discrete
+derivative (forward-mode dual numbers through the same FP64 formulation): the full
+transposed Jacobian on small grids, column by column, for every boundary kind, the viscous
+terms, artificial viscosity and the immersed cylinder; parameter gradients for gamma, mu,
+Pr, nu and the inflow states; dot-product tests on larger grids."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2601_04400_gb300 import workloads as W
+from jsutil import to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2601_04400_gb300 import binding
+    binding.lib()
+    return binding
+
+
+def _small_cases():
+    out = []
+    p = W.random_periodic(12, 10, seed=1)
+    out.append(("euler_periodic_12x10", p, p.W0))
+    p = W.random_periodic(12, 10, seed=2, mu=5e-3, nu=1e-3)
+    out.append(("ns_av_periodic_12x10", p, p.W0))
+    p = W.random_periodic(11, 9, seed=3, mu=2e-3).with_(bc=(3, 1, 0, 3), inflow=np.array(
+        [[1.1, 0.3, 0.1, 0.9], [1.0, 0.0, 0.0, 1.0], [1.0, 0.0, 0.0, 1.0], [1.2, -0.1, -0.2, 0.8]]))
+    out.append(("mixed_inflow_reflective_11x9", p, p.W0))
+    p = W.sod(16)
+    out.append(("sod16", p, W.random_state(p, seed=4, amp=0.02)))
+    p = W.shock_cylinder(nx=24, ny=16, mach=2.0, Re=100.0, Lx=3.0, Ly=2.0, centre=(1.5, 1.0), radius=0.45,
+                         x_shock=0.6)
+    out.append(("cylinder_ns_24x16", p, W.random_state(p, seed=5, amp=0.02)))
+    p = W.shock_cylinder(nx=24, ny=16, mach=2.0, viscous=False, Lx=3.0, Ly=2.0, centre=(1.5, 1.0), radius=0.45,
+                         x_shock=0.6).with_(wall=1)
+    out.append(("cylinder_noslip_euler_24x16", p, W.random_state(p, seed=6, amp=0.02)))
+    return out
+
+
+SMALL = _small_cases()
+
+
+def _oracle_vjp(prob, U, lam, tangent_fn):
+    """(J^T lam, dL/dtheta . lam) column by column from the oracle's forward mode."""
+    n = U.size
+    Ub = np.zeros(n)
+    e = np.zeros(n)
+    dth0 = np.zeros(20)
+    for k in range(n):
+        e[k] = 1.0
+        dL = tangent_fn(e.reshape(U.shape), dth0)
+        Ub[k] = np.dot(lam.reshape(-1), dL.reshape(-1))
+        e[k] = 0.0
+    pb = np.zeros(20)
+    zero = np.zeros_like(U)
+    for k in range(20):
+        d = np.zeros(20)
+        d[k] = 1.0
+        pb[k] = np.dot(lam.reshape(-1), tangent_fn(zero, d).reshape(-1))
+    return Ub.reshape(U.shape), pb
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def _pbar_mask(prob):
+    """Parameters whose gradient the library computes for this problem: gamma always; mu and
+    Pr for viscous problems (mu > 0); nu when the artificial viscosity is on (nu > 0); the
+    inflow state of inflow sides."""
+    m = np.zeros(20, dtype=bool)
+    m[0] = True
+    if prob.mu > 0:
+        m[1] = m[2] = True
+    if prob.nu > 0:
+        m[3] = True
+    for s in range(4):
+        if prob.bc[s] == 3 and not (prob.ny == 1 and s >= 2):
+            m[4 + 4 * s:8 + 4 * s] = True
+    return m
+
+
+@pytest.mark.parametrize("name,prob,Wp", SMALL, ids=[c[0] for c in SMALL])
+def test_rhs_vjp_equals_oracle_transposed_jacobian(B, name, prob, Wp):
+    import torch
+    U = O.prim_to_cons(prob, Wp)
+    lam = W.uniform_normal(U.shape, seed=11)
+    ref_U, ref_p = _oracle_vjp(prob, U, lam, lambda dU, dth: O.rhs_tangent(prob, U, dU, dth)[1])
+    s = B.Solver.from_problem(prob)
+    Ub, pb = s.rhs_vjp(to_dev(U), to_dev(lam))
+    assert s.status() == 0
+    assert _rel(to_host(Ub), ref_U) < TOL
+    m = _pbar_mask(prob)
+    got = to_host(pb)
+    assert np.abs(got[m] - ref_p[m]).max() <= TOL * max(np.abs(ref_p[m]).max(), 1e-300)
+
+
+@pytest.mark.parametrize("name,prob,Wp", SMALL, ids=[c[0] for c in SMALL])
+def test_step_vjp_equals_oracle_transposed_jacobian(B, name, prob, Wp):
+    U = O.prim_to_cons(prob, Wp)
+    dt = 0.4 * O.max_dt(prob, U, 0.5)
+    lam = W.uniform_normal(U.shape, seed=12)
+    ref_U, ref_p = _oracle_vjp(prob, U, lam, lambda dU, dth: O.step_tangent(prob, U, dU, dth, [dt])[1])
+    s = B.Solver.from_problem(prob)
+    Ub, pb = s.step_vjp(to_dev(U), dt, to_dev(lam))
+    assert s.status() == 0
+    assert _rel(to_host(Ub), ref_U) < TOL
+    m = _pbar_mask(prob)
+    got = to_host(pb)
+    assert np.abs(got[m] - ref_p[m]).max() <= TOL * max(np.abs(ref_p[m]).max(), 1e-300)
+
+
+@pytest.mark.parametrize("which", ["cylinder_ns_96x64", "riemann_ragged_70x45", "sod200"])
+def test_step_vjp_dot_product(B, which):
+    """<lam, J v> from the oracle's tangent equals <J^T lam, v> from the GPU on larger grids."""
+    if which == "cylinder_ns_96x64":
+        prob = W.shock_cylinder(nx=96, ny=64, Lx=6.0, Ly=4.0, Re=300.0)
+    elif which == "riemann_ragged_70x45":
+        prob = W.riemann2d(70, ny=45)
+    else:
+        prob = W.sod(200)
+    U = O.prim_to_cons(prob, W.random_state(prob, seed=7, amp=0.02))
+    dt = 0.4 * O.max_dt(prob, U, 0.5)
+    rng = np.random.default_rng(3)
+    v = rng.standard_normal(U.shape) * np.abs(U).max(axis=(1, 2), keepdims=True) * 1e-3
+    dth = np.zeros(20)
+    dth[0] = 0.1
+    if prob.mu > 0:
+        dth[1] = 1e-3
+    lam = rng.standard_normal(U.shape)
+    _, Jv = O.step_tangent(prob, U, v, dth, [dt])
+    s = B.Solver.from_problem(prob)
+    Ub, pb = s.step_vjp(to_dev(U), dt, to_dev(lam))
+    lhs = np.dot(lam.reshape(-1), Jv.reshape(-1))
+    rhs = np.dot(to_host(Ub).reshape(-1), v.reshape(-1)) + np.dot(to_host(pb), dth)
+    scale = np.abs(lam).sum() * np.abs(Jv).max()
+    assert abs(lhs - rhs) <= 1e-12 * scale
