@@ -238,6 +238,35 @@ def run_ours(args):
     e2e_ms = sum(a.elapsed_time(b) for a, b in ee)
     solver.check()
 
+    # ---- adjoint / forward cost of one SSP-RK3 step (same state, same dt) ---------------
+    adj = None
+    if not args.no_adjoint:
+        dt = solver.max_dt(U, cfl)
+        lam = torch.randn(U.shape, dtype=torch.float64, device="cuda")
+        lam_out = torch.empty_like(lam)
+        pbar = torch.zeros(20, dtype=torch.float64, device="cuda")
+        Uw = U.clone()
+        solver.step_vjp(U, dt, lam, lam_n=lam_out, p_bar=pbar)  # allocates the adjoint workspace
+        reps = max(3, min(args.steps, 20))
+        fa = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        ba = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        barrier()
+        for k in range(reps):
+            flush.zero_()
+            fa[k][0].record(stream)
+            solver.step(Uw, dt, 1)
+            fa[k][1].record(stream)
+            flush.zero_()
+            ba[k][0].record(stream)
+            solver.step_vjp(U, dt, lam, lam_n=lam_out, p_bar=pbar)
+            ba[k][1].record(stream)
+        barrier()
+        solver.check()
+        f_ms = sum(a.elapsed_time(b) for a, b in fa) / reps
+        b_ms = sum(a.elapsed_time(b) for a, b in ba) / reps
+        adj = {"ms_per_step_forward": f_ms, "ms_per_step_vjp": b_ms, "ratio": b_ms / f_ms,
+               "note": "js_step_vjp (recomputes the 3 stage states, then reverses them) / js_step, one step"}
+
     if dist is not None:
         t = torch.tensor([step_ms, e2e_ms, stage_ms / max(stage_launches, 1)], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -265,6 +294,8 @@ def run_ours(args):
                          "flops_per_launch": flop_launch},
             "e2e": {"value": e2e_value, "unit": "cell-updates/s", "h2d_bytes_per_step": state_bytes,
                     "d2h_bytes_per_step": state_bytes},
+            "adjoint_forward_ratio": None if adj is None else adj["ratio"],
+            "adjoint": adj,
             "gpu_launches": launches,
             "clocks": sampler.summary(),
         }
@@ -284,6 +315,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="riemann2d", choices=["riemann2d", "shock_cylinder"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

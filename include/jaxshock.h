@@ -118,6 +118,50 @@ int js_sync_status(js_ctx* ctx);
  * (0 fluid, 1 solid, 2 ghost) as host uint8 [ny][nx]. */
 int js_ib_info(js_ctx* ctx, int* n_ghost, unsigned char* tag_host);
 
+/* ---- batched path ---------------------------------------------------------------------
+ * Many independent 2D problems (uneven grids, parameters, boundaries, immersed bodies)
+ * advanced together by ONE persistent cooperative kernel launch per js_batch_step call (the
+ * solver step mapped over a batch of problems; the paper's vmap, Sec. 1).  Each instance's
+ * dt is recomputed on the device before every step from its own state (CFL rule of
+ * js_max_dt, same arithmetic, so a batched run equals per-instance js_max_dt + js_step runs
+ * bit for bit).  Grid barriers inside the launch wait at most 2 s each; a wait that runs out
+ * sets JS_ERR_TIMEOUT (read by js_batch_sync_status) and the launch returns. */
+typedef struct js_batch js_batch;
+
+/* Create a batch of `count` problems: arrays grids[count], params[count], bcs[count];
+ * sdf_host: NULL or an array of `count` host pointers (entries may be NULL).  All grids must
+ * be 2D.  Allocates per-instance buffers.  Errors as js_create. */
+int js_batch_create(int count, const js_grid* grids, const js_params* params, const js_boundary* bcs,
+                    const double* const* sdf_host, void* stream, js_batch** out);
+
+/* Register the instances' states: U is a host array of `count` device pointers, each
+ * [4][ny_k][nx_k], advanced in place by js_batch_step.  Copies the pointer table to the
+ * device and synchronises; call again when the pointers change (not inside a capture). */
+int js_batch_set_states(js_batch* b, double* const* U);
+
+/* Advance every instance by n_steps SSP-RK3 steps with its own CFL time step (cfl > 0) in
+ * one launch.  t_dev: optional device double[count] to which each instance's elapsed time
+ * is added.  Asynchronous; allocates nothing, so it can be captured into a CUDA graph. */
+int js_batch_step(js_batch* b, double cfl, int n_steps, double* t_dev);
+
+/* Read and clear the batch's device error flag (synchronises): JS_OK, JS_ERR_NONPHYSICAL,
+ * JS_ERR_TIMEOUT. */
+int js_batch_sync_status(js_batch* b);
+
+/* Launch shape and size: resident blocks of the persistent kernel, 32x16 tiles, cells. */
+int js_batch_info(js_batch* b, int* blocks, int* tiles, long long* cells);
+
+/* The context of instance k (owned by the batch; do not destroy it), e.g. for js_step_vjp. */
+js_ctx* js_batch_instance(js_batch* b, int k);
+
+/* Failure-detection check of the bounded barrier: launches the persistent kernel with a
+ * barrier that can never complete (one arrival short) and a wait budget of budget_s
+ * (0 < budget_s <= 2) seconds; the launch must end by itself with JS_ERR_TIMEOUT in the
+ * batch's error flag.  Requires js_batch_set_states. */
+int js_batch_test_timeout(js_batch* b, double budget_s);
+
+void js_batch_destroy(js_batch* b);
+
 /* Instrumentation.  js_profile_begin(ctx, capacity) starts timing every launch of the fused
  * stage kernel (up to `capacity` launches) with CUDA events recorded on the context's stream,
  * and counting every kernel the context launches.  js_profile_end synchronises the stream,

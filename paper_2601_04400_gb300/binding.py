@@ -61,6 +61,15 @@ SIGNATURES = {
     "js_profile_end": (_I, [_P, C.POINTER(_D), C.POINTER(_I), C.POINTER(C.c_longlong)]),
     "js_max_dt_noalloc": (_I, [C.POINTER(JsGrid), C.POINTER(JsParams), _P, _P, _D, _P, C.POINTER(_D)]),
     "js_strerror": (C.c_char_p, [_I]),
+    "js_batch_create": (_I, [_I, C.POINTER(JsGrid), C.POINTER(JsParams), C.POINTER(JsBoundary), C.POINTER(_P), _P,
+                             C.POINTER(_P)]),
+    "js_batch_set_states": (_I, [_P, C.POINTER(_P)]),
+    "js_batch_step": (_I, [_P, _D, _I, _P]),
+    "js_batch_sync_status": (_I, [_P]),
+    "js_batch_info": (_I, [_P, C.POINTER(_I), C.POINTER(_I), C.POINTER(C.c_longlong)]),
+    "js_batch_instance": (_P, [_P, _I]),
+    "js_batch_test_timeout": (_I, [_P, _D]),
+    "js_batch_destroy": (None, [_P]),
 }
 
 
@@ -294,6 +303,67 @@ class Solver:
         if getattr(self, "ctx", None):
             js_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------------------
+# batched path: one persistent launch advances many independent problems
+# ---------------------------------------------------------------------------------------
+class Batch:
+    """Independent 2D problems advanced together by js_batch_step (one persistent launch)."""
+
+    def __init__(self, problems, stream=None):
+        n = len(problems)
+        grids = (JsGrid * n)()
+        params = (JsParams * n)()
+        bcs = (JsBoundary * n)()
+        sdfs = (C.c_void_p * n)()
+        self._keep = []
+        for k, p in enumerate(problems):
+            g, pp, b = make_structs(p.nx, p.ny, p.x0, p.y0, p.dx, p.dy, p.bc, p.gamma, p.mu, p.Pr, p.nu, p.inflow,
+                                    getattr(p, "wall", 0))
+            grids[k], params[k], bcs[k] = g, pp, b
+            if p.sdf is not None:
+                a = np.ascontiguousarray(p.sdf, dtype=np.float64)
+                self._keep.append(a)
+                sdfs[k] = a.ctypes.data_as(C.c_void_p)
+        out = C.c_void_p()
+        _check(lib().js_batch_create(n, grids, params, bcs, sdfs, _stream_ptr(stream), C.byref(out)),
+               "js_batch_create")
+        self.handle = out
+        self.count = n
+        self.shapes = [(4, p.ny, p.nx) for p in problems]
+
+    def set_states(self, states):
+        if len(states) != self.count:
+            raise ValueError("one state per instance")
+        ptrs = (C.c_void_p * self.count)(*[_ptr(t).value for t in states])
+        self._states = list(states)
+        _check(lib().js_batch_set_states(self.handle, ptrs), "js_batch_set_states")
+
+    def step(self, cfl, n_steps, t=None):
+        _check(lib().js_batch_step(self.handle, float(cfl), int(n_steps), _ptr(t)), "js_batch_step")
+
+    def status(self):
+        return lib().js_batch_sync_status(self.handle)
+
+    def info(self):
+        b, t, c = C.c_int(0), C.c_int(0), C.c_longlong(0)
+        _check(lib().js_batch_info(self.handle, C.byref(b), C.byref(t), C.byref(c)), "js_batch_info")
+        return dict(blocks=b.value, tiles=t.value, cells=c.value)
+
+    def test_timeout(self, budget_s):
+        _check(lib().js_batch_test_timeout(self.handle, float(budget_s)), "js_batch_test_timeout")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().js_batch_destroy(self.handle)
+            self.handle = None
 
     def __del__(self):
         try:

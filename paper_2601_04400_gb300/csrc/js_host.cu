@@ -261,6 +261,32 @@ int stage(js_ctx* c, const StageArgs& a, bool visc, bool rhs) {
 
 }  // namespace
 
+// batched kernel description of a context (used by js_batch.cu)
+void js_internal_desc(js_ctx* c, js::InstDesc* d) {
+  std::memset(d, 0, sizeof(*d));
+  d->lay = c->lay;
+  d->N = c->N;
+  d->A = c->A;
+  d->B = c->B;
+  d->tag = c->tag;
+  d->ib = ib_args(c);
+  d->bc = c->bc;
+  d->gamma = c->p.gamma;
+  d->mu = c->p.mu;
+  d->Pr = c->p.Pr;
+  d->nu = c->p.nu;
+  d->dx = c->g.dx;
+  d->dy = c->g.dy;
+  d->hmin = (c->g.ny > 1) ? (c->g.dx < c->g.dy ? c->g.dx : c->g.dy) : c->g.dx;
+  d->lim = (c->p.mu > 0.0) ? ((4.0 / 3.0 < c->p.gamma / c->p.Pr) ? c->p.gamma / c->p.Pr : 4.0 / 3.0) : 1.0;
+  const StageArgs a = base_args(c);
+  d->vx = a.vx;
+  d->vy = a.vy;
+  d->wall = c->p.wall;
+  d->visc = c->p.mu > 0.0 ? 1 : 0;
+  d->has_av = c->p.nu > 0.0 ? 1 : 0;
+}
+
 extern "C" {
 
 const char* js_strerror(int code) {

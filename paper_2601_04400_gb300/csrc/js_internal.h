@@ -70,6 +70,22 @@ cudaError_t launch_adj_stage(const AdjArgs& a, const BcArgs& bc, const IbArgs& i
                              long long* launches);
 cudaError_t launch_adj_unpack(const double* P, const double* P2, double* U, const Lay& lay, cudaStream_t s);
 
+// one instance of the batched kernel (js_batch.cu), filled from a context by js_internal_desc
+struct InstDesc {
+  Lay lay;
+  double* N;
+  double* A;
+  double* B;
+  double* U;                 // user state [4][ny][nx]
+  const unsigned char* tag;
+  IbArgs ib;
+  BcArgs bc;
+  double gamma, mu, Pr, nu, dx, dy;
+  double hmin, lim;          // viscous dt cap: cfl hmin^2 rho_min / (2 mu lim)
+  ViscC vx, vy;
+  int wall, visc, has_av, ntx, nty;
+};
+
 cudaError_t launch_stage(const StageArgs& a, bool visc, bool rhs, cudaStream_t s);
 cudaError_t launch_bc_fill(double* U, const Lay& lay, const BcArgs& bc, cudaStream_t s);
 cudaError_t launch_ib_fill(double* U, const Lay& lay, const IbArgs& ib, double gamma, int wall, cudaStream_t s);

@@ -1,0 +1,200 @@
+// Fused stage of the FP64 finite-volume step on one 2D tile (arXiv 2601.04400, Sec. 2):
+// conserved tile + 3-cell halo -> primitives in shared memory -> x sweep (WENO5, HLLC,
+// viscous flux) into a shared accumulator -> y sweep, divergence, artificial viscosity and
+// the SSP-RK3 stage combination.  Used by the per-grid stage kernel and by the persistent
+// batched kernel.
+#pragma once
+#include "js_device.cuh"
+#include "js_internal.h"
+
+namespace js {
+
+// =======================================================================================
+// line sweep: WENO5 -> HLLC (+ viscous) -> flux differences, on primitives in shared memory
+// =======================================================================================
+// sq: shared planes rho, u, v, p (and T when VISC), plane stride ps; `base` = index of the
+// first output cell of the segment, `st` = stride along the line, `ts` = stride across it.
+// emit(k, dF) receives F_{k+1/2} - F_{k-1/2} (conserved order) for output cells k = 0..L-1.
+template <int DIR, bool VISC, bool HAS_T, int L, class Emit>
+__device__ __forceinline__ void sweep_line(const double* __restrict__ sq, int ps, int base, int st, int ts,
+                                           const Gas& g, const ViscC& vc, Emit&& emit) {
+  constexpr int PN = (DIR == 0) ? 1 : 2;  // plane of the face-normal velocity
+  constexpr int PT = (DIR == 0) ? 2 : 1;  // plane of the tangential velocity
+  Win w[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const double* q = sq + c * ps;
+    w[c].init(q[base - 3 * st], q[base - 2 * st], q[base - st], q[base]);
+  }
+  double prevL[4], prevF[4];
+#pragma unroll 1
+  for (int k = -1; k <= L; ++k) {
+    const int cell = base + k * st;
+    double Lf[4], Rf[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) w[c].step(sq[c * ps + cell + 2 * st], Lf[c], Rf[c]);
+    if (k >= 0) {
+      // face k - 1/2 between cells k-1 (left state prevL) and k (right state Rf)
+      double ql[4], qr[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) { ql[c] = prevL[c]; qr[c] = Rf[c]; }
+      if (!(ql[0] > 0.0 && ql[3] > 0.0 && qr[0] > 0.0 && qr[3] > 0.0)) {
+        // positivity fallback: first-order (cell) states at this face
+#pragma unroll
+        for (int c = 0; c < 4; ++c) { ql[c] = sq[c * ps + cell - st]; qr[c] = sq[c * ps + cell]; }
+      }
+      double Fn[4];
+      hllc(ql[0], ql[PN], ql[PT], ql[3], qr[0], qr[PN], qr[PT], qr[3], g, Fn);
+      double F[4];
+      F[0] = Fn[0];
+      F[PN] = Fn[1];
+      F[PT] = Fn[2];
+      F[3] = Fn[3];
+      if (VISC) {
+        const int a = cell - st, b = cell;
+        const double* un = sq + PN * ps;
+        const double* ut = sq + PT * ps;
+        const double* Tq = sq + 4 * ps;
+        const double dun = un[b] - un[a], dut = ut[b] - ut[a], dT = Tq[b] - Tq[a];
+        double tnn, tnt;
+        if (HAS_T) {
+          const double sun = (un[a + ts] - un[a - ts]) + (un[b + ts] - un[b - ts]);
+          const double sut = (ut[a + ts] - ut[a - ts]) + (ut[b + ts] - ut[b - ts]);
+          tnn = fma(vc.c43n, dun, -vc.c23t * sut);
+          tnt = fma(vc.cn, dut, vc.ct * sun);
+        } else {
+          tnn = vc.c43n * dun;
+          tnt = vc.cn * dut;
+        }
+        const double sbn = un[a] + un[b], sbt = ut[a] + ut[b];
+        const double e = fma(0.5, fma(sbn, tnn, sbt * tnt), vc.ck * dT);
+        F[PN] -= tnn;
+        F[PT] -= tnt;
+        F[3] -= e;
+      }
+      if (k >= 1) {
+        double dF[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) dF[c] = F[c] - prevF[c];
+        emit(k - 1, dF);
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) prevF[c] = F[c];
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) prevL[c] = Lf[c];
+  }
+}
+
+// final combination for one interior cell; returns the value stored in the output
+template <bool RHS>
+__device__ __forceinline__ void finish_cell(const StageArgs& a, int gi, int gj, const double acc[4],
+                                            const double dG[4], double rho, double p) {
+  const long long pid = a.lay.idx(gi, gj);
+  const bool fluid = (a.tag == nullptr) || (a.tag[(long long)gj * a.lay.nx + gi] == 0);
+  double out[4];
+  if (fluid) {
+    if (!(rho > 0.0 && p > 0.0)) atomicOr(a.err, ERR_NONPHYSICAL_BIT);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const double* Uc = a.Uin + c * a.lay.plane;
+      const double us = RHS ? 0.0 : Uc[pid];
+      double v = fma(-a.cy, dG[c], us - acc[c]);
+      if (a.has_av) {
+        v = fma(a.avx, (Uc[pid + 1] - 2.0 * Uc[pid]) + Uc[pid - 1], v);
+        if (a.lay.ny > 1) v = fma(a.avy, (Uc[pid + a.lay.pitch] - 2.0 * Uc[pid]) + Uc[pid - a.lay.pitch], v);
+      }
+      if (!RHS && a.use_un) v = fma(a.rk_a, a.Un[c * a.lay.plane + pid], a.rk_b * v);
+      out[c] = v;
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) out[c] = RHS ? 0.0 : a.Uin[c * a.lay.plane + pid];
+  }
+  if (RHS) {
+    const long long n = (long long)a.lay.nx * a.lay.ny;
+    const long long o = (long long)gj * a.lay.nx + gi;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) a.Uout[c * n + o] = out[c];
+  } else {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) a.Uout[c * a.lay.plane + pid] = out[c];
+  }
+}
+
+// load the conserved tile with halo and convert to primitives in shared memory
+template <int TX, int TY, int NPL, int NT>
+__device__ __forceinline__ void load_tile(const StageArgs& a, double* sq, int ps, int sp, int ox, int oy,
+                                          const Gas& g) {
+  constexpr int CW = TX + 6, CH = TY + 6;
+  const int W = a.lay.nx + 6;
+  for (int e = threadIdx.x; e < CW * CH; e += NT) {
+    const int row = e / CW, col = e - row * CW;
+    int gx = ox + col, gy = oy + row;  // padded coordinates
+    gx = (gx < W) ? gx : W - 1;
+    gy = (gy < a.lay.H) ? gy : a.lay.H - 1;
+    const long long s = (long long)gy * a.lay.pitch + gx;
+    const double r = a.Uin[s], mx = a.Uin[a.lay.plane + s], my = a.Uin[2 * a.lay.plane + s],
+                 E = a.Uin[3 * a.lay.plane + s];
+    double u, v, p, T;
+    cons_to_prim(r, mx, my, E, g, u, v, p, T);
+    const int d = row * sp + col;
+    sq[d] = r;
+    sq[ps + d] = u;
+    sq[2 * ps + d] = v;
+    sq[3 * ps + d] = p;
+    if (NPL == 5) sq[4 * ps + d] = T;
+  }
+}
+
+template <int TX, int TY, int LX, int LY, bool VISC, bool RHS>
+struct Stage2D {
+  static constexpr int NPL = VISC ? 5 : 4;
+  static constexpr int SP = TX + 7;  // odd row pitch (in doubles) of the shared tile
+  static constexpr int PS = (TY + 6) * SP;
+  static constexpr int NX_ITEMS = TY * (TX / LX);
+  static constexpr int NY_ITEMS = TX * (TY / LY);
+  static constexpr int NT = (NX_ITEMS > NY_ITEMS) ? NX_ITEMS : NY_ITEMS;
+  static constexpr size_t SMEM = sizeof(double) * ((size_t)NPL * PS + 4 * TX * TY);
+};
+
+// one tile (bx, by) of one stage; smem holds Stage2D::SMEM bytes; all NT threads take part
+template <int TX, int TY, int LX, int LY, bool VISC, bool RHS>
+__device__ __forceinline__ void stage_tile(const StageArgs& a, int bx, int by, double* smem) {
+  using S = Stage2D<TX, TY, LX, LY, VISC, RHS>;
+  double* sq = smem;
+  double* acc = smem + S::NPL * S::PS;
+  const Gas g{a.gamma, a.gm1, a.g1};
+  const int tx0 = bx * TX, ty0 = by * TY;  // interior origin of the tile
+  load_tile<TX, TY, S::NPL, S::NT>(a, sq, S::PS, S::SP, tx0, ty0, g);
+  __syncthreads();
+  // x sweep: one thread per (row, segment)
+  for (int it = threadIdx.x; it < S::NX_ITEMS; it += S::NT) {
+    const int ty = it % TY, xs = (it / TY) * LX;
+    const int base = (ty + 3) * S::SP + xs + 3;
+    sweep_line<0, VISC, true, LX>(sq, S::PS, base, 1, S::SP, g, a.vx, [&](int k, const double dF[4]) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[c * TX * TY + ty * TX + xs + k] = a.cx * dF[c];
+    });
+  }
+  __syncthreads();
+  // y sweep + stage combination: one thread per (column, segment)
+  for (int it = threadIdx.x; it < S::NY_ITEMS; it += S::NT) {
+    const int tx = it % TX, ys = (it / TX) * LY;
+    const int base = (ys + 3) * S::SP + tx + 3;
+    const int gi = tx0 + tx;
+    sweep_line<1, VISC, true, LY>(sq, S::PS, base, S::SP, 1, g, a.vy, [&](int k, const double dG[4]) {
+      const int ty = ys + k, gj = ty0 + ty;
+      if (gi < a.lay.nx && gj < a.lay.ny) {
+        double ax[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) ax[c] = acc[c * TX * TY + ty * TX + tx];
+        const int sc = (ty + 3) * S::SP + tx + 3;
+        finish_cell<RHS>(a, gi, gj, ax, dG, sq[sc], sq[3 * S::PS + sc]);
+      }
+    });
+  }
+}
+
+
+}  // namespace js

@@ -1,0 +1,128 @@
+"""The batched persistent path (js_batch_*): many shock-cylinder instances with seeded Mach
+numbers, radii and uneven grids, advanced in one launch with per-instance device CFL steps.
+It must equal per-instance js_max_dt + js_step runs bit for bit, match the oracle, be
+capturable in a CUDA graph, and report a barrier that cannot complete as JS_ERR_TIMEOUT
+without hanging."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2601_04400_gb300 import workloads as W
+from jsutil import TOL, normwise_err, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2601_04400_gb300 import binding as B
+    B.lib()
+    return torch, B
+
+
+def _cases(count=5, seed=3):
+    return W.batched_cases(count, seed=seed, nx_choices=(64, 96, 128), ny_choices=(48, 64))
+
+
+def _states(torch, problems):
+    return [torch.tensor(O.prim_to_cons(p, p.W0), device="cuda") for p in problems]
+
+
+def _sequential(torch, B, problems, states, cfl, n):
+    out, times = [], []
+    for p, U in zip(problems, states):
+        s = B.Solver.from_problem(p)
+        U = U.clone()
+        t = 0.0
+        for _ in range(n):
+            dt = s.max_dt(U, cfl)
+            s.step(U, dt, 1)
+            t += dt
+        out.append(to_host(U))
+        times.append(t)
+        s.close()
+    return out, times
+
+
+def test_batch_equals_per_instance_steps_bitwise(env):
+    torch, B = env
+    probs = _cases()
+    states = _states(torch, probs)
+    ref, ref_t = _sequential(torch, B, probs, states, 0.5, 8)
+    b = B.Batch(probs)
+    work = [U.clone() for U in states]
+    b.set_states(work)
+    t = torch.zeros(len(probs), dtype=torch.float64, device="cuda")
+    b.step(0.5, 5, t)
+    b.step(0.5, 3, t)
+    assert b.status() == 0
+    for k, U in enumerate(work):
+        assert np.array_equal(to_host(U), ref[k]), k
+    assert np.array_equal(to_host(t), np.array(ref_t))
+    b.close()
+
+
+def test_batch_matches_oracle(env):
+    torch, B = env
+    probs = _cases(2, seed=5)
+    states = _states(torch, probs)
+    b = B.Batch(probs)
+    work = [U.clone() for U in states]
+    b.set_states(work)
+    b.step(0.5, 4)
+    assert b.status() == 0
+    for p, U in zip(probs, work):
+        Uo = O.prim_to_cons(p, p.W0)
+        for _ in range(4):
+            Uo = O.step(p, Uo, [O.max_dt(p, Uo, 0.5)])
+        assert normwise_err(to_host(U), Uo) < TOL
+
+
+def test_batch_step_is_graph_capturable(env):
+    torch, B = env
+    probs = _cases(3, seed=7)
+    states = _states(torch, probs)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        b = B.Batch(probs, stream=side)
+        eager = [U.clone() for U in states]
+        b.set_states(eager)
+        b.step(0.5, 4)
+        torch.cuda.synchronize()
+        work = [U.clone() for U in states]
+        b.set_states(work)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=side):
+            b.step(0.5, 2)
+    torch.cuda.synchronize()
+    for U, U0 in zip(work, states):
+        U.copy_(U0)
+    torch.cuda.synchronize()
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    assert b.status() == 0
+    for a, e in zip(work, eager):
+        assert np.array_equal(to_host(a), to_host(e))
+
+
+def test_barrier_timeout_is_reported_and_recoverable(env):
+    torch, B = env
+    probs = _cases(2, seed=9)
+    states = _states(torch, probs)
+    b = B.Batch(probs)
+    work = [U.clone() for U in states]
+    b.set_states(work)
+    b.test_timeout(0.05)
+    assert b.status() == B.JS_ERR_TIMEOUT
+    # the context stays usable: a normal launch afterwards is correct
+    for U, U0 in zip(work, states):
+        U.copy_(U0)
+    b.step(0.5, 2)
+    assert b.status() == 0
+    ref, _ = _sequential(torch, B, probs, states, 0.5, 2)
+    for k, U in enumerate(work):
+        assert np.array_equal(to_host(U), ref[k])
