@@ -162,6 +162,12 @@ int js_batch_test_timeout(js_batch* b, double budget_s);
 
 void js_batch_destroy(js_batch* b);
 
+/* Stage-kernel tuning: tile shape variant (0 .. n_variants-1) used by this context's
+ * js_rhs / js_step / js_step_vjp; 0 = 32x32-cell tiles with concurrent x/y sweeps.  Results are identical for every
+ * variant; only speed differs (the Python autotuner times them and caches the choice). */
+int js_set_tuning(js_ctx* ctx, int variant);
+int js_get_tuning(js_ctx* ctx, int* variant, int* n_variants);
+
 /* Instrumentation.  js_profile_begin(ctx, capacity) starts timing every launch of the fused
  * stage kernel (up to `capacity` launches) with CUDA events recorded on the context's stream,
  * and counting every kernel the context launches.  js_profile_end synchronises the stream,

@@ -57,6 +57,8 @@ SIGNATURES = {
     "js_step_vjp": (_I, [_P, _P, _D, _P, _P, _P]),
     "js_sync_status": (_I, [_P]),
     "js_ib_info": (_I, [_P, C.POINTER(_I), _P]),
+    "js_set_tuning": (_I, [_P, _I]),
+    "js_get_tuning": (_I, [_P, C.POINTER(_I), C.POINTER(_I)]),
     "js_profile_begin": (_I, [_P, _I]),
     "js_profile_end": (_I, [_P, C.POINTER(_D), C.POINTER(_I), C.POINTER(C.c_longlong)]),
     "js_max_dt_noalloc": (_I, [C.POINTER(JsGrid), C.POINTER(JsParams), _P, _P, _D, _P, C.POINTER(_D)]),
@@ -234,6 +236,7 @@ class Solver:
         self._spec = dict(nx=nx, ny=ny, x0=x0, y0=y0, dx=dx, dy=dy, bc=tuple(bc), gamma=gamma, mu=mu, Pr=Pr,
                           nu=nu, inflow=np.asarray(inflow, dtype=np.float64).reshape(4, 4), wall=wall)
         self._g, self._p, self._b = make_structs(**self._spec)
+        self.has_ib = sdf is not None
         self.ctx = js_create(self._g, self._p, self._b, sdf, stream)
 
     @classmethod
@@ -256,6 +259,14 @@ class Solver:
 
     def set_stream(self, stream=None):
         js_set_stream(self.ctx, stream)
+
+    def set_tuning(self, variant):
+        _check(lib().js_set_tuning(self.ctx, int(variant)), "js_set_tuning")
+
+    def tuning(self):
+        v, n = C.c_int(0), C.c_int(0)
+        _check(lib().js_get_tuning(self.ctx, C.byref(v), C.byref(n)), "js_get_tuning")
+        return v.value, n.value
 
     def prim_to_cons(self, W):
         import torch

@@ -9,14 +9,10 @@
 
 namespace js {
 
-// quotient a/b with the refined reciprocal it used (r ~ 1/b to ~2^-44, enough for a derivative)
+// quotient a/b exactly as the forward kernel forms it (quot), with the reciprocal it used
 __device__ __forceinline__ double quot_r(double a, double b, double& r) {
-  r = rcp_seed(b);
-  const double e = fma(-b, r, 1.0);
-  r = fma(r, e, r);
-  const double q = a * r;
-  const double res = fma(-b, q, a);
-  return fma(r, res, q);
+  r = recip(b);
+  return a * r;
 }
 
 // ---------------------------------------------------------------------------------------

@@ -206,6 +206,8 @@ __global__ void __launch_bounds__(32) batch_kernel(BatchArgs b) {
         a.Un = d.N;
         a.Uout = (s == 0) ? d.A : ((s == 1) ? d.B : d.N);
         a.tag = d.tag;
+        a.acc = d.acc;
+        a.acc2 = nullptr;
         a.err = b.err;
         a.lay = d.lay;
         a.gamma = d.gamma;

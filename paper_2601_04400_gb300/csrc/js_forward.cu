@@ -117,6 +117,17 @@ stage2d_kernel(StageArgs a) {
   stage_tile<TX, TY, LX, LY, VISC, RHS>(a, blockIdx.x, blockIdx.y, smem);
 }
 
+// persistent concurrent-sweep stage kernel: blocks stride over the tiles
+template <int TX, int TY, int LX, int LY, bool VISC, bool RHS>
+__global__ void __launch_bounds__(Stage2DC<TX, TY, LX, LY, VISC>::NT)
+stage2dc_kernel(StageArgs a, int ntx, int ntiles) {
+  extern __shared__ double smem[];
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    stage_tile_c<TX, TY, LX, LY, VISC, RHS>(a, t % ntx, t / ntx, smem);
+    __syncthreads();
+  }
+}
+
 template <int TX, int LX, bool VISC, bool RHS>
 __global__ void __launch_bounds__(TX / LX) stage1d_kernel(StageArgs a) {
   constexpr int NPL = VISC ? 5 : 4;
@@ -148,7 +159,7 @@ __global__ void __launch_bounds__(TX / LX) stage1d_kernel(StageArgs a) {
       double ax[4];
 #pragma unroll
       for (int c = 0; c < 4; ++c) ax[c] = a.cx * dF[c];
-      finish_cell<RHS>(a, gi, 0, ax, zero, sq[xs + k + 3], sq[3 * PS + xs + k + 3]);
+      finish_cell<RHS, true>(a, gi, 0, ax, zero, sq[xs + k + 3], sq[3 * PS + xs + k + 3]);
     }
   });
 }
@@ -157,22 +168,54 @@ __global__ void __launch_bounds__(TX / LX) stage1d_kernel(StageArgs a) {
 // launchers
 // =======================================================================================
 namespace {
-constexpr int TX2 = 32, TY2 = 16, LX2 = 16, LY2 = 16;
 constexpr int TX1 = 64, LX1 = 16;
 
-template <bool VISC, bool RHS>
+template <int TX, int TY, int LX, int LY, bool VISC, bool RHS>
 cudaError_t launch_stage2d(const StageArgs& a, cudaStream_t s) {
-  using S = Stage2D<TX2, TY2, LX2, LY2, VISC, RHS>;
-  auto k = stage2d_kernel<TX2, TY2, LX2, LY2, VISC, RHS>;
+  using S = Stage2D<TX, TY, LX, LY, VISC, RHS>;
+  auto k = stage2d_kernel<TX, TY, LX, LY, VISC, RHS>;
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  dim3 grid((a.lay.nx + TX2 - 1) / TX2, (a.lay.ny + TY2 - 1) / TY2);
+  dim3 grid((a.lay.nx + TX - 1) / TX, (a.lay.ny + TY - 1) / TY);
   k<<<grid, S::NT, S::SMEM, s>>>(a);
   return cudaGetLastError();
+}
+
+template <int TX, int TY, int LX, int LY, bool VISC, bool RHS>
+cudaError_t launch_stage2dc(const StageArgs& a, cudaStream_t s) {
+  using S = Stage2DC<TX, TY, LX, LY, VISC>;
+  auto k = stage2dc_kernel<TX, TY, LX, LY, VISC, RHS>;
+  static int resident = 0;  // blocks resident on the whole GPU
+  if (resident == 0) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, S::NT, S::SMEM);
+    if (e != cudaSuccess) return e;
+    resident = sms * (per_sm > 0 ? per_sm : 1);
+  }
+  const int ntx = (a.lay.nx + TX - 1) / TX, nty = (a.lay.ny + TY - 1) / TY;
+  const int ntiles = ntx * nty;
+  k<<<ntiles < resident ? ntiles : resident, S::NT, S::SMEM, s>>>(a, ntx, ntiles);
+  return cudaGetLastError();
+}
+
+// tile shapes (TX x TY cells, x / y segment lengths LX / LY) the tuner chooses from:
+// 0-2 concurrent sweeps in persistent blocks, 3 sequential sweeps in one warp per tile
+template <bool VISC, bool RHS>
+cudaError_t launch_stage2d_variant(const StageArgs& a, int variant, cudaStream_t s) {
+  switch (variant) {
+    case 1: return launch_stage2dc<32, 16, 16, 16, VISC, RHS>(a, s);
+    case 2: return launch_stage2dc<64, 16, 16, 16, VISC, RHS>(a, s);
+    case 3: return launch_stage2d<32, 16, 16, 16, VISC, RHS>(a, s);
+    default: return launch_stage2dc<32, 32, 16, 16, VISC, RHS>(a, s);
+  }
 }
 
 template <bool VISC, bool RHS>
@@ -183,13 +226,14 @@ cudaError_t launch_stage1d(const StageArgs& a, cudaStream_t s) {
 }
 }  // namespace
 
-cudaError_t launch_stage(const StageArgs& a, bool visc, bool rhs, cudaStream_t s) {
+cudaError_t launch_stage(const StageArgs& a, bool visc, bool rhs, int variant, cudaStream_t s) {
   if (a.lay.ny == 1) {
     if (visc) return rhs ? launch_stage1d<true, true>(a, s) : launch_stage1d<true, false>(a, s);
     return rhs ? launch_stage1d<false, true>(a, s) : launch_stage1d<false, false>(a, s);
   }
-  if (visc) return rhs ? launch_stage2d<true, true>(a, s) : launch_stage2d<true, false>(a, s);
-  return rhs ? launch_stage2d<false, true>(a, s) : launch_stage2d<false, false>(a, s);
+  if (visc)
+    return rhs ? launch_stage2d_variant<true, true>(a, variant, s) : launch_stage2d_variant<true, false>(a, variant, s);
+  return rhs ? launch_stage2d_variant<false, true>(a, variant, s) : launch_stage2d_variant<false, false>(a, variant, s);
 }
 
 cudaError_t launch_bc_fill(double* U, const Lay& lay, const BcArgs& bc, cudaStream_t s) {

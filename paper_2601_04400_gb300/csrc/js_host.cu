@@ -27,6 +27,8 @@ struct js_ctx {
   double* N = nullptr;  // padded U^n / step output
   double* A = nullptr;  // padded stage buffers
   double* B = nullptr;
+  double* acc = nullptr;   // stage scratch [4][ny][nx]: x-flux differences
+  double* acc2 = nullptr;  // y-flux differences
   unsigned char* tag = nullptr;       // device [ny][nx] or null (no immersed body)
   std::vector<unsigned char> tag_host;
   int n_ghost = 0;
@@ -56,6 +58,7 @@ struct js_ctx {
   double* inflow_acc = nullptr;   // 16
   double* inflow_prim = nullptr;  // 16
   double* qIb = nullptr;     // 4 per ghost
+  int variant = 0;  // stage-kernel tile shape (js_set_tuning)
   // instrumentation
   bool profiling = false;
   std::vector<cudaEvent_t> ev;  // 2 per timed stage launch
@@ -226,6 +229,8 @@ StageArgs base_args(const js_ctx* c) {
   StageArgs a;
   std::memset(&a, 0, sizeof(a));
   a.tag = c->tag;
+  a.acc = c->acc;
+  a.acc2 = c->acc2;
   a.err = c->err;
   a.lay = c->lay;
   a.gamma = c->p.gamma;
@@ -250,7 +255,7 @@ int fill_halos(js_ctx* c, double* X) {
 int stage(js_ctx* c, const StageArgs& a, bool visc, bool rhs) {
   const bool timed = c->profiling && c->ev_used + 2 <= (int)c->ev.size();
   if (timed) JS_CUDA(cudaEventRecord(c->ev[c->ev_used], c->stream));
-  JS_CUDA(js::launch_stage(a, visc, rhs, c->stream));
+  JS_CUDA(js::launch_stage(a, visc, rhs, c->variant, c->stream));
   if (timed) {
     JS_CUDA(cudaEventRecord(c->ev[c->ev_used + 1], c->stream));
     c->ev_used += 2;
@@ -268,6 +273,7 @@ void js_internal_desc(js_ctx* c, js::InstDesc* d) {
   d->N = c->N;
   d->A = c->A;
   d->B = c->B;
+  d->acc = c->acc;
   d->tag = c->tag;
   d->ib = ib_args(c);
   d->bc = c->bc;
@@ -305,7 +311,7 @@ const char* js_strerror(int code) {
 void js_destroy(js_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
-  cudaFree(c->N); cudaFree(c->A); cudaFree(c->B);
+  cudaFree(c->N); cudaFree(c->A); cudaFree(c->B); cudaFree(c->acc); cudaFree(c->acc2);
   cudaFree(c->tag);
   cudaFree(c->ib_dst); cudaFree(c->ib_src); cudaFree(c->ib_w); cudaFree(c->ib_nrm);
   cudaFree(c->err); cudaFree(c->red);
@@ -338,6 +344,8 @@ int js_create(const js_grid* grid, const js_params* params, const js_boundary* b
   const size_t bytes = sizeof(double) * 4 * (size_t)L.plane;
   if (cudaMalloc(&c->N, bytes) != cudaSuccess || cudaMalloc(&c->A, bytes) != cudaSuccess ||
       cudaMalloc(&c->B, bytes) != cudaSuccess || cudaMalloc(&c->err, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&c->acc, sizeof(double) * 4 * (size_t)grid->nx * grid->ny) != cudaSuccess ||
+      cudaMalloc(&c->acc2, sizeof(double) * 4 * (size_t)grid->nx * grid->ny) != cudaSuccess ||
       cudaMalloc(&c->red, 4 * sizeof(unsigned long long)) != cudaSuccess) {
     js_destroy(c);
     return JS_ERR_NOMEM;
@@ -606,6 +614,19 @@ int js_sync_status(js_ctx* c) {
   JS_CUDA(cudaStreamSynchronize(c->stream));
   if (h & js::ERR_TIMEOUT_BIT) return JS_ERR_TIMEOUT;
   if (h & js::ERR_NONPHYSICAL_BIT) return JS_ERR_NONPHYSICAL;
+  return JS_OK;
+}
+
+int js_set_tuning(js_ctx* c, int variant) {
+  if (!c || variant < 0 || variant >= js::STAGE_VARIANTS) return JS_ERR_ARG;
+  c->variant = variant;
+  return JS_OK;
+}
+
+int js_get_tuning(js_ctx* c, int* variant, int* n_variants) {
+  if (!c) return JS_ERR_ARG;
+  if (variant) *variant = c->variant;
+  if (n_variants) *n_variants = js::STAGE_VARIANTS;
   return JS_OK;
 }
 

@@ -11,6 +11,8 @@ struct StageArgs {
   const double* Un;          // padded U^n (RK combination), may alias Uout
   double* Uout;              // padded stage output, or [4][ny][nx] in RHS mode
   const unsigned char* tag;  // [ny][nx] cell tags (0 fluid) or nullptr
+  double* acc;               // [4][ny][nx] scratch: x-flux differences of the stage
+  double* acc2;              // [4][ny][nx] scratch: y-flux differences (concurrent sweeps)
   int* err;                  // device error flag
   Lay lay;
   double gamma, gm1, g1;
@@ -77,6 +79,7 @@ struct InstDesc {
   double* A;
   double* B;
   double* U;                 // user state [4][ny][nx]
+  double* acc;               // stage scratch [4][ny][nx]
   const unsigned char* tag;
   IbArgs ib;
   BcArgs bc;
@@ -86,7 +89,8 @@ struct InstDesc {
   int wall, visc, has_av, ntx, nty;
 };
 
-cudaError_t launch_stage(const StageArgs& a, bool visc, bool rhs, cudaStream_t s);
+constexpr int STAGE_VARIANTS = 4;
+cudaError_t launch_stage(const StageArgs& a, bool visc, bool rhs, int variant, cudaStream_t s);
 cudaError_t launch_bc_fill(double* U, const Lay& lay, const BcArgs& bc, cudaStream_t s);
 cudaError_t launch_ib_fill(double* U, const Lay& lay, const IbArgs& ib, double gamma, int wall, cudaStream_t s);
 cudaError_t launch_pack(const double* U, double* P, const Lay& lay, cudaStream_t s);

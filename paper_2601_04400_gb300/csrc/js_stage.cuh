@@ -1,6 +1,7 @@
 // Fused stage of the FP64 finite-volume step on one 2D tile (arXiv 2601.04400, Sec. 2):
 // conserved tile + 3-cell halo -> primitives in shared memory -> x sweep (WENO5, HLLC,
-// viscous flux) into a shared accumulator -> y sweep, divergence, artificial viscosity and
+// viscous flux) into a global accumulator (it stays in L2; keeping it out of shared memory
+// lets more blocks share an SM's FP64 pipe) -> y sweep, divergence, artificial viscosity and
 // the SSP-RK3 stage combination.  Used by the per-grid stage kernel and by the persistent
 // batched kernel.
 #pragma once
@@ -27,13 +28,28 @@ __device__ __forceinline__ void sweep_line(const double* __restrict__ sq, int ps
     w[c].init(q[base - 3 * st], q[base - 2 * st], q[base - st], q[base]);
   }
   double prevL[4], prevF[4];
+  {
+    // cell -1 of the segment: only its right-face (left-biased) state is needed
+    double Rf[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) w[c].template step<true, false>(sq[c * ps + base - st + 2 * st], prevL[c], Rf[c]);
+  }
 #pragma unroll 1
-  for (int k = -1; k <= L; ++k) {
+  for (int k = 0; k <= L; ++k) {
     const int cell = base + k * st;
     double Lf[4], Rf[4];
+    if (k < L) {
 #pragma unroll
-    for (int c = 0; c < 4; ++c) w[c].step(sq[c * ps + cell + 2 * st], Lf[c], Rf[c]);
-    if (k >= 0) {
+      for (int c = 0; c < 4; ++c) w[c].step(sq[c * ps + cell + 2 * st], Lf[c], Rf[c]);
+    } else {
+      // cell L (first cell of the next segment): only its left-face state is needed
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        w[c].template step<false, true>(sq[c * ps + cell + 2 * st], Lf[c], Rf[c]);
+        Lf[c] = 0.0;  // unused
+      }
+    }
+    {
       // face k - 1/2 between cells k-1 (left state prevL) and k (right state Rf)
       double ql[4], qr[4];
 #pragma unroll
@@ -87,7 +103,8 @@ __device__ __forceinline__ void sweep_line(const double* __restrict__ sq, int ps
 }
 
 // final combination for one interior cell; returns the value stored in the output
-template <bool RHS>
+// dG: raw y-flux differences (scaled here by cy), or already scaled when YSCALED
+template <bool RHS, bool YSCALED = false>
 __device__ __forceinline__ void finish_cell(const StageArgs& a, int gi, int gj, const double acc[4],
                                             const double dG[4], double rho, double p) {
   const long long pid = a.lay.idx(gi, gj);
@@ -99,7 +116,7 @@ __device__ __forceinline__ void finish_cell(const StageArgs& a, int gi, int gj, 
     for (int c = 0; c < 4; ++c) {
       const double* Uc = a.Uin + c * a.lay.plane;
       const double us = RHS ? 0.0 : Uc[pid];
-      double v = fma(-a.cy, dG[c], us - acc[c]);
+      double v = YSCALED ? (us - acc[c]) - dG[c] : fma(-a.cy, dG[c], us - acc[c]);
       if (a.has_av) {
         v = fma(a.avx, (Uc[pid + 1] - 2.0 * Uc[pid]) + Uc[pid - 1], v);
         if (a.lay.ny > 1) v = fma(a.avy, (Uc[pid + a.lay.pitch] - 2.0 * Uc[pid]) + Uc[pid - a.lay.pitch], v);
@@ -155,7 +172,7 @@ struct Stage2D {
   static constexpr int NX_ITEMS = TY * (TX / LX);
   static constexpr int NY_ITEMS = TX * (TY / LY);
   static constexpr int NT = (NX_ITEMS > NY_ITEMS) ? NX_ITEMS : NY_ITEMS;
-  static constexpr size_t SMEM = sizeof(double) * ((size_t)NPL * PS + 4 * TX * TY);
+  static constexpr size_t SMEM = sizeof(double) * (size_t)NPL * PS;
 };
 
 // one tile (bx, by) of one stage; smem holds Stage2D::SMEM bytes; all NT threads take part
@@ -163,7 +180,7 @@ template <int TX, int TY, int LX, int LY, bool VISC, bool RHS>
 __device__ __forceinline__ void stage_tile(const StageArgs& a, int bx, int by, double* smem) {
   using S = Stage2D<TX, TY, LX, LY, VISC, RHS>;
   double* sq = smem;
-  double* acc = smem + S::NPL * S::PS;
+  const long long ncell = (long long)a.lay.nx * a.lay.ny;
   const Gas g{a.gamma, a.gm1, a.g1};
   const int tx0 = bx * TX, ty0 = by * TY;  // interior origin of the tile
   load_tile<TX, TY, S::NPL, S::NT>(a, sq, S::PS, S::SP, tx0, ty0, g);
@@ -172,9 +189,14 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int bx, int by, d
   for (int it = threadIdx.x; it < S::NX_ITEMS; it += S::NT) {
     const int ty = it % TY, xs = (it / TY) * LX;
     const int base = (ty + 3) * S::SP + xs + 3;
+    const int gj = ty0 + ty;
     sweep_line<0, VISC, true, LX>(sq, S::PS, base, 1, S::SP, g, a.vx, [&](int k, const double dF[4]) {
+      const int gi = tx0 + xs + k;
+      if (gi < a.lay.nx && gj < a.lay.ny) {
+        const long long o = (long long)gj * a.lay.nx + gi;
 #pragma unroll
-      for (int c = 0; c < 4; ++c) acc[c * TX * TY + ty * TX + xs + k] = a.cx * dF[c];
+        for (int c = 0; c < 4; ++c) a.acc[c * ncell + o] = __dmul_rn(a.cx, dF[c]);
+      }
     });
   }
   __syncthreads();
@@ -187,14 +209,90 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int bx, int by, d
       const int ty = ys + k, gj = ty0 + ty;
       if (gi < a.lay.nx && gj < a.lay.ny) {
         double ax[4];
+        const long long o = (long long)gj * a.lay.nx + gi;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) ax[c] = acc[c * TX * TY + ty * TX + tx];
+        for (int c = 0; c < 4; ++c) ax[c] = a.acc[c * ncell + o];
+        double ay[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) ay[c] = __dmul_rn(a.cy, dG[c]);  // rounded as when stored
         const int sc = (ty + 3) * S::SP + tx + 3;
-        finish_cell<RHS>(a, gi, gj, ax, dG, sq[sc], sq[3 * S::PS + sc]);
+        finish_cell<RHS, true>(a, gi, gj, ax, ay, sq[sc], sq[3 * S::PS + sc]);
       }
     });
   }
 }
 
+
+// ---------------------------------------------------------------------------------------
+// Concurrent-sweep tile: the x sweep (first NX_ITEMS threads) and the y sweep (next
+// NY_ITEMS threads, warp-aligned) run at the same time on the shared primitive tile and
+// write their scaled flux differences to two global accumulators (L2-resident); after a
+// barrier every thread combines cells of the tile.  Twice the warps per block at the same
+// shared memory: more warps hide the FP64 pipe's latency.
+// ---------------------------------------------------------------------------------------
+template <int TX, int TY, int LX, int LY, bool VISC>
+struct Stage2DC {
+  static constexpr int NPL = VISC ? 5 : 4;
+  static constexpr int SP = TX + 7;
+  static constexpr int PS = (TY + 6) * SP;
+  static constexpr int NX_ITEMS = TY * (TX / LX);
+  static constexpr int NY_ITEMS = TX * (TY / LY);
+  static_assert(NX_ITEMS % 32 == 0 && NY_ITEMS % 32 == 0, "sweep roles must be whole warps");
+  static constexpr int NT = NX_ITEMS + NY_ITEMS;
+  static constexpr size_t SMEM = sizeof(double) * (size_t)NPL * PS;
+};
+
+template <int TX, int TY, int LX, int LY, bool VISC, bool RHS>
+__device__ __forceinline__ void stage_tile_c(const StageArgs& a, int bx, int by, double* smem) {
+  using S = Stage2DC<TX, TY, LX, LY, VISC>;
+  double* sq = smem;
+  const long long ncell = (long long)a.lay.nx * a.lay.ny;
+  const Gas g{a.gamma, a.gm1, a.g1};
+  const int tx0 = bx * TX, ty0 = by * TY;
+  load_tile<TX, TY, S::NPL, S::NT>(a, sq, S::PS, S::SP, tx0, ty0, g);
+  __syncthreads();
+  if (threadIdx.x < S::NX_ITEMS) {
+    const int it = threadIdx.x;
+    const int ty = it % TY, xs = (it / TY) * LX;
+    const int gj = ty0 + ty;
+    sweep_line<0, VISC, true, LX>(sq, S::PS, (ty + 3) * S::SP + xs + 3, 1, S::SP, g, a.vx,
+                                  [&](int k, const double dF[4]) {
+      const int gi = tx0 + xs + k;
+      if (gi < a.lay.nx && gj < a.lay.ny) {
+        const long long o = (long long)gj * a.lay.nx + gi;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) a.acc[c * ncell + o] = __dmul_rn(a.cx, dF[c]);
+      }
+    });
+  } else {
+    const int it = threadIdx.x - S::NX_ITEMS;
+    const int tx = it % TX, ys = (it / TX) * LY;
+    const int gi = tx0 + tx;
+    sweep_line<1, VISC, true, LY>(sq, S::PS, (ys + 3) * S::SP + tx + 3, S::SP, 1, g, a.vy,
+                                  [&](int k, const double dG[4]) {
+      const int gj = ty0 + ys + k;
+      if (gi < a.lay.nx && gj < a.lay.ny) {
+        const long long o = (long long)gj * a.lay.nx + gi;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) a.acc2[c * ncell + o] = __dmul_rn(a.cy, dG[c]);
+      }
+    });
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < TX * TY; e += S::NT) {
+    const int tx = e % TX, ty = e / TX;
+    const int gi = tx0 + tx, gj = ty0 + ty;
+    if (gi >= a.lay.nx || gj >= a.lay.ny) continue;
+    const long long o = (long long)gj * a.lay.nx + gi;
+    double ax[4], ay[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      ax[c] = a.acc[c * ncell + o];
+      ay[c] = a.acc2[c * ncell + o];
+    }
+    const int sc = (ty + 3) * S::SP + tx + 3;
+    finish_cell<RHS, true>(a, gi, gj, ax, ay, sq[sc], sq[3 * S::PS + sc]);
+  }
+}
 
 }  // namespace js

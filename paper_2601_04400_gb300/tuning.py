@@ -1,0 +1,74 @@
+"""Autotuner of the fused stage kernel's tile shape.
+
+Every variant computes identical results; only speed differs.  `autotune` times a few
+js_step calls per variant with CUDA events on the solver's stream, selects the fastest and
+caches the choice in a JSON file keyed by grid size, physics and immersed body, so later
+solvers with the same key start tuned.
+"""
+import json
+import os
+
+_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "tuning.json")
+
+
+def _key(solver):
+    sp = solver._spec
+    return "%dx%d|visc=%d|av=%d|ib=%d" % (sp["nx"], sp["ny"], int(sp["mu"] > 0), int(sp["nu"] > 0),
+                                          int(getattr(solver, "has_ib", False)))
+
+
+def _load():
+    try:
+        with open(_CACHE) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _save(cache):
+    os.makedirs(os.path.dirname(_CACHE), exist_ok=True)
+    tmp = _CACHE + ".tmp%d" % os.getpid()
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    os.replace(tmp, _CACHE)
+
+
+def cached_variant(solver):
+    return _load().get(_key(solver), {}).get("variant")
+
+
+def apply_cached(solver):
+    v = cached_variant(solver)
+    if v is not None:
+        solver.set_tuning(v)
+    return v
+
+
+def autotune(solver, U, reps=3, use_cache=True):
+    """Time every stage-kernel variant on state U (not modified) and select the fastest.
+    Returns {variant: ms per step}."""
+    import torch
+    if use_cache and apply_cached(solver) is not None:
+        return {}
+    dt = 0.5 * solver.max_dt(U, 0.5)
+    _, n = solver.tuning()
+    stream = torch.cuda.current_stream()
+    times = {}
+    work = U.clone()
+    for v in range(n):
+        solver.set_tuning(v)
+        solver.step(work, dt, 1)  # warm-up (first launch sets kernel attributes)
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(reps):
+            solver.step(work, dt, 1)
+        t1.record(stream)
+        t1.synchronize()
+        times[v] = t0.elapsed_time(t1) / reps
+        work.copy_(U)
+    best = min(times, key=times.get)
+    solver.set_tuning(best)
+    cache = _load()
+    cache[_key(solver)] = {"variant": best, "ms_per_step": times}
+    _save(cache)
+    return times

@@ -180,3 +180,24 @@ def test_full_size_matches_oracle(B, which):
     s.step(Ud, dt2, 1)
     assert normwise_err(to_host(Ud), O.step(p, Ug, [dt2])) < TOL
     assert s.status() == 0
+
+
+def test_every_tile_variant_gives_identical_results(B):
+    for prob in (W.riemann2d(100, ny=70), W.shock_cylinder(nx=130, ny=66)):
+        U0 = O.prim_to_cons(prob, W.random_state(prob, seed=8, amp=0.02))
+        s = B.Solver.from_problem(prob)
+        dt = 0.5 * s.max_dt(to_dev(U0), 0.5)
+        _, n = s.tuning()
+        assert n >= 2
+        res = []
+        for v in range(n):
+            s.set_tuning(v)
+            Ud = to_dev(U0)
+            s.step(Ud, dt, 3)
+            res.append(to_host(Ud))
+            Lr = to_host(s.rhs(to_dev(U0)))
+            res.append(Lr)
+        for v in range(1, n):
+            assert np.array_equal(res[2 * v], res[0]), v
+            assert np.array_equal(res[2 * v + 1], res[1]), v
+        assert s.status() == 0
