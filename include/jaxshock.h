@@ -110,6 +110,19 @@ int js_rhs_vjp(js_ctx* ctx, const double* U, const double* lam, double* U_bar, d
 int js_step_vjp(js_ctx* ctx, const double* U_n, double dt, const double* lam_np1, double* lam_n,
                 double* p_bar);
 
+/* Tape for reverse passes over recorded steps (the backward pass of a checkpointed rollout
+ * re-runs a segment forward and then reverses it; recording the stage states saves
+ * js_step_vjp from recomputing them).
+ *   js_tape_reserve(ctx, n)  allocates n slots of three padded stage states (and the adjoint
+ *                            workspace); call it before any stream capture.
+ *   js_step_taped(ctx, U, dt, slot)  = js_step(ctx, U, dt, 1), keeping the three filled
+ *                            stage states of this step in `slot`.
+ *   js_step_vjp_taped(ctx, slot, dt, lam_np1, lam_n, p_bar)  = js_step_vjp for the step
+ *                            recorded in `slot` (same dt), without recomputing its stages. */
+int js_tape_reserve(js_ctx* ctx, int n_slots);
+int js_step_taped(js_ctx* ctx, double* U, double dt, int slot);
+int js_step_vjp_taped(js_ctx* ctx, int slot, double dt, const double* lam_np1, double* lam_n, double* p_bar);
+
 /* Read and clear the device error flag; synchronises the stream.  Returns JS_OK,
  * JS_ERR_NONPHYSICAL or JS_ERR_TIMEOUT (or JS_ERR_CUDA if the stream itself failed). */
 int js_sync_status(js_ctx* ctx);

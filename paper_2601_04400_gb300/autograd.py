@@ -1,10 +1,11 @@
 """Differentiable rollouts of the SSP-RK3 solver step (Sec. 2: U^{n+k} = S(U^{n+k-1}, theta),
 gradients by the chain rule through the unrolled steps, Fig. 1(d)).
 
-Forward steps run js_step; the backward pass walks the steps in reverse with js_step_vjp.
-Only every `checkpoint_every`-th state is kept (default ceil(sqrt(n))); each segment is
-recomputed from its checkpoint during the backward pass, so a rollout of n steps holds about
-2 sqrt(n) states instead of n.
+Forward steps run js_step; the backward pass walks the steps in reverse.  Only every
+`checkpoint_every`-th state is kept (default ceil(sqrt(n))); during the backward pass each
+segment is re-run from its checkpoint with js_step_taped (which records the stage states of
+every step) and reversed with js_step_vjp_taped, so a rollout of n steps holds about
+sqrt(n) checkpoints plus 3 sqrt(n) stage states instead of n states.
 
 theta is the 20-entry parameter vector of the library (gamma, mu, Pr, nu, then the inflow
 state rho, u, v, p of the x-low, x-high, y-low and y-high sides); its gradient is returned
@@ -68,16 +69,16 @@ class _Rollout(torch.autograd.Function):
             lam += inject[n]
         pbar = torch.zeros(B.JS_NPARAM, dtype=torch.float64, device=g.device)
         scratch = torch.empty_like(lam)
+        solver.tape_reserve(every)
         for seg in reversed(range(len(ctx.ckpts))):
             start = seg * every
             stop = min(start + every, n)
-            states = [ctx.ckpts[seg]]
+            # re-run the segment, recording every step's stage states on the tape
             U = ctx.ckpts[seg].clone()
-            for k in range(start, stop - 1):
-                solver.step(U, dts[k], 1)
-                states.append(U.clone())
+            for k in range(start, stop):
+                solver.step_taped(U, dts[k], k - start)
             for k in reversed(range(start, stop)):
-                solver.step_vjp(states[k - start], dts[k], lam, lam_n=scratch, p_bar=pbar)
+                solver.step_vjp_taped(k - start, dts[k], lam, lam_n=scratch, p_bar=pbar)
                 lam, scratch = scratch, lam
                 if k in inject:
                     lam = lam + inject[k]

@@ -57,6 +57,9 @@ SIGNATURES = {
     "js_step_vjp": (_I, [_P, _P, _D, _P, _P, _P]),
     "js_sync_status": (_I, [_P]),
     "js_ib_info": (_I, [_P, C.POINTER(_I), _P]),
+    "js_tape_reserve": (_I, [_P, _I]),
+    "js_step_taped": (_I, [_P, _P, _D, _I]),
+    "js_step_vjp_taped": (_I, [_P, _I, _D, _P, _P, _P]),
     "js_set_tuning": (_I, [_P, _I]),
     "js_get_tuning": (_I, [_P, C.POINTER(_I), C.POINTER(_I)]),
     "js_profile_begin": (_I, [_P, _I]),
@@ -299,6 +302,21 @@ class Solver:
         lam_n = torch.empty_like(U_n) if lam_n is None else lam_n
         p_bar = torch.zeros(JS_NPARAM, dtype=torch.float64, device=U_n.device) if p_bar is None else p_bar
         js_step_vjp(self.ctx, U_n, dt, lam_np1, lam_n, p_bar)
+        return lam_n, p_bar
+
+    def tape_reserve(self, n_slots):
+        _check(lib().js_tape_reserve(self.ctx, int(n_slots)), "js_tape_reserve")
+
+    def step_taped(self, U, dt, slot):
+        _check(lib().js_step_taped(self.ctx, _ptr(U), float(dt), int(slot)), "js_step_taped")
+        return U
+
+    def step_vjp_taped(self, slot, dt, lam_np1, lam_n=None, p_bar=None):
+        import torch
+        lam_n = torch.empty_like(lam_np1) if lam_n is None else lam_n
+        p_bar = torch.zeros(JS_NPARAM, dtype=torch.float64, device=lam_np1.device) if p_bar is None else p_bar
+        _check(lib().js_step_vjp_taped(self.ctx, int(slot), float(dt), _ptr(lam_np1), _ptr(lam_n), _ptr(p_bar)),
+               "js_step_vjp_taped")
         return lam_n, p_bar
 
     def status(self):

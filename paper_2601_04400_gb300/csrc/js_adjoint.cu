@@ -46,6 +46,14 @@ __device__ __forceinline__ bool valid_padded(const Lay& L, long long t, int& i, 
   return true;
 }
 
+// Position of cell k of line `line` in the saved arrays: y lines use the padded layout
+// (lanes = consecutive columns); x lines are stored transposed so that the lanes of a warp
+// (consecutive rows) also write consecutive addresses.
+template <int DIR>
+__device__ __forceinline__ long long save_id(const AdjArgs& a, int k, int line) {
+  return (DIR == 0) ? (long long)(k + 3) * a.tpitch + (line + a.lay.gy) : a.lay.idx(line, k);
+}
+
 }  // namespace
 
 // =======================================================================================
@@ -102,7 +110,7 @@ __global__ void adj_prims_kernel(AdjArgs a) {
 // DIR 0: lines are rows, faces f in [0, nx] (face f between cells f-1 and f).
 // DIR 1: lines are columns, faces f in [0, ny].
 template <int DIR, bool VISC, bool HAS_T>
-__global__ void __launch_bounds__(128) adj_pass1_kernel(AdjArgs a, int seg_len) {
+__global__ void __launch_bounds__(64) adj_pass1_kernel(AdjArgs a, int seg_len) {
   const Lay& L = a.lay;
   const int nline = (DIR == 0) ? L.ny : L.nx;
   const int ncell = (DIR == 0) ? L.nx : L.ny;
@@ -142,6 +150,7 @@ __global__ void __launch_bounds__(128) adj_pass1_kernel(AdjArgs a, int seg_len) 
 #pragma unroll 1
     for (int i = f0 - 1; i < f1; ++i) {
       const long long ci = cell_id(i);
+      const long long si = save_id<DIR>(a, i, line);
       double Lf[4], Rf[4];
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
@@ -154,7 +163,7 @@ __global__ void __launch_bounds__(128) adj_pass1_kernel(AdjArgs a, int seg_len) 
         double sv[WENO_SAVE];
         weno_cell_fwd(q0[c], d[c], Lf[c], Rf[c], sv);
 #pragma unroll
-        for (int k = 0; k < WENO_SAVE; ++k) a.wsave[(long long)(wdir + c * WENO_SAVE + k) * L.plane + ci] = sv[k];
+        for (int k = 0; k < WENO_SAVE; ++k) a.wsave[(long long)(wdir + c * WENO_SAVE + k) * a.splane + si] = sv[k];
         q0[c] = q1[c];
         q1[c] = q2;
       }
@@ -185,14 +194,14 @@ __global__ void __launch_bounds__(128) adj_pass1_kernel(AdjArgs a, int seg_len) 
           for (int c = 0; c < 4; ++c) {
             atomicAdd(a.Qb + c * L.plane + ca, bql[c]);
             atomicAdd(a.Qb + c * L.plane + cb, bqr[c]);
-            a.fadj[(long long)(fdir + c) * L.plane + cb] = 0.0;
-            a.fadj[(long long)(fdir + 4 + c) * L.plane + cb] = 0.0;
+            a.fadj[(long long)(fdir + c) * a.splane + si] = 0.0;
+            a.fadj[(long long)(fdir + 4 + c) * a.splane + si] = 0.0;
           }
         } else {
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
-            a.fadj[(long long)(fdir + c) * L.plane + cb] = bql[c];      // left state of face
-            a.fadj[(long long)(fdir + 4 + c) * L.plane + cb] = bqr[c];  // right state of face
+            a.fadj[(long long)(fdir + c) * a.splane + si] = bql[c];      // left state of face
+            a.fadj[(long long)(fdir + 4 + c) * a.splane + si] = bqr[c];  // right state of face
           }
         }
         if (VISC) {
@@ -259,7 +268,7 @@ __global__ void __launch_bounds__(128) adj_pass1_kernel(AdjArgs a, int seg_len) 
 // pass 2: WENO reverse from the saved internals, accumulated along the line
 // =======================================================================================
 template <int DIR>
-__global__ void __launch_bounds__(128) adj_pass2_kernel(AdjArgs a, int seg_len) {
+__global__ void __launch_bounds__(64) adj_pass2_kernel(AdjArgs a, int seg_len) {
   const Lay& L = a.lay;
   const int nline = (DIR == 0) ? L.ny : L.nx;
   const int ncell = (DIR == 0) ? L.nx : L.ny;
@@ -279,16 +288,18 @@ __global__ void __launch_bounds__(128) adj_pass2_kernel(AdjArgs a, int seg_len) 
     double* qb = a.Qb + c * L.plane;
     double win[5] = {0.0, 0.0, 0.0, 0.0, 0.0};  // adjoints of cells i-2 .. i+2
     long long ci = cell_id(c0);
+    const long long sst = (DIR == 0) ? a.tpitch : L.pitch;  // stride along the line in saved arrays
+    long long si = save_id<DIR>(a, c0, line);
     double qm2 = q[ci - 2 * st], qm1 = q[ci - st], qc = q[ci], qp1 = q[ci + st];
 #pragma unroll 1
-    for (int i = c0; i < c1; ++i, ci += st) {
+    for (int i = c0; i < c1; ++i, ci += st, si += sst) {
       const double qp2 = q[ci + 2 * st];
       Dl d{qm1 - qm2, qc - qm1, qp1 - qc, qp2 - qp1};
       double sv[WENO_SAVE];
 #pragma unroll
-      for (int k = 0; k < WENO_SAVE; ++k) sv[k] = a.wsave[(long long)(wdir + c * WENO_SAVE + k) * L.plane + ci];
-      const double Lb = a.fadj[(long long)(fdir + c) * L.plane + ci + st];  // left state of face i+1/2
-      const double Rb = a.fadj[(long long)(fdir + 4 + c) * L.plane + ci];   // right state of face i-1/2
+      for (int k = 0; k < WENO_SAVE; ++k) sv[k] = a.wsave[(long long)(wdir + c * WENO_SAVE + k) * a.splane + si];
+      const double Lb = a.fadj[(long long)(fdir + c) * a.splane + si + sst];  // left state of face i+1/2
+      const double Rb = a.fadj[(long long)(fdir + 4 + c) * a.splane + si];    // right state of face i-1/2
       double g[5];
       weno_cell_vjp(d, sv, Lb, Rb, g);
 #pragma unroll
@@ -530,7 +541,9 @@ __global__ void adj_unpack_add_kernel(const double* __restrict__ P, const double
 // launchers
 // =======================================================================================
 namespace {
-constexpr int kSeg1 = 32, kSeg2 = 32;
+// short segments and small blocks: enough blocks to fill every SM (one line per thread
+// would leave most of the GPU idle); pass 1 pays one extra WENO cell per segment
+constexpr int kSeg1 = 16, kSeg2 = 8, kBlk = 64;
 
 unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
@@ -539,12 +552,12 @@ cudaError_t pass1(const AdjArgs& a, bool visc, bool has_t, cudaStream_t s) {
   const int nline = (DIR == 0) ? a.lay.ny : a.lay.nx;
   const int ncell = (DIR == 0) ? a.lay.nx : a.lay.ny;
   const long long items = (long long)nline * ((ncell + 1 + kSeg1 - 1) / kSeg1);
-  const unsigned g = blocks_for(items, 128);
+  const unsigned g = blocks_for(items, kBlk);
   if (visc) {
-    if (has_t) adj_pass1_kernel<DIR, true, true><<<g, 128, 0, s>>>(a, kSeg1);
-    else adj_pass1_kernel<DIR, true, false><<<g, 128, 0, s>>>(a, kSeg1);
+    if (has_t) adj_pass1_kernel<DIR, true, true><<<g, kBlk, 0, s>>>(a, kSeg1);
+    else adj_pass1_kernel<DIR, true, false><<<g, kBlk, 0, s>>>(a, kSeg1);
   } else {
-    adj_pass1_kernel<DIR, false, false><<<g, 128, 0, s>>>(a, kSeg1);
+    adj_pass1_kernel<DIR, false, false><<<g, kBlk, 0, s>>>(a, kSeg1);
   }
   return cudaGetLastError();
 }
@@ -554,7 +567,7 @@ cudaError_t pass2(const AdjArgs& a, cudaStream_t s) {
   const int nline = (DIR == 0) ? a.lay.ny : a.lay.nx;
   const int ncell = (DIR == 0) ? a.lay.nx : a.lay.ny;
   const long long items = (long long)nline * ((ncell + 2 + kSeg2 - 1) / kSeg2);
-  adj_pass2_kernel<DIR><<<blocks_for(items, 128), 128, 0, s>>>(a, kSeg2);
+  adj_pass2_kernel<DIR><<<blocks_for(items, kBlk), kBlk, 0, s>>>(a, kSeg2);
   return cudaGetLastError();
 }
 }  // namespace

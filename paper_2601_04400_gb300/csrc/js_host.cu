@@ -59,6 +59,8 @@ struct js_ctx {
   double* inflow_prim = nullptr;  // 16
   double* qIb = nullptr;     // 4 per ghost
   int variant = 0;  // stage-kernel tile shape (js_set_tuning)
+  // tape: per slot the three filled stage states of one recorded step
+  std::vector<double*> tape;
   // instrumentation
   bool profiling = false;
   std::vector<cudaEvent_t> ev;  // 2 per timed stage launch
@@ -319,6 +321,7 @@ void js_destroy(js_ctx* c) {
   cudaFree(c->Q); cudaFree(c->Qb); cudaFree(c->lam); cudaFree(c->P0); cudaFree(c->P1); cudaFree(c->Uacc);
   cudaFree(c->wsave); cudaFree(c->fadj); cudaFree(c->inflow_acc); cudaFree(c->inflow_prim); cudaFree(c->qIb);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+  for (double* t : c->tape) cudaFree(t);
   delete c;
 }
 
@@ -465,16 +468,28 @@ int js_step(js_ctx* c, double* U, double dt, int n_steps) {
 
 namespace {
 
+// saved-array layouts: y lines padded (pitch x H), x lines transposed ((nx+6) x tpitch)
+int transposed_pitch(const js_ctx* c) { return (c->lay.H + 3) / 4 * 4; }
+long long saved_plane(const js_ctx* c) {
+  const long long t = (long long)(c->lay.nx + 6) * transposed_pitch(c);
+  const long long m = t > c->lay.plane ? t : c->lay.plane;
+  return (m + 31) / 32 * 32;
+}
+
 int adj_reserve(js_ctx* c) {
   if (c->adj_ready) return JS_OK;
   const size_t pl = sizeof(double) * (size_t)c->lay.plane;
   struct { double** p; size_t planes; } bufs[] = {
-      {&c->Q, 5}, {&c->Qb, 5}, {&c->lam, 4}, {&c->P0, 4}, {&c->P1, 4}, {&c->Uacc, 4},
-      {&c->wsave, 2 * 4 * 7 /* js::WENO_SAVE */}, {&c->fadj, 16}};
+      {&c->Q, 5}, {&c->Qb, 5}, {&c->lam, 4}, {&c->P0, 4}, {&c->P1, 4}, {&c->Uacc, 4}};
   for (auto& b : bufs) {
     if (cudaMalloc(b.p, b.planes * pl) != cudaSuccess) return JS_ERR_NOMEM;
     JS_CUDA(cudaMemset(*b.p, 0, b.planes * pl));
   }
+  const size_t spl = sizeof(double) * (size_t)saved_plane(c);
+  if (cudaMalloc(&c->wsave, 2 * 4 * 7 * spl) != cudaSuccess || cudaMalloc(&c->fadj, 16 * spl) != cudaSuccess)
+    return JS_ERR_NOMEM;
+  JS_CUDA(cudaMemset(c->wsave, 0, 2 * 4 * 7 * spl));
+  JS_CUDA(cudaMemset(c->fadj, 0, 16 * spl));
   if (cudaMalloc(&c->inflow_acc, 16 * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&c->inflow_prim, 16 * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&c->qIb, sizeof(double) * 4 * (size_t)(c->n_ghost > 0 ? c->n_ghost : 1)) != cudaSuccess)
@@ -494,6 +509,8 @@ js::AdjArgs adj_args(js_ctx* c, const double* X, double* Ub, double* p_bar) {
   a.Ub = Ub;
   a.wsave = c->wsave;
   a.fadj = c->fadj;
+  a.splane = saved_plane(c);
+  a.tpitch = transposed_pitch(c);
   a.pbar = p_bar;
   a.tag = c->tag;
   const double g = c->p.gamma;
@@ -596,6 +613,84 @@ int js_step_vjp(js_ctx* c, const double* U_n, double dt, const double* lam_np1, 
   double* dst = c->P1;
   for (int s = 2; s >= 0; --s) {
     if ((rc = adj_stage(c, X[s], src, dst, ra[s], rb[s], dt, false, p_bar))) return rc;
+    double* t = src;
+    src = dst;
+    dst = t;
+  }
+  JS_CUDA(js::launch_adj_unpack(src, c->Uacc, lam_n, c->lay, c->stream));
+  ++c->launches;
+  return JS_OK;
+}
+
+namespace {
+size_t state_bytes(const js_ctx* c) { return sizeof(double) * 4 * (size_t)c->lay.plane; }
+double* tape_state(js_ctx* c, int slot, int s) { return c->tape[(size_t)slot * 3 + s]; }
+
+// one SSP-RK3 step whose three stage inputs live in X[0..2] (X[0] already holds U^n);
+// the step result goes to `out` (padded)
+int step_through(js_ctx* c, double* const X[3], double* out, double dt) {
+  StageArgs a = base_args(c);
+  a.cx = dt / c->g.dx;
+  a.cy = dt / c->g.dy;
+  a.avx = dt * c->p.nu / (c->g.dx * c->g.dx);
+  a.avy = dt * c->p.nu / (c->g.dy * c->g.dy);
+  const bool visc = c->p.mu > 0.0;
+  const double ra[3] = {0.0, 0.75, 1.0 / 3.0};
+  const double rb[3] = {1.0, 0.25, 2.0 / 3.0};
+  for (int s = 0; s < 3; ++s) {
+    int rc = fill_halos(c, X[s]);
+    if (rc) return rc;
+    a.Uin = X[s];
+    a.Un = X[0];
+    a.Uout = (s < 2) ? X[s + 1] : out;
+    a.rk_a = ra[s];
+    a.rk_b = rb[s];
+    a.use_un = (s > 0) ? 1 : 0;
+    if ((rc = stage(c, a, visc, false))) return rc;
+  }
+  return JS_OK;
+}
+}  // namespace
+
+int js_tape_reserve(js_ctx* c, int n_slots) {
+  if (!c || n_slots < 0) return JS_ERR_ARG;
+  const size_t need = (size_t)n_slots * 3;
+  while (c->tape.size() < need) {
+    double* p = nullptr;
+    if (cudaMalloc(&p, state_bytes(c)) != cudaSuccess) return JS_ERR_NOMEM;
+    if (cudaMemset(p, 0, state_bytes(c)) != cudaSuccess) { cudaFree(p); return JS_ERR_CUDA; }
+    c->tape.push_back(p);
+  }
+  int rc = adj_reserve(c);
+  return rc;
+}
+
+int js_step_taped(js_ctx* c, double* U, double dt, int slot) {
+  if (!c || !U || !(dt > 0.0) || slot < 0 || (size_t)(slot + 1) * 3 > c->tape.size()) return JS_ERR_ARG;
+  double* X[3] = {tape_state(c, slot, 0), tape_state(c, slot, 1), tape_state(c, slot, 2)};
+  JS_CUDA(js::launch_pack(U, X[0], c->lay, c->stream));
+  int rc = step_through(c, X, c->N, dt);
+  if (rc) return rc;
+  JS_CUDA(js::launch_unpack(c->N, U, c->lay, c->stream));
+  c->launches += 2;
+  return JS_OK;
+}
+
+int js_step_vjp_taped(js_ctx* c, int slot, double dt, const double* lam_np1, double* lam_n, double* p_bar) {
+  if (!c || !lam_np1 || !lam_n || !(dt > 0.0) || slot < 0 || (size_t)(slot + 1) * 3 > c->tape.size())
+    return JS_ERR_ARG;
+  int rc = adj_reserve(c);
+  if (rc) return rc;
+  if ((rc = upload_inflow(c))) return rc;
+  JS_CUDA(js::launch_pack(lam_np1, c->P0, c->lay, c->stream));
+  ++c->launches;
+  JS_CUDA(cudaMemsetAsync(c->Uacc, 0, state_bytes(c), c->stream));
+  const double ra[3] = {0.0, 0.75, 1.0 / 3.0};
+  const double rb[3] = {1.0, 0.25, 2.0 / 3.0};
+  double* src = c->P0;
+  double* dst = c->P1;
+  for (int s = 2; s >= 0; --s) {
+    if ((rc = adj_stage(c, tape_state(c, slot, s), src, dst, ra[s], rb[s], dt, false, p_bar))) return rc;
     double* t = src;
     src = dst;
     dst = t;

@@ -53,8 +53,10 @@ struct AdjArgs {
   double* lam;               // padded lambda' (4 planes), zero outside fluid cells
   double* Qb;                // padded primitive adjoints (5 planes)
   double* Ub;                // padded conserved adjoints of X (4 planes)
-  double* wsave;             // WENO internals [dir][var][7] planes
-  double* fadj;              // face-state adjoints [dir][left/right][var] planes
+  double* wsave;             // WENO internals [dir][var][7] planes of splane doubles
+  double* fadj;              // face-state adjoints [dir][left/right][var] planes of splane
+  long long splane;          // plane size of wsave / fadj (>= both layouts below)
+  int tpitch;                // x-direction planes are stored transposed: (i+3)*tpitch + j+gy
   double* pbar;              // parameter gradient (JS_NPARAM) or nullptr
   const unsigned char* tag;
   Gas gas;

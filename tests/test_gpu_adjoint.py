@@ -143,3 +143,21 @@ def test_step_vjp_dot_product(B, which):
     rhs = np.dot(to_host(Ub).reshape(-1), v.reshape(-1)) + np.dot(to_host(pb), dth)
     scale = np.abs(lam).sum() * np.abs(Jv).max()
     assert abs(lhs - rhs) <= 1e-12 * scale
+
+
+def test_taped_step_and_vjp_equal_the_recomputing_ones(B):
+    prob = W.shock_cylinder(nx=96, ny=64, Lx=6.0, Ly=4.0, Re=300.0)
+    U = O.prim_to_cons(prob, W.random_state(prob, seed=9, amp=0.02))
+    dt = 0.4 * O.max_dt(prob, U, 0.5)
+    lam = W.uniform_normal(U.shape, seed=13)
+    s = B.Solver.from_problem(prob)
+    s.tape_reserve(3)
+    Ut, Ur = to_dev(U), to_dev(U)
+    s.step_taped(Ut, dt, 2)
+    s.step(Ur, dt, 1)
+    assert np.array_equal(to_host(Ut), to_host(Ur))
+    lt, pt = s.step_vjp_taped(2, dt, to_dev(lam))
+    lr, pr = s.step_vjp(to_dev(U), dt, to_dev(lam))
+    assert s.status() == 0
+    assert np.abs(to_host(lt) - to_host(lr)).max() <= 1e-12 * np.abs(to_host(lr)).max()
+    assert np.abs(to_host(pt) - to_host(pr)).max() <= 1e-12 * np.abs(to_host(pr)).max()
