@@ -110,12 +110,11 @@ __global__ void adj_prims_kernel(AdjArgs a) {
 // DIR 0: lines are rows, faces f in [0, nx] (face f between cells f-1 and f).
 // DIR 1: lines are columns, faces f in [0, ny].
 template <int DIR, bool VISC, bool HAS_T>
-__global__ void __launch_bounds__(64) adj_pass1_kernel(AdjArgs a, int seg_len) {
+__device__ __forceinline__ void pass1_body(const AdjArgs& a, int seg_len, long long item) {
   const Lay& L = a.lay;
   const int nline = (DIR == 0) ? L.ny : L.nx;
   const int ncell = (DIR == 0) ? L.nx : L.ny;
   const int nseg = (ncell + 1 + seg_len - 1) / seg_len;
-  const long long item = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const bool active = item < (long long)nline * nseg;
   double gb = 0.0, mub = 0.0, prb = 0.0;
   if (active) {
@@ -264,16 +263,24 @@ __global__ void __launch_bounds__(64) adj_pass1_kernel(AdjArgs a, int seg_len) {
   }
 }
 
+// x lines in blocks [0, bx), y lines (2D) in the blocks after them: one launch, both directions
+template <bool VISC, bool HAS_T>
+__global__ void __launch_bounds__(64) adj_pass1_kernel(AdjArgs a, int seg_len, int bx) {
+  if ((int)blockIdx.x < bx)
+    pass1_body<0, VISC, HAS_T>(a, seg_len, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+  else
+    pass1_body<1, VISC, HAS_T>(a, seg_len, (long long)(blockIdx.x - bx) * blockDim.x + threadIdx.x);
+}
+
 // =======================================================================================
 // pass 2: WENO reverse from the saved internals, accumulated along the line
 // =======================================================================================
 template <int DIR>
-__global__ void __launch_bounds__(64) adj_pass2_kernel(AdjArgs a, int seg_len) {
+__device__ __forceinline__ void pass2_body(const AdjArgs& a, int seg_len, long long item) {
   const Lay& L = a.lay;
   const int nline = (DIR == 0) ? L.ny : L.nx;
   const int ncell = (DIR == 0) ? L.nx : L.ny;
   const int nseg = (ncell + 2 + seg_len - 1) / seg_len;  // cells -1 .. ncell
-  const long long item = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (item >= (long long)nline * nseg) return;
   const int line = (int)(item % nline), seg = (int)(item / nline);
   const int c0 = -1 + seg * seg_len;
@@ -319,6 +326,13 @@ __global__ void __launch_bounds__(64) adj_pass2_kernel(AdjArgs a, int seg_len) {
     // flush cells c1-2 .. c1+1
     for (int k = 0; k < 4; ++k) atomicAdd(qb + ci + (k - 2) * st, win[k]);
   }
+}
+
+__global__ void __launch_bounds__(64) adj_pass2_kernel(AdjArgs a, int seg_len, int bx) {
+  if ((int)blockIdx.x < bx)
+    pass2_body<0>(a, seg_len, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+  else
+    pass2_body<1>(a, seg_len, (long long)(blockIdx.x - bx) * blockDim.x + threadIdx.x);
 }
 
 // =======================================================================================
@@ -547,27 +561,28 @@ constexpr int kSeg1 = 16, kSeg2 = 8, kBlk = 64;
 
 unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
-template <int DIR>
-cudaError_t pass1(const AdjArgs& a, bool visc, bool has_t, cudaStream_t s) {
-  const int nline = (DIR == 0) ? a.lay.ny : a.lay.nx;
-  const int ncell = (DIR == 0) ? a.lay.nx : a.lay.ny;
-  const long long items = (long long)nline * ((ncell + 1 + kSeg1 - 1) / kSeg1);
-  const unsigned g = blocks_for(items, kBlk);
+long long line_items(const AdjArgs& a, int dir, int extra, int seg) {
+  const int nline = (dir == 0) ? a.lay.ny : a.lay.nx;
+  const int ncell = (dir == 0) ? a.lay.nx : a.lay.ny;
+  return (long long)nline * ((ncell + extra + seg - 1) / seg);
+}
+
+cudaError_t pass1(const AdjArgs& a, bool visc, bool two_d, cudaStream_t s) {
+  const int bx = (int)blocks_for(line_items(a, 0, 1, kSeg1), kBlk);
+  const int by = two_d ? (int)blocks_for(line_items(a, 1, 1, kSeg1), kBlk) : 0;
   if (visc) {
-    if (has_t) adj_pass1_kernel<DIR, true, true><<<g, kBlk, 0, s>>>(a, kSeg1);
-    else adj_pass1_kernel<DIR, true, false><<<g, kBlk, 0, s>>>(a, kSeg1);
+    if (two_d) adj_pass1_kernel<true, true><<<bx + by, kBlk, 0, s>>>(a, kSeg1, bx);
+    else adj_pass1_kernel<true, false><<<bx + by, kBlk, 0, s>>>(a, kSeg1, bx);
   } else {
-    adj_pass1_kernel<DIR, false, false><<<g, kBlk, 0, s>>>(a, kSeg1);
+    adj_pass1_kernel<false, false><<<bx + by, kBlk, 0, s>>>(a, kSeg1, bx);
   }
   return cudaGetLastError();
 }
 
-template <int DIR>
-cudaError_t pass2(const AdjArgs& a, cudaStream_t s) {
-  const int nline = (DIR == 0) ? a.lay.ny : a.lay.nx;
-  const int ncell = (DIR == 0) ? a.lay.nx : a.lay.ny;
-  const long long items = (long long)nline * ((ncell + 2 + kSeg2 - 1) / kSeg2);
-  adj_pass2_kernel<DIR><<<blocks_for(items, kBlk), kBlk, 0, s>>>(a, kSeg2);
+cudaError_t pass2(const AdjArgs& a, bool two_d, cudaStream_t s) {
+  const int bx = (int)blocks_for(line_items(a, 0, 2, kSeg2), kBlk);
+  const int by = two_d ? (int)blocks_for(line_items(a, 1, 2, kSeg2), kBlk) : 0;
+  adj_pass2_kernel<<<bx + by, kBlk, 0, s>>>(a, kSeg2, bx);
   return cudaGetLastError();
 }
 }  // namespace
@@ -585,18 +600,9 @@ cudaError_t launch_adj_stage(const AdjArgs& a, const BcArgs& bc, const IbArgs& i
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const bool two_d = L.ny > 1;
-  if ((e = pass1<0>(a, a.visc != 0, two_d, s)) != cudaSuccess) return e;
-  ++n;
-  if (two_d) {
-    if ((e = pass1<1>(a, a.visc != 0, true, s)) != cudaSuccess) return e;
-    ++n;
-  }
-  if ((e = pass2<0>(a, s)) != cudaSuccess) return e;
-  ++n;
-  if (two_d) {
-    if ((e = pass2<1>(a, s)) != cudaSuccess) return e;
-    ++n;
-  }
+  if ((e = pass1(a, a.visc != 0, two_d, s)) != cudaSuccess) return e;
+  if ((e = pass2(a, two_d, s)) != cudaSuccess) return e;
+  n += 2;
   adj_primvjp_kernel<<<gp, 256, 0, s>>>(a);
   ++n;
   cudaMemsetAsync(inflow_acc, 0, 16 * sizeof(double), s);
