@@ -30,6 +30,10 @@ import numpy as np  # noqa: E402
 FLOPS_PER_CELL_STAGE = {"riemann2d": 1281.0, "shock_cylinder": 1357.0}
 # FP64 peak of one GB300: 152 SMs x 2070 MHz boost, NVIDIA's 1.25 TFLOP/s FP64 figure.
 FP64_PEAK_TFLOPS = 1.25
+# DRAM bytes (read + write) per stage-kernel launch, mean of the three stages of one step,
+# from the ncu capture summarised in profiles/stage2dc_riemann2d_1024.md (variant 0); None
+# for other workloads or variants.
+STAGE_TRAFFIC_BYTES = {("riemann2d", 0): 121.6e6}
 L2_FLUSH_BYTES = 256 << 20
 METRIC = "FP64 cell-updates/s per RK step on 1 GB300 (% roofline); adjoint/forward time ratio"
 
@@ -308,7 +312,8 @@ def run_ours(args):
                        "step": "CFL reduction + 3 x (IB fill, halo fill, fused stage kernel)",
                        "stage_variant": solver.tuning()[0]},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                         "frac": achieved / FP64_PEAK_TFLOPS,
+                         "traffic": STAGE_TRAFFIC_BYTES.get((args.workload, solver.tuning()[0])),
                          "kernel": "stage2d (fused WENO5-HLLC stage)", "stage_ms_avg": stage_avg,
                          "flops_per_launch": flop_launch},
             "e2e": {"value": e2e_value, "unit": "cell-updates/s", "h2d_bytes_per_step": state_bytes,
