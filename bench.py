@@ -331,13 +331,75 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batched(args):
+    """Many independent shock-cylinder instances: one persistent launch per js_batch_step
+    (device CFL per instance) against one-at-a-time js_max_dt + js_step per instance."""
+    import torch
+    from paper_2601_04400_gb300 import binding as B
+    from paper_2601_04400_gb300 import workloads as W
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    probs = W.batched_cases(args.instances, seed=0)
+    # instances are sharded over ranks (no exchange between them)
+    mine = [p for k, p in enumerate(probs) if k % world == rank]
+    stream = torch.cuda.current_stream()
+    states = []
+    for p in mine:
+        s = B.Solver.from_problem(p, stream=stream)
+        states.append(s.prim_to_cons(torch.tensor(p.W0, dtype=torch.float64, device="cuda")))
+        s.close()
+    cells = sum(p.cells for p in mine)
+    batch = B.Batch(mine, stream=stream)
+    work = [U.clone() for U in states]
+    batch.set_states(work)
+    batch.step(0.5, args.warmup)
+    torch.cuda.synchronize()
+    if batch.status() != 0:
+        raise SystemExit("batched warm-up failed")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    batch.step(0.5, args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    t_batch = e0.elapsed_time(e1)
+    ok = batch.status() == 0
+    # one at a time: each instance its own context, js_max_dt + js_step per step
+    solvers = [B.Solver.from_problem(p, stream=stream) for p in mine]
+    seq = [U.clone() for U in states]
+    for s, U in zip(solvers, seq):
+        for _ in range(args.warmup):
+            s.step(U, s.max_dt(U, 0.5), 1)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for s, U in zip(solvers, seq):
+        for _ in range(args.steps):
+            s.step(U, s.max_dt(U, 0.5), 1)
+    e1.record(stream)
+    e1.synchronize()
+    t_seq = e0.elapsed_time(e1)
+    info = batch.info()
+    if rank == 0:
+        print(json.dumps({
+            "metric": "FP64 cell-updates/s, batched shock-cylinder instances", "value": cells * args.steps / (t_batch * 1e-3),
+            "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_batch / args.steps, "higher_is_better": True, "scaling": "weak", "dtype": "f64",
+            "data": "synthetic", "status_ok": ok,
+            "config": {"workload": "%d viscous shock-cylinder instances (seed 0: Mach U[1.5,3], radius U[0.3,0.7], "
+                                   "nx 128..512, ny 128..256), per-instance device CFL 0.5" % len(mine),
+                       "cells": cells, "persistent_blocks": info["blocks"], "tiles": info["tiles"]},
+            "one_at_a_time": {"value": cells * args.steps / (t_seq * 1e-3), "ms_per_step": t_seq / args.steps,
+                              "how": "per instance: js_max_dt (synchronising) + js_step, one step at a time"},
+            "speedup_vs_one_at_a_time": t_seq / t_batch}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="riemann2d", choices=["riemann2d", "shock_cylinder"])
+    ap.add_argument("--workload", default="riemann2d", choices=["riemann2d", "shock_cylinder", "batched"])
+    ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
@@ -345,6 +407,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
     else:
         run_ours(args)
 

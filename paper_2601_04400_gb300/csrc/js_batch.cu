@@ -28,10 +28,12 @@
 
 namespace js {
 
-constexpr int BTX = 32, BTY = 16, BLX = 16, BLY = 16;
-using BStageV = Stage2D<BTX, BTY, BLX, BLY, true, false>;
-using BStageE = Stage2D<BTX, BTY, BLX, BLY, false, false>;
-static_assert(BStageV::NT == 32 && BStageE::NT == 32, "batched kernel assumes one warp per block");
+// the per-grid default tile (variant 0): 32x32 cells, concurrent x/y sweeps
+constexpr int BTX = 32, BTY = 32, BLX = 16, BLY = 16;
+using BStageV = Stage2DC<BTX, BTY, BLX, BLY, true>;
+using BStageE = Stage2DC<BTX, BTY, BLX, BLY, false>;
+constexpr int BNT = BStageV::NT;
+static_assert(BStageV::NT == BStageE::NT && BNT % 32 == 0, "one block shape for both physics");
 
 struct BatchArgs {
   const InstDesc* inst;
@@ -113,11 +115,11 @@ __device__ __forceinline__ double inst_dt(const InstDesc& d, const unsigned long
   return dt;
 }
 
-__global__ void __launch_bounds__(32) batch_kernel(BatchArgs b) {
+__global__ void __launch_bounds__(BNT) batch_kernel(BatchArgs b) {
   extern __shared__ double smem[];
   const int ntiles = b.tile0[b.count];
   const long long nghost = b.ghost0[b.count], nhalo = b.halo0[b.count];
-  const int lane = threadIdx.x;
+  const int tid = threadIdx.x, lane = threadIdx.x & 31;
   // ---- pack user states; reset both reduction buffers
   for (int it = blockIdx.x; it < ntiles; it += gridDim.x) {
     const int k = find_inst(b.tile0, b.count, it);
@@ -125,7 +127,7 @@ __global__ void __launch_bounds__(32) batch_kernel(BatchArgs b) {
     const int t = it - b.tile0[k];
     const int i0 = (t % d.ntx) * BTX, j0 = (t / d.ntx) * BTY;
     const long long n = (long long)d.lay.nx * d.lay.ny;
-    for (int e = lane; e < BTX * BTY; e += 32) {
+    for (int e = tid; e < BTX * BTY; e += BNT) {
       const int i = i0 + (e % BTX), j = j0 + (e / BTX);
       if (i >= d.lay.nx || j >= d.lay.ny) continue;
       const long long o = (long long)j * d.lay.nx + i, p = d.lay.idx(i, j);
@@ -134,7 +136,7 @@ __global__ void __launch_bounds__(32) batch_kernel(BatchArgs b) {
     }
   }
   if (blockIdx.x == 0)
-    for (int k = lane; k < 2 * b.count; k += 32) {
+    for (int k = tid; k < 2 * b.count; k += BNT) {
       b.red[2 * k] = 0ULL;
       b.red[2 * k + 1] = 0x7ff0000000000000ULL;
     }
@@ -149,7 +151,7 @@ __global__ void __launch_bounds__(32) batch_kernel(BatchArgs b) {
       const int t = it - b.tile0[k];
       const int i0 = (t % d.ntx) * BTX, j0 = (t / d.ntx) * BTY;
       double rate = 0.0, rmin = __longlong_as_double(0x7ff0000000000000LL);
-      for (int e = lane; e < BTX * BTY; e += 32) {
+      for (int e = tid; e < BTX * BTY; e += BNT) {
         const int i = i0 + (e % BTX), j = j0 + (e / BTX);
         if (i >= d.lay.nx || j >= d.lay.ny) continue;
         if (d.tag && d.tag[(long long)j * d.lay.nx + i] != 0) continue;
@@ -172,7 +174,7 @@ __global__ void __launch_bounds__(32) batch_kernel(BatchArgs b) {
     if (blockIdx.x == 0) {
       // the other parity was last read in the previous step: reset it for the next one
       unsigned long long* nxt = b.red + 2 * (long long)b.count * (par ^ 1);
-      for (int k = lane; k < b.count; k += 32) {
+      for (int k = tid; k < b.count; k += BNT) {
         nxt[2 * k] = 0ULL;
         nxt[2 * k + 1] = 0x7ff0000000000000ULL;
         if (b.t) b.t[k] += inst_dt(b.inst[k], red + 2 * k, b.cfl);
@@ -180,7 +182,7 @@ __global__ void __launch_bounds__(32) batch_kernel(BatchArgs b) {
     }
     for (int s = 0; s < 3; ++s) {
       // ---- immersed-boundary ghosts of the stage input
-      for (long long g = (long long)blockIdx.x * 32 + lane; g < nghost; g += (long long)gridDim.x * 32) {
+      for (long long g = (long long)blockIdx.x * BNT + tid; g < nghost; g += (long long)gridDim.x * BNT) {
         const int k = find_inst64(b.ghost0, b.count, g);
         const InstDesc& d = b.inst[k];
         double* X = (s == 0) ? d.N : ((s == 1) ? d.A : d.B);
@@ -188,7 +190,7 @@ __global__ void __launch_bounds__(32) batch_kernel(BatchArgs b) {
       }
       if (!grid_sync(b)) return;
       // ---- domain halos
-      for (long long h = (long long)blockIdx.x * 32 + lane; h < nhalo; h += (long long)gridDim.x * 32) {
+      for (long long h = (long long)blockIdx.x * BNT + tid; h < nhalo; h += (long long)gridDim.x * BNT) {
         const int k = find_inst64(b.halo0, b.count, h);
         const InstDesc& d = b.inst[k];
         double* X = (s == 0) ? d.N : ((s == 1) ? d.A : d.B);
@@ -207,7 +209,7 @@ __global__ void __launch_bounds__(32) batch_kernel(BatchArgs b) {
         a.Uout = (s == 0) ? d.A : ((s == 1) ? d.B : d.N);
         a.tag = d.tag;
         a.acc = d.acc;
-        a.acc2 = nullptr;
+        a.acc2 = d.acc2;
         a.err = b.err;
         a.lay = d.lay;
         a.gamma = d.gamma;
@@ -223,8 +225,8 @@ __global__ void __launch_bounds__(32) batch_kernel(BatchArgs b) {
         a.vy = d.vy;
         a.use_un = (s > 0) ? 1 : 0;
         a.has_av = d.has_av;
-        if (d.visc) stage_tile<BTX, BTY, BLX, BLY, true, false>(a, t % d.ntx, t / d.ntx, smem);
-        else stage_tile<BTX, BTY, BLX, BLY, false, false>(a, t % d.ntx, t / d.ntx, smem);
+        if (d.visc) stage_tile_c<BTX, BTY, BLX, BLY, true, false>(a, t % d.ntx, t / d.ntx, smem);
+        else stage_tile_c<BTX, BTY, BLX, BLY, false, false>(a, t % d.ntx, t / d.ntx, smem);
         __syncthreads();  // the next tile reuses shared memory
       }
       if (!grid_sync(b)) return;
@@ -237,7 +239,7 @@ __global__ void __launch_bounds__(32) batch_kernel(BatchArgs b) {
     const int t = it - b.tile0[k];
     const int i0 = (t % d.ntx) * BTX, j0 = (t / d.ntx) * BTY;
     const long long n = (long long)d.lay.nx * d.lay.ny;
-    for (int e = lane; e < BTX * BTY; e += 32) {
+    for (int e = tid; e < BTX * BTY; e += BNT) {
       const int i = i0 + (e % BTX), j = j0 + (e / BTX);
       if (i >= d.lay.nx || j >= d.lay.ny) continue;
       const long long o = (long long)j * d.lay.nx + i, p = d.lay.idx(i, j);
@@ -326,7 +328,7 @@ int js_batch_create(int count, const js_grid* grids, const js_params* params, co
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, js::batch_kernel, 32, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, js::batch_kernel, js::BNT, smem);
   if (!coop || per_sm < 1) { js_batch_destroy(b); return JS_ERR_CUDA; }
   b->blocks = sms * per_sm;
   if (cudaMalloc(&b->d_desc, sizeof(InstDesc) * count) != cudaSuccess ||
@@ -384,7 +386,7 @@ static int batch_launch(js_batch* b, double cfl, int n_steps, double* t_dev, int
   cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
   a.budget = (long long)(budget_s * 1e3 * (khz > 0 ? khz : 2000000));
   void* args[] = {&a};
-  const cudaError_t e = cudaLaunchCooperativeKernel((const void*)js::batch_kernel, dim3(b->blocks), dim3(32), args,
+  const cudaError_t e = cudaLaunchCooperativeKernel((const void*)js::batch_kernel, dim3(b->blocks), dim3(js::BNT), args,
                                                     batch_smem(), b->stream);
   return e == cudaSuccess ? JS_OK : JS_ERR_CUDA;
 }

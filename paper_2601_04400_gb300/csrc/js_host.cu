@@ -276,6 +276,7 @@ void js_internal_desc(js_ctx* c, js::InstDesc* d) {
   d->A = c->A;
   d->B = c->B;
   d->acc = c->acc;
+  d->acc2 = c->acc2;
   d->tag = c->tag;
   d->ib = ib_args(c);
   d->bc = c->bc;

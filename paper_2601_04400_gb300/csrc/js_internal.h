@@ -82,6 +82,7 @@ struct InstDesc {
   double* B;
   double* U;                 // user state [4][ny][nx]
   double* acc;               // stage scratch [4][ny][nx]
+  double* acc2;
   const unsigned char* tag;
   IbArgs ib;
   BcArgs bc;
