@@ -154,8 +154,20 @@ int js_batch_set_states(js_batch* b, double* const* U);
 
 /* Advance every instance by n_steps SSP-RK3 steps with its own CFL time step (cfl > 0) in
  * one launch.  t_dev: optional device double[count] to which each instance's elapsed time
- * is added.  Asynchronous; allocates nothing, so it can be captured into a CUDA graph. */
-int js_batch_step(js_batch* b, double cfl, int n_steps, double* t_dev);
+ * is added.  dt_log: optional device double[n_steps][count] receiving the step sizes used
+ * (the reverse pass needs them).  Asynchronous; allocates nothing, so it can be captured
+ * into a CUDA graph. */
+int js_batch_step(js_batch* b, double cfl, int n_steps, double* t_dev, double* dt_log);
+
+/* Reverse of one batched step (the gradient chain rule of Sec. 2 per instance): for every
+ * instance k, lam_n[k] = (dU_{n+1}/dU_n)^T lam_np1[k] for the step of size dt[k] taken from
+ * U_n[k], and p_bar[k] += (dU_{n+1}/dtheta_k)^T lam_np1[k] (JS_NPARAM doubles each; p_bar or
+ * an entry may be NULL).  dt: host array of `count` step sizes (e.g. a row of the dt log,
+ * which treats each CFL step size as fixed).  U_n, lam_np1, lam_n, p_bar: host arrays of
+ * device pointers.  Enqueued on the batch's stream; the first call allocates each instance's
+ * adjoint workspace. */
+int js_batch_step_vjp(js_batch* b, double* const* U_n, const double* dt, double* const* lam_np1,
+                      double* const* lam_n, double* const* p_bar);
 
 /* Read and clear the batch's device error flag (synchronises): JS_OK, JS_ERR_NONPHYSICAL,
  * JS_ERR_TIMEOUT. */
@@ -176,7 +188,7 @@ int js_batch_test_timeout(js_batch* b, double budget_s);
 void js_batch_destroy(js_batch* b);
 
 /* Stage-kernel tuning: tile shape variant (0 .. n_variants-1) used by this context's
- * js_rhs / js_step / js_step_vjp; 0 = 32x32-cell tiles with concurrent x/y sweeps.  Results are identical for every
+ * js_rhs / js_step / js_step_vjp; 0 = 32x32-cell tiles staged by TMA with concurrent x/y sweeps.  Results are identical for every
  * variant; only speed differs (the Python autotuner times them and caches the choice). */
 int js_set_tuning(js_ctx* ctx, int variant);
 int js_get_tuning(js_ctx* ctx, int* variant, int* n_variants);

@@ -69,7 +69,8 @@ SIGNATURES = {
     "js_batch_create": (_I, [_I, C.POINTER(JsGrid), C.POINTER(JsParams), C.POINTER(JsBoundary), C.POINTER(_P), _P,
                              C.POINTER(_P)]),
     "js_batch_set_states": (_I, [_P, C.POINTER(_P)]),
-    "js_batch_step": (_I, [_P, _D, _I, _P]),
+    "js_batch_step": (_I, [_P, _D, _I, _P, _P]),
+    "js_batch_step_vjp": (_I, [_P, C.POINTER(_P), C.POINTER(_D), C.POINTER(_P), C.POINTER(_P), C.POINTER(_P)]),
     "js_batch_sync_status": (_I, [_P]),
     "js_batch_info": (_I, [_P, C.POINTER(_I), C.POINTER(_I), C.POINTER(C.c_longlong)]),
     "js_batch_instance": (_P, [_P, _I]),
@@ -375,8 +376,16 @@ class Batch:
         self._states = list(states)
         _check(lib().js_batch_set_states(self.handle, ptrs), "js_batch_set_states")
 
-    def step(self, cfl, n_steps, t=None):
-        _check(lib().js_batch_step(self.handle, float(cfl), int(n_steps), _ptr(t)), "js_batch_step")
+    def step(self, cfl, n_steps, t=None, dt_log=None):
+        _check(lib().js_batch_step(self.handle, float(cfl), int(n_steps), _ptr(t), _ptr(dt_log)), "js_batch_step")
+
+    def step_vjp(self, U_n, dts, lam_np1, lam_n, p_bar=None):
+        """Reverse of one batched step; lists of per-instance tensors, dts: per-instance floats."""
+        n = self.count
+        arr = lambda ts: (C.c_void_p * n)(*[_ptr(t).value for t in ts])
+        dt = (C.c_double * n)(*[float(x) for x in dts])
+        pb = arr(p_bar) if p_bar is not None else None
+        _check(lib().js_batch_step_vjp(self.handle, arr(U_n), dt, arr(lam_np1), arr(lam_n), pb), "js_batch_step_vjp")
 
     def status(self):
         return lib().js_batch_sync_status(self.handle)

@@ -45,6 +45,7 @@ struct BatchArgs {
   unsigned* bar;              // [0] arrivals, [1] generation
   int* err;
   double* t;                  // accumulated time per instance or nullptr
+  double* dt_log;             // [n_steps][count] step sizes used, or nullptr
   double cfl;
   int n_steps;
   int extra_arrivals;         // > 0 only to exercise the barrier timeout
@@ -177,7 +178,9 @@ __global__ void __launch_bounds__(BNT) batch_kernel(BatchArgs b) {
       for (int k = tid; k < b.count; k += BNT) {
         nxt[2 * k] = 0ULL;
         nxt[2 * k + 1] = 0x7ff0000000000000ULL;
-        if (b.t) b.t[k] += inst_dt(b.inst[k], red + 2 * k, b.cfl);
+        const double dtk = inst_dt(b.inst[k], red + 2 * k, b.cfl);
+        if (b.t) b.t[k] += dtk;
+        if (b.dt_log) b.dt_log[(long long)step * b.count + k] = dtk;
       }
     }
     for (int s = 0; s < 3; ++s) {
@@ -367,7 +370,8 @@ int js_batch_set_states(js_batch* b, double* const* U) {
   return JS_OK;
 }
 
-static int batch_launch(js_batch* b, double cfl, int n_steps, double* t_dev, int extra, double budget_s) {
+static int batch_launch(js_batch* b, double cfl, int n_steps, double* t_dev, double* dt_log, int extra,
+                        double budget_s) {
   js::BatchArgs a;
   a.inst = b->d_desc;
   a.count = b->count;
@@ -378,6 +382,7 @@ static int batch_launch(js_batch* b, double cfl, int n_steps, double* t_dev, int
   a.bar = b->d_bar;
   a.err = b->d_err;
   a.t = t_dev;
+  a.dt_log = dt_log;
   a.cfl = cfl;
   a.n_steps = n_steps;
   a.extra_arrivals = extra;
@@ -391,14 +396,26 @@ static int batch_launch(js_batch* b, double cfl, int n_steps, double* t_dev, int
   return e == cudaSuccess ? JS_OK : JS_ERR_CUDA;
 }
 
-int js_batch_step(js_batch* b, double cfl, int n_steps, double* t_dev) {
+int js_batch_step(js_batch* b, double cfl, int n_steps, double* t_dev, double* dt_log) {
   if (!b || !b->states_set || !(cfl > 0.0) || n_steps < 0) return JS_ERR_ARG;
-  return batch_launch(b, cfl, n_steps, t_dev, 0, 2.0);
+  return batch_launch(b, cfl, n_steps, t_dev, dt_log, 0, 2.0);
+}
+
+int js_batch_step_vjp(js_batch* b, double* const* U_n, const double* dt, double* const* lam_np1,
+                      double* const* lam_n, double* const* p_bar) {
+  if (!b || !U_n || !dt || !lam_np1 || !lam_n) return JS_ERR_ARG;
+  for (int k = 0; k < b->count; ++k) {
+    js_ctx* c = b->ctx[k];
+    js_set_stream(c, b->stream);
+    const int rc = js_step_vjp(c, U_n[k], dt[k], lam_np1[k], lam_n[k], p_bar ? p_bar[k] : nullptr);
+    if (rc != JS_OK) return rc;
+  }
+  return JS_OK;
 }
 
 int js_batch_test_timeout(js_batch* b, double budget_s) {
   if (!b || !b->states_set || !(budget_s > 0.0) || budget_s > 2.0) return JS_ERR_ARG;
-  return batch_launch(b, 0.5, 0, nullptr, 1, budget_s);
+  return batch_launch(b, 0.5, 0, nullptr, nullptr, 1, budget_s);
 }
 
 int js_batch_sync_status(js_batch* b) {

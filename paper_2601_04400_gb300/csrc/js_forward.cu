@@ -128,6 +128,21 @@ stage2dc_kernel(StageArgs a, int ntx, int ntiles) {
   }
 }
 
+// the same with the tile staged by TMA (tensor map of the stage input as a grid constant)
+template <int TX, int TY, int LX, int LY, bool VISC, bool RHS>
+__global__ void __launch_bounds__(Stage2DC<TX, TY, LX, LY, VISC, true>::NT)
+stage2dc_tma_kernel(StageArgs a, int ntx, int ntiles, const __grid_constant__ TensorMap128 tmap) {
+  extern __shared__ __align__(128) double smem[];
+  __shared__ __align__(8) unsigned long long bar;
+  if (threadIdx.x == 0) mbar_init(&bar);
+  __syncthreads();
+  unsigned phase = 0;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    stage_tile_c<TX, TY, LX, LY, VISC, RHS, true>(a, t % ntx, t / ntx, smem, &tmap, &bar, &phase);
+    __syncthreads();
+  }
+}
+
 template <int TX, int LX, bool VISC, bool RHS>
 __global__ void __launch_bounds__(TX / LX) stage1d_kernel(StageArgs a) {
   constexpr int NPL = VISC ? 5 : 4;
@@ -206,15 +221,40 @@ cudaError_t launch_stage2dc(const StageArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <int TX, int TY, int LX, int LY, bool VISC, bool RHS>
+cudaError_t launch_stage2dc_tma(const StageArgs& a, const TensorMap128* tmap, cudaStream_t s) {
+  using S = Stage2DC<TX, TY, LX, LY, VISC, true>;
+  auto k = stage2dc_tma_kernel<TX, TY, LX, LY, VISC, RHS>;
+  static int resident = 0;
+  if (resident == 0) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, S::NT, S::SMEM);
+    if (e != cudaSuccess) return e;
+    resident = sms * (per_sm > 0 ? per_sm : 1);
+  }
+  const int ntx = (a.lay.nx + TX - 1) / TX, nty = (a.lay.ny + TY - 1) / TY;
+  const int ntiles = ntx * nty;
+  k<<<ntiles < resident ? ntiles : resident, S::NT, S::SMEM, s>>>(a, ntx, ntiles, *tmap);
+  return cudaGetLastError();
+}
+
 // tile shapes (TX x TY cells, x / y segment lengths LX / LY) the tuner chooses from:
-// 0-2 concurrent sweeps in persistent blocks, 3 sequential sweeps in one warp per tile
+// 0 concurrent sweeps with TMA staging, 1-3 concurrent sweeps with plain loads in
+// persistent blocks, 4 sequential sweeps in one warp per tile
 template <bool VISC, bool RHS>
-cudaError_t launch_stage2d_variant(const StageArgs& a, int variant, cudaStream_t s) {
+cudaError_t launch_stage2d_variant(const StageArgs& a, int variant, const TensorMap128* tmap, cudaStream_t s) {
   switch (variant) {
-    case 1: return launch_stage2dc<32, 16, 16, 16, VISC, RHS>(a, s);
-    case 2: return launch_stage2dc<64, 16, 16, 16, VISC, RHS>(a, s);
-    case 3: return launch_stage2d<32, 16, 16, 16, VISC, RHS>(a, s);
-    default: return launch_stage2dc<32, 32, 16, 16, VISC, RHS>(a, s);
+    case 1: return launch_stage2dc<32, 32, 16, 16, VISC, RHS>(a, s);
+    case 2: return launch_stage2dc<32, 16, 16, 16, VISC, RHS>(a, s);
+    case 3: return launch_stage2dc<64, 16, 16, 16, VISC, RHS>(a, s);
+    case 4: return launch_stage2d<32, 16, 16, 16, VISC, RHS>(a, s);
+    default:
+      if (tmap == nullptr) return launch_stage2dc<32, 32, 16, 16, VISC, RHS>(a, s);
+      return launch_stage2dc_tma<32, 32, 16, 16, VISC, RHS>(a, tmap, s);
   }
 }
 
@@ -226,14 +266,17 @@ cudaError_t launch_stage1d(const StageArgs& a, cudaStream_t s) {
 }
 }  // namespace
 
-cudaError_t launch_stage(const StageArgs& a, bool visc, bool rhs, int variant, cudaStream_t s) {
+cudaError_t launch_stage(const StageArgs& a, bool visc, bool rhs, int variant, const TensorMap128* tmap,
+                         cudaStream_t s) {
   if (a.lay.ny == 1) {
     if (visc) return rhs ? launch_stage1d<true, true>(a, s) : launch_stage1d<true, false>(a, s);
     return rhs ? launch_stage1d<false, true>(a, s) : launch_stage1d<false, false>(a, s);
   }
   if (visc)
-    return rhs ? launch_stage2d_variant<true, true>(a, variant, s) : launch_stage2d_variant<true, false>(a, variant, s);
-  return rhs ? launch_stage2d_variant<false, true>(a, variant, s) : launch_stage2d_variant<false, false>(a, variant, s);
+    return rhs ? launch_stage2d_variant<true, true>(a, variant, tmap, s)
+               : launch_stage2d_variant<true, false>(a, variant, tmap, s);
+  return rhs ? launch_stage2d_variant<false, true>(a, variant, tmap, s)
+             : launch_stage2d_variant<false, false>(a, variant, tmap, s);
 }
 
 cudaError_t launch_bc_fill(double* U, const Lay& lay, const BcArgs& bc, cudaStream_t s) {

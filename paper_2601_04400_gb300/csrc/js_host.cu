@@ -1,5 +1,6 @@
 // Host side of libjaxshock.so: solver contexts, immersed-boundary precomputation and the
 // C ABI declared in include/jaxshock.h.
+#include <cuda.h>  // tensor-map types only; the encoder is looked up at run time
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -59,6 +60,7 @@ struct js_ctx {
   double* inflow_prim = nullptr;  // 16
   double* qIb = nullptr;     // 4 per ghost
   int variant = 0;  // stage-kernel tile shape (js_set_tuning)
+  std::vector<std::pair<const double*, js::TensorMap128>> tmaps;  // TMA maps of stage inputs
   // tape: per slot the three filled stage states of one recorded step
   std::vector<double*> tape;
   // instrumentation
@@ -253,11 +255,53 @@ int fill_halos(js_ctx* c, double* X) {
   return JS_OK;
 }
 
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+// Tensor map of a padded state buffer: 3D (column, row, plane) FP64 tensor, box of the
+// 32x32 tile with its 3-cell halo and all 4 planes; reads past the array return zeros.
+const js::TensorMap128* stage_tmap(js_ctx* c, const double* buf) {
+  if (c->lay.ny == 1) return nullptr;
+  for (auto& e : c->tmaps)
+    if (e.first == buf) return &e.second;
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) return nullptr;
+  static_assert(sizeof(CUtensorMap) == sizeof(js::TensorMap128), "tensor map size");
+  js::TensorMap128 m;
+  const cuuint64_t dims[3] = {(cuuint64_t)c->lay.pitch, (cuuint64_t)c->lay.H, 4};
+  const cuuint64_t strides[2] = {(cuuint64_t)c->lay.pitch * sizeof(double), (cuuint64_t)c->lay.plane * sizeof(double)};
+  const cuuint32_t box[3] = {js::TMA_TX + 6, js::TMA_TY + 6, 4};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const CUresult r = enc(reinterpret_cast<CUtensorMap*>(&m), CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, (void*)buf, dims,
+                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return nullptr;
+  c->tmaps.push_back({buf, m});
+  return &c->tmaps.back().second;
+}
+
 // fused stage kernel, bracketed by events while profiling
 int stage(js_ctx* c, const StageArgs& a, bool visc, bool rhs) {
   const bool timed = c->profiling && c->ev_used + 2 <= (int)c->ev.size();
   if (timed) JS_CUDA(cudaEventRecord(c->ev[c->ev_used], c->stream));
-  JS_CUDA(js::launch_stage(a, visc, rhs, c->variant, c->stream));
+  const js::TensorMap128* tm = (c->variant == 0) ? stage_tmap(c, a.Uin) : nullptr;
+  JS_CUDA(js::launch_stage(a, visc, rhs, c->variant, tm, c->stream));
   if (timed) {
     JS_CUDA(cudaEventRecord(c->ev[c->ev_used + 1], c->stream));
     c->ev_used += 2;

@@ -92,8 +92,17 @@ struct InstDesc {
   int wall, visc, has_av, ntx, nty;
 };
 
-constexpr int STAGE_VARIANTS = 4;
-cudaError_t launch_stage(const StageArgs& a, bool visc, bool rhs, int variant, cudaStream_t s);
+// opaque 128-byte, 64-byte aligned tensor map (CUtensorMap) for TMA copies
+struct alignas(64) TensorMap128 {
+  unsigned long long opaque[16];
+};
+
+// box of the TMA-staged stage tile (32x32 cells + 3-cell halo, 4 planes)
+constexpr int TMA_TX = 32, TMA_TY = 32;
+
+constexpr int STAGE_VARIANTS = 5;
+cudaError_t launch_stage(const StageArgs& a, bool visc, bool rhs, int variant, const TensorMap128* tmap,
+                         cudaStream_t s);
 cudaError_t launch_bc_fill(double* U, const Lay& lay, const BcArgs& bc, cudaStream_t s);
 cudaError_t launch_ib_fill(double* U, const Lay& lay, const IbArgs& ib, double gamma, int wall, cudaStream_t s);
 cudaError_t launch_pack(const double* U, double* P, const Lay& lay, cudaStream_t s);

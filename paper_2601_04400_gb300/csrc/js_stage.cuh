@@ -230,10 +230,10 @@ __device__ __forceinline__ void stage_tile(const StageArgs& a, int bx, int by, d
 // barrier every thread combines cells of the tile.  Twice the warps per block at the same
 // shared memory: more warps hide the FP64 pipe's latency.
 // ---------------------------------------------------------------------------------------
-template <int TX, int TY, int LX, int LY, bool VISC>
+template <int TX, int TY, int LX, int LY, bool VISC, bool TMA = false>
 struct Stage2DC {
   static constexpr int NPL = VISC ? 5 : 4;
-  static constexpr int SP = TX + 7;
+  static constexpr int SP = TMA ? TX + 6 : TX + 7;  // TMA writes dense box rows
   static constexpr int PS = (TY + 6) * SP;
   static constexpr int NX_ITEMS = TY * (TX / LX);
   static constexpr int NY_ITEMS = TX * (TY / LY);
@@ -242,14 +242,94 @@ struct Stage2DC {
   static constexpr size_t SMEM = sizeof(double) * (size_t)NPL * PS;
 };
 
-template <int TX, int TY, int LX, int LY, bool VISC, bool RHS>
-__device__ __forceinline__ void stage_tile_c(const StageArgs& a, int bx, int by, double* smem) {
-  using S = Stage2DC<TX, TY, LX, LY, VISC>;
+// ---------------------------------------------------------------------------------------
+// TMA staging: one cp.async.bulk.tensor brings the conserved (TX+6) x (TY+6) x 4 box of the
+// padded state into shared memory ([plane][row][col], row pitch TX+6); an mbarrier tracks
+// completion.  Waits are bounded: on timeout the block records JS_ERR_TIMEOUT, drains its copy
+// (bounded again) and skips the tile.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// wait for the mbarrier phase `parity` to complete, for at most `budget` SM clock cycles
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, long long budget) {
+  const long long t0 = clock64();
+  while (true) {
+    unsigned ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > budget) return false;
+  }
+}
+__device__ __forceinline__ void tma_box3d(void* dst, const void* map, int x, int y, int z,
+                                          unsigned long long* bar, unsigned bytes) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Stage the tile with TMA and convert it to primitives in place (T in plane 4 when VISC).
+// Returns false when the copy did not complete in time (the tile must be skipped).
+template <int TX, int TY, int NPL, int NT>
+__device__ __forceinline__ bool load_tile_tma(const StageArgs& a, const void* tmap, double* sq, int ps, int ox,
+                                              int oy, const Gas& g, unsigned long long* bar, unsigned& phase) {
+  constexpr int CW = TX + 6, CH = TY + 6;
+  constexpr unsigned BYTES = 4u * CW * CH * sizeof(double);
+  static_assert(CW * CH * sizeof(double) % 16 == 0 && CW * sizeof(double) % 16 == 0, "TMA box rows");
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    // the box origin is the tile origin in padded coordinates: x = ox is a multiple of 32
+    tma_box3d(sq, tmap, ox, oy, 0, bar, BYTES);
+    constexpr long long kBudget = 2000000000LL;  // about one second of SM clock
+    bool ok = mbar_wait(bar, phase, kBudget);
+    if (!ok) {
+      atomicOr(a.err, ERR_TIMEOUT_BIT);
+      mbar_wait(bar, phase, kBudget);  // drain the copy in flight before the block moves on
+    }
+    s_ok = ok ? 1 : 0;
+  }
+  __syncthreads();
+  phase ^= 1u;
+  if (!s_ok) return false;
+  for (int e = threadIdx.x; e < CW * CH; e += NT) {
+    const double r = sq[e], mx = sq[ps + e], my = sq[2 * ps + e], E = sq[3 * ps + e];
+    double u, v, p, T;
+    cons_to_prim(r, mx, my, E, g, u, v, p, T);
+    sq[ps + e] = u;
+    sq[2 * ps + e] = v;
+    sq[3 * ps + e] = p;
+    if (NPL == 5) sq[4 * ps + e] = T;
+  }
+  return true;
+}
+
+template <int TX, int TY, int LX, int LY, bool VISC, bool RHS, bool TMA = false>
+__device__ __forceinline__ void stage_tile_c(const StageArgs& a, int bx, int by, double* smem,
+                                             const void* tmap = nullptr, unsigned long long* bar = nullptr,
+                                             unsigned* phase = nullptr) {
+  using S = Stage2DC<TX, TY, LX, LY, VISC, TMA>;
   double* sq = smem;
   const long long ncell = (long long)a.lay.nx * a.lay.ny;
   const Gas g{a.gamma, a.gm1, a.g1};
   const int tx0 = bx * TX, ty0 = by * TY;
-  load_tile<TX, TY, S::NPL, S::NT>(a, sq, S::PS, S::SP, tx0, ty0, g);
+  if (TMA) {
+    if (!load_tile_tma<TX, TY, S::NPL, S::NT>(a, tmap, sq, S::PS, tx0, ty0, g, bar, *phase)) return;
+  } else {
+    load_tile<TX, TY, S::NPL, S::NT>(a, sq, S::PS, S::SP, tx0, ty0, g);
+  }
   __syncthreads();
   if (threadIdx.x < S::NX_ITEMS) {
     const int it = threadIdx.x;

@@ -126,3 +126,32 @@ def test_barrier_timeout_is_reported_and_recoverable(env):
     ref, _ = _sequential(torch, B, probs, states, 0.5, 2)
     for k, U in enumerate(work):
         assert np.array_equal(to_host(U), ref[k])
+
+
+def test_batched_reverse_step_matches_oracle_tangent(env):
+    """One batched step with logged device dt, then js_batch_step_vjp: <lam, J v> from the
+    oracle's forward mode equals <J^T lam, v> for every instance."""
+    torch, B = env
+    probs = _cases(3, seed=11)
+    states = _states(torch, probs)
+    b = B.Batch(probs)
+    work = [U.clone() for U in states]
+    b.set_states(work)
+    log = torch.zeros((1, len(probs)), dtype=torch.float64, device="cuda")
+    b.step(0.5, 1, dt_log=log)
+    assert b.status() == 0
+    dts = to_host(log)[0].tolist()
+    rng = np.random.default_rng(5)
+    lams = [torch.tensor(rng.standard_normal(U.shape), device="cuda") for U in states]
+    outs = [torch.empty_like(U) for U in states]
+    pbs = [torch.zeros(20, dtype=torch.float64, device="cuda") for _ in states]
+    b.step_vjp(states, dts, lams, outs, pbs)
+    assert b.status() == 0
+    for p, U, lam, Ub, dt in zip(probs, states, lams, outs, dts):
+        U0 = to_host(U)
+        assert dt == O.max_dt(p, U0, 0.5)
+        v = rng.standard_normal(U0.shape) * np.abs(U0).max(axis=(1, 2), keepdims=True) * 1e-3
+        _, Jv = O.step_tangent(p, U0, v, np.zeros(20), [dt])
+        lhs = np.dot(to_host(lam).reshape(-1), Jv.reshape(-1))
+        rhs = np.dot(to_host(Ub).reshape(-1), v.reshape(-1))
+        assert abs(lhs - rhs) <= 1e-12 * np.abs(to_host(lam)).sum() * np.abs(Jv).max()
