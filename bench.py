@@ -270,24 +270,34 @@ def run_ours(args):
         solver.check()
         f_ms = sum(a.elapsed_time(b) for a, b in fa) / reps
         b_ms = sum(a.elapsed_time(b) for a, b in ba) / reps
-        # reverse of a step whose stage states were recorded (the checkpointed rollout's path)
-        solver.tape_reserve(1)
+        # reverse of a step whose stage states (and WENO internals) were recorded: the
+        # checkpointed rollout's path; its backward re-runs each step taped, then reverses it
+        solver.tape_reserve(1, weno=True)
         solver.step_taped(Uw, dt, 0)
+        tf = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
         ta = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
         barrier()
         for k in range(reps):
+            Ut = U.clone()
+            flush.zero_()
+            tf[k][0].record(stream)
+            solver.step_taped(Ut, dt, 0)
+            tf[k][1].record(stream)
             flush.zero_()
             ta[k][0].record(stream)
             solver.step_vjp_taped(0, dt, lam, lam_n=lam_out, p_bar=pbar)
             ta[k][1].record(stream)
         barrier()
         solver.check()
+        tf_ms = sum(a.elapsed_time(b) for a, b in tf) / reps
         t_ms = sum(a.elapsed_time(b) for a, b in ta) / reps
         adj = {"ms_per_step_forward": f_ms, "ms_per_step_vjp": b_ms, "ratio": b_ms / f_ms,
-               "ms_per_step_vjp_taped": t_ms, "ratio_taped": t_ms / f_ms,
+               "ms_per_step_taped_forward": tf_ms, "ms_per_step_vjp_taped": t_ms, "ratio_taped": t_ms / f_ms,
+               "ratio_rollout_backward": (tf_ms + t_ms) / f_ms,
                "note": "ratio: js_step_vjp (recomputes the stage states, then reverses the 3 stages) / "
-                       "js_step; ratio_taped: js_step_vjp_taped (stage states recorded by js_step_taped, "
-                       "as in the checkpointed rollout) / js_step"}
+                       "js_step; ratio_taped: js_step_vjp_taped (stage states and WENO5 internals recorded "
+                       "by js_step_taped) / js_step; ratio_rollout_backward: (js_step_taped + "
+                       "js_step_vjp_taped) / js_step, the backward cost per step of a checkpointed rollout"}
 
     if dist is not None:
         t = torch.tensor([step_ms, e2e_ms, stage_ms / max(stage_launches, 1)], dtype=torch.float64, device="cuda")

@@ -105,8 +105,9 @@ int js_rhs_vjp(js_ctx* ctx, const double* U, const double* lam, double* U_bar, d
 /* Vector-Jacobian product of ONE SSP-RK3 step of size dt taken from U_n:
  *   lam_n  = (dU_{n+1}/dU_n)^T lam_np1     (overwritten), device [4][ny][nx]
  *   p_bar += (dU_{n+1}/dtheta)^T lam_np1   (accumulated), device double[JS_NPARAM] or NULL
- * The three stage states are recomputed from U_n inside the call.  lam_n may alias
- * lam_np1.  Asynchronous. */
+ * The three stage states are recomputed from U_n inside the call (on 2D grids the first
+ * two forward stages also store their WENO5 internals for the reverse pass, which needs
+ * 2 x 56 extra padded planes of workspace).  lam_n may alias lam_np1.  Asynchronous. */
 int js_step_vjp(js_ctx* ctx, const double* U_n, double dt, const double* lam_np1, double* lam_n,
                 double* p_bar);
 
@@ -120,6 +121,15 @@ int js_step_vjp(js_ctx* ctx, const double* U_n, double dt, const double* lam_np1
  *   js_step_vjp_taped(ctx, slot, dt, lam_np1, lam_n, p_bar)  = js_step_vjp for the step
  *                            recorded in `slot` (same dt), without recomputing its stages. */
 int js_tape_reserve(js_ctx* ctx, int n_slots);
+
+/* js_tape_reserve with options.  JS_TAPE_WENO (2D grids; ignored for ny == 1): every slot
+ * also holds the WENO5 internals of its three stages (56 padded planes per stage, about
+ * 1.3 KB per cell and slot), written by js_step_taped; js_step_vjp_taped then skips the
+ * WENO forward recompute of its reverse pass.  Results are identical with and without.
+ * flags = 0 is js_tape_reserve; the choice applies to the js_step_taped calls that follow.
+ * Returns JS_ERR_NOMEM (nothing freed) when the device memory does not suffice. */
+#define JS_TAPE_WENO 1
+int js_tape_reserve_ex(js_ctx* ctx, int n_slots, int flags);
 int js_step_taped(js_ctx* ctx, double* U, double dt, int slot);
 int js_step_vjp_taped(js_ctx* ctx, int slot, double dt, const double* lam_np1, double* lam_n, double* p_bar);
 

@@ -5,7 +5,9 @@ Forward steps run js_step; the backward pass walks the steps in reverse.  Only e
 `checkpoint_every`-th state is kept (default ceil(sqrt(n))); during the backward pass each
 segment is re-run from its checkpoint with js_step_taped (which records the stage states of
 every step) and reversed with js_step_vjp_taped, so a rollout of n steps holds about
-sqrt(n) checkpoints plus 3 sqrt(n) stage states instead of n states.
+sqrt(n) checkpoints plus 3 sqrt(n) stage states instead of n states.  On 2D grids the tape
+also records the WENO5 internals of every stage (about 1.3 KB per cell and step) when they
+fit in half of the free device memory, which spares the reverse pass their recompute.
 
 theta is the 20-entry parameter vector of the library (gamma, mu, Pr, nu, then the inflow
 state rho, u, v, p of the x-low, x-high, y-low and y-high sides); its gradient is returned
@@ -36,7 +38,7 @@ def _apply_theta(solver, theta):
 
 class _Rollout(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, U0, theta, solver, dts, outputs, every):
+    def forward(ctx, U0, theta, solver, dts, outputs, every, internals):
         _apply_theta(solver, theta)
         n = len(dts)
         want = {k: i for i, k in enumerate(outputs)}
@@ -52,6 +54,7 @@ class _Rollout(torch.autograd.Function):
             if k + 1 in want:
                 outs[want[k + 1]] = U.clone()
         ctx.solver, ctx.dts, ctx.outputs, ctx.every = solver, list(dts), list(outputs), every
+        ctx.internals = internals
         ctx.ckpts = ckpts
         ctx.theta = theta.detach().clone()
         return torch.stack(outs)
@@ -69,7 +72,11 @@ class _Rollout(torch.autograd.Function):
             lam += inject[n]
         pbar = torch.zeros(B.JS_NPARAM, dtype=torch.float64, device=g.device)
         scratch = torch.empty_like(lam)
-        solver.tape_reserve(every)
+        weno = ctx.internals
+        if weno is None:
+            free = torch.cuda.mem_get_info(g.device)[0]
+            weno = solver.tape_weno_bytes(every) < 0.5 * free
+        solver.tape_reserve(every, weno=bool(weno))
         for seg in reversed(range(len(ctx.ckpts))):
             start = seg * every
             stop = min(start + every, n)
@@ -85,19 +92,21 @@ class _Rollout(torch.autograd.Function):
         st = solver.status()
         if st != 0:
             raise B.JsError(st, "rollout backward")
-        return lam, pbar.to(ctx.theta.device), None, None, None, None
+        return lam, pbar.to(ctx.theta.device), None, None, None, None, None
 
 
-def rollout(solver, U0, theta, dts, outputs=None, checkpoint_every=None):
+def rollout(solver, U0, theta, dts, outputs=None, checkpoint_every=None, tape_internals=None):
     """Differentiable rollout.
 
     solver: binding.Solver; U0: float64 CUDA tensor [4, ny, nx]; theta: float64 tensor [20]
     (see module docstring); dts: list of step sizes (one per step).  outputs: step indices
     whose states are returned stacked (default: only the final state, index len(dts)).
+    tape_internals: record the WENO5 internals on the tape (True / False; None decides by
+    free device memory).  The gradient is the same either way.
     Returns a tensor [len(outputs), 4, ny, nx] (or [4, ny, nx] for the default)."""
     n = len(dts)
     default = outputs is None
     outputs = [n] if default else list(outputs)
     every = checkpoint_every or max(1, int(math.ceil(math.sqrt(max(n, 1)))))
-    out = _Rollout.apply(U0, theta, solver, list(dts), outputs, every)
+    out = _Rollout.apply(U0, theta, solver, list(dts), outputs, every, tape_internals)
     return out[0] if default else out

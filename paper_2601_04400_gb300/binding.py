@@ -15,6 +15,7 @@ from . import build as _build
 
 JS_OK, JS_ERR_ARG, JS_ERR_CUDA, JS_ERR_NONPHYSICAL, JS_ERR_TIMEOUT, JS_ERR_IB, JS_ERR_NOMEM = 0, -1, -2, -3, -4, -5, -6
 JS_NPARAM = 20
+JS_TAPE_WENO = 1
 
 _lib = None
 
@@ -58,6 +59,7 @@ SIGNATURES = {
     "js_sync_status": (_I, [_P]),
     "js_ib_info": (_I, [_P, C.POINTER(_I), _P]),
     "js_tape_reserve": (_I, [_P, _I]),
+    "js_tape_reserve_ex": (_I, [_P, _I, _I]),
     "js_step_taped": (_I, [_P, _P, _D, _I]),
     "js_step_vjp_taped": (_I, [_P, _I, _D, _P, _P, _P]),
     "js_set_tuning": (_I, [_P, _I]),
@@ -305,8 +307,20 @@ class Solver:
         js_step_vjp(self.ctx, U_n, dt, lam_np1, lam_n, p_bar)
         return lam_n, p_bar
 
-    def tape_reserve(self, n_slots):
-        _check(lib().js_tape_reserve(self.ctx, int(n_slots)), "js_tape_reserve")
+    def tape_reserve(self, n_slots, weno=False):
+        """n_slots tape slots; weno=True also records the WENO5 internals of each stage
+        (2D grids), so that step_vjp_taped skips their recompute."""
+        _check(lib().js_tape_reserve_ex(self.ctx, int(n_slots), JS_TAPE_WENO if weno else 0),
+               "js_tape_reserve_ex")
+
+    def tape_weno_bytes(self, n_slots):
+        """Device bytes the WENO5 internals of n_slots tape slots take (0 on 1D grids)."""
+        nx, ny = self._spec["nx"], self._spec["ny"]
+        if ny == 1:
+            return 0
+        pitch = (nx + 6 + 3) // 4 * 4
+        plane = max((nx + 6) * ((ny + 6 + 3) // 4 * 4), (pitch * (ny + 6) + 31) // 32 * 32)
+        return int(n_slots) * 3 * 56 * 8 * ((plane + 31) // 32 * 32)
 
     def step_taped(self, U, dt, slot):
         _check(lib().js_step_taped(self.ctx, _ptr(U), float(dt), int(slot)), "js_step_taped")

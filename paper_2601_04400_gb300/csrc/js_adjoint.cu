@@ -6,9 +6,11 @@
 //   seed      lambda' = b dt Ubar_next on fluid cells (0 elsewhere); Ubar(X) gets the
 //             identity and carry terms; Ubar_0 += a Ubar_next on fluid cells
 //   prims     Q = prim(X) on every padded cell (same arithmetic as the forward kernel)
-//   pass 1    per line: WENO5 forward (internals saved to HBM), HLLC + viscous forward and
-//             reverse per face with Fbar = (lambda'_right - lambda'_left)/h; face-state
-//             adjoints saved, viscous and positivity-fallback adjoints added to Qbar
+//   pass 1    per line: WENO5 forward (internals saved to HBM; skipped when the forward
+//             stage kernel already stored them, then the face states are re-formed from the
+//             saved quotients), HLLC + viscous forward and reverse per face with
+//             Fbar = (lambda'_right - lambda'_left)/h; face-state adjoints saved, viscous and
+//             positivity-fallback adjoints added to Qbar
 //   pass 2    per line: WENO5 reverse from the saved internals; a 5-cell register window
 //             accumulates Qbar along the line
 //   primvjp   Ubar(X) += (dprim/dX)^T Qbar (+ nu * lap of lambda')
@@ -109,7 +111,7 @@ __global__ void adj_prims_kernel(AdjArgs a) {
 // =======================================================================================
 // DIR 0: lines are rows, faces f in [0, nx] (face f between cells f-1 and f).
 // DIR 1: lines are columns, faces f in [0, ny].
-template <int DIR, bool VISC, bool HAS_T>
+template <int DIR, bool VISC, bool HAS_T, bool SAVED>
 __device__ __forceinline__ void pass1_body(const AdjArgs& a, int seg_len, long long item) {
   const Lay& L = a.lay;
   const int nline = (DIR == 0) ? L.ny : L.nx;
@@ -131,7 +133,7 @@ __device__ __forceinline__ void pass1_body(const AdjArgs& a, int seg_len, long l
     // window at cell i = f0 - 1: q_{i-2..i+1}
     double q0[4], q1[4];
     Dl d[4];
-    {
+    if (!SAVED) {
       const long long b = cell_id(f0 - 1);
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
@@ -151,6 +153,16 @@ __device__ __forceinline__ void pass1_body(const AdjArgs& a, int seg_len, long l
       const long long ci = cell_id(i);
       const long long si = save_id<DIR>(a, i, line);
       double Lf[4], Rf[4];
+      if (SAVED) {
+        // face states of cell i from the quotients the forward stage stored
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const double qc = a.Q[c * L.plane + ci];
+          const double* sv = a.wsave + (long long)(wdir + c * WENO_SAVE) * a.splane + si;
+          Lf[c] = fma(sv[3 * a.splane], SIXTH, qc);
+          Rf[c] = fma(sv[5 * a.splane], SIXTH, qc);
+        }
+      } else {
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         // slide: d.m2 <- d.m1 ... and bring in q_{i+2}
@@ -165,6 +177,7 @@ __device__ __forceinline__ void pass1_body(const AdjArgs& a, int seg_len, long l
         for (int k = 0; k < WENO_SAVE; ++k) a.wsave[(long long)(wdir + c * WENO_SAVE + k) * a.splane + si] = sv[k];
         q0[c] = q1[c];
         q1[c] = q2;
+      }
       }
       if (i >= f0) {
         // face f = i between cells i-1 (state prevL) and i (state Rf)
@@ -264,12 +277,12 @@ __device__ __forceinline__ void pass1_body(const AdjArgs& a, int seg_len, long l
 }
 
 // x lines in blocks [0, bx), y lines (2D) in the blocks after them: one launch, both directions
-template <bool VISC, bool HAS_T>
+template <bool VISC, bool HAS_T, bool SAVED>
 __global__ void __launch_bounds__(64) adj_pass1_kernel(AdjArgs a, int seg_len, int bx) {
   if ((int)blockIdx.x < bx)
-    pass1_body<0, VISC, HAS_T>(a, seg_len, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+    pass1_body<0, VISC, HAS_T, SAVED>(a, seg_len, (long long)blockIdx.x * blockDim.x + threadIdx.x);
   else
-    pass1_body<1, VISC, HAS_T>(a, seg_len, (long long)(blockIdx.x - bx) * blockDim.x + threadIdx.x);
+    pass1_body<1, VISC, HAS_T, SAVED>(a, seg_len, (long long)(blockIdx.x - bx) * blockDim.x + threadIdx.x);
 }
 
 // =======================================================================================
@@ -570,11 +583,15 @@ long long line_items(const AdjArgs& a, int dir, int extra, int seg) {
 cudaError_t pass1(const AdjArgs& a, bool visc, bool two_d, cudaStream_t s) {
   const int bx = (int)blocks_for(line_items(a, 0, 1, kSeg1), kBlk);
   const int by = two_d ? (int)blocks_for(line_items(a, 1, 1, kSeg1), kBlk) : 0;
-  if (visc) {
-    if (two_d) adj_pass1_kernel<true, true><<<bx + by, kBlk, 0, s>>>(a, kSeg1, bx);
-    else adj_pass1_kernel<true, false><<<bx + by, kBlk, 0, s>>>(a, kSeg1, bx);
+  if (a.weno_saved) {
+    if (!two_d) return cudaErrorInvalidValue;  // the forward saves exist for 2D grids only
+    if (visc) adj_pass1_kernel<true, true, true><<<bx + by, kBlk, 0, s>>>(a, kSeg1, bx);
+    else adj_pass1_kernel<false, false, true><<<bx + by, kBlk, 0, s>>>(a, kSeg1, bx);
+  } else if (visc) {
+    if (two_d) adj_pass1_kernel<true, true, false><<<bx + by, kBlk, 0, s>>>(a, kSeg1, bx);
+    else adj_pass1_kernel<true, false, false><<<bx + by, kBlk, 0, s>>>(a, kSeg1, bx);
   } else {
-    adj_pass1_kernel<false, false><<<bx + by, kBlk, 0, s>>>(a, kSeg1, bx);
+    adj_pass1_kernel<false, false, false><<<bx + by, kBlk, 0, s>>>(a, kSeg1, bx);
   }
   return cudaGetLastError();
 }

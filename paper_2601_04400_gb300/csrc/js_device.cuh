@@ -116,9 +116,11 @@ struct Win {
   }
 
   // given q_{i+2}: face states at i+1/2 (Lf, left-biased; if NL) and i-1/2 (Rf,
-  // right-biased; if NR), then slide to cell i+1
-  template <bool NL = true, bool NR = true>
-  __device__ __forceinline__ void step(double q2, double& Lf, double& Rf) {
+  // right-biased; if NR), then slide to cell i+1.  With SV the internals the reverse pass
+  // needs go to sv[0..6] = s0, s1, s2, qL, rL, qR, rR (state = q_i + q/6, q = num r, r the
+  // reciprocal of den; zeros for a side not formed).
+  template <bool NL = true, bool NR = true, bool SV = false>
+  __device__ __forceinline__ void step(double q2, double& Lf, double& Rf, double* sv = nullptr) {
     const double dp2 = q2 - q1;
     const double D2 = dp2 - dp1;
     const double cD2 = K13 * D2;
@@ -139,7 +141,12 @@ struct Win {
       const double e2 = fma(4.0, dp1, -dp2);    // -4q_i + 5q_{i+1} - q_{i+2}
       const double num = fma(w0, e0, fma(w1_6, e1, w2_3 * e2));
       const double den = w0 + w1_6 + w2_3;
-      Lf = fma(quot(num, den), SIXTH, q0);
+      const double r = recip(den), q = num * r;  // = quot(num, den)
+      Lf = fma(q, SIXTH, q0);
+      if (SV) { sv[3] = q; sv[4] = r; }
+    } else if (SV) {
+      sv[3] = 0.0;
+      sv[4] = 0.0;
     }
     // right-biased (linear weights 0.3 : 0.6 : 0.1)
     const double f5p2 = 5.0 * dp2;
@@ -150,8 +157,14 @@ struct Win {
       const double e2 = fma(2.0, dp2, -f5p1);   // 5q_i - 7q_{i+1} + 2q_{i+2}
       const double num = fma(w0_3, e0, fma(w1_6, e1, w2 * e2));
       const double den = w0_3 + w1_6 + w2;
-      Rf = fma(quot(num, den), SIXTH, q0);
+      const double r = recip(den), q = num * r;  // = quot(num, den)
+      Rf = fma(q, SIXTH, q0);
+      if (SV) { sv[5] = q; sv[6] = r; }
+    } else if (SV) {
+      sv[5] = 0.0;
+      sv[6] = 0.0;
     }
+    if (SV) { sv[0] = s0; sv[1] = s1; sv[2] = s2; }
     // slide
     q0 = q1;
     q1 = q2;

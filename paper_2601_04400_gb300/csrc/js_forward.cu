@@ -117,20 +117,21 @@ stage2d_kernel(StageArgs a) {
   stage_tile<TX, TY, LX, LY, VISC, RHS>(a, blockIdx.x, blockIdx.y, smem);
 }
 
-// persistent concurrent-sweep stage kernel: blocks stride over the tiles
-template <int TX, int TY, int LX, int LY, bool VISC, bool RHS>
-__global__ void __launch_bounds__(Stage2DC<TX, TY, LX, LY, VISC>::NT)
+// persistent concurrent-sweep stage kernel: blocks stride over the tiles; with SAVE the
+// WENO5 internals of the stage go to a.wsave for the reverse pass
+template <int TX, int TY, int LX, int LY, bool VISC, bool RHS, bool SAVE>
+__global__ void __launch_bounds__(Stage2DC<TX, TY, LX, LY, VISC>::NT, SAVE ? 3 : 1)
 stage2dc_kernel(StageArgs a, int ntx, int ntiles) {
   extern __shared__ double smem[];
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    stage_tile_c<TX, TY, LX, LY, VISC, RHS>(a, t % ntx, t / ntx, smem);
+    stage_tile_c<TX, TY, LX, LY, VISC, RHS, false, SAVE>(a, t % ntx, t / ntx, smem);
     __syncthreads();
   }
 }
 
 // the same with the tile staged by TMA (tensor map of the stage input as a grid constant)
-template <int TX, int TY, int LX, int LY, bool VISC, bool RHS>
-__global__ void __launch_bounds__(Stage2DC<TX, TY, LX, LY, VISC, true>::NT)
+template <int TX, int TY, int LX, int LY, bool VISC, bool RHS, bool SAVE>
+__global__ void __launch_bounds__(Stage2DC<TX, TY, LX, LY, VISC, true>::NT, SAVE ? 3 : 1)
 stage2dc_tma_kernel(StageArgs a, int ntx, int ntiles, const __grid_constant__ TensorMap128 tmap) {
   extern __shared__ __align__(128) double smem[];
   __shared__ __align__(8) unsigned long long bar;
@@ -138,7 +139,7 @@ stage2dc_tma_kernel(StageArgs a, int ntx, int ntiles, const __grid_constant__ Te
   __syncthreads();
   unsigned phase = 0;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    stage_tile_c<TX, TY, LX, LY, VISC, RHS, true>(a, t % ntx, t / ntx, smem, &tmap, &bar, &phase);
+    stage_tile_c<TX, TY, LX, LY, VISC, RHS, true, SAVE>(a, t % ntx, t / ntx, smem, &tmap, &bar, &phase);
     __syncthreads();
   }
 }
@@ -200,10 +201,10 @@ cudaError_t launch_stage2d(const StageArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int TX, int TY, int LX, int LY, bool VISC, bool RHS>
+template <int TX, int TY, int LX, int LY, bool VISC, bool RHS, bool SAVE = false>
 cudaError_t launch_stage2dc(const StageArgs& a, cudaStream_t s) {
   using S = Stage2DC<TX, TY, LX, LY, VISC>;
-  auto k = stage2dc_kernel<TX, TY, LX, LY, VISC, RHS>;
+  auto k = stage2dc_kernel<TX, TY, LX, LY, VISC, RHS, SAVE>;
   static int resident = 0;  // blocks resident on the whole GPU
   if (resident == 0) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
@@ -221,10 +222,10 @@ cudaError_t launch_stage2dc(const StageArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int TX, int TY, int LX, int LY, bool VISC, bool RHS>
+template <int TX, int TY, int LX, int LY, bool VISC, bool RHS, bool SAVE = false>
 cudaError_t launch_stage2dc_tma(const StageArgs& a, const TensorMap128* tmap, cudaStream_t s) {
   using S = Stage2DC<TX, TY, LX, LY, VISC, true>;
-  auto k = stage2dc_tma_kernel<TX, TY, LX, LY, VISC, RHS>;
+  auto k = stage2dc_tma_kernel<TX, TY, LX, LY, VISC, RHS, SAVE>;
   static int resident = 0;
   if (resident == 0) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
@@ -265,6 +266,15 @@ cudaError_t launch_stage1d(const StageArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 }  // namespace
+
+cudaError_t launch_stage_save(const StageArgs& a, bool visc, const TensorMap128* tmap, cudaStream_t s) {
+  if (a.lay.ny == 1 || a.wsave == nullptr) return cudaErrorInvalidValue;
+  if (tmap != nullptr)
+    return visc ? launch_stage2dc_tma<32, 32, 16, 16, true, false, true>(a, tmap, s)
+                : launch_stage2dc_tma<32, 32, 16, 16, false, false, true>(a, tmap, s);
+  return visc ? launch_stage2dc<32, 32, 16, 16, true, false, true>(a, s)
+              : launch_stage2dc<32, 32, 16, 16, false, false, true>(a, s);
+}
 
 cudaError_t launch_stage(const StageArgs& a, bool visc, bool rhs, int variant, const TensorMap128* tmap,
                          cudaStream_t s) {

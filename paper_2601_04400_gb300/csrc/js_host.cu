@@ -55,14 +55,19 @@ struct js_ctx {
   double* P1 = nullptr;      // 4 planes (pong)
   double* Uacc = nullptr;    // 4 planes
   double* wsave = nullptr;   // 56 planes
+  double* wsave_fwd = nullptr;  // 2 x 56 planes: internals stored by the forward stages 1, 2
   double* fadj = nullptr;    // 16 planes
   double* inflow_acc = nullptr;   // 16
   double* inflow_prim = nullptr;  // 16
   double* qIb = nullptr;     // 4 per ghost
   int variant = 0;  // stage-kernel tile shape (js_set_tuning)
   std::vector<std::pair<const double*, js::TensorMap128>> tmaps;  // TMA maps of stage inputs
-  // tape: per slot the three filled stage states of one recorded step
+  // tape: per slot the three filled stage states of one recorded step and, when recording
+  // internals (2D), the WENO5 internals of its three stages
   std::vector<double*> tape;
+  std::vector<double*> tape_w;     // 3 per slot (56 planes each) or nullptr
+  std::vector<char> tape_w_ok;     // per slot: internals of the recorded step are present
+  bool tape_weno = false;
   // instrumentation
   bool profiling = false;
   std::vector<cudaEvent_t> ev;  // 2 per timed stage launch
@@ -364,9 +369,10 @@ void js_destroy(js_ctx* c) {
   cudaFree(c->err); cudaFree(c->red);
   cudaFree(c->ibt_cell); cudaFree(c->ibt_ptr); cudaFree(c->ibt_ghost); cudaFree(c->ibt_w);
   cudaFree(c->Q); cudaFree(c->Qb); cudaFree(c->lam); cudaFree(c->P0); cudaFree(c->P1); cudaFree(c->Uacc);
-  cudaFree(c->wsave); cudaFree(c->fadj); cudaFree(c->inflow_acc); cudaFree(c->inflow_prim); cudaFree(c->qIb);
+  cudaFree(c->wsave); cudaFree(c->wsave_fwd); cudaFree(c->fadj); cudaFree(c->inflow_acc); cudaFree(c->inflow_prim); cudaFree(c->qIb);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   for (double* t : c->tape) cudaFree(t);
+  for (double* t : c->tape_w) cudaFree(t);
   delete c;
 }
 
@@ -535,11 +541,38 @@ int adj_reserve(js_ctx* c) {
     return JS_ERR_NOMEM;
   JS_CUDA(cudaMemset(c->wsave, 0, 2 * 4 * 7 * spl));
   JS_CUDA(cudaMemset(c->fadj, 0, 16 * spl));
+  // internals stored by the forward stages 1, 2 of js_step_vjp (2D)
+  if (c->g.ny > 1) {
+    if (cudaMalloc(&c->wsave_fwd, 2 * 56 * spl) != cudaSuccess) {
+      c->wsave_fwd = nullptr;
+      return JS_ERR_NOMEM;
+    }
+    JS_CUDA(cudaMemset(c->wsave_fwd, 0, 2 * 56 * spl));
+  }
   if (cudaMalloc(&c->inflow_acc, 16 * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&c->inflow_prim, 16 * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&c->qIb, sizeof(double) * 4 * (size_t)(c->n_ghost > 0 ? c->n_ghost : 1)) != cudaSuccess)
     return JS_ERR_NOMEM;
   c->adj_ready = true;
+  return JS_OK;
+}
+
+size_t internals_bytes(const js_ctx* c) { return sizeof(double) * 56 * (size_t)saved_plane(c); }
+
+// stage update that also stores its WENO5 internals to `wsave` (2D), bracketed by events
+// while profiling like stage()
+int stage_save(js_ctx* c, StageArgs a, bool visc, double* wsave) {
+  a.wsave = wsave;
+  a.splane = saved_plane(c);
+  a.tpitch = transposed_pitch(c);
+  const bool timed = c->profiling && c->ev_used + 2 <= (int)c->ev.size();
+  if (timed) JS_CUDA(cudaEventRecord(c->ev[c->ev_used], c->stream));
+  JS_CUDA(js::launch_stage_save(a, visc, stage_tmap(c, a.Uin), c->stream));
+  if (timed) {
+    JS_CUDA(cudaEventRecord(c->ev[c->ev_used + 1], c->stream));
+    c->ev_used += 2;
+  }
+  ++c->launches;
   return JS_OK;
 }
 
@@ -588,9 +621,15 @@ js::IbTArgs ibt_args(const js_ctx* c) {
   return t;
 }
 
+// one stage VJP; `saved` = WENO internals of this stage stored by its forward (or nullptr:
+// pass 1 recomputes them into the context's own buffer)
 int adj_stage(js_ctx* c, const double* X, const double* Unext, double* Ub, double ra, double rb, double dt,
-              bool rhs_mode, double* p_bar) {
-  const js::AdjArgs a = adj_args(c, X, Ub, p_bar);
+              bool rhs_mode, double* p_bar, double* saved = nullptr) {
+  js::AdjArgs a = adj_args(c, X, Ub, p_bar);
+  if (saved) {
+    a.wsave = saved;
+    a.weno_saved = 1;
+  }
   JS_CUDA(js::launch_adj_stage(a, c->bc, ib_args(c), ibt_args(c), c->p.wall, Unext, c->Uacc, ra, rb, dt, rhs_mode,
                                c->inflow_acc, c->inflow_prim, c->qIb, c->stream, &c->launches));
   return JS_OK;
@@ -636,6 +675,11 @@ int js_step_vjp(js_ctx* c, const double* U_n, double dt, const double* lam_np1, 
   a.avx = dt * c->p.nu / (c->g.dx * c->g.dx);
   a.avy = dt * c->p.nu / (c->g.dy * c->g.dy);
   const bool visc = c->p.mu > 0.0;
+  // 2D: the forward stages 1 and 2 also store their WENO internals, so that their reverse
+  // skips the WENO recompute (stage 3 is not run forward; its pass 1 recomputes them)
+  const bool keep = c->g.ny > 1 && c->wsave_fwd != nullptr;
+  double* saved[3] = {keep ? c->wsave_fwd : nullptr,
+                      keep ? c->wsave_fwd + 56 * (size_t)saved_plane(c) : nullptr, nullptr};
   double* in[2] = {c->N, c->A};
   double* outp[2] = {c->A, c->B};
   const double ra[3] = {0.0, 0.75, 1.0 / 3.0};
@@ -648,7 +692,8 @@ int js_step_vjp(js_ctx* c, const double* U_n, double dt, const double* lam_np1, 
     a.rk_a = ra[s];
     a.rk_b = rb[s];
     a.use_un = (s > 0) ? 1 : 0;
-    if ((rc = stage(c, a, visc, false))) return rc;
+    rc = keep ? stage_save(c, a, visc, saved[s]) : stage(c, a, visc, false);
+    if (rc) return rc;
   }
   if ((rc = fill_halos(c, c->B))) return rc;
   // reverse through the stages: P0 -> P1 -> P0 -> P1
@@ -657,7 +702,7 @@ int js_step_vjp(js_ctx* c, const double* U_n, double dt, const double* lam_np1, 
   double* src = c->P0;
   double* dst = c->P1;
   for (int s = 2; s >= 0; --s) {
-    if ((rc = adj_stage(c, X[s], src, dst, ra[s], rb[s], dt, false, p_bar))) return rc;
+    if ((rc = adj_stage(c, X[s], src, dst, ra[s], rb[s], dt, false, p_bar, saved[s]))) return rc;
     double* t = src;
     src = dst;
     dst = t;
@@ -672,8 +717,8 @@ size_t state_bytes(const js_ctx* c) { return sizeof(double) * 4 * (size_t)c->lay
 double* tape_state(js_ctx* c, int slot, int s) { return c->tape[(size_t)slot * 3 + s]; }
 
 // one SSP-RK3 step whose three stage inputs live in X[0..2] (X[0] already holds U^n);
-// the step result goes to `out` (padded)
-int step_through(js_ctx* c, double* const X[3], double* out, double dt) {
+// the step result goes to `out` (padded); W[s] (if non-null) receives stage s's internals
+int step_through(js_ctx* c, double* const X[3], double* out, double dt, double* const W[3]) {
   StageArgs a = base_args(c);
   a.cx = dt / c->g.dx;
   a.cy = dt / c->g.dy;
@@ -691,14 +736,17 @@ int step_through(js_ctx* c, double* const X[3], double* out, double dt) {
     a.rk_a = ra[s];
     a.rk_b = rb[s];
     a.use_un = (s > 0) ? 1 : 0;
-    if ((rc = stage(c, a, visc, false))) return rc;
+    rc = W[s] ? stage_save(c, a, visc, W[s]) : stage(c, a, visc, false);
+    if (rc) return rc;
   }
   return JS_OK;
 }
 }  // namespace
 
-int js_tape_reserve(js_ctx* c, int n_slots) {
-  if (!c || n_slots < 0) return JS_ERR_ARG;
+int js_tape_reserve_ex(js_ctx* c, int n_slots, int flags) {
+  if (!c || n_slots < 0 || (flags & ~JS_TAPE_WENO) != 0) return JS_ERR_ARG;
+  int rc = adj_reserve(c);
+  if (rc) return rc;
   const size_t need = (size_t)n_slots * 3;
   while (c->tape.size() < need) {
     double* p = nullptr;
@@ -706,16 +754,36 @@ int js_tape_reserve(js_ctx* c, int n_slots) {
     if (cudaMemset(p, 0, state_bytes(c)) != cudaSuccess) { cudaFree(p); return JS_ERR_CUDA; }
     c->tape.push_back(p);
   }
-  int rc = adj_reserve(c);
-  return rc;
+  c->tape_weno = (flags & JS_TAPE_WENO) != 0 && c->g.ny > 1;
+  c->tape_w.resize(c->tape.size(), nullptr);
+  c->tape_w_ok.resize(c->tape.size() / 3, 0);
+  if (c->tape_weno) {
+    for (size_t k = 0; k < need; ++k) {
+      if (c->tape_w[k]) continue;
+      if (cudaMalloc(&c->tape_w[k], internals_bytes(c)) != cudaSuccess) {
+        c->tape_w[k] = nullptr;
+        c->tape_weno = false;
+        return JS_ERR_NOMEM;
+      }
+    }
+  }
+  return JS_OK;
 }
+
+int js_tape_reserve(js_ctx* c, int n_slots) { return js_tape_reserve_ex(c, n_slots, 0); }
 
 int js_step_taped(js_ctx* c, double* U, double dt, int slot) {
   if (!c || !U || !(dt > 0.0) || slot < 0 || (size_t)(slot + 1) * 3 > c->tape.size()) return JS_ERR_ARG;
   double* X[3] = {tape_state(c, slot, 0), tape_state(c, slot, 1), tape_state(c, slot, 2)};
+  const size_t b = (size_t)slot * 3;
+  const bool keep = c->tape_weno && c->tape_w[b] && c->tape_w[b + 1] && c->tape_w[b + 2];
+  double* W[3] = {keep ? c->tape_w[b] : nullptr, keep ? c->tape_w[b + 1] : nullptr,
+                  keep ? c->tape_w[b + 2] : nullptr};
+  c->tape_w_ok[slot] = 0;
   JS_CUDA(js::launch_pack(U, X[0], c->lay, c->stream));
-  int rc = step_through(c, X, c->N, dt);
+  int rc = step_through(c, X, c->N, dt, W);
   if (rc) return rc;
+  c->tape_w_ok[slot] = keep ? 1 : 0;
   JS_CUDA(js::launch_unpack(c->N, U, c->lay, c->stream));
   c->launches += 2;
   return JS_OK;
@@ -734,8 +802,10 @@ int js_step_vjp_taped(js_ctx* c, int slot, double dt, const double* lam_np1, dou
   const double rb[3] = {1.0, 0.25, 2.0 / 3.0};
   double* src = c->P0;
   double* dst = c->P1;
+  const bool saved = c->tape_w_ok[slot] != 0;
   for (int s = 2; s >= 0; --s) {
-    if ((rc = adj_stage(c, tape_state(c, slot, s), src, dst, ra[s], rb[s], dt, false, p_bar))) return rc;
+    double* w = saved ? c->tape_w[(size_t)slot * 3 + s] : nullptr;
+    if ((rc = adj_stage(c, tape_state(c, slot, s), src, dst, ra[s], rb[s], dt, false, p_bar, w))) return rc;
     double* t = src;
     src = dst;
     dst = t;

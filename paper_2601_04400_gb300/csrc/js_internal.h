@@ -21,6 +21,11 @@ struct StageArgs {
   double avx, avy;           // (dt) nu / dx^2, (dt) nu / dy^2
   ViscC vx, vy;              // viscous constants of x and y faces
   int use_un, has_av;
+  // WENO5 internals for the reverse pass (kernels instantiated with SAVE): 56 planes of
+  // `splane` doubles, x lines transposed (row pitch tpitch), y lines in the padded layout
+  double* wsave;
+  long long splane;
+  int tpitch;
 };
 
 struct BcArgs {
@@ -66,6 +71,7 @@ struct AdjArgs {
   ViscC vx, vy;
   double inv_mu, kg, kp;     // 1/mu, -1/(gamma (gamma-1)), -1/Pr
   int visc, has_av, two_d;
+  int weno_saved;            // wsave already holds the stage's WENO internals (forward SAVE)
 };
 
 cudaError_t launch_adj_stage(const AdjArgs& a, const BcArgs& bc, const IbArgs& ib, const IbTArgs& ibt, int wall,
@@ -103,6 +109,9 @@ constexpr int TMA_TX = 32, TMA_TY = 32;
 constexpr int STAGE_VARIANTS = 5;
 cudaError_t launch_stage(const StageArgs& a, bool visc, bool rhs, int variant, const TensorMap128* tmap,
                          cudaStream_t s);
+// stage update (not RHS mode) that also stores the WENO5 internals to a.wsave (2D only;
+// 32x32 concurrent tile, TMA-staged when tmap is given)
+cudaError_t launch_stage_save(const StageArgs& a, bool visc, const TensorMap128* tmap, cudaStream_t s);
 cudaError_t launch_bc_fill(double* U, const Lay& lay, const BcArgs& bc, cudaStream_t s);
 cudaError_t launch_ib_fill(double* U, const Lay& lay, const IbArgs& ib, double gamma, int wall, cudaStream_t s);
 cudaError_t launch_pack(const double* U, double* P, const Lay& lay, cudaStream_t s);

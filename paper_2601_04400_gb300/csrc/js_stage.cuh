@@ -5,6 +5,8 @@
 // the SSP-RK3 stage combination.  Used by the per-grid stage kernel and by the persistent
 // batched kernel.
 #pragma once
+#include <type_traits>
+
 #include "js_device.cuh"
 #include "js_internal.h"
 
@@ -16,9 +18,16 @@ namespace js {
 // sq: shared planes rho, u, v, p (and T when VISC), plane stride ps; `base` = index of the
 // first output cell of the segment, `st` = stride along the line, `ts` = stride across it.
 // emit(k, dF) receives F_{k+1/2} - F_{k-1/2} (conserved order) for output cells k = 0..L-1.
-template <int DIR, bool VISC, bool HAS_T, int L, class Emit>
+// keep(k, c, sv), when given, receives the WENO5 internals of variable c at cell k for
+// k = -1 (left-biased side only), 0..L-1 (both sides) and L (right-biased side only).
+struct NoKeep {
+  __device__ __forceinline__ void operator()(int, int, const double*) const {}
+};
+
+template <int DIR, bool VISC, bool HAS_T, int L, class Emit, class Keep = NoKeep>
 __device__ __forceinline__ void sweep_line(const double* __restrict__ sq, int ps, int base, int st, int ts,
-                                           const Gas& g, const ViscC& vc, Emit&& emit) {
+                                           const Gas& g, const ViscC& vc, Emit&& emit, Keep keep = Keep{}) {
+  constexpr bool SV = !std::is_same<Keep, NoKeep>::value;
   constexpr int PN = (DIR == 0) ? 1 : 2;  // plane of the face-normal velocity
   constexpr int PT = (DIR == 0) ? 2 : 1;  // plane of the tangential velocity
   Win w[4];
@@ -32,7 +41,11 @@ __device__ __forceinline__ void sweep_line(const double* __restrict__ sq, int ps
     // cell -1 of the segment: only its right-face (left-biased) state is needed
     double Rf[4];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) w[c].template step<true, false>(sq[c * ps + base - st + 2 * st], prevL[c], Rf[c]);
+    for (int c = 0; c < 4; ++c) {
+      double sv[SV ? 7 : 1];
+      w[c].template step<true, false, SV>(sq[c * ps + base - st + 2 * st], prevL[c], Rf[c], sv);
+      if (SV) keep(-1, c, sv);
+    }
   }
 #pragma unroll 1
   for (int k = 0; k <= L; ++k) {
@@ -40,12 +53,18 @@ __device__ __forceinline__ void sweep_line(const double* __restrict__ sq, int ps
     double Lf[4], Rf[4];
     if (k < L) {
 #pragma unroll
-      for (int c = 0; c < 4; ++c) w[c].step(sq[c * ps + cell + 2 * st], Lf[c], Rf[c]);
+      for (int c = 0; c < 4; ++c) {
+        double sv[SV ? 7 : 1];
+        w[c].template step<true, true, SV>(sq[c * ps + cell + 2 * st], Lf[c], Rf[c], sv);
+        if (SV) keep(k, c, sv);
+      }
     } else {
       // cell L (first cell of the next segment): only its left-face state is needed
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        w[c].template step<false, true>(sq[c * ps + cell + 2 * st], Lf[c], Rf[c]);
+        double sv[SV ? 7 : 1];
+        w[c].template step<false, true, SV>(sq[c * ps + cell + 2 * st], Lf[c], Rf[c], sv);
+        if (SV) keep(L, c, sv);
         Lf[c] = 0.0;  // unused
       }
     }
@@ -316,7 +335,25 @@ __device__ __forceinline__ bool load_tile_tma(const StageArgs& a, const void* tm
   return true;
 }
 
-template <int TX, int TY, int LX, int LY, bool VISC, bool RHS, bool TMA = false>
+// Store the WENO5 internals of variable c at cell `k` of line `line` (DIR 0: row, stored
+// transposed; DIR 1: column, padded layout), for the cells -1 .. n the reverse pass reads
+// (n = cells along the line).  `part` is -1 / 0 / +1 for a cell whose left-biased side only /
+// both sides / right-biased side only were formed.  Cell n keeps only its right-biased side,
+// so that every writer of a cell stores the same values.
+template <int DIR>
+__device__ __forceinline__ void keep_internals(const StageArgs& a, int k, int line, int c, const double* sv,
+                                               int part) {
+  const int n = (DIR == 0) ? a.lay.nx : a.lay.ny;
+  const bool store = (part < 0) ? (k == -1) : (part > 0) ? (k == n) : (k >= 0 && k <= n);
+  if (!store) return;
+  const long long si = (DIR == 0) ? (long long)(k + 3) * a.tpitch + (line + a.lay.gy) : a.lay.idx(line, k);
+  double* dst = a.wsave + (long long)(DIR * 28 + c * 7) * a.splane + si;
+  const bool left = k < n;
+#pragma unroll
+  for (int m = 0; m < 7; ++m) dst[m * a.splane] = (m == 3 || m == 4) && !left ? 0.0 : sv[m];
+}
+
+template <int TX, int TY, int LX, int LY, bool VISC, bool RHS, bool TMA = false, bool SAVE = false>
 __device__ __forceinline__ void stage_tile_c(const StageArgs& a, int bx, int by, double* smem,
                                              const void* tmap = nullptr, unsigned long long* bar = nullptr,
                                              unsigned* phase = nullptr) {
@@ -335,28 +372,42 @@ __device__ __forceinline__ void stage_tile_c(const StageArgs& a, int bx, int by,
     const int it = threadIdx.x;
     const int ty = it % TY, xs = (it / TY) * LX;
     const int gj = ty0 + ty;
-    sweep_line<0, VISC, true, LX>(sq, S::PS, (ty + 3) * S::SP + xs + 3, 1, S::SP, g, a.vx,
-                                  [&](int k, const double dF[4]) {
+    auto emit = [&](int k, const double dF[4]) {
       const int gi = tx0 + xs + k;
       if (gi < a.lay.nx && gj < a.lay.ny) {
         const long long o = (long long)gj * a.lay.nx + gi;
 #pragma unroll
         for (int c = 0; c < 4; ++c) a.acc[c * ncell + o] = __dmul_rn(a.cx, dF[c]);
       }
-    });
+    };
+    if constexpr (SAVE) {
+      sweep_line<0, VISC, true, LX>(sq, S::PS, (ty + 3) * S::SP + xs + 3, 1, S::SP, g, a.vx, emit,
+                                    [&](int k, int c, const double* sv) {
+        if (gj < a.lay.ny) keep_internals<0>(a, tx0 + xs + k, gj, c, sv, k < 0 ? -1 : (k == LX ? 1 : 0));
+      });
+    } else {
+      sweep_line<0, VISC, true, LX>(sq, S::PS, (ty + 3) * S::SP + xs + 3, 1, S::SP, g, a.vx, emit);
+    }
   } else {
     const int it = threadIdx.x - S::NX_ITEMS;
     const int tx = it % TX, ys = (it / TX) * LY;
     const int gi = tx0 + tx;
-    sweep_line<1, VISC, true, LY>(sq, S::PS, (ys + 3) * S::SP + tx + 3, S::SP, 1, g, a.vy,
-                                  [&](int k, const double dG[4]) {
+    auto emit = [&](int k, const double dG[4]) {
       const int gj = ty0 + ys + k;
       if (gi < a.lay.nx && gj < a.lay.ny) {
         const long long o = (long long)gj * a.lay.nx + gi;
 #pragma unroll
         for (int c = 0; c < 4; ++c) a.acc2[c * ncell + o] = __dmul_rn(a.cy, dG[c]);
       }
-    });
+    };
+    if constexpr (SAVE) {
+      sweep_line<1, VISC, true, LY>(sq, S::PS, (ys + 3) * S::SP + tx + 3, S::SP, 1, g, a.vy, emit,
+                                    [&](int k, int c, const double* sv) {
+        if (gi < a.lay.nx) keep_internals<1>(a, ty0 + ys + k, gi, c, sv, k < 0 ? -1 : (k == LY ? 1 : 0));
+      });
+    } else {
+      sweep_line<1, VISC, true, LY>(sq, S::PS, (ys + 3) * S::SP + tx + 3, S::SP, 1, g, a.vy, emit);
+    }
   }
   __syncthreads();
   for (int e = threadIdx.x; e < TX * TY; e += S::NT) {

@@ -161,3 +161,38 @@ def test_taped_step_and_vjp_equal_the_recomputing_ones(B):
     assert s.status() == 0
     assert np.abs(to_host(lt) - to_host(lr)).max() <= 1e-12 * np.abs(to_host(lr)).max()
     assert np.abs(to_host(pt) - to_host(pr)).max() <= 1e-12 * np.abs(to_host(pr)).max()
+
+
+@pytest.mark.parametrize("shape", [(48, 32), (32, 48), (37, 21)])
+@pytest.mark.parametrize("viscous", [False, True])
+def test_reverse_with_forward_stored_weno_internals(B, shape, viscous):
+    """The WENO5 internals stored by the forward stage (js_step_vjp's stages 1-2, a tape with
+    JS_TAPE_WENO) give the same reverse step as recomputing them in pass 1 (a tape without
+    internals).  48 and 32 cells put a segment end on the last cell of a line; 48 also has
+    two writers of that cell; 37 x 21 is ragged."""
+    nx, ny = shape
+    if viscous:
+        prob = W.shock_cylinder(nx=nx, ny=ny, Lx=nx / 16.0, Ly=ny / 16.0, centre=(nx / 32.0, ny / 32.0),
+                                radius=min(nx, ny) / 64.0, x_shock=nx / 64.0, Re=200.0)
+    else:
+        prob = W.random_periodic(nx, ny, seed=21)
+    U = O.prim_to_cons(prob, W.random_state(prob, seed=5, amp=0.02))
+    dt = 0.4 * O.max_dt(prob, U, 0.5)
+    lam = W.uniform_normal(U.shape, seed=17)
+    s = B.Solver.from_problem(prob)
+    s.tape_reserve(2, weno=False)
+    Ua = to_dev(U)
+    s.step_taped(Ua, dt, 0)
+    l0, p0 = s.step_vjp_taped(0, dt, to_dev(lam))     # pass 1 recomputes every stage
+    s.tape_reserve(2, weno=True)
+    Ub = to_dev(U)
+    s.step_taped(Ub, dt, 1)
+    assert np.array_equal(to_host(Ua), to_host(Ub))
+    l1, p1 = s.step_vjp_taped(1, dt, to_dev(lam))     # all three stages from the tape
+    l2, p2 = s.step_vjp(to_dev(U), dt, to_dev(lam))   # stages 1-2 stored, stage 3 recomputed
+    assert s.status() == 0
+    ref, pref = to_host(l0), to_host(p0)
+    for l, p in ((l1, p1), (l2, p2)):
+        # summation order of the atomics is the only difference
+        assert np.abs(to_host(l) - ref).max() <= 1e-12 * np.abs(ref).max()
+        assert np.abs(to_host(p) - pref).max() <= 1e-12 * max(np.abs(pref).max(), 1e-300)

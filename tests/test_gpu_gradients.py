@@ -98,10 +98,12 @@ def test_checkpointing_does_not_change_the_gradient(env):
     U0 = torch.tensor(_cons(p.W0, p.gamma), device="cuda")
     dt = 0.5 * s.max_dt(U0, 0.5)
     grads = []
-    for every in (1, 3, 12):
+    # segment lengths 1, 3, 12, each with and without the WENO internals on the tape
+    for every, internals in ((1, False), (3, True), (3, False), (12, True)):
         U = U0.clone().requires_grad_(True)
         th = A.theta_of(s).requires_grad_(True)
-        out = A.rollout(s, U, th, [dt] * 12, outputs=[4, 12], checkpoint_every=every)
+        out = A.rollout(s, U, th, [dt] * 12, outputs=[4, 12], checkpoint_every=every,
+                        tape_internals=internals)
         (out[0, 0].square().sum() + out[1, 3].sum()).backward()
         grads.append((U.grad.cpu().numpy(), th.grad.numpy()))
     for gU, gp in grads[1:]:
