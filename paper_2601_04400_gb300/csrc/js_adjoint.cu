@@ -306,38 +306,25 @@ __device__ __forceinline__ void pass2_body(const AdjArgs& a, int seg_len, long l
     // one variable at a time keeps the register window small
     const double* q = a.Q + c * L.plane;
     double* qb = a.Qb + c * L.plane;
-    double win[5] = {0.0, 0.0, 0.0, 0.0, 0.0};  // adjoints of cells i-2 .. i+2
     long long ci = cell_id(c0);
     const long long sst = (DIR == 0) ? a.tpitch : L.pitch;  // stride along the line in saved arrays
     long long si = save_id<DIR>(a, c0, line);
-    double qm2 = q[ci - 2 * st], qm1 = q[ci - st], qc = q[ci], qp1 = q[ci + st];
+    WenoRev w;
+    w.init(q[ci - 2 * st], q[ci - st], q[ci], q[ci + st]);
 #pragma unroll 1
     for (int i = c0; i < c1; ++i, ci += st, si += sst) {
-      const double qp2 = q[ci + 2 * st];
-      Dl d{qm1 - qm2, qc - qm1, qp1 - qc, qp2 - qp1};
       double sv[WENO_SAVE];
 #pragma unroll
       for (int k = 0; k < WENO_SAVE; ++k) sv[k] = a.wsave[(long long)(wdir + c * WENO_SAVE + k) * a.splane + si];
       const double Lb = a.fadj[(long long)(fdir + c) * a.splane + si + sst];  // left state of face i+1/2
       const double Rb = a.fadj[(long long)(fdir + 4 + c) * a.splane + si];    // right state of face i-1/2
-      double g[5];
-      weno_cell_vjp(d, sv, Lb, Rb, g);
-#pragma unroll
-      for (int k = 0; k < 5; ++k) win[k] += g[k];
       // cell i-2 is complete
-      atomicAdd(qb + ci - 2 * st, win[0]);
-      win[0] = win[1];
-      win[1] = win[2];
-      win[2] = win[3];
-      win[3] = win[4];
-      win[4] = 0.0;
-      qm2 = qm1;
-      qm1 = qc;
-      qc = qp1;
-      qp1 = qp2;
+      atomicAdd(qb + ci - 2 * st, w.step(q[ci + 2 * st], sv, Lb, Rb));
     }
     // flush cells c1-2 .. c1+1
-    for (int k = 0; k < 4; ++k) atomicAdd(qb + ci + (k - 2) * st, win[k]);
+    double rest[4];
+    w.flush(rest);
+    for (int k = 0; k < 4; ++k) atomicAdd(qb + ci + (k - 2) * st, rest[k]);
   }
 }
 

@@ -48,59 +48,102 @@ __device__ __forceinline__ void weno_cell_fwd(double q0, const Dl& d, double& Lf
   sv[3] = qL; sv[4] = rL; sv[5] = qR; sv[6] = rR;
 }
 
-// Reverse of weno_cell_fwd: given the adjoints Lb (state at i+1/2) and Rb (state at i-1/2),
-// returns the adjoints of q_{i-2..i+2} in g[0..4] (overwritten).
-__device__ __forceinline__ void weno_cell_vjp(const Dl& d, const double sv[WENO_SAVE], double Lb, double Rb,
-                                              double g[5]) {
-  const double D0 = d.m1 - d.m2, D1 = d.p1 - d.m1, D2 = d.p2 - d.p1;
-  const double t0 = fma(2.0, d.m1, D0), t1 = d.m1 + d.p1, t2 = fma(-2.0, d.p1, D2);
-  const double s0 = sv[0], s1 = sv[1], s2 = sv[2];
-  const double p01 = s0 * s1, p02 = s0 * s2, p12 = s1 * s2;
-  const double w0 = p12 * p12, w1 = p02 * p02, w2 = p01 * p01;
-  const double w1_6 = 6.0 * w1, w2_3 = 3.0 * w2, w0_3 = 3.0 * w0;
-  const double e0L = fma(-2.0, d.m2, 5.0 * d.m1), e1L = fma(2.0, d.p1, d.m1), e2L = fma(4.0, d.p1, -d.p2);
-  const double e0R = fma(-4.0, d.m1, d.m2), e1R = fma(-2.0, d.m1, -d.p1), e2R = fma(2.0, d.p2, -5.0 * d.p1);
-  // state = q_i + q/6, q = num/den
-  const double nL = (SIXTH * Lb) * sv[4], dL = -nL * sv[3];
-  const double nR = (SIXTH * Rb) * sv[6], dR = -nR * sv[5];
-  // left-biased: num = w0 e0 + 6w1 e1 + 3w2 e2, den = w0 + 6w1 + 3w2
-  // right-biased: num = 3w0 e0 + 6w1 e1 + w2 e2, den = 3w0 + 6w1 + w2
-  const double bw0 = fma(nL, e0L, dL) + 3.0 * fma(nR, e0R, dR);
-  const double bw1 = 6.0 * (fma(nL, e1L, dL) + fma(nR, e1R, dR));
-  const double bw2 = fma(3.0, fma(nL, e2L, dL), fma(nR, e2R, dR));
-  const double be0L = nL * w0, be1L = nL * w1_6, be2L = nL * w2_3;
-  const double be0R = nR * w0_3, be1R = nR * w1_6, be2R = nR * w2;
-  // w0 = p12^2, w1 = p02^2, w2 = p01^2
-  const double bp12 = 2.0 * p12 * bw0, bp02 = 2.0 * p02 * bw1, bp01 = 2.0 * p01 * bw2;
-  const double bs0 = fma(bp01, s1, bp02 * s2);
-  const double bs1 = fma(bp01, s0, bp12 * s2);
-  const double bs2 = fma(bp02, s0, bp12 * s1);
-  // s_k = 13/3 D_k^2 + t_k^2 + 4 eps
-  double bD0 = (2.0 * K13) * D0 * bs0, bD1 = (2.0 * K13) * D1 * bs1, bD2 = (2.0 * K13) * D2 * bs2;
-  const double bt0 = 2.0 * t0 * bs0, bt1 = 2.0 * t1 * bs1, bt2 = 2.0 * t2 * bs2;
-  double bm2 = 0.0, bm1 = 0.0, bp1 = 0.0, bp2 = 0.0;
-  // t0 = D0 + 2 d_m1, t1 = d_m1 + d_p1, t2 = D2 - 2 d_p1
-  bD0 += bt0;
-  bm1 += 2.0 * bt0 + bt1;
-  bp1 += bt1 - 2.0 * bt2;
-  bD2 += bt2;
-  // candidate corrections
-  bm2 += -2.0 * be0L + be0R;
-  bm1 += 5.0 * be0L + be1L - 4.0 * be0R - 2.0 * be1R;
-  bp1 += 2.0 * be1L + 4.0 * be2L - be1R - 5.0 * be2R;
-  bp2 += -be2L + 2.0 * be2R;
-  // D0 = d_m1 - d_m2, D1 = d_p1 - d_m1, D2 = d_p2 - d_p1
-  bm1 += bD0 - bD1;
-  bm2 -= bD0;
-  bp1 += bD1 - bD2;
-  bp2 += bD2;
-  // d's of q_{i-2..i+2}; the centre value also enters both states directly
-  g[0] = -bm2;
-  g[1] = bm2 - bm1;
-  g[2] = (bm1 - bp1) + (Lb + Rb);
-  g[3] = bp1 - bp2;
-  g[4] = bp2;
-}
+// Reverse of the cell-centred WENO5 along one line, for one variable.  Like the forward
+// window it slides over the first differences d (d_{i+3/2} = q_{i+2} - q_{i+1} is the only
+// new one per cell); it also slides over the adjoints of the differences, so that each cell
+// emits the complete adjoint of q_{i-2} (d_{i-5/2} adds, d_{i-3/2} subtracts, plus the
+// direct term Lb + Rb of the face states q_{i-2} + q/6).
+//
+// Algebra per cell, with n = Lb rL / 6 and Rb rR / 6 the adjoints of the two quotients
+// num/den (scaled by 4 below, which the fma constants undo):
+//   dq/dw_k = c_k (e_k - q) / den        (c = 1, 6, 3 left-biased; 3, 6, 1 right-biased)
+//   w0 = (s1 s2)^2, w1 = (s0 s2)^2, w2 = (s0 s1)^2
+//   s_k = 13/3 D_k^2 + t_k^2 + 4 eps, t0 = 3 d_{i-1/2} - d_{i-3/2}, t1 = d_{i-1/2} + d_{i+1/2},
+//   t2 = d_{i+3/2} - 3 d_{i+1/2}
+//   the candidate corrections e_k are fixed 2-term combinations of d.
+struct WenoRev {
+  double q1;                // q_{i+1}
+  double m2, m1, p1;        // d_{i-3/2}, d_{i-1/2}, d_{i+1/2}
+  double D0, D1, cD0, cD1;  // D_{i-1}, D_i and 13/3 of them
+  double bprev;             // adjoint of d_{i-5/2} (complete)
+  double b0, b1, b2;        // adjoints of d_{i-3/2}, d_{i-1/2}, d_{i+1/2} so far
+  double dir1, dir2;        // direct adjoints of cells i-1, i-2
+
+  __device__ __forceinline__ void init(double qm2, double qm1, double q, double qp1) {
+    q1 = qp1;
+    m2 = qm1 - qm2;
+    m1 = q - qm1;
+    p1 = qp1 - q;
+    D0 = m1 - m2;
+    D1 = p1 - m1;
+    cD0 = K13 * D0;
+    cD1 = K13 * D1;
+    bprev = b0 = b1 = b2 = 0.0;
+    dir1 = dir2 = 0.0;
+  }
+
+  // cell i: q_{i+2}, its saved internals sv (s0, s1, s2, qL, rL, qR, rR), the adjoints Lb
+  // (state at i+1/2) and Rb (state at i-1/2).  Returns the adjoint of q_{i-2}, then
+  // slides to cell i+1.
+  __device__ __forceinline__ double step(double q2, const double sv[WENO_SAVE], double Lb, double Rb) {
+    const double p2 = q2 - q1, D2 = p2 - p1, cD2 = K13 * D2;
+    const double t0 = fma(2.0, m1, D0), t1 = m1 + p1, t2 = fma(-2.0, p1, D2);
+    const double s0 = sv[0], s1 = sv[1], s2 = sv[2];
+    const double p01 = s0 * s1, p02 = s0 * s2, p12 = s1 * s2;
+    const double w0 = p12 * p12, w1 = p02 * p02, w2 = p01 * p01;
+    constexpr double TWO_THIRDS = 2.0 / 3.0;  // 4 x 1/6
+    const double nL = (TWO_THIRDS * Lb) * sv[4], nR = (TWO_THIRDS * Rb) * sv[6];
+    const double dL = -nL * sv[3], dR = -nR * sv[5];
+    const double e0L = fma(-2.0, m2, 5.0 * m1), e1L = fma(2.0, p1, m1), e2L = fma(4.0, p1, -p2);
+    const double e0R = fma(-4.0, m1, m2), e1R = fma(-2.0, m1, -p1), e2R = fma(2.0, p2, -5.0 * p1);
+    // 4 x adjoints of w0, w1 / 6, w2
+    const double bw0 = fma(3.0, fma(nR, e0R, dR), fma(nL, e0L, dL));
+    const double bw1 = fma(nL, e1L, dL) + fma(nR, e1R, dR);
+    const double bw2 = fma(3.0, fma(nL, e2L, dL), fma(nR, e2R, dR));
+    // 2 x adjoints of p12, p02, p01 and of s0, s1, s2
+    const double bp12 = p12 * bw0, bp02 = (6.0 * p02) * bw1, bp01 = p01 * bw2;
+    const double bs0 = fma(bp01, s1, bp02 * s2);
+    const double bs1 = fma(bp01, s0, bp12 * s2);
+    const double bs2 = fma(bp02, s0, bp12 * s1);
+    // half the derivatives of s_k with respect to the differences
+    const double a0 = cD0 + t0, c0 = fma(3.0, t0, cD0);  // -ds0/dm2, ds0/dm1
+    const double a1 = t1 - cD1, c1 = t1 + cD1;           // ds1/dm1, ds1/dp1
+    const double a2 = fma(3.0, t2, cD2), c2 = cD2 + t2;  // -ds2/dp1, ds2/dp2
+    // candidate-correction terms: products of the (scaled) quotient adjoints and the weights
+    const double A = w0 * nL, B = w0 * nR, C = w1 * nL, Dd = w1 * nR, E = w2 * nL, F = w2 * nR;
+    const double gm2 = fma(-0.5, A, fma(0.75, B, -a0 * bs0));
+    const double gm1 = fma(1.25, A, fma(-3.0, B, fma(1.5, C, fma(-3.0, Dd, fma(c0, bs0, a1 * bs1)))));
+    const double gp1 = fma(3.0, C, fma(-1.5, Dd, fma(3.0, E, fma(-1.25, F, fma(c1, bs1, -a2 * bs2)))));
+    const double gp2 = fma(-0.75, E, fma(0.5, F, c2 * bs2));
+    // d_{i-3/2} is complete: emit q_{i-2}
+    const double done = b0 + gm2;
+    const double out = (bprev - done) + dir2;
+    bprev = done;
+    b0 = b1 + gm1;
+    b1 = b2 + gp1;
+    b2 = gp2;
+    dir2 = dir1;
+    dir1 = Lb + Rb;
+    // slide
+    q1 = q2;
+    m2 = m1;
+    m1 = p1;
+    p1 = p2;
+    D0 = D1;
+    D1 = D2;
+    cD0 = cD1;
+    cD1 = cD2;
+    return out;
+  }
+
+  // after the last cell c1 - 1 of a segment: adjoints of q_{c1-2}, q_{c1-1}, q_{c1}, q_{c1+1}
+  __device__ __forceinline__ void flush(double out[4]) const {
+    out[0] = (bprev - b0) + dir2;
+    out[1] = (b0 - b1) + dir1;
+    out[2] = b1 - b2;
+    out[3] = b2;
+  }
+};
 
 // ---------------------------------------------------------------------------------------
 // HLLC forward + reverse (face-normal frame)
