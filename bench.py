@@ -27,7 +27,7 @@ import numpy as np  # noqa: E402
 
 # Algorithmic FP64 operations (add/sub, mul, div, sqrt; each face once) per cell and RHS
 # evaluation, counted by oracle/count_flops.py on a seeded perturbation of each workload.
-FLOPS_PER_CELL_STAGE = {"riemann2d": 1281.0, "shock_cylinder": 1357.0}
+FLOPS_PER_CELL_STAGE = {"riemann2d": 1281.0, "shock_cylinder": 1357.0, "mach5_cylinder": 1276.2}
 # FP64 peak of one GB300: 152 SMs x 2070 MHz boost, NVIDIA's 1.25 TFLOP/s FP64 figure.
 FP64_PEAK_TFLOPS = 1.25
 # DRAM bytes (read + write) per stage-kernel launch, mean of the three stages of one step,
@@ -47,6 +47,10 @@ def workload(name):
         p = W.shock_cylinder()
         desc = ("viscous Mach-2 shock over an immersed cylinder, Navier-Stokes Re=1000 Pr=0.72, 2048x1024, "
                 "WENO5+HLLC+IB+SSP-RK3, CFL 0.5")
+    elif name == "mach5_cylinder":
+        p = W.mach5_cylinder()
+        desc = ("the paper's Mach-5 shock over an immersed cylinder, Euler, 4347x1932 (8.40e6 cells) on "
+                "[-0.5,4]x[0,2], WENO5+HLLC+IB+SSP-RK3, CFL 0.5, inflow/outflow/reflective")
     else:
         raise SystemExit("unknown workload %s" % name)
     return p, desc
@@ -425,7 +429,7 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="riemann2d", choices=["riemann2d", "shock_cylinder", "batched"])
+    ap.add_argument("--workload", default="riemann2d", choices=["riemann2d", "shock_cylinder", "mach5_cylinder", "batched"])
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")

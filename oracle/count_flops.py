@@ -25,5 +25,5 @@ def count(prob, seed=0, amp=0.01):
 
 
 if __name__ == "__main__":
-    for p in (W.riemann2d(1024), W.shock_cylinder(), W.sod(200)):
+    for p in (W.riemann2d(1024), W.shock_cylinder(), W.mach5_cylinder(), W.sod(200)):
         print(json.dumps(count(p)))

@@ -43,21 +43,21 @@ def warm_cosine(k, warm, total, lr_start, lr_end):
 
 
 def fit_gamma(solver, W0, targets, dts, gamma0, iters, lr=0.1, schedule=None, mask=None, outputs=None,
-              checkpoint_every=None):
+              checkpoint_every=None, betas=(0.9, 0.999)):
     """Recover gamma by Adam on the multi-step loss.
 
     solver: binding.Solver of the problem (its other parameters stay fixed); W0: primitive
     initial state, float64 CUDA tensor [4, ny, nx]; targets: [m, 4, ny, nx] states at the steps
     listed in `outputs` (default 1..m); dts: the fixed step sizes of the rollout (len(dts) >=
     max(outputs)); gamma0: initial guess; schedule: None (constant lr) or a function
-    k -> learning rate.  Returns dict(gamma=[...], loss=[...]) with one entry per iteration
+    k -> learning rate; betas: Adam's moment decay rates.  Returns dict(gamma=[...], loss=[...]) with one entry per iteration
     (the loss and gamma before that iteration's update) and the final gamma last."""
     outputs = list(range(1, targets.shape[0] + 1)) if outputs is None else list(outputs)
     if len(outputs) != targets.shape[0] or max(outputs) > len(dts):
         raise ValueError("outputs must index one target per entry within the rollout")
     theta_rest = A.theta_of(solver)[1:].clone()
     g = torch.tensor(float(gamma0), dtype=torch.float64, requires_grad=True)
-    opt = torch.optim.Adam([g], lr=lr)
+    opt = torch.optim.Adam([g], lr=lr, betas=tuple(betas))
     hist = {"gamma": [], "loss": []}
     dts = list(dts)[:max(outputs)]
     for k in range(iters):

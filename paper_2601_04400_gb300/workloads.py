@@ -157,6 +157,29 @@ def shock_cylinder(nx=2048, ny=1024, mach=2.0, Re=1000.0, Pr=0.72, gamma=1.4, D=
                    meta=dict(mach=mach, Re=Re, D=D, radius=r, centre=centre, x_shock=x_shock))
 
 
+def mach5_cylinder(nx=4347, ny=1932, t_end=1.2, cfl=0.5):
+    """The paper's shock-cylinder case (Sec. 3): (x, y) in [-0.5, 4] x [0, 2], cylinder of
+    radius 0.25 at (0.6, 1), Euler, gamma = 1.4; (rho, u, v, p) = (7, 4, 0, 29) for x < 0.3
+    (a Mach-5 shock moving into the gas at rest) and (1.4, 0, 0, 1) beyond; left inflow at the
+    left state, right outflow (transmissive), reflective top and bottom.  The default grid has
+    8.40e6 nearly square cells (the paper's uniform grid of about 8.4e6 cells)."""
+    x0, y0, Lx, Ly = -0.5, 0.0, 4.5, 2.0
+    dx, dy = Lx / nx, Ly / ny
+    X, Y = cell_centres(nx, ny, x0, y0, dx, dy)
+    left = np.array([7.0, 4.0, 0.0, 29.0])
+    right = np.array([1.4, 0.0, 0.0, 1.0])
+    W = np.zeros((4, ny, nx))
+    behind = X < 0.3
+    for c in range(4):
+        W[c] = np.where(behind, left[c], right[c])
+    sdf = np.sqrt((X - 0.6) ** 2 + (Y - 1.0) ** 2) - 0.25
+    inflow = np.array([left, right, right, right])
+    return Problem("mach5_cylinder", nx, ny, x0, y0, dx, dy,
+                   bc=(BC_INFLOW, BC_TRANSMISSIVE, BC_REFLECTIVE, BC_REFLECTIVE), gamma=1.4, mu=0.0,
+                   inflow=inflow, sdf=sdf, W0=W, cfl=cfl, t_end=t_end,
+                   meta=dict(radius=0.25, centre=(0.6, 1.0), x_shock=0.3))
+
+
 def adjoint_case(n=512, mach=2.0, n_steps=400, Re=1000.0, gamma=1.4):
     """Shock-cylinder case scaled to [0,4D]^2, cylinder r = D/2 at (2D, 2D), shock at x = D."""
     return shock_cylinder(nx=n, ny=n, mach=mach, Re=Re, gamma=gamma, Lx=4.0, Ly=4.0, n_steps=n_steps)

@@ -4,7 +4,8 @@ The gradient of L = (1/m) sum_s ||U^s - T^s||^2 (over a subdomain in 2D) with re
 -- entering the solver and the conserved initial state -- from the checkpointed reverse pass,
 against the oracle's exact discrete derivative (forward-mode dual numbers through the same
 steps) and against central finite differences of the GPU forward solver.  Targets are
-oracle runs at gamma = 1.4; the recoveries start away from it."""
+oracle runs at a known gamma (1.4 for Sod, 2 for the cylinder subdomain, whose recovery
+starts from 1.4 as in the paper's)."""
 import numpy as np
 import pytest
 
@@ -117,17 +118,20 @@ def test_gamma_recovery_sod_constant_learning_rate(env):
 
 def test_gamma_recovery_cylinder_subdomain_warm_cosine(env):
     """Loss restricted to the subdomain [0, 1.5] x [0, 1]; constant learning rate, then a
-    cosine decay (the schedule of the shock-cylinder recovery of Sec. 3), from 1.6."""
+    cosine decay (the schedule of the shock-cylinder recovery of Sec. 3); as in the paper's
+    recovery, the initial guess is 1.4 and the target data are made with gamma = 2."""
     torch, B, I = env
     prob = W.shock_cylinder(nx=96, ny=64, Lx=6.0, Ly=4.0, centre=(2.0, 2.0), x_shock=1.0, Re=1000.0, n_steps=40)
     dt = O.max_dt(prob, _cons(prob.W0, GAMMA_TRUE), 0.5)
     dts = [dt] * 40
     outputs = list(range(4, 41, 4))
-    T = torch.tensor(_targets(prob, dts, outputs, GAMMA_TRUE), device="cuda")
+    T = torch.tensor(_targets(prob, dts, outputs, 2.0), device="cuda")
     X, Y = W.cell_centres(prob.nx, prob.ny, prob.x0, prob.y0, prob.dx, prob.dy)
     mask = torch.tensor((X <= 1.5) & (Y <= 1.0), device="cuda")
-    s = B.Solver.from_problem(prob.with_(gamma=1.6))
-    h = I.fit_gamma(s, torch.tensor(prob.W0, device="cuda"), T, dts, 1.6, iters=80, lr=0.02, mask=mask,
-                    outputs=outputs, schedule=lambda k: I.warm_cosine(k, 30, 80, 0.02, 2e-4))
-    assert abs(h["gamma"][-1] - GAMMA_TRUE) < 2e-3
+    s = B.Solver.from_problem(prob.with_(gamma=1.4))
+    # a short second-moment memory: Adam's default 0.999 remembers the large early gradients
+    # and stalls past the overshoot
+    h = I.fit_gamma(s, torch.tensor(prob.W0, device="cuda"), T, dts, 1.4, iters=80, lr=0.05, mask=mask,
+                    outputs=outputs, betas=(0.9, 0.9), schedule=lambda k: I.warm_cosine(k, 30, 80, 0.05, 5e-4))
+    assert abs(h["gamma"][-1] - 2.0) < 5e-3
     assert h["loss"][-1] < 1e-4 * h["loss"][0]
