@@ -556,8 +556,10 @@ __global__ void adj_unpack_add_kernel(const double* __restrict__ P, const double
 // =======================================================================================
 namespace {
 // short segments and small blocks: enough blocks to fill every SM (one line per thread
-// would leave most of the GPU idle); pass 1 pays one extra WENO cell per segment
-constexpr int kSeg1 = 16, kSeg2 = 8, kBlk = 64;
+// would leave most of the GPU idle); pass 1 pays one extra WENO cell per segment, except
+// when the forward stored the internals: then a segment costs almost nothing to start and
+// shorter ones split the work into finer waves
+constexpr int kSeg1 = 16, kSeg1Saved = 8, kSeg2 = 8, kBlk = 64;
 
 unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
@@ -568,13 +570,17 @@ long long line_items(const AdjArgs& a, int dir, int extra, int seg) {
 }
 
 cudaError_t pass1(const AdjArgs& a, bool visc, bool two_d, cudaStream_t s) {
-  const int bx = (int)blocks_for(line_items(a, 0, 1, kSeg1), kBlk);
-  const int by = two_d ? (int)blocks_for(line_items(a, 1, 1, kSeg1), kBlk) : 0;
   if (a.weno_saved) {
     if (!two_d) return cudaErrorInvalidValue;  // the forward saves exist for 2D grids only
-    if (visc) adj_pass1_kernel<true, true, true><<<bx + by, kBlk, 0, s>>>(a, kSeg1, bx);
-    else adj_pass1_kernel<false, false, true><<<bx + by, kBlk, 0, s>>>(a, kSeg1, bx);
-  } else if (visc) {
+    const int sx = (int)blocks_for(line_items(a, 0, 1, kSeg1Saved), kBlk);
+    const int sy = (int)blocks_for(line_items(a, 1, 1, kSeg1Saved), kBlk);
+    if (visc) adj_pass1_kernel<true, true, true><<<sx + sy, kBlk, 0, s>>>(a, kSeg1Saved, sx);
+    else adj_pass1_kernel<false, false, true><<<sx + sy, kBlk, 0, s>>>(a, kSeg1Saved, sx);
+    return cudaGetLastError();
+  }
+  const int bx = (int)blocks_for(line_items(a, 0, 1, kSeg1), kBlk);
+  const int by = two_d ? (int)blocks_for(line_items(a, 1, 1, kSeg1), kBlk) : 0;
+  if (visc) {
     if (two_d) adj_pass1_kernel<true, true, false><<<bx + by, kBlk, 0, s>>>(a, kSeg1, bx);
     else adj_pass1_kernel<true, false, false><<<bx + by, kBlk, 0, s>>>(a, kSeg1, bx);
   } else {
