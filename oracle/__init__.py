@@ -50,6 +50,9 @@ def lib():
         L.or_weno5_beta.argtypes = [_D, _D]
         L.or_hllc.argtypes = [_D, _D, C.c_double, C.c_int, _D, _D]
         L.or_exact_riemann.argtypes = [C.c_double] * 9 + [_D, C.c_int, _D, _D, _D, _D]
+        L.or_nn_set.argtypes = [_D, _D, _D]
+        L.or_nn_eval.argtypes = [_D, C.c_int, C.c_int, _D]
+        L.or_nn_nparam.restype = C.c_int
         L.or_set_threads.argtypes = [C.c_int]
         L.or_get_threads.restype = C.c_int
         _lib = L
@@ -249,3 +252,49 @@ def exact_riemann(left, right, gamma, x, x0, t):
                                   float(right[1]), float(right[2]), float(gamma), float(x0), float(t),
                                   _p(x), n, _p(r), _p(u), _p(p), _p(star)), "exact_riemann")
     return r, u, p, dict(p=star[0], u=star[1], rhoL=star[2], rhoR=star[3])
+
+
+# ---------------------------------------------------------------------------------------
+# neural flux (Sec. 2.3)
+# ---------------------------------------------------------------------------------------
+def nn_nparam():
+    return lib().or_nn_nparam()
+
+
+def nn_set(w, norm, dw=None):
+    """Switch the neural flux on for every later call: w = the network's parameters, norm =
+    (mean[4], sd[4], scale[4]) of the frame channels (rho, normal momentum, tangential
+    momentum, E); dw = tangent of w for the *_tangent calls.  nn_set(None, None) switches it
+    off."""
+    if w is None:
+        _check(lib().or_nn_set(None, None, None), "nn_set")
+        return
+    w = _f64(w).reshape(-1)
+    if w.size != nn_nparam():
+        raise ValueError("expected %d network parameters" % nn_nparam())
+    dw = None if dw is None else _f64(dw).reshape(-1)
+    _check(lib().or_nn_set(_p(w), _p(dw), _p(_f64(norm).reshape(12))), "nn_set")
+
+
+def nn_eval(X):
+    """The network on one normalised image X[4, H, W] -> scaled flux Y[4, H, W]."""
+    X = _f64(X)
+    Y = np.empty_like(X)
+    _check(lib().or_nn_eval(_p(X), X.shape[1], X.shape[2], _p(Y)), "nn_eval")
+    return Y
+
+
+class neural:
+    """Context manager: the neural flux switched on inside the block."""
+
+    def __init__(self, w, norm, dw=None):
+        self.args = (w, norm, dw)
+
+    def __enter__(self):
+        nn_set(self.args[0], self.args[1], dw=self.args[2])
+        return self
+
+    def __exit__(self, *exc):
+        nn_set(None, None)
+        return False
+

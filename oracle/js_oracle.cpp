@@ -26,11 +26,19 @@
 //     case) three cells deep, x sides on interior rows first, then y sides on the full
 //     padded width;
 //   * three-stage SSP Runge-Kutta (Shu-Osher) in place of the forward-Euler update that the
-//     paper prints; CFL time step from the maximum wave speed.
+//     paper prints; CFL time step from the maximum wave speed;
+//   * optionally the neural flux of Sec. 2.3 (or_nn_set): a three-layer 3x3 convolutional
+//     network (4 -> 16 -> 32 -> 4 channels, ReLU, ReLU, tanh, zero "SAME" padding; 6388
+//     parameters, the paper's count) on the normalised mean of the two WENO5 face states in
+//     conserved variables, per direction, added to the HLLC flux of every face; both
+//     directions share the network, y faces enter as transposed images with the normal
+//     momentum first (readings: the paper fixes the layers and the parameter count, not the
+//     channel widths, the input's face frame or the normalisation).
 //
 // Every routine is templated on the scalar type so that the same plain code gives FP64
 // values (double), forward-mode tangents (Dual<N>, the oracle's discrete derivative) and
 // operation counts (Cnt).  Compile with -ffp-contract=off: no fused multiply-adds.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -135,6 +143,84 @@ using std::sqrt;
 template <class T> T tmin(const T& a, const T& b) { return (b < a) ? b : a; }  // tie -> a
 template <class T> T tmax(const T& a, const T& b) { return (a < b) ? b : a; }  // tie -> a
 template <class T> T tabs(const T& a) { return (a < 0.0) ? -a : a; }
+
+// tanh and a value carrying a tangent (slot 0 of a dual number)
+inline double ttanh(double x) { return std::tanh(x); }
+template <int N> Dual<N> ttanh(const Dual<N>& a) {
+  const double t = std::tanh(a.v);
+  Dual<N> r(t);
+  for (int k = 0; k < N; ++k) r.d[k] = (1.0 - t * t) * a.d[k];
+  return r;
+}
+inline Cnt ttanh(Cnt a) { return Cnt(std::tanh(a.v)); }
+template <class T> T seeded(double v, double) { return T(v); }
+template <> Dual<1> seeded<Dual<1>>(double v, double d) { Dual<1> r(v); r.d[0] = d; return r; }
+
+// ---------------------------------------------------------------------------------------
+// Neural flux (Sec. 2.3): a fully convolutional network of three 3x3 layers with zero
+// ("SAME") padding, 4 -> 16 -> 32 -> 4 channels, ReLU, ReLU, tanh (6388 parameters), maps
+// the normalised WENO5 face states of one direction to a flux correction added to HLLC.
+// Parameter layout: w1[16][4][3][3], b1[16], w2[32][16][3][3], b2[32], w3[4][32][3][3], b3[4].
+// ---------------------------------------------------------------------------------------
+const int NN_C[4] = {4, 16, 32, 4};
+const int NN_NPARAM = 16 * 4 * 9 + 16 + 32 * 16 * 9 + 32 + 4 * 32 * 9 + 4;  // 6388
+
+struct NnCfg {
+  bool on = false;
+  std::vector<double> w, dw;               // parameters and their tangent
+  double mean[4], sd[4], scale[4];         // input normalisation and output scale (frame channels)
+};
+NnCfg g_nn;
+
+// one 3x3 layer with zero padding: out[co][h][x] = b[co] + sum_ci,ky,kx w[co][ci][ky][kx] in[ci][h+ky-1][x+kx-1]
+template <class T>
+void nn_conv(const std::vector<T>& in, int cin, int H, int Wd, const T* w, const T* b, int cout, std::vector<T>& out) {
+  out.assign((size_t)cout * H * Wd, T(0.0));
+  for (int co = 0; co < cout; ++co)
+    for (int h = 0; h < H; ++h)
+      for (int x = 0; x < Wd; ++x) {
+        T acc = b[co];
+        for (int ci = 0; ci < cin; ++ci)
+          for (int ky = 0; ky < 3; ++ky) {
+            const int hh = h + ky - 1;
+            if (hh < 0 || hh >= H) continue;
+            for (int kx = 0; kx < 3; ++kx) {
+              const int xx = x + kx - 1;
+              if (xx < 0 || xx >= Wd) continue;
+              acc = acc + w[((co * cin + ci) * 3 + ky) * 3 + kx] * in[((size_t)ci * H + hh) * Wd + xx];
+            }
+          }
+        out[((size_t)co * H + h) * Wd + x] = acc;
+      }
+}
+
+// the network on one image x[4][H][W] (normalised frame channels) -> y[4][H][W] (scaled flux)
+template <class T>
+void nn_forward(const std::vector<T>& x, int H, int Wd, const std::vector<T>& P, std::vector<T>& y) {
+  const T* w1 = P.data();
+  const T* b1 = w1 + 16 * 4 * 9;
+  const T* w2 = b1 + 16;
+  const T* b2 = w2 + 32 * 16 * 9;
+  const T* w3 = b2 + 32;
+  const T* b3 = w3 + 4 * 32 * 9;
+  std::vector<T> a1, a2, z3;
+  nn_conv(x, 4, H, Wd, w1, b1, 16, a1);
+  for (auto& v : a1) v = (v > 0.0) ? v : T(0.0);
+  nn_conv(a1, 16, H, Wd, w2, b2, 32, a2);
+  for (auto& v : a2) v = (v > 0.0) ? v : T(0.0);
+  nn_conv(a2, 32, H, Wd, w3, b3, 4, z3);
+  y.resize(z3.size());
+  const size_t plane = (size_t)H * Wd;
+  for (int c = 0; c < 4; ++c)
+    for (size_t o = 0; o < plane; ++o) y[c * plane + o] = g_nn.scale[c] * ttanh(z3[c * plane + o]);
+}
+
+template <class T>
+std::vector<T> nn_params() {
+  std::vector<T> P(NN_NPARAM);
+  for (int k = 0; k < NN_NPARAM; ++k) P[k] = seeded<T>(g_nn.w[k], g_nn.dw.empty() ? 0.0 : g_nn.dw[k]);
+  return P;
+}
 
 // ---------------------------------------------------------------------------------------
 // problem description
@@ -524,13 +610,15 @@ struct Solver {
 
   // numerical + viscous flux through the face between padded ids il (left/low) and ir
   // (right/high).  dir 0: x face, stride 1; dir 1: y face, stride W.
-  void face_flux(long il, long ir, long stride, long tstride, int dir, T out[4]) {
+  // wL, wR (optional): the WENO5 face states (primitive) before the positivity fallback
+  void face_flux(long il, long ir, long stride, long tstride, int dir, T out[4], T* wL = nullptr, T* wR = nullptr) {
     T qL[4], qR[4];
     for (int c = 0; c < 4; ++c) {
       const std::vector<T>& q = Q[c];
       qL[c] = weno5(q[il - 2 * stride], q[il - stride], q[il], q[il + stride], q[il + 2 * stride]);
       qR[c] = weno5(q[ir + 2 * stride], q[ir + stride], q[ir], q[ir - stride], q[ir - 2 * stride]);
     }
+    if (wL) for (int c = 0; c < 4; ++c) { wL[c] = qL[c]; wR[c] = qR[c]; }
     if (!(qL[0] > 0.0) || !(qL[3] > 0.0) || !(qR[0] > 0.0) || !(qR[3] > 0.0)) {
       // positivity fallback: first-order (cell) states at this face
       for (int c = 0; c < 4; ++c) { qL[c] = Q[c][il]; qR[c] = Q[c][ir]; }
@@ -570,21 +658,70 @@ struct Solver {
     if (!primitives()) return ERR_NONPHYSICAL;
     const int nx = g.nx, ny = g.ny;
     const long W = L.W;
+    const bool nn = g_nn.on;
+    // network input images, frame channels (rho, normal momentum, tangential momentum, E):
+    // x faces as [4][ny][nx+1]; y faces transposed, [4][nx][ny+1], so that the second image
+    // axis is always the face-normal one
+    std::vector<T> Xx, Xy;
+    if (nn) {
+      Xx.assign((size_t)4 * ny * (nx + 1), T(0.0));
+      if (ny > 1) Xy.assign((size_t)4 * nx * (ny + 1), T(0.0));
+    }
+    auto image_value = [&](const T wL[4], const T wR[4], int dir, T x[4]) {
+      const int n = (dir == 0) ? 1 : 2, t = (dir == 0) ? 2 : 1;
+      const T EL = energy(wL[0], wL[1], wL[2], wL[3], P.gamma), ER = energy(wR[0], wR[1], wR[2], wR[3], P.gamma);
+      const T m[4] = {0.5 * (wL[0] + wR[0]), 0.5 * (wL[0] * wL[n] + wR[0] * wR[n]),
+                      0.5 * (wL[0] * wL[t] + wR[0] * wR[t]), 0.5 * (EL + ER)};
+      for (int c = 0; c < 4; ++c) x[c] = (m[c] - g_nn.mean[c]) / g_nn.sd[c];
+    };
 #pragma omp parallel for schedule(static) if (parallel)
     for (int j = 0; j < ny; ++j)
       for (int f = 0; f <= nx; ++f) {
-        T out[4];
-        face_flux(L.idx(f - 1, j), L.idx(f, j), 1, W, 0, out);
+        T out[4], wL[4], wR[4];
+        face_flux(L.idx(f - 1, j), L.idx(f, j), 1, W, 0, out, nn ? wL : nullptr, nn ? wR : nullptr);
         for (int c = 0; c < 4; ++c) Fx[c][(size_t)j * (nx + 1) + f] = out[c];
+        if (nn) {
+          T x[4];
+          image_value(wL, wR, 0, x);
+          for (int c = 0; c < 4; ++c) Xx[((size_t)c * ny + j) * (nx + 1) + f] = x[c];
+        }
       }
     if (ny > 1) {
 #pragma omp parallel for schedule(static) if (parallel)
       for (int f = 0; f <= ny; ++f)
         for (int i = 0; i < nx; ++i) {
-          T out[4];
-          face_flux(L.idx(i, f - 1), L.idx(i, f), W, 1, 1, out);
+          T out[4], wL[4], wR[4];
+          face_flux(L.idx(i, f - 1), L.idx(i, f), W, 1, 1, out, nn ? wL : nullptr, nn ? wR : nullptr);
           for (int c = 0; c < 4; ++c) Gy[c][(size_t)f * nx + i] = out[c];
+          if (nn) {
+            T x[4];
+            image_value(wL, wR, 1, x);
+            for (int c = 0; c < 4; ++c) Xy[((size_t)c * nx + i) * (ny + 1) + f] = x[c];
+          }
         }
+    }
+    if (nn) {
+      // neural flux added to the numerical flux of every face (same network both ways)
+      const std::vector<T> Pn = nn_params<T>();
+      std::vector<T> Y;
+      nn_forward(Xx, ny, nx + 1, Pn, Y);
+      const int fx[4] = {0, 1, 2, 3};  // conserved component of each frame channel, x faces
+      for (int c = 0; c < 4; ++c)
+        for (int j = 0; j < ny; ++j)
+          for (int f = 0; f <= nx; ++f) {
+            T& F = Fx[fx[c]][(size_t)j * (nx + 1) + f];
+            F = F + Y[((size_t)c * ny + j) * (nx + 1) + f];
+          }
+      if (ny > 1) {
+        nn_forward(Xy, nx, ny + 1, Pn, Y);
+        const int fy[4] = {0, 2, 1, 3};  // y faces: normal momentum is rho v
+        for (int c = 0; c < 4; ++c)
+          for (int i = 0; i < nx; ++i)
+            for (int f = 0; f <= ny; ++f) {
+              T& G = Gy[fy[c]][(size_t)f * nx + i];
+              G = G + Y[((size_t)c * nx + i) * (ny + 1) + f];
+            }
+      }
     }
     const bool av = !is_off(P.nu);
 #pragma omp parallel for schedule(static) if (parallel)
@@ -889,6 +1026,31 @@ int or_step_tangent(const or_grid* g, const double* theta, const double* dtheta,
   }
   for (int c = 0; c < 4; ++c)
     for (size_t o = 0; o < n; ++o) { U[c * n + o] = Uc[c][o].v; dU[c * n + o] = Uc[c][o].d[0]; }
+  return OK;
+}
+
+// Neural flux: w = NN_NPARAM parameters (NULL switches the network off), dw = their tangent
+// for the *_tangent calls (NULL: zero), norm = mean[4], sd[4], scale[4] of the frame channels.
+// The setting applies to every later call.
+int or_nn_set(const double* w, const double* dw, const double* norm) {
+  if (!w) { g_nn.on = false; g_nn.w.clear(); g_nn.dw.clear(); return OK; }
+  if (!norm) return ERR_ARG;
+  for (int c = 0; c < 4; ++c) if (!(norm[4 + c] > 0.0)) return ERR_ARG;
+  g_nn.w.assign(w, w + NN_NPARAM);
+  if (dw) g_nn.dw.assign(dw, dw + NN_NPARAM); else g_nn.dw.clear();
+  for (int c = 0; c < 4; ++c) { g_nn.mean[c] = norm[c]; g_nn.sd[c] = norm[4 + c]; g_nn.scale[c] = norm[8 + c]; }
+  g_nn.on = true;
+  return OK;
+}
+
+int or_nn_nparam(void) { return NN_NPARAM; }
+
+// The network alone on one image X[4][H][W] -> Y[4][H][W] (uses the parameters of or_nn_set).
+int or_nn_eval(const double* X, int H, int Wd, double* Y) {
+  if (!g_nn.on || H < 1 || Wd < 1) return ERR_ARG;
+  std::vector<double> x(X, X + (size_t)4 * H * Wd), y;
+  nn_forward(x, H, Wd, nn_params<double>(), y);
+  std::copy(y.begin(), y.end(), Y);
   return OK;
 }
 
