@@ -133,6 +133,32 @@ int js_tape_reserve_ex(js_ctx* ctx, int n_slots, int flags);
 int js_step_taped(js_ctx* ctx, double* U, double dt, int slot);
 int js_step_vjp_taped(js_ctx* ctx, int slot, double dt, const double* lam_np1, double* lam_n, double* p_bar);
 
+/* Neural flux (Sec. 2.3).  A fully convolutional network of three 3x3 layers with zero
+ * ("SAME") padding, 4 -> 16 -> 32 -> 4 channels, ReLU, ReLU, tanh (JS_NN_NPARAM = 6388
+ * parameters, the paper's count), evaluated on one image per direction and added to the HLLC
+ * flux of every face; the update then takes the divergence of F_HLLC + F_neural.
+ *   image: x faces [4][ny][nx+1], y faces transposed [4][nx][ny+1] (1D: x faces only);
+ *   pixel (line, face f) = (m - mean) / sd per frame channel, m = the mean of the two WENO5
+ *   face states of face f in conserved variables of the face frame (rho, normal momentum,
+ *   tangential momentum, E); both directions share the network;
+ *   neural flux of frame component k through the face = scale[k] * output channel k.
+ * Parameter layout (doubles): w1[16][4][3][3], b1[16], w2[32][16][3][3], b2[32],
+ * w3[4][32][3][3], b3[4].
+ *   w      device pointer to the parameters, read at every later stage (so they may be
+ *          updated in place between calls); NULL switches the neural flux off
+ *   w_bar  device pointer, JS_NN_NPARAM doubles, or NULL: every later js_rhs_vjp /
+ *          js_step_vjp / js_step_vjp_taped ADDS the parameter gradient (summed in a fixed
+ *          order: reproducible)
+ *   norm   host array mean[4], sd[4] (> 0), scale[4] (copied)
+ *   precision  JS_NN_F64 (FP64 network arithmetic) or JS_NN_F32 (FP32; the solver stays FP64)
+ * Applies to js_rhs, js_step, the taped steps and the reverse calls of this context (not to
+ * js_batch_*).  The first call allocates the network workspace (before any stream capture).
+ * Returns JS_ERR_ARG for a bad norm or precision, JS_ERR_NOMEM. */
+#define JS_NN_NPARAM 6388
+#define JS_NN_F64 0
+#define JS_NN_F32 1
+int js_set_neural(js_ctx* ctx, const double* w, double* w_bar, const double* norm, int precision);
+
 /* Read and clear the device error flag; synchronises the stream.  Returns JS_OK,
  * JS_ERR_NONPHYSICAL or JS_ERR_TIMEOUT (or JS_ERR_CUDA if the stream itself failed). */
 int js_sync_status(js_ctx* ctx);

@@ -16,6 +16,8 @@ from . import build as _build
 JS_OK, JS_ERR_ARG, JS_ERR_CUDA, JS_ERR_NONPHYSICAL, JS_ERR_TIMEOUT, JS_ERR_IB, JS_ERR_NOMEM = 0, -1, -2, -3, -4, -5, -6
 JS_NPARAM = 20
 JS_TAPE_WENO = 1
+JS_NN_NPARAM = 6388
+JS_NN_F64, JS_NN_F32 = 0, 1
 
 _lib = None
 
@@ -60,6 +62,7 @@ SIGNATURES = {
     "js_ib_info": (_I, [_P, C.POINTER(_I), _P]),
     "js_tape_reserve": (_I, [_P, _I]),
     "js_tape_reserve_ex": (_I, [_P, _I, _I]),
+    "js_set_neural": (_I, [_P, _P, _P, _P, _I]),
     "js_step_taped": (_I, [_P, _P, _D, _I]),
     "js_step_vjp_taped": (_I, [_P, _I, _D, _P, _P, _P]),
     "js_set_tuning": (_I, [_P, _I]),
@@ -265,6 +268,23 @@ class Solver:
 
     def set_stream(self, stream=None):
         js_set_stream(self.ctx, stream)
+
+    def set_neural(self, w, norm=None, w_bar=None, fp32=False):
+        """Neural flux on (w: float64 CUDA tensor of JS_NN_NPARAM parameters, kept by
+        reference: later updates in place take effect; norm: mean[4], sd[4], scale[4] of the
+        frame channels; w_bar: float64 CUDA tensor that reverse calls add the parameter
+        gradient to, or None; fp32: network arithmetic in FP32) or off (w = None)."""
+        if w is None:
+            _check(lib().js_set_neural(self.ctx, None, None, None, 0), "js_set_neural")
+            self._nn = None
+            return
+        if w.numel() != JS_NN_NPARAM or (w_bar is not None and w_bar.numel() != JS_NN_NPARAM):
+            raise ValueError("w and w_bar hold %d parameters" % JS_NN_NPARAM)
+        nm = np.ascontiguousarray(np.asarray(norm, dtype=np.float64).reshape(12))
+        _check(lib().js_set_neural(self.ctx, _ptr(w), None if w_bar is None else _ptr(w_bar),
+                                   nm.ctypes.data_as(C.c_void_p), JS_NN_F32 if fp32 else JS_NN_F64),
+               "js_set_neural")
+        self._nn = (w, w_bar, nm)  # keep the device buffers alive while the library uses them
 
     def set_tuning(self, variant):
         _check(lib().js_set_tuning(self.ctx, int(variant)), "js_set_tuning")

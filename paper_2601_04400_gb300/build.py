@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libjaxshock.so")
-SOURCES = ["js_forward.cu", "js_adjoint.cu", "js_batch.cu", "js_host.cu", "js_noalloc.cu"]
+SOURCES = ["js_forward.cu", "js_adjoint.cu", "js_batch.cu", "js_host.cu", "js_noalloc.cu", "js_neural.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 

@@ -600,7 +600,7 @@ cudaError_t pass2(const AdjArgs& a, bool two_d, cudaStream_t s) {
 cudaError_t launch_adj_stage(const AdjArgs& a, const BcArgs& bc, const IbArgs& ib, const IbTArgs& ibt, int wall,
                              const double* Unext, double* Uacc, double ra, double rb, double dt, bool rhs_mode,
                              double* inflow_acc, const double* inflow_prim, double* qIb, cudaStream_t s,
-                             long long* launches) {
+                             long long* launches, const NnArgs* nn) {
   const Lay& L = a.lay;
   const unsigned gp = blocks_for(L.plane, 256);
   long long n = 0;
@@ -611,6 +611,11 @@ cudaError_t launch_adj_stage(const AdjArgs& a, const BcArgs& bc, const IbArgs& i
   if (e != cudaSuccess) return e;
   const bool two_d = L.ny > 1;
   if ((e = pass1(a, a.visc != 0, two_d, s)) != cudaSuccess) return e;
+  if (nn) {
+    // the neural flux: its face-state adjoints join the HLLC ones before the WENO5 reverse
+    if ((e = nn_reverse(*nn, a, s)) != cudaSuccess) return e;
+    n += nn->w_bar ? 13 : 9;
+  }
   if ((e = pass2(a, two_d, s)) != cudaSuccess) return e;
   n += 2;
   adj_primvjp_kernel<<<gp, 256, 0, s>>>(a);

@@ -60,6 +60,12 @@ struct js_ctx {
   double* inflow_acc = nullptr;   // 16
   double* inflow_prim = nullptr;  // 16
   double* qIb = nullptr;     // 4 per ghost
+  // neural flux (js_set_neural)
+  bool nn_on = false;
+  js::NnArgs nn;
+  double* nnQ = nullptr;        // primitives of the stage input (4 planes)
+  void* nn_buf[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  double* nn_partial = nullptr;
   int variant = 0;  // stage-kernel tile shape (js_set_tuning)
   std::vector<std::pair<const double*, js::TensorMap128>> tmaps;  // TMA maps of stage inputs
   // tape: per slot the three filled stage states of one recorded step and, when recording
@@ -301,8 +307,27 @@ const js::TensorMap128* stage_tmap(js_ctx* c, const double* buf) {
   return &c->tmaps.back().second;
 }
 
+// neural flux of the stage input a.Uin (before the stage kernel) and its divergence
+// subtracted from the stage output (after it)
+int nn_before(js_ctx* c, const StageArgs& a) {
+  if (!c->nn_on) return JS_OK;
+  c->nn.g1 = 1.0 / (c->p.gamma - 1.0);
+  JS_CUDA(js::nn_prims(a.Uin, c->nnQ, c->lay, c->p.gamma, c->stream));
+  JS_CUDA(js::nn_forward(c->nn, c->nnQ, c->lay.plane, c->stream));
+  c->launches += 5;
+  return JS_OK;
+}
+int nn_after(js_ctx* c, const StageArgs& a, bool rhs) {
+  if (!c->nn_on) return JS_OK;
+  JS_CUDA(js::nn_apply(c->nn, a, rhs, c->stream));
+  ++c->launches;
+  return JS_OK;
+}
+
 // fused stage kernel, bracketed by events while profiling
 int stage(js_ctx* c, const StageArgs& a, bool visc, bool rhs) {
+  int rc = nn_before(c, a);
+  if (rc) return rc;
   const bool timed = c->profiling && c->ev_used + 2 <= (int)c->ev.size();
   if (timed) JS_CUDA(cudaEventRecord(c->ev[c->ev_used], c->stream));
   const js::TensorMap128* tm = (c->variant == 0) ? stage_tmap(c, a.Uin) : nullptr;
@@ -312,7 +337,7 @@ int stage(js_ctx* c, const StageArgs& a, bool visc, bool rhs) {
     c->ev_used += 2;
   }
   ++c->launches;
-  return JS_OK;
+  return nn_after(c, a, rhs);
 }
 
 }  // namespace
@@ -369,7 +394,9 @@ void js_destroy(js_ctx* c) {
   cudaFree(c->err); cudaFree(c->red);
   cudaFree(c->ibt_cell); cudaFree(c->ibt_ptr); cudaFree(c->ibt_ghost); cudaFree(c->ibt_w);
   cudaFree(c->Q); cudaFree(c->Qb); cudaFree(c->lam); cudaFree(c->P0); cudaFree(c->P1); cudaFree(c->Uacc);
-  cudaFree(c->wsave); cudaFree(c->wsave_fwd); cudaFree(c->fadj); cudaFree(c->inflow_acc); cudaFree(c->inflow_prim); cudaFree(c->qIb);
+  cudaFree(c->wsave); cudaFree(c->wsave_fwd); cudaFree(c->fadj);
+  cudaFree(c->nnQ); cudaFree(c->nn_partial);
+  for (void* b : c->nn_buf) cudaFree(b); cudaFree(c->inflow_acc); cudaFree(c->inflow_prim); cudaFree(c->qIb);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   for (double* t : c->tape) cudaFree(t);
   for (double* t : c->tape_w) cudaFree(t);
@@ -419,6 +446,60 @@ int js_create(const js_grid* grid, const js_params* params, const js_boundary* b
     }
   }
   *out = c;
+  return JS_OK;
+}
+
+int js_set_neural(js_ctx* c, const double* w, double* w_bar, const double* norm, int precision) {
+  if (!c) return JS_ERR_ARG;
+  if (!w) {
+    c->nn_on = false;
+    return JS_OK;
+  }
+  if (!norm || (precision != JS_NN_F64 && precision != JS_NN_F32)) return JS_ERR_ARG;
+  for (int k = 0; k < 4; ++k)
+    if (!(norm[4 + k] > 0.0) || !std::isfinite(norm[k]) || !std::isfinite(norm[8 + k])) return JS_ERR_ARG;
+  js::NnArgs& n = c->nn;
+  const bool two_d = c->g.ny > 1;
+  n.lay = c->lay;
+  n.nimg = two_d ? 2 : 1;
+  n.H[0] = c->g.ny;
+  n.W[0] = c->g.nx + 1;
+  n.H[1] = two_d ? c->g.nx : 0;
+  n.W[1] = two_d ? c->g.ny + 1 : 0;
+  n.pix0 = (long long)n.H[0] * n.W[0];
+  const long long pix = n.pix0 + (long long)n.H[1] * n.W[1];
+  if (!c->nnQ) {
+    // buffers sized for FP64 (either precision fits): channels 4, 16, 32, 4, 4, 16, 32
+    const int ch[7] = {4, 16, 32, 4, 4, 16, 32};
+    for (int k = 0; k < 7; ++k)
+      if (cudaMalloc(&c->nn_buf[k], sizeof(double) * ch[k] * (size_t)pix) != cudaSuccess) return JS_ERR_NOMEM;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    n.nwblk = 2 * (sms > 0 ? sms : 1);  // weight-gradient blocks (each keeps a partial sum)
+    if (cudaMalloc(&c->nn_partial, sizeof(double) * js::NN_NPARAM * (size_t)n.nwblk) != cudaSuccess ||
+        cudaMalloc(&c->nnQ, sizeof(double) * 4 * (size_t)c->lay.plane) != cudaSuccess)
+      return JS_ERR_NOMEM;
+    JS_CUDA(cudaMemset(c->nnQ, 0, sizeof(double) * 4 * (size_t)c->lay.plane));
+  }
+  n.X = c->nn_buf[0];
+  n.A1 = c->nn_buf[1];
+  n.A2 = c->nn_buf[2];
+  n.T3 = c->nn_buf[3];
+  n.G4 = c->nn_buf[4];
+  n.G16 = c->nn_buf[5];
+  n.G32 = c->nn_buf[6];
+  n.partial = c->nn_partial;
+  n.fp32 = (precision == JS_NN_F32) ? 1 : 0;
+  n.w = w;
+  n.w_bar = w_bar;
+  for (int k = 0; k < 4; ++k) {
+    n.mean[k] = norm[k];
+    n.inv_sd[k] = 1.0 / norm[4 + k];
+    n.scale[k] = norm[8 + k];
+  }
+  n.g1 = 1.0 / (c->p.gamma - 1.0);
+  c->nn_on = true;
   return JS_OK;
 }
 
@@ -565,6 +646,8 @@ int stage_save(js_ctx* c, StageArgs a, bool visc, double* wsave) {
   a.wsave = wsave;
   a.splane = saved_plane(c);
   a.tpitch = transposed_pitch(c);
+  int rc = nn_before(c, a);
+  if (rc) return rc;
   const bool timed = c->profiling && c->ev_used + 2 <= (int)c->ev.size();
   if (timed) JS_CUDA(cudaEventRecord(c->ev[c->ev_used], c->stream));
   JS_CUDA(js::launch_stage_save(a, visc, stage_tmap(c, a.Uin), c->stream));
@@ -573,7 +656,7 @@ int stage_save(js_ctx* c, StageArgs a, bool visc, double* wsave) {
     c->ev_used += 2;
   }
   ++c->launches;
-  return JS_OK;
+  return nn_after(c, a, false);
 }
 
 js::AdjArgs adj_args(js_ctx* c, const double* X, double* Ub, double* p_bar) {
@@ -630,8 +713,10 @@ int adj_stage(js_ctx* c, const double* X, const double* Unext, double* Ub, doubl
     a.wsave = saved;
     a.weno_saved = 1;
   }
+  c->nn.g1 = 1.0 / (c->p.gamma - 1.0);
   JS_CUDA(js::launch_adj_stage(a, c->bc, ib_args(c), ibt_args(c), c->p.wall, Unext, c->Uacc, ra, rb, dt, rhs_mode,
-                               c->inflow_acc, c->inflow_prim, c->qIb, c->stream, &c->launches));
+                               c->inflow_acc, c->inflow_prim, c->qIb, c->stream, &c->launches,
+                               c->nn_on ? &c->nn : nullptr));
   return JS_OK;
 }
 

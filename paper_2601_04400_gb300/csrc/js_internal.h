@@ -74,10 +74,50 @@ struct AdjArgs {
   int weno_saved;            // wsave already holds the stage's WENO internals (forward SAVE)
 };
 
+// ---------------------------------------------------------------------------------------
+// neural flux (Sec. 2.3): three 3x3 convolution layers 4 -> 16 -> 32 -> 4 (ReLU, ReLU, tanh)
+// over the face images of each direction (x faces [C][ny][nx+1]; y faces transposed,
+// [C][nx][ny+1]); parameter blocks (weights [co][ci][3][3] then biases) at NN_OFF*
+// ---------------------------------------------------------------------------------------
+constexpr int NN_NPARAM = 6388;
+constexpr int NN_OFF1 = 0, NN_OFF2 = 592, NN_OFF3 = 5232;
+
+struct NnArgs {
+  Lay lay;
+  int fp32;                   // network arithmetic: 0 FP64, 1 FP32
+  int nimg;                   // face images: 1 (1D: x faces only) or 2
+  int H[2], W[2];             // image extents (lines x faces per line)
+  long long pix0;             // H[0] * W[0]: image 1 starts at C * pix0 in a C-channel buffer
+  const double* w;            // parameters (device, NN_NPARAM)
+  double* w_bar;              // accumulated parameter gradient or nullptr
+  double mean[4], inv_sd[4], scale[4];  // frame channels (rho, normal mom., tangential mom., E)
+  double g1;                  // 1/(gamma - 1)
+  void* X;                    // 4-channel network input
+  void* A1;                   // 16-channel activations of layer 1
+  void* A2;                   // 32-channel activations of layer 2
+  void* T3;                   // 4-channel tanh outputs (unscaled)
+  void* G4;                   // 4-channel gradient scratch
+  void* G16;                  // 16-channel gradient scratch
+  void* G32;                  // 32-channel gradient scratch
+  double* partial;            // weight-gradient partial sums [nwblk][NN_NPARAM]
+  int nwblk;
+};
+
+// forward: images of the stage input (primitives Q, plane qplane) and the network, into T3
+cudaError_t nn_forward(const NnArgs& n, const double* Q, long long qplane, cudaStream_t s);
+// primitive variables of every padded cell of U into Q (4 planes)
+cudaError_t nn_prims(const double* U, double* Q, const Lay& lay, double gamma, cudaStream_t s);
+// stage output (or RHS) minus the divergence of the neural flux held in T3
+cudaError_t nn_apply(const NnArgs& n, const StageArgs& a, bool rhs, cudaStream_t s);
+// reverse: recompute the network on a.Q, seed with the face-flux adjoints of a.lam, back-
+// propagate (parameter gradient into n.w_bar), add the face-state adjoints to a.fadj
+cudaError_t nn_reverse(const NnArgs& n, const AdjArgs& a, cudaStream_t s);
+
+// nn: the neural flux's reverse (run between pass 1 and pass 2) or nullptr
 cudaError_t launch_adj_stage(const AdjArgs& a, const BcArgs& bc, const IbArgs& ib, const IbTArgs& ibt, int wall,
                              const double* Unext, double* Uacc, double ra, double rb, double dt, bool rhs_mode,
                              double* inflow_acc, const double* inflow_prim, double* qIb, cudaStream_t s,
-                             long long* launches);
+                             long long* launches, const NnArgs* nn = nullptr);
 cudaError_t launch_adj_unpack(const double* P, const double* P2, double* U, const Lay& lay, cudaStream_t s);
 
 // one instance of the batched kernel (js_batch.cu), filled from a context by js_internal_desc

@@ -1,0 +1,481 @@
+// Neural flux (arXiv 2601.04400, Sec. 2.3): a fully convolutional network of three 3x3
+// layers with zero ("SAME") padding, 4 -> 16 -> 32 -> 4 channels, ReLU, ReLU, tanh (6388
+// parameters), evaluated on the face images of each direction and added to the HLLC flux;
+// the update of Sec. 2.3 then takes the divergence of F_HLLC + F_neural.
+//
+// Face image of direction d (d = 0: x faces as [C][ny][nx+1]; d = 1: y faces transposed,
+// [C][nx][ny+1], so that the second axis is always the face-normal one and both directions
+// share the network): pixel (line h, face f) holds the normalised mean of the two WENO5 face
+// states of face f in conserved variables of the face frame (rho, normal momentum,
+// tangential momentum, E).  The network's output channel k, times scale[k], is the neural
+// flux of frame component k through that face.
+//
+// Forward per stage: primitives -> images -> three convolution launches (T3 = tanh output)
+// -> the fused stage kernel (HLLC part) -> nn_apply subtracts the neural flux divergence.
+// Reverse per stage: the images and activations are recomputed from the stage state; the
+// seed is the face-flux adjoint (lambda'_right - lambda'_left)/h (the same as for the HLLC
+// flux); three data-gradient launches (ReLU masks fused), three weight-gradient launches
+// (per-block partial sums, reduced in a fixed order, so the parameter gradient is
+// reproducible) and the image reverse, which adds the face-state adjoints to the WENO5
+// reverse's inputs and d/dgamma of the face energies to the parameter gradient.
+//
+// Arithmetic type T: double (FP64, the oracle's precision) or float (FP32 on the CUDA
+// cores; the network is a dense contraction of 6336 multiply-adds per face, which FP64
+// would make about 20x the cost of the FP64 solver it corrects).
+#include <cuda_runtime.h>
+
+#include "js_device.cuh"
+#include "js_internal.h"
+
+namespace js {
+
+namespace {
+
+constexpr int TILE = 16;            // pixels per tile side; one thread per pixel
+constexpr int TH = TILE + 2;        // tile with its 1-pixel halo
+constexpr int NTHR = TILE * TILE;
+
+template <class T>
+__device__ __forceinline__ T* chan_img(void* base, int C, int d, long long pix0) {
+  return static_cast<T*>(base) + (d == 0 ? 0LL : (long long)C * pix0);
+}
+template <class T>
+__device__ __forceinline__ const T* chan_img(const void* base, int C, int d, long long pix0) {
+  return static_cast<const T*>(base) + (d == 0 ? 0LL : (long long)C * pix0);
+}
+
+__device__ __forceinline__ double act_tanh(double x) { return tanh(x); }
+__device__ __forceinline__ float act_tanh(float x) { return tanhf(x); }
+
+// WENO5 face states (primitive, before any positivity fallback) of face f of line h in
+// direction d: left-biased from cell f-1, right-biased from cell f (the stage kernel's
+// formulation, so the same values)
+__device__ __forceinline__ void face_states(const Lay& L, const double* Q, long long qplane, int d, int h, int f,
+                                            double wl[4], double wr[4]) {
+  const long long st = (d == 0) ? 1 : L.pitch;
+  const long long cf = (d == 0) ? L.idx(f, h) : L.idx(h, f);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const double* q = Q + c * qplane + cf;
+    const double qm3 = q[-3 * st], qm2 = q[-2 * st], qm1 = q[-st], q0 = q[0], qp1 = q[st], qp2 = q[2 * st];
+    double dummy;
+    Win a;
+    a.init(qm3, qm2, qm1, q0);
+    a.step<true, false>(qp1, wl[c], dummy);
+    Win b;
+    b.init(qm2, qm1, q0, qp1);
+    b.step<false, true>(qp2, dummy, wr[c]);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// forward
+// ---------------------------------------------------------------------------------------
+__global__ void nn_prims_kernel(const double* __restrict__ U, double* __restrict__ Q, Lay L, Gas g) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= L.plane) return;
+  const int col = (int)(t % L.pitch), row = (int)(t / L.pitch);
+  if (col >= L.nx + 6 || row >= L.H) return;
+  double u, v, p, T;
+  const double r = U[t];
+  cons_to_prim(r, U[L.plane + t], U[2 * L.plane + t], U[3 * L.plane + t], g, u, v, p, T);
+  Q[t] = r;
+  Q[L.plane + t] = u;
+  Q[2 * L.plane + t] = v;
+  Q[3 * L.plane + t] = p;
+}
+
+template <class T>
+__global__ void nn_image_kernel(NnArgs n, const double* __restrict__ Q, long long qplane) {
+  const int d = blockIdx.y;
+  const int Wd = n.W[d];
+  const long long pix = (long long)n.H[d] * Wd;
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= pix) return;
+  const int h = (int)(p / Wd), f = (int)(p % Wd);
+  double wl[4], wr[4];
+  face_states(n.lay, Q, qplane, d, h, f, wl, wr);
+  const int un = (d == 0) ? 1 : 2, ut = (d == 0) ? 2 : 1;
+  double m[4];
+  {
+    const double rL = wl[0], rR = wr[0];
+    const double EL = fma(0.5 * rL, fma(wl[un], wl[un], wl[ut] * wl[ut]), wl[3] * n.g1);
+    const double ER = fma(0.5 * rR, fma(wr[un], wr[un], wr[ut] * wr[ut]), wr[3] * n.g1);
+    m[0] = 0.5 * (rL + rR);
+    m[1] = 0.5 * fma(rL, wl[un], rR * wr[un]);
+    m[2] = 0.5 * fma(rL, wl[ut], rR * wr[ut]);
+    m[3] = 0.5 * (EL + ER);
+  }
+  T* X = chan_img<T>(n.X, 4, d, n.pix0);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) X[k * pix + p] = (T)((m[k] - n.mean[k]) * n.inv_sd[k]);
+}
+
+// one 3x3 layer on a 16x16 pixel tile per block; ACT 0: ReLU, 1: tanh
+template <class T, int CIN, int COUT, int ACT>
+__global__ void __launch_bounds__(NTHR) nn_conv_kernel(NnArgs n, const void* in, void* out, int woff) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int NW = COUT * CIN * 9 + COUT;
+  T* sw = reinterpret_cast<T*>(smem_raw);
+  T* sx = sw + ((NW + 1) & ~1);
+  const int d = blockIdx.z;
+  const int H = n.H[d], Wd = n.W[d];
+  const int x0 = blockIdx.x * TILE, y0 = blockIdx.y * TILE;
+  if (x0 >= Wd || y0 >= H) return;  // the grid covers the larger image
+  const long long pix = (long long)H * Wd;
+  const T* X = chan_img<T>(in, CIN, d, n.pix0);
+  T* Y = chan_img<T>(out, COUT, d, n.pix0);
+  for (int k = threadIdx.x; k < NW; k += NTHR) sw[k] = (T)n.w[woff + k];
+  for (int k = threadIdx.x; k < CIN * TH * TH; k += NTHR) {
+    const int ci = k / (TH * TH), r = k % (TH * TH);
+    const int gy = y0 + r / TH - 1, gx = x0 + r % TH - 1;
+    sx[k] = (gy >= 0 && gy < H && gx >= 0 && gx < Wd) ? X[ci * pix + (long long)gy * Wd + gx] : (T)0;
+  }
+  __syncthreads();
+  const int tx = threadIdx.x % TILE, ty = threadIdx.x / TILE;
+  T acc[COUT];
+#pragma unroll
+  for (int co = 0; co < COUT; ++co) acc[co] = sw[COUT * CIN * 9 + co];
+  for (int ci = 0; ci < CIN; ++ci)
+#pragma unroll
+    for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+      for (int kx = 0; kx < 3; ++kx) {
+        const T v = sx[ci * TH * TH + (ty + ky) * TH + tx + kx];
+#pragma unroll
+        for (int co = 0; co < COUT; ++co) acc[co] = fma(sw[((co * CIN + ci) * 3 + ky) * 3 + kx], v, acc[co]);
+      }
+  const int gx = x0 + tx, gy = y0 + ty;
+  if (gx < Wd && gy < H) {
+    const long long o = (long long)gy * Wd + gx;
+#pragma unroll
+    for (int co = 0; co < COUT; ++co) Y[co * pix + o] = (ACT == 0) ? (acc[co] > (T)0 ? acc[co] : (T)0) : act_tanh(acc[co]);
+  }
+}
+
+// stage output (or RHS) minus the neural flux divergence on fluid cells
+template <class T>
+__global__ void nn_apply_kernel(NnArgs n, StageArgs a, int rhs) {
+  const Lay& L = a.lay;
+  const long long ncell = (long long)L.nx * L.ny;
+  const long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= ncell) return;
+  const int i = (int)(o % L.nx), j = (int)(o / L.nx);
+  if (a.tag && a.tag[o] != 0) return;
+  const T* Fx = chan_img<T>(n.T3, 4, 0, n.pix0);
+  const long long px = (long long)n.H[0] * n.W[0];
+  const T* Fy = chan_img<T>(n.T3, 4, 1, n.pix0);
+  const long long py = (n.nimg > 1) ? (long long)n.H[1] * n.W[1] : 0;
+  const double fac = (!rhs && a.use_un) ? a.rk_b : 1.0;
+  const int ky_of[4] = {0, 2, 1, 3};  // frame channel of each conserved component, y faces
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const long long ox = (long long)j * n.W[0] + i;
+    double corr = a.cx * (n.scale[c] * ((double)Fx[c * px + ox + 1] - (double)Fx[c * px + ox]));
+    if (n.nimg > 1) {
+      const int k = ky_of[c];
+      const long long oy = (long long)i * n.W[1] + j;
+      corr = fma(a.cy, n.scale[k] * ((double)Fy[k * py + oy + 1] - (double)Fy[k * py + oy]), corr);
+    }
+    if (rhs) a.Uout[c * ncell + o] -= corr;
+    else a.Uout[c * L.plane + L.idx(i, j)] -= fac * corr;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// reverse
+// ---------------------------------------------------------------------------------------
+// dZ3 = (face-flux adjoint in the frame) * scale * (1 - t^2)
+template <class T>
+__global__ void nn_seed_kernel(NnArgs n, AdjArgs a) {
+  const int d = blockIdx.y;
+  const int Wd = n.W[d];
+  const long long pix = (long long)n.H[d] * Wd;
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= pix) return;
+  const int h = (int)(p / Wd), f = (int)(p % Wd);
+  const Lay& L = a.lay;
+  const long long ca = (d == 0) ? L.idx(f - 1, h) : L.idx(h, f - 1);
+  const long long cb = (d == 0) ? L.idx(f, h) : L.idx(h, f);
+  const double invh = (d == 0) ? a.inv_dx : a.inv_dy;
+  const T* t3 = chan_img<T>(n.T3, 4, d, n.pix0);
+  T* g = chan_img<T>(n.G4, 4, d, n.pix0);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int c = (d == 0) ? k : (k == 1 ? 2 : (k == 2 ? 1 : k));
+    const double Fb = (a.lam[c * L.plane + cb] - a.lam[c * L.plane + ca]) * invh;
+    const double t = (double)t3[k * pix + p];
+    g[k * pix + p] = (T)(Fb * n.scale[k] * (1.0 - t * t));
+  }
+}
+
+// data gradient of one layer: gin[ci] = sum_co,ky,kx w[co][ci][ky][kx] gout[co][h-ky+1][x-kx+1],
+// times the ReLU mask of the layer below when MASK
+template <class T, int CIN, int COUT, bool MASK>
+__global__ void __launch_bounds__(NTHR) nn_dgrad_kernel(NnArgs n, const void* gout, const void* aprev, void* gin,
+                                                        int woff) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int NWW = COUT * CIN * 9;
+  T* sw = reinterpret_cast<T*>(smem_raw);
+  T* sg = sw + ((NWW + 1) & ~1);
+  const int d = blockIdx.z;
+  const int H = n.H[d], Wd = n.W[d];
+  const int x0 = blockIdx.x * TILE, y0 = blockIdx.y * TILE;
+  if (x0 >= Wd || y0 >= H) return;
+  const long long pix = (long long)H * Wd;
+  const T* G = chan_img<T>(gout, COUT, d, n.pix0);
+  T* D = chan_img<T>(gin, CIN, d, n.pix0);
+  for (int k = threadIdx.x; k < NWW; k += NTHR) sw[k] = (T)n.w[woff + k];
+  for (int k = threadIdx.x; k < COUT * TH * TH; k += NTHR) {
+    const int co = k / (TH * TH), r = k % (TH * TH);
+    const int gy = y0 + r / TH - 1, gx = x0 + r % TH - 1;
+    sg[k] = (gy >= 0 && gy < H && gx >= 0 && gx < Wd) ? G[co * pix + (long long)gy * Wd + gx] : (T)0;
+  }
+  __syncthreads();
+  const int tx = threadIdx.x % TILE, ty = threadIdx.x / TILE;
+  T acc[CIN];
+#pragma unroll
+  for (int ci = 0; ci < CIN; ++ci) acc[ci] = (T)0;
+  for (int co = 0; co < COUT; ++co)
+#pragma unroll
+    for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+      for (int kx = 0; kx < 3; ++kx) {
+        const T v = sg[co * TH * TH + (ty - ky + 2) * TH + tx - kx + 2];
+#pragma unroll
+        for (int ci = 0; ci < CIN; ++ci) acc[ci] = fma(sw[((co * CIN + ci) * 3 + ky) * 3 + kx], v, acc[ci]);
+      }
+  const int gx = x0 + tx, gy = y0 + ty;
+  if (gx < Wd && gy < H) {
+    const long long o = (long long)gy * Wd + gx;
+    const T* A = MASK ? chan_img<T>(aprev, CIN, d, n.pix0) : nullptr;
+#pragma unroll
+    for (int ci = 0; ci < CIN; ++ci) {
+      T v = acc[ci];
+      if (MASK && !(A[ci * pix + o] > (T)0)) v = (T)0;
+      D[ci * pix + o] = v;
+    }
+  }
+}
+
+// weight gradient of one layer: blocks stride over the tiles of both images and keep
+// per-thread sums of the weights they own; each block writes its sums to partial[block]
+template <class T, int CIN, int COUT>
+__global__ void __launch_bounds__(NTHR) nn_wgrad_kernel(NnArgs n, const void* gout, const void* ain, int woff) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int NW = COUT * CIN * 9 + COUT;
+  constexpr int PER = (NW + NTHR - 1) / NTHR;
+  T* sg = reinterpret_cast<T*>(smem_raw);  // [COUT][256]
+  T* sa = sg + COUT * NTHR;                // [CIN][18][18]
+  T acc[PER];
+#pragma unroll
+  for (int r = 0; r < PER; ++r) acc[r] = (T)0;
+  int ntx[2], nty[2];
+  for (int d = 0; d < 2; ++d) {
+    ntx[d] = (d < n.nimg) ? (n.W[d] + TILE - 1) / TILE : 0;
+    nty[d] = (d < n.nimg) ? (n.H[d] + TILE - 1) / TILE : 0;
+  }
+  const int t0 = ntx[0] * nty[0], total = t0 + ntx[1] * nty[1];
+  for (int t = blockIdx.x; t < total; t += gridDim.x) {
+    const int d = (t < t0) ? 0 : 1;
+    const int tl = (d == 0) ? t : t - t0;
+    const int x0 = (tl % ntx[d]) * TILE, y0 = (tl / ntx[d]) * TILE;
+    const int H = n.H[d], Wd = n.W[d];
+    const long long pix = (long long)H * Wd;
+    const T* G = chan_img<T>(gout, COUT, d, n.pix0);
+    const T* A = chan_img<T>(ain, CIN, d, n.pix0);
+    __syncthreads();
+    for (int k = threadIdx.x; k < COUT * NTHR; k += NTHR) {
+      const int co = k / NTHR, r = k % NTHR;
+      const int gy = y0 + r / TILE, gx = x0 + r % TILE;
+      sg[k] = (gy < H && gx < Wd) ? G[co * pix + (long long)gy * Wd + gx] : (T)0;
+    }
+    for (int k = threadIdx.x; k < CIN * TH * TH; k += NTHR) {
+      const int ci = k / (TH * TH), r = k % (TH * TH);
+      const int gy = y0 + r / TH - 1, gx = x0 + r % TH - 1;
+      sa[k] = (gy >= 0 && gy < H && gx >= 0 && gx < Wd) ? A[ci * pix + (long long)gy * Wd + gx] : (T)0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+      const int k = threadIdx.x + r * NTHR;
+      if (k >= NW) continue;
+      T s = (T)0;
+      if (k < COUT * CIN * 9) {
+        const int co = k / (CIN * 9), rem = k % (CIN * 9);
+        const int ci = rem / 9, ky = (rem % 9) / 3, kx = rem % 3;
+        const T* g = sg + co * NTHR;
+        const T* a = sa + ci * TH * TH + ky * TH + kx;
+        for (int py = 0; py < TILE; ++py)
+#pragma unroll
+          for (int px = 0; px < TILE; ++px) s = fma(g[py * TILE + px], a[py * TH + px], s);
+      } else {
+        const T* g = sg + (k - COUT * CIN * 9) * NTHR;
+        for (int q = 0; q < NTHR; ++q) s += g[q];
+      }
+      acc[r] += s;
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < PER; ++r) {
+    const int k = threadIdx.x + r * NTHR;
+    if (k < NW) n.partial[(long long)blockIdx.x * NN_NPARAM + woff + k] = (double)acc[r];
+  }
+}
+
+__global__ void nn_wreduce_kernel(NnArgs n) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= NN_NPARAM) return;
+  double s = 0.0;
+  for (int b = 0; b < n.nwblk; ++b) s += n.partial[(long long)b * NN_NPARAM + k];
+  n.w_bar[k] += s;
+}
+
+__device__ __forceinline__ double nn_warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// image reverse: network-input adjoint -> WENO face-state adjoints (added to a.fadj) and
+// d/dgamma of the face energies (added to pbar[0])
+template <class T>
+__global__ void nn_image_vjp_kernel(NnArgs n, AdjArgs a) {
+  const int d = blockIdx.y;
+  const int Wd = n.W[d];
+  const long long pix = (long long)n.H[d] * Wd;
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double gbar = 0.0;
+  if (p < pix) {
+    const int h = (int)(p / Wd), f = (int)(p % Wd);
+    double wl[4], wr[4];
+    face_states(a.lay, a.Q, a.lay.plane, d, h, f, wl, wr);
+    const T* dX = chan_img<T>(n.G4, 4, d, n.pix0);
+    double gk[4];  // adjoint of each side's conserved frame state (the image is their mean)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) gk[k] = 0.5 * n.inv_sd[k] * (double)dX[k * pix + p];
+    const int un = (d == 0) ? 1 : 2, ut = (d == 0) ? 2 : 1;
+    const int fdir = d * 8;
+    const long long si = (d == 0) ? (long long)(f + 3) * a.tpitch + (h + a.lay.gy) : a.lay.idx(h, f);
+    for (int s = 0; s < 2; ++s) {
+      const double* w = (s == 0) ? wl : wr;
+      const double r = w[0], vn = w[un], vt = w[ut], pr = w[3];
+      double b[4];
+      b[0] = fma(0.5 * fma(vn, vn, vt * vt), gk[3], fma(vn, gk[1], fma(vt, gk[2], gk[0])));
+      b[un] = r * fma(vn, gk[3], gk[1]);
+      b[ut] = r * fma(vt, gk[3], gk[2]);
+      b[3] = gk[3] * n.g1;
+      gbar -= pr * n.g1 * n.g1 * gk[3];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) a.fadj[(long long)(fdir + 4 * s + c) * a.splane + si] += b[c];
+    }
+  }
+  gbar = nn_warp_sum(gbar);
+  if (a.pbar && (threadIdx.x & 31) == 0 && gbar != 0.0) atomicAdd(a.pbar, gbar);
+}
+
+// ---------------------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------------------
+unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
+
+long long max_pix(const NnArgs& n) {
+  long long m = (long long)n.H[0] * n.W[0];
+  if (n.nimg > 1 && (long long)n.H[1] * n.W[1] > m) m = (long long)n.H[1] * n.W[1];
+  return m;
+}
+
+dim3 tile_grid(const NnArgs& n) {
+  int W = n.W[0], H = n.H[0];
+  if (n.nimg > 1) {
+    W = W > n.W[1] ? W : n.W[1];
+    H = H > n.H[1] ? H : n.H[1];
+  }
+  return dim3(cdiv(W, TILE), cdiv(H, TILE), n.nimg);
+}
+
+template <class T, int CIN, int COUT, int ACT>
+cudaError_t conv(const NnArgs& n, const void* in, void* out, int woff, cudaStream_t s) {
+  constexpr int NW = COUT * CIN * 9 + COUT;
+  const size_t sm = sizeof(T) * (((NW + 1) & ~1) + CIN * TH * TH);
+  auto k = nn_conv_kernel<T, CIN, COUT, ACT>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k<<<tile_grid(n), NTHR, sm, s>>>(n, in, out, woff);
+  return cudaGetLastError();
+}
+
+template <class T, int CIN, int COUT, bool MASK>
+cudaError_t dgrad(const NnArgs& n, const void* gout, const void* aprev, void* gin, int woff, cudaStream_t s) {
+  constexpr int NWW = COUT * CIN * 9;
+  const size_t sm = sizeof(T) * (((NWW + 1) & ~1) + COUT * TH * TH);
+  auto k = nn_dgrad_kernel<T, CIN, COUT, MASK>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k<<<tile_grid(n), NTHR, sm, s>>>(n, gout, aprev, gin, woff);
+  return cudaGetLastError();
+}
+
+template <class T, int CIN, int COUT>
+cudaError_t wgrad(const NnArgs& n, const void* gout, const void* ain, int woff, cudaStream_t s) {
+  const size_t sm = sizeof(T) * (COUT * NTHR + CIN * TH * TH);
+  auto k = nn_wgrad_kernel<T, CIN, COUT>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k<<<n.nwblk, NTHR, sm, s>>>(n, gout, ain, woff);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t forward_t(const NnArgs& n, const double* Q, long long qplane, cudaStream_t s) {
+  nn_image_kernel<T><<<dim3(cdiv(max_pix(n), 256), n.nimg), 256, 0, s>>>(n, Q, qplane);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if ((e = conv<T, 4, 16, 0>(n, n.X, n.A1, NN_OFF1, s)) != cudaSuccess) return e;
+  if ((e = conv<T, 16, 32, 0>(n, n.A1, n.A2, NN_OFF2, s)) != cudaSuccess) return e;
+  return conv<T, 32, 4, 1>(n, n.A2, n.T3, NN_OFF3, s);
+}
+
+template <class T>
+cudaError_t reverse_t(const NnArgs& n, const AdjArgs& a, cudaStream_t s) {
+  cudaError_t e = forward_t<T>(n, a.Q, a.lay.plane, s);
+  if (e != cudaSuccess) return e;
+  const dim3 pg(cdiv(max_pix(n), 256), n.nimg);
+  nn_seed_kernel<T><<<pg, 256, 0, s>>>(n, a);                                   // G4 = dZ3
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = dgrad<T, 32, 4, true>(n, n.G4, n.A2, n.G32, NN_OFF3, s)) != cudaSuccess) return e;   // G32 = dZ2
+  if (n.w_bar && (e = wgrad<T, 32, 4>(n, n.G4, n.A2, NN_OFF3, s)) != cudaSuccess) return e;
+  if ((e = dgrad<T, 16, 32, true>(n, n.G32, n.A1, n.G16, NN_OFF2, s)) != cudaSuccess) return e;  // G16 = dZ1
+  if (n.w_bar && (e = wgrad<T, 16, 32>(n, n.G32, n.A1, NN_OFF2, s)) != cudaSuccess) return e;
+  if ((e = dgrad<T, 4, 16, false>(n, n.G16, nullptr, n.G4, NN_OFF1, s)) != cudaSuccess) return e;  // G4 = dX
+  if (n.w_bar) {
+    if ((e = wgrad<T, 4, 16>(n, n.G16, n.X, NN_OFF1, s)) != cudaSuccess) return e;
+    nn_wreduce_kernel<<<cdiv(NN_NPARAM, 256), 256, 0, s>>>(n);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  nn_image_vjp_kernel<T><<<pg, 256, 0, s>>>(n, a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t nn_prims(const double* U, double* Q, const Lay& lay, double gamma, cudaStream_t s) {
+  nn_prims_kernel<<<cdiv(lay.plane, 256), 256, 0, s>>>(U, Q, lay, Gas{gamma, gamma - 1.0, 1.0 / (gamma - 1.0)});
+  return cudaGetLastError();
+}
+
+cudaError_t nn_forward(const NnArgs& n, const double* Q, long long qplane, cudaStream_t s) {
+  return n.fp32 ? forward_t<float>(n, Q, qplane, s) : forward_t<double>(n, Q, qplane, s);
+}
+
+cudaError_t nn_apply(const NnArgs& n, const StageArgs& a, bool rhs, cudaStream_t s) {
+  const long long ncell = (long long)a.lay.nx * a.lay.ny;
+  if (n.fp32) nn_apply_kernel<float><<<cdiv(ncell, 256), 256, 0, s>>>(n, a, rhs ? 1 : 0);
+  else nn_apply_kernel<double><<<cdiv(ncell, 256), 256, 0, s>>>(n, a, rhs ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t nn_reverse(const NnArgs& n, const AdjArgs& a, cudaStream_t s) {
+  return n.fp32 ? reverse_t<float>(n, a, s) : reverse_t<double>(n, a, s);
+}
+
+}  // namespace js

@@ -1,0 +1,168 @@
+"""The neural flux (Sec. 2.3) through the CUDA path against the oracle.
+
+FP64 network arithmetic: RHS and steps equal the oracle within the FP64 bar (1e-10
+normwise); the reverse calls (js_rhs_vjp, js_step_vjp, taped) pass dot-product tests against
+the oracle's forward-mode tangent in the state, the solver parameters and the network
+weights at once.  FP32 network arithmetic: the neural part of the RHS within 1e-4 of its
+size (FP32 dot products of up to 289 terms, three layers: rounding of order 1e-6 relative,
+1e-4 leaves room for the tanh and the face-difference cancellation), the gradient within
+the same relative bound."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2601_04400_gb300 import workloads as W
+from jsutil import normwise_err, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+NP = 6388
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2601_04400_gb300 import binding as B
+    B.lib()
+    return torch, B
+
+
+def _params(seed, amp=0.12):
+    return np.random.default_rng(seed).standard_normal(NP) * amp
+
+
+def _norm(prob, U, scale=0.2):
+    r, mx, my, E = U
+    m = np.concatenate([mx.ravel(), my.ravel()])
+    mean = [r.mean(), m.mean(), 0.0, E.mean()]
+    sd = [r.std() + 1e-3, m.std() + 1e-3, m.std() + 1e-3, E.std() + 1e-3]
+    return np.concatenate([mean, sd, np.full(4, scale)])
+
+
+def _cases():
+    p = W.random_periodic(40, 33, seed=1, mu=3e-3, nu=1e-3)
+    yield "ns_av_periodic_40x33", p, O.prim_to_cons(p, p.W0)
+    p = W.shock_cylinder(nx=70, ny=45, Lx=3.5, Ly=2.25, centre=(1.6, 1.1), radius=0.45, x_shock=0.8, viscous=False)
+    yield "euler_cylinder_70x45", p, O.prim_to_cons(p, W.random_state(p, seed=2, amp=0.02))
+    p = W.sod(120)
+    yield "sod120", p, O.prim_to_cons(p, W.random_state(p, seed=3, amp=0.02))
+
+
+CASES = list(_cases())
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: c[0])
+def test_fp64_network_matches_oracle(env, case):
+    torch, B = env
+    _, prob, U = case
+    w, norm = _params(4), _norm(prob, U)
+    s = B.Solver.from_problem(prob)
+    wd = torch.tensor(w, device="cuda")
+    s.set_neural(wd, norm)
+    with O.neural(w, norm):
+        L_ref = O.rhs(prob, U)
+        dt = 0.4 * O.max_dt(prob, U, 0.5)
+        S_ref = O.step(prob, U, [dt] * 3)
+    L0 = O.rhs(prob, U)
+    assert np.abs(L_ref - L0).max() > 1e-3 * np.abs(L0).max()  # the network changes the RHS
+    assert normwise_err(to_host(s.rhs(to_dev(U))), L_ref) < TOL
+    Ud = to_dev(U)
+    s.step(Ud, dt, 3)
+    assert normwise_err(to_host(Ud), S_ref) < TOL
+    assert s.status() == 0
+
+
+@pytest.mark.parametrize("case", CASES[:2], ids=lambda c: c[0])
+def test_fp32_network_within_fp32_bound(env, case):
+    torch, B = env
+    _, prob, U = case
+    w, norm = _params(5), _norm(prob, U)
+    s = B.Solver.from_problem(prob)
+    s.set_neural(torch.tensor(w, device="cuda"), norm, fp32=True)
+    with O.neural(w, norm):
+        L_ref = O.rhs(prob, U)
+    part = np.abs(L_ref - O.rhs(prob, U)).max()
+    err = np.abs(to_host(s.rhs(to_dev(U))) - L_ref).max()
+    assert err <= 1e-4 * part + TOL * np.abs(L_ref).max()
+
+
+def _dot_test(torch, B, prob, U, fp32, taped=False, rhs=False):
+    rng = np.random.default_rng(7)
+    w, norm = _params(6), _norm(prob, U)
+    dw = rng.standard_normal(NP)
+    th = O.theta_of(prob)
+    dth = np.zeros_like(th)
+    dth[0] = 0.3
+    if prob.mu > 0:
+        dth[1] = 1e-3
+    dU = rng.standard_normal(U.shape) * 1e-3 * np.abs(U).max(axis=(1, 2), keepdims=True)
+    lam = rng.standard_normal(U.shape)
+    dt = 0.3 * O.max_dt(prob, U, 0.5)
+    with O.neural(w, norm, dw=dw):
+        if rhs:
+            _, Jv = O.rhs_tangent(prob, U, dU, dth)
+        else:
+            _, Jv = O.step_tangent(prob, U, dU, dth, [dt])
+    s = B.Solver.from_problem(prob)
+    wb = torch.zeros(NP, dtype=torch.float64, device="cuda")
+    s.set_neural(torch.tensor(w, device="cuda"), norm, w_bar=wb, fp32=fp32)
+    if rhs:
+        Ub, pb = s.rhs_vjp(to_dev(U), to_dev(lam))
+    elif taped:
+        s.tape_reserve(1, weno=True)
+        s.step_taped(to_dev(U), dt, 0)
+        Ub, pb = s.step_vjp_taped(0, dt, to_dev(lam))
+    else:
+        Ub, pb = s.step_vjp(to_dev(U), dt, to_dev(lam))
+    assert s.status() == 0
+    lhs = np.dot(lam.ravel(), Jv.ravel())
+    parts = (np.dot(to_host(Ub).ravel(), dU.ravel()), np.dot(to_host(pb), dth), np.dot(to_host(wb), dw))
+    return lhs, parts, np.abs(lam).sum() * np.abs(Jv).max(), to_host(wb)
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: c[0])
+@pytest.mark.parametrize("mode", ["rhs", "step", "taped"])
+def test_fp64_reverse_dot_products(env, case, mode):
+    torch, B = env
+    _, prob, U = case
+    lhs, parts, scale, wb = _dot_test(torch, B, prob, U, False, taped=(mode == "taped"), rhs=(mode == "rhs"))
+    assert abs(parts[2]) > 1e-3 * abs(lhs)  # the weight gradient carries part of the product
+    assert abs(lhs - sum(parts)) <= 1e-11 * scale, (lhs, parts)
+
+
+@pytest.mark.parametrize("case", CASES[:2], ids=lambda c: c[0])
+def test_fp32_reverse_within_fp32_bound(env, case):
+    torch, B = env
+    _, prob, U = case
+    lhs, parts, scale, _ = _dot_test(torch, B, prob, U, True)
+    assert abs(lhs - sum(parts)) <= 1e-4 * (abs(parts[2]) + abs(parts[0])) + 1e-11 * scale, (lhs, parts)
+
+
+def test_weight_gradient_accumulates_and_paths_agree(env):
+    torch, B = env
+    _, prob, U = CASES[1]
+    w, norm = _params(8), _norm(prob, U)
+    lam = np.random.default_rng(9).standard_normal(U.shape)
+    dt = 0.3 * O.max_dt(prob, U, 0.5)
+    s = B.Solver.from_problem(prob)
+    wb = torch.zeros(NP, dtype=torch.float64, device="cuda")
+    s.set_neural(torch.tensor(w, device="cuda"), norm, w_bar=wb)
+    l1, _ = s.step_vjp(to_dev(U), dt, to_dev(lam))
+    g1 = wb.clone()
+    l2, _ = s.step_vjp(to_dev(U), dt, to_dev(lam))
+    assert torch.allclose(wb, 2 * g1, rtol=1e-13, atol=0)
+    # the reverse of a taped step (with and without WENO internals) equals the recomputing one
+    for weno in (False, True):
+        wb.zero_()
+        s.tape_reserve(1, weno=weno)
+        s.step_taped(to_dev(U), dt, 0)
+        lt, _ = s.step_vjp_taped(0, dt, to_dev(lam))
+        assert np.abs(to_host(lt) - to_host(l1)).max() <= 1e-12 * np.abs(to_host(l1)).max()
+        assert torch.allclose(wb, g1, rtol=1e-12, atol=1e-14 * float(g1.abs().max()))
+    s.set_neural(None)
+    Ud, Ur = to_dev(U), to_dev(U)
+    s.step(Ud, dt, 1)
+    assert normwise_err(to_host(Ud), O.step(prob, U, [dt])) < TOL  # off again
