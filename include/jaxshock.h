@@ -159,6 +159,12 @@ int js_step_vjp_taped(js_ctx* ctx, int slot, double dt, const double* lam_np1, d
 #define JS_NN_F32 1
 int js_set_neural(js_ctx* ctx, const double* w, double* w_bar, const double* norm, int precision);
 
+/* Block average (the downsampling that turns high-resolution states into the coarse
+ * training targets of Sec. 2.4): out[4][ny/fy][nx/fx] (device) = the means of the fx x fy
+ * cell blocks of U[4][ny][nx] (device).  nx % fx == 0 and ny % fy == 0 or JS_ERR_ARG.
+ * Asynchronous on `stream` (a cudaStream_t, NULL = default stream); no context needed. */
+int js_block_average(const double* U, int nx, int ny, int fx, int fy, double* out, void* stream);
+
 /* Read and clear the device error flag; synchronises the stream.  Returns JS_OK,
  * JS_ERR_NONPHYSICAL or JS_ERR_TIMEOUT (or JS_ERR_CUDA if the stream itself failed). */
 int js_sync_status(js_ctx* ctx);

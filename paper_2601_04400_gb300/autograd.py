@@ -13,6 +13,10 @@ theta is the 20-entry parameter vector of the library (gamma, mu, Pr, nu, then t
 state rho, u, v, p of the x-low, x-high, y-low and y-high sides); its gradient is returned
 for gamma, for mu and Pr when mu > 0, for nu when nu > 0 and for the inflow states of inflow
 sides (the other entries receive zero).
+
+With `weights` (the 6388 parameters of the neural flux of Sec. 2.3) the steps include the
+neural flux and the backward pass also returns the weights' gradient (the per-step chain
+rule of Sec. 2.4 through every unrolled step).
 """
 import math
 
@@ -38,8 +42,15 @@ def _apply_theta(solver, theta):
 
 class _Rollout(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, U0, theta, solver, dts, outputs, every, internals):
+    def forward(ctx, U0, theta, weights, solver, dts, outputs, every, internals, nn_cfg):
         _apply_theta(solver, theta)
+        ctx.nn = None
+        if weights is not None:
+            # a private copy: the library reads the parameters at every stage, also when the
+            # backward pass re-runs the segments
+            w = weights.detach().to(U0.device, torch.float64).contiguous().clone()
+            solver.set_neural(w, nn_cfg["norm"], fp32=nn_cfg.get("fp32", False))
+            ctx.nn = (w, nn_cfg)
         n = len(dts)
         want = {k: i for i, k in enumerate(outputs)}
         U = U0.detach().clone().contiguous()
@@ -55,6 +66,7 @@ class _Rollout(torch.autograd.Function):
                 outs[want[k + 1]] = U.clone()
         ctx.solver, ctx.dts, ctx.outputs, ctx.every = solver, list(dts), list(outputs), every
         ctx.internals = internals
+        ctx.w_device = None if weights is None else weights.device
         ctx.ckpts = ckpts
         ctx.theta = theta.detach().clone()
         return torch.stack(outs)
@@ -71,6 +83,11 @@ class _Rollout(torch.autograd.Function):
         if n in inject:
             lam += inject[n]
         pbar = torch.zeros(B.JS_NPARAM, dtype=torch.float64, device=g.device)
+        wbar = None
+        if ctx.nn is not None:
+            w, cfg = ctx.nn
+            wbar = torch.zeros_like(w)
+            solver.set_neural(w, cfg["norm"], w_bar=wbar, fp32=cfg.get("fp32", False))
         scratch = torch.empty_like(lam)
         weno = ctx.internals
         if weno is None:
@@ -90,12 +107,16 @@ class _Rollout(torch.autograd.Function):
                 if k in inject:
                     lam = lam + inject[k]
         st = solver.status()
+        if ctx.nn is not None:
+            solver.set_neural(ctx.nn[0], ctx.nn[1]["norm"], fp32=ctx.nn[1].get("fp32", False))
         if st != 0:
             raise B.JsError(st, "rollout backward")
-        return lam, pbar.to(ctx.theta.device), None, None, None, None, None
+        gw = None if wbar is None else wbar.to(ctx.w_device)
+        return lam, pbar.to(ctx.theta.device), gw, None, None, None, None, None, None
 
 
-def rollout(solver, U0, theta, dts, outputs=None, checkpoint_every=None, tape_internals=None):
+def rollout(solver, U0, theta, dts, outputs=None, checkpoint_every=None, tape_internals=None, weights=None,
+            norm=None, fp32=False):
     """Differentiable rollout.
 
     solver: binding.Solver; U0: float64 CUDA tensor [4, ny, nx]; theta: float64 tensor [20]
@@ -103,10 +124,16 @@ def rollout(solver, U0, theta, dts, outputs=None, checkpoint_every=None, tape_in
     whose states are returned stacked (default: only the final state, index len(dts)).
     tape_internals: record the WENO5 internals on the tape (True / False; None decides by
     free device memory).  The gradient is the same either way.
+    weights: float64 tensor [6388] of neural-flux parameters (Sec. 2.3) or None; norm: its
+    input normalisation and output scale (mean[4], sd[4], scale[4]); fp32: FP32 network
+    arithmetic.  The solver keeps the neural flux switched on after the call.
     Returns a tensor [len(outputs), 4, ny, nx] (or [4, ny, nx] for the default)."""
     n = len(dts)
     default = outputs is None
     outputs = [n] if default else list(outputs)
     every = checkpoint_every or max(1, int(math.ceil(math.sqrt(max(n, 1)))))
-    out = _Rollout.apply(U0, theta, solver, list(dts), outputs, every, tape_internals)
+    if weights is not None and norm is None:
+        raise ValueError("the neural flux needs its normalisation (norm)")
+    cfg = None if weights is None else {"norm": norm, "fp32": bool(fp32)}
+    out = _Rollout.apply(U0, theta, weights, solver, list(dts), outputs, every, tape_internals, cfg)
     return out[0] if default else out

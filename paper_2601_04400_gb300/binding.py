@@ -63,6 +63,7 @@ SIGNATURES = {
     "js_tape_reserve": (_I, [_P, _I]),
     "js_tape_reserve_ex": (_I, [_P, _I, _I]),
     "js_set_neural": (_I, [_P, _P, _P, _P, _I]),
+    "js_block_average": (_I, [_P, _I, _I, _I, _I, _P, _P]),
     "js_step_taped": (_I, [_P, _P, _D, _I]),
     "js_step_vjp_taped": (_I, [_P, _I, _D, _P, _P, _P]),
     "js_set_tuning": (_I, [_P, _I]),
@@ -442,3 +443,15 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def block_average(U, fx, fy=1, stream=None):
+    """Means of fx x fy cell blocks of a float64 CUDA state [4, ny, nx] (js_block_average)."""
+    import torch
+    U = U.contiguous()
+    ny, nx = U.shape[1], U.shape[2]
+    out = torch.empty((4, ny // fy, nx // fx), dtype=torch.float64, device=U.device)
+    _check(lib().js_block_average(_ptr(U), nx, ny, int(fx), int(fy), _ptr(out), _stream_ptr(stream)),
+           "js_block_average")
+    return out
+

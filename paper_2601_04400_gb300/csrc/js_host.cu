@@ -503,6 +503,12 @@ int js_set_neural(js_ctx* c, const double* w, double* w_bar, const double* norm,
   return JS_OK;
 }
 
+int js_block_average(const double* U, int nx, int ny, int fx, int fy, double* out, void* stream) {
+  if (!U || !out || nx < 1 || ny < 1 || fx < 1 || fy < 1 || nx % fx != 0 || ny % fy != 0) return JS_ERR_ARG;
+  JS_CUDA(js::launch_block_average(U, nx, ny, fx, fy, out, static_cast<cudaStream_t>(stream)));
+  return JS_OK;
+}
+
 int js_set_params(js_ctx* c, const js_params* params, const js_boundary* bc) {
   if (!c || !params_valid(params, bc)) return JS_ERR_ARG;
   c->p = *params;

@@ -112,6 +112,8 @@ cudaError_t nn_apply(const NnArgs& n, const StageArgs& a, bool rhs, cudaStream_t
 // reverse: recompute the network on a.Q, seed with the face-flux adjoints of a.lam, back-
 // propagate (parameter gradient into n.w_bar), add the face-state adjoints to a.fadj
 cudaError_t nn_reverse(const NnArgs& n, const AdjArgs& a, cudaStream_t s);
+// out[4][ny/fy][nx/fx] = means of fx x fy blocks of U[4][ny][nx]
+cudaError_t launch_block_average(const double* U, int nx, int ny, int fx, int fy, double* out, cudaStream_t s);
 
 // nn: the neural flux's reverse (run between pass 1 and pass 2) or nullptr
 cudaError_t launch_adj_stage(const AdjArgs& a, const BcArgs& bc, const IbArgs& ib, const IbTArgs& ibt, int wall,

@@ -478,4 +478,32 @@ cudaError_t nn_reverse(const NnArgs& n, const AdjArgs& a, cudaStream_t s) {
   return n.fp32 ? reverse_t<float>(n, a, s) : reverse_t<double>(n, a, s);
 }
 
+// ---------------------------------------------------------------------------------------
+// block averaging of a state (the downsampling d(U) that makes the training targets of
+// Sec. 2.4 from high-resolution runs)
+// ---------------------------------------------------------------------------------------
+namespace {
+__global__ void block_average_kernel(const double* __restrict__ U, int nx, int ny, int fx, int fy,
+                                     double* __restrict__ out) {
+  const int cx = nx / fx, cy = ny / fy;
+  const long long n = (long long)cx * cy;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 4 * n) return;
+  const int c = (int)(t / n);
+  const long long o = t % n;
+  const int i = (int)(o % cx), j = (int)(o / cx);
+  const double* u = U + (long long)c * nx * ny;
+  double s = 0.0;
+  for (int b = 0; b < fy; ++b)
+    for (int a = 0; a < fx; ++a) s += u[(long long)(j * fy + b) * nx + i * fx + a];
+  out[t] = s / (double)(fx * fy);
+}
+}  // namespace
+
+cudaError_t launch_block_average(const double* U, int nx, int ny, int fx, int fy, double* out, cudaStream_t s) {
+  const long long n = 4LL * (nx / fx) * (ny / fy);
+  block_average_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(U, nx, ny, fx, fy, out);
+  return cudaGetLastError();
+}
+
 }  // namespace js
