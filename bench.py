@@ -30,6 +30,8 @@ import numpy as np  # noqa: E402
 FLOPS_PER_CELL_STAGE = {"riemann2d": 1281.0, "shock_cylinder": 1357.0, "mach5_cylinder": 1276.2}
 # FP64 peak of one GB300: 152 SMs x 2070 MHz boost, NVIDIA's 1.25 TFLOP/s FP64 figure.
 FP64_PEAK_TFLOPS = 1.25
+# neural flux network per cell and stage: x and y face images, 2 x 6336 multiply-adds each
+NN_FLOPS_PER_CELL_STAGE = 2 * 2 * 6336
 # DRAM bytes (read + write) per stage-kernel launch, mean of the three stages of one step,
 # from the ncu capture summarised in profiles/stage2dc_riemann2d_1024.md (variant 0); None
 # for other workloads or variants.
@@ -303,6 +305,47 @@ def run_ours(args):
                        "by js_step_taped) / js_step; ratio_rollout_backward: (js_step_taped + "
                        "js_step_vjp_taped) / js_step, the backward cost per step of a checkpointed rollout"}
 
+    # ---- neural flux (Sec. 2.3): step and reverse step with the network, FP32 and FP64 -----
+    neural = None
+    if args.neural:
+        from paper_2601_04400_gb300 import neural as NN
+        w = NN.init_weights(0, zero_last=False) * 0.5
+        norm = NN.frame_norm(U, scale=0.1)
+        wb = torch.zeros_like(w)
+        dt = solver.max_dt(U, cfl)
+        lam = torch.randn(U.shape, dtype=torch.float64, device="cuda")
+        lam_out = torch.empty_like(lam)
+        pbar = torch.zeros(20, dtype=torch.float64, device="cuda")
+        reps = max(3, min(args.steps, 10))
+        neural = {"flops_per_cell_stage_network": NN_FLOPS_PER_CELL_STAGE,
+                  "note": "network forward per stage: 2 face images (x faces, y faces) x 6336 multiply-adds "
+                          "per face; ms per SSP-RK3 step with the network on, and the reverse step "
+                          "(js_step_vjp with the weight gradient)"}
+        for name, fp32 in (("fp32", True), ("fp64", False)):
+            solver.set_neural(w, norm, w_bar=wb, fp32=fp32)
+            Uw = U.clone()
+            solver.step(Uw, dt, 1)
+            solver.step_vjp(U, dt, lam, lam_n=lam_out, p_bar=pbar)
+            fa = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+            ba = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+            barrier()
+            for k in range(reps):
+                flush.zero_()
+                fa[k][0].record(stream)
+                solver.step(Uw, dt, 1)
+                fa[k][1].record(stream)
+                flush.zero_()
+                ba[k][0].record(stream)
+                solver.step_vjp(U, dt, lam, lam_n=lam_out, p_bar=pbar)
+                ba[k][1].record(stream)
+            barrier()
+            solver.check()
+            f_ms = sum(a.elapsed_time(b) for a, b in fa) / reps
+            b_ms = sum(a.elapsed_time(b) for a, b in ba) / reps
+            neural[name] = {"ms_per_step": f_ms, "ms_per_step_vjp": b_ms,
+                            "network_tflops_over_whole_step": 3 * NN_FLOPS_PER_CELL_STAGE * prob.cells / (f_ms * 1e-3) / 1e12}
+        solver.set_neural(None)
+
     if dist is not None:
         t = torch.tensor([step_ms, e2e_ms, stage_ms / max(stage_launches, 1)], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -334,6 +377,7 @@ def run_ours(args):
                     "d2h_bytes_per_step": state_bytes},
             "adjoint_forward_ratio": None if adj is None else adj["ratio"],
             "adjoint": adj,
+            "neural": neural,
             "gpu_launches": launches,
             "clocks": sampler.summary(),
         }
@@ -433,6 +477,7 @@ def main():
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--neural", action="store_true", help="also time steps with the neural flux")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

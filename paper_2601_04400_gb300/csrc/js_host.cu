@@ -64,6 +64,7 @@ struct js_ctx {
   bool nn_on = false;
   js::NnArgs nn;
   double* nnQ = nullptr;        // primitives of the stage input (4 planes)
+  double* nn_wsave = nullptr;   // WENO5 internals of the current stage (2D; 56 planes)
   void* nn_buf[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   double* nn_partial = nullptr;
   int variant = 0;  // stage-kernel tile shape (js_set_tuning)
@@ -309,11 +310,16 @@ const js::TensorMap128* stage_tmap(js_ctx* c, const double* buf) {
 
 // neural flux of the stage input a.Uin (before the stage kernel) and its divergence
 // subtracted from the stage output (after it)
-int nn_before(js_ctx* c, const StageArgs& a) {
+// (wsave: the stage's stored WENO5 internals, or nullptr to recompute the face states)
+int nn_before(js_ctx* c, const StageArgs& a, const double* wsave = nullptr, long long splane = 0, int tpitch = 0) {
   if (!c->nn_on) return JS_OK;
   c->nn.g1 = 1.0 / (c->p.gamma - 1.0);
+  js::NnArgs n = c->nn;
+  n.wsave = wsave;
+  n.splane = splane;
+  n.tpitch = tpitch;
   JS_CUDA(js::nn_prims(a.Uin, c->nnQ, c->lay, c->p.gamma, c->stream));
-  JS_CUDA(js::nn_forward(c->nn, c->nnQ, c->lay.plane, c->stream));
+  JS_CUDA(js::nn_forward(n, c->nnQ, c->lay.plane, c->stream));
   c->launches += 5;
   return JS_OK;
 }
@@ -324,8 +330,40 @@ int nn_after(js_ctx* c, const StageArgs& a, bool rhs) {
   return JS_OK;
 }
 
+// saved-array layouts: y lines padded (pitch x H), x lines transposed ((nx+6) x tpitch)
+int transposed_pitch(const js_ctx* c) { return (c->lay.H + 3) / 4 * 4; }
+long long saved_plane(const js_ctx* c) {
+  const long long t = (long long)(c->lay.nx + 6) * transposed_pitch(c);
+  const long long m = t > c->lay.plane ? t : c->lay.plane;
+  return (m + 31) / 32 * 32;
+}
+
+size_t internals_bytes(const js_ctx* c) { return sizeof(double) * 56 * (size_t)saved_plane(c); }
+
+// stage update that also stores its WENO5 internals to `wsave` (2D), bracketed by events
+// while profiling like stage()
+int stage_save(js_ctx* c, StageArgs a, bool visc, double* wsave) {
+  a.wsave = wsave;
+  a.splane = saved_plane(c);
+  a.tpitch = transposed_pitch(c);
+  const bool timed = c->profiling && c->ev_used + 2 <= (int)c->ev.size();
+  if (timed) JS_CUDA(cudaEventRecord(c->ev[c->ev_used], c->stream));
+  JS_CUDA(js::launch_stage_save(a, visc, stage_tmap(c, a.Uin), c->stream));
+  if (timed) {
+    JS_CUDA(cudaEventRecord(c->ev[c->ev_used + 1], c->stream));
+    c->ev_used += 2;
+  }
+  ++c->launches;
+  int rc = nn_before(c, a, wsave, a.splane, a.tpitch);
+  if (rc) return rc;
+  return nn_after(c, a, false);
+}
+
 // fused stage kernel, bracketed by events while profiling
 int stage(js_ctx* c, const StageArgs& a, bool visc, bool rhs) {
+  // with the neural flux on a 2D grid the stage kernel also stores its WENO5 internals and
+  // the network's face images are formed from them
+  if (c->nn_on && c->nn_wsave && !rhs) return stage_save(c, a, visc, c->nn_wsave);
   int rc = nn_before(c, a);
   if (rc) return rc;
   const bool timed = c->profiling && c->ev_used + 2 <= (int)c->ev.size();
@@ -395,7 +433,7 @@ void js_destroy(js_ctx* c) {
   cudaFree(c->ibt_cell); cudaFree(c->ibt_ptr); cudaFree(c->ibt_ghost); cudaFree(c->ibt_w);
   cudaFree(c->Q); cudaFree(c->Qb); cudaFree(c->lam); cudaFree(c->P0); cudaFree(c->P1); cudaFree(c->Uacc);
   cudaFree(c->wsave); cudaFree(c->wsave_fwd); cudaFree(c->fadj);
-  cudaFree(c->nnQ); cudaFree(c->nn_partial);
+  cudaFree(c->nnQ); cudaFree(c->nn_partial); cudaFree(c->nn_wsave);
   for (void* b : c->nn_buf) cudaFree(b); cudaFree(c->inflow_acc); cudaFree(c->inflow_prim); cudaFree(c->qIb);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   for (double* t : c->tape) cudaFree(t);
@@ -446,60 +484,6 @@ int js_create(const js_grid* grid, const js_params* params, const js_boundary* b
     }
   }
   *out = c;
-  return JS_OK;
-}
-
-int js_set_neural(js_ctx* c, const double* w, double* w_bar, const double* norm, int precision) {
-  if (!c) return JS_ERR_ARG;
-  if (!w) {
-    c->nn_on = false;
-    return JS_OK;
-  }
-  if (!norm || (precision != JS_NN_F64 && precision != JS_NN_F32)) return JS_ERR_ARG;
-  for (int k = 0; k < 4; ++k)
-    if (!(norm[4 + k] > 0.0) || !std::isfinite(norm[k]) || !std::isfinite(norm[8 + k])) return JS_ERR_ARG;
-  js::NnArgs& n = c->nn;
-  const bool two_d = c->g.ny > 1;
-  n.lay = c->lay;
-  n.nimg = two_d ? 2 : 1;
-  n.H[0] = c->g.ny;
-  n.W[0] = c->g.nx + 1;
-  n.H[1] = two_d ? c->g.nx : 0;
-  n.W[1] = two_d ? c->g.ny + 1 : 0;
-  n.pix0 = (long long)n.H[0] * n.W[0];
-  const long long pix = n.pix0 + (long long)n.H[1] * n.W[1];
-  if (!c->nnQ) {
-    // buffers sized for FP64 (either precision fits): channels 4, 16, 32, 4, 4, 16, 32
-    const int ch[7] = {4, 16, 32, 4, 4, 16, 32};
-    for (int k = 0; k < 7; ++k)
-      if (cudaMalloc(&c->nn_buf[k], sizeof(double) * ch[k] * (size_t)pix) != cudaSuccess) return JS_ERR_NOMEM;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    n.nwblk = 2 * (sms > 0 ? sms : 1);  // weight-gradient blocks (each keeps a partial sum)
-    if (cudaMalloc(&c->nn_partial, sizeof(double) * js::NN_NPARAM * (size_t)n.nwblk) != cudaSuccess ||
-        cudaMalloc(&c->nnQ, sizeof(double) * 4 * (size_t)c->lay.plane) != cudaSuccess)
-      return JS_ERR_NOMEM;
-    JS_CUDA(cudaMemset(c->nnQ, 0, sizeof(double) * 4 * (size_t)c->lay.plane));
-  }
-  n.X = c->nn_buf[0];
-  n.A1 = c->nn_buf[1];
-  n.A2 = c->nn_buf[2];
-  n.T3 = c->nn_buf[3];
-  n.G4 = c->nn_buf[4];
-  n.G16 = c->nn_buf[5];
-  n.G32 = c->nn_buf[6];
-  n.partial = c->nn_partial;
-  n.fp32 = (precision == JS_NN_F32) ? 1 : 0;
-  n.w = w;
-  n.w_bar = w_bar;
-  for (int k = 0; k < 4; ++k) {
-    n.mean[k] = norm[k];
-    n.inv_sd[k] = 1.0 / norm[4 + k];
-    n.scale[k] = norm[8 + k];
-  }
-  n.g1 = 1.0 / (c->p.gamma - 1.0);
-  c->nn_on = true;
   return JS_OK;
 }
 
@@ -606,14 +590,6 @@ int js_step(js_ctx* c, double* U, double dt, int n_steps) {
 
 namespace {
 
-// saved-array layouts: y lines padded (pitch x H), x lines transposed ((nx+6) x tpitch)
-int transposed_pitch(const js_ctx* c) { return (c->lay.H + 3) / 4 * 4; }
-long long saved_plane(const js_ctx* c) {
-  const long long t = (long long)(c->lay.nx + 6) * transposed_pitch(c);
-  const long long m = t > c->lay.plane ? t : c->lay.plane;
-  return (m + 31) / 32 * 32;
-}
-
 int adj_reserve(js_ctx* c) {
   if (c->adj_ready) return JS_OK;
   const size_t pl = sizeof(double) * (size_t)c->lay.plane;
@@ -642,27 +618,6 @@ int adj_reserve(js_ctx* c) {
     return JS_ERR_NOMEM;
   c->adj_ready = true;
   return JS_OK;
-}
-
-size_t internals_bytes(const js_ctx* c) { return sizeof(double) * 56 * (size_t)saved_plane(c); }
-
-// stage update that also stores its WENO5 internals to `wsave` (2D), bracketed by events
-// while profiling like stage()
-int stage_save(js_ctx* c, StageArgs a, bool visc, double* wsave) {
-  a.wsave = wsave;
-  a.splane = saved_plane(c);
-  a.tpitch = transposed_pitch(c);
-  int rc = nn_before(c, a);
-  if (rc) return rc;
-  const bool timed = c->profiling && c->ev_used + 2 <= (int)c->ev.size();
-  if (timed) JS_CUDA(cudaEventRecord(c->ev[c->ev_used], c->stream));
-  JS_CUDA(js::launch_stage_save(a, visc, stage_tmap(c, a.Uin), c->stream));
-  if (timed) {
-    JS_CUDA(cudaEventRecord(c->ev[c->ev_used + 1], c->stream));
-    c->ev_used += 2;
-  }
-  ++c->launches;
-  return nn_after(c, a, false);
 }
 
 js::AdjArgs adj_args(js_ctx* c, const double* X, double* Ub, double* p_bar) {
@@ -973,3 +928,65 @@ int js_ib_info(js_ctx* c, int* n_ghost, unsigned char* tag_host) {
 }
 
 }  // extern "C"
+
+int js_set_neural(js_ctx* c, const double* w, double* w_bar, const double* norm, int precision) {
+  if (!c) return JS_ERR_ARG;
+  if (!w) {
+    c->nn_on = false;
+    return JS_OK;
+  }
+  if (!norm || (precision != JS_NN_F64 && precision != JS_NN_F32)) return JS_ERR_ARG;
+  for (int k = 0; k < 4; ++k)
+    if (!(norm[4 + k] > 0.0) || !std::isfinite(norm[k]) || !std::isfinite(norm[8 + k])) return JS_ERR_ARG;
+  js::NnArgs& n = c->nn;
+  const bool two_d = c->g.ny > 1;
+  n.lay = c->lay;
+  n.nimg = two_d ? 2 : 1;
+  n.H[0] = c->g.ny;
+  n.W[0] = c->g.nx + 1;
+  n.H[1] = two_d ? c->g.nx : 0;
+  n.W[1] = two_d ? c->g.ny + 1 : 0;
+  n.pix0 = (long long)n.H[0] * n.W[0];
+  const long long pix = n.pix0 + (long long)n.H[1] * n.W[1];
+  if (!c->nnQ) {
+    // buffers sized for FP64 (either precision fits): channels 4, 16, 32, 4, 4, 16, 32
+    const int ch[7] = {4, 16, 32, 4, 4, 16, 32};
+    for (int k = 0; k < 7; ++k)
+      if (cudaMalloc(&c->nn_buf[k], sizeof(double) * ch[k] * (size_t)pix) != cudaSuccess) return JS_ERR_NOMEM;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    n.nwblk = 2 * (sms > 0 ? sms : 1);  // weight-gradient blocks (each keeps a partial sum)
+    if (cudaMalloc(&c->nn_partial, sizeof(double) * js::NN_NPARAM * (size_t)n.nwblk) != cudaSuccess ||
+        cudaMalloc(&c->nnQ, sizeof(double) * 4 * (size_t)c->lay.plane) != cudaSuccess)
+      return JS_ERR_NOMEM;
+    JS_CUDA(cudaMemset(c->nnQ, 0, sizeof(double) * 4 * (size_t)c->lay.plane));
+  }
+  n.X = c->nn_buf[0];
+  n.A1 = c->nn_buf[1];
+  n.A2 = c->nn_buf[2];
+  n.T3 = c->nn_buf[3];
+  n.G4 = c->nn_buf[4];
+  n.G16 = c->nn_buf[5];
+  n.G32 = c->nn_buf[6];
+  n.partial = c->nn_partial;
+  n.fp32 = (precision == JS_NN_F32) ? 1 : 0;
+  n.w = w;
+  n.w_bar = w_bar;
+  for (int k = 0; k < 4; ++k) {
+    n.mean[k] = norm[k];
+    n.inv_sd[k] = 1.0 / norm[4 + k];
+    n.scale[k] = norm[8 + k];
+  }
+  n.g1 = 1.0 / (c->p.gamma - 1.0);
+  // 2D: the stage kernel stores the WENO5 internals the face images are formed from
+  if (two_d && !c->nn_wsave) {
+    if (cudaMalloc(&c->nn_wsave, internals_bytes(c)) != cudaSuccess) {
+      c->nn_wsave = nullptr;
+      return JS_ERR_NOMEM;
+    }
+    JS_CUDA(cudaMemset(c->nn_wsave, 0, internals_bytes(c)));
+  }
+  c->nn_on = true;
+  return JS_OK;
+}

@@ -101,6 +101,11 @@ struct NnArgs {
   void* G32;                  // 32-channel gradient scratch
   double* partial;            // weight-gradient partial sums [nwblk][NN_NPARAM]
   int nwblk;
+  // WENO5 internals of the stage (2D, layout of StageArgs::wsave) to form the face states
+  // from, or nullptr: the image kernels then recompute WENO5
+  const double* wsave;
+  long long splane;
+  int tpitch;
 };
 
 // forward: images of the stage input (primitives Q, plane qplane) and the network, into T3

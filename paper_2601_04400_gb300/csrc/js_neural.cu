@@ -24,6 +24,8 @@
 // would make about 20x the cost of the FP64 solver it corrects).
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "js_device.cuh"
 #include "js_internal.h"
 
@@ -68,6 +70,28 @@ __device__ __forceinline__ void face_states(const Lay& L, const double* Q, long 
   }
 }
 
+// the same face states from the stage's stored WENO5 internals: state = q_cell + q/6 with the
+// quotient q saved for the left-biased state of cell f-1 and the right-biased one of cell f
+__device__ __forceinline__ void face_states_saved(const NnArgs& n, const Lay& L, const double* Q, long long qplane,
+                                                  int d, int h, int f, double wl[4], double wr[4]) {
+  const long long ca = (d == 0) ? L.idx(f - 1, h) : L.idx(h, f - 1);
+  const long long cb = (d == 0) ? L.idx(f, h) : L.idx(h, f);
+  const long long sa = (d == 0) ? (long long)(f + 2) * n.tpitch + (h + L.gy) : ca;
+  const long long sb = (d == 0) ? (long long)(f + 3) * n.tpitch + (h + L.gy) : cb;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const double* sv = n.wsave + (long long)(d * 28 + c * 7) * n.splane;
+    wl[c] = fma(sv[3 * n.splane + sa], SIXTH, Q[c * qplane + ca]);
+    wr[c] = fma(sv[5 * n.splane + sb], SIXTH, Q[c * qplane + cb]);
+  }
+}
+
+__device__ __forceinline__ void face_states_any(const NnArgs& n, const Lay& L, const double* Q, long long qplane,
+                                                int d, int h, int f, double wl[4], double wr[4]) {
+  if (n.wsave) face_states_saved(n, L, Q, qplane, d, h, f, wl, wr);
+  else face_states(L, Q, qplane, d, h, f, wl, wr);
+}
+
 // ---------------------------------------------------------------------------------------
 // forward
 // ---------------------------------------------------------------------------------------
@@ -94,7 +118,7 @@ __global__ void nn_image_kernel(NnArgs n, const double* __restrict__ Q, long lon
   if (p >= pix) return;
   const int h = (int)(p / Wd), f = (int)(p % Wd);
   double wl[4], wr[4];
-  face_states(n.lay, Q, qplane, d, h, f, wl, wr);
+  face_states_any(n, n.lay, Q, qplane, d, h, f, wl, wr);
   const int un = (d == 0) ? 1 : 2, ut = (d == 0) ? 2 : 1;
   double m[4];
   {
@@ -151,6 +175,245 @@ __global__ void __launch_bounds__(NTHR) nn_conv_kernel(NnArgs n, const void* in,
 #pragma unroll
     for (int co = 0; co < COUT; ++co) Y[co * pix + o] = (ACT == 0) ? (acc[co] > (T)0 ? acc[co] : (T)0) : act_tanh(acc[co]);
   }
+}
+
+// FP32 layer with register blocking: 128 threads per 16x16 tile, each computing 2 adjacent
+// pixels for all output channels; weights tap-major with the output channels contiguous, so
+// one 16-byte shared load feeds 8 fused multiply-adds
+constexpr int PB = 2;                 // pixels per thread (along the tile row)
+constexpr int NTHR_F = NTHR / PB;     // 128
+
+template <int CIN, int COUT, int ACT>
+__global__ void __launch_bounds__(NTHR_F) nn_conv_f32_kernel(NnArgs n, const void* in, void* out, int woff) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  static_assert(COUT % 4 == 0, "output channels in groups of 4");
+  float* sw = reinterpret_cast<float*>(smem_raw);  // [CIN*9][COUT]
+  float* sb = sw + CIN * 9 * COUT;                  // [COUT]
+  float* sx = sb + COUT;                            // [CIN][18][18]
+  const int d = blockIdx.z;
+  const int H = n.H[d], Wd = n.W[d];
+  const int x0 = blockIdx.x * TILE, y0 = blockIdx.y * TILE;
+  if (x0 >= Wd || y0 >= H) return;
+  const long long pix = (long long)H * Wd;
+  const float* X = chan_img<float>(in, CIN, d, n.pix0);
+  float* Y = chan_img<float>(out, COUT, d, n.pix0);
+  for (int k = threadIdx.x; k < COUT * CIN * 9; k += NTHR_F) {
+    const int co = k / (CIN * 9), r = k % (CIN * 9);
+    sw[r * COUT + co] = (float)n.w[woff + k];
+  }
+  for (int k = threadIdx.x; k < COUT; k += NTHR_F) sb[k] = (float)n.w[woff + COUT * CIN * 9 + k];
+  for (int k = threadIdx.x; k < CIN * TH * TH; k += NTHR_F) {
+    const int ci = k / (TH * TH), r = k % (TH * TH);
+    const int gy = y0 + r / TH - 1, gx = x0 + r % TH - 1;
+    sx[k] = (gy >= 0 && gy < H && gx >= 0 && gx < Wd) ? X[ci * pix + (long long)gy * Wd + gx] : 0.0f;
+  }
+  __syncthreads();
+  const int ty = threadIdx.x / (TILE / PB), tx0 = (threadIdx.x % (TILE / PB)) * PB;
+  float acc[PB][COUT];
+#pragma unroll
+  for (int q = 0; q < PB; ++q)
+#pragma unroll
+    for (int co = 0; co < COUT; ++co) acc[q][co] = sb[co];
+  for (int ci = 0; ci < CIN; ++ci)
+#pragma unroll
+    for (int ky = 0; ky < 3; ++ky) {
+      const float* row = sx + ci * TH * TH + (ty + ky) * TH + tx0;
+      float x[PB + 2];
+#pragma unroll
+      for (int j = 0; j < PB + 2; ++j) x[j] = row[j];
+#pragma unroll
+      for (int kx = 0; kx < 3; ++kx) {
+        const float4* w4 = reinterpret_cast<const float4*>(sw + ((ci * 3 + ky) * 3 + kx) * COUT);
+#pragma unroll
+        for (int c4 = 0; c4 < COUT / 4; ++c4) {
+          const float4 wv = w4[c4];
+#pragma unroll
+          for (int q = 0; q < PB; ++q) {
+            const float v = x[q + kx];
+            acc[q][4 * c4 + 0] = fmaf(wv.x, v, acc[q][4 * c4 + 0]);
+            acc[q][4 * c4 + 1] = fmaf(wv.y, v, acc[q][4 * c4 + 1]);
+            acc[q][4 * c4 + 2] = fmaf(wv.z, v, acc[q][4 * c4 + 2]);
+            acc[q][4 * c4 + 3] = fmaf(wv.w, v, acc[q][4 * c4 + 3]);
+          }
+        }
+      }
+    }
+  const int gy = y0 + ty;
+#pragma unroll
+  for (int q = 0; q < PB; ++q) {
+    const int gx = x0 + tx0 + q;
+    if (gx < Wd && gy < H) {
+      const long long o = (long long)gy * Wd + gx;
+#pragma unroll
+      for (int co = 0; co < COUT; ++co) {
+        const float v = acc[q][co];
+        Y[co * pix + o] = (ACT == 0) ? (v > 0.0f ? v : 0.0f) : tanhf(v);
+      }
+    }
+  }
+}
+
+// FP32 data gradient with the same blocking: weights [co][ky][kx][ci], input channels
+// contiguous; the ReLU mask of the layer below is applied when MASK
+template <int CIN, int COUT, bool MASK>
+__global__ void __launch_bounds__(NTHR_F) nn_dgrad_f32_kernel(NnArgs n, const void* gout, const void* aprev, void* gin,
+                                                              int woff) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  static_assert(CIN % 4 == 0, "input channels in groups of 4");
+  float* sw = reinterpret_cast<float*>(smem_raw);  // [COUT*9][CIN]
+  float* sg = sw + COUT * 9 * CIN;                  // [COUT][18][18]
+  const int d = blockIdx.z;
+  const int H = n.H[d], Wd = n.W[d];
+  const int x0 = blockIdx.x * TILE, y0 = blockIdx.y * TILE;
+  if (x0 >= Wd || y0 >= H) return;
+  const long long pix = (long long)H * Wd;
+  const float* G = chan_img<float>(gout, COUT, d, n.pix0);
+  float* D = chan_img<float>(gin, CIN, d, n.pix0);
+  for (int k = threadIdx.x; k < COUT * CIN * 9; k += NTHR_F) {
+    const int co = k / (CIN * 9), r = k % (CIN * 9), ci = r / 9, t = r % 9;
+    sw[(co * 9 + t) * CIN + ci] = (float)n.w[woff + k];
+  }
+  for (int k = threadIdx.x; k < COUT * TH * TH; k += NTHR_F) {
+    const int co = k / (TH * TH), r = k % (TH * TH);
+    const int gy = y0 + r / TH - 1, gx = x0 + r % TH - 1;
+    sg[k] = (gy >= 0 && gy < H && gx >= 0 && gx < Wd) ? G[co * pix + (long long)gy * Wd + gx] : 0.0f;
+  }
+  __syncthreads();
+  const int ty = threadIdx.x / (TILE / PB), tx0 = (threadIdx.x % (TILE / PB)) * PB;
+  float acc[PB][CIN];
+#pragma unroll
+  for (int q = 0; q < PB; ++q)
+#pragma unroll
+    for (int ci = 0; ci < CIN; ++ci) acc[q][ci] = 0.0f;
+  for (int co = 0; co < COUT; ++co)
+#pragma unroll
+    for (int ky = 0; ky < 3; ++ky) {
+      // gout at (ty - ky + 1, tx - kx + 1): tile row ty - ky + 2, columns tx0 .. tx0 + 5
+      const float* row = sg + co * TH * TH + (ty - ky + 2) * TH + tx0;
+      float x[PB + 2];
+#pragma unroll
+      for (int j = 0; j < PB + 2; ++j) x[j] = row[j];
+#pragma unroll
+      for (int kx = 0; kx < 3; ++kx) {
+        const float4* w4 = reinterpret_cast<const float4*>(sw + ((co * 3 + ky) * 3 + kx) * CIN);
+#pragma unroll
+        for (int c4 = 0; c4 < CIN / 4; ++c4) {
+          const float4 wv = w4[c4];
+#pragma unroll
+          for (int q = 0; q < PB; ++q) {
+            const float v = x[q + 2 - kx];
+            acc[q][4 * c4 + 0] = fmaf(wv.x, v, acc[q][4 * c4 + 0]);
+            acc[q][4 * c4 + 1] = fmaf(wv.y, v, acc[q][4 * c4 + 1]);
+            acc[q][4 * c4 + 2] = fmaf(wv.z, v, acc[q][4 * c4 + 2]);
+            acc[q][4 * c4 + 3] = fmaf(wv.w, v, acc[q][4 * c4 + 3]);
+          }
+        }
+      }
+    }
+  const int gy = y0 + ty;
+  const float* A = MASK ? chan_img<float>(aprev, CIN, d, n.pix0) : nullptr;
+#pragma unroll
+  for (int q = 0; q < PB; ++q) {
+    const int gx = x0 + tx0 + q;
+    if (gx < Wd && gy < H) {
+      const long long o = (long long)gy * Wd + gx;
+#pragma unroll
+      for (int ci = 0; ci < CIN; ++ci) {
+        float v = acc[q][ci];
+        if (MASK && !(A[ci * pix + o] > 0.0f)) v = 0.0f;
+        D[ci * pix + o] = v;
+      }
+    }
+  }
+}
+
+// FP32 weight gradient: a work item is (group of 4 output channels, input channel, kernel
+// row) with 4 x 3 sums (the three kernel columns); per pixel one 16-byte load of the output
+// gradient and one input value slid along the row
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(NTHR) nn_wgrad_f32_kernel(NnArgs n, const void* gout, const void* ain, int woff) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int NI = (COUT / 4) * CIN * 3;          // work items
+  constexpr int PER = (NI + NTHR - 1) / NTHR;
+  float* sg = reinterpret_cast<float*>(smem_raw);   // [256 pixels][COUT]
+  float* sa = sg + NTHR * COUT;                     // [CIN][18][18]
+  float acc[PER][12];
+  float bacc = 0.0f;                                // bias sums (threads < COUT)
+#pragma unroll
+  for (int r = 0; r < PER; ++r)
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[r][k] = 0.0f;
+  int ntx[2], nty[2];
+  for (int d = 0; d < 2; ++d) {
+    ntx[d] = (d < n.nimg) ? (n.W[d] + TILE - 1) / TILE : 0;
+    nty[d] = (d < n.nimg) ? (n.H[d] + TILE - 1) / TILE : 0;
+  }
+  const int t0 = ntx[0] * nty[0], total = t0 + ntx[1] * nty[1];
+  for (int t = blockIdx.x; t < total; t += gridDim.x) {
+    const int d = (t < t0) ? 0 : 1;
+    const int tl = (d == 0) ? t : t - t0;
+    const int x0 = (tl % ntx[d]) * TILE, y0 = (tl / ntx[d]) * TILE;
+    const int H = n.H[d], Wd = n.W[d];
+    const long long pix = (long long)H * Wd;
+    const float* G = chan_img<float>(gout, COUT, d, n.pix0);
+    const float* A = chan_img<float>(ain, CIN, d, n.pix0);
+    __syncthreads();
+    for (int k = threadIdx.x; k < COUT * NTHR; k += NTHR) {
+      const int co = k / NTHR, r = k % NTHR;
+      const int gy = y0 + r / TILE, gx = x0 + r % TILE;
+      sg[r * COUT + co] = (gy < H && gx < Wd) ? G[co * pix + (long long)gy * Wd + gx] : 0.0f;
+    }
+    for (int k = threadIdx.x; k < CIN * TH * TH; k += NTHR) {
+      const int ci = k / (TH * TH), r = k % (TH * TH);
+      const int gy = y0 + r / TH - 1, gx = x0 + r % TH - 1;
+      sa[k] = (gy >= 0 && gy < H && gx >= 0 && gx < Wd) ? A[ci * pix + (long long)gy * Wd + gx] : 0.0f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+      const int item = threadIdx.x + r * NTHR;
+      if (item >= NI) continue;
+      const int c4 = item / (CIN * 3), rem = item % (CIN * 3), ci = rem / 3, ky = rem % 3;
+      for (int py = 0; py < TILE; ++py) {
+        const float* arow = sa + ci * TH * TH + (py + ky) * TH;
+        const float4* g4 = reinterpret_cast<const float4*>(sg + py * TILE * COUT) + c4;
+        float a0 = arow[0], a1 = arow[1];
+#pragma unroll
+        for (int px = 0; px < TILE; ++px) {
+          const float a2 = arow[px + 2];
+          const float4 g = g4[px * (COUT / 4)];
+          acc[r][0] = fmaf(g.x, a0, acc[r][0]);
+          acc[r][1] = fmaf(g.y, a0, acc[r][1]);
+          acc[r][2] = fmaf(g.z, a0, acc[r][2]);
+          acc[r][3] = fmaf(g.w, a0, acc[r][3]);
+          acc[r][4] = fmaf(g.x, a1, acc[r][4]);
+          acc[r][5] = fmaf(g.y, a1, acc[r][5]);
+          acc[r][6] = fmaf(g.z, a1, acc[r][6]);
+          acc[r][7] = fmaf(g.w, a1, acc[r][7]);
+          acc[r][8] = fmaf(g.x, a2, acc[r][8]);
+          acc[r][9] = fmaf(g.y, a2, acc[r][9]);
+          acc[r][10] = fmaf(g.z, a2, acc[r][10]);
+          acc[r][11] = fmaf(g.w, a2, acc[r][11]);
+          a0 = a1;
+          a1 = a2;
+        }
+      }
+    }
+    if (threadIdx.x < COUT)
+      for (int q = 0; q < NTHR; ++q) bacc += sg[q * COUT + threadIdx.x];
+  }
+  double* part = n.partial + (long long)blockIdx.x * NN_NPARAM + woff;
+#pragma unroll
+  for (int r = 0; r < PER; ++r) {
+    const int item = threadIdx.x + r * NTHR;
+    if (item >= NI) continue;
+    const int c4 = item / (CIN * 3), rem = item % (CIN * 3), ci = rem / 3, ky = rem % 3;
+#pragma unroll
+    for (int kx = 0; kx < 3; ++kx)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) part[(((4 * c4 + j) * CIN + ci) * 3 + ky) * 3 + kx] = (double)acc[r][4 * kx + j];
+  }
+  if (threadIdx.x < COUT) part[COUT * CIN * 9 + threadIdx.x] = (double)bacc;
 }
 
 // stage output (or RHS) minus the neural flux divergence on fluid cells
@@ -348,7 +611,7 @@ __global__ void nn_image_vjp_kernel(NnArgs n, AdjArgs a) {
   if (p < pix) {
     const int h = (int)(p / Wd), f = (int)(p % Wd);
     double wl[4], wr[4];
-    face_states(a.lay, a.Q, a.lay.plane, d, h, f, wl, wr);
+    face_states_any(n, a.lay, a.Q, a.lay.plane, d, h, f, wl, wr);
     const T* dX = chan_img<T>(n.G4, 4, d, n.pix0);
     double gk[4];  // adjoint of each side's conserved frame state (the image is their mean)
 #pragma unroll
@@ -369,8 +632,16 @@ __global__ void nn_image_vjp_kernel(NnArgs n, AdjArgs a) {
       for (int c = 0; c < 4; ++c) a.fadj[(long long)(fdir + 4 * s + c) * a.splane + si] += b[c];
     }
   }
+  // one atomic per block: many blocks add to the same entry
+  __shared__ double red[8];
   gbar = nn_warp_sum(gbar);
-  if (a.pbar && (threadIdx.x & 31) == 0 && gbar != 0.0) atomicAdd(a.pbar, gbar);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = gbar;
+  __syncthreads();
+  if (threadIdx.x == 0 && a.pbar) {
+    double t = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+    if (t != 0.0) atomicAdd(a.pbar, t);
+  }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -395,6 +666,14 @@ dim3 tile_grid(const NnArgs& n) {
 
 template <class T, int CIN, int COUT, int ACT>
 cudaError_t conv(const NnArgs& n, const void* in, void* out, int woff, cudaStream_t s) {
+  if (std::is_same<T, float>::value) {
+    const size_t sm = sizeof(float) * (CIN * 9 * COUT + COUT + CIN * TH * TH);
+    auto k = nn_conv_f32_kernel<CIN, COUT, ACT>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k<<<tile_grid(n), NTHR_F, sm, s>>>(n, in, out, woff);
+    return cudaGetLastError();
+  }
   constexpr int NW = COUT * CIN * 9 + COUT;
   const size_t sm = sizeof(T) * (((NW + 1) & ~1) + CIN * TH * TH);
   auto k = nn_conv_kernel<T, CIN, COUT, ACT>;
@@ -406,6 +685,14 @@ cudaError_t conv(const NnArgs& n, const void* in, void* out, int woff, cudaStrea
 
 template <class T, int CIN, int COUT, bool MASK>
 cudaError_t dgrad(const NnArgs& n, const void* gout, const void* aprev, void* gin, int woff, cudaStream_t s) {
+  if (std::is_same<T, float>::value) {
+    const size_t sm = sizeof(float) * (COUT * 9 * CIN + COUT * TH * TH);
+    auto k = nn_dgrad_f32_kernel<CIN, COUT, MASK>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k<<<tile_grid(n), NTHR_F, sm, s>>>(n, gout, aprev, gin, woff);
+    return cudaGetLastError();
+  }
   constexpr int NWW = COUT * CIN * 9;
   const size_t sm = sizeof(T) * (((NWW + 1) & ~1) + COUT * TH * TH);
   auto k = nn_dgrad_kernel<T, CIN, COUT, MASK>;
@@ -417,6 +704,14 @@ cudaError_t dgrad(const NnArgs& n, const void* gout, const void* aprev, void* gi
 
 template <class T, int CIN, int COUT>
 cudaError_t wgrad(const NnArgs& n, const void* gout, const void* ain, int woff, cudaStream_t s) {
+  if (std::is_same<T, float>::value) {
+    const size_t sm = sizeof(float) * (NTHR * COUT + CIN * TH * TH);
+    auto k = nn_wgrad_f32_kernel<CIN, COUT>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k<<<n.nwblk, NTHR, sm, s>>>(n, gout, ain, woff);
+    return cudaGetLastError();
+  }
   const size_t sm = sizeof(T) * (COUT * NTHR + CIN * TH * TH);
   auto k = nn_wgrad_kernel<T, CIN, COUT>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -475,7 +770,12 @@ cudaError_t nn_apply(const NnArgs& n, const StageArgs& a, bool rhs, cudaStream_t
 }
 
 cudaError_t nn_reverse(const NnArgs& n, const AdjArgs& a, cudaStream_t s) {
-  return n.fp32 ? reverse_t<float>(n, a, s) : reverse_t<double>(n, a, s);
+  // pass 1 has run: on 2D grids a.wsave holds the stage's WENO5 internals
+  NnArgs m = n;
+  m.wsave = a.two_d ? a.wsave : nullptr;
+  m.splane = a.splane;
+  m.tpitch = a.tpitch;
+  return m.fp32 ? reverse_t<float>(m, a, s) : reverse_t<double>(m, a, s);
 }
 
 // ---------------------------------------------------------------------------------------
