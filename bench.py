@@ -33,9 +33,9 @@ FP64_PEAK_TFLOPS = 1.25
 # neural flux network per cell and stage: x and y face images, 2 x 6336 multiply-adds each
 NN_FLOPS_PER_CELL_STAGE = 2 * 2 * 6336
 # DRAM bytes (read + write) per stage-kernel launch, mean of the three stages of one step,
-# from the ncu capture summarised in profiles/stage2dc_riemann2d_1024.md (variant 0); None
-# for other workloads or variants.
-STAGE_TRAFFIC_BYTES = {("riemann2d", 0): 121.6e6}
+# from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of this bench's default
+# run with the TMA-staged variant 0; None for other workloads or variants.
+STAGE_TRAFFIC_BYTES = {("riemann2d", 0): 111.1e6}
 L2_FLUSH_BYTES = 256 << 20
 METRIC = "FP64 cell-updates/s per RK step on 1 GB300 (% roofline); adjoint/forward time ratio"
 
