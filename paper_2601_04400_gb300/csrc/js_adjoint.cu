@@ -559,7 +559,7 @@ namespace {
 // would leave most of the GPU idle); pass 1 pays one extra WENO cell per segment, except
 // when the forward stored the internals: then a segment costs almost nothing to start and
 // shorter ones split the work into finer waves
-constexpr int kSeg1 = 16, kSeg1Saved = 8, kSeg2 = 8, kBlk = 64;
+constexpr int kSeg1 = 16, kSeg1Saved = 8, kSeg2 = 8, kSeg1D = 4, kBlk = 64;
 
 unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
@@ -578,21 +578,24 @@ cudaError_t pass1(const AdjArgs& a, bool visc, bool two_d, cudaStream_t s) {
     else adj_pass1_kernel<false, false, true><<<sx + sy, kBlk, 0, s>>>(a, kSeg1Saved, sx);
     return cudaGetLastError();
   }
-  const int bx = (int)blocks_for(line_items(a, 0, 1, kSeg1), kBlk);
-  const int by = two_d ? (int)blocks_for(line_items(a, 1, 1, kSeg1), kBlk) : 0;
+  // a 1D grid is one line: short segments give it more threads
+  const int seg = two_d ? kSeg1 : kSeg1D;
+  const int bx = (int)blocks_for(line_items(a, 0, 1, seg), kBlk);
+  const int by = two_d ? (int)blocks_for(line_items(a, 1, 1, seg), kBlk) : 0;
   if (visc) {
-    if (two_d) adj_pass1_kernel<true, true, false><<<bx + by, kBlk, 0, s>>>(a, kSeg1, bx);
-    else adj_pass1_kernel<true, false, false><<<bx + by, kBlk, 0, s>>>(a, kSeg1, bx);
+    if (two_d) adj_pass1_kernel<true, true, false><<<bx + by, kBlk, 0, s>>>(a, seg, bx);
+    else adj_pass1_kernel<true, false, false><<<bx + by, kBlk, 0, s>>>(a, seg, bx);
   } else {
-    adj_pass1_kernel<false, false, false><<<bx + by, kBlk, 0, s>>>(a, kSeg1, bx);
+    adj_pass1_kernel<false, false, false><<<bx + by, kBlk, 0, s>>>(a, seg, bx);
   }
   return cudaGetLastError();
 }
 
 cudaError_t pass2(const AdjArgs& a, bool two_d, cudaStream_t s) {
-  const int bx = (int)blocks_for(line_items(a, 0, 2, kSeg2), kBlk);
-  const int by = two_d ? (int)blocks_for(line_items(a, 1, 2, kSeg2), kBlk) : 0;
-  adj_pass2_kernel<<<bx + by, kBlk, 0, s>>>(a, kSeg2, bx);
+  const int seg = two_d ? kSeg2 : kSeg1D;
+  const int bx = (int)blocks_for(line_items(a, 0, 2, seg), kBlk);
+  const int by = two_d ? (int)blocks_for(line_items(a, 1, 2, seg), kBlk) : 0;
+  adj_pass2_kernel<<<bx + by, kBlk, 0, s>>>(a, seg, bx);
   return cudaGetLastError();
 }
 }  // namespace

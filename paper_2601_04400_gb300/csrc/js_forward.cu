@@ -184,7 +184,9 @@ __global__ void __launch_bounds__(TX / LX) stage1d_kernel(StageArgs a) {
 // launchers
 // =======================================================================================
 namespace {
-constexpr int TX1 = 64, LX1 = 16;
+// 1D grids are small (a few hundred cells): short segments, so that more threads share the
+// latency-bound sweep
+constexpr int TX1 = 32, LX1 = 4;
 
 template <int TX, int TY, int LX, int LY, bool VISC, bool RHS>
 cudaError_t launch_stage2d(const StageArgs& a, cudaStream_t s) {

@@ -731,7 +731,12 @@ cudaError_t forward_t(const NnArgs& n, const double* Q, long long qplane, cudaSt
 }
 
 template <class T>
-cudaError_t reverse_t(const NnArgs& n, const AdjArgs& a, cudaStream_t s) {
+cudaError_t reverse_t(const NnArgs& n0, const AdjArgs& a, cudaStream_t s) {
+  // no more weight-gradient blocks than tiles (small images leave most blocks idle)
+  NnArgs n = n0;
+  long long tiles = 0;
+  for (int d = 0; d < n.nimg; ++d) tiles += (long long)cdiv(n.W[d], TILE) * cdiv(n.H[d], TILE);
+  if (tiles < n.nwblk) n.nwblk = (int)tiles;
   cudaError_t e = forward_t<T>(n, a.Q, a.lay.plane, s);
   if (e != cudaSuccess) return e;
   const dim3 pg(cdiv(max_pix(n), 256), n.nimg);
