@@ -166,3 +166,22 @@ def test_weight_gradient_accumulates_and_paths_agree(env):
     Ud, Ur = to_dev(U), to_dev(U)
     s.step(Ud, dt, 1)
     assert normwise_err(to_host(Ud), O.step(prob, U, [dt])) < TOL  # off again
+
+
+def test_fp64_network_full_size_matches_oracle(env):
+    """The benchmark grid (1024 x 1024 four-quadrant, from a GPU state a few steps in): the RHS
+    with the FP64 network equals the oracle on every cell (steps are covered above; the
+    oracle's network at this size costs ~10 s per evaluation)."""
+    torch, B = env
+    prob = W.riemann2d(1024)
+    s = B.Solver.from_problem(prob)
+    Ud = s.prim_to_cons(torch.tensor(prob.W0, device="cuda"))
+    s.step(Ud, s.max_dt(Ud, prob.cfl), 5)
+    U = to_host(Ud)
+    w, norm = _params(12), _norm(prob, U)
+    s.set_neural(torch.tensor(w, device="cuda"), norm)
+    with O.neural(w, norm):
+        L_ref = O.rhs(prob, U)
+    assert normwise_err(to_host(s.rhs(to_dev(U))), L_ref) < TOL
+    assert s.status() == 0
+
