@@ -282,6 +282,58 @@ def test_viscous_terms_are_second_order_diffusion():
     assert orders.min() > 1.9, orders
 
 
+def _viscous_part(p, Wp, mu):
+    """rhs(mu) - rhs(0): the inviscid terms do not depend on mu, so this is the viscous part."""
+    U = O.prim_to_cons(p, Wp)
+    return O.rhs(p.with_(mu=mu), U) - O.rhs(p.with_(mu=0.0), U)
+
+
+@pytest.mark.parametrize("case", ["normal_stress_and_work", "heat_conduction", "shear_heating"])
+def test_viscous_stress_work_and_heat_terms_converge_to_closed_forms(case):
+    """The viscous part of the RHS against the Navier-Stokes terms it discretises (constant mu,
+    Stokes hypothesis, kappa = mu gamma / ((gamma - 1) Pr), T = p / rho), second order:
+    u = u0 sin(2 pi x): d(tau_xx)/dx = 4/3 mu u'', energy 4/3 mu (u'^2 + u u'');
+    T = 1 + 0.1 sin(2 pi y) at rest, p = 1: energy kappa T'';
+    u = u0 sin(2 pi y): energy mu (u'^2 + u u'')."""
+    mu, g, Pr, u0 = 1e-2, 1.4, 0.72, 0.3
+    kappa = mu * g / ((g - 1.0) * Pr)
+    errs = []
+    for n in (32, 64, 128):
+        s = (np.arange(n) + 0.5) / n
+        k = 2 * np.pi
+        if case == "normal_stress_and_work":
+            p = W.random_periodic(n, 8, seed=0).with_(dx=1.0 / n, dy=1.0 / n, Pr=Pr, gamma=g)
+            Wp = np.zeros((4, 8, n))
+            Wp[0], Wp[3] = 1.0, 1.0
+            u = u0 * np.sin(k * s)
+            Wp[1] = u[None, :]
+            V = _viscous_part(p, Wp, mu)[:, 0, :]
+            up, upp = u0 * k * np.cos(k * s), -u0 * k * k * np.sin(k * s)
+            ex = {1: 4.0 / 3.0 * mu * upp, 3: 4.0 / 3.0 * mu * (up * up + u * upp)}
+            assert np.abs(V[0]).max() < 1e-12 and np.abs(V[2]).max() < 1e-12
+        elif case == "heat_conduction":
+            p = W.random_periodic(8, n, seed=0).with_(dx=1.0 / n, dy=1.0 / n, Pr=Pr, gamma=g)
+            Wp = np.zeros((4, n, 8))
+            T = 1.0 + 0.1 * np.sin(k * s)
+            Wp[0] = (1.0 / T)[:, None]
+            Wp[3] = 1.0
+            V = _viscous_part(p, Wp, mu)[:, :, 0]
+            ex = {3: kappa * (-0.1 * k * k * np.sin(k * s))}
+            assert np.abs(V[:3]).max() < 1e-12
+        else:
+            p = W.random_periodic(8, n, seed=0).with_(dx=1.0 / n, dy=1.0 / n, Pr=Pr, gamma=g)
+            Wp = np.zeros((4, n, 8))
+            Wp[0], Wp[3] = 1.0, 1.0
+            u = u0 * np.sin(k * s)
+            Wp[1] = u[:, None]
+            V = _viscous_part(p, Wp, mu)[:, :, 0]
+            up, upp = u0 * k * np.cos(k * s), -u0 * k * k * np.sin(k * s)
+            ex = {1: mu * upp, 3: mu * (up * up + u * upp)}
+        errs.append(max(np.abs(V[c] - e).max() / np.abs(e).max() for c, e in ex.items()))
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert orders.min() > 1.9 and errs[-1] < 5e-3, (errs, orders)
+
+
 # ---------------------------------------------------------------------------------------
 # immersed boundary (Sec. 2, Fig. 1(c)) and Rankine-Hugoniot initial states
 # ---------------------------------------------------------------------------------------
