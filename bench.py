@@ -468,6 +468,21 @@ def run_batched(args):
     e1.record(stream)
     e1.synchronize()
     t_seq = e0.elapsed_time(e1)
+    # reverse of one batched step (js_batch_step_vjp: every instance's js_step_vjp, spread
+    # over a few streams) against one batched forward step
+    dts = [s.max_dt(U, 0.5) for s, U in zip(solvers, states)]
+    lams = [torch.randn_like(U) for U in states]
+    outs = [torch.empty_like(U) for U in states]
+    batch.step_vjp(states, dts, lams, outs)
+    torch.cuda.synchronize()
+    reps = 3
+    e0.record(stream)
+    for _ in range(reps):
+        batch.step_vjp(states, dts, lams, outs)
+    e1.record(stream)
+    e1.synchronize()
+    t_vjp = e0.elapsed_time(e1) / reps
+    ok = ok and batch.status() == 0
     info = batch.info()
     if rank == 0:
         print(json.dumps({
@@ -491,7 +506,10 @@ def run_batched(args):
             "one_at_a_time": {"value": local_cells * args.steps / (t_seq * 1e-3), "ms_per_step": t_seq / args.steps,
                               "how": "rank 0's instances, each: js_max_dt (synchronising) + js_step, one step "
                                      "at a time"},
-            "speedup_vs_one_at_a_time": t_seq / t_batch}), flush=True)
+            "speedup_vs_one_at_a_time": t_seq / t_batch,
+            "adjoint": {"ms_per_step_vjp": t_vjp, "ratio": t_vjp / (t_batch / args.steps),
+                        "note": "js_batch_step_vjp (each instance's js_step_vjp, recomputing its stage "
+                                "states) / one batched forward step, rank 0's instances"}}), flush=True)
     if dist is not None:
         dist.destroy_process_group()
 

@@ -275,6 +275,9 @@ struct js_batch {
   int ntiles = 0;
   long long cells = 0;
   bool states_set = false;
+  // reverse: instances spread over a few streams (each has its own workspace)
+  std::vector<cudaStream_t> rstreams;
+  std::vector<cudaEvent_t> revents;  // [0]: fork from the batch stream, [1..]: joins
 };
 
 // accessors of a context's internals (defined in js_host.cu)
@@ -289,6 +292,8 @@ extern "C" {
 void js_batch_destroy(js_batch* b) {
   if (!b) return;
   if (b->stream) cudaStreamSynchronize(b->stream); else cudaDeviceSynchronize();
+  for (cudaStream_t r : b->rstreams) cudaStreamDestroy(r);
+  for (cudaEvent_t e : b->revents) cudaEventDestroy(e);
   for (js_ctx* c : b->ctx) js_destroy(c);
   cudaFree(b->d_desc); cudaFree(b->d_tile0); cudaFree(b->d_ghost0); cudaFree(b->d_halo0);
   cudaFree(b->d_red); cudaFree(b->d_bar); cudaFree(b->d_err);
@@ -348,7 +353,8 @@ int js_batch_create(int count, const js_grid* grids, const js_params* params, co
       cudaMemcpy(b->d_ghost0, ghost0.data(), sizeof(long long) * (count + 1), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(b->d_halo0, halo0.data(), sizeof(long long) * (count + 1), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemset(b->d_bar, 0, 2 * sizeof(unsigned)) != cudaSuccess ||
-      cudaMemset(b->d_err, 0, sizeof(int)) != cudaSuccess) {
+      cudaMemset(b->d_err, 0, sizeof(int)) != cudaSuccess ||
+      cudaDeviceSynchronize() != cudaSuccess) {  // the batch stream may be non-blocking
     js_batch_destroy(b);
     return JS_ERR_CUDA;
   }
@@ -404,13 +410,36 @@ int js_batch_step(js_batch* b, double cfl, int n_steps, double* t_dev, double* d
 int js_batch_step_vjp(js_batch* b, double* const* U_n, const double* dt, double* const* lam_np1,
                       double* const* lam_n, double* const* p_bar) {
   if (!b || !U_n || !dt || !lam_np1 || !lam_n) return JS_ERR_ARG;
-  for (int k = 0; k < b->count; ++k) {
-    js_ctx* c = b->ctx[k];
-    js_set_stream(c, b->stream);
-    const int rc = js_step_vjp(c, U_n[k], dt[k], lam_np1[k], lam_n[k], p_bar ? p_bar[k] : nullptr);
-    if (rc != JS_OK) return rc;
+  // the instances are independent: up to kRevStreams of them run at once, each on its own
+  // stream forked from and joined back to the batch stream
+  constexpr int kRevStreams = 8;
+  const int ns = b->count < kRevStreams ? b->count : kRevStreams;
+  while ((int)b->rstreams.size() < ns) {
+    cudaStream_t r;
+    if (cudaStreamCreateWithFlags(&r, cudaStreamNonBlocking) != cudaSuccess) return JS_ERR_CUDA;
+    b->rstreams.push_back(r);
   }
-  return JS_OK;
+  while ((int)b->revents.size() < ns + 1) {
+    cudaEvent_t e;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return JS_ERR_CUDA;
+    b->revents.push_back(e);
+  }
+  if (cudaEventRecord(b->revents[0], b->stream) != cudaSuccess) return JS_ERR_CUDA;
+  for (int r = 0; r < ns; ++r)
+    if (cudaStreamWaitEvent(b->rstreams[r], b->revents[0], 0) != cudaSuccess) return JS_ERR_CUDA;
+  int rc = JS_OK;
+  for (int k = 0; k < b->count && rc == JS_OK; ++k) {
+    js_ctx* c = b->ctx[k];
+    js_set_stream(c, b->rstreams[k % ns]);
+    rc = js_step_vjp(c, U_n[k], dt[k], lam_np1[k], lam_n[k], p_bar ? p_bar[k] : nullptr);
+  }
+  for (int r = 0; r < ns; ++r) {
+    if (cudaEventRecord(b->revents[r + 1], b->rstreams[r]) != cudaSuccess ||
+        cudaStreamWaitEvent(b->stream, b->revents[r + 1], 0) != cudaSuccess)
+      return JS_ERR_CUDA;
+  }
+  for (int k = 0; k < b->count; ++k) js_set_stream(b->ctx[k], b->stream);
+  return rc;
 }
 
 int js_batch_test_timeout(js_batch* b, double budget_s) {

@@ -59,6 +59,8 @@ struct js_ctx {
   double* fadj = nullptr;    // 16 planes
   double* inflow_acc = nullptr;   // 16
   double* inflow_prim = nullptr;  // 16
+  double* inflow_host = nullptr;  // 16, pinned
+  bool inflow_dirty = true;       // inflow_prim to be uploaded
   double* qIb = nullptr;     // 4 per ghost
   // neural flux (js_set_neural)
   bool nn_on = false;
@@ -433,6 +435,7 @@ void js_destroy(js_ctx* c) {
   cudaFree(c->ibt_cell); cudaFree(c->ibt_ptr); cudaFree(c->ibt_ghost); cudaFree(c->ibt_w);
   cudaFree(c->Q); cudaFree(c->Qb); cudaFree(c->lam); cudaFree(c->P0); cudaFree(c->P1); cudaFree(c->Uacc);
   cudaFree(c->wsave); cudaFree(c->wsave_fwd); cudaFree(c->fadj);
+  if (c->inflow_host) cudaFreeHost(c->inflow_host);
   cudaFree(c->nnQ); cudaFree(c->nn_partial); cudaFree(c->nn_wsave);
   for (void* b : c->nn_buf) cudaFree(b); cudaFree(c->inflow_acc); cudaFree(c->inflow_prim); cudaFree(c->qIb);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
@@ -470,8 +473,11 @@ int js_create(const js_grid* grid, const js_params* params, const js_boundary* b
     return JS_ERR_NOMEM;
   }
   // padding never holds NaN garbage
+  // (a device-wide synchronisation: the context's stream may be a non-blocking one that does
+  // not wait for work on the legacy default stream)
   if (cudaMemset(c->N, 0, bytes) != cudaSuccess || cudaMemset(c->A, 0, bytes) != cudaSuccess ||
-      cudaMemset(c->B, 0, bytes) != cudaSuccess || cudaMemset(c->err, 0, sizeof(int)) != cudaSuccess) {
+      cudaMemset(c->B, 0, bytes) != cudaSuccess || cudaMemset(c->err, 0, sizeof(int)) != cudaSuccess ||
+      cudaDeviceSynchronize() != cudaSuccess) {
     js_destroy(c);
     return JS_ERR_CUDA;
   }
@@ -497,6 +503,7 @@ int js_set_params(js_ctx* c, const js_params* params, const js_boundary* bc) {
   if (!c || !params_valid(params, bc)) return JS_ERR_ARG;
   c->p = *params;
   c->b = *bc;
+  c->inflow_dirty = true;
   set_bc(c);
   return JS_OK;
 }
@@ -597,20 +604,20 @@ int adj_reserve(js_ctx* c) {
       {&c->Q, 5}, {&c->Qb, 5}, {&c->lam, 4}, {&c->P0, 4}, {&c->P1, 4}, {&c->Uacc, 4}};
   for (auto& b : bufs) {
     if (cudaMalloc(b.p, b.planes * pl) != cudaSuccess) return JS_ERR_NOMEM;
-    JS_CUDA(cudaMemset(*b.p, 0, b.planes * pl));
+    JS_CUDA(cudaMemsetAsync(*b.p, 0, b.planes * pl, c->stream));  // ordered with the caller's work
   }
   const size_t spl = sizeof(double) * (size_t)saved_plane(c);
   if (cudaMalloc(&c->wsave, 2 * 4 * 7 * spl) != cudaSuccess || cudaMalloc(&c->fadj, 16 * spl) != cudaSuccess)
     return JS_ERR_NOMEM;
-  JS_CUDA(cudaMemset(c->wsave, 0, 2 * 4 * 7 * spl));
-  JS_CUDA(cudaMemset(c->fadj, 0, 16 * spl));
+  JS_CUDA(cudaMemsetAsync(c->wsave, 0, 2 * 4 * 7 * spl, c->stream));
+  JS_CUDA(cudaMemsetAsync(c->fadj, 0, 16 * spl, c->stream));
   // internals stored by the forward stages 1, 2 of js_step_vjp (2D)
   if (c->g.ny > 1) {
     if (cudaMalloc(&c->wsave_fwd, 2 * 56 * spl) != cudaSuccess) {
       c->wsave_fwd = nullptr;
       return JS_ERR_NOMEM;
     }
-    JS_CUDA(cudaMemset(c->wsave_fwd, 0, 2 * 56 * spl));
+    JS_CUDA(cudaMemsetAsync(c->wsave_fwd, 0, 2 * 56 * spl, c->stream));
   }
   if (cudaMalloc(&c->inflow_acc, 16 * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&c->inflow_prim, 16 * sizeof(double)) != cudaSuccess ||
@@ -681,11 +688,20 @@ int adj_stage(js_ctx* c, const double* X, const double* Unext, double* Ub, doubl
   return JS_OK;
 }
 
+// the inflow states on the device for the reverse pass: uploaded from a pinned buffer when
+// they changed (js_create / js_set_params), so that reverse calls do not block the host
 int upload_inflow(js_ctx* c) {
-  double h[16];
+  if (!c->inflow_dirty) return JS_OK;
+  if (!c->inflow_host && cudaMallocHost(&c->inflow_host, 16 * sizeof(double)) != cudaSuccess) {
+    c->inflow_host = nullptr;
+    return JS_ERR_NOMEM;
+  }
+  // the previous upload from this buffer must have completed before it is rewritten
+  JS_CUDA(cudaStreamSynchronize(c->stream));
   for (int s = 0; s < 4; ++s)
-    for (int k = 0; k < 4; ++k) h[4 * s + k] = c->b.inflow[s][k];
-  JS_CUDA(cudaMemcpyAsync(c->inflow_prim, h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
+    for (int k = 0; k < 4; ++k) c->inflow_host[4 * s + k] = c->b.inflow[s][k];
+  JS_CUDA(cudaMemcpyAsync(c->inflow_prim, c->inflow_host, 16 * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  c->inflow_dirty = false;
   return JS_OK;
 }
 
@@ -797,7 +813,7 @@ int js_tape_reserve_ex(js_ctx* c, int n_slots, int flags) {
   while (c->tape.size() < need) {
     double* p = nullptr;
     if (cudaMalloc(&p, state_bytes(c)) != cudaSuccess) return JS_ERR_NOMEM;
-    if (cudaMemset(p, 0, state_bytes(c)) != cudaSuccess) { cudaFree(p); return JS_ERR_CUDA; }
+    if (cudaMemsetAsync(p, 0, state_bytes(c), c->stream) != cudaSuccess) { cudaFree(p); return JS_ERR_CUDA; }
     c->tape.push_back(p);
   }
   c->tape_weno = (flags & JS_TAPE_WENO) != 0 && c->g.ny > 1;
@@ -813,6 +829,7 @@ int js_tape_reserve_ex(js_ctx* c, int n_slots, int flags) {
       }
     }
   }
+  JS_CUDA(cudaStreamSynchronize(c->stream));
   return JS_OK;
 }
 
@@ -960,7 +977,7 @@ int js_set_neural(js_ctx* c, const double* w, double* w_bar, const double* norm,
     if (cudaMalloc(&c->nn_partial, sizeof(double) * js::NN_NPARAM * (size_t)n.nwblk) != cudaSuccess ||
         cudaMalloc(&c->nnQ, sizeof(double) * 4 * (size_t)c->lay.plane) != cudaSuccess)
       return JS_ERR_NOMEM;
-    JS_CUDA(cudaMemset(c->nnQ, 0, sizeof(double) * 4 * (size_t)c->lay.plane));
+    JS_CUDA(cudaMemsetAsync(c->nnQ, 0, sizeof(double) * 4 * (size_t)c->lay.plane, c->stream));
   }
   n.X = c->nn_buf[0];
   n.A1 = c->nn_buf[1];
@@ -985,8 +1002,9 @@ int js_set_neural(js_ctx* c, const double* w, double* w_bar, const double* norm,
       c->nn_wsave = nullptr;
       return JS_ERR_NOMEM;
     }
-    JS_CUDA(cudaMemset(c->nn_wsave, 0, internals_bytes(c)));
+    JS_CUDA(cudaMemsetAsync(c->nn_wsave, 0, internals_bytes(c), c->stream));
   }
+  JS_CUDA(cudaStreamSynchronize(c->stream));
   c->nn_on = true;
   return JS_OK;
 }
