@@ -11,6 +11,8 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
     config.addinivalue_line("markers", "slow: long-running CPU test")
+    config.addinivalue_line("markers", "fullrun: full-size, full-step-count GPU parity (tens of CPU minutes for "
+                                       "the oracle); runs only with JS_FULLRUN=1")
 
 
 def golden(name):
