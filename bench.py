@@ -320,9 +320,10 @@ def run_ours(args):
         neural = {"flops_per_cell_stage_network": NN_FLOPS_PER_CELL_STAGE,
                   "note": "network forward per stage: 2 face images (x faces, y faces) x 6336 multiply-adds "
                           "per face; ms per SSP-RK3 step with the network on, and the reverse step "
-                          "(js_step_vjp with the weight gradient)"}
-        for name, fp32 in (("fp32", True), ("fp64", False)):
-            solver.set_neural(w, norm, w_bar=wb, fp32=fp32)
+                          "(js_step_vjp with the weight gradient); bf16: layers 2-3 of the forward on the "
+                          "tensor cores, the rest FP32"}
+        for name in ("bf16", "fp32", "fp64"):
+            solver.set_neural(w, norm, w_bar=wb, precision=name)
             Uw = U.clone()
             solver.step(Uw, dt, 1)
             solver.step_vjp(U, dt, lam, lam_n=lam_out, p_bar=pbar)

@@ -150,14 +150,23 @@ int js_step_vjp_taped(js_ctx* ctx, int slot, double dt, const double* lam_np1, d
  *          js_step_vjp / js_step_vjp_taped ADDS the parameter gradient (summed in a fixed
  *          order: reproducible)
  *   norm   host array mean[4], sd[4] (> 0), scale[4] (copied)
- *   precision  JS_NN_F64 (FP64 network arithmetic) or JS_NN_F32 (FP32; the solver stays FP64)
+ *   precision  JS_NN_F64 (FP64 network arithmetic), JS_NN_F32 (FP32 on the CUDA cores) or
+ *          JS_NN_BF16 (the 16->32 and 32->4 layers of the forward pass on the tensor cores with
+ *          BF16 operands and FP32 accumulation, the rest FP32); the solver stays FP64
  * Applies to js_rhs, js_step, the taped steps and the reverse calls of this context (not to
  * js_batch_*).  The first call allocates the network workspace (before any stream capture).
  * Returns JS_ERR_ARG for a bad norm or precision, JS_ERR_NOMEM. */
 #define JS_NN_NPARAM 6388
 #define JS_NN_F64 0
 #define JS_NN_F32 1
+#define JS_NN_BF16 2
 int js_set_neural(js_ctx* ctx, const double* w, double* w_bar, const double* norm, int precision);
+
+/* The network of js_set_neural alone (its parameters, normalisation scale and precision) on one
+ * normalised image: X [4][H][W] (device, FP64) -> Y [4][H][W] = scale[k] * output channel k
+ * (device, FP64).  H * W may not exceed the context's face-image capacity (2 nx ny + nx + ny on 2D
+ * grids) or JS_ERR_ARG; JS_ERR_ARG also without the neural flux on.  Asynchronous. */
+int js_nn_eval(js_ctx* ctx, const double* X, int H, int W, double* Y);
 
 /* Block average (the downsampling that turns high-resolution states into the coarse
  * training targets of Sec. 2.4): out[4][ny/fy][nx/fx] (device) = the means of the fx x fy

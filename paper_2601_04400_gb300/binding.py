@@ -17,7 +17,7 @@ JS_OK, JS_ERR_ARG, JS_ERR_CUDA, JS_ERR_NONPHYSICAL, JS_ERR_TIMEOUT, JS_ERR_IB, J
 JS_NPARAM = 20
 JS_TAPE_WENO = 1
 JS_NN_NPARAM = 6388
-JS_NN_F64, JS_NN_F32 = 0, 1
+JS_NN_F64, JS_NN_F32, JS_NN_BF16 = 0, 1, 2
 
 _lib = None
 
@@ -64,6 +64,7 @@ SIGNATURES = {
     "js_tape_reserve_ex": (_I, [_P, _I, _I]),
     "js_set_neural": (_I, [_P, _P, _P, _P, _I]),
     "js_block_average": (_I, [_P, _I, _I, _I, _I, _P, _P]),
+    "js_nn_eval": (_I, [_P, _P, _I, _I, _P]),
     "js_step_taped": (_I, [_P, _P, _D, _I]),
     "js_step_vjp_taped": (_I, [_P, _I, _D, _P, _P, _P]),
     "js_set_tuning": (_I, [_P, _I]),
@@ -270,11 +271,12 @@ class Solver:
     def set_stream(self, stream=None):
         js_set_stream(self.ctx, stream)
 
-    def set_neural(self, w, norm=None, w_bar=None, fp32=False):
+    def set_neural(self, w, norm=None, w_bar=None, fp32=False, precision=None):
         """Neural flux on (w: float64 CUDA tensor of JS_NN_NPARAM parameters, kept by
         reference: later updates in place take effect; norm: mean[4], sd[4], scale[4] of the
         frame channels; w_bar: float64 CUDA tensor that reverse calls add the parameter
-        gradient to, or None; fp32: network arithmetic in FP32) or off (w = None)."""
+        gradient to, or None; precision: "fp64", "fp32" or "bf16" (tensor-core layers);
+        fp32=True is precision="fp32") or off (w = None)."""
         if w is None:
             _check(lib().js_set_neural(self.ctx, None, None, None, 0), "js_set_neural")
             self._nn = None
@@ -282,9 +284,10 @@ class Solver:
         if w.numel() != JS_NN_NPARAM or (w_bar is not None and w_bar.numel() != JS_NN_NPARAM):
             raise ValueError("w and w_bar hold %d parameters" % JS_NN_NPARAM)
         nm = np.ascontiguousarray(np.asarray(norm, dtype=np.float64).reshape(12))
+        prec = precision or ("fp32" if fp32 else "fp64")
+        code = {"fp64": JS_NN_F64, "fp32": JS_NN_F32, "bf16": JS_NN_BF16}[prec]
         _check(lib().js_set_neural(self.ctx, _ptr(w), None if w_bar is None else _ptr(w_bar),
-                                   nm.ctypes.data_as(C.c_void_p), JS_NN_F32 if fp32 else JS_NN_F64),
-               "js_set_neural")
+                                   nm.ctypes.data_as(C.c_void_p), code), "js_set_neural")
         self._nn = (w, w_bar, nm)  # keep the device buffers alive while the library uses them
 
     def set_tuning(self, variant):
@@ -333,6 +336,14 @@ class Solver:
         (2D grids), so that step_vjp_taped skips their recompute."""
         _check(lib().js_tape_reserve_ex(self.ctx, int(n_slots), JS_TAPE_WENO if weno else 0),
                "js_tape_reserve_ex")
+
+    def nn_eval(self, X):
+        """The neural network alone on a normalised image X [4, H, W] (float64 CUDA)."""
+        import torch
+        X = X.contiguous()
+        Y = torch.empty_like(X)
+        _check(lib().js_nn_eval(self.ctx, _ptr(X), X.shape[1], X.shape[2], _ptr(Y)), "js_nn_eval")
+        return Y
 
     def tape_weno_bytes(self, n_slots):
         """Device bytes the WENO5 internals of n_slots tape slots take (0 on 1D grids)."""

@@ -952,7 +952,7 @@ int js_set_neural(js_ctx* c, const double* w, double* w_bar, const double* norm,
     c->nn_on = false;
     return JS_OK;
   }
-  if (!norm || (precision != JS_NN_F64 && precision != JS_NN_F32)) return JS_ERR_ARG;
+  if (!norm || (precision != JS_NN_F64 && precision != JS_NN_F32 && precision != JS_NN_BF16)) return JS_ERR_ARG;
   for (int k = 0; k < 4; ++k)
     if (!(norm[4 + k] > 0.0) || !std::isfinite(norm[k]) || !std::isfinite(norm[8 + k])) return JS_ERR_ARG;
   js::NnArgs& n = c->nn;
@@ -987,7 +987,9 @@ int js_set_neural(js_ctx* c, const double* w, double* w_bar, const double* norm,
   n.G16 = c->nn_buf[5];
   n.G32 = c->nn_buf[6];
   n.partial = c->nn_partial;
-  n.fp32 = (precision == JS_NN_F32) ? 1 : 0;
+  n.fp32 = (precision != JS_NN_F64) ? 1 : 0;
+  n.bf16 = (precision == JS_NN_BF16) ? 1 : 0;
+  n.err = c->err;
   n.w = w;
   n.w_bar = w_bar;
   for (int k = 0; k < 4; ++k) {
@@ -1006,5 +1008,13 @@ int js_set_neural(js_ctx* c, const double* w, double* w_bar, const double* norm,
   }
   JS_CUDA(cudaStreamSynchronize(c->stream));
   c->nn_on = true;
+  return JS_OK;
+}
+
+int js_nn_eval(js_ctx* c, const double* X, int H, int W, double* Y) {
+  if (!c || !c->nn_on || !X || !Y || H < 1 || W < 1) return JS_ERR_ARG;
+  const long long cap = c->nn.pix0 + (long long)c->nn.H[1] * c->nn.W[1];
+  if ((long long)H * W > cap) return JS_ERR_ARG;
+  JS_CUDA(js::nn_eval(c->nn, X, H, W, Y, c->stream));
   return JS_OK;
 }

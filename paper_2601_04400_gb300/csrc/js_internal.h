@@ -106,6 +106,8 @@ struct NnArgs {
   const double* wsave;
   long long splane;
   int tpitch;
+  int bf16;                   // layers 2 and 3 on the tensor cores (BF16 operands, FP32 accumulate)
+  int* err;                   // device error flag (bounded waits of the tensor-core layers)
 };
 
 // forward: images of the stage input (primitives Q, plane qplane) and the network, into T3
@@ -117,6 +119,8 @@ cudaError_t nn_apply(const NnArgs& n, const StageArgs& a, bool rhs, cudaStream_t
 // reverse: recompute the network on a.Q, seed with the face-flux adjoints of a.lam, back-
 // propagate (parameter gradient into n.w_bar), add the face-state adjoints to a.fadj
 cudaError_t nn_reverse(const NnArgs& n, const AdjArgs& a, cudaStream_t s);
+// the network alone on one image X[4][H][W] (FP64, device) -> scaled output Y[4][H][W]
+cudaError_t nn_eval(const NnArgs& n, const double* X, int H, int W, double* Y, cudaStream_t s);
 // out[4][ny/fy][nx/fx] = means of fx x fy blocks of U[4][ny][nx]
 cudaError_t launch_block_average(const double* U, int nx, int ny, int fx, int fy, double* out, cudaStream_t s);
 

@@ -22,12 +22,15 @@
 // Arithmetic type T: double (FP64, the oracle's precision) or float (FP32 on the CUDA
 // cores; the network is a dense contraction of 6336 multiply-adds per face, which FP64
 // would make about 20x the cost of the FP64 solver it corrects).
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <cstdint>
 #include <type_traits>
 
 #include "js_device.cuh"
 #include "js_internal.h"
+#include "js_stage.cuh"  // smem_u32, mbar_init, mbar_wait
 
 namespace js {
 
@@ -416,6 +419,164 @@ __global__ void __launch_bounds__(NTHR) nn_wgrad_f32_kernel(NnArgs n, const void
   if (threadIdx.x < COUT) part[COUT * CIN * 9 + threadIdx.x] = (double)bacc;
 }
 
+// ---------------------------------------------------------------------------------------
+// BF16 tensor-core layer (tcgen05): a 3x3 convolution as an implicit GEMM
+//   D[pixel][co] = sum over taps (ky, kx) and input channels ci of
+//                  A_tap[pixel][ci] * W_tap[co][ci],   A_tap[pixel] = input[pixel + (ky-1, kx-1)]
+// A block computes M = 128 consecutive pixels of one image row.  The haloed input rows (3 x 130
+// pixels) sit in shared memory as BF16 in the no-swizzle K-major core-matrix layout
+// [channel group of 8][row][column][8 channels] (a core matrix = 8 consecutive pixels x 16 bytes),
+// so every tap's A operand is the same buffer at a shifted start address; the weights per tap as
+// [channel group][co][8 channels].  One thread issues, per tap and group of 16 channels, a
+// tcgen05.mma (kind::f16, M = 128, N = output channels rounded up to 16, K = 16) accumulating in
+// FP32 in tensor memory; tcgen05.commit signals an mbarrier (bounded wait); each warp then reads
+// its 32 accumulator lanes with tcgen05.ld and applies bias and activation.
+// ---------------------------------------------------------------------------------------
+constexpr int TC_M = 128;                 // pixels per block
+constexpr int TC_COLS = TC_M + 2;         // with the halo
+// shared bytes reserved for the A tile: generous, so that every operand read stays inside the
+// block's allocation whatever the input width
+constexpr int TC_AREGION = 112 * 1024;
+
+__device__ __forceinline__ uint64_t umma_smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;   // leading (K-direction) core-matrix offset
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;   // stride (M/N-direction) 8-row-group offset
+  d |= (uint64_t)1 << 46;                        // descriptor version of tcgen05; no swizzle
+  return d;
+}
+// kind::f16 instruction descriptor: FP32 accumulator, BF16 A and B, both K-major, M x N
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, int acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(unsigned long long* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t r[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+
+template <int CIN, int COUT, int ACT>
+__global__ void __launch_bounds__(128) nn_conv_tc_kernel(NnArgs n, const void* in, void* out, int woff) {
+  static_assert(CIN % 16 == 0, "input channels in groups of 16 (K of one MMA)");
+  constexpr int N = (COUT + 15) / 16 * 16;   // MMA N (multiple of 16 for M = 128)
+  constexpr int KG = CIN / 8;                // 8-channel groups
+  constexpr int APLANE = 3 * TC_COLS * 16;   // bytes of one channel group of the A tile
+  constexpr int BTAP = KG * N * 16;          // bytes of one tap of the weights
+  static_assert(KG * APLANE <= TC_AREGION, "A tile");
+  extern __shared__ __align__(16) unsigned char smem_raw[];  // 16-byte rows: no swizzle
+  unsigned char* sA = smem_raw;
+  unsigned char* sB = smem_raw + TC_AREGION;
+  float* sbias = reinterpret_cast<float*>(sB + 9 * BTAP);
+  __shared__ __align__(8) unsigned long long bar;
+  __shared__ uint32_t tmem_base;
+  const int d = blockIdx.z;
+  const int H = n.H[d], Wd = n.W[d];
+  const int h = blockIdx.y, x0 = blockIdx.x * TC_M;
+  if (h >= H || x0 >= Wd) return;  // uniform per block, before any allocation
+  const long long pix = (long long)H * Wd;
+  const float* X = chan_img<float>(in, CIN, d, n.pix0);
+  float* Y = chan_img<float>(out, COUT, d, n.pix0);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_u32(&tmem_base))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) mbar_init(&bar);
+  __nv_bfloat16* B16 = reinterpret_cast<__nv_bfloat16*>(sB);
+  for (int k = tid; k < 9 * CIN * N; k += 128) {
+    const int tap = k / (CIN * N), r = k % (CIN * N), ci = r / N, co = r % N;
+    const float v = (co < COUT) ? (float)n.w[woff + (co * CIN + ci) * 9 + tap] : 0.0f;
+    B16[tap * (BTAP / 2) + ((ci >> 3) * N + co) * 8 + (ci & 7)] = __float2bfloat16_rn(v);
+  }
+  for (int k = tid; k < COUT; k += 128) sbias[k] = (float)n.w[woff + COUT * CIN * 9 + k];
+  __nv_bfloat16* A16 = reinterpret_cast<__nv_bfloat16*>(sA);
+  for (int k = tid; k < CIN * 3 * TC_COLS; k += 128) {
+    const int ci = k / (3 * TC_COLS), r = k % (3 * TC_COLS), row = r / TC_COLS, col = r % TC_COLS;
+    const int gy = h + row - 1, gx = x0 + col - 1;
+    const float v = (gy >= 0 && gy < H && gx >= 0 && gx < Wd) ? X[ci * pix + (long long)gy * Wd + gx] : 0.0f;
+    A16[(ci >> 3) * (APLANE / 2) + (row * TC_COLS + col) * 8 + (ci & 7)] = __float2bfloat16_rn(v);
+  }
+  // generic-proxy shared stores must be visible to the tensor core (async proxy)
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  if (tid == 0) {
+    constexpr uint32_t idesc = umma_idesc_bf16(TC_M, N);
+    const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+    int acc = 0;
+    for (int tap = 0; tap < 9; ++tap) {
+      const int ky = tap / 3, kx = tap % 3;
+      for (int kc = 0; kc < KG / 2; ++kc) {
+        const uint64_t ad = umma_smem_desc(a0 + 2 * kc * APLANE + (ky * TC_COLS + kx) * 16, APLANE, 128);
+        const uint64_t bd = umma_smem_desc(b0 + tap * BTAP + 2 * kc * N * 16, N * 16, 128);
+        umma_bf16(tmem, ad, bd, idesc, acc);
+        acc = 1;
+      }
+    }
+    umma_commit(&bar);
+  }
+  constexpr long long kBudget = 2000000000LL;  // about one second of SM clock
+  bool ok = mbar_wait(&bar, 0, kBudget);
+  if (!ok) {
+    if (tid == 0) atomicOr(n.err, ERR_TIMEOUT_BIT);
+    mbar_wait(&bar, 0, kBudget);  // drain before the accumulator is released
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (ok) {
+    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+    const int gx = x0 + warp * 32 + lane;
+#pragma unroll
+    for (int c0 = 0; c0 < N; c0 += 16) {
+      uint32_t r[16];
+      tmem_ld16(taddr + c0, r);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (gx < Wd) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int co = c0 + j;
+          if (co < COUT) {
+            const float v = __uint_as_float(r[j]) + sbias[co];
+            Y[co * pix + (long long)h * Wd + gx] = (ACT == 0) ? (v > 0.0f ? v : 0.0f) : tanhf(v);
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
+}
+
+// network input from an FP64 image / scaled FP64 output (js_nn_eval)
+template <class T>
+__global__ void nn_load_kernel(const double* __restrict__ Xd, T* __restrict__ X, long long n4) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n4) X[t] = (T)Xd[t];
+}
+template <class T>
+__global__ void nn_store_kernel(const T* __restrict__ T3, double* __restrict__ Y, long long pix, NnArgs n) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < 4 * pix) Y[t] = n.scale[t / pix] * (double)T3[t];
+}
+
 // stage output (or RHS) minus the neural flux divergence on fluid cells
 template <class T>
 __global__ void nn_apply_kernel(NnArgs n, StageArgs a, int rhs) {
@@ -720,14 +881,58 @@ cudaError_t wgrad(const NnArgs& n, const void* gout, const void* ain, int woff, 
   return cudaGetLastError();
 }
 
+template <int CIN, int COUT, int ACT>
+cudaError_t conv_tc(const NnArgs& n, const void* in, void* out, int woff, cudaStream_t s) {
+  constexpr int N = (COUT + 15) / 16 * 16;
+  // (+ slack past the weights: operand reads stay inside the allocation whatever the offsets)
+  const size_t sm = TC_AREGION + 9 * (CIN / 8) * N * 16 + COUT * sizeof(float) + 4096;
+  auto k = nn_conv_tc_kernel<CIN, COUT, ACT>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  int W = n.W[0], H = n.H[0];
+  if (n.nimg > 1) {
+    W = W > n.W[1] ? W : n.W[1];
+    H = H > n.H[1] ? H : n.H[1];
+  }
+  k<<<dim3(cdiv(W, TC_M), H, n.nimg), 128, sm, s>>>(n, in, out, woff);
+  return cudaGetLastError();
+}
+
+// the three layers on n.X -> n.T3
+template <class T>
+cudaError_t layers_t(const NnArgs& n, cudaStream_t s) {
+  cudaError_t e;
+  if ((e = conv<T, 4, 16, 0>(n, n.X, n.A1, NN_OFF1, s)) != cudaSuccess) return e;
+  if (std::is_same<T, float>::value && n.bf16) {
+    if ((e = conv_tc<16, 32, 0>(n, n.A1, n.A2, NN_OFF2, s)) != cudaSuccess) return e;
+    return conv_tc<32, 4, 1>(n, n.A2, n.T3, NN_OFF3, s);
+  }
+  if ((e = conv<T, 16, 32, 0>(n, n.A1, n.A2, NN_OFF2, s)) != cudaSuccess) return e;
+  return conv<T, 32, 4, 1>(n, n.A2, n.T3, NN_OFF3, s);
+}
+
 template <class T>
 cudaError_t forward_t(const NnArgs& n, const double* Q, long long qplane, cudaStream_t s) {
   nn_image_kernel<T><<<dim3(cdiv(max_pix(n), 256), n.nimg), 256, 0, s>>>(n, Q, qplane);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  if ((e = conv<T, 4, 16, 0>(n, n.X, n.A1, NN_OFF1, s)) != cudaSuccess) return e;
-  if ((e = conv<T, 16, 32, 0>(n, n.A1, n.A2, NN_OFF2, s)) != cudaSuccess) return e;
-  return conv<T, 32, 4, 1>(n, n.A2, n.T3, NN_OFF3, s);
+  return layers_t<T>(n, s);
+}
+
+template <class T>
+cudaError_t eval_t(const NnArgs& n0, const double* X, int H, int W, double* Y, cudaStream_t s) {
+  NnArgs n = n0;
+  n.nimg = 1;
+  n.H[0] = H;
+  n.W[0] = W;
+  n.pix0 = (long long)H * W;
+  const long long pix = n.pix0;
+  nn_load_kernel<T><<<cdiv(4 * pix, 256), 256, 0, s>>>(X, static_cast<T*>(n.X), 4 * pix);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if ((e = layers_t<T>(n, s)) != cudaSuccess) return e;
+  nn_store_kernel<T><<<cdiv(4 * pix, 256), 256, 0, s>>>(static_cast<const T*>(n.T3), Y, pix, n);
+  return cudaGetLastError();
 }
 
 template <class T>
@@ -765,6 +970,10 @@ cudaError_t nn_prims(const double* U, double* Q, const Lay& lay, double gamma, c
 
 cudaError_t nn_forward(const NnArgs& n, const double* Q, long long qplane, cudaStream_t s) {
   return n.fp32 ? forward_t<float>(n, Q, qplane, s) : forward_t<double>(n, Q, qplane, s);
+}
+
+cudaError_t nn_eval(const NnArgs& n, const double* X, int H, int W, double* Y, cudaStream_t s) {
+  return n.fp32 ? eval_t<float>(n, X, H, W, Y, s) : eval_t<double>(n, X, H, W, Y, s);
 }
 
 cudaError_t nn_apply(const NnArgs& n, const StageArgs& a, bool rhs, cudaStream_t s) {
