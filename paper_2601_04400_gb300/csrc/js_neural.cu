@@ -434,9 +434,8 @@ __global__ void __launch_bounds__(NTHR) nn_wgrad_f32_kernel(NnArgs n, const void
 // ---------------------------------------------------------------------------------------
 constexpr int TC_M = 128;                 // pixels per block
 constexpr int TC_COLS = TC_M + 2;         // with the halo
-// shared bytes reserved for the A tile: generous, so that every operand read stays inside the
-// block's allocation whatever the input width
-constexpr int TC_AREGION = 112 * 1024;
+// shared bytes of the A tile: 3 rows x 130 pixels x 32 channels (the widest input) in BF16
+constexpr int TC_AREGION = 4 * 3 * TC_COLS * 16;
 
 __device__ __forceinline__ uint64_t umma_smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
   uint64_t d = (uint64_t)((addr >> 4) & 0x3FFFu);
@@ -884,8 +883,7 @@ cudaError_t wgrad(const NnArgs& n, const void* gout, const void* ain, int woff, 
 template <int CIN, int COUT, int ACT>
 cudaError_t conv_tc(const NnArgs& n, const void* in, void* out, int woff, cudaStream_t s) {
   constexpr int N = (COUT + 15) / 16 * 16;
-  // (+ slack past the weights: operand reads stay inside the allocation whatever the offsets)
-  const size_t sm = TC_AREGION + 9 * (CIN / 8) * N * 16 + COUT * sizeof(float) + 4096;
+  const size_t sm = TC_AREGION + 9 * (CIN / 8) * N * 16 + COUT * sizeof(float);
   auto k = nn_conv_tc_kernel<CIN, COUT, ACT>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;

@@ -3,9 +3,10 @@ tcgen05 implicit GEMMs, BF16 operands, FP32 accumulation) and js_nn_eval.
 
 * js_nn_eval in FP64 equals the oracle's network; in FP32 within FP32 rounding.
 * BF16: equal to a CPU emulation of the same arithmetic (torch: FP32 first layer, inputs and
-  weights of layers 2 and 3 rounded to BF16, FP32 accumulation) within 2e-3 of the output
-  range -- rounding of values that sit on a BF16 boundary and the summation order differ; a
-  wrong operand layout gives errors of order one.  Images span several 128-pixel blocks with a
+  weights of layers 2 and 3 rounded to BF16, FP32 accumulation): the median difference at
+  FP32 rounding, the 99th percentile within 1e-3 and every output within 1e-2 of the output
+  range (a layer input on a BF16 rounding boundary may round the other way); a wrong operand
+  layout gives errors of order one everywhere.  Images span several 128-pixel blocks with a
   ragged tail, a block narrower than 128 and a single row.
 * The solver with the BF16 network: RHS within 3e-2 of the network's contribution of the
   oracle (FP64 network), the rest at the FP64 bar."""
@@ -86,7 +87,11 @@ def test_bf16_tensor_core_layers_match_emulation(env, shape):
     assert s.status() == 0
     emu = _emulate_bf16(torch, w, X, NORM[8:])
     span = np.abs(emu).max()
-    assert np.abs(Y - emu).max() <= 2e-3 * span
+    d = np.abs(Y - emu)
+    # almost every output equals the emulation to FP32 accumulation rounding; a layer input that
+    # sits on a BF16 rounding boundary may round the other way (one BF16 step, 2^-8 relative)
+    assert np.median(d) <= 1e-5 * span and np.quantile(d, 0.99) <= 1e-3 * span
+    assert d.max() <= 1e-2 * span
     with O.neural(w, NORM):
         ref = O.nn_eval(X)
     # BF16 against the exact network: of the order of the BF16 rounding
