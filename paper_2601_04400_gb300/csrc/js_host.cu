@@ -68,6 +68,7 @@ struct js_ctx {
   double* nnQ = nullptr;        // primitives of the stage input (4 planes)
   double* nn_wsave = nullptr;   // WENO5 internals of the current stage (2D; 56 planes)
   void* nn_buf[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  void* nn_bf16[2] = {nullptr, nullptr};  // BF16 pixel-major activations (16 and 32 channels)
   double* nn_partial = nullptr;
   int variant = 0;  // stage-kernel tile shape (js_set_tuning)
   std::vector<std::pair<const double*, js::TensorMap128>> tmaps;  // TMA maps of stage inputs
@@ -437,7 +438,8 @@ void js_destroy(js_ctx* c) {
   cudaFree(c->wsave); cudaFree(c->wsave_fwd); cudaFree(c->fadj);
   if (c->inflow_host) cudaFreeHost(c->inflow_host);
   cudaFree(c->nnQ); cudaFree(c->nn_partial); cudaFree(c->nn_wsave);
-  for (void* b : c->nn_buf) cudaFree(b); cudaFree(c->inflow_acc); cudaFree(c->inflow_prim); cudaFree(c->qIb);
+  for (void* b : c->nn_buf) cudaFree(b);
+  for (void* b : c->nn_bf16) cudaFree(b); cudaFree(c->inflow_acc); cudaFree(c->inflow_prim); cudaFree(c->qIb);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   for (double* t : c->tape) cudaFree(t);
   for (double* t : c->tape_w) cudaFree(t);
@@ -987,6 +989,13 @@ int js_set_neural(js_ctx* c, const double* w, double* w_bar, const double* norm,
   n.G16 = c->nn_buf[5];
   n.G32 = c->nn_buf[6];
   n.partial = c->nn_partial;
+  if (precision == JS_NN_BF16 && !c->nn_bf16[0]) {
+    if (cudaMalloc(&c->nn_bf16[0], 2 * 16 * (size_t)pix) != cudaSuccess ||
+        cudaMalloc(&c->nn_bf16[1], 2 * 32 * (size_t)pix) != cudaSuccess)
+      return JS_ERR_NOMEM;
+  }
+  n.A1h = c->nn_bf16[0];
+  n.A2h = c->nn_bf16[1];
   n.fp32 = (precision != JS_NN_F64) ? 1 : 0;
   n.bf16 = (precision == JS_NN_BF16) ? 1 : 0;
   n.err = c->err;

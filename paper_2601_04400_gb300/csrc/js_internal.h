@@ -107,6 +107,8 @@ struct NnArgs {
   long long splane;
   int tpitch;
   int bf16;                   // layers 2 and 3 on the tensor cores (BF16 operands, FP32 accumulate)
+  void* A1h;                  // BF16 copies of the activations of layers 1 and 2, pixel-major with
+  void* A2h;                  //   the channels contiguous ([image][H][W][C]), tensor-core inputs
   int* err;                   // device error flag (bounded waits of the tensor-core layers)
 };
 

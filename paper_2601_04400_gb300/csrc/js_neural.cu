@@ -187,7 +187,8 @@ constexpr int PB = 2;                 // pixels per thread (along the tile row)
 constexpr int NTHR_F = NTHR / PB;     // 128
 
 template <int CIN, int COUT, int ACT>
-__global__ void __launch_bounds__(NTHR_F) nn_conv_f32_kernel(NnArgs n, const void* in, void* out, int woff) {
+__global__ void __launch_bounds__(NTHR_F) nn_conv_f32_kernel(NnArgs n, const void* in, void* out, int woff,
+                                                             void* outh) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   static_assert(COUT % 4 == 0, "output channels in groups of 4");
   float* sw = reinterpret_cast<float*>(smem_raw);  // [CIN*9][COUT]
@@ -250,7 +251,19 @@ __global__ void __launch_bounds__(NTHR_F) nn_conv_f32_kernel(NnArgs n, const voi
 #pragma unroll
       for (int co = 0; co < COUT; ++co) {
         const float v = acc[q][co];
-        Y[co * pix + o] = (ACT == 0) ? (v > 0.0f ? v : 0.0f) : tanhf(v);
+        acc[q][co] = (ACT == 0) ? (v > 0.0f ? v : 0.0f) : tanhf(v);
+        Y[co * pix + o] = acc[q][co];
+      }
+      if (outh) {
+        // BF16 pixel-major copy (the tensor-core layer's input), 8 channels per 16-byte store
+        __nv_bfloat16* Yh = static_cast<__nv_bfloat16*>(outh) + (d == 0 ? 0LL : (long long)COUT * n.pix0);
+#pragma unroll
+        for (int c8 = 0; c8 < COUT / 8; ++c8) {
+          __align__(16) __nv_bfloat16 v8[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) v8[e] = __float2bfloat16_rn(acc[q][8 * c8 + e]);
+          *reinterpret_cast<uint4*>(Yh + o * COUT + 8 * c8) = *reinterpret_cast<const uint4*>(v8);
+        }
       }
     }
   }
@@ -434,7 +447,7 @@ __global__ void __launch_bounds__(NTHR) nn_wgrad_f32_kernel(NnArgs n, const void
 // ---------------------------------------------------------------------------------------
 constexpr int TC_M = 128;                 // pixels per block
 constexpr int TC_COLS = TC_M + 2;         // with the halo
-// shared bytes of the A tile: 3 rows x 130 pixels x 32 channels (the widest input) in BF16
+// shared bytes of the input row ring: 3 rows x 130 pixels x 32 channels (the widest input), BF16
 constexpr int TC_AREGION = 4 * 3 * TC_COLS * 16;
 
 __device__ __forceinline__ uint64_t umma_smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
@@ -468,27 +481,35 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t r[16]) {
       : "r"(taddr));
 }
 
+// A block owns work items of one 128-pixel-wide column strip and TC_ROWS output rows.  It loads
+// the weights and allocates tensor memory once, then walks its rows keeping the three input rows
+// it needs in a ring of row slots: each output row loads one new input row (8 channels of a pixel
+// per thread, stored as one 16-byte vector), issues the MMAs, waits, and stores the row.
+constexpr int TC_ROWS = 16;
+
 template <int CIN, int COUT, int ACT>
-__global__ void __launch_bounds__(128) nn_conv_tc_kernel(NnArgs n, const void* in, void* out, int woff) {
+__global__ void __launch_bounds__(128) nn_conv_tc_kernel(NnArgs n, const void* inh, void* out, int woff,
+                                                         void* outh) {
   static_assert(CIN % 16 == 0, "input channels in groups of 16 (K of one MMA)");
   constexpr int N = (COUT + 15) / 16 * 16;   // MMA N (multiple of 16 for M = 128)
   constexpr int KG = CIN / 8;                // 8-channel groups
-  constexpr int APLANE = 3 * TC_COLS * 16;   // bytes of one channel group of the A tile
+  constexpr int GSTRIDE = TC_COLS * 16;      // bytes of one channel group of one row slot
+  constexpr int SLOT = KG * GSTRIDE;         // bytes of one input row slot
   constexpr int BTAP = KG * N * 16;          // bytes of one tap of the weights
-  static_assert(KG * APLANE <= TC_AREGION, "A tile");
+  static_assert(3 * SLOT <= TC_AREGION, "row slots");
   extern __shared__ __align__(16) unsigned char smem_raw[];  // 16-byte rows: no swizzle
   unsigned char* sA = smem_raw;
   unsigned char* sB = smem_raw + TC_AREGION;
   float* sbias = reinterpret_cast<float*>(sB + 9 * BTAP);
   __shared__ __align__(8) unsigned long long bar;
   __shared__ uint32_t tmem_base;
-  const int d = blockIdx.z;
-  const int H = n.H[d], Wd = n.W[d];
-  const int h = blockIdx.y, x0 = blockIdx.x * TC_M;
-  if (h >= H || x0 >= Wd) return;  // uniform per block, before any allocation
-  const long long pix = (long long)H * Wd;
-  const float* X = chan_img<float>(in, CIN, d, n.pix0);
-  float* Y = chan_img<float>(out, COUT, d, n.pix0);
+  int nxs[2], nys[2];
+  for (int d = 0; d < 2; ++d) {
+    nxs[d] = (d < n.nimg) ? (n.W[d] + TC_M - 1) / TC_M : 0;
+    nys[d] = (d < n.nimg) ? (n.H[d] + TC_ROWS - 1) / TC_ROWS : 0;
+  }
+  const int items0 = nxs[0] * nys[0], items = items0 + nxs[1] * nys[1];
+  if ((int)blockIdx.x >= items) return;  // uniform per block, before any allocation
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_u32(&tmem_base))
@@ -503,59 +524,102 @@ __global__ void __launch_bounds__(128) nn_conv_tc_kernel(NnArgs n, const void* i
     B16[tap * (BTAP / 2) + ((ci >> 3) * N + co) * 8 + (ci & 7)] = __float2bfloat16_rn(v);
   }
   for (int k = tid; k < COUT; k += 128) sbias[k] = (float)n.w[woff + COUT * CIN * 9 + k];
-  __nv_bfloat16* A16 = reinterpret_cast<__nv_bfloat16*>(sA);
-  for (int k = tid; k < CIN * 3 * TC_COLS; k += 128) {
-    const int ci = k / (3 * TC_COLS), r = k % (3 * TC_COLS), row = r / TC_COLS, col = r % TC_COLS;
-    const int gy = h + row - 1, gx = x0 + col - 1;
-    const float v = (gy >= 0 && gy < H && gx >= 0 && gx < Wd) ? X[ci * pix + (long long)gy * Wd + gx] : 0.0f;
-    A16[(ci >> 3) * (APLANE / 2) + (row * TC_COLS + col) * 8 + (ci & 7)] = __float2bfloat16_rn(v);
-  }
-  // generic-proxy shared stores must be visible to the tensor core (async proxy)
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
-  if (tid == 0) {
-    constexpr uint32_t idesc = umma_idesc_bf16(TC_M, N);
-    const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
-    int acc = 0;
-    for (int tap = 0; tap < 9; ++tap) {
-      const int ky = tap / 3, kx = tap % 3;
-      for (int kc = 0; kc < KG / 2; ++kc) {
-        const uint64_t ad = umma_smem_desc(a0 + 2 * kc * APLANE + (ky * TC_COLS + kx) * 16, APLANE, 128);
-        const uint64_t bd = umma_smem_desc(b0 + tap * BTAP + 2 * kc * N * 16, N * 16, 128);
-        umma_bf16(tmem, ad, bd, idesc, acc);
-        acc = 1;
-      }
-    }
-    umma_commit(&bar);
-  }
+  const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+  constexpr uint32_t idesc = umma_idesc_bf16(TC_M, N);
   constexpr long long kBudget = 2000000000LL;  // about one second of SM clock
-  bool ok = mbar_wait(&bar, 0, kBudget);
-  if (!ok) {
-    if (tid == 0) atomicOr(n.err, ERR_TIMEOUT_BIT);
-    mbar_wait(&bar, 0, kBudget);  // drain before the accumulator is released
-  }
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (ok) {
-    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
-    const int gx = x0 + warp * 32 + lane;
+  unsigned phase = 0;
+  bool ok = true;
+  for (int it = blockIdx.x; it < items && ok; it += gridDim.x) {
+    const int d = (it < items0) ? 0 : 1;
+    const int il = (d == 0) ? it : it - items0;
+    const int x0 = (il % nxs[d]) * TC_M, h0 = (il / nxs[d]) * TC_ROWS;
+    const int H = n.H[d], Wd = n.W[d];
+    const int h1 = (h0 + TC_ROWS < H) ? h0 + TC_ROWS : H;
+    const long long pix = (long long)H * Wd;
+    const uint4* Xh = reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(inh) +
+                                                     (d == 0 ? 0LL : (long long)CIN * n.pix0));
+    float* Y = chan_img<float>(out, COUT, d, n.pix0);
+    __nv_bfloat16* Yh = outh ? static_cast<__nv_bfloat16*>(outh) + (d == 0 ? 0LL : (long long)COUT * n.pix0)
+                             : nullptr;
+    // input row r (zeros outside the image) into its ring slot: 16-byte copies of 8 channels
+    // of a pixel from the BF16 pixel-major input (consecutive threads: consecutive 16 bytes)
+    auto load_row = [&](int r) {
+      unsigned char* slot = sA + ((r + 3) % 3) * SLOT;
+      for (int k = tid; k < KG * TC_COLS; k += 128) {
+        const int col = k / KG, g = k % KG, gx = x0 + col - 1;
+        const bool inside = r >= 0 && r < H && gx >= 0 && gx < Wd;
+        const uint4 v = inside ? Xh[((long long)r * Wd + gx) * KG + g] : make_uint4(0u, 0u, 0u, 0u);
+        *reinterpret_cast<uint4*>(slot + g * GSTRIDE + col * 16) = v;
+      }
+    };
+    load_row(h0 - 1);
+    load_row(h0);
+    for (int h = h0; h < h1; ++h) {
+      load_row(h + 1);
+      // generic-proxy shared stores must be visible to the tensor core (async proxy)
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (tid == 0) {
+        int acc = 0;
+        for (int tap = 0; tap < 9; ++tap) {
+          const int ky = tap / 3, kx = tap % 3;
+          const uint32_t slot = a0 + ((h + ky - 1 + 3) % 3) * SLOT;
+          for (int kc = 0; kc < KG / 2; ++kc) {
+            const uint64_t ad = umma_smem_desc(slot + 2 * kc * GSTRIDE + kx * 16, GSTRIDE, 128);
+            const uint64_t bd = umma_smem_desc(b0 + tap * BTAP + 2 * kc * N * 16, N * 16, 128);
+            umma_bf16(tmem, ad, bd, idesc, acc);
+            acc = 1;
+          }
+        }
+        umma_commit(&bar);
+      }
+      // every thread waits (bounded); the outcome is made uniform so that the block leaves the
+      // loop together on a timeout
+      ok = __syncthreads_and(mbar_wait(&bar, phase, kBudget) ? 1 : 0) != 0;
+      if (!ok) {
+        if (tid == 0) atomicOr(n.err, ERR_TIMEOUT_BIT);
+        mbar_wait(&bar, phase, kBudget);  // drain before the accumulator is released
+        break;
+      }
+      phase ^= 1u;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+      const int gx = x0 + warp * 32 + lane;
+      const long long o = (long long)h * Wd + gx;
 #pragma unroll
-    for (int c0 = 0; c0 < N; c0 += 16) {
-      uint32_t r[16];
-      tmem_ld16(taddr + c0, r);
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (gx < Wd) {
+      for (int c0 = 0; c0 < N; c0 += 16) {
+        uint32_t r[16];
+        tmem_ld16(taddr + c0, r);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (gx < Wd) {
+          float v[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int co = c0 + j;
-          if (co < COUT) {
-            const float v = __uint_as_float(r[j]) + sbias[co];
-            Y[co * pix + (long long)h * Wd + gx] = (ACT == 0) ? (v > 0.0f ? v : 0.0f) : tanhf(v);
+          for (int j = 0; j < 16; ++j) {
+            const int co = c0 + j;
+            if (co < COUT) {
+              const float z = __uint_as_float(r[j]) + sbias[co];
+              v[j] = (ACT == 0) ? (z > 0.0f ? z : 0.0f) : tanhf(z);
+              Y[co * pix + o] = v[j];
+            }
+          }
+          if (Yh && c0 + 16 <= COUT) {
+#pragma unroll
+            for (int c8 = 0; c8 < 2; ++c8) {
+              __align__(16) __nv_bfloat16 v8[8];
+#pragma unroll
+              for (int e = 0; e < 8; ++e) v8[e] = __float2bfloat16_rn(v[8 * c8 + e]);
+              *reinterpret_cast<uint4*>(Yh + o * COUT + c0 + 8 * c8) = *reinterpret_cast<const uint4*>(v8);
+            }
           }
         }
       }
+      // the accumulator is read and the oldest row slot may be refilled
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -825,13 +889,13 @@ dim3 tile_grid(const NnArgs& n) {
 }
 
 template <class T, int CIN, int COUT, int ACT>
-cudaError_t conv(const NnArgs& n, const void* in, void* out, int woff, cudaStream_t s) {
+cudaError_t conv(const NnArgs& n, const void* in, void* out, int woff, cudaStream_t s, void* outh = nullptr) {
   if (std::is_same<T, float>::value) {
     const size_t sm = sizeof(float) * (CIN * 9 * COUT + COUT + CIN * TH * TH);
     auto k = nn_conv_f32_kernel<CIN, COUT, ACT>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k<<<tile_grid(n), NTHR_F, sm, s>>>(n, in, out, woff);
+    k<<<tile_grid(n), NTHR_F, sm, s>>>(n, in, out, woff, outh);
     return cudaGetLastError();
   }
   constexpr int NW = COUT * CIN * 9 + COUT;
@@ -881,18 +945,18 @@ cudaError_t wgrad(const NnArgs& n, const void* gout, const void* ain, int woff, 
 }
 
 template <int CIN, int COUT, int ACT>
-cudaError_t conv_tc(const NnArgs& n, const void* in, void* out, int woff, cudaStream_t s) {
+cudaError_t conv_tc(const NnArgs& n, const void* inh, void* out, int woff, cudaStream_t s, void* outh = nullptr) {
   constexpr int N = (COUT + 15) / 16 * 16;
   const size_t sm = TC_AREGION + 9 * (CIN / 8) * N * 16 + COUT * sizeof(float);
   auto k = nn_conv_tc_kernel<CIN, COUT, ACT>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  int W = n.W[0], H = n.H[0];
-  if (n.nimg > 1) {
-    W = W > n.W[1] ? W : n.W[1];
-    H = H > n.H[1] ? H : n.H[1];
-  }
-  k<<<dim3(cdiv(W, TC_M), H, n.nimg), 128, sm, s>>>(n, in, out, woff);
+  // one block per work item: the occupancy query reports one block per SM for this kernel
+  // (it allocates tensor memory), while shared memory admits several, which the hardware
+  // co-schedules; each block allocates its 32 tensor-memory columns once and frees them
+  long long items = 0;
+  for (int d = 0; d < n.nimg; ++d) items += (long long)cdiv(n.W[d], TC_M) * cdiv(n.H[d], TC_ROWS);
+  k<<<(unsigned)items, 128, sm, s>>>(n, inh, out, woff, outh);
   return cudaGetLastError();
 }
 
@@ -900,10 +964,12 @@ cudaError_t conv_tc(const NnArgs& n, const void* in, void* out, int woff, cudaSt
 template <class T>
 cudaError_t layers_t(const NnArgs& n, cudaStream_t s) {
   cudaError_t e;
-  if ((e = conv<T, 4, 16, 0>(n, n.X, n.A1, NN_OFF1, s)) != cudaSuccess) return e;
-  if (std::is_same<T, float>::value && n.bf16) {
-    if ((e = conv_tc<16, 32, 0>(n, n.A1, n.A2, NN_OFF2, s)) != cudaSuccess) return e;
-    return conv_tc<32, 4, 1>(n, n.A2, n.T3, NN_OFF3, s);
+  const bool tc = std::is_same<T, float>::value && n.bf16;
+  // (the tensor-core layers read BF16 pixel-major copies written by the layer before them)
+  if ((e = conv<T, 4, 16, 0>(n, n.X, n.A1, NN_OFF1, s, tc ? n.A1h : nullptr)) != cudaSuccess) return e;
+  if (tc) {
+    if ((e = conv_tc<16, 32, 0>(n, n.A1h, n.A2, NN_OFF2, s, n.A2h)) != cudaSuccess) return e;
+    return conv_tc<32, 4, 1>(n, n.A2h, n.T3, NN_OFF3, s);
   }
   if ((e = conv<T, 16, 32, 0>(n, n.A1, n.A2, NN_OFF2, s)) != cudaSuccess) return e;
   return conv<T, 32, 4, 1>(n, n.A2, n.T3, NN_OFF3, s);
