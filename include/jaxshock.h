@@ -133,6 +133,66 @@ int js_tape_reserve_ex(js_ctx* ctx, int n_slots, int flags);
 int js_step_taped(js_ctx* ctx, double* U, double dt, int slot);
 int js_step_vjp_taped(js_ctx* ctx, int slot, double dt, const double* lam_np1, double* lam_n, double* p_bar);
 
+/* ---- Stage-wise stepping ----------------------------------------------------------------
+ * One stage of the SSP-RK3 step (Shu-Osher form; the paper prints forward Euler, Sec. 2):
+ *   U_out = a_k U_n + b_k (X + dt L(X)),  (a_k, b_k) = (0, 1), (3/4, 1/4), (1/3, 2/3),
+ * X = U_in with its boundary ghost layers and immersed-boundary ghost cells filled.  js_step
+ * is stage 0 from U_n, stage 1 from its result, stage 2 from that.  U_n is read only for
+ * stage > 0 (may be NULL for stage 0).  All arrays device [4][ny][nx]; any may alias.
+ * Asynchronous.  This is the entry for callers that act between stages (the halo exchange of
+ * a y-decomposed grid, below). */
+int js_step_stage(js_ctx* ctx, const double* U_n, const double* U_in, double* U_out, double dt, int stage);
+
+/* Reverse of js_step_stage, called for the stages of one step in the order 2, 1, 0 (any other
+ * order returns JS_ERR_ARG; js_rhs_vjp / js_step_vjp / js_step_vjp_taped restart the order):
+ *   lam_in  = (dU_out/dX)^T lam_out through the ghost fills to U_in   (overwritten)
+ *   p_bar  += (dU_out/dtheta)^T lam_out                                (accumulated, or NULL)
+ * The U_n part a_k lam_out of stages 2 and 1 is kept in the context and added to the lam_in
+ * of stage 0 (whose U_in is U_n): with lam_out of stage k-1 = lam_in of stage k, the stage-0
+ * lam_in equals js_step_vjp's lam_n.  lam_in may alias lam_out.  Asynchronous. */
+int js_step_stage_vjp(js_ctx* ctx, const double* U_in, double dt, int stage, const double* lam_out,
+                      double* lam_in, double* p_bar);
+
+/* ---- Single-grid domain decomposition in y slabs -----------------------------------------
+ * A grid is split into slabs of whole rows, one context (one rank, one GPU) per slab.  A slab
+ * context holds a window of the grid: its own rows [row0, row0 + nrows) and `overlap` rows of
+ * each neighbouring slab (clipped at non-periodic y sides; wrapping around when both y sides
+ * are periodic).  A stage output reads cells within 3 rows, so when, after every stage, the
+ * overlap rows are overwritten with their owners' new values (the halo exchange), the owned
+ * rows evolve exactly as in the undecomposed grid and the overlap rows' own stage outputs are
+ * never used.  Reverse mode transposes the exchange: after every reversed stage the adjoint
+ * of the overlap rows is added to the owner's rows and cleared locally; p_bar is then the sum
+ * over the slabs.  The CFL step of the grid is the minimum of the slabs' js_max_dt. */
+
+/* Create the context of one slab.
+ *   grid, params, bc, sdf_host : the WHOLE grid, as for js_create (sdf_host [grid->ny][nx]).
+ *   row0, nrows                : owned rows; nrows == grid->ny gives a plain context.
+ *   overlap                    : rows of each neighbour held (>= 3; with an immersed body,
+ *                                also enough that every ghost cell within 3 rows of the owned
+ *                                rows has its image-point cells inside the window).
+ * The context's arrays are [4][rows][nx] over the window (js_slab_info); y sides that border
+ * another slab get transmissive ghost layers.  Immersed-boundary tables are those of the
+ * whole grid restricted to the window; a ghost cell whose image-point cells leave the window
+ * is frozen (it reaches no owned output), or JS_ERR_IB when it lies within 3 rows of the
+ * owned rows.  The neural flux (js_set_neural) is not available on a slab of a decomposed grid.
+ * Errors: JS_ERR_ARG (ny == 1, rows out of range, overlap < 3, a window that would wrap onto
+ * itself or fewer than 6 rows, only one y side periodic), JS_ERR_IB, JS_ERR_NOMEM, JS_ERR_CUDA. */
+int js_create_slab(const js_grid* grid, const js_params* params, const js_boundary* bc, const double* sdf_host,
+                   int row0, int nrows, int overlap, void* stream, js_ctx** out);
+
+/* Window of a context: its first row in the whole grid (row_lo; local row k is grid row
+ * (row_lo + k) mod grid ny), its number of rows, the local index of its first owned row and
+ * the number of owned rows.  A plain context reports 0, ny, 0, ny.  Any output may be NULL. */
+int js_slab_info(js_ctx* ctx, int* row_lo, int* rows, int* own_lo, int* own_rows);
+
+/* Row blocks for the halo exchange: rows [row0, row0 + nrows) of the four planes of a
+ * context-shaped array U ([4][rows][nx]) to / from a contiguous device buffer [4][nrows][nx].
+ *   js_rows_pack   : buf = those rows; zero != 0 also sets them to 0 in U (reverse exchange).
+ *   js_rows_unpack : those rows = buf, or += buf when add != 0.
+ * JS_ERR_ARG when the rows leave the context's window.  Asynchronous. */
+int js_rows_pack(js_ctx* ctx, double* U, int row0, int nrows, double* buf, int zero);
+int js_rows_unpack(js_ctx* ctx, double* U, int row0, int nrows, const double* buf, int add);
+
 /* Neural flux (Sec. 2.3).  A fully convolutional network of three 3x3 layers with zero
  * ("SAME") padding, 4 -> 16 -> 32 -> 4 channels, ReLU, ReLU, tanh (JS_NN_NPARAM = 6388
  * parameters, the paper's count), evaluated on one image per direction and added to the HLLC

@@ -66,6 +66,13 @@ SIGNATURES = {
     "js_block_average": (_I, [_P, _I, _I, _I, _I, _P, _P]),
     "js_nn_eval": (_I, [_P, _P, _I, _I, _P]),
     "js_step_taped": (_I, [_P, _P, _D, _I]),
+    "js_step_stage": (_I, [_P, _P, _P, _P, _D, _I]),
+    "js_step_stage_vjp": (_I, [_P, _P, _D, _I, _P, _P, _P]),
+    "js_create_slab": (_I, [C.POINTER(JsGrid), C.POINTER(JsParams), C.POINTER(JsBoundary), _P, _I, _I, _I, _P,
+                            C.POINTER(_P)]),
+    "js_slab_info": (_I, [_P, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
+    "js_rows_pack": (_I, [_P, _P, _I, _I, _P, _I]),
+    "js_rows_unpack": (_I, [_P, _P, _I, _I, _P, _I]),
     "js_step_vjp_taped": (_I, [_P, _I, _D, _P, _P, _P]),
     "js_set_tuning": (_I, [_P, _I]),
     "js_get_tuning": (_I, [_P, C.POINTER(_I), C.POINTER(_I)]),
@@ -155,6 +162,23 @@ def js_create(grid, params, boundary, sdf=None, stream=None):
     _check(lib().js_create(C.byref(grid), C.byref(params), C.byref(boundary), sdf_p, _stream_ptr(stream),
                            C.byref(out)), "js_create")
     return out
+
+
+def js_create_slab(grid, params, boundary, sdf, row0, nrows, overlap, stream=None):
+    sdf_p = None
+    if sdf is not None:
+        sdf = np.ascontiguousarray(sdf, dtype=np.float64)
+        sdf_p = sdf.ctypes.data_as(C.c_void_p)
+    out = C.c_void_p()
+    _check(lib().js_create_slab(C.byref(grid), C.byref(params), C.byref(boundary), sdf_p, int(row0), int(nrows),
+                                int(overlap), _stream_ptr(stream), C.byref(out)), "js_create_slab")
+    return out
+
+
+def js_slab_info(ctx):
+    v = [C.c_int(0) for _ in range(4)]
+    _check(lib().js_slab_info(ctx, *[C.byref(x) for x in v]), "js_slab_info")
+    return tuple(x.value for x in v)
 
 
 def js_destroy(ctx):
@@ -255,6 +279,24 @@ class Solver:
         return cls(prob.nx, prob.ny, prob.x0, prob.y0, prob.dx, prob.dy, prob.bc, prob.gamma, prob.mu, prob.Pr,
                    prob.nu, prob.inflow, getattr(prob, "wall", 0), prob.sdf, stream)
 
+    @classmethod
+    def slab(cls, prob, row0, nrows, overlap, stream=None):
+        """Context of the y slab owning rows [row0, row0 + nrows) of the problem's grid, holding
+        `overlap` rows of each neighbour (js_create_slab).  Its arrays are [4, rows, nx] over
+        the window; `window` = (first grid row, rows, local first owned row, owned rows)."""
+        self = cls.__new__(cls)
+        self._spec = dict(nx=prob.nx, ny=prob.ny, x0=prob.x0, y0=prob.y0, dx=prob.dx, dy=prob.dy, bc=tuple(prob.bc),
+                          gamma=prob.gamma, mu=prob.mu, Pr=prob.Pr, nu=prob.nu,
+                          inflow=np.asarray(prob.inflow, dtype=np.float64).reshape(4, 4),
+                          wall=getattr(prob, "wall", 0))
+        self._g, self._p, self._b = make_structs(**self._spec)
+        self.has_ib = prob.sdf is not None
+        self.ctx = js_create_slab(self._g, self._p, self._b, prob.sdf, row0, nrows, overlap, stream)
+        self.window = js_slab_info(self.ctx)
+        self.nx, self.ny = int(prob.nx), self.window[1]
+        self.dx, self.dy = float(prob.dx), float(prob.dy)
+        return self
+
     @property
     def shape(self):
         return (4, self.ny, self.nx)
@@ -330,6 +372,28 @@ class Solver:
         p_bar = torch.zeros(JS_NPARAM, dtype=torch.float64, device=U_n.device) if p_bar is None else p_bar
         js_step_vjp(self.ctx, U_n, dt, lam_np1, lam_n, p_bar)
         return lam_n, p_bar
+
+    def step_stage(self, U_n, U_in, U_out, dt, k):
+        """One SSP-RK3 stage k (0, 1, 2): U_out = a_k U_n + b_k (U_in + dt L(U_in))."""
+        _check(lib().js_step_stage(self.ctx, _ptr(U_n) if k > 0 else None, _ptr(U_in), _ptr(U_out), float(dt),
+                                   int(k)), "js_step_stage")
+        return U_out
+
+    def step_stage_vjp(self, U_in, dt, k, lam_out, lam_in, p_bar=None):
+        """Reverse of stage k (called for k = 2, 1, 0 of one step; stage 0 adds the U^n part)."""
+        _check(lib().js_step_stage_vjp(self.ctx, _ptr(U_in), float(dt), int(k), _ptr(lam_out), _ptr(lam_in),
+                                       _ptr(p_bar)), "js_step_stage_vjp")
+        return lam_in
+
+    def rows_pack(self, U, row0, nrows, buf, zero=False):
+        _check(lib().js_rows_pack(self.ctx, _ptr(U), int(row0), int(nrows), _ptr(buf), int(bool(zero))),
+               "js_rows_pack")
+        return buf
+
+    def rows_unpack(self, U, row0, nrows, buf, add=False):
+        _check(lib().js_rows_unpack(self.ctx, _ptr(U), int(row0), int(nrows), _ptr(buf), int(bool(add))),
+               "js_rows_unpack")
+        return U
 
     def tape_reserve(self, n_slots, weno=False):
         """n_slots tape slots; weno=True also records the WENO5 internals of each stage

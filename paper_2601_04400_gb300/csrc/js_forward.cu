@@ -55,6 +55,24 @@ __global__ void unpack_kernel(const double* __restrict__ P, double* __restrict__
   U[t] = P[c * lay.plane + lay.idx(i, j)];
 }
 
+// row blocks of a [4][ny][nx] state for the halo exchange of a y-decomposed grid
+__global__ void rows_pack_kernel(double* __restrict__ U, long long plane, long long off, long long m,
+                                 double* __restrict__ buf, int zero) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 4 * m) return;
+  const long long k = (t / m) * plane + off + t % m;
+  buf[t] = U[k];
+  if (zero) U[k] = 0.0;
+}
+
+__global__ void rows_unpack_kernel(double* __restrict__ U, long long plane, long long off, long long m,
+                                   const double* __restrict__ buf, int add) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 4 * m) return;
+  const long long k = (t / m) * plane + off + t % m;
+  U[k] = add ? U[k] + buf[t] : buf[t];
+}
+
 __global__ void prim_to_cons_kernel(const double* W, double* U, long long n, double g1) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
@@ -316,6 +334,23 @@ cudaError_t launch_unpack(const double* P, double* U, const Lay& lay, cudaStream
   const long long n = 4LL * lay.nx * lay.ny;
   const int bs = 256;
   unpack_kernel<<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>(P, U, lay);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rows_pack(double* U, int nx, int ny, int row0, int nrows, double* buf, int zero, cudaStream_t s) {
+  const long long m = (long long)nrows * nx;
+  if (m == 0) return cudaSuccess;
+  rows_pack_kernel<<<(unsigned)((4 * m + 255) / 256), 256, 0, s>>>(U, (long long)nx * ny, (long long)row0 * nx, m,
+                                                                   buf, zero);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rows_unpack(double* U, int nx, int ny, int row0, int nrows, const double* buf, int add,
+                               cudaStream_t s) {
+  const long long m = (long long)nrows * nx;
+  if (m == 0) return cudaSuccess;
+  rows_unpack_kernel<<<(unsigned)((4 * m + 255) / 256), 256, 0, s>>>(U, (long long)nx * ny, (long long)row0 * nx,
+                                                                     m, buf, add);
   return cudaGetLastError();
 }
 

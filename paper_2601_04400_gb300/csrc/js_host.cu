@@ -78,6 +78,13 @@ struct js_ctx {
   std::vector<double*> tape_w;     // 3 per slot (56 planes each) or nullptr
   std::vector<char> tape_w_ok;     // per slot: internals of the recorded step are present
   bool tape_weno = false;
+  // y slab of a decomposed grid (js_create_slab): local row k is global row
+  // (slab_lo + k) mod slab_nyg; rows [slab_own, slab_own + slab_nown) are owned; the y sides
+  // in slab_xchg[0] (low) / [1] (high) border a neighbouring slab
+  bool slab = false;
+  int slab_nyg = 0, slab_lo = 0, slab_own = 0, slab_nown = 0;
+  bool slab_xchg[2] = {false, false};
+  int svjp_next = 2;  // stage expected by the next js_step_stage_vjp (2, 1, 0, 2, ...)
   // instrumentation
   bool profiling = false;
   std::vector<cudaEvent_t> ev;  // 2 per timed stage launch
@@ -112,7 +119,9 @@ bool params_valid(const js_params* p, const js_boundary* b) {
 
 void set_bc(js_ctx* c) {
   for (int s = 0; s < 4; ++s) {
-    c->bc.kind[s] = c->b.kind[s];
+    // a side bordering a neighbouring slab: transmissive ghost layers (they reach only overlap
+    // rows, which the halo exchange overwrites)
+    c->bc.kind[s] = (s >= 2 && c->slab_xchg[s - 2]) ? JS_BC_TRANSMISSIVE : c->b.kind[s];
     const double r = c->b.inflow[s][0], u = c->b.inflow[s][1], v = c->b.inflow[s][2], pr = c->b.inflow[s][3];
     c->bc.inflow_cons[s][0] = r;
     c->bc.inflow_cons[s][1] = r * u;
@@ -126,57 +135,75 @@ void set_bc(js_ctx* c) {
 // at grid edges); image point = ghost centre - 2 sdf n; bilinear weights over the 2x2 block
 // of cell centres around it (clamped into the grid), restricted to fluid cells and
 // renormalised.
-int build_ib(js_ctx* c, const double* sdf) {
+// The tables cover the context's rows, a window of a grid of nyg rows (global y origin y0g):
+// local row k is global row (row_lo + k) mod nyg, and every quantity above is evaluated on the
+// global grid, so that the entries equal those of the whole grid.  A ghost cell whose
+// interpolation cells leave the window is frozen (tagged plain solid, not filled) unless its
+// row lies in [exact_lo, exact_hi), which is an error.
+int build_ib(js_ctx* c, const double* sdf, int nyg, double y0g, int row_lo, int exact_lo, int exact_hi) {
   const int nx = c->g.nx, ny = c->g.ny;
-  const double dx = c->g.dx, dy = c->g.dy, x0 = c->g.x0, y0 = c->g.y0;
+  const double dx = c->g.dx, dy = c->g.dy, x0 = c->g.x0;
   std::vector<unsigned char>& tag = c->tag_host;
   tag.assign((size_t)nx * ny, 0);
-  auto S = [&](int i, int j) { return sdf[(size_t)j * nx + i]; };
-  for (int j = 0; j < ny; ++j)
-    for (int i = 0; i < nx; ++i) tag[(size_t)j * nx + i] = (S(i, j) < 0.0) ? 1 : 0;
-  for (int j = 0; j < ny; ++j)
+  auto S = [&](int i, int jg) { return sdf[(size_t)jg * nx + i]; };
+  auto glob = [&](int k) { return (row_lo + k) % nyg; };
+  auto loc = [&](int jg) {
+    const int k = ((jg - row_lo) % nyg + nyg) % nyg;
+    return k < ny ? k : -1;
+  };
+  for (int k = 0; k < ny; ++k)
+    for (int i = 0; i < nx; ++i) tag[(size_t)k * nx + i] = (S(i, glob(k)) < 0.0) ? 1 : 0;
+  for (int k = 0; k < ny; ++k)
     for (int i = 0; i < nx; ++i) {
-      if (tag[(size_t)j * nx + i] == 0) continue;
+      if (tag[(size_t)k * nx + i] == 0) continue;
+      const int j = glob(k);
       bool fluid_near = false;
       for (int jj = j - 3; jj <= j + 3 && !fluid_near; ++jj)
         for (int ii = i - 3; ii <= i + 3; ++ii) {
-          if (ii < 0 || jj < 0 || ii >= nx || jj >= ny) continue;
+          if (ii < 0 || jj < 0 || ii >= nx || jj >= nyg) continue;
           if (!(S(ii, jj) < 0.0)) { fluid_near = true; break; }
         }
-      if (fluid_near) tag[(size_t)j * nx + i] = 2;
+      if (fluid_near) tag[(size_t)k * nx + i] = 2;
     }
   std::vector<long long> dst, src;
   std::vector<double> w, nrm;
-  for (int j = 0; j < ny; ++j)
+  for (int k = 0; k < ny; ++k)
     for (int i = 0; i < nx; ++i) {
-      if (tag[(size_t)j * nx + i] != 2) continue;
+      if (tag[(size_t)k * nx + i] != 2) continue;
+      const int j = glob(k);
       const int il = i > 0 ? i - 1 : i, ir = i < nx - 1 ? i + 1 : i;
-      const int jl = j > 0 ? j - 1 : j, jr = j < ny - 1 ? j + 1 : j;
+      const int jl = j > 0 ? j - 1 : j, jr = j < nyg - 1 ? j + 1 : j;
       const double gx = (S(ir, j) - S(il, j)) / ((ir - il) * dx);
       const double gy = (S(i, jr) - S(i, jl)) / ((jr - jl) * dy);
       const double gn = std::sqrt(gx * gx + gy * gy);
       if (!(gn > 0.0)) return JS_ERR_IB;
       const double nxv = gx / gn, nyv = gy / gn;
       const double phi = S(i, j);
-      const double xg = x0 + (i + 0.5) * dx, yg = y0 + (j + 0.5) * dy;
+      const double xg = x0 + (i + 0.5) * dx, yg = y0g + (j + 0.5) * dy;
       const double xi = xg - 2.0 * phi * nxv, yi = yg - 2.0 * phi * nyv;
-      const double fx = (xi - x0) / dx - 0.5, fy = (yi - y0) / dy - 0.5;
-      if (!(fx >= -0.5 && fy >= -0.5 && fx <= nx - 0.5 && fy <= ny - 0.5)) return JS_ERR_IB;
+      const double fx = (xi - x0) / dx - 0.5, fy = (yi - y0g) / dy - 0.5;
+      if (!(fx >= -0.5 && fy >= -0.5 && fx <= nx - 0.5 && fy <= nyg - 0.5)) return JS_ERR_IB;
       int i0 = (int)std::floor(fx), j0 = (int)std::floor(fy);
       i0 = i0 < 0 ? 0 : (i0 > nx - 2 ? nx - 2 : i0);
-      j0 = j0 < 0 ? 0 : (j0 > ny - 2 ? ny - 2 : j0);
+      j0 = j0 < 0 ? 0 : (j0 > nyg - 2 ? nyg - 2 : j0);
+      const int k0 = loc(j0), k1 = loc(j0 + 1);
+      if (k0 < 0 || k1 < 0) {
+        if (k >= exact_lo && k < exact_hi) return JS_ERR_IB;
+        tag[(size_t)k * nx + i] = 1;
+        continue;
+      }
       const double tx = fx - i0, ty = fy - j0;
-      const int ci[4] = {i0, i0 + 1, i0, i0 + 1}, cj[4] = {j0, j0, j0 + 1, j0 + 1};
+      const int ci[4] = {i0, i0 + 1, i0, i0 + 1}, ck[4] = {k0, k0, k1, k1};
       double wk[4] = {(1.0 - tx) * (1.0 - ty), tx * (1.0 - ty), (1.0 - tx) * ty, tx * ty};
       double sum = 0.0;
       for (int m = 0; m < 4; ++m) {
-        if (tag[(size_t)cj[m] * nx + ci[m]] != 0) wk[m] = 0.0;
+        if (tag[(size_t)ck[m] * nx + ci[m]] != 0) wk[m] = 0.0;
         sum = sum + wk[m];
       }
       if (!(sum > 0.0)) return JS_ERR_IB;
-      dst.push_back(c->lay.idx(i, j));
+      dst.push_back(c->lay.idx(i, k));
       for (int m = 0; m < 4; ++m) {
-        src.push_back(c->lay.idx(ci[m], cj[m]));
+        src.push_back(c->lay.idx(ci[m], ck[m]));
         w.push_back(wk[m] / sum);
       }
       nrm.push_back(nxv);
@@ -446,14 +473,30 @@ void js_destroy(js_ctx* c) {
   delete c;
 }
 
-int js_create(const js_grid* grid, const js_params* params, const js_boundary* bc, const double* sdf_host,
-              void* stream, js_ctx** out) {
-  if (!out) return JS_ERR_ARG;
-  *out = nullptr;
-  if (!grid_valid(grid) || !params_valid(params, bc)) return JS_ERR_ARG;
-  if (sdf_host && grid->ny == 1) return JS_ERR_ARG;
+}  // extern "C"
+
+namespace {
+
+// a context over `grid` (a whole grid, or the window of a slab described by `slab`); the IB
+// tables come from the sdf of the whole grid (nyg rows, y origin y0g)
+struct SlabDesc {
+  bool on;
+  int nyg, lo, own, nown;
+  bool xchg[2];
+  double y0g;
+};
+
+int create_ctx(const js_grid* grid, const js_params* params, const js_boundary* bc, const double* sdf_host,
+               void* stream, const SlabDesc& sd, js_ctx** out) {
   js_ctx* c = new (std::nothrow) js_ctx();
   if (!c) return JS_ERR_NOMEM;
+  c->slab = sd.on;
+  c->slab_nyg = sd.nyg;
+  c->slab_lo = sd.lo;
+  c->slab_own = sd.own;
+  c->slab_nown = sd.nown;
+  c->slab_xchg[0] = sd.xchg[0];
+  c->slab_xchg[1] = sd.xchg[1];
   c->g = *grid;
   c->p = *params;
   c->b = *bc;
@@ -485,13 +528,85 @@ int js_create(const js_grid* grid, const js_params* params, const js_boundary* b
   }
   set_bc(c);
   if (sdf_host) {
-    const int rc = build_ib(c, sdf_host);
+    // ghost cells within 3 rows of the owned rows feed owned stage outputs: they must be exact
+    const int lo = sd.on ? sd.own - 3 : 0, hi = sd.on ? sd.own + sd.nown + 3 : grid->ny;
+    const int rc = build_ib(c, sdf_host, sd.nyg, sd.y0g, sd.lo, lo, hi);
     if (rc != JS_OK) {
       js_destroy(c);
       return rc;
     }
   }
   *out = c;
+  return JS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int js_create(const js_grid* grid, const js_params* params, const js_boundary* bc, const double* sdf_host,
+              void* stream, js_ctx** out) {
+  if (!out) return JS_ERR_ARG;
+  *out = nullptr;
+  if (!grid_valid(grid) || !params_valid(params, bc)) return JS_ERR_ARG;
+  if (sdf_host && grid->ny == 1) return JS_ERR_ARG;
+  const SlabDesc sd{false, grid->ny, 0, 0, grid->ny, {false, false}, grid->y0};
+  return create_ctx(grid, params, bc, sdf_host, stream, sd, out);
+}
+
+int js_create_slab(const js_grid* grid, const js_params* params, const js_boundary* bc, const double* sdf_host,
+                   int row0, int nrows, int overlap, void* stream, js_ctx** out) {
+  if (!out) return JS_ERR_ARG;
+  *out = nullptr;
+  if (!grid_valid(grid) || !params_valid(params, bc) || grid->ny == 1) return JS_ERR_ARG;
+  const int ny = grid->ny;
+  if (row0 < 0 || nrows < 1 || row0 + nrows > ny || overlap < 0) return JS_ERR_ARG;
+  const bool py0 = bc->kind[2] == JS_BC_PERIODIC, py1 = bc->kind[3] == JS_BC_PERIODIC;
+  SlabDesc sd{true, ny, 0, row0, nrows, {false, false}, grid->y0};
+  int rows = ny;
+  if (nrows < ny) {
+    if (overlap < 3 || py0 != py1) return JS_ERR_ARG;
+    if (py0) {
+      if (nrows + 2 * overlap > ny) return JS_ERR_ARG;
+      sd.lo = ((row0 - overlap) % ny + ny) % ny;
+      rows = nrows + 2 * overlap;
+      sd.xchg[0] = sd.xchg[1] = true;
+    } else {
+      sd.lo = row0 > overlap ? row0 - overlap : 0;
+      const int hi = (row0 + nrows + overlap < ny) ? row0 + nrows + overlap : ny;
+      rows = hi - sd.lo;
+      sd.xchg[0] = row0 > 0;
+      sd.xchg[1] = row0 + nrows < ny;
+    }
+  }
+  sd.own = (nrows < ny) ? ((row0 - sd.lo) % ny + ny) % ny : 0;
+  js_grid g = *grid;
+  g.ny = rows;
+  g.y0 = grid->y0 + sd.lo * grid->dy;
+  if (!grid_valid(&g)) return JS_ERR_ARG;
+  return create_ctx(&g, params, bc, sdf_host, stream, sd, out);
+}
+
+int js_slab_info(js_ctx* c, int* row_lo, int* rows, int* own_lo, int* own_rows) {
+  if (!c) return JS_ERR_ARG;
+  if (row_lo) *row_lo = c->slab ? c->slab_lo : 0;
+  if (rows) *rows = c->g.ny;
+  if (own_lo) *own_lo = c->slab ? c->slab_own : 0;
+  if (own_rows) *own_rows = c->slab ? c->slab_nown : c->g.ny;
+  return JS_OK;
+}
+
+int js_rows_pack(js_ctx* c, double* U, int row0, int nrows, double* buf, int zero) {
+  if (!c || !U || !buf || row0 < 0 || nrows < 0 || row0 + nrows > c->g.ny) return JS_ERR_ARG;
+  JS_CUDA(js::launch_rows_pack(U, c->g.nx, c->g.ny, row0, nrows, buf, zero, c->stream));
+  ++c->launches;
+  return JS_OK;
+}
+
+int js_rows_unpack(js_ctx* c, double* U, int row0, int nrows, const double* buf, int add) {
+  if (!c || !U || !buf || row0 < 0 || nrows < 0 || row0 + nrows > c->g.ny) return JS_ERR_ARG;
+  JS_CUDA(js::launch_rows_unpack(U, c->g.nx, c->g.ny, row0, nrows, buf, add, c->stream));
+  ++c->launches;
   return JS_OK;
 }
 
@@ -594,6 +709,37 @@ int js_step(js_ctx* c, double* U, double dt, int n_steps) {
   }
   JS_CUDA(js::launch_unpack(c->N, U, c->lay, c->stream));
   c->launches += 2;  // pack + unpack
+  return JS_OK;
+}
+
+int js_step_stage(js_ctx* c, const double* U_n, const double* U_in, double* U_out, double dt, int stage_k) {
+  if (!c || !U_in || !U_out || stage_k < 0 || stage_k > 2 || !(dt > 0.0) || (stage_k > 0 && !U_n))
+    return JS_ERR_ARG;
+  double* X = (stage_k == 0) ? c->N : c->A;
+  JS_CUDA(js::launch_pack(U_in, X, c->lay, c->stream));
+  ++c->launches;
+  if (stage_k > 0) {
+    JS_CUDA(js::launch_pack(U_n, c->N, c->lay, c->stream));
+    ++c->launches;
+  }
+  StageArgs a = base_args(c);
+  a.cx = dt / c->g.dx;
+  a.cy = dt / c->g.dy;
+  a.avx = dt * c->p.nu / (c->g.dx * c->g.dx);
+  a.avy = dt * c->p.nu / (c->g.dy * c->g.dy);
+  const double ra[3] = {0.0, 0.75, 1.0 / 3.0};
+  const double rb[3] = {1.0, 0.25, 2.0 / 3.0};
+  int rc = fill_halos(c, X);
+  if (rc) return rc;
+  a.Uin = X;
+  a.Un = c->N;
+  a.Uout = c->B;
+  a.rk_a = ra[stage_k];
+  a.rk_b = rb[stage_k];
+  a.use_un = (stage_k > 0) ? 1 : 0;
+  if ((rc = stage(c, a, c->p.mu > 0.0, false))) return rc;
+  JS_CUDA(js::launch_unpack(c->B, U_out, c->lay, c->stream));
+  ++c->launches;
   return JS_OK;
 }
 
@@ -711,6 +857,7 @@ int upload_inflow(js_ctx* c) {
 
 int js_rhs_vjp(js_ctx* c, const double* U, const double* lam, double* U_bar, double* p_bar) {
   if (!c || !U || !lam || !U_bar) return JS_ERR_ARG;
+  c->svjp_next = 2;  // the stage-wise reverse sequence (js_step_stage_vjp) restarts
   int rc = adj_reserve(c);
   if (rc) return rc;
   if ((rc = upload_inflow(c))) return rc;
@@ -726,6 +873,7 @@ int js_rhs_vjp(js_ctx* c, const double* U, const double* lam, double* U_bar, dou
 
 int js_step_vjp(js_ctx* c, const double* U_n, double dt, const double* lam_np1, double* lam_n, double* p_bar) {
   if (!c || !U_n || !lam_np1 || !lam_n || !(dt > 0.0)) return JS_ERR_ARG;
+  c->svjp_next = 2;  // the stage-wise reverse sequence (js_step_stage_vjp) restarts
   int rc = adj_reserve(c);
   if (rc) return rc;
   if ((rc = upload_inflow(c))) return rc;
@@ -773,6 +921,28 @@ int js_step_vjp(js_ctx* c, const double* U_n, double dt, const double* lam_np1, 
   }
   JS_CUDA(js::launch_adj_unpack(src, c->Uacc, lam_n, c->lay, c->stream));
   ++c->launches;
+  return JS_OK;
+}
+
+int js_step_stage_vjp(js_ctx* c, const double* U_in, double dt, int stage_k, const double* lam_out, double* lam_in,
+                      double* p_bar) {
+  if (!c || !U_in || !lam_out || !lam_in || stage_k < 0 || stage_k > 2 || !(dt > 0.0)) return JS_ERR_ARG;
+  if (stage_k != 2 && stage_k != c->svjp_next) return JS_ERR_ARG;
+  int rc = adj_reserve(c);
+  if (rc) return rc;
+  if ((rc = upload_inflow(c))) return rc;
+  JS_CUDA(js::launch_pack(U_in, c->N, c->lay, c->stream));
+  JS_CUDA(js::launch_pack(lam_out, c->P0, c->lay, c->stream));
+  c->launches += 2;
+  if ((rc = fill_halos(c, c->N))) return rc;
+  // the U^n adjoint of stages 2 and 1 collects in Uacc and is added to stage 0's result
+  if (stage_k == 2) JS_CUDA(cudaMemsetAsync(c->Uacc, 0, sizeof(double) * 4 * (size_t)c->lay.plane, c->stream));
+  const double ra[3] = {0.0, 0.75, 1.0 / 3.0};
+  const double rb[3] = {1.0, 0.25, 2.0 / 3.0};
+  if ((rc = adj_stage(c, c->N, c->P0, c->P1, ra[stage_k], rb[stage_k], dt, false, p_bar))) return rc;
+  JS_CUDA(js::launch_adj_unpack(c->P1, stage_k == 0 ? c->Uacc : nullptr, lam_in, c->lay, c->stream));
+  ++c->launches;
+  c->svjp_next = (stage_k == 0) ? 2 : stage_k - 1;
   return JS_OK;
 }
 
@@ -857,6 +1027,7 @@ int js_step_taped(js_ctx* c, double* U, double dt, int slot) {
 int js_step_vjp_taped(js_ctx* c, int slot, double dt, const double* lam_np1, double* lam_n, double* p_bar) {
   if (!c || !lam_np1 || !lam_n || !(dt > 0.0) || slot < 0 || (size_t)(slot + 1) * 3 > c->tape.size())
     return JS_ERR_ARG;
+  c->svjp_next = 2;
   int rc = adj_reserve(c);
   if (rc) return rc;
   if ((rc = upload_inflow(c))) return rc;
@@ -949,7 +1120,7 @@ int js_ib_info(js_ctx* c, int* n_ghost, unsigned char* tag_host) {
 }  // extern "C"
 
 int js_set_neural(js_ctx* c, const double* w, double* w_bar, const double* norm, int precision) {
-  if (!c) return JS_ERR_ARG;
+  if (!c || (w && c->slab && c->slab_nown < c->g.ny)) return JS_ERR_ARG;
   if (!w) {
     c->nn_on = false;
     return JS_OK;

@@ -170,6 +170,11 @@ cudaError_t launch_ib_fill(double* U, const Lay& lay, const IbArgs& ib, double g
 cudaError_t launch_pack(const double* U, double* P, const Lay& lay, cudaStream_t s);
 cudaError_t launch_unpack(const double* P, double* U, const Lay& lay, cudaStream_t s);
 cudaError_t launch_prim_to_cons(const double* W, double* U, long long n, double gamma, cudaStream_t s);
+// rows [row0, row0 + nrows) of the 4 planes of a [4][ny][nx] array <-> a [4][nrows][nx] buffer
+// (pack: zero != 0 also clears those rows of U; unpack: add != 0 adds instead of copying)
+cudaError_t launch_rows_pack(double* U, int nx, int ny, int row0, int nrows, double* buf, int zero, cudaStream_t s);
+cudaError_t launch_rows_unpack(double* U, int nx, int ny, int row0, int nrows, const double* buf, int add,
+                               cudaStream_t s);
 cudaError_t launch_cfl(const double* U, const Lay& lay, const unsigned char* tag, double gamma, double dx,
                        double dy, unsigned long long* red, cudaStream_t s);
 
