@@ -228,6 +228,14 @@ int js_set_neural(js_ctx* ctx, const double* w, double* w_bar, const double* nor
  * grids) or JS_ERR_ARG; JS_ERR_ARG also without the neural flux on.  Asynchronous. */
 int js_nn_eval(js_ctx* ctx, const double* X, int H, int W, double* Y);
 
+/* Reverse of js_nn_eval on the same image (the network's forward is recomputed):
+ *   GX     = (dY/dX)^T GY          (overwritten), device [4][H][W] FP64
+ *   w_bar += (dY/dw)^T GY          (the w_bar of js_set_neural, when one was given)
+ * In BF16 precision the data gradients of layers 3 and 2 run on the tensor cores with BF16
+ * output gradients; weight gradients and the first layer are FP32.  GX may alias X or GY.
+ * Errors as js_nn_eval.  Asynchronous. */
+int js_nn_eval_vjp(js_ctx* ctx, const double* X, int H, int W, const double* GY, double* GX);
+
 /* Block average (the downsampling that turns high-resolution states into the coarse
  * training targets of Sec. 2.4): out[4][ny/fy][nx/fx] (device) = the means of the fx x fy
  * cell blocks of U[4][ny][nx] (device).  nx % fx == 0 and ny % fy == 0 or JS_ERR_ARG.

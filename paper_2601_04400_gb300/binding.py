@@ -65,6 +65,7 @@ SIGNATURES = {
     "js_set_neural": (_I, [_P, _P, _P, _P, _I]),
     "js_block_average": (_I, [_P, _I, _I, _I, _I, _P, _P]),
     "js_nn_eval": (_I, [_P, _P, _I, _I, _P]),
+    "js_nn_eval_vjp": (_I, [_P, _P, _I, _I, _P, _P]),
     "js_step_taped": (_I, [_P, _P, _D, _I]),
     "js_step_stage": (_I, [_P, _P, _P, _P, _D, _I]),
     "js_step_stage_vjp": (_I, [_P, _P, _D, _I, _P, _P, _P]),
@@ -408,6 +409,16 @@ class Solver:
         Y = torch.empty_like(X)
         _check(lib().js_nn_eval(self.ctx, _ptr(X), X.shape[1], X.shape[2], _ptr(Y)), "js_nn_eval")
         return Y
+
+    def nn_eval_vjp(self, X, GY):
+        """Reverse of nn_eval: the input gradient for the output gradient GY [4, H, W]; the
+        weight gradient is added to the w_bar given to set_neural."""
+        import torch
+        X, GY = X.contiguous(), GY.contiguous()
+        GX = torch.empty_like(X)
+        _check(lib().js_nn_eval_vjp(self.ctx, _ptr(X), X.shape[1], X.shape[2], _ptr(GY), _ptr(GX)),
+               "js_nn_eval_vjp")
+        return GX
 
     def tape_weno_bytes(self, n_slots):
         """Device bytes the WENO5 internals of n_slots tape slots take (0 on 1D grids)."""

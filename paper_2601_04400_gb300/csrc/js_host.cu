@@ -1198,3 +1198,11 @@ int js_nn_eval(js_ctx* c, const double* X, int H, int W, double* Y) {
   JS_CUDA(js::nn_eval(c->nn, X, H, W, Y, c->stream));
   return JS_OK;
 }
+
+int js_nn_eval_vjp(js_ctx* c, const double* X, int H, int W, const double* GY, double* GX) {
+  if (!c || !c->nn_on || !X || !GY || !GX || H < 1 || W < 1) return JS_ERR_ARG;
+  const long long cap = c->nn.pix0 + (long long)c->nn.H[1] * c->nn.W[1];
+  if ((long long)H * W > cap) return JS_ERR_ARG;
+  JS_CUDA(js::nn_eval_vjp(c->nn, X, H, W, GY, GX, c->stream));
+  return JS_OK;
+}

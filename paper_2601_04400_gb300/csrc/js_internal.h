@@ -123,6 +123,8 @@ cudaError_t nn_apply(const NnArgs& n, const StageArgs& a, bool rhs, cudaStream_t
 cudaError_t nn_reverse(const NnArgs& n, const AdjArgs& a, cudaStream_t s);
 // the network alone on one image X[4][H][W] (FP64, device) -> scaled output Y[4][H][W]
 cudaError_t nn_eval(const NnArgs& n, const double* X, int H, int W, double* Y, cudaStream_t s);
+cudaError_t nn_eval_vjp(const NnArgs& n, const double* X, int H, int W, const double* GY, double* GX,
+                        cudaStream_t s);
 // out[4][ny/fy][nx/fx] = means of fx x fy blocks of U[4][ny][nx]
 cudaError_t launch_block_average(const double* U, int nx, int ny, int fx, int fy, double* out, cudaStream_t s);
 

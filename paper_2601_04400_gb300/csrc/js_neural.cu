@@ -345,27 +345,56 @@ __global__ void __launch_bounds__(NTHR_F) nn_dgrad_f32_kernel(NnArgs n, const vo
 
 // FP32 weight gradient: a work item is (group of 4 output channels, input channel, kernel
 // row) with 4 x 3 sums (the three kernel columns); per pixel one 16-byte load of the output
-// gradient and one input value slid along the row
+// gradient and one input value slid along the row.  The tile's 16 rows are split into R
+// parts so that every thread carries exactly 3 (item, part) units (NI * R = 768 for the three
+// layers); the parts, and the bias sums (every thread sums a strided subset of the tile's
+// pixels for one channel), are added in shared memory in a fixed order at the end.
+constexpr int WG_UNITS = 3 * NTHR;
+
+// 4-byte asynchronous global -> shared copy (zero-filled, nothing read, when !valid; src must
+// still be a valid address), and its group commit / wait
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(valid ? 4 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <int CIN, int COUT>
+__host__ __device__ constexpr int wgrad_tile_floats() {
+  return NTHR * COUT + CIN * TH * TH;
+}
+
 template <int CIN, int COUT>
 __global__ void __launch_bounds__(NTHR) nn_wgrad_f32_kernel(NnArgs n, const void* gout, const void* ain, int woff) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int NI = (COUT / 4) * CIN * 3;          // work items
-  constexpr int PER = (NI + NTHR - 1) / NTHR;
-  float* sg = reinterpret_cast<float*>(smem_raw);   // [256 pixels][COUT]
-  float* sa = sg + NTHR * COUT;                     // [CIN][18][18]
-  float acc[PER][12];
-  float bacc = 0.0f;                                // bias sums (threads < COUT)
+  constexpr int R = WG_UNITS / NI;                  // row parts per item
+  static_assert(NI * R == WG_UNITS && TILE % R == 0 && NTHR % COUT == 0, "work split");
+  constexpr int RROWS = TILE / R;
+  constexpr int TF = wgrad_tile_floats<CIN, COUT>();
+  // two tile buffers, each [256 pixels][COUT] output gradient + [CIN][18][18] input: the next
+  // tile is copied asynchronously while the current one is summed
+  float* const buf0 = reinterpret_cast<float*>(smem_raw);
+  float acc[3][12];
+  float bacc = 0.0f;                                // bias: channel tid % COUT, pixels tid / COUT + k * (NTHR / COUT)
 #pragma unroll
-  for (int r = 0; r < PER; ++r)
+  for (int u = 0; u < 3; ++u)
 #pragma unroll
-    for (int k = 0; k < 12; ++k) acc[r][k] = 0.0f;
+    for (int k = 0; k < 12; ++k) acc[u][k] = 0.0f;
   int ntx[2], nty[2];
   for (int d = 0; d < 2; ++d) {
     ntx[d] = (d < n.nimg) ? (n.W[d] + TILE - 1) / TILE : 0;
     nty[d] = (d < n.nimg) ? (n.H[d] + TILE - 1) / TILE : 0;
   }
   const int t0 = ntx[0] * nty[0], total = t0 + ntx[1] * nty[1];
-  for (int t = blockIdx.x; t < total; t += gridDim.x) {
+  // output gradient tile, pixel-major: pixel r's channel group c4 (4 channels, 16 bytes) at
+  // group slot c4 ^ (r mod COUT/4), which spreads a warp's accesses of one group over the banks
+  auto fetch = [&](int t, float* sg) {
+    float* sa = sg + NTHR * COUT;
     const int d = (t < t0) ? 0 : 1;
     const int tl = (d == 0) ? t : t - t0;
     const int x0 = (tl % ntx[d]) * TILE, y0 = (tl / ntx[d]) * TILE;
@@ -373,63 +402,96 @@ __global__ void __launch_bounds__(NTHR) nn_wgrad_f32_kernel(NnArgs n, const void
     const long long pix = (long long)H * Wd;
     const float* G = chan_img<float>(gout, COUT, d, n.pix0);
     const float* A = chan_img<float>(ain, CIN, d, n.pix0);
-    __syncthreads();
-    for (int k = threadIdx.x; k < COUT * NTHR; k += NTHR) {
-      const int co = k / NTHR, r = k % NTHR;
+    for (int k = threadIdx.x; k < (COUT / 4) * NTHR; k += NTHR) {
+      const int c4 = k / NTHR, r = k % NTHR;
       const int gy = y0 + r / TILE, gx = x0 + r % TILE;
-      sg[r * COUT + co] = (gy < H && gx < Wd) ? G[co * pix + (long long)gy * Wd + gx] : 0.0f;
+      const bool in = gy < H && gx < Wd;
+      const long long o = in ? (long long)gy * Wd + gx : 0;
+      float* dst = sg + 4 * (r * (COUT / 4) + (c4 ^ (r % (COUT / 4))));
+#pragma unroll
+      for (int j = 0; j < 4; ++j) cp_async4(dst + j, G + (4 * c4 + j) * pix + o, in);
     }
     for (int k = threadIdx.x; k < CIN * TH * TH; k += NTHR) {
       const int ci = k / (TH * TH), r = k % (TH * TH);
       const int gy = y0 + r / TH - 1, gx = x0 + r % TH - 1;
-      sa[k] = (gy >= 0 && gy < H && gx >= 0 && gx < Wd) ? A[ci * pix + (long long)gy * Wd + gx] : 0.0f;
+      const bool in = gy >= 0 && gy < H && gx >= 0 && gx < Wd;
+      cp_async4(sa + k, A + ci * pix + (in ? (long long)gy * Wd + gx : 0), in);
     }
-    __syncthreads();
+  };
+  int cur = 0;
+  if ((int)blockIdx.x < total) fetch(blockIdx.x, buf0);
+  cp_async_commit();
+  for (int t = blockIdx.x; t < total; t += gridDim.x) {
+    const int tn = t + gridDim.x;
+    if (tn < total) fetch(tn, buf0 + (cur ^ 1) * TF);
+    cp_async_commit();
+    cp_async_wait<1>();  // this thread's copies of tile t are done
+    __syncthreads();     // and everyone's
+    const float* sg = buf0 + cur * TF;
+    const float* sa = sg + NTHR * COUT;
 #pragma unroll
-    for (int r = 0; r < PER; ++r) {
-      const int item = threadIdx.x + r * NTHR;
-      if (item >= NI) continue;
+    for (int u = 0; u < 3; ++u) {
+      const int unit = threadIdx.x + u * NTHR;
+      const int item = unit % NI, part = unit / NI;
       const int c4 = item / (CIN * 3), rem = item % (CIN * 3), ci = rem / 3, ky = rem % 3;
-      for (int py = 0; py < TILE; ++py) {
+      for (int py = part * RROWS; py < (part + 1) * RROWS; ++py) {
         const float* arow = sa + ci * TH * TH + (py + ky) * TH;
-        const float4* g4 = reinterpret_cast<const float4*>(sg + py * TILE * COUT) + c4;
+        const float4* g4 = reinterpret_cast<const float4*>(sg + py * TILE * COUT);
         float a0 = arow[0], a1 = arow[1];
 #pragma unroll
         for (int px = 0; px < TILE; ++px) {
           const float a2 = arow[px + 2];
-          const float4 g = g4[px * (COUT / 4)];
-          acc[r][0] = fmaf(g.x, a0, acc[r][0]);
-          acc[r][1] = fmaf(g.y, a0, acc[r][1]);
-          acc[r][2] = fmaf(g.z, a0, acc[r][2]);
-          acc[r][3] = fmaf(g.w, a0, acc[r][3]);
-          acc[r][4] = fmaf(g.x, a1, acc[r][4]);
-          acc[r][5] = fmaf(g.y, a1, acc[r][5]);
-          acc[r][6] = fmaf(g.z, a1, acc[r][6]);
-          acc[r][7] = fmaf(g.w, a1, acc[r][7]);
-          acc[r][8] = fmaf(g.x, a2, acc[r][8]);
-          acc[r][9] = fmaf(g.y, a2, acc[r][9]);
-          acc[r][10] = fmaf(g.z, a2, acc[r][10]);
-          acc[r][11] = fmaf(g.w, a2, acc[r][11]);
+          const float4 g = g4[px * (COUT / 4) + (c4 ^ ((py * TILE + px) % (COUT / 4)))];
+          acc[u][0] = fmaf(g.x, a0, acc[u][0]);
+          acc[u][1] = fmaf(g.y, a0, acc[u][1]);
+          acc[u][2] = fmaf(g.z, a0, acc[u][2]);
+          acc[u][3] = fmaf(g.w, a0, acc[u][3]);
+          acc[u][4] = fmaf(g.x, a1, acc[u][4]);
+          acc[u][5] = fmaf(g.y, a1, acc[u][5]);
+          acc[u][6] = fmaf(g.z, a1, acc[u][6]);
+          acc[u][7] = fmaf(g.w, a1, acc[u][7]);
+          acc[u][8] = fmaf(g.x, a2, acc[u][8]);
+          acc[u][9] = fmaf(g.y, a2, acc[u][9]);
+          acc[u][10] = fmaf(g.z, a2, acc[u][10]);
+          acc[u][11] = fmaf(g.w, a2, acc[u][11]);
           a0 = a1;
           a1 = a2;
         }
       }
     }
-    if (threadIdx.x < COUT)
-      for (int q = 0; q < NTHR; ++q) bacc += sg[q * COUT + threadIdx.x];
+    {
+      const int co = threadIdx.x % COUT, c4 = co / 4, j = co % 4;
+      for (int q = threadIdx.x / COUT; q < NTHR; q += NTHR / COUT)
+        bacc += sg[(q * (COUT / 4) + (c4 ^ (q % (COUT / 4)))) * 4 + j];
+    }
+    __syncthreads();  // tile t is read: its buffer takes tile t + 2 gridDim.x next
+    cur ^= 1;
   }
+  cp_async_wait<0>();
+  // block sums: (item, part) units and bias partials through shared memory, added in part order
+  __syncthreads();
+  float* red = reinterpret_cast<float*>(smem_raw);  // [WG_UNITS][12], then [NTHR] bias partials
+  float* bred = red + WG_UNITS * 12;
+#pragma unroll
+  for (int u = 0; u < 3; ++u)
+#pragma unroll
+    for (int k = 0; k < 12; ++k) red[(threadIdx.x + u * NTHR) * 12 + k] = acc[u][k];
+  bred[threadIdx.x] = bacc;
+  __syncthreads();
   double* part = n.partial + (long long)blockIdx.x * NN_NPARAM + woff;
-#pragma unroll
-  for (int r = 0; r < PER; ++r) {
-    const int item = threadIdx.x + r * NTHR;
-    if (item >= NI) continue;
+  for (int e = threadIdx.x; e < NI * 12; e += NTHR) {
+    const int item = e / 12, k = e % 12;
+    float sum = 0.0f;
+    for (int pr = 0; pr < R; ++pr) sum += red[(pr * NI + item) * 12 + k];
     const int c4 = item / (CIN * 3), rem = item % (CIN * 3), ci = rem / 3, ky = rem % 3;
-#pragma unroll
-    for (int kx = 0; kx < 3; ++kx)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) part[(((4 * c4 + j) * CIN + ci) * 3 + ky) * 3 + kx] = (double)acc[r][4 * kx + j];
+    const int kx = k / 4, jj = k % 4;
+    part[(((4 * c4 + jj) * CIN + ci) * 3 + ky) * 3 + kx] = (double)sum;
   }
-  if (threadIdx.x < COUT) part[COUT * CIN * 9 + threadIdx.x] = (double)bacc;
+  if (threadIdx.x < COUT) {
+    float sum = 0.0f;
+    for (int q = 0; q < NTHR / COUT; ++q) sum += bred[q * COUT + threadIdx.x];
+    part[COUT * CIN * 9 + threadIdx.x] = (double)sum;
+  }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -487,10 +549,16 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t r[16]) {
 // per thread, stored as one 16-byte vector), issues the MMAs, waits, and stores the row.
 constexpr int TC_ROWS = 16;
 
-template <int CIN, int COUT, int ACT>
+// MODE 0: a layer's forward (bias, then ReLU for ACT 0, tanh for ACT 1).  MODE 1: a layer's data
+// gradient, the same implicit GEMM over the output gradient with the weights transposed and
+// flipped, gin[ci] = sum over taps and co of w[co][ci][2-ky][2-kx] gout[co](pixel + (ky-1, kx-1)),
+// times the ReLU mask (aprev > 0) of the layer below for ACT 1.  CINR <= CIN: channels present
+// in the input (the rest are zero padding up to the MMA's K of 16).
+template <int CIN, int COUT, int ACT, int MODE = 0, int CINR = CIN>
 __global__ void __launch_bounds__(128) nn_conv_tc_kernel(NnArgs n, const void* inh, void* out, int woff,
-                                                         void* outh) {
+                                                         void* outh, const void* aprev) {
   static_assert(CIN % 16 == 0, "input channels in groups of 16 (K of one MMA)");
+  static_assert(CINR <= CIN && (MODE == 1 || CINR == CIN), "padding only in the data gradient");
   constexpr int N = (COUT + 15) / 16 * 16;   // MMA N (multiple of 16 for M = 128)
   constexpr int KG = CIN / 8;                // 8-channel groups
   constexpr int GSTRIDE = TC_COLS * 16;      // bytes of one channel group of one row slot
@@ -520,10 +588,13 @@ __global__ void __launch_bounds__(128) nn_conv_tc_kernel(NnArgs n, const void* i
   __nv_bfloat16* B16 = reinterpret_cast<__nv_bfloat16*>(sB);
   for (int k = tid; k < 9 * CIN * N; k += 128) {
     const int tap = k / (CIN * N), r = k % (CIN * N), ci = r / N, co = r % N;
-    const float v = (co < COUT) ? (float)n.w[woff + (co * CIN + ci) * 9 + tap] : 0.0f;
+    float v = 0.0f;
+    if (co < COUT && ci < CINR)
+      v = (MODE == 0) ? (float)n.w[woff + (co * CIN + ci) * 9 + tap] : (float)n.w[woff + (ci * COUT + co) * 9 + 8 - tap];
     B16[tap * (BTAP / 2) + ((ci >> 3) * N + co) * 8 + (ci & 7)] = __float2bfloat16_rn(v);
   }
-  for (int k = tid; k < COUT; k += 128) sbias[k] = (float)n.w[woff + COUT * CIN * 9 + k];
+  if (MODE == 0)
+    for (int k = tid; k < COUT; k += 128) sbias[k] = (float)n.w[woff + COUT * CIN * 9 + k];
   __syncthreads();
   const uint32_t tmem = tmem_base;
   const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
@@ -543,6 +614,7 @@ __global__ void __launch_bounds__(128) nn_conv_tc_kernel(NnArgs n, const void* i
     float* Y = chan_img<float>(out, COUT, d, n.pix0);
     __nv_bfloat16* Yh = outh ? static_cast<__nv_bfloat16*>(outh) + (d == 0 ? 0LL : (long long)COUT * n.pix0)
                              : nullptr;
+    const float* Ap = (MODE == 1 && ACT == 1) ? chan_img<float>(aprev, COUT, d, n.pix0) : nullptr;
     // input row r (zeros outside the image) into its ring slot: 16-byte copies of 8 channels
     // of a pixel from the BF16 pixel-major input (consecutive threads: consecutive 16 bytes)
     auto load_row = [&](int r) {
@@ -597,12 +669,21 @@ __global__ void __launch_bounds__(128) nn_conv_tc_kernel(NnArgs n, const void* i
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (gx < Wd) {
           float v[16];
+          if (MODE == 1 && ACT == 1) {
+            // the 16 mask values are loaded before any store, so that they are in flight together
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] = (c0 + j < COUT) ? __ldg(Ap + (c0 + j) * pix + o) : 0.0f;
+          }
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const int co = c0 + j;
             if (co < COUT) {
-              const float z = __uint_as_float(r[j]) + sbias[co];
-              v[j] = (ACT == 0) ? (z > 0.0f ? z : 0.0f) : tanhf(z);
+              if (MODE == 0) {
+                const float z = __uint_as_float(r[j]) + sbias[co];
+                v[j] = (ACT == 0) ? (z > 0.0f ? z : 0.0f) : tanhf(z);
+              } else {
+                v[j] = (ACT == 1 && !(v[j] > 0.0f)) ? 0.0f : __uint_as_float(r[j]);
+              }
               Y[co * pix + o] = v[j];
             }
           }
@@ -640,6 +721,34 @@ __global__ void nn_store_kernel(const T* __restrict__ T3, double* __restrict__ Y
   if (t < 4 * pix) Y[t] = n.scale[t / pix] * (double)T3[t];
 }
 
+// reverse of js_nn_eval: seed G4 = GY * scale * (1 - T3^2) (the derivative of scale * tanh) with an
+// optional BF16 pixel-major copy padded to 16 channels, and the input gradient back to FP64
+template <class T>
+__global__ void nn_seed_eval_kernel(NnArgs n, const double* __restrict__ GY, long long pix, __nv_bfloat16* gh) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= pix) return;
+  const T* t3 = static_cast<const T*>(n.T3);
+  T* g = static_cast<T*>(n.G4);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const double t = (double)t3[k * pix + p];
+    g[k * pix + p] = (T)(GY[k * pix + p] * n.scale[k] * (1.0 - t * t));
+  }
+  if (gh) {
+    __align__(16) __nv_bfloat16 v8[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v8[e] = __float2bfloat16_rn(e < 4 ? (float)g[e * pix + p] : 0.0f);
+    uint4* dst = reinterpret_cast<uint4*>(gh + p * 16);
+    dst[0] = *reinterpret_cast<const uint4*>(v8);
+    dst[1] = make_uint4(0u, 0u, 0u, 0u);
+  }
+}
+template <class T>
+__global__ void nn_unload_kernel(const T* __restrict__ G, double* __restrict__ GX, long long n4) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n4) GX[t] = (double)G[t];
+}
+
 // stage output (or RHS) minus the neural flux divergence on fluid cells
 template <class T>
 __global__ void nn_apply_kernel(NnArgs n, StageArgs a, int rhs) {
@@ -673,8 +782,10 @@ __global__ void nn_apply_kernel(NnArgs n, StageArgs a, int rhs) {
 // reverse
 // ---------------------------------------------------------------------------------------
 // dZ3 = (face-flux adjoint in the frame) * scale * (1 - t^2)
+// (gh: optional BF16 pixel-major copy, 16 channels per pixel with 12 zeros, the input of the
+// tensor-core data gradient of the last layer)
 template <class T>
-__global__ void nn_seed_kernel(NnArgs n, AdjArgs a) {
+__global__ void nn_seed_kernel(NnArgs n, AdjArgs a, __nv_bfloat16* gh) {
   const int d = blockIdx.y;
   const int Wd = n.W[d];
   const long long pix = (long long)n.H[d] * Wd;
@@ -693,6 +804,14 @@ __global__ void nn_seed_kernel(NnArgs n, AdjArgs a) {
     const double Fb = (a.lam[c * L.plane + cb] - a.lam[c * L.plane + ca]) * invh;
     const double t = (double)t3[k * pix + p];
     g[k * pix + p] = (T)(Fb * n.scale[k] * (1.0 - t * t));
+  }
+  if (gh) {
+    __align__(16) __nv_bfloat16 v8[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v8[e] = __float2bfloat16_rn(e < 4 ? (float)g[e * pix + p] : 0.0f);
+    uint4* dst = reinterpret_cast<uint4*>(gh + (d == 0 ? 0LL : 16LL * n.pix0) + p * 16);
+    dst[0] = *reinterpret_cast<const uint4*>(v8);
+    dst[1] = make_uint4(0u, 0u, 0u, 0u);
   }
 }
 
@@ -929,7 +1048,8 @@ cudaError_t dgrad(const NnArgs& n, const void* gout, const void* aprev, void* gi
 template <class T, int CIN, int COUT>
 cudaError_t wgrad(const NnArgs& n, const void* gout, const void* ain, int woff, cudaStream_t s) {
   if (std::is_same<T, float>::value) {
-    const size_t sm = sizeof(float) * (NTHR * COUT + CIN * TH * TH);
+    const size_t tiles = 2 * wgrad_tile_floats<CIN, COUT>(), sums = WG_UNITS * 12 + NTHR;
+    const size_t sm = sizeof(float) * (tiles > sums ? tiles : sums);
     auto k = nn_wgrad_f32_kernel<CIN, COUT>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
@@ -944,11 +1064,12 @@ cudaError_t wgrad(const NnArgs& n, const void* gout, const void* ain, int woff, 
   return cudaGetLastError();
 }
 
-template <int CIN, int COUT, int ACT>
-cudaError_t conv_tc(const NnArgs& n, const void* inh, void* out, int woff, cudaStream_t s, void* outh = nullptr) {
+template <int CIN, int COUT, int ACT, int MODE = 0, int CINR = CIN>
+cudaError_t conv_tc(const NnArgs& n, const void* inh, void* out, int woff, cudaStream_t s, void* outh = nullptr,
+                    const void* aprev = nullptr) {
   constexpr int N = (COUT + 15) / 16 * 16;
   const size_t sm = TC_AREGION + 9 * (CIN / 8) * N * 16 + COUT * sizeof(float);
-  auto k = nn_conv_tc_kernel<CIN, COUT, ACT>;
+  auto k = nn_conv_tc_kernel<CIN, COUT, ACT, MODE, CINR>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   // one block per work item: the occupancy query reports one block per SM for this kernel
@@ -956,7 +1077,7 @@ cudaError_t conv_tc(const NnArgs& n, const void* inh, void* out, int woff, cudaS
   // co-schedules; each block allocates its 32 tensor-memory columns once and frees them
   long long items = 0;
   for (int d = 0; d < n.nimg; ++d) items += (long long)cdiv(n.W[d], TC_M) * cdiv(n.H[d], TC_ROWS);
-  k<<<(unsigned)items, 128, sm, s>>>(n, inh, out, woff, outh);
+  k<<<(unsigned)items, 128, sm, s>>>(n, inh, out, woff, outh, aprev);
   return cudaGetLastError();
 }
 
@@ -999,21 +1120,31 @@ cudaError_t eval_t(const NnArgs& n0, const double* X, int H, int W, double* Y, c
   return cudaGetLastError();
 }
 
-template <class T>
-cudaError_t reverse_t(const NnArgs& n0, const AdjArgs& a, cudaStream_t s) {
-  // no more weight-gradient blocks than tiles (small images leave most blocks idle)
+// no more weight-gradient blocks than tiles (small images leave most blocks idle)
+NnArgs capped_wblocks(const NnArgs& n0) {
   NnArgs n = n0;
   long long tiles = 0;
   for (int d = 0; d < n.nimg; ++d) tiles += (long long)cdiv(n.W[d], TILE) * cdiv(n.H[d], TILE);
   if (tiles < n.nwblk) n.nwblk = (int)tiles;
-  cudaError_t e = forward_t<T>(n, a.Q, a.lay.plane, s);
+  return n;
+}
+
+// the layers' reverse from G4 = dZ3 (activations A1, A2 of the forward in place): data gradients
+// down to G4 = dX, weight gradients added to w_bar when it is set.  BF16 mode: the data
+// gradients of layers 3 and 2 run on the tensor cores, reading BF16 pixel-major copies of G4
+// (written by the seed into the A1h buffer) and G32 (into A2h): the forward's BF16 activations
+// are no longer needed there.
+template <class T>
+cudaError_t layers_vjp_t(const NnArgs& n, cudaStream_t s) {
+  cudaError_t e;
+  const bool tc = std::is_same<T, float>::value && n.bf16;
+  if (tc) e = conv_tc<16, 32, 1, 1, 4>(n, n.A1h, n.G32, NN_OFF3, s, n.A2h, n.A2);                 // G32 = dZ2
+  else e = dgrad<T, 32, 4, true>(n, n.G4, n.A2, n.G32, NN_OFF3, s);
   if (e != cudaSuccess) return e;
-  const dim3 pg(cdiv(max_pix(n), 256), n.nimg);
-  nn_seed_kernel<T><<<pg, 256, 0, s>>>(n, a);                                   // G4 = dZ3
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if ((e = dgrad<T, 32, 4, true>(n, n.G4, n.A2, n.G32, NN_OFF3, s)) != cudaSuccess) return e;   // G32 = dZ2
   if (n.w_bar && (e = wgrad<T, 32, 4>(n, n.G4, n.A2, NN_OFF3, s)) != cudaSuccess) return e;
-  if ((e = dgrad<T, 16, 32, true>(n, n.G32, n.A1, n.G16, NN_OFF2, s)) != cudaSuccess) return e;  // G16 = dZ1
+  if (tc) e = conv_tc<32, 16, 1, 1>(n, n.A2h, n.G16, NN_OFF2, s, nullptr, n.A1);                   // G16 = dZ1
+  else e = dgrad<T, 16, 32, true>(n, n.G32, n.A1, n.G16, NN_OFF2, s);
+  if (e != cudaSuccess) return e;
   if (n.w_bar && (e = wgrad<T, 16, 32>(n, n.G32, n.A1, NN_OFF2, s)) != cudaSuccess) return e;
   if ((e = dgrad<T, 4, 16, false>(n, n.G16, nullptr, n.G4, NN_OFF1, s)) != cudaSuccess) return e;  // G4 = dX
   if (n.w_bar) {
@@ -1021,7 +1152,42 @@ cudaError_t reverse_t(const NnArgs& n0, const AdjArgs& a, cudaStream_t s) {
     nn_wreduce_kernel<<<cdiv(NN_NPARAM, 256), 256, 0, s>>>(n);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
+  return cudaSuccess;
+}
+
+template <class T>
+cudaError_t reverse_t(const NnArgs& n0, const AdjArgs& a, cudaStream_t s) {
+  const NnArgs n = capped_wblocks(n0);
+  cudaError_t e = forward_t<T>(n, a.Q, a.lay.plane, s);
+  if (e != cudaSuccess) return e;
+  const dim3 pg(cdiv(max_pix(n), 256), n.nimg);
+  const bool tc = std::is_same<T, float>::value && n.bf16;
+  nn_seed_kernel<T><<<pg, 256, 0, s>>>(n, a, tc ? static_cast<__nv_bfloat16*>(n.A1h) : nullptr);  // G4 = dZ3
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = layers_vjp_t<T>(n, s)) != cudaSuccess) return e;
   nn_image_vjp_kernel<T><<<pg, 256, 0, s>>>(n, a);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t eval_vjp_t(const NnArgs& n0, const double* X, int H, int W, const double* GY, double* GX,
+                       cudaStream_t s) {
+  NnArgs n = n0;
+  n.nimg = 1;
+  n.H[0] = H;
+  n.W[0] = W;
+  n.pix0 = (long long)H * W;
+  n = capped_wblocks(n);
+  const long long pix = n.pix0;
+  nn_load_kernel<T><<<cdiv(4 * pix, 256), 256, 0, s>>>(X, static_cast<T*>(n.X), 4 * pix);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if ((e = layers_t<T>(n, s)) != cudaSuccess) return e;
+  const bool tc = std::is_same<T, float>::value && n.bf16;
+  nn_seed_eval_kernel<T><<<cdiv(pix, 256), 256, 0, s>>>(n, GY, pix, tc ? static_cast<__nv_bfloat16*>(n.A1h) : nullptr);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = layers_vjp_t<T>(n, s)) != cudaSuccess) return e;
+  nn_unload_kernel<T><<<cdiv(4 * pix, 256), 256, 0, s>>>(static_cast<const T*>(n.G4), GX, 4 * pix);
   return cudaGetLastError();
 }
 
@@ -1038,6 +1204,11 @@ cudaError_t nn_forward(const NnArgs& n, const double* Q, long long qplane, cudaS
 
 cudaError_t nn_eval(const NnArgs& n, const double* X, int H, int W, double* Y, cudaStream_t s) {
   return n.fp32 ? eval_t<float>(n, X, H, W, Y, s) : eval_t<double>(n, X, H, W, Y, s);
+}
+
+cudaError_t nn_eval_vjp(const NnArgs& n, const double* X, int H, int W, const double* GY, double* GX,
+                        cudaStream_t s) {
+  return n.fp32 ? eval_vjp_t<float>(n, X, H, W, GY, GX, s) : eval_vjp_t<double>(n, X, H, W, GY, GX, s);
 }
 
 cudaError_t nn_apply(const NnArgs& n, const StageArgs& a, bool rhs, cudaStream_t s) {

@@ -9,7 +9,17 @@ tcgen05 implicit GEMMs, BF16 operands, FP32 accumulation) and js_nn_eval.
   layout gives errors of order one everywhere.  Images span several 128-pixel blocks with a
   ragged tail, a block narrower than 128 and a single row.
 * The solver with the BF16 network: RHS within 3e-2 of the network's contribution of the
-  oracle (FP64 network), the rest at the FP64 bar."""
+  oracle (FP64 network), the rest at the FP64 bar.
+* js_nn_eval_vjp (the network's reverse alone): FP64 equal to torch's float64 autograd of the
+  same network (itself pinned to the oracle's network on the CPU) to 1e-12, FP32 within FP32
+  rounding; BF16 (data gradients of layers 3 and 2 on the tensor cores from BF16 copies of
+  the output gradients, padded from 4 to 16 channels for layer 3; weight gradients FP32)
+  equal to a CPU emulation of that arithmetic with the same bounds as the forward (a
+  transposed or unflipped weight layout gives errors of order one).
+* The solver's reverse in BF16 mode against its FP32 mode (which the oracle pins): the
+  network's part of the state adjoint and the weight gradient within the BF16 forward's
+  own deviation (its activations, tanh output and ReLU masks differ from FP32 by BF16
+  rounding), the median element at the 1e-2 level."""
 import numpy as np
 import pytest
 
@@ -113,3 +123,112 @@ def test_bf16_solver_rhs_within_bound(env):
     err = np.abs(to_host(s.rhs(to_dev(U))) - L_ref).max()
     assert s.status() == 0
     assert part > 0 and err <= 3e-2 * part + 1e-10 * np.abs(L_ref).max(), (err, part)
+
+
+@pytest.mark.parametrize("viscous", [False, True])
+def test_bf16_reverse_matches_fp32_reverse(env, viscous):
+    torch, B = env
+    p = W.shock_cylinder(nx=70, ny=45, Lx=3.5, Ly=2.25, centre=(1.6, 1.1), radius=0.45, x_shock=0.8,
+                         viscous=viscous)
+    U = to_dev(O.prim_to_cons(p, W.random_state(p, seed=2, amp=0.02)))
+    lam = to_dev(np.random.default_rng(6).standard_normal((4, p.ny, p.nx)))
+    w = torch.tensor(_params(5, amp=0.12), device="cuda")
+    s = B.Solver.from_problem(p)
+    dt = 0.3 * s.max_dt(U, 0.5)
+    off, _ = s.rhs_vjp(U, lam)
+    off_step, _ = s.step_vjp(U, dt, lam)
+    out = {}
+    for prec in ("fp32", "bf16"):
+        wb = torch.zeros(NP, dtype=torch.float64, device="cuda")
+        s.set_neural(w, NORM, w_bar=wb, precision=prec)
+        Ub, pb = s.rhs_vjp(U, lam)
+        wb2 = torch.zeros_like(wb)
+        s.set_neural(w, NORM, w_bar=wb2, precision=prec)
+        ls, _ = s.step_vjp(U, dt, lam)
+        out[prec] = (to_host(Ub), to_host(wb), to_host(ls), to_host(wb2))
+        assert s.status() == 0
+    net = np.abs(out["fp32"][0] - to_host(off)).max()
+    net_step = np.abs(out["fp32"][2] - to_host(off_step)).max()
+    assert net > 0 and net_step > 0
+    for k, ref_scale in ((0, net), (1, None), (2, net_step), (3, None)):
+        a, b = out["bf16"][k], out["fp32"][k]
+        scale = ref_scale if ref_scale is not None else np.abs(b).max()
+        d = np.abs(a - b)
+        assert d.max() <= 0.25 * scale, (k, d.max() / scale)
+        assert np.median(d) <= 1e-2 * scale, (k, np.median(d) / scale)
+
+
+def _torch_net(torch, w, dtype):
+    t = torch.tensor(w, dtype=dtype)
+    return (t[:576].view(16, 4, 3, 3), t[576:592], t[592:5200].view(32, 16, 3, 3), t[5200:5232],
+            t[5232:6384].view(4, 32, 3, 3), t[6384:])
+
+
+def _grads_flat(dw1, db1, dw2, db2, dw3, db3):
+    return np.concatenate([x.reshape(-1).double().numpy() for x in (dw1, db1, dw2, db2, dw3, db3)])
+
+
+def _autograd_vjp(torch, w, X, GY, scale):
+    import torch.nn.functional as F
+    ps = [p.clone().requires_grad_(True) for p in _torch_net(torch, w, torch.float64)]
+    x = torch.tensor(X, dtype=torch.float64, requires_grad=True)
+    a1 = torch.relu(F.conv2d(x[None], ps[0], ps[1], padding=1))
+    a2 = torch.relu(F.conv2d(a1, ps[2], ps[3], padding=1))
+    y = torch.tensor(scale, dtype=torch.float64)[:, None, None] * torch.tanh(F.conv2d(a2, ps[4], ps[5], padding=1)[0])
+    g = torch.autograd.grad(y, [x] + ps, torch.tensor(GY, dtype=torch.float64))
+    return g[0].numpy(), _grads_flat(*g[1:])
+
+
+def _emulate_bf16_vjp(torch, w, X, GY, scale):
+    """The BF16 mode's reverse, rounding where the kernels round (FP32 elsewhere)."""
+    import torch.nn.functional as F
+    from torch.nn.grad import conv2d_input, conv2d_weight
+    w1, b1, w2, b2, w3, b3 = _torch_net(torch, w, torch.float32)
+    bf = lambda a: a.to(torch.bfloat16).to(torch.float32)
+    x = torch.tensor(X, dtype=torch.float32)[None]
+    a1 = torch.relu(F.conv2d(x, w1, b1, padding=1))
+    a2 = torch.relu(F.conv2d(bf(a1), bf(w2), b2, padding=1))
+    t3 = torch.tanh(F.conv2d(bf(a2), bf(w3), b3, padding=1))
+    g4 = (torch.tensor(GY, dtype=torch.float64)[None] * torch.tensor(scale, dtype=torch.float64)[:, None, None]
+          * (1.0 - t3.double() ** 2)).float()
+    g32 = conv2d_input(a2.shape, bf(w3), bf(g4), padding=1) * (a2 > 0)
+    g16 = conv2d_input(a1.shape, bf(w2), bf(g32), padding=1) * (a1 > 0)
+    gx = conv2d_input(x.shape, w1, g16, padding=1)
+    dw3 = conv2d_weight(a2, w3.shape, g4, padding=1)
+    dw2 = conv2d_weight(a1, w2.shape, g32, padding=1)
+    dw1 = conv2d_weight(x, w1.shape, g16, padding=1)
+    return gx[0].double().numpy(), _grads_flat(dw1, g16.sum((0, 2, 3)), dw2, g32.sum((0, 2, 3)), dw3,
+                                               g4.sum((0, 2, 3)))
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_nn_eval_vjp_fp64_fp32_and_bf16(env, shape):
+    torch, B = env
+    w = _params(7)
+    rng = np.random.default_rng(8)
+    X = rng.standard_normal((4,) + shape)
+    GY = rng.standard_normal((4,) + shape)
+    gx_ref, gw_ref = _autograd_vjp(torch, w, X, GY, NORM[8:])
+    s = _solver(B)
+    wd = torch.tensor(w, device="cuda")
+    for prec, tol in (("fp64", 1e-12), ("fp32", 2e-4)):
+        wb = torch.zeros(NP, dtype=torch.float64, device="cuda")
+        s.set_neural(wd, NORM, w_bar=wb, precision=prec)
+        gx = to_host(s.nn_eval_vjp(to_dev(X), to_dev(GY)))
+        assert np.abs(gx - gx_ref).max() <= tol * np.abs(gx_ref).max(), prec
+        assert np.abs(to_host(wb) - gw_ref).max() <= tol * np.abs(gw_ref).max(), prec
+    wb = torch.zeros(NP, dtype=torch.float64, device="cuda")
+    s.set_neural(wd, NORM, w_bar=wb, precision="bf16")
+    gx = to_host(s.nn_eval_vjp(to_dev(X), to_dev(GY)))
+    gb = to_host(wb)
+    assert s.status() == 0
+    ex, ew = _emulate_bf16_vjp(torch, w, X, GY, NORM[8:])
+    span = np.abs(ex).max()
+    d = np.abs(gx - ex)
+    assert np.median(d) <= 1e-5 * span and np.quantile(d, 0.99) <= 1e-3 * span, (np.median(d) / span,
+                                                                                   np.quantile(d, 0.99) / span)
+    assert d.max() <= 1e-2 * span, d.max() / span
+    dw = np.abs(gb - ew)
+    assert dw.max() <= 1e-3 * np.abs(ew).max(), dw.max() / np.abs(ew).max()
+    # and against the exact reverse: of the order of BF16 rounding
+    assert np.quantile(np.abs(gx - gx_ref), 0.99) <= 5e-2 * np.abs(gx_ref).max()
