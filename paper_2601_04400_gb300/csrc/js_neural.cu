@@ -112,30 +112,44 @@ __global__ void nn_prims_kernel(const double* __restrict__ U, double* __restrict
   Q[3 * L.plane + t] = p;
 }
 
+// The image kernels work on 32 x 32 tiles of (line h, face f) pixels: the FP64 face-state
+// arithmetic runs with consecutive threads on consecutive lines, the direction along which the
+// stage's stored WENO5 internals and the face adjoints are contiguous in both directions, and the
+// image values (contiguous along f) pass through a shared-memory tile.
+constexpr int IT = 32;
+
 template <class T>
-__global__ void nn_image_kernel(NnArgs n, const double* __restrict__ Q, long long qplane) {
-  const int d = blockIdx.y;
-  const int Wd = n.W[d];
-  const long long pix = (long long)n.H[d] * Wd;
-  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= pix) return;
-  const int h = (int)(p / Wd), f = (int)(p % Wd);
-  double wl[4], wr[4];
-  face_states_any(n, n.lay, Q, qplane, d, h, f, wl, wr);
+__global__ void __launch_bounds__(256) nn_image_kernel(NnArgs n, const double* __restrict__ Q, long long qplane) {
+  __shared__ T sx[4][IT][IT + 1];
+  const int d = blockIdx.z;
+  const int H = n.H[d], Wd = n.W[d];
+  const int f0 = blockIdx.x * IT, h0 = blockIdx.y * IT;
+  if (f0 >= Wd || h0 >= H) return;  // uniform per block
+  const long long pix = (long long)H * Wd;
+  const int hl = threadIdx.x % IT;
   const int un = (d == 0) ? 1 : 2, ut = (d == 0) ? 2 : 1;
-  double m[4];
-  {
+  for (int fl = threadIdx.x / IT; fl < IT; fl += 256 / IT) {
+    const int h = h0 + hl, f = f0 + fl;
+    if (h >= H || f >= Wd) continue;
+    double wl[4], wr[4];
+    face_states_any(n, n.lay, Q, qplane, d, h, f, wl, wr);
     const double rL = wl[0], rR = wr[0];
     const double EL = fma(0.5 * rL, fma(wl[un], wl[un], wl[ut] * wl[ut]), wl[3] * n.g1);
     const double ER = fma(0.5 * rR, fma(wr[un], wr[un], wr[ut] * wr[ut]), wr[3] * n.g1);
+    double m[4];
     m[0] = 0.5 * (rL + rR);
     m[1] = 0.5 * fma(rL, wl[un], rR * wr[un]);
     m[2] = 0.5 * fma(rL, wl[ut], rR * wr[ut]);
     m[3] = 0.5 * (EL + ER);
-  }
-  T* X = chan_img<T>(n.X, 4, d, n.pix0);
 #pragma unroll
-  for (int k = 0; k < 4; ++k) X[k * pix + p] = (T)((m[k] - n.mean[k]) * n.inv_sd[k]);
+    for (int k = 0; k < 4; ++k) sx[k][hl][fl] = (T)((m[k] - n.mean[k]) * n.inv_sd[k]);
+  }
+  __syncthreads();
+  T* X = chan_img<T>(n.X, 4, d, n.pix0);
+  for (int e = threadIdx.x; e < 4 * IT * IT; e += 256) {
+    const int k = e / (IT * IT), r = e % (IT * IT), h = h0 + r / IT, f = f0 + r % IT;
+    if (h < H && f < Wd) X[k * pix + (long long)h * Wd + f] = sx[k][r / IT][r % IT];
+  }
 }
 
 // one 3x3 layer on a 16x16 pixel tile per block; ACT 0: ReLU, 1: tanh
@@ -943,27 +957,37 @@ __device__ __forceinline__ double nn_warp_sum(double v) {
 }
 
 // image reverse: network-input adjoint -> WENO face-state adjoints (added to a.fadj) and
-// d/dgamma of the face energies (added to pbar[0])
+// d/dgamma of the face energies (added to pbar[0]); 32 x 32 pixel tiles as nn_image_kernel
 template <class T>
-__global__ void nn_image_vjp_kernel(NnArgs n, AdjArgs a) {
-  const int d = blockIdx.y;
-  const int Wd = n.W[d];
-  const long long pix = (long long)n.H[d] * Wd;
-  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256) nn_image_vjp_kernel(NnArgs n, AdjArgs a) {
+  __shared__ T sx[4][IT][IT + 1];
+  __shared__ double red[8];
+  const int d = blockIdx.z;
+  const int H = n.H[d], Wd = n.W[d];
+  const int f0 = blockIdx.x * IT, h0 = blockIdx.y * IT;
+  if (f0 >= Wd || h0 >= H) return;  // uniform per block
+  const long long pix = (long long)H * Wd;
+  const T* dX = chan_img<T>(n.G4, 4, d, n.pix0);
+  for (int e = threadIdx.x; e < 4 * IT * IT; e += 256) {
+    const int k = e / (IT * IT), r = e % (IT * IT), h = h0 + r / IT, f = f0 + r % IT;
+    sx[k][r / IT][r % IT] = (h < H && f < Wd) ? dX[k * pix + (long long)h * Wd + f] : (T)0;
+  }
+  __syncthreads();
   double gbar = 0.0;
-  if (p < pix) {
-    const int h = (int)(p / Wd), f = (int)(p % Wd);
+  const int hl = threadIdx.x % IT;
+  const int un = (d == 0) ? 1 : 2, ut = (d == 0) ? 2 : 1;
+  const int fdir = d * 8;
+  for (int fl = threadIdx.x / IT; fl < IT; fl += 256 / IT) {
+    const int h = h0 + hl, f = f0 + fl;
+    if (h >= H || f >= Wd) continue;
     double wl[4], wr[4];
     face_states_any(n, a.lay, a.Q, a.lay.plane, d, h, f, wl, wr);
-    const T* dX = chan_img<T>(n.G4, 4, d, n.pix0);
     double gk[4];  // adjoint of each side's conserved frame state (the image is their mean)
 #pragma unroll
-    for (int k = 0; k < 4; ++k) gk[k] = 0.5 * n.inv_sd[k] * (double)dX[k * pix + p];
-    const int un = (d == 0) ? 1 : 2, ut = (d == 0) ? 2 : 1;
-    const int fdir = d * 8;
+    for (int k = 0; k < 4; ++k) gk[k] = 0.5 * n.inv_sd[k] * (double)sx[k][hl][fl];
     const long long si = (d == 0) ? (long long)(f + 3) * a.tpitch + (h + a.lay.gy) : a.lay.idx(h, f);
-    for (int s = 0; s < 2; ++s) {
-      const double* w = (s == 0) ? wl : wr;
+    for (int sd = 0; sd < 2; ++sd) {
+      const double* w = (sd == 0) ? wl : wr;
       const double r = w[0], vn = w[un], vt = w[ut], pr = w[3];
       double b[4];
       b[0] = fma(0.5 * fma(vn, vn, vt * vt), gk[3], fma(vn, gk[1], fma(vt, gk[2], gk[0])));
@@ -972,17 +996,16 @@ __global__ void nn_image_vjp_kernel(NnArgs n, AdjArgs a) {
       b[3] = gk[3] * n.g1;
       gbar -= pr * n.g1 * n.g1 * gk[3];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) a.fadj[(long long)(fdir + 4 * s + c) * a.splane + si] += b[c];
+      for (int c = 0; c < 4; ++c) a.fadj[(long long)(fdir + 4 * sd + c) * a.splane + si] += b[c];
     }
   }
   // one atomic per block: many blocks add to the same entry
-  __shared__ double red[8];
   gbar = nn_warp_sum(gbar);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = gbar;
   __syncthreads();
   if (threadIdx.x == 0 && a.pbar) {
     double t = 0.0;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+    for (int k = 0; k < 8; ++k) t += red[k];
     if (t != 0.0) atomicAdd(a.pbar, t);
   }
 }
@@ -996,6 +1019,15 @@ long long max_pix(const NnArgs& n) {
   long long m = (long long)n.H[0] * n.W[0];
   if (n.nimg > 1 && (long long)n.H[1] * n.W[1] > m) m = (long long)n.H[1] * n.W[1];
   return m;
+}
+
+dim3 image_grid(const NnArgs& n) {
+  int W = n.W[0], H = n.H[0];
+  if (n.nimg > 1) {
+    W = W > n.W[1] ? W : n.W[1];
+    H = H > n.H[1] ? H : n.H[1];
+  }
+  return dim3(cdiv(W, IT), cdiv(H, IT), n.nimg);
 }
 
 dim3 tile_grid(const NnArgs& n) {
@@ -1098,7 +1130,7 @@ cudaError_t layers_t(const NnArgs& n, cudaStream_t s) {
 
 template <class T>
 cudaError_t forward_t(const NnArgs& n, const double* Q, long long qplane, cudaStream_t s) {
-  nn_image_kernel<T><<<dim3(cdiv(max_pix(n), 256), n.nimg), 256, 0, s>>>(n, Q, qplane);
+  nn_image_kernel<T><<<image_grid(n), 256, 0, s>>>(n, Q, qplane);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return layers_t<T>(n, s);
@@ -1165,7 +1197,7 @@ cudaError_t reverse_t(const NnArgs& n0, const AdjArgs& a, cudaStream_t s) {
   nn_seed_kernel<T><<<pg, 256, 0, s>>>(n, a, tc ? static_cast<__nv_bfloat16*>(n.A1h) : nullptr);  // G4 = dZ3
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = layers_vjp_t<T>(n, s)) != cudaSuccess) return e;
-  nn_image_vjp_kernel<T><<<pg, 256, 0, s>>>(n, a);
+  nn_image_vjp_kernel<T><<<image_grid(n), 256, 0, s>>>(n, a);
   return cudaGetLastError();
 }
 
