@@ -107,7 +107,9 @@ int js_rhs_vjp(js_ctx* ctx, const double* U, const double* lam, double* U_bar, d
  *   p_bar += (dU_{n+1}/dtheta)^T lam_np1   (accumulated), device double[JS_NPARAM] or NULL
  * The three stage states are recomputed from U_n inside the call (on 2D grids the first
  * two forward stages also store their WENO5 internals for the reverse pass, which needs
- * 2 x 56 extra padded planes of workspace).  lam_n may alias lam_np1.  Asynchronous. */
+ * 2 x 56 extra padded planes of workspace; with the neural flux on, their network input and
+ * activations are kept too, 2 x 56 face-image channels allocated by the first such call, and
+ * recomputed instead when that allocation fails).  lam_n may alias lam_np1.  Asynchronous. */
 int js_step_vjp(js_ctx* ctx, const double* U_n, double dt, const double* lam_np1, double* lam_n,
                 double* p_bar);
 

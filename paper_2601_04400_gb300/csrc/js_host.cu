@@ -69,6 +69,10 @@ struct js_ctx {
   double* nn_wsave = nullptr;   // WENO5 internals of the current stage (2D; 56 planes)
   void* nn_buf[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   void* nn_bf16[2] = {nullptr, nullptr};  // BF16 pixel-major activations (16 and 32 channels)
+  // network input and activations (X, A1, A2, T3: 56 channels) of the forward stages 0 and 1 of
+  // js_step_vjp, kept for their reverse (allocated by the first js_step_vjp with the network on)
+  void* nn_keep[2] = {nullptr, nullptr};
+  bool nn_keep_failed = false;
   double* nn_partial = nullptr;
   int variant = 0;  // stage-kernel tile shape (js_set_tuning)
   std::vector<std::pair<const double*, js::TensorMap128>> tmaps;  // TMA maps of stage inputs
@@ -466,7 +470,9 @@ void js_destroy(js_ctx* c) {
   if (c->inflow_host) cudaFreeHost(c->inflow_host);
   cudaFree(c->nnQ); cudaFree(c->nn_partial); cudaFree(c->nn_wsave);
   for (void* b : c->nn_buf) cudaFree(b);
-  for (void* b : c->nn_bf16) cudaFree(b); cudaFree(c->inflow_acc); cudaFree(c->inflow_prim); cudaFree(c->qIb);
+  for (void* b : c->nn_bf16) cudaFree(b);
+  for (void* b : c->nn_keep) cudaFree(b);
+  cudaFree(c->inflow_acc); cudaFree(c->inflow_prim); cudaFree(c->qIb);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   for (double* t : c->tape) cudaFree(t);
   for (double* t : c->tape_w) cudaFree(t);
@@ -871,6 +877,40 @@ int js_rhs_vjp(js_ctx* c, const double* U, const double* lam, double* U_bar, dou
   return JS_OK;
 }
 
+namespace {
+
+// the network's kept forward of stage s (0, 1) of js_step_vjp: c->nn points at set s while the
+// forward stage runs (keep = 1) and while its reverse runs (fwd_ready = 1); false when the sets
+// are unavailable (the reverse then recomputes the forward)
+bool nn_keep_ready(js_ctx* c) {
+  if (!c->nn_on || c->nn_keep_failed) return false;
+  if (c->nn_keep[0] && c->nn_keep[1]) return true;
+  const size_t pix = (size_t)(c->nn.pix0 + (long long)c->nn.H[1] * c->nn.W[1]);
+  for (int k = 0; k < 2; ++k)
+    if (!c->nn_keep[k] && cudaMalloc(&c->nn_keep[k], sizeof(double) * 56 * pix) != cudaSuccess) {
+      c->nn_keep[k] = nullptr;
+      cudaGetLastError();  // clear the allocation error
+      c->nn_keep_failed = true;
+      return false;
+    }
+  return true;
+}
+js::NnArgs nn_use_kept(js_ctx* c, int s, bool reverse) {
+  const js::NnArgs prev = c->nn;
+  const size_t pix = (size_t)(c->nn.pix0 + (long long)c->nn.H[1] * c->nn.W[1]);
+  const size_t el = c->nn.fp32 ? sizeof(float) : sizeof(double);
+  char* b = static_cast<char*>(c->nn_keep[s]);
+  c->nn.X = b;
+  c->nn.A1 = b + el * 4 * pix;
+  c->nn.A2 = b + el * 20 * pix;
+  c->nn.T3 = b + el * 52 * pix;
+  c->nn.keep = 1;
+  c->nn.fwd_ready = reverse ? 1 : 0;
+  return prev;
+}
+
+}  // namespace
+
 int js_step_vjp(js_ctx* c, const double* U_n, double dt, const double* lam_np1, double* lam_n, double* p_bar) {
   if (!c || !U_n || !lam_np1 || !lam_n || !(dt > 0.0)) return JS_ERR_ARG;
   c->svjp_next = 2;  // the stage-wise reverse sequence (js_step_stage_vjp) restarts
@@ -896,6 +936,8 @@ int js_step_vjp(js_ctx* c, const double* U_n, double dt, const double* lam_np1, 
   double* outp[2] = {c->A, c->B};
   const double ra[3] = {0.0, 0.75, 1.0 / 3.0};
   const double rb[3] = {1.0, 0.25, 2.0 / 3.0};
+  // with the neural flux, the network's forward of stages 0 and 1 is kept for their reverse
+  const bool nnk = nn_keep_ready(c);
   for (int s = 0; s < 2; ++s) {
     if ((rc = fill_halos(c, in[s]))) return rc;
     a.Uin = in[s];
@@ -904,7 +946,9 @@ int js_step_vjp(js_ctx* c, const double* U_n, double dt, const double* lam_np1, 
     a.rk_a = ra[s];
     a.rk_b = rb[s];
     a.use_un = (s > 0) ? 1 : 0;
+    const js::NnArgs prev = nnk ? nn_use_kept(c, s, false) : c->nn;
     rc = keep ? stage_save(c, a, visc, saved[s]) : stage(c, a, visc, false);
+    c->nn = prev;
     if (rc) return rc;
   }
   if ((rc = fill_halos(c, c->B))) return rc;
@@ -914,7 +958,10 @@ int js_step_vjp(js_ctx* c, const double* U_n, double dt, const double* lam_np1, 
   double* src = c->P0;
   double* dst = c->P1;
   for (int s = 2; s >= 0; --s) {
-    if ((rc = adj_stage(c, X[s], src, dst, ra[s], rb[s], dt, false, p_bar, saved[s]))) return rc;
+    const js::NnArgs prev = (nnk && s < 2) ? nn_use_kept(c, s, true) : c->nn;
+    rc = adj_stage(c, X[s], src, dst, ra[s], rb[s], dt, false, p_bar, saved[s]);
+    c->nn = prev;
+    if (rc) return rc;
     double* t = src;
     src = dst;
     dst = t;
@@ -1169,6 +1216,8 @@ int js_set_neural(js_ctx* c, const double* w, double* w_bar, const double* norm,
   n.A2h = c->nn_bf16[1];
   n.fp32 = (precision != JS_NN_F64) ? 1 : 0;
   n.bf16 = (precision == JS_NN_BF16) ? 1 : 0;
+  n.keep = 0;
+  n.fwd_ready = 0;
   n.err = c->err;
   n.w = w;
   n.w_bar = w_bar;

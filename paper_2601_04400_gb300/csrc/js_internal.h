@@ -110,6 +110,9 @@ struct NnArgs {
   void* A1h;                  // BF16 copies of the activations of layers 1 and 2, pixel-major with
   void* A2h;                  //   the channels contiguous ([image][H][W][C]), tensor-core inputs
   int* err;                   // device error flag (bounded waits of the tensor-core layers)
+  int keep;                   // 1: the FP32 activations A1, A2 are written (a reverse pass reads
+                              //   them); 0: BF16 forward-only stages skip them
+  int fwd_ready;              // reverse: X, A1, A2, T3 of this stage's forward are in place
 };
 
 // forward: images of the stage input (primitives Q, plane qplane) and the network, into T3

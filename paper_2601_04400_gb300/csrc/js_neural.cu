@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(NTHR_F) nn_conv_f32_kernel(NnArgs n, const voi
   if (x0 >= Wd || y0 >= H) return;
   const long long pix = (long long)H * Wd;
   const float* X = chan_img<float>(in, CIN, d, n.pix0);
-  float* Y = chan_img<float>(out, COUT, d, n.pix0);
+  float* Y = out ? chan_img<float>(out, COUT, d, n.pix0) : nullptr;  // FP32 output (optional)
   for (int k = threadIdx.x; k < COUT * CIN * 9; k += NTHR_F) {
     const int co = k / (CIN * 9), r = k % (CIN * 9);
     sw[r * COUT + co] = (float)n.w[woff + k];
@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(NTHR_F) nn_conv_f32_kernel(NnArgs n, const voi
       for (int co = 0; co < COUT; ++co) {
         const float v = acc[q][co];
         acc[q][co] = (ACT == 0) ? (v > 0.0f ? v : 0.0f) : tanhf(v);
-        Y[co * pix + o] = acc[q][co];
+        if (Y) Y[co * pix + o] = acc[q][co];
       }
       if (outh) {
         // BF16 pixel-major copy (the tensor-core layer's input), 8 channels per 16-byte store
@@ -625,7 +625,7 @@ __global__ void __launch_bounds__(128) nn_conv_tc_kernel(NnArgs n, const void* i
     const long long pix = (long long)H * Wd;
     const uint4* Xh = reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(inh) +
                                                      (d == 0 ? 0LL : (long long)CIN * n.pix0));
-    float* Y = chan_img<float>(out, COUT, d, n.pix0);
+    float* Y = out ? chan_img<float>(out, COUT, d, n.pix0) : nullptr;  // FP32 output (optional)
     __nv_bfloat16* Yh = outh ? static_cast<__nv_bfloat16*>(outh) + (d == 0 ? 0LL : (long long)COUT * n.pix0)
                              : nullptr;
     const float* Ap = (MODE == 1 && ACT == 1) ? chan_img<float>(aprev, COUT, d, n.pix0) : nullptr;
@@ -698,7 +698,7 @@ __global__ void __launch_bounds__(128) nn_conv_tc_kernel(NnArgs n, const void* i
               } else {
                 v[j] = (ACT == 1 && !(v[j] > 0.0f)) ? 0.0f : __uint_as_float(r[j]);
               }
-              Y[co * pix + o] = v[j];
+              if (Y) Y[co * pix + o] = v[j];
             }
           }
           if (Yh && c0 + 16 <= COUT) {
@@ -1118,10 +1118,13 @@ template <class T>
 cudaError_t layers_t(const NnArgs& n, cudaStream_t s) {
   cudaError_t e;
   const bool tc = std::is_same<T, float>::value && n.bf16;
-  // (the tensor-core layers read BF16 pixel-major copies written by the layer before them)
-  if ((e = conv<T, 4, 16, 0>(n, n.X, n.A1, NN_OFF1, s, tc ? n.A1h : nullptr)) != cudaSuccess) return e;
+  // (the tensor-core layers read BF16 pixel-major copies written by the layer before them; their
+  // FP32 activations are written only for a reverse pass)
+  void* a1 = (tc && !n.keep) ? nullptr : n.A1;
+  void* a2 = (tc && !n.keep) ? nullptr : n.A2;
+  if ((e = conv<T, 4, 16, 0>(n, n.X, a1, NN_OFF1, s, tc ? n.A1h : nullptr)) != cudaSuccess) return e;
   if (tc) {
-    if ((e = conv_tc<16, 32, 0>(n, n.A1h, n.A2, NN_OFF2, s, n.A2h)) != cudaSuccess) return e;
+    if ((e = conv_tc<16, 32, 0>(n, n.A1h, a2, NN_OFF2, s, n.A2h)) != cudaSuccess) return e;
     return conv_tc<32, 4, 1>(n, n.A2h, n.T3, NN_OFF3, s);
   }
   if ((e = conv<T, 16, 32, 0>(n, n.A1, n.A2, NN_OFF2, s)) != cudaSuccess) return e;
@@ -1189,8 +1192,9 @@ cudaError_t layers_vjp_t(const NnArgs& n, cudaStream_t s) {
 
 template <class T>
 cudaError_t reverse_t(const NnArgs& n0, const AdjArgs& a, cudaStream_t s) {
-  const NnArgs n = capped_wblocks(n0);
-  cudaError_t e = forward_t<T>(n, a.Q, a.lay.plane, s);
+  NnArgs n = capped_wblocks(n0);
+  n.keep = 1;
+  cudaError_t e = n.fwd_ready ? cudaSuccess : forward_t<T>(n, a.Q, a.lay.plane, s);  // else kept
   if (e != cudaSuccess) return e;
   const dim3 pg(cdiv(max_pix(n), 256), n.nimg);
   const bool tc = std::is_same<T, float>::value && n.bf16;
@@ -1210,6 +1214,7 @@ cudaError_t eval_vjp_t(const NnArgs& n0, const double* X, int H, int W, const do
   n.W[0] = W;
   n.pix0 = (long long)H * W;
   n = capped_wblocks(n);
+  n.keep = 1;
   const long long pix = n.pix0;
   nn_load_kernel<T><<<cdiv(4 * pix, 256), 256, 0, s>>>(X, static_cast<T*>(n.X), 4 * pix);
   cudaError_t e = cudaGetLastError();
