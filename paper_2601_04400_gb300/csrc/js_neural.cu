@@ -523,8 +523,15 @@ __global__ void __launch_bounds__(NTHR) nn_wgrad_f32_kernel(NnArgs n, const void
 // ---------------------------------------------------------------------------------------
 constexpr int TC_M = 128;                 // pixels per block
 constexpr int TC_COLS = TC_M + 2;         // with the halo
-// shared bytes of the input row ring: 3 rows x 130 pixels x 32 channels (the widest input), BF16
-constexpr int TC_AREGION = 4 * 3 * TC_COLS * 16;
+// shared bytes of the input row ring: 4 rows x 130 pixels x 32 channels (the widest input), BF16
+constexpr int TC_NSLOT = 4;
+constexpr int TC_AREGION = 4 * TC_NSLOT * TC_COLS * 16;
+
+// 16-byte asynchronous global -> shared copy (zero-filled, nothing read, when !valid)
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(valid ? 16 : 0)
+               : "memory");
+}
 
 __device__ __forceinline__ uint64_t umma_smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
   uint64_t d = (uint64_t)((addr >> 4) & 0x3FFFu);
@@ -558,9 +565,10 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t r[16]) {
 }
 
 // A block owns work items of one 128-pixel-wide column strip and TC_ROWS output rows.  It loads
-// the weights and allocates tensor memory once, then walks its rows keeping the three input rows
-// it needs in a ring of row slots: each output row loads one new input row (8 channels of a pixel
-// per thread, stored as one 16-byte vector), issues the MMAs, waits, and stores the row.
+// the weights and allocates tensor memory once, then walks its rows keeping its input rows in a
+// ring of four row slots: while the MMAs of output row h (input rows h-1, h, h+1) run and its
+// epilogue stores it, the asynchronous 16-byte copies of input row h+2 (8 channels of a pixel
+// each) fill the slot of row h-2.
 constexpr int TC_ROWS = 16;
 
 // MODE 0: a layer's forward (bias, then ReLU for ACT 0, tanh for ACT 1).  MODE 1: a layer's data
@@ -578,7 +586,7 @@ __global__ void __launch_bounds__(128) nn_conv_tc_kernel(NnArgs n, const void* i
   constexpr int GSTRIDE = TC_COLS * 16;      // bytes of one channel group of one row slot
   constexpr int SLOT = KG * GSTRIDE;         // bytes of one input row slot
   constexpr int BTAP = KG * N * 16;          // bytes of one tap of the weights
-  static_assert(3 * SLOT <= TC_AREGION, "row slots");
+  static_assert(TC_NSLOT * SLOT <= TC_AREGION, "row slots");
   extern __shared__ __align__(16) unsigned char smem_raw[];  // 16-byte rows: no swizzle
   unsigned char* sA = smem_raw;
   unsigned char* sB = smem_raw + TC_AREGION;
@@ -629,22 +637,23 @@ __global__ void __launch_bounds__(128) nn_conv_tc_kernel(NnArgs n, const void* i
     __nv_bfloat16* Yh = outh ? static_cast<__nv_bfloat16*>(outh) + (d == 0 ? 0LL : (long long)COUT * n.pix0)
                              : nullptr;
     const float* Ap = (MODE == 1 && ACT == 1) ? chan_img<float>(aprev, COUT, d, n.pix0) : nullptr;
-    // input row r (zeros outside the image) into its ring slot: 16-byte copies of 8 channels
-    // of a pixel from the BF16 pixel-major input (consecutive threads: consecutive 16 bytes)
+    // input row r (zeros outside the image) into its ring slot: asynchronous 16-byte copies of 8
+    // channels of a pixel from the BF16 pixel-major input (consecutive threads: consecutive 16 bytes)
     auto load_row = [&](int r) {
-      unsigned char* slot = sA + ((r + 3) % 3) * SLOT;
+      unsigned char* slot = sA + ((r + TC_NSLOT) % TC_NSLOT) * SLOT;
       for (int k = tid; k < KG * TC_COLS; k += 128) {
         const int col = k / KG, g = k % KG, gx = x0 + col - 1;
         const bool inside = r >= 0 && r < H && gx >= 0 && gx < Wd;
-        const uint4 v = inside ? Xh[((long long)r * Wd + gx) * KG + g] : make_uint4(0u, 0u, 0u, 0u);
-        *reinterpret_cast<uint4*>(slot + g * GSTRIDE + col * 16) = v;
+        cp_async16(slot + g * GSTRIDE + col * 16, inside ? Xh + (((long long)r * Wd + gx) * KG + g) : Xh, inside);
       }
+      cp_async_commit();
     };
     load_row(h0 - 1);
     load_row(h0);
+    load_row(h0 + 1);
     for (int h = h0; h < h1; ++h) {
-      load_row(h + 1);
-      // generic-proxy shared stores must be visible to the tensor core (async proxy)
+      cp_async_wait<0>();  // this thread's copies of rows up to h + 1 have landed
+      // shared stores of the generic proxy must be visible to the tensor core (async proxy)
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncthreads();
@@ -653,7 +662,7 @@ __global__ void __launch_bounds__(128) nn_conv_tc_kernel(NnArgs n, const void* i
         int acc = 0;
         for (int tap = 0; tap < 9; ++tap) {
           const int ky = tap / 3, kx = tap % 3;
-          const uint32_t slot = a0 + ((h + ky - 1 + 3) % 3) * SLOT;
+          const uint32_t slot = a0 + ((h + ky - 1 + TC_NSLOT) % TC_NSLOT) * SLOT;
           for (int kc = 0; kc < KG / 2; ++kc) {
             const uint64_t ad = umma_smem_desc(slot + 2 * kc * GSTRIDE + kx * 16, GSTRIDE, 128);
             const uint64_t bd = umma_smem_desc(b0 + tap * BTAP + 2 * kc * N * 16, N * 16, 128);
@@ -663,6 +672,8 @@ __global__ void __launch_bounds__(128) nn_conv_tc_kernel(NnArgs n, const void* i
         }
         umma_commit(&bar);
       }
+      // row h + 2 into the slot of row h - 2: the MMAs that read it (row h - 1's) have completed
+      if (h + 2 <= h1) load_row(h + 2);
       // every thread waits (bounded); the outcome is made uniform so that the block leaves the
       // loop together on a timeout
       ok = __syncthreads_and(mbar_wait(&bar, phase, kBudget) ? 1 : 0) != 0;
@@ -717,6 +728,7 @@ __global__ void __launch_bounds__(128) nn_conv_tc_kernel(NnArgs n, const void* i
       __syncthreads();
     }
   }
+  cp_async_wait<0>();  // no copy of this block may land after it leaves (a timeout breaks early)
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0)
