@@ -6,6 +6,7 @@ kernel (WENO5, HLLC, viscous fluxes, divergence, stage combination).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload riemann2d|shock_cylinder]
     python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
+    python bench.py --workload mach5_cylinder --to-end   # one whole run to the end time
 
 Prints ONE JSON line (rank 0).  `value` is cell-updates/s with the state resident in HBM;
 `e2e` is the same metric through the C ABI with the state copied from pinned host memory
@@ -515,6 +516,55 @@ def run_batched(args):
         dist.destroy_process_group()
 
 
+def run_to_end(args):
+    """A whole run of a single-grid workload from t = 0 to its end time with the CFL step (the
+    last step before each output time clipped to it), timed with CUDA events around the loop: the
+    wall time of the application, next to the paper's reported wall times (context only).  At the
+    output times it reports the density range and the x position of the leading shock front on
+    the bottom wall (the last cell of the bottom row whose density exceeds twice the undisturbed
+    gas's)."""
+    import torch
+    from paper_2601_04400_gb300 import binding as B
+    B.lib()
+    prob, desc = workload(args.workload)
+    if prob.t_end is None:
+        raise SystemExit("workload %s has no end time" % args.workload)
+    stream = torch.cuda.current_stream()
+    solver = B.Solver.from_problem(prob, stream=stream)
+    U = solver.prim_to_cons(torch.tensor(prob.W0, dtype=torch.float64, device="cuda"))
+    outputs = sorted(set([t for t in (0.3, 1.0) if t < prob.t_end] + [prob.t_end]))
+    rho_far = float(np.min(prob.W0[0]))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t, steps, snaps = 0.0, 0, []
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    e0.record(stream)
+    for t_out in outputs:
+        while t < t_out:
+            dt = solver.max_dt(U, prob.cfl)
+            last = t + dt >= t_out
+            if last:
+                dt = t_out - t
+            solver.step(U, dt, 1)
+            t = t_out if last else t + dt
+            steps += 1
+        r = U[0]
+        bottom = (r[0] > 2.0 * rho_far).nonzero()
+        front = float(prob.x0 + (int(bottom[-1]) + 0.5) * prob.dx) if bottom.numel() else None
+        snaps.append({"t": t_out, "steps": steps, "rho_min": float(r.min()), "rho_max": float(r.max()),
+                      "wall_shock_x": front})
+    e1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    status = solver.status()
+    gpu_s = e0.elapsed_time(e1) * 1e-3
+    cells = prob.nx * prob.ny
+    print(json.dumps({"mode": "run_to_t_end", "workload": desc, "t_end": prob.t_end, "steps": steps,
+                      "cells": cells, "seconds": gpu_s, "wall_seconds": wall,
+                      "cell_updates_per_s": cells * steps / gpu_s, "dtype": "f64", "status_ok": status == 0,
+                      "outputs": snaps}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -526,10 +576,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--neural", action="store_true", help="also time steps with the neural flux")
+    ap.add_argument("--to-end", action="store_true",
+                    help="one whole run of the workload to its end time (CFL steps), timed as an application")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.to_end and args.impl == "ours" and args.workload != "batched":
+        run_to_end(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched":
         run_batched(args)
