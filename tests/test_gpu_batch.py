@@ -155,3 +155,67 @@ def test_batched_reverse_step_matches_oracle_tangent(env):
         lhs = np.dot(to_host(lam).reshape(-1), Jv.reshape(-1))
         rhs = np.dot(to_host(Ub).reshape(-1), v.reshape(-1))
         assert abs(lhs - rhs) <= 1e-12 * np.abs(to_host(lam)).sum() * np.abs(Jv).max()
+
+
+def test_full_batched_configuration(env):
+    """The batched configuration itself: the 256 seeded instances (Mach U[1.5,3], radius U[0.3,0.7],
+    nx 128..512, ny 128..256, seed 0), 500 steps in ONE launch with per-instance device CFL steps
+    (logged).  The three smallest instances, advanced by the oracle with its own CFL steps, agree
+    within the 1e-10 bar and their step sequences to rounding; a sample of others, re-run one at a
+    time with js_max_dt + js_step, reproduce every logged step and the final state bit for bit; one
+    batched reverse step of all 256 instances passes the dot-product test against the oracle's
+    forward mode on the three smallest."""
+    torch, B = env
+    n_steps = 500
+    probs = W.batched_cases(256, seed=0)
+    states = _states(torch, probs)
+    b = B.Batch(probs)
+    work = [U.clone() for U in states]
+    b.set_states(work)
+    log = torch.zeros((n_steps, len(probs)), dtype=torch.float64, device="cuda")
+    b.step(0.5, n_steps, dt_log=log)
+    assert b.status() == 0
+    dts = to_host(log)
+    cells = [p.nx * p.ny for p in probs]
+    order = sorted(range(len(probs)), key=lambda k: (cells[k], k))
+    small = order[:3]
+    for k in small:
+        p = probs[k]
+        Uo = O.prim_to_cons(p, p.W0)
+        seq = []
+        for _ in range(n_steps):
+            dt = O.max_dt(p, Uo, 0.5)
+            seq.append(dt)
+            Uo = O.step(p, Uo, [dt])
+        assert np.abs(np.array(seq) - dts[:, k]).max() <= 1e-12 * dts[:, k].max(), k
+        assert normwise_err(to_host(work[k]), Uo) < TOL, k
+    for k in (order[len(order) // 2], order[-1], 0, 255):
+        p = probs[k]
+        s = B.Solver.from_problem(p)
+        U = states[k].clone()
+        for j in range(n_steps):
+            dt = s.max_dt(U, 0.5)
+            assert dt == dts[j, k], (k, j)
+            s.step(U, dt, 1)
+        assert torch.equal(U, work[k]), k
+        s.close()
+    # one batched reverse step from the initial states (their first logged steps are the
+    # oracle's own CFL steps)
+    rng = np.random.default_rng(13)
+    lams = [torch.tensor(rng.standard_normal(U.shape), device="cuda") for U in states]
+    outs = [torch.empty_like(U) for U in states]
+    pbs = [torch.zeros(20, dtype=torch.float64, device="cuda") for _ in states]
+    b.step_vjp(states, dts[0].tolist(), lams, outs, pbs)
+    assert b.status() == 0
+    for k in small:
+        p = probs[k]
+        U0 = O.prim_to_cons(p, p.W0)
+        dt = O.max_dt(p, U0, 0.5)
+        assert dt == dts[0, k]
+        v = rng.standard_normal(U0.shape) * np.abs(U0).max(axis=(1, 2), keepdims=True) * 1e-3
+        _, Jv = O.step_tangent(p, U0, v, np.zeros(20), [dt])
+        lam = to_host(lams[k])
+        lhs = np.dot(lam.reshape(-1), Jv.reshape(-1))
+        rhs = np.dot(to_host(outs[k]).reshape(-1), v.reshape(-1))
+        assert abs(lhs - rhs) <= 1e-12 * np.abs(lam).sum() * np.abs(Jv).max(), k
+    b.close()
