@@ -72,10 +72,17 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+        # the raw samples go to $JS_CLOCKS_CSV when set (to keep them), else to a temporary file
+        self.path = os.environ.get("JS_CLOCKS_CSV")
+        if not self.path:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+            os.close(fd)
 
     def __enter__(self):
-        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        d = os.path.dirname(self.path)
+        if d:
+            os.makedirs(d, exist_ok=True)
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
