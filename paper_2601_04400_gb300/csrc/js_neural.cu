@@ -777,30 +777,45 @@ __global__ void nn_unload_kernel(const T* __restrict__ G, double* __restrict__ G
 
 // stage output (or RHS) minus the neural flux divergence on fluid cells
 template <class T>
-__global__ void nn_apply_kernel(NnArgs n, StageArgs a, int rhs) {
+__global__ void __launch_bounds__(256) nn_apply_kernel(NnArgs n, StageArgs a, int rhs) {
+  // 32 x 32 cells per block: the tile's y-face fluxes (image 1: line = column i, face = row j)
+  // pass through shared memory, so both images are read along their contiguous axis
+  __shared__ T sy[4][IT][IT + 2];
   const Lay& L = a.lay;
+  const int i0 = blockIdx.x * IT, j0 = blockIdx.y * IT;
   const long long ncell = (long long)L.nx * L.ny;
-  const long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (o >= ncell) return;
-  const int i = (int)(o % L.nx), j = (int)(o / L.nx);
-  if (a.tag && a.tag[o] != 0) return;
+  const bool two = n.nimg > 1;
+  if (two) {
+    const T* Fy = chan_img<T>(n.T3, 4, 1, n.pix0);
+    const long long py = (long long)n.H[1] * n.W[1];
+    for (int e = threadIdx.x; e < 4 * IT * (IT + 1); e += 256) {
+      const int k = e / (IT * (IT + 1)), r = e % (IT * (IT + 1)), il = r / (IT + 1), jl = r % (IT + 1);
+      const int i = i0 + il, j = j0 + jl;
+      sy[k][il][jl] = (i < L.nx && j <= L.ny) ? Fy[k * py + (long long)i * n.W[1] + j] : (T)0;
+    }
+  }
+  __syncthreads();
   const T* Fx = chan_img<T>(n.T3, 4, 0, n.pix0);
   const long long px = (long long)n.H[0] * n.W[0];
-  const T* Fy = chan_img<T>(n.T3, 4, 1, n.pix0);
-  const long long py = (n.nimg > 1) ? (long long)n.H[1] * n.W[1] : 0;
   const double fac = (!rhs && a.use_un) ? a.rk_b : 1.0;
   const int ky_of[4] = {0, 2, 1, 3};  // frame channel of each conserved component, y faces
+  const int il = threadIdx.x % IT;
+  for (int jl = threadIdx.x / IT; jl < IT; jl += 256 / IT) {
+    const int i = i0 + il, j = j0 + jl;
+    if (i >= L.nx || j >= L.ny) continue;
+    const long long o = (long long)j * L.nx + i;
+    if (a.tag && a.tag[o] != 0) continue;
 #pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    const long long ox = (long long)j * n.W[0] + i;
-    double corr = a.cx * (n.scale[c] * ((double)Fx[c * px + ox + 1] - (double)Fx[c * px + ox]));
-    if (n.nimg > 1) {
-      const int k = ky_of[c];
-      const long long oy = (long long)i * n.W[1] + j;
-      corr = fma(a.cy, n.scale[k] * ((double)Fy[k * py + oy + 1] - (double)Fy[k * py + oy]), corr);
+    for (int c = 0; c < 4; ++c) {
+      const long long ox = (long long)j * n.W[0] + i;
+      double corr = a.cx * (n.scale[c] * ((double)Fx[c * px + ox + 1] - (double)Fx[c * px + ox]));
+      if (two) {
+        const int k = ky_of[c];
+        corr = fma(a.cy, n.scale[k] * ((double)sy[k][il][jl + 1] - (double)sy[k][il][jl]), corr);
+      }
+      if (rhs) a.Uout[c * ncell + o] -= corr;
+      else a.Uout[c * L.plane + L.idx(i, j)] -= fac * corr;
     }
-    if (rhs) a.Uout[c * ncell + o] -= corr;
-    else a.Uout[c * L.plane + L.idx(i, j)] -= fac * corr;
   }
 }
 
@@ -1261,9 +1276,9 @@ cudaError_t nn_eval_vjp(const NnArgs& n, const double* X, int H, int W, const do
 }
 
 cudaError_t nn_apply(const NnArgs& n, const StageArgs& a, bool rhs, cudaStream_t s) {
-  const long long ncell = (long long)a.lay.nx * a.lay.ny;
-  if (n.fp32) nn_apply_kernel<float><<<cdiv(ncell, 256), 256, 0, s>>>(n, a, rhs ? 1 : 0);
-  else nn_apply_kernel<double><<<cdiv(ncell, 256), 256, 0, s>>>(n, a, rhs ? 1 : 0);
+  const dim3 grid(cdiv(a.lay.nx, IT), cdiv(a.lay.ny, IT));
+  if (n.fp32) nn_apply_kernel<float><<<grid, 256, 0, s>>>(n, a, rhs ? 1 : 0);
+  else nn_apply_kernel<double><<<grid, 256, 0, s>>>(n, a, rhs ? 1 : 0);
   return cudaGetLastError();
 }
 
