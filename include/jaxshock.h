@@ -142,7 +142,11 @@ int js_step_vjp_taped(js_ctx* ctx, int slot, double dt, const double* lam_np1, d
  * is stage 0 from U_n, stage 1 from its result, stage 2 from that.  U_n is read only for
  * stage > 0 (may be NULL for stage 0).  All arrays device [4][ny][nx]; any may alias.
  * Asynchronous.  This is the entry for callers that act between stages (the halo exchange of
- * a y-decomposed grid, below). */
+ * a y-decomposed grid, below).  stage | JS_STAGE_INTERNALS (stages 0 and 1 of a 2D grid; the
+ * flag is ignored otherwise) also stores the stage's WENO5 internals in the context (the
+ * workspace of js_step_vjp, allocated by the first such call), for a js_step_stage_vjp of the
+ * same stage and U_in that passes the flag too. */
+#define JS_STAGE_INTERNALS 16
 int js_step_stage(js_ctx* ctx, const double* U_n, const double* U_in, double* U_out, double dt, int stage);
 
 /* Reverse of js_step_stage, called for the stages of one step in the order 2, 1, 0 (any other
@@ -151,7 +155,10 @@ int js_step_stage(js_ctx* ctx, const double* U_n, const double* U_in, double* U_
  *   p_bar  += (dU_out/dtheta)^T lam_out                                (accumulated, or NULL)
  * The U_n part a_k lam_out of stages 2 and 1 is kept in the context and added to the lam_in
  * of stage 0 (whose U_in is U_n): with lam_out of stage k-1 = lam_in of stage k, the stage-0
- * lam_in equals js_step_vjp's lam_n.  lam_in may alias lam_out.  Asynchronous. */
+ * lam_in equals js_step_vjp's lam_n.  lam_in may alias lam_out.  stage | JS_STAGE_INTERNALS
+ * uses the internals js_step_stage stored for that stage (stages 0, 1 of a 2D grid; JS_ERR_ARG
+ * when it stored none since the last js_step_vjp) instead of recomputing WENO5: same results.
+ * Asynchronous. */
 int js_step_stage_vjp(js_ctx* ctx, const double* U_in, double dt, int stage, const double* lam_out,
                       double* lam_in, double* p_bar);
 

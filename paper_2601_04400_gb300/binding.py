@@ -16,6 +16,7 @@ from . import build as _build
 JS_OK, JS_ERR_ARG, JS_ERR_CUDA, JS_ERR_NONPHYSICAL, JS_ERR_TIMEOUT, JS_ERR_IB, JS_ERR_NOMEM = 0, -1, -2, -3, -4, -5, -6
 JS_NPARAM = 20
 JS_TAPE_WENO = 1
+JS_STAGE_INTERNALS = 16
 JS_NN_NPARAM = 6388
 JS_NN_F64, JS_NN_F32, JS_NN_BF16 = 0, 1, 2
 
@@ -374,16 +375,20 @@ class Solver:
         js_step_vjp(self.ctx, U_n, dt, lam_np1, lam_n, p_bar)
         return lam_n, p_bar
 
-    def step_stage(self, U_n, U_in, U_out, dt, k):
-        """One SSP-RK3 stage k (0, 1, 2): U_out = a_k U_n + b_k (U_in + dt L(U_in))."""
+    def step_stage(self, U_n, U_in, U_out, dt, k, internals=False):
+        """One SSP-RK3 stage k (0, 1, 2): U_out = a_k U_n + b_k (U_in + dt L(U_in)); internals:
+        also store the stage's WENO5 internals for step_stage_vjp (stages 0, 1)."""
+        flag = JS_STAGE_INTERNALS if internals else 0
         _check(lib().js_step_stage(self.ctx, _ptr(U_n) if k > 0 else None, _ptr(U_in), _ptr(U_out), float(dt),
-                                   int(k)), "js_step_stage")
+                                   int(k) | flag), "js_step_stage")
         return U_out
 
-    def step_stage_vjp(self, U_in, dt, k, lam_out, lam_in, p_bar=None):
-        """Reverse of stage k (called for k = 2, 1, 0 of one step; stage 0 adds the U^n part)."""
-        _check(lib().js_step_stage_vjp(self.ctx, _ptr(U_in), float(dt), int(k), _ptr(lam_out), _ptr(lam_in),
-                                       _ptr(p_bar)), "js_step_stage_vjp")
+    def step_stage_vjp(self, U_in, dt, k, lam_out, lam_in, p_bar=None, internals=False):
+        """Reverse of stage k (called for k = 2, 1, 0 of one step; stage 0 adds the U^n part);
+        internals: use the internals step_stage stored for this stage."""
+        flag = JS_STAGE_INTERNALS if internals else 0
+        _check(lib().js_step_stage_vjp(self.ctx, _ptr(U_in), float(dt), int(k) | flag, _ptr(lam_out),
+                                       _ptr(lam_in), _ptr(p_bar)), "js_step_stage_vjp")
         return lam_in
 
     def rows_pack(self, U, row0, nrows, buf, zero=False):

@@ -89,6 +89,7 @@ struct js_ctx {
   int slab_nyg = 0, slab_lo = 0, slab_own = 0, slab_nown = 0;
   bool slab_xchg[2] = {false, false};
   int svjp_next = 2;  // stage expected by the next js_step_stage_vjp (2, 1, 0, 2, ...)
+  bool stage_kept[2] = {false, false};  // js_step_stage stored stage 0 / 1 internals in wsave_fwd
   // instrumentation
   bool profiling = false;
   std::vector<cudaEvent_t> ev;  // 2 per timed stage launch
@@ -718,9 +719,21 @@ int js_step(js_ctx* c, double* U, double dt, int n_steps) {
   return JS_OK;
 }
 
-int js_step_stage(js_ctx* c, const double* U_n, const double* U_in, double* U_out, double dt, int stage_k) {
+namespace {
+int adj_reserve(js_ctx* c);  // defined with the reverse-pass entry points below
+}  // namespace
+
+int js_step_stage(js_ctx* c, const double* U_n, const double* U_in, double* U_out, double dt, int stage_flags) {
+  const int stage_k = stage_flags & ~JS_STAGE_INTERNALS;
   if (!c || !U_in || !U_out || stage_k < 0 || stage_k > 2 || !(dt > 0.0) || (stage_k > 0 && !U_n))
     return JS_ERR_ARG;
+  // stages 0 and 1 of a 2D grid may store their WENO5 internals for js_step_stage_vjp
+  const bool keep = (stage_flags & JS_STAGE_INTERNALS) && stage_k < 2 && c->g.ny > 1;
+  if (keep) {
+    const int rc = adj_reserve(c);
+    if (rc) return rc;
+    if (!c->wsave_fwd) return JS_ERR_NOMEM;
+  }
   double* X = (stage_k == 0) ? c->N : c->A;
   JS_CUDA(js::launch_pack(U_in, X, c->lay, c->stream));
   ++c->launches;
@@ -743,7 +756,10 @@ int js_step_stage(js_ctx* c, const double* U_n, const double* U_in, double* U_ou
   a.rk_a = ra[stage_k];
   a.rk_b = rb[stage_k];
   a.use_un = (stage_k > 0) ? 1 : 0;
-  if ((rc = stage(c, a, c->p.mu > 0.0, false))) return rc;
+  if (keep) rc = stage_save(c, a, c->p.mu > 0.0, c->wsave_fwd + 56 * (size_t)saved_plane(c) * stage_k);
+  else rc = stage(c, a, c->p.mu > 0.0, false);
+  if (rc) return rc;
+  if (stage_k < 2) c->stage_kept[stage_k] = keep;
   JS_CUDA(js::launch_unpack(c->B, U_out, c->lay, c->stream));
   ++c->launches;
   return JS_OK;
@@ -914,6 +930,7 @@ js::NnArgs nn_use_kept(js_ctx* c, int s, bool reverse) {
 int js_step_vjp(js_ctx* c, const double* U_n, double dt, const double* lam_np1, double* lam_n, double* p_bar) {
   if (!c || !U_n || !lam_np1 || !lam_n || !(dt > 0.0)) return JS_ERR_ARG;
   c->svjp_next = 2;  // the stage-wise reverse sequence (js_step_stage_vjp) restarts
+  c->stage_kept[0] = c->stage_kept[1] = false;  // wsave_fwd is reused here
   int rc = adj_reserve(c);
   if (rc) return rc;
   if ((rc = upload_inflow(c))) return rc;
@@ -971,10 +988,13 @@ int js_step_vjp(js_ctx* c, const double* U_n, double dt, const double* lam_np1, 
   return JS_OK;
 }
 
-int js_step_stage_vjp(js_ctx* c, const double* U_in, double dt, int stage_k, const double* lam_out, double* lam_in,
-                      double* p_bar) {
+int js_step_stage_vjp(js_ctx* c, const double* U_in, double dt, int stage_flags, const double* lam_out,
+                      double* lam_in, double* p_bar) {
+  const int stage_k = stage_flags & ~JS_STAGE_INTERNALS;
   if (!c || !U_in || !lam_out || !lam_in || stage_k < 0 || stage_k > 2 || !(dt > 0.0)) return JS_ERR_ARG;
   if (stage_k != 2 && stage_k != c->svjp_next) return JS_ERR_ARG;
+  const bool kept = (stage_flags & JS_STAGE_INTERNALS) && stage_k < 2 && c->g.ny > 1;
+  if (kept && !c->stage_kept[stage_k]) return JS_ERR_ARG;
   int rc = adj_reserve(c);
   if (rc) return rc;
   if ((rc = upload_inflow(c))) return rc;
@@ -986,7 +1006,8 @@ int js_step_stage_vjp(js_ctx* c, const double* U_in, double dt, int stage_k, con
   if (stage_k == 2) JS_CUDA(cudaMemsetAsync(c->Uacc, 0, sizeof(double) * 4 * (size_t)c->lay.plane, c->stream));
   const double ra[3] = {0.0, 0.75, 1.0 / 3.0};
   const double rb[3] = {1.0, 0.25, 2.0 / 3.0};
-  if ((rc = adj_stage(c, c->N, c->P0, c->P1, ra[stage_k], rb[stage_k], dt, false, p_bar))) return rc;
+  double* saved = kept ? c->wsave_fwd + 56 * (size_t)saved_plane(c) * stage_k : nullptr;
+  if ((rc = adj_stage(c, c->N, c->P0, c->P1, ra[stage_k], rb[stage_k], dt, false, p_bar, saved))) return rc;
   JS_CUDA(js::launch_adj_unpack(c->P1, stage_k == 0 ? c->Uacc : nullptr, lam_in, c->lay, c->stream));
   ++c->launches;
   c->svjp_next = (stage_k == 0) ? 2 : stage_k - 1;

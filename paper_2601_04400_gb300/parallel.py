@@ -40,6 +40,15 @@ def rank_loads(cells, world):
 # ---------------------------------------------------------------------------------------
 # y-slab decomposition of one grid
 # ---------------------------------------------------------------------------------------
+def _takes_internals(slab):
+    """Whether a slab solver can store stage internals (binding.Solver on a 2D grid)."""
+    import inspect
+    try:
+        return "internals" in inspect.signature(slab.step_stage).parameters and slab.ny > 1
+    except (TypeError, ValueError, AttributeError):
+        return False
+
+
 class SlabPlan:
     """Rows of an ny-row grid split over `world` slabs (sizes within one row of each other,
     lower ranks first), each slab holding `overlap` rows of each neighbour; with periodic y
@@ -267,6 +276,12 @@ class SlabGroup:
             self.exchange(U)
         return U
 
+    def _stage(self, r, U_n, U_in, U_out, dt, k, internals):
+        if internals:
+            self.slabs[r].step_stage(U_n, U_in, U_out, dt, k, internals=True)
+        else:
+            self.slabs[r].step_stage(U_n, U_in, U_out, dt, k)
+
     # -- reverse ----------------------------------------------------------------------
     def step_vjp(self, U_n, dt, lam, p_bar=None):
         """Reverse of one step from U_n: returns ({rank: lam_n}, p_bar) where lam holds the
@@ -276,11 +291,13 @@ class SlabGroup:
         from .binding import JS_NPARAM
         X1 = {r: self._buf(("x1", r), u) for r, u in U_n.items()}
         X2 = {r: self._buf(("x2", r), u) for r, u in U_n.items()}
+        # the recomputed stages 0 and 1 store their WENO5 internals for their reverse
+        keep = {r: _takes_internals(s) for r, s in self.slabs.items()}
         for r, u in U_n.items():
-            self.slabs[r].step_stage(u, u, X1[r], dt, 0)
+            self._stage(r, u, u, X1[r], dt, 0, keep[r])
         self.exchange(X1)
         for r, u in U_n.items():
-            self.slabs[r].step_stage(u, X1[r], X2[r], dt, 1)
+            self._stage(r, u, X1[r], X2[r], dt, 1, keep[r])
         self.exchange(X2)
         any_u = next(iter(U_n.values()))
         pb = torch.zeros(JS_NPARAM, dtype=torch.float64, device=any_u.device)
@@ -295,7 +312,10 @@ class SlabGroup:
         Xs = (U_n, X1, X2)
         for k in (2, 1, 0):
             for r in L:
-                self.slabs[r].step_stage_vjp(Xs[k][r], dt, k, L[r], L[r], pb)
+                if keep[r] and k < 2:
+                    self.slabs[r].step_stage_vjp(Xs[k][r], dt, k, L[r], L[r], pb, internals=True)
+                else:
+                    self.slabs[r].step_stage_vjp(Xs[k][r], dt, k, L[r], L[r], pb)
             self.exchange(L, transpose=True)
         pb = self.transport.sum_(pb)
         if p_bar is not None:

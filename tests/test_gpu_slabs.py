@@ -80,6 +80,22 @@ def test_stage_entry_points_equal_step_and_step_vjp(env, case):
     s.step_stage_vjp(X2s, dt, 2, L, L, p)
     with pytest.raises(B.JsError):
         s.step_stage_vjp(Ud, dt, 0, L, L, p)
+    # stages 0 and 1 storing their WENO5 internals, their reverse using them: the same result
+    if prob.ny > 1:
+        s.step_vjp(Ud, dt, lam)  # reuses the internals' workspace: none are stored now
+        L2 = lam.clone()
+        s.step_stage_vjp(X2s, dt, 2, L2, L2, None)
+        with pytest.raises(B.JsError):
+            s.step_stage_vjp(X1, dt, 1, L2, L2, None, internals=True)
+        X1k = s.step_stage(None, Ud, torch.empty_like(Ud), dt, 0, internals=True)
+        X2k = s.step_stage(Ud, X1k, torch.empty_like(Ud), dt, 1, internals=True)
+        assert torch.equal(X1k, X1) and torch.equal(X2k, X2s)
+        p2 = torch.zeros_like(p_ref)
+        L2 = lam.clone()
+        for k, X in ((2, X2k), (1, X1k), (0, Ud)):
+            s.step_stage_vjp(X, dt, k, L2, L2, p2, internals=k < 2)
+        assert float((L2 - l_ref).abs().max()) <= 1e-13 * float(l_ref.abs().max())
+        assert float((p2 - p_ref).abs().max()) <= 1e-13 * float(p_ref.abs().max())
     assert s.status() == 0
 
 
