@@ -7,6 +7,7 @@ kernel (WENO5, HLLC, viscous fluxes, divergence, stage combination).
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload riemann2d|shock_cylinder]
     python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
     python bench.py --workload mach5_cylinder --to-end   # one whole run to the end time
+    python bench.py --slabs 2,4 --steps 20               # the y-slab decomposition on one GPU
 
 Prints ONE JSON line (rank 0).  `value` is cell-updates/s with the state resident in HBM;
 `e2e` is the same metric through the C ABI with the state copied from pinned host memory
@@ -572,6 +573,48 @@ def run_to_end(args):
                       "outputs": snaps}), flush=True)
 
 
+def run_slabs(args):
+    """The single-grid workload decomposed into K y slabs held by this process (one GPU, the
+    slabs' launches run one after another, so this times the decomposition's own cost: overlap
+    rows, per-stage packing and exchange, not a multi-GPU step) next to the undecomposed step:
+    forward step and reverse step (js_step_vjp against SlabGroup.step_vjp), ms per step."""
+    import torch
+    from paper_2601_04400_gb300 import binding as B
+    from paper_2601_04400_gb300 import parallel
+    B.lib()
+    prob, desc = workload(args.workload)
+    s = B.Solver.from_problem(prob)
+    U0 = s.prim_to_cons(torch.tensor(prob.W0, dtype=torch.float64, device="cuda"))
+    dt = 0.5 * s.max_dt(U0, prob.cfl)
+    lam = torch.randn_like(U0)
+
+    def timed(fn, n):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(n):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / n
+
+    U = U0.clone()
+    out = {"mode": "slabs", "workload": desc, "dtype": "f64",
+           "whole": {"ms_step": timed(lambda: s.step(U, dt, 1), args.steps),
+                     "ms_step_vjp": timed(lambda: s.step_vjp(U0, dt, lam), max(1, args.steps // 4))}}
+    periodic = prob.bc[2] == 2
+    for k in sorted(set(int(v) for v in args.slabs.split(","))):
+        plan = parallel.SlabPlan(prob.ny, k, args.overlap, periodic=periodic)
+        G = parallel.SlabGroup.build(prob, plan, range(k))
+        X, XU, XL = G.scatter(U0), G.scatter(U0), G.scatter(lam)
+        out["slabs_%d" % k] = {"ms_step": timed(lambda: G.step(X, dt, 1), args.steps),
+                               "ms_step_vjp": timed(lambda: G.step_vjp(XU, dt, XL), max(1, args.steps // 4)),
+                               "overlap": plan.overlap}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -585,10 +628,15 @@ def main():
     ap.add_argument("--neural", action="store_true", help="also time steps with the neural flux")
     ap.add_argument("--to-end", action="store_true",
                     help="one whole run of the workload to its end time (CFL steps), timed as an application")
+    ap.add_argument("--slabs", default=None,
+                    help="comma-separated slab counts: time the y-slab decomposition held by this process")
+    ap.add_argument("--overlap", type=int, default=3, help="overlap rows of the slabs (--slabs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.to_end and args.impl == "ours" and args.workload != "batched":
+    if args.slabs and args.impl == "ours" and args.workload != "batched":
+        run_slabs(args)
+    elif args.to_end and args.impl == "ours" and args.workload != "batched":
         run_to_end(args)
     elif args.impl == "reference":
         run_reference(args)
