@@ -215,3 +215,28 @@ def test_two_processes_gloo_exchange_equal_whole_grid(env):
     assert np.array_equal(out, to_host(Ud))
     lr = to_host(l_ref)
     assert np.abs(lo - lr).max() <= 1e-12 * np.abs(lr).max()
+
+
+def test_full_size_cylinder_in_four_slabs(env):
+    """The 2048 x 1024 viscous shock-cylinder configuration (inflow, outflow, reflective walls, the
+    immersed cylinder centred on the middle slab boundary) in 4 slabs of 256 rows: 10 steps equal
+    to the whole grid bit for bit, and one reverse step equal to js_step_vjp to 1e-12."""
+    torch, B = env
+    prob = W.shock_cylinder()
+    s = B.Solver.from_problem(prob)
+    Ud = s.prim_to_cons(torch.tensor(prob.W0, device="cuda"))
+    G = _group(B, prob, 4, 14)
+    X = G.scatter(Ud)
+    for _ in range(10):
+        dt = s.max_dt(Ud, 0.5)
+        assert G.max_dt(X, 0.5) == dt
+        s.step(Ud, dt, 1)
+        G.step(X, dt, 1)
+    assert torch.equal(G.gather(X), Ud)
+    lam = torch.randn_like(Ud)
+    dt = 0.8 * s.max_dt(Ud, 0.5)
+    l_ref, p_ref = s.step_vjp(Ud, dt, lam)
+    L, p = G.step_vjp(G.scatter(Ud), dt, G.scatter(lam))
+    assert float((G.gather(L) - l_ref).abs().max()) <= 1e-12 * float(l_ref.abs().max())
+    assert float((p - p_ref).abs().max()) <= 1e-12 * float(p_ref.abs().max())
+    assert s.status() == 0 and all(sl.status() == 0 for sl in G.slabs.values())
