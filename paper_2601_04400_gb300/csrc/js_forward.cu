@@ -84,48 +84,99 @@ __global__ void prim_to_cons_kernel(const double* W, double* U, long long n, dou
 }
 
 // =======================================================================================
-// CFL reduction: rate = (|u| + a)/dx [+ (|v| + a)/dy] and rho over fluid cells.
+// CFL reduction: rate = (|u| + a)/dx [+ (|v| + a)/dy] and rho over fluid cells, the rate in
 // IEEE-rounded intrinsics in the oracle's operation order, so equal states give equal dt.
+// Two passes keep that result while taking the IEEE rate of few cells: pass 1 takes every
+// fluid cell's rate with the fast reciprocal and reciprocal square root (relative error a few
+// ulp plus the pressure's cancellation, about (E/p) ulp), the exact minimum density, the
+// maximum of these approximate rates and each block's maximum; pass 2 takes the IEEE rate only
+// in blocks, and of cells, whose approximate rate reaches (1 - CFL_MARGIN) of that maximum.
+// While the approximation is within CFL_MARGIN/2 of the IEEE rate (E/p below about 1e10) the
+// cell of the largest IEEE rate is among them, so the maximum is the one-pass maximum.
 // =======================================================================================
-__global__ void cfl_kernel(const double* __restrict__ U, long long n, int nx, int two_d,
-                           const unsigned char* __restrict__ tag, double gamma, double dx, double dy,
-                           unsigned long long* __restrict__ red) {
+constexpr double CFL_MARGIN = 4e-6;
+
+__device__ __forceinline__ double cfl_rate_fast(double r, double mx, double my, double E, double gamma, double dx,
+                                                double dy, double idx, double idy, bool two_d) {
+  if (!(r > 1e-290)) return cfl_rate(r, mx, my, E, gamma, dx, dy, two_d);  // tiny, zero or NaN density
+  const double rr = recip(r);
+  const double u = mx * rr, v = my * rr;
+  const double ke = (0.5 * r) * fma(u, u, v * v);
+  const double p = (gamma - 1.0) * (E - ke);
+  const double c2 = (gamma * p) * rr;
+  const double a = (c2 > 1e-290) ? c2 * rsqrt_nr(c2) : sqrt(c2);
+  double s = (fabs(u) + a) * idx;
+  if (two_d) s = fma(fabs(v) + a, idy, s);
+  return s;
+}
+
+// block maximum (thread 0 holds it) and, when rmin != nullptr, block minimum
+__device__ __forceinline__ void cfl_block_reduce(double& rate, double* rmin) {
+  for (int o = 16; o > 0; o >>= 1) {
+    rate = fmax(rate, __shfl_xor_sync(0xffffffffu, rate, o));
+    if (rmin) *rmin = fmin(*rmin, __shfl_xor_sync(0xffffffffu, *rmin, o));
+  }
+  __shared__ double sr[32], sm[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    sr[wid] = rate;
+    if (rmin) sm[wid] = *rmin;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+    rate = (lane < nw) ? sr[lane] : 0.0;
+    if (rmin) *rmin = (lane < nw) ? sm[lane] : __longlong_as_double(0x7ff0000000000000LL);
+    for (int o = 16; o > 0; o >>= 1) {
+      rate = fmax(rate, __shfl_xor_sync(0xffffffffu, rate, o));
+      if (rmin) *rmin = fmin(*rmin, __shfl_xor_sync(0xffffffffu, *rmin, o));
+    }
+  }
+}
+
+__global__ void cfl_pass1_kernel(const double* __restrict__ U, long long n, int two_d,
+                                 const unsigned char* __restrict__ tag, double gamma, double dx, double dy,
+                                 double idx, double idy, unsigned long long* __restrict__ red,
+                                 double* __restrict__ bmax) {
   double rate = 0.0, rmin = __longlong_as_double(0x7ff0000000000000LL);
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
        t += (long long)gridDim.x * blockDim.x) {
     if (tag && tag[t] != 0) continue;
     const double r = U[t];
-    rate = fmax(rate, cfl_rate(r, U[n + t], U[2 * n + t], U[3 * n + t], gamma, dx, dy, two_d != 0));
+    rate = fmax(rate, cfl_rate_fast(r, U[n + t], U[2 * n + t], U[3 * n + t], gamma, dx, dy, idx, idy, two_d != 0));
     rmin = fmin(rmin, r);
-    (void)nx;
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    rate = fmax(rate, __shfl_xor_sync(0xffffffffu, rate, o));
-    rmin = fmin(rmin, __shfl_xor_sync(0xffffffffu, rmin, o));
-  }
-  __shared__ double sr[32], sm[32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) { sr[wid] = rate; sm[wid] = rmin; }
-  __syncthreads();
-  if (wid == 0) {
-    const int nw = blockDim.x >> 5;
-    rate = (lane < nw) ? sr[lane] : 0.0;
-    rmin = (lane < nw) ? sm[lane] : __longlong_as_double(0x7ff0000000000000LL);
-    for (int o = 16; o > 0; o >>= 1) {
-      rate = fmax(rate, __shfl_xor_sync(0xffffffffu, rate, o));
-      rmin = fmin(rmin, __shfl_xor_sync(0xffffffffu, rmin, o));
-    }
-    if (lane == 0) {
-      // non-negative doubles order like their bit patterns
-      atomicMax(&red[0], (unsigned long long)__double_as_longlong(rate));
-      atomicMin(&red[1], (unsigned long long)__double_as_longlong(rmin));
-    }
+  cfl_block_reduce(rate, &rmin);
+  if (threadIdx.x == 0) {
+    // non-negative doubles order like their bit patterns
+    bmax[blockIdx.x] = rate;
+    atomicMax(&red[2], (unsigned long long)__double_as_longlong(rate));
+    atomicMin(&red[1], (unsigned long long)__double_as_longlong(rmin));
   }
 }
 
+__global__ void cfl_pass2_kernel(const double* __restrict__ U, long long n, int two_d,
+                                 const unsigned char* __restrict__ tag, double gamma, double dx, double dy,
+                                 double idx, double idy, unsigned long long* __restrict__ red,
+                                 const double* __restrict__ bmax) {
+  const double thr = __longlong_as_double((long long)red[2]) * (1.0 - CFL_MARGIN);
+  if (!(bmax[blockIdx.x] >= thr)) return;  // the same for the whole block
+  double rate = 0.0;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    if (tag && tag[t] != 0) continue;
+    const double r = U[t], mx = U[n + t], my = U[2 * n + t], E = U[3 * n + t];
+    if (cfl_rate_fast(r, mx, my, E, gamma, dx, dy, idx, idy, two_d != 0) >= thr)
+      rate = fmax(rate, cfl_rate(r, mx, my, E, gamma, dx, dy, two_d != 0));
+  }
+  cfl_block_reduce(rate, nullptr);
+  if (threadIdx.x == 0) atomicMax(&red[0], (unsigned long long)__double_as_longlong(rate));
+}
+
 __global__ void cfl_init_kernel(unsigned long long* red) {
-  red[0] = 0ULL;
-  red[1] = 0x7ff0000000000000ULL;
+  red[0] = 0ULL;                    // IEEE rate maximum
+  red[1] = 0x7ff0000000000000ULL;   // density minimum
+  red[2] = 0ULL;                    // approximate rate maximum
 }
 
 template <int TX, int TY, int LX, int LY, bool VISC, bool RHS>
@@ -361,13 +412,16 @@ cudaError_t launch_prim_to_cons(const double* W, double* U, long long n, double 
 }
 
 cudaError_t launch_cfl(const double* U, const Lay& lay, const unsigned char* tag, double gamma, double dx,
-                       double dy, unsigned long long* red, cudaStream_t s) {
+                       double dy, unsigned long long* red, double* bmax, cudaStream_t s) {
   cfl_init_kernel<<<1, 1, 0, s>>>(red);
   const long long n = (long long)lay.nx * lay.ny;
   const int bs = 256;
   long long blocks = (n + bs - 1) / bs;
-  if (blocks > 152 * 8) blocks = 152 * 8;
-  cfl_kernel<<<(unsigned)blocks, bs, 0, s>>>(U, n, lay.nx, lay.ny > 1 ? 1 : 0, tag, gamma, dx, dy, red);
+  if (blocks > CFL_MAX_BLOCKS) blocks = CFL_MAX_BLOCKS;
+  const int two_d = lay.ny > 1 ? 1 : 0;
+  // both passes on the same grid: a block of pass 2 visits the cells its pass-1 maximum covers
+  cfl_pass1_kernel<<<(unsigned)blocks, bs, 0, s>>>(U, n, two_d, tag, gamma, dx, dy, 1.0 / dx, 1.0 / dy, red, bmax);
+  cfl_pass2_kernel<<<(unsigned)blocks, bs, 0, s>>>(U, n, two_d, tag, gamma, dx, dy, 1.0 / dx, 1.0 / dy, red, bmax);
   return cudaGetLastError();
 }
 

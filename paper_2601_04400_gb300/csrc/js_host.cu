@@ -39,6 +39,7 @@ struct js_ctx {
   double* ib_nrm = nullptr;
   int* err = nullptr;
   unsigned long long* red = nullptr;
+  double* cfl_bmax = nullptr;  // per-block scratch of the CFL reduction
   BcArgs bc;
   // transposed IB tables
   int n_src = 0;
@@ -464,7 +465,7 @@ void js_destroy(js_ctx* c) {
   cudaFree(c->N); cudaFree(c->A); cudaFree(c->B); cudaFree(c->acc); cudaFree(c->acc2);
   cudaFree(c->tag);
   cudaFree(c->ib_dst); cudaFree(c->ib_src); cudaFree(c->ib_w); cudaFree(c->ib_nrm);
-  cudaFree(c->err); cudaFree(c->red);
+  cudaFree(c->err); cudaFree(c->red); cudaFree(c->cfl_bmax);
   cudaFree(c->ibt_cell); cudaFree(c->ibt_ptr); cudaFree(c->ibt_ghost); cudaFree(c->ibt_w);
   cudaFree(c->Q); cudaFree(c->Qb); cudaFree(c->lam); cudaFree(c->P0); cudaFree(c->P1); cudaFree(c->Uacc);
   cudaFree(c->wsave); cudaFree(c->wsave_fwd); cudaFree(c->fadj);
@@ -520,7 +521,8 @@ int create_ctx(const js_grid* grid, const js_params* params, const js_boundary* 
       cudaMalloc(&c->B, bytes) != cudaSuccess || cudaMalloc(&c->err, sizeof(int)) != cudaSuccess ||
       cudaMalloc(&c->acc, sizeof(double) * 4 * (size_t)grid->nx * grid->ny) != cudaSuccess ||
       cudaMalloc(&c->acc2, sizeof(double) * 4 * (size_t)grid->nx * grid->ny) != cudaSuccess ||
-      cudaMalloc(&c->red, 4 * sizeof(unsigned long long)) != cudaSuccess) {
+      cudaMalloc(&c->red, 4 * sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMalloc(&c->cfl_bmax, sizeof(double) * js::CFL_MAX_BLOCKS) != cudaSuccess) {
     js_destroy(c);
     return JS_ERR_NOMEM;
   }
@@ -666,8 +668,8 @@ int js_rhs(js_ctx* c, const double* U, double* dUdt) {
 
 int js_max_dt(js_ctx* c, const double* U, double cfl, double* dt_out) {
   if (!c || !U || !dt_out || !(cfl > 0.0)) return JS_ERR_ARG;
-  JS_CUDA(js::launch_cfl(U, c->lay, c->tag, c->p.gamma, c->g.dx, c->g.dy, c->red, c->stream));
-  c->launches += 2;
+  JS_CUDA(js::launch_cfl(U, c->lay, c->tag, c->p.gamma, c->g.dx, c->g.dy, c->red, c->cfl_bmax, c->stream));
+  c->launches += 3;
   unsigned long long h[2];
   JS_CUDA(cudaMemcpyAsync(h, c->red, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
   JS_CUDA(cudaStreamSynchronize(c->stream));

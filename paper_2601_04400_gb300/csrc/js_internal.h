@@ -180,7 +180,10 @@ cudaError_t launch_prim_to_cons(const double* W, double* U, long long n, double 
 cudaError_t launch_rows_pack(double* U, int nx, int ny, int row0, int nrows, double* buf, int zero, cudaStream_t s);
 cudaError_t launch_rows_unpack(double* U, int nx, int ny, int row0, int nrows, const double* buf, int add,
                                cudaStream_t s);
+// CFL reduction of U (user layout): red[0] = bits of the largest rate, red[1] = bits of the
+// smallest density over fluid cells (red: 3 words; bmax: CFL_MAX_BLOCKS doubles of scratch)
+constexpr int CFL_MAX_BLOCKS = 152 * 8;
 cudaError_t launch_cfl(const double* U, const Lay& lay, const unsigned char* tag, double gamma, double dx,
-                       double dy, unsigned long long* red, cudaStream_t s);
+                       double dy, unsigned long long* red, double* bmax, cudaStream_t s);
 
 }  // namespace js
