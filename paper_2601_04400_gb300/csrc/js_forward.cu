@@ -90,7 +90,8 @@ __global__ void prim_to_cons_kernel(const double* W, double* U, long long n, dou
 // fluid cell's rate with the fast reciprocal and reciprocal square root (relative error a few
 // ulp plus the pressure's cancellation, about (E/p) ulp), the exact minimum density, the
 // maximum of these approximate rates and each block's maximum; pass 2 takes the IEEE rate only
-// in blocks, and of cells, whose approximate rate reaches (1 - CFL_MARGIN) of that maximum.
+// in blocks, and of cells, whose approximate rate reaches (1 - CFL_MARGIN) of that maximum
+// (once per run of cells with identical states along a row).
 // While the approximation is within CFL_MARGIN/2 of the IEEE rate (E/p below about 1e10) the
 // cell of the largest IEEE rate is among them, so the maximum is the one-pass maximum.
 // =======================================================================================
@@ -155,19 +156,51 @@ __global__ void cfl_pass1_kernel(const double* __restrict__ U, long long n, int 
   }
 }
 
-__global__ void cfl_pass2_kernel(const double* __restrict__ U, long long n, int two_d,
+// bitwise equality of two states (identical states have identical IEEE rates)
+__device__ __forceinline__ bool same_bits(double a, double b) {
+  return __double_as_longlong(a) == __double_as_longlong(b);
+}
+
+// A candidate cell whose left neighbour in its row is a fluid cell with the identical state
+// leaves the IEEE rate to that neighbour (also a candidate, in a block that passes the test):
+// of a uniform run of cells, only the first takes it.  The threads of a warp hold consecutive
+// cells, so the neighbour's state comes from the next lower lane.
+__global__ void cfl_pass2_kernel(const double* __restrict__ U, long long n, int nx, int two_d,
                                  const unsigned char* __restrict__ tag, double gamma, double dx, double dy,
                                  double idx, double idy, unsigned long long* __restrict__ red,
                                  const double* __restrict__ bmax) {
   const double thr = __longlong_as_double((long long)red[2]) * (1.0 - CFL_MARGIN);
   if (!(bmax[blockIdx.x] >= thr)) return;  // the same for the whole block
+  const int lane = threadIdx.x & 31;
+  const long long stride = (long long)gridDim.x * blockDim.x;
   double rate = 0.0;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
-       t += (long long)gridDim.x * blockDim.x) {
-    if (tag && tag[t] != 0) continue;
-    const double r = U[t], mx = U[n + t], my = U[2 * n + t], E = U[3 * n + t];
-    if (cfl_rate_fast(r, mx, my, E, gamma, dx, dy, idx, idy, two_d != 0) >= thr)
-      rate = fmax(rate, cfl_rate(r, mx, my, E, gamma, dx, dy, two_d != 0));
+  for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x - lane); base < n; base += stride) {
+    const long long t = base + lane;
+    const bool in = t < n;
+    bool fl = false;
+    double r = 0.0, mx = 0.0, my = 0.0, E = 0.0;
+    if (in) {
+      fl = !(tag && tag[t] != 0);
+      r = U[t];
+      mx = U[n + t];
+      my = U[2 * n + t];
+      E = U[3 * n + t];
+    }
+    double rl = __shfl_up_sync(0xffffffffu, r, 1), mxl = __shfl_up_sync(0xffffffffu, mx, 1);
+    double myl = __shfl_up_sync(0xffffffffu, my, 1), El = __shfl_up_sync(0xffffffffu, E, 1);
+    bool fll = __shfl_up_sync(0xffffffffu, fl ? 1 : 0, 1) != 0;
+    if (lane == 0 && in && t > 0) {
+      fll = !(tag && tag[t - 1] != 0);
+      rl = U[t - 1];
+      mxl = U[n + t - 1];
+      myl = U[2 * n + t - 1];
+      El = U[3 * n + t - 1];
+    }
+    if (in && fl && cfl_rate_fast(r, mx, my, E, gamma, dx, dy, idx, idy, two_d != 0) >= thr) {
+      const bool same = (t % nx != 0) && fll && same_bits(r, rl) && same_bits(mx, mxl) && same_bits(my, myl) &&
+                        same_bits(E, El);
+      if (!same) rate = fmax(rate, cfl_rate(r, mx, my, E, gamma, dx, dy, two_d != 0));
+    }
   }
   cfl_block_reduce(rate, nullptr);
   if (threadIdx.x == 0) atomicMax(&red[0], (unsigned long long)__double_as_longlong(rate));
@@ -421,7 +454,8 @@ cudaError_t launch_cfl(const double* U, const Lay& lay, const unsigned char* tag
   const int two_d = lay.ny > 1 ? 1 : 0;
   // both passes on the same grid: a block of pass 2 visits the cells its pass-1 maximum covers
   cfl_pass1_kernel<<<(unsigned)blocks, bs, 0, s>>>(U, n, two_d, tag, gamma, dx, dy, 1.0 / dx, 1.0 / dy, red, bmax);
-  cfl_pass2_kernel<<<(unsigned)blocks, bs, 0, s>>>(U, n, two_d, tag, gamma, dx, dy, 1.0 / dx, 1.0 / dy, red, bmax);
+  cfl_pass2_kernel<<<(unsigned)blocks, bs, 0, s>>>(U, n, lay.nx, two_d, tag, gamma, dx, dy, 1.0 / dx, 1.0 / dy, red,
+                                                    bmax);
   return cudaGetLastError();
 }
 
