@@ -53,6 +53,8 @@ def lib():
         L.or_nn_set.argtypes = [_D, _D, _D]
         L.or_nn_eval.argtypes = [_D, C.c_int, C.c_int, _D]
         L.or_nn_nparam.restype = C.c_int
+        L.or_fallback_faces.restype = C.c_longlong
+        L.or_ib_fill.argtypes = [C.POINTER(OrGrid), _D, _D, _D, _D]
         L.or_set_threads.argtypes = [C.c_int]
         L.or_get_threads.restype = C.c_int
         _lib = L
@@ -216,6 +218,23 @@ def ib_tables(prob):
                           _p(w), _p(nrm)), "ib_tables")
     return dict(tag=tag.reshape(prob.ny, prob.nx), gcell=gcell[:k], icell=icell[:4 * k].reshape(k, 4),
                 w=w[:4 * k].reshape(k, 4), nrm=nrm[:2 * k].reshape(k, 2))
+
+
+def fallback_faces():
+    """Faces at which the positivity fallback (first-order cell states) was taken since the
+    last call, over every RHS evaluation in between; resets the count."""
+    return int(lib().or_fallback_faces())
+
+
+def ib_fill(prob, U, theta=None):
+    """The immersed-boundary ghost fill alone: U with every ghost cell set to its mirrored
+    image-point state (other cells copied)."""
+    g = grid_of(prob)
+    th = _f64(theta_of(prob) if theta is None else theta)
+    U = _f64(U)
+    out = np.empty_like(U)
+    _check(lib().or_ib_fill(C.byref(g), _p(th), _p(_sdf(prob)), _p(U), _p(out)), "ib_fill")
+    return out
 
 
 def weno5(q, linear=False):

@@ -229,6 +229,10 @@ enum { BC_TRANSMISSIVE = 0, BC_REFLECTIVE = 1, BC_PERIODIC = 2, BC_INFLOW = 3 };
 enum { OK = 0, ERR_ARG = -1, ERR_NONPHYSICAL = -3, ERR_IB = -5 };
 const int NG = 3;  // halo depth
 
+// faces at which face_flux took the positivity fallback (reading of "positivity-preserving
+// HLLC", Sec. 2): counted for the tests, reset by or_fallback_faces
+long long g_fallback_faces = 0;
+
 }  // namespace
 
 extern "C" {
@@ -622,6 +626,8 @@ struct Solver {
     if (!(qL[0] > 0.0) || !(qL[3] > 0.0) || !(qR[0] > 0.0) || !(qR[3] > 0.0)) {
       // positivity fallback: first-order (cell) states at this face
       for (int c = 0; c < 4; ++c) { qL[c] = Q[c][il]; qR[c] = Q[c][ir]; }
+#pragma omp atomic
+      ++g_fallback_faces;
     }
     const int n = (dir == 0) ? 1 : 2, t = (dir == 0) ? 2 : 1;  // normal / tangential velocity
     T F[4];
@@ -1073,6 +1079,34 @@ int or_count_rhs(const or_grid* g, const double* theta, const double* sdf, const
   rc = S.rhs(Lv);
   out[0] = g_tally.add; out[1] = g_tally.mul; out[2] = g_tally.div; out[3] = g_tally.sqrt; out[4] = g_tally.cmp;
   return rc;
+}
+
+// Number of faces at which the positivity fallback was taken since the last call (every RHS
+// evaluation of every entry point counts); resets the count.
+long long or_fallback_faces(void) {
+  const long long n = g_fallback_faces;
+  g_fallback_faces = 0;
+  return n;
+}
+
+// The immersed-boundary ghost fill alone (Sec. 2, Fig. 1(c)): U (unpadded [4][ny][nx]) with
+// every ghost cell replaced by the slip-wall (or no-slip) mirror of the interpolated image-point
+// state, written to out; other cells are copied.
+int or_ib_fill(const or_grid* g, const double* theta, const double* sdf, const double* U, double* out) {
+  if (!grid_ok(g)) return ERR_ARG;
+  IbTable ib;
+  int rc = build_ib(*g, sdf, ib);
+  if (rc) return rc;
+  Solver<double> S(*g, make_par<double>(theta), ib, false);
+  std::vector<double> Uc[4];
+  to_vec<double>(U, g->nx, g->ny, Uc);
+  S.load(Uc);
+  S.ib_fill();
+  const size_t n = (size_t)g->nx * g->ny;
+  for (int c = 0; c < 4; ++c)
+    for (int j = 0; j < g->ny; ++j)
+      for (int i = 0; i < g->nx; ++i) out[c * n + (size_t)j * g->nx + i] = S.U[c][S.L.idx(i, j)];
+  return OK;
 }
 
 // ---- building blocks exposed for the pins -------------------------------------------------

@@ -437,3 +437,221 @@ def test_op_counts_are_plausible():
     flops = c["add"] + c["mul"] + c["div"] + c["sqrt"]
     per_cell = flops / p.cells
     assert 800 < per_cell < 2500, c
+
+
+# ---------------------------------------------------------------------------------------
+# the immersed boundary on an oblique wall (Sec. 2, Fig. 1(c): ghost states mirror the flow at
+# the image point so that the wall has no normal flux and keeps the tangential velocity)
+# ---------------------------------------------------------------------------------------
+THETA_WALL = np.pi / 6  # 30 degrees
+
+
+def _oblique_wall_problem(n=64):
+    """Solid below the line through (0.3, 0) at 30 degrees on [0,1]^2 (it leaves through the
+    bottom and right sides, so every image point lies inside the domain); transmissive sides.
+    Returns the problem, the unit normal into the fluid and the tangent."""
+    dx = 1.0 / n
+    t = np.array([np.cos(THETA_WALL), np.sin(THETA_WALL)])
+    nrm = np.array([-np.sin(THETA_WALL), np.cos(THETA_WALL)])
+    X, Y = W.cell_centres(n, n, 0.0, 0.0, dx, dx)
+    sdf = (X - 0.3) * nrm[0] + Y * nrm[1]  # exact signed distance to the line
+    p = W.riemann2d(n).with_(sdf=sdf, bc=(0, 0, 0, 0))
+    return p, nrm, t
+
+
+def _garbage_in_solid(p, Wp):
+    """Solid cells hold an unrelated state: the ghost fill, not the initial data, must give
+    the wall its values."""
+    solid = p.sdf < 0
+    for c, v in enumerate((5.0, -3.0, 2.0, 7.0)):
+        Wp[c][solid] = v
+    return Wp
+
+
+def test_oblique_slip_wall_keeps_uniform_tangential_flow():
+    """Uniform flow parallel to a 30-degree wall is an exact steady solution: the mirrored
+    ghosts reproduce it, so the RHS vanishes to round-off.  Fails if ghosts are not filled
+    (garbage in the solid), for a no-slip mirror, or for a mirror that flips the tangential
+    component."""
+    p, nrm, t = _oblique_wall_problem()
+    Wp = np.zeros((4, p.ny, p.nx))
+    Wp[0], Wp[1], Wp[2], Wp[3] = 1.3, 0.7 * t[0], 0.7 * t[1], 0.9
+    U = O.prim_to_cons(p, _garbage_in_solid(p, Wp))
+    L = O.rhs(p, U)
+    assert O.ib_tables(p)["gcell"].size > 100
+    assert np.abs(L).max() < 1e-11  # fluxes O(1), 1/dx = 64
+
+
+def _linear_prims(X, Y):
+    return np.stack([1.0 + 0.3 * X + 0.2 * Y, 0.4 - 0.5 * X + 0.3 * Y, -0.2 + 0.6 * X - 0.1 * Y,
+                     1.0 + 0.2 * X - 0.4 * Y])
+
+
+def _ghost_cells(sdf):
+    """Solid cells with a fluid cell in their 7x7 box (reading O7), computed here directly."""
+    ny, nx = sdf.shape
+    out = []
+    for j in range(ny):
+        for i in range(nx):
+            if sdf[j, i] >= 0:
+                continue
+            box = sdf[max(0, j - 3):j + 4, max(0, i - 3):i + 4]
+            if (box >= 0).any():
+                out.append((j, i))
+    return out
+
+
+def _prims_of(U, gamma=1.4):
+    r = U[0]
+    u, v = U[1] / r, U[2] / r
+    return np.stack([r, u, v, (gamma - 1.0) * (U[3] - 0.5 * r * (u * u + v * v))])
+
+
+def test_oblique_slip_wall_ghosts_mirror_a_linear_field_at_the_image_point():
+    """Ghost state = the slip-wall mirror (rho, p kept, V - 2 (V.n) n) of the interpolated
+    primitive state at the image point x_G - 2 sdf_G n, computed here from the exact geometry.
+    Bilinear interpolation reproduces a linear field exactly, so where the 2x2 interpolation
+    block is all fluid the ghost equals the mirrored linear field at the image point; elsewhere
+    it equals the bilinear weights restricted to fluid cells and renormalised (reading O7),
+    written out here.  Fails for a wrong image-point distance (x_G - sdf n), a mirror of the
+    wrong sign, swapped x/y weights or an inward normal."""
+    p, nrm, _ = _oblique_wall_problem()
+    n, dx = p.nx, p.dx
+    X, Y = W.cell_centres(n, n, 0.0, 0.0, dx, dx)
+    Wp = _garbage_in_solid(p, _linear_prims(X, Y))
+    U = O.prim_to_cons(p, Wp)
+    out = O.ib_fill(p, U)
+    ghosts = _ghost_cells(p.sdf)
+    changed = np.argwhere((out != U).any(axis=0))
+    assert sorted(map(tuple, changed)) == sorted(ghosts)
+    Q = _prims_of(out)
+    Qf = _prims_of(U)
+    exact_checked = 0
+    for j, i in ghosts:
+        xg, yg = X[j, i], Y[j, i]
+        phi = p.sdf[j, i]
+        xi, yi = xg - 2.0 * phi * nrm[0], yg - 2.0 * phi * nrm[1]
+        fx, fy = xi / dx - 0.5, yi / dx - 0.5
+        i0 = min(max(int(np.floor(fx)), 0), n - 2)
+        j0 = min(max(int(np.floor(fy)), 0), n - 2)
+        tx, ty = fx - i0, fy - j0
+        cells = [(j0, i0), (j0, i0 + 1), (j0 + 1, i0), (j0 + 1, i0 + 1)]
+        w = np.array([(1 - tx) * (1 - ty), tx * (1 - ty), (1 - tx) * ty, tx * ty])
+        fluid = np.array([p.sdf[c] >= 0 for c in cells])
+        w = np.where(fluid, w, 0.0)
+        w = w / w.sum()
+        q = sum(w[k] * Qf[:, cells[k][0], cells[k][1]] for k in range(4))
+        if fluid.all():
+            q_lin = _linear_prims(np.array(xi), np.array(yi))
+            assert np.abs(q - q_lin).max() < 1e-13
+            q = q_lin
+            exact_checked += 1
+        V = q[1:3]
+        Vg = V - 2.0 * (V @ nrm) * nrm
+        want = np.array([q[0], Vg[0], Vg[1], q[3]])
+        assert np.abs(Q[:, j, i] - want).max() < 1e-12, (j, i, Q[:, j, i], want)
+    assert exact_checked > 50
+
+
+# ---------------------------------------------------------------------------------------
+# the positivity fallback (reading O6 of "positivity-preserving HLLC", Sec. 2)
+# ---------------------------------------------------------------------------------------
+def _rough_1d(n=200, seed=0):
+    rng = np.random.default_rng(seed)
+    p = W.sod(n).with_(name="rough")
+    Wp = np.zeros((4, 1, n))
+    Wp[0, 0] = 10 ** rng.uniform(-2, 1, n)
+    Wp[1, 0] = rng.uniform(-1, 1, n)
+    Wp[2, 0] = rng.uniform(-0.5, 0.5, n)
+    Wp[3, 0] = 10 ** rng.uniform(-4, 2, n)
+    return p, Wp
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_positivity_fallback_uses_first_order_states_exactly_where_weno_fails(seed):
+    """On a rough 1D state (density over 3 and pressure over 6 decades) WENO5 reconstructs a
+    non-positive density or pressure at many faces.  The RHS must equal the flux divergence
+    built here from the pinned building blocks: at faces where a reconstructed rho or p is
+    <= 0, HLLC of the two adjacent CELL states; elsewhere HLLC of the WENO5 states.  The
+    oracle's count of fallback faces must equal the count found here.  Fails if the fallback is
+    skipped, tests only rho, or takes other cells' states."""
+    p, Wp = _rough_1d(seed=seed)
+    n = p.nx
+    U = O.prim_to_cons(p, Wp)
+    q = _prims_of(U[:, 0, :])
+    qp = np.concatenate([np.repeat(q[:, :1], 3, axis=1), q, np.repeat(q[:, -1:], 3, axis=1)], axis=1)
+    F = np.zeros((4, n + 1))
+    fallbacks = 0
+    for f in range(n + 1):
+        il, ir = f + 2, f + 3  # padded indices of the cells left and right of face f
+        qL = np.array([O.weno5(qp[c, il - 2:il + 3]) for c in range(4)])
+        qR = np.array([O.weno5(qp[c, ir - 2:ir + 3][::-1]) for c in range(4)])
+        if not (qL[0] > 0 and qL[3] > 0 and qR[0] > 0 and qR[3] > 0):
+            qL, qR = qp[:, il], qp[:, ir]
+            fallbacks += 1
+        F[:, f], _ = O.hllc(qL, qR, p.gamma)
+    want = -(F[:, 1:] - F[:, :-1]) / p.dx
+    O.fallback_faces()
+    L = O.rhs(p, U)[:, 0, :]
+    assert O.fallback_faces() == fallbacks and fallbacks > 20
+    assert np.abs(L - want).max() <= 1e-12 * np.abs(want).max()
+
+
+def test_positivity_fallback_occurs_in_the_blast_wave_problem():
+    """The two interacting blast waves (pressures 1000 | 0.01 | 100, reflective ends): the
+    fallback is first taken at step 942 (t = 0.02706), at two faces, and the run stays
+    physical through it."""
+    n = 400
+    p = W.sod(n).with_(name="blast", bc=(1, 1, 0, 0))
+    x = (np.arange(n) + 0.5) / n
+    Wp = np.zeros((4, 1, n))
+    Wp[0] = 1.0
+    Wp[3, 0] = np.where(x < 0.1, 1000.0, np.where(x < 0.9, 0.01, 100.0))
+    U = O.prim_to_cons(p, Wp)
+    O.fallback_faces()
+    first = None
+    for k in range(1, 960):
+        U = O.step(p, U, [O.max_dt(p, U, 0.5)])
+        c = O.fallback_faces()
+        if c and first is None:
+            first = (k, c)
+    assert first == (942, 2)
+    assert U[0].min() > 0 and _prims_of(U[:, 0, :])[3].min() > 0
+
+
+# ---------------------------------------------------------------------------------------
+# the CFL rule (reading O2), from values worked out by hand
+# ---------------------------------------------------------------------------------------
+def _cfl_problem(mu, Pr):
+    """A 6 x 6 grid (dx = 0.1, dy = 0.2, gamma = 1.4) tiled with three states whose sound
+    speeds are whole numbers: (rho, u, v, a) = (1, 0.5, -0.25, 1), (4, -2, 0, 0.5),
+    (0.25, 0, 1, 2), p = rho a^2 / 1.4 = 1/1.4 for all three.  Their rates
+    (|u| + a)/dx + (|v| + a)/dy are 15 + 6.25 = 21.25, 25 + 2.5 = 27.5 and 20 + 15 = 35.
+    A solid cell (sdf < 0) holds a state with a rate of 10^4 that must not count."""
+    states = [(1.0, 0.5, -0.25, 1.0 / 1.4), (4.0, -2.0, 0.0, 1.0 / 1.4), (0.25, 0.0, 1.0, 1.0 / 1.4)]
+    Wp = np.zeros((4, 6, 6))
+    for j in range(6):
+        for i in range(6):
+            Wp[:, j, i] = states[(i + j) % 3]
+    Wp[:, 2, 3] = (1.0, 1000.0, 0.0, 1.0)
+    X, Y = W.cell_centres(6, 6, 0.0, 0.0, 0.1, 0.2)
+    sdf = np.hypot(X - (0.35 + 0.01), Y - (0.5 + 0.02)) - 0.05  # a small body: cell (2, 3) alone is solid
+    assert (sdf < 0).sum() == 1 and sdf[2, 3] < 0
+    p = W.Problem("cfl", 6, 6, 0.0, 0.0, 0.1, 0.2, bc=(0, 0, 0, 0), mu=mu, Pr=Pr, sdf=sdf, W0=Wp)
+    return p
+
+
+@pytest.mark.parametrize("mu,Pr,want", [
+    (0.0, 0.72, 0.5 / 35.0),                                      # convective limit
+    (1e-3, 0.72, 0.5 / 35.0),                                     # viscous cap above it
+    (0.1, 0.72, 0.5 * 0.1 * 0.1 * 0.25 / (2 * 0.1 * (1.4 / 0.72))),  # cap: gamma/Pr > 4/3
+    (0.1, 2.0, 0.5 * 0.1 * 0.1 * 0.25 / (2 * 0.1 * (4.0 / 3.0))),    # cap: 4/3 > gamma/Pr
+])
+def test_cfl_step_matches_hand_computed_values(mu, Pr, want):
+    """dt = CFL / 35 from the fastest fluid state, or the viscous cap
+    CFL h^2 rho_min / (2 mu max(4/3, gamma/Pr)) with h = min(dx, dy) = 0.1, rho_min = 0.25,
+    when that is smaller.  Fails for a wrong max/min, h = max(dx, dy), a missing viscous
+    factor or a solid cell counted."""
+    p = _cfl_problem(mu, Pr)
+    U = O.prim_to_cons(p, p.W0)
+    assert O.max_dt(p, U, 0.5) == pytest.approx(want, rel=1e-14)
