@@ -2,9 +2,11 @@
 
 One "step" = one pass of the whole hot path over the grid: CFL reduction for dt, then three
 Runge-Kutta stages, each = immersed-boundary ghost fill + domain halo fill + fused stage
-kernel (WENO5, HLLC, viscous fluxes, divergence, stage combination).
+kernel (WENO5, HLLC, viscous fluxes, divergence, stage combination).  The default workload is
+the largest single-GPU configuration: the viscous Mach-2 shock over the immersed cylinder,
+2048 x 1024 cells (Navier-Stokes, Re = 1000, Pr = 0.72).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload riemann2d|shock_cylinder]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload shock_cylinder|riemann2d|...]
     python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
     python bench.py --workload mach5_cylinder --to-end   # one whole run to the end time
     python bench.py --slabs 2,4 --steps 20               # the y-slab decomposition on one GPU
@@ -36,8 +38,9 @@ FP64_PEAK_TFLOPS = 1.25
 NN_FLOPS_PER_CELL_STAGE = 2 * 2 * 6336
 # DRAM bytes (read + write) per stage-kernel launch, mean of the three stages of one step,
 # from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of this bench's default
-# run with the TMA-staged variant 0; None for other workloads or variants.
-STAGE_TRAFFIC_BYTES = {("riemann2d", 0): 111.1e6}
+# run with the TMA-staged variant 0 and the current kernel; None for other workloads or
+# variants.
+STAGE_TRAFFIC_BYTES = {("shock_cylinder", 0): 288.9e6}
 L2_FLUSH_BYTES = 256 << 20
 METRIC = "FP64 cell-updates/s per RK step on 1 GB300 (% roofline); adjoint/forward time ratio"
 
@@ -214,8 +217,8 @@ def run_ours(args):
     cfl = prob.cfl
 
     def one_step(Ud):
-        dt = solver.max_dt(Ud, cfl)
-        solver.step(Ud, dt, 1)
+        # CFL reduction, device step size and the three stages; no host synchronisation
+        solver.step_cfl(Ud, cfl, 1)
 
     for _ in range(args.warmup):
         one_step(U)
@@ -376,7 +379,8 @@ def run_ours(args):
             "config": {"workload": desc, "nx": prob.nx, "ny": prob.ny, "cells": cells,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "flushed between steps (256 MiB write)",
-                       "step": "CFL reduction + 3 x (IB fill, halo fill, fused stage kernel)",
+                       "step": "CFL reduction + device step size + 3 x (IB fill, halo fill, fused stage "
+                               "kernel) (js_step_cfl)",
                        "stage_variant": solver.tuning()[0]},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP64_PEAK_TFLOPS,
@@ -621,7 +625,7 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="riemann2d", choices=["riemann2d", "shock_cylinder", "mach5_cylinder", "batched"])
+    ap.add_argument("--workload", default="shock_cylinder", choices=["riemann2d", "shock_cylinder", "mach5_cylinder", "batched"])
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")

@@ -88,13 +88,32 @@ int js_prim_to_cons(js_ctx* ctx, const double* W, double* U);
 int js_rhs(js_ctx* ctx, const double* U, double* dUdt);
 
 /* Largest stable time step of U: dt = cfl / max over fluid cells of
- * (|u| + a)/dx + (|v| + a)/dy, capped by the explicit viscous limit when mu > 0.
- * U: device [4][ny][nx].  dt_out: host.  Synchronises the stream. */
+ * (|u| + a)/dx + (|v| + a)/dy, capped by the explicit viscous limit
+ * cfl h^2 rho_min / (2 mu max(4/3, gamma/Pr)), h = min(dx, dy), when mu > 0 (the paper gives
+ * no CFL rule; this is the reading both implementations take).  The rates are IEEE-rounded in
+ * a fixed operation order, so the result does not depend on the reduction order.
+ * U: device [4][ny][nx].  dt_out: host.  Synchronises the stream.
+ * JS_ERR_NONPHYSICAL when a fluid cell has rho <= 0, p <= 0 or a value that is not finite
+ * (*dt_out is then 0 or not a usable step size). */
 int js_max_dt(js_ctx* ctx, const double* U, double cfl, double* dt_out);
 
 /* Advance U in place by n_steps three-stage SSP-RK3 steps of size dt (the solver step
  * S(U, theta) of Sec. 2 applied n_steps times).  U: device [4][ny][nx].  Asynchronous. */
 int js_step(js_ctx* ctx, double* U, double dt, int n_steps);
+
+/* Advance U in place by n_steps SSP-RK3 steps, each of the CFL step size of the current state
+ * (js_max_dt's rule, computed on the device with the same IEEE operations in the same order, so
+ * the steps equal js_max_dt + js_step ones bit for bit).  No host synchronisation: a loop of
+ * these calls can be captured into a CUDA graph.
+ *   t_dev  : optional device double, the running time; each step adds its dt (t = t + dt)
+ *   t_end  : with t_dev and t_end > 0, the end time: a step with t + dt > t_end takes
+ *            dt = t_end - t, and steps once t >= t_end leave U unchanged
+ *   dt_log : optional device double[n_steps] receiving the step sizes (0 for a step that did
+ *            nothing)
+ * A non-physical state (rho <= 0, p <= 0 or not finite in a fluid cell) makes its step size 0:
+ * the steps leave U unchanged and the device error flag is set (js_sync_status).  Not with
+ * the neural flux (JS_ERR_ARG).  U: device [4][ny][nx].  Asynchronous. */
+int js_step_cfl(js_ctx* ctx, double* U, double cfl, int n_steps, double* t_dev, double t_end, double* dt_log);
 
 /* Vector-Jacobian product of the RHS (reverse mode of js_rhs, Sec. 2 gradient chain rule):
  *   U_bar  = (dL/dU)^T lam          (overwritten), device [4][ny][nx]
@@ -315,6 +334,27 @@ int js_batch_test_timeout(js_batch* b, double budget_s);
 
 void js_batch_destroy(js_batch* b);
 
+/* Arithmetic mode of the forward path (js_rhs, js_step, and js_step_stage without
+ * JS_STAGE_INTERNALS) of this context:
+ *   JS_ARITH_FAST (default): the fused stage kernel, which contracts products into fused
+ *     multiply-adds and replaces division and square root by a refined reciprocal (within
+ *     about 2 ulp) -- each stage agrees with the IEEE-order result to about 1e-15 relative;
+ *   JS_ARITH_IEEE: every operation of the right-hand side (Sec. 2: WENO5 of the primitive
+ *     variables, HLLC with the positivity fallback, viscous fluxes, divergence, artificial
+ *     viscosity), the immersed-boundary ghost fill and the Runge-Kutta stage is one
+ *     IEEE-rounded double operation in a fixed canonical expression order (written out in
+ *     js_ieee.cu), each face and cell computed on its own: the results are reproducible bit for
+ *     bit by any implementation that follows that order, independent of launch shape or
+ *     device.  About 3x slower; extra workspace of 4 padded planes plus the face fluxes
+ *     (allocated by the first switch to it: call before any stream capture).
+ * The reverse-mode entry points, the taped steps and the batched path keep the fast
+ * arithmetic.  JS_ARITH_IEEE does not combine with the neural flux (js_rhs / js_step then
+ * return JS_ERR_ARG).  Errors: JS_ERR_ARG, JS_ERR_NOMEM. */
+#define JS_ARITH_FAST 0
+#define JS_ARITH_IEEE 1
+int js_set_arith(js_ctx* ctx, int mode);
+int js_get_arith(js_ctx* ctx, int* mode);
+
 /* Stage-kernel tuning: tile shape variant (0 .. n_variants-1) used by this context's
  * js_rhs / js_step / js_step_vjp; 0 = 32x32-cell tiles staged by TMA with concurrent x/y sweeps.  Results are identical for every
  * variant; only speed differs (the Python autotuner times them and caches the choice). */
@@ -332,7 +372,8 @@ int js_profile_end(js_ctx* ctx, double* stage_ms, int* stage_launches, long long
 /* Allocation-free CFL time step -- the paper has no counterpart.  It serves callers that
  * cannot allocate device memory, such as a host application or plugin that owns every
  * device allocation through its own pool and forbids libraries to call cudaMalloc.  Same
- * result as js_max_dt (the same IEEE operation order), without a context:
+ * result as js_max_dt, bit for bit (the same IEEE operation order; JS_ERR_NONPHYSICAL for the
+ * same states), without a context:
  *   grid, params : the problem (only nx, ny, dx, dy, gamma, mu, Pr are used)
  *   U            : device [4][ny][nx];  tag: optional device uint8 [ny][nx], 0 = fluid
  *                  cell (only fluid cells count), or NULL for all cells
@@ -341,8 +382,9 @@ int js_profile_end(js_ctx* ctx, double* stage_ms, int* stage_launches, long long
  * process exits: grids above JS_NOALLOC_MAX_CELLS cells return JS_ERR_ARG.  All calls on a
  * device share the array and it keeps the last call's partial results, so calls whose
  * kernels overlap on the GPU race -- serialise them.  The first call on a device looks up
- * the array's device address (cudaGetSymbolAddress); make that first call before any stream
- * capture.  Calls no allocating routine. */
+ * the array's device address (cudaGetSymbolAddress) and keeps it for the process; make that
+ * first call before any stream capture, and do not call it after a cudaDeviceReset of that
+ * device (the kept address belongs to the destroyed context).  Calls no allocating routine. */
 #define JS_NOALLOC_MAX_CELLS 8388608
 int js_max_dt_noalloc(const js_grid* grid, const js_params* params, const double* U,
                       const unsigned char* tag, double cfl, void* stream, double* dt_out);

@@ -14,6 +14,7 @@ import numpy as np
 from . import build as _build
 
 JS_OK, JS_ERR_ARG, JS_ERR_CUDA, JS_ERR_NONPHYSICAL, JS_ERR_TIMEOUT, JS_ERR_IB, JS_ERR_NOMEM = 0, -1, -2, -3, -4, -5, -6
+JS_ARITH_FAST, JS_ARITH_IEEE = 0, 1
 JS_NPARAM = 20
 JS_TAPE_WENO = 1
 JS_STAGE_INTERNALS = 16
@@ -57,6 +58,7 @@ SIGNATURES = {
     "js_rhs": (_I, [_P, _P, _P]),
     "js_max_dt": (_I, [_P, _P, _D, C.POINTER(_D)]),
     "js_step": (_I, [_P, _P, _D, _I]),
+    "js_step_cfl": (_I, [_P, _P, _D, _I, _P, _D, _P]),
     "js_rhs_vjp": (_I, [_P, _P, _P, _P, _P]),
     "js_step_vjp": (_I, [_P, _P, _D, _P, _P, _P]),
     "js_sync_status": (_I, [_P]),
@@ -76,6 +78,8 @@ SIGNATURES = {
     "js_rows_pack": (_I, [_P, _P, _I, _I, _P, _I]),
     "js_rows_unpack": (_I, [_P, _P, _I, _I, _P, _I]),
     "js_step_vjp_taped": (_I, [_P, _I, _D, _P, _P, _P]),
+    "js_set_arith": (_I, [_P, _I]),
+    "js_get_arith": (_I, [_P, C.POINTER(_I)]),
     "js_set_tuning": (_I, [_P, _I]),
     "js_get_tuning": (_I, [_P, C.POINTER(_I), C.POINTER(_I)]),
     "js_profile_begin": (_I, [_P, _I]),
@@ -334,6 +338,17 @@ class Solver:
                                    nm.ctypes.data_as(C.c_void_p), code), "js_set_neural")
         self._nn = (w, w_bar, nm)  # keep the device buffers alive while the library uses them
 
+    def set_arith(self, mode):
+        """"fast" (default: the fused stage kernel) or "ieee" (every operation IEEE-rounded in
+        the canonical order: bit-reproducible)."""
+        code = {"fast": JS_ARITH_FAST, "ieee": JS_ARITH_IEEE}[mode]
+        _check(lib().js_set_arith(self.ctx, code), "js_set_arith")
+
+    def arith(self):
+        m = C.c_int(0)
+        _check(lib().js_get_arith(self.ctx, C.byref(m)), "js_get_arith")
+        return {JS_ARITH_FAST: "fast", JS_ARITH_IEEE: "ieee"}[m.value]
+
     def set_tuning(self, variant):
         _check(lib().js_set_tuning(self.ctx, int(variant)), "js_set_tuning")
 
@@ -360,6 +375,13 @@ class Solver:
     def step(self, U, dt, n_steps=1):
         js_step(self.ctx, U, dt, n_steps)
         return U
+
+    def step_cfl(self, U, cfl, n_steps=1, t=None, t_end=0.0, dt_log=None):
+        """n_steps SSP-RK3 steps of the device-computed CFL step size (no host synchronisation);
+        t: optional float64 CUDA scalar tensor of the running time (advanced; steps stop at
+        t_end > 0); dt_log: optional float64 CUDA tensor of n_steps step sizes."""
+        _check(lib().js_step_cfl(self.ctx, _ptr(U), float(cfl), int(n_steps), None if t is None else _ptr(t),
+                                 float(t_end), None if dt_log is None else _ptr(dt_log)), "js_step_cfl")
 
     def rhs_vjp(self, U, lam, U_bar=None, p_bar=None):
         import torch

@@ -14,7 +14,11 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libjaxshock.so")
-SOURCES = ["js_forward.cu", "js_adjoint.cu", "js_batch.cu", "js_host.cu", "js_noalloc.cu", "js_neural.cu"]
+SOURCES = ["js_forward.cu", "js_adjoint.cu", "js_batch.cu", "js_host.cu", "js_noalloc.cu", "js_neural.cu",
+           "js_ieee.cu"]
+# js_ieee.cu is the IEEE-order arithmetic mode: every operation rounded on its own (no
+# fused multiply-add contraction)
+EXTRA = {"js_ieee.cu": ["-fmad=false"]}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 
@@ -38,7 +42,7 @@ def _compile(src, verbose):
     path = os.path.join(CSRC, src)
     if not _stale(obj, path):
         return obj, ""
-    cmd = [NVCC, "-c", path, "-o", obj + ".tmp"] + _flags()
+    cmd = [NVCC, "-c", path, "-o", obj + ".tmp"] + _flags() + EXTRA.get(src, [])
     if verbose:
         cmd += ["-Xptxas", "-v"]
     r = subprocess.run(cmd, capture_output=True, text=True)

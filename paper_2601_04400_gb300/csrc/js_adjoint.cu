@@ -9,17 +9,24 @@
 //   pass 1    per line: WENO5 forward (internals saved to HBM; skipped when the forward
 //             stage kernel already stored them, then the face states are re-formed from the
 //             saved quotients), HLLC + viscous forward and reverse per face with
-//             Fbar = (lambda'_right - lambda'_left)/h; face-state adjoints saved, viscous and
-//             positivity-fallback adjoints added to Qbar
-//   pass 2    per line: WENO5 reverse from the saved internals; a 5-cell register window
-//             accumulates Qbar along the line
-//   primvjp   Ubar(X) += (dprim/dX)^T Qbar (+ nu * lap of lambda')
+//             Fbar = (lambda'_right - lambda'_left)/h; face-state adjoints saved; the adjoints
+//             that go straight to cells (positivity fallback, viscous terms) saved per face
+//   pass 2    per line segment: WENO5 reverse from the saved internals; a 5-cell register
+//             window emits each cell's adjoint into the segment's own output slots
+//   primvjp   per cell, a gather in a fixed order: Qbar = the slots of the (at most three)
+//             segments of its x line and of its y line that reach it + the per-face adjoints
+//             of the faces that touch it; Ubar(X) += (dprim/dX)^T Qbar (+ nu * lap of lambda')
 //   bcT       transposed halo fill (y sides, then x sides), written as gathers;
 //             inflow halos accumulate into the inflow-state gradient
 //   ibT       transposed immersed-boundary fill: ghost adjoint -> image-point adjoint ->
 //             gathered onto the fluid source cells (CSR built on the host)
 // Parameter gradients (gamma, mu, Pr, nu, inflow states) are accumulated in pbar.
+// No floating-point atomics: every sum runs in a fixed order (per-block partials of the
+// parameter gradient reduced in block order by one block at the end of the stage), so the
+// reverse pass gives the same bits on every run.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include "js_adjoint_device.cuh"
 #include "js_internal.h"
@@ -33,10 +40,28 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// add a per-thread partial to pbar[k] (one atomic per warp)
-__device__ __forceinline__ void pbar_add(double* pbar, int k, double v) {
-  v = warp_sum(v);
-  if (pbar && (threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(pbar + k, v);
+// Per-warp partial sums of the parameter gradient's gamma, mu, Pr and nu entries:
+// pp[4 * w + k] = the sum over warp w's lanes (a fixed shuffle tree), w = the warp's global
+// index (thread index / 32 over the launch).  Every lane calls it (no lane may have left);
+// pp == nullptr (no pbar) skips it.  The partials are summed in warp order at the end of the
+// stage, so the parameter gradient does not depend on timing, and two launch shapes that map
+// the same items to the same warps give the same bits.
+__device__ __forceinline__ void warp_partials(double* pp, long long w, double g, double m, double pr, double n) {
+  if (pp == nullptr) return;
+  g = warp_sum(g);
+  m = warp_sum(m);
+  pr = warp_sum(pr);
+  n = warp_sum(n);
+  if ((threadIdx.x & 31) == 0) {
+    double* o = pp + 4 * w;
+    o[0] = g;
+    o[1] = m;
+    o[2] = pr;
+    o[3] = n;
+  }
+}
+__device__ __forceinline__ long long global_warp() {
+  return ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
 }
 
 __device__ __forceinline__ bool valid_padded(const Lay& L, long long t, int& i, int& j) {
@@ -86,8 +111,6 @@ __global__ void adj_seed_kernel(AdjArgs a, const double* __restrict__ Unext, dou
     a.lam[o] = lam;
     a.Ub[o] = ub;
   }
-#pragma unroll
-  for (int c = 0; c < 5; ++c) a.Qb[c * L.plane + t] = 0.0;
 }
 
 __global__ void adj_prims_kernel(AdjArgs a) {
@@ -112,7 +135,7 @@ __global__ void adj_prims_kernel(AdjArgs a) {
 // DIR 0: lines are rows, faces f in [0, nx] (face f between cells f-1 and f).
 // DIR 1: lines are columns, faces f in [0, ny].
 template <int DIR, bool VISC, bool HAS_T, bool SAVED>
-__device__ __forceinline__ void pass1_body(const AdjArgs& a, int seg_len, long long item) {
+__device__ __forceinline__ void pass1_body(const AdjArgs& a, int seg_len, long long item, long long wbase) {
   const Lay& L = a.lay;
   const int nline = (DIR == 0) ? L.ny : L.nx;
   const int ncell = (DIR == 0) ? L.nx : L.ny;
@@ -201,11 +224,13 @@ __device__ __forceinline__ void pass1_body(const AdjArgs& a, int seg_len, long l
         bql[0] = bL.r; bql[PN] = bL.un; bql[PT] = bL.ut; bql[3] = bL.p;
         bqr[0] = bR.r; bqr[PN] = bR.un; bqr[PT] = bR.ut; bqr[3] = bR.p;
         const int fdir = DIR * 8;
+        // adjoints that go straight to the face's cells ca (left) and cb (right): rho, u, v, p, T
+        double dca[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, dcb[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
         if (fallback) {
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
-            atomicAdd(a.Qb + c * L.plane + ca, bql[c]);
-            atomicAdd(a.Qb + c * L.plane + cb, bqr[c]);
+            dca[c] = bql[c];
+            dcb[c] = bqr[c];
             a.fadj[(long long)(fdir + c) * a.splane + si] = 0.0;
             a.fadj[(long long)(fdir + 4 + c) * a.splane + si] = 0.0;
           }
@@ -216,6 +241,7 @@ __device__ __forceinline__ void pass1_body(const AdjArgs& a, int seg_len, long l
             a.fadj[(long long)(fdir + 4 + c) * a.splane + si] = bqr[c];  // right state of face
           }
         }
+        double* fc = a.fcell + (long long)(DIR * 12) * a.splane + si;
         if (VISC) {
           // F[n] -= tnn; F[t] -= tnt; F[3] -= 0.5 (sbn tnn + sbt tnt) + ck dT
           const double* un = a.Q + PN * L.plane;
@@ -239,55 +265,60 @@ __device__ __forceinline__ void pass1_body(const AdjArgs& a, int seg_len, long l
           const double bck = -Fb[3] * dT;
           const double bdT = -Fb[3] * vc.ck;
           const double bdun = vc.c43n * btnn, bdut = vc.cn * btnt;
-          double* bun = a.Qb + PN * L.plane;
-          double* but = a.Qb + PT * L.plane;
-          double* bT = a.Qb + 4 * L.plane;
-          atomicAdd(bun + ca, bsbn - bdun);
-          atomicAdd(bun + cb, bsbn + bdun);
-          atomicAdd(but + ca, bsbt - bdut);
-          atomicAdd(but + cb, bsbt + bdut);
-          atomicAdd(bT + ca, -bdT);
-          atomicAdd(bT + cb, bdT);
-          if (HAS_T) {
-            const double bsun = vc.ct * btnt, bsut = -vc.c23t * btnn;
-            atomicAdd(bun + ca + ts, bsun);
-            atomicAdd(bun + ca - ts, -bsun);
-            atomicAdd(bun + cb + ts, bsun);
-            atomicAdd(bun + cb - ts, -bsun);
-            atomicAdd(but + ca + ts, bsut);
-            atomicAdd(but + ca - ts, -bsut);
-            atomicAdd(but + cb + ts, bsut);
-            atomicAdd(but + cb - ts, -bsut);
-          }
+          dca[PN] += bsbn - bdun;
+          dcb[PN] += bsbn + bdun;
+          dca[PT] += bsbt - bdut;
+          dcb[PT] += bsbt + bdut;
+          dca[4] = -bdT;
+          dcb[4] = bdT;
+          // tangential differences: +(bsun, bsut) to the cells ca + ts and cb + ts, minus to
+          // ca - ts and cb - ts (gathered by those cells)
+          fc[10 * a.splane] = HAS_T ? vc.ct * btnt : 0.0;
+          fc[11 * a.splane] = HAS_T ? -vc.c23t * btnn : 0.0;
           const double ckck = bck * vc.ck;
           mub += a.inv_mu * fma(btnn, tnn, fma(btnt, tnt, ckck));
           gb += a.kg * ckck;
           prb += a.kp * ckck;
+        }
+#pragma unroll
+        for (int c = 0; c < (VISC ? 5 : 4); ++c) {
+          fc[c * a.splane] = dca[c];
+          fc[(5 + c) * a.splane] = dcb[c];
         }
       }
 #pragma unroll
       for (int c = 0; c < 4; ++c) prevL[c] = Lf[c];
     }
   }
-  pbar_add(a.pbar, 0, gb);
-  if (VISC) {
-    pbar_add(a.pbar, 1, mub);
-    pbar_add(a.pbar, 2, prb);
-  }
+  warp_partials(a.pp, wbase + (item >> 5), gb, mub, prb, 0.0);
 }
 
 // x lines in blocks [0, bx), y lines (2D) in the blocks after them: one launch, both directions
 template <bool VISC, bool HAS_T, bool SAVED>
 __global__ void __launch_bounds__(64) adj_pass1_kernel(AdjArgs a, int seg_len, int bx) {
   if ((int)blockIdx.x < bx)
-    pass1_body<0, VISC, HAS_T, SAVED>(a, seg_len, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+    pass1_body<0, VISC, HAS_T, SAVED>(a, seg_len, (long long)blockIdx.x * blockDim.x + threadIdx.x, 0);
   else
-    pass1_body<1, VISC, HAS_T, SAVED>(a, seg_len, (long long)(blockIdx.x - bx) * blockDim.x + threadIdx.x);
+    pass1_body<1, VISC, HAS_T, SAVED>(a, seg_len, (long long)(blockIdx.x - bx) * blockDim.x + threadIdx.x,
+                                      ((long long)bx * blockDim.x) >> 5);
 }
 
 // =======================================================================================
-// pass 2: WENO reverse from the saved internals, accumulated along the line
+// pass 2: WENO reverse from the saved internals, along line segments.  Segment `seg` of a
+// line runs cells c0 = -1 + seg * L .. c1 - 1 and emits the adjoints of cells c0 - 2 .. c1 + 1
+// (its whole reach) into its own slots; a cell's total is gathered later from the (at most
+// three) segments that reach it, in segment order.
 // =======================================================================================
+// slot k of segment seg, variable c, in direction DIR's part of wrev (lines fastest)
+template <int DIR>
+__device__ __forceinline__ long long wrev_slot(const Lay& L, int seg_len, int c, int seg, int k, int line) {
+  const int nline = (DIR == 0) ? L.ny : L.nx;
+  const int ncell = (DIR == 0) ? L.nx : L.ny;
+  const long long nseg = (ncell + 2 + seg_len - 1) / seg_len;
+  const long long base = (DIR == 0) ? 0 : 4LL * ((L.nx + 2 + seg_len - 1) / seg_len) * (seg_len + 4) * L.ny;
+  return base + ((c * nseg + seg) * (seg_len + 4) + k) * nline + line;
+}
+
 template <int DIR>
 __device__ __forceinline__ void pass2_body(const AdjArgs& a, int seg_len, long long item) {
   const Lay& L = a.lay;
@@ -305,27 +336,48 @@ __device__ __forceinline__ void pass2_body(const AdjArgs& a, int seg_len, long l
   for (int c = 0; c < 4; ++c) {
     // one variable at a time keeps the register window small
     const double* q = a.Q + c * L.plane;
-    double* qb = a.Qb + c * L.plane;
+    double* out = a.wrev + wrev_slot<DIR>(L, seg_len, c, seg, 0, line);
     long long ci = cell_id(c0);
     const long long sst = (DIR == 0) ? a.tpitch : L.pitch;  // stride along the line in saved arrays
     long long si = save_id<DIR>(a, c0, line);
     WenoRev w;
     w.init(q[ci - 2 * st], q[ci - st], q[ci], q[ci + st]);
+    int k = 0;  // slot of cell c0 - 2 + k
 #pragma unroll 1
-    for (int i = c0; i < c1; ++i, ci += st, si += sst) {
+    for (int i = c0; i < c1; ++i, ci += st, si += sst, ++k) {
       double sv[WENO_SAVE];
 #pragma unroll
-      for (int k = 0; k < WENO_SAVE; ++k) sv[k] = a.wsave[(long long)(wdir + c * WENO_SAVE + k) * a.splane + si];
+      for (int m = 0; m < WENO_SAVE; ++m) sv[m] = a.wsave[(long long)(wdir + c * WENO_SAVE + m) * a.splane + si];
       const double Lb = a.fadj[(long long)(fdir + c) * a.splane + si + sst];  // left state of face i+1/2
       const double Rb = a.fadj[(long long)(fdir + 4 + c) * a.splane + si];    // right state of face i-1/2
-      // cell i-2 is complete
-      atomicAdd(qb + ci - 2 * st, w.step(q[ci + 2 * st], sv, Lb, Rb));
+      // cell i-2: this segment's contribution is complete
+      out[(long long)k * nline] = w.step(q[ci + 2 * st], sv, Lb, Rb);
     }
-    // flush cells c1-2 .. c1+1
+    // cells c1-2 .. c1+1
     double rest[4];
     w.flush(rest);
-    for (int k = 0; k < 4; ++k) atomicAdd(qb + ci + (k - 2) * st, rest[k]);
+    for (int m = 0; m < 4; ++m) out[(long long)(k + m) * nline] = rest[m];
   }
+}
+
+// sum of the pass-2 slots of the segments of a DIR line that reach cell m (-3 <= m <= ncell + 2),
+// in segment order
+template <int DIR>
+__device__ __forceinline__ double wrev_gather(const AdjArgs& a, int seg_len, int c, int m, int line) {
+  const Lay& L = a.lay;
+  const int ncell = (DIR == 0) ? L.nx : L.ny;
+  const int nseg = (ncell + 2 + seg_len - 1) / seg_len;
+  int s = (m + 1 >= 0) ? (m + 1) / seg_len : 0;
+  s = min(s, nseg - 1);
+  double t = 0.0;
+  for (int q = s - 1; q <= s + 1; ++q) {
+    if (q < 0 || q >= nseg) continue;
+    const int c0 = -1 + q * seg_len;
+    const int c1 = min(c0 + seg_len, ncell + 1);
+    if (m < c0 - 2 || m >= c1 + 2) continue;
+    t += a.wrev[wrev_slot<DIR>(L, seg_len, c, q, m - (c0 - 2), line)];
+  }
+  return t;
 }
 
 __global__ void __launch_bounds__(64) adj_pass2_kernel(AdjArgs a, int seg_len, int bx) {
@@ -336,17 +388,72 @@ __global__ void __launch_bounds__(64) adj_pass2_kernel(AdjArgs a, int seg_len, i
 }
 
 // =======================================================================================
-// prim reverse (+ artificial viscosity)
+// prim reverse (+ artificial viscosity), after gathering each cell's primitive adjoint
 // =======================================================================================
-__global__ void adj_primvjp_kernel(AdjArgs a) {
+// per-face adjoints of direction DIR that reach padded cell (i, j), added to qb in a fixed
+// order: the face to its low side (the cell is its right cell), the face to its high side,
+// then (viscous, 2D) the tangential-difference terms of the faces of the two neighbouring
+// lines: + from the line below, - from the line above
+template <int DIR, bool VISC>
+__device__ __forceinline__ void face_gather(const AdjArgs& a, int i, int j, double qb[5]) {
+  const Lay& L = a.lay;
+  const int m = (DIR == 0) ? i : j, line = (DIR == 0) ? j : i;
+  const int nline = (DIR == 0) ? L.ny : L.nx, ncell = (DIR == 0) ? L.nx : L.ny;
+  constexpr int PN = (DIR == 0) ? 1 : 2, PT = (DIR == 0) ? 2 : 1, NC = VISC ? 5 : 4;
+  const long long sp = a.splane;
+  const double* fc = a.fcell + (long long)(DIR * 12) * sp;
+  if (line >= 0 && line < nline) {
+    if (m >= 0 && m <= ncell) {
+      const long long f = save_id<DIR>(a, m, line);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) qb[c] += fc[(5 + c) * sp + f];
+    }
+    if (m + 1 >= 0 && m + 1 <= ncell) {
+      const long long f = save_id<DIR>(a, m + 1, line);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) qb[c] += fc[c * sp + f];
+    }
+  }
+  if (VISC && a.two_d) {
+#pragma unroll
+    for (int dl = -1; dl <= 1; dl += 2) {
+      const int ln = line + dl;
+      if (ln < 0 || ln >= nline) continue;
+      for (int f = m; f <= m + 1; ++f) {
+        if (f < 0 || f > ncell) continue;
+        const long long id = save_id<DIR>(a, f, ln);
+        if (dl < 0) {
+          qb[PN] += fc[10 * sp + id];
+          qb[PT] += fc[11 * sp + id];
+        } else {
+          qb[PN] -= fc[10 * sp + id];
+          qb[PT] -= fc[11 * sp + id];
+        }
+      }
+    }
+  }
+}
+
+template <bool VISC>
+__global__ void adj_primvjp_kernel(AdjArgs a, int seg_len) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const Lay& L = a.lay;
   double gb = 0.0, nb = 0.0;
   int i = 0, j = 0;
   if (t < L.plane && valid_padded(L, t, i, j)) {
-    double qb[5], ub[4];
+    // primitive adjoint: WENO5 reverse of the cell's x line and y line, then the faces
+    double qb[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    if (j >= 0 && j < L.ny) {
 #pragma unroll
-    for (int c = 0; c < 5; ++c) qb[c] = a.Qb[c * L.plane + t];
+      for (int c = 0; c < 4; ++c) qb[c] += wrev_gather<0>(a, seg_len, c, i, j);
+    }
+    if (a.two_d && i >= 0 && i < L.nx) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) qb[c] += wrev_gather<1>(a, seg_len, c, j, i);
+    }
+    face_gather<0, VISC>(a, i, j, qb);
+    if (a.two_d) face_gather<1, VISC>(a, i, j, qb);
+    double ub[4];
     prim_vjp(a.X[t], a.X[L.plane + t], a.X[2 * L.plane + t], a.X[3 * L.plane + t], a.gas, qb, ub, gb);
     if (a.has_av) {
       const bool near = i >= -1 && i <= L.nx && j >= (a.two_d ? -1 : 0) && j <= (a.two_d ? L.ny : 0);
@@ -370,8 +477,7 @@ __global__ void adj_primvjp_kernel(AdjArgs a) {
 #pragma unroll
     for (int c = 0; c < 4; ++c) a.Ub[c * L.plane + t] += ub[c];
   }
-  pbar_add(a.pbar, 0, gb);
-  if (a.has_av) pbar_add(a.pbar, 3, nb);
+  warp_partials(a.pp, global_warp(), gb, 0.0, 0.0, nb);
 }
 
 // =======================================================================================
@@ -388,7 +494,7 @@ __device__ __forceinline__ bool halo_source(int kind, int k, int n, bool low, in
   }
 }
 
-__global__ void adj_bcT_kernel(AdjArgs a, BcArgs bc, int phase_y, double* inflow_acc) {
+__global__ void adj_bcT_kernel(AdjArgs a, BcArgs bc, int phase_y, double* inflow_part, int tmax) {
   const Lay& L = a.lay;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   // targets: 6 source rows/columns next to each boundary
@@ -419,37 +525,82 @@ __global__ void adj_bcT_kernel(AdjArgs a, BcArgs bc, int phase_y, double* inflow
 #pragma unroll
     for (int c = 0; c < 4; ++c) a.Ub[c * L.plane + tid] += acc[c];
   }
-  // inflow sides: sum the halo adjoints of each inflow side
-  const long long nh = 6LL * ntan;
-  if (t < nh) {
-    const int r = (int)(t % 6);
-    const int tan = (int)(t / 6) - (phase_y ? 3 : 0);
-    const int s = (r < 3) ? 0 : 1;
-    const int k = (r < 3) ? r + 1 : r - 2;
+  // inflow sides: the halo adjoints of each (side, tangential position), its three layers in
+  // order, into inflow_part[side][position] (summed over positions by adj_inflow_kernel)
+  if (t < 2LL * ntan) {
+    const int s = (int)(t % 2);
+    const int tpos = (int)(t / 2);  // 0 .. ntan - 1
+    const int tan = tpos - (phase_y ? 3 : 0);
     const int side = (phase_y ? 2 : 0) + s;
     if (bc.kind[side] == 3) {
       const int n = phase_y ? L.ny : L.nx;
-      const int h = (s == 0) ? -k : n - 1 + k;
-      const long long hid = phase_y ? L.idx(tan, h) : L.idx(h, tan);
+      double acc[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int k = 1; k <= 3; ++k) {
+        const int h = (s == 0) ? -k : n - 1 + k;
+        const long long hid = phase_y ? L.idx(tan, h) : L.idx(h, tan);
 #pragma unroll
-      for (int c = 0; c < 4; ++c) atomicAdd(inflow_acc + 4 * side + c, a.Ub[c * L.plane + hid]);
+        for (int c = 0; c < 4; ++c) acc[c] += a.Ub[c * L.plane + hid];
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) inflow_part[((long long)side * tmax + tpos) * 4 + c] = acc[c];
     }
   }
 }
 
-// inflow halo adjoints (conserved) -> gradient of the inflow primitive state and gamma
-__global__ void adj_inflow_kernel(AdjArgs a, BcArgs bc, const double* inflow_acc, const double* inflow_prim) {
-  const int side = threadIdx.x;
-  if (side >= 4 || bc.kind[side] != 3 || a.pbar == nullptr) return;
-  const double* S = inflow_acc + 4 * side;
-  const double r = inflow_prim[4 * side], u = inflow_prim[4 * side + 1], v = inflow_prim[4 * side + 2],
-               p = inflow_prim[4 * side + 3];
-  // U = (r, r u, r v, p/(gamma-1) + r (u^2 + v^2)/2)
-  atomicAdd(a.pbar + 4 + 4 * side + 0, S[0] + S[1] * u + S[2] * v + S[3] * 0.5 * (u * u + v * v));
-  atomicAdd(a.pbar + 4 + 4 * side + 1, S[1] * r + S[3] * r * u);
-  atomicAdd(a.pbar + 4 + 4 * side + 2, S[2] * r + S[3] * r * v);
-  atomicAdd(a.pbar + 4 + 4 * side + 3, S[3] * a.gas.g1);
-  atomicAdd(a.pbar + 0, -S[3] * p * a.gas.g1 * a.gas.g1);
+// inflow halo adjoints (conserved) -> gradient of the inflow primitive state and gamma; one
+// warp per side sums its partials in a fixed order, then one thread adds to pbar side by side
+__global__ void __launch_bounds__(128) adj_inflow_kernel(AdjArgs a, BcArgs bc, const double* inflow_part, int tmax,
+                                                         const double* inflow_prim) {
+  __shared__ double S[4][4];
+  const int side = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const Lay& L = a.lay;
+  if (bc.kind[side] == 3 && a.pbar != nullptr) {
+    const int ntan = (side < 2) ? L.ny : L.nx + 6;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int k = lane; k < ntan; k += 32)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) v[c] += inflow_part[((long long)side * tmax + k) * 4 + c];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) v[c] = warp_sum(v[c]);
+    if (lane == 0)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) S[side][c] = v[c];
+  }
+  __syncthreads();
+  if (threadIdx.x != 0 || a.pbar == nullptr) return;
+  for (int sd = 0; sd < 4; ++sd) {
+    if (bc.kind[sd] != 3) continue;
+    const double* s = S[sd];
+    const double r = inflow_prim[4 * sd], u = inflow_prim[4 * sd + 1], v = inflow_prim[4 * sd + 2],
+                 p = inflow_prim[4 * sd + 3];
+    // U = (r, r u, r v, p/(gamma-1) + r (u^2 + v^2)/2)
+    a.pbar[4 + 4 * sd + 0] += s[0] + s[1] * u + s[2] * v + s[3] * 0.5 * (u * u + v * v);
+    a.pbar[4 + 4 * sd + 1] += s[1] * r + s[3] * r * u;
+    a.pbar[4 + 4 * sd + 2] += s[2] * r + s[3] * r * v;
+    a.pbar[4 + 4 * sd + 3] += s[3] * a.gas.g1;
+    a.pbar[0] += -s[3] * p * a.gas.g1 * a.gas.g1;
+  }
+}
+
+// pbar[0..3] += the warp partials pp[4 * b + k], b < nblk: one block, each thread over a fixed
+// set of partials, then a fixed reduction tree
+__global__ void __launch_bounds__(256) adj_pbar_reduce_kernel(const double* __restrict__ pp, long long nblk,
+                                                              double* pbar) {
+  __shared__ double red[4][256];
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  for (long long b = threadIdx.x; b < nblk; b += 256)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] += pp[4 * b + k];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) red[k][threadIdx.x] = v[k];
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x < 4) pbar[threadIdx.x] += red[threadIdx.x][0];
 }
 
 // =======================================================================================
@@ -511,7 +662,7 @@ __global__ void adj_ib_ghost_kernel(AdjArgs a, IbArgs ib, int wall, double* qIb)
     qIb[4 * k + 2] = bv;
     qIb[4 * k + 3] = G[3] * g1;
   }
-  pbar_add(a.pbar, 0, gb);
+  warp_partials(a.pp, global_warp(), gb, 0.0, 0.0, 0.0);
 }
 
 __global__ void adj_ib_src_kernel(AdjArgs a, IbTArgs tb, const double* qIb) {
@@ -533,7 +684,7 @@ __global__ void adj_ib_src_kernel(AdjArgs a, IbTArgs tb, const double* qIb) {
 #pragma unroll
     for (int c = 0; c < 4; ++c) a.Ub[c * L.plane + id] += ub[c];
   }
-  pbar_add(a.pbar, 0, gb);
+  warp_partials(a.pp, global_warp(), gb, 0.0, 0.0, 0.0);
 }
 
 // =======================================================================================
@@ -559,7 +710,7 @@ namespace {
 // would leave most of the GPU idle); pass 1 pays one extra WENO cell per segment, except
 // when the forward stored the internals: then a segment costs almost nothing to start and
 // shorter ones split the work into finer waves
-constexpr int kSeg1 = 16, kSeg1Saved = 8, kSeg2 = 8, kSeg1D = 4, kBlk = 64;
+constexpr int kSeg1 = 16, kSeg1Saved = 8, kSeg1D = 4, kBlk = 64;
 
 unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
@@ -569,19 +720,26 @@ long long line_items(const AdjArgs& a, int dir, int extra, int seg) {
   return (long long)nline * ((ncell + extra + seg - 1) / seg);
 }
 
+// blocks of pass 1 for the x lines (bx) and the y lines (by); seg = segment length
+void pass1_shape(const AdjArgs& a, bool two_d, int& seg, int& bx, int& by) {
+  if (a.weno_saved) {
+    seg = kSeg1Saved;
+  } else {
+    seg = two_d ? kSeg1 : kSeg1D;  // a 1D grid is one line: short segments give it more threads
+  }
+  bx = (int)blocks_for(line_items(a, 0, 1, seg), kBlk);
+  by = two_d ? (int)blocks_for(line_items(a, 1, 1, seg), kBlk) : 0;
+}
+
 cudaError_t pass1(const AdjArgs& a, bool visc, bool two_d, cudaStream_t s) {
+  int seg, bx, by;
+  pass1_shape(a, two_d, seg, bx, by);
   if (a.weno_saved) {
     if (!two_d) return cudaErrorInvalidValue;  // the forward saves exist for 2D grids only
-    const int sx = (int)blocks_for(line_items(a, 0, 1, kSeg1Saved), kBlk);
-    const int sy = (int)blocks_for(line_items(a, 1, 1, kSeg1Saved), kBlk);
-    if (visc) adj_pass1_kernel<true, true, true><<<sx + sy, kBlk, 0, s>>>(a, kSeg1Saved, sx);
-    else adj_pass1_kernel<false, false, true><<<sx + sy, kBlk, 0, s>>>(a, kSeg1Saved, sx);
+    if (visc) adj_pass1_kernel<true, true, true><<<bx + by, kBlk, 0, s>>>(a, seg, bx);
+    else adj_pass1_kernel<false, false, true><<<bx + by, kBlk, 0, s>>>(a, seg, bx);
     return cudaGetLastError();
   }
-  // a 1D grid is one line: short segments give it more threads
-  const int seg = two_d ? kSeg1 : kSeg1D;
-  const int bx = (int)blocks_for(line_items(a, 0, 1, seg), kBlk);
-  const int by = two_d ? (int)blocks_for(line_items(a, 1, 1, seg), kBlk) : 0;
   if (visc) {
     if (two_d) adj_pass1_kernel<true, true, false><<<bx + by, kBlk, 0, s>>>(a, seg, bx);
     else adj_pass1_kernel<true, false, false><<<bx + by, kBlk, 0, s>>>(a, seg, bx);
@@ -591,50 +749,108 @@ cudaError_t pass1(const AdjArgs& a, bool visc, bool two_d, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+int seg2_of(const Lay& L) { return L.ny > 1 ? ADJ_SEG2 : ADJ_SEG2_1D; }
+
 cudaError_t pass2(const AdjArgs& a, bool two_d, cudaStream_t s) {
-  const int seg = two_d ? kSeg2 : kSeg1D;
+  const int seg = seg2_of(a.lay);
   const int bx = (int)blocks_for(line_items(a, 0, 2, seg), kBlk);
   const int by = two_d ? (int)blocks_for(line_items(a, 1, 2, seg), kBlk) : 0;
   adj_pass2_kernel<<<bx + by, kBlk, 0, s>>>(a, seg, bx);
   return cudaGetLastError();
 }
+
+unsigned ib_blocks(int n) { return n > 0 ? blocks_for(n, 128) : 0; }
 }  // namespace
 
-cudaError_t launch_adj_stage(const AdjArgs& a, const BcArgs& bc, const IbArgs& ib, const IbTArgs& ibt, int wall,
+long long adj_wrev_doubles(const Lay& L) {
+  const int seg = seg2_of(L);
+  long long n = 4LL * ((L.nx + 2 + seg - 1) / seg) * (seg + 4) * L.ny;
+  if (L.ny > 1) n += 4LL * ((L.ny + 2 + seg - 1) / seg) * (seg + 4) * L.nx;
+  return n;
+}
+
+long long adj_ppart_doubles(const Lay& L, int n_ghost, int n_src, long long nn_blocks) {
+  // pass 1 takes the most blocks with the shortest segments (saved internals)
+  AdjArgs a;
+  a.lay = L;
+  const bool two_d = L.ny > 1;
+  long long b1 = 0;
+  for (int saved = 0; saved < 2; ++saved) {
+    if (saved && !two_d) continue;
+    a.weno_saved = saved;
+    int seg, bx, by;
+    pass1_shape(a, two_d, seg, bx, by);
+    b1 = std::max(b1, (long long)bx + by);
+  }
+  // warps: pass 1 (64-thread blocks), the neural image reverse and primvjp (256), IB (128)
+  const long long warps = 2 * b1 + 8 * nn_blocks + 8 * (long long)blocks_for(L.plane, 256) +
+                          4 * (long long)(ib_blocks(n_ghost) + ib_blocks(n_src));
+  return 4 * warps;
+}
+
+cudaError_t launch_adj_stage(const AdjArgs& a0, const BcArgs& bc, const IbArgs& ib, const IbTArgs& ibt, int wall,
                              const double* Unext, double* Uacc, double ra, double rb, double dt, bool rhs_mode,
-                             double* inflow_acc, const double* inflow_prim, double* qIb, cudaStream_t s,
+                             double* inflow_part, const double* inflow_prim, double* qIb, cudaStream_t s,
                              long long* launches, const NnArgs* nn) {
+  AdjArgs a = a0;
   const Lay& L = a.lay;
   const unsigned gp = blocks_for(L.plane, 256);
   long long n = 0;
+  // warp partials of pbar[0..3]: consecutive slices for the launches that produce them
+  double* const pp0 = a0.pbar ? a0.pp : nullptr;
+  long long used = 0;
+  auto slice = [&](long long warps) {
+    double* p = pp0 ? pp0 + 4 * used : nullptr;
+    used += warps;
+    return p;
+  };
+  a.pp = nullptr;
   adj_seed_kernel<<<gp, 256, 0, s>>>(a, Unext, Uacc, ra, rb, dt, rhs_mode ? 1 : 0);
   adj_prims_kernel<<<gp, 256, 0, s>>>(a);
   n += 2;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const bool two_d = L.ny > 1;
-  if ((e = pass1(a, a.visc != 0, two_d, s)) != cudaSuccess) return e;
+  {
+    int seg, bx, by;
+    pass1_shape(a, two_d, seg, bx, by);
+    a.pp = slice(2LL * (bx + by));
+    if ((e = pass1(a, a.visc != 0, two_d, s)) != cudaSuccess) return e;
+  }
   if (nn) {
     // the neural flux: its face-state adjoints join the HLLC ones before the WENO5 reverse
+    a.pp = slice(8 * nn_image_vjp_blocks(L));
     if ((e = nn_reverse(*nn, a, s)) != cudaSuccess) return e;
     n += nn->w_bar ? 13 : 9;
   }
+  a.pp = nullptr;
   if ((e = pass2(a, two_d, s)) != cudaSuccess) return e;
   n += 2;
-  adj_primvjp_kernel<<<gp, 256, 0, s>>>(a);
+  a.pp = slice(8LL * gp);
+  if (a.visc) adj_primvjp_kernel<true><<<gp, 256, 0, s>>>(a, seg2_of(L));
+  else adj_primvjp_kernel<false><<<gp, 256, 0, s>>>(a, seg2_of(L));
   ++n;
-  cudaMemsetAsync(inflow_acc, 0, 16 * sizeof(double), s);
+  a.pp = nullptr;
+  const int tmax = std::max(L.nx + 6, L.ny);
   if (two_d) {
-    adj_bcT_kernel<<<blocks_for(6LL * (L.nx + 6), 128), 128, 0, s>>>(a, bc, 1, inflow_acc);
+    adj_bcT_kernel<<<blocks_for(6LL * (L.nx + 6), 128), 128, 0, s>>>(a, bc, 1, inflow_part, tmax);
     ++n;
   }
-  adj_bcT_kernel<<<blocks_for(6LL * L.ny, 128), 128, 0, s>>>(a, bc, 0, inflow_acc);
-  adj_inflow_kernel<<<1, 32, 0, s>>>(a, bc, inflow_acc, inflow_prim);
+  adj_bcT_kernel<<<blocks_for(6LL * L.ny, 128), 128, 0, s>>>(a, bc, 0, inflow_part, tmax);
+  adj_inflow_kernel<<<1, 128, 0, s>>>(a, bc, inflow_part, tmax, inflow_prim);
   n += 2;
   if (ib.n > 0) {
-    adj_ib_ghost_kernel<<<blocks_for(ib.n, 128), 128, 0, s>>>(a, ib, wall, qIb);
-    adj_ib_src_kernel<<<blocks_for(ibt.nsrc, 128), 128, 0, s>>>(a, ibt, qIb);
+    a.pp = slice(4LL * ib_blocks(ib.n));
+    adj_ib_ghost_kernel<<<ib_blocks(ib.n), 128, 0, s>>>(a, ib, wall, qIb);
+    if (ibt.nsrc > 0) {
+      a.pp = slice(4LL * ib_blocks(ibt.nsrc));
+      adj_ib_src_kernel<<<ib_blocks(ibt.nsrc), 128, 0, s>>>(a, ibt, qIb);
+    }
     n += 2;
+  }
+  if (pp0) {
+    adj_pbar_reduce_kernel<<<1, 256, 0, s>>>(pp0, used, a0.pbar);
+    ++n;
   }
   if (launches) *launches += n;
   return cudaGetLastError();

@@ -179,6 +179,8 @@ __global__ void __launch_bounds__(BNT) batch_kernel(BatchArgs b) {
         nxt[2 * k] = 0ULL;
         nxt[2 * k + 1] = 0x7ff0000000000000ULL;
         const double dtk = inst_dt(b.inst[k], red + 2 * k, b.cfl);
+        // a non-physical fluid cell has an infinite rate (cfl_rate): dt = 0
+        if (!(dtk > 0.0) || !(dtk < CUDART_INF)) atomicOr(b.err, ERR_NONPHYSICAL_BIT);
         if (b.t) b.t[k] += dtk;
         if (b.dt_log) b.dt_log[(long long)step * b.count + k] = dtk;
       }
@@ -213,6 +215,7 @@ __global__ void __launch_bounds__(BNT) batch_kernel(BatchArgs b) {
         a.tag = d.tag;
         a.acc = d.acc;
         a.acc2 = d.acc2;
+        a.dtc = nullptr;
         a.err = b.err;
         a.lay = d.lay;
         a.gamma = d.gamma;

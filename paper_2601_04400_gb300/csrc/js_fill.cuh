@@ -2,6 +2,7 @@
 // batched kernel: one domain-halo cell, one immersed-boundary ghost cell (Sec. 2, Fig. 1(c))
 // and the CFL wave-speed rate of one cell.
 #pragma once
+#include <math_constants.h>
 #include "js_device.cuh"
 #include "js_internal.h"
 
@@ -103,12 +104,15 @@ __device__ __forceinline__ void ib_fill_one(double* __restrict__ U, const Lay& l
 }
 
 // CFL rate (|u| + a)/dx [+ (|v| + a)/dy] of one cell with conserved values (r, mx, my, E),
-// IEEE-rounded in the oracle's operation order.
+// IEEE-rounded in the oracle's operation order.  A non-physical cell (rho or p not positive,
+// or not finite) gets the rate +infinity: it dominates every maximum, so the step size of a
+// state holding one is 0 and the CFL entry points report JS_ERR_NONPHYSICAL.
 __device__ __forceinline__ double cfl_rate(double r, double mx, double my, double E, double gamma, double dx,
                                            double dy, bool two_d) {
   const double u = __ddiv_rn(mx, r), v = __ddiv_rn(my, r);
   const double ke = __dmul_rn(__dmul_rn(0.5, r), __dadd_rn(__dmul_rn(u, u), __dmul_rn(v, v)));
   const double p = __dmul_rn(gamma - 1.0, __dsub_rn(E, ke));
+  if (!(r > 0.0) || !(r < CUDART_INF) || !(p > 0.0) || !(p < CUDART_INF)) return CUDART_INF;
   const double a = __dsqrt_rn(__ddiv_rn(__dmul_rn(gamma, p), r));
   double s = __ddiv_rn(__dadd_rn(fabs(u), a), dx);
   if (two_d) s = __dadd_rn(s, __ddiv_rn(__dadd_rn(fabs(v), a), dy));

@@ -8,6 +8,7 @@
 //   stage1d      the same along a single line (ny == 1)
 //   cfl_reduce   maximum wave speed and minimum density (bit-exact IEEE arithmetic)
 #include <cuda_runtime.h>
+#include <math_constants.h>
 
 #include "js_device.cuh"
 #include "js_internal.h"
@@ -87,23 +88,28 @@ __global__ void prim_to_cons_kernel(const double* W, double* U, long long n, dou
 // CFL reduction: rate = (|u| + a)/dx [+ (|v| + a)/dy] and rho over fluid cells, the rate in
 // IEEE-rounded intrinsics in the oracle's operation order, so equal states give equal dt.
 // Two passes keep that result while taking the IEEE rate of few cells: pass 1 takes every
-// fluid cell's rate with the fast reciprocal and reciprocal square root (relative error a few
-// ulp plus the pressure's cancellation, about (E/p) ulp), the exact minimum density, the
-// maximum of these approximate rates and each block's maximum; pass 2 takes the IEEE rate only
-// in blocks, and of cells, whose approximate rate reaches (1 - CFL_MARGIN) of that maximum
-// (once per run of cells with identical states along a row).
-// While the approximation is within CFL_MARGIN/2 of the IEEE rate (E/p below about 1e10) the
-// cell of the largest IEEE rate is among them, so the maximum is the one-pass maximum.
+// fluid cell's rate with the fast reciprocal and reciprocal square root, the exact minimum
+// density, the maximum of these approximate rates and each block's maximum; pass 2 takes the
+// IEEE rate only in blocks, and of cells, whose approximate rate reaches (1 - CFL_MARGIN) of
+// that maximum (once per run of cells with identical states along a row).
+// The approximation's relative error is a few ulp plus the pressure's cancellation error,
+// about (E/p) ulp.  Pass 1 therefore uses it only where p > 1e-8 E (error below 1e-7) and takes
+// the IEEE rate itself elsewhere (near-vacuum or hypersonic cells, non-physical ones), so every
+// pass-1 rate is within CFL_MARGIN/2 of the IEEE rate, the cell of the largest IEEE rate is
+// always a pass-2 candidate, and the result is the one-pass IEEE maximum for every state.
+// A non-physical fluid cell has the rate +infinity in both passes (cfl_rate).
 // =======================================================================================
 constexpr double CFL_MARGIN = 4e-6;
 
 __device__ __forceinline__ double cfl_rate_fast(double r, double mx, double my, double E, double gamma, double dx,
                                                 double dy, double idx, double idy, bool two_d) {
-  if (!(r > 1e-290)) return cfl_rate(r, mx, my, E, gamma, dx, dy, two_d);  // tiny, zero or NaN density
+  if (!(r > 1e-290) || !(r < 1e290)) return cfl_rate(r, mx, my, E, gamma, dx, dy, two_d);
   const double rr = recip(r);
   const double u = mx * rr, v = my * rr;
   const double ke = (0.5 * r) * fma(u, u, v * v);
   const double p = (gamma - 1.0) * (E - ke);
+  // p <= 1e-8 E, p <= 0 or NaN: the approximation's error bound does not hold
+  if (!(p > 1e-8 * E) || !(E < 1e290)) return cfl_rate(r, mx, my, E, gamma, dx, dy, two_d);
   const double c2 = (gamma * p) * rr;
   const double a = (c2 > 1e-290) ? c2 * rsqrt_nr(c2) : sqrt(c2);
   double s = (fabs(u) + a) * idx;
@@ -149,7 +155,8 @@ __global__ void cfl_pass1_kernel(const double* __restrict__ U, long long n, int 
   }
   cfl_block_reduce(rate, &rmin);
   if (threadIdx.x == 0) {
-    // non-negative doubles order like their bit patterns
+    // non-negative doubles order like their bit patterns (a negative density is a non-physical
+    // cell, whose infinite rate makes the step size 0 whatever the minimum holds)
     bmax[blockIdx.x] = rate;
     atomicMax(&red[2], (unsigned long long)__double_as_longlong(rate));
     atomicMin(&red[1], (unsigned long long)__double_as_longlong(rmin));
@@ -206,15 +213,65 @@ __global__ void cfl_pass2_kernel(const double* __restrict__ U, long long n, int 
   if (threadIdx.x == 0) atomicMax(&red[0], (unsigned long long)__double_as_longlong(rate));
 }
 
+// Device step size from the CFL reduction in red, with js_max_dt's arithmetic (the same IEEE
+// operations in the same order): dt = cfl / rate, capped by the viscous limit
+// cfl hmin^2 rho_min / (2 mu lim); clipped to t_end - t when t + dt > t_end (t: running time,
+// or nullptr), the step inactive once t reaches t_end or when dt is not a positive number
+// (a non-physical state: the error flag is set).  Writes the stage constants dtc and dt_log[k].
+__global__ void cfl_dt_kernel(const unsigned long long* __restrict__ red, double cfl, double dx, double dy,
+                              double nu, int visc, double mu, double lim, double hmin, double* t, double t_end,
+                              double* __restrict__ dtc, double* __restrict__ dt_log, int k, int* err) {
+  const double rate = __longlong_as_double((long long)red[0]);
+  const double rmin = __longlong_as_double((long long)red[1]);
+  double dt = __ddiv_rn(cfl, rate);
+  if (visc) {
+    const double dtv = __ddiv_rn(__dmul_rn(__dmul_rn(__dmul_rn(cfl, hmin), hmin), rmin),
+                                 __dmul_rn(__dmul_rn(2.0, mu), lim));
+    dt = (dtv < dt) ? dtv : dt;
+  }
+  bool active = true;
+  if (!(dt > 0.0) || !(dt < CUDART_INF)) {
+    atomicOr(err, ERR_NONPHYSICAL_BIT);
+    active = false;
+  }
+  if (active && t != nullptr && t_end > 0.0) {
+    const double tc = *t;
+    if (!(tc < t_end)) active = false;
+    else if (__dadd_rn(tc, dt) > t_end) dt = __dsub_rn(t_end, tc);
+  }
+  if (!active) dt = 0.0;
+  if (active && t != nullptr) *t = __dadd_rn(*t, dt);
+  dtc[0] = __ddiv_rn(dt, dx);
+  dtc[1] = __ddiv_rn(dt, dy);
+  dtc[2] = __ddiv_rn(__dmul_rn(dt, nu), __dmul_rn(dx, dx));
+  dtc[3] = __ddiv_rn(__dmul_rn(dt, nu), __dmul_rn(dy, dy));
+  dtc[4] = active ? 1.0 : 0.0;
+  dtc[5] = dt;
+  if (dt_log) dt_log[k] = dt;
+}
+
 __global__ void cfl_init_kernel(unsigned long long* red) {
   red[0] = 0ULL;                    // IEEE rate maximum
   red[1] = 0x7ff0000000000000ULL;   // density minimum
   red[2] = 0ULL;                    // approximate rate maximum
 }
 
+// the stage constants of a launch: the arguments, or those of the device step size
+__device__ __forceinline__ bool stage_constants(const StageArgs& a0, StageArgs& a) {
+  a = a0;
+  if (a0.dtc == nullptr) return true;
+  a.cx = a0.dtc[0];
+  a.cy = a0.dtc[1];
+  a.avx = a0.dtc[2];
+  a.avy = a0.dtc[3];
+  return a0.dtc[4] != 0.0;
+}
+
 template <int TX, int TY, int LX, int LY, bool VISC, bool RHS>
 __global__ void __launch_bounds__(Stage2D<TX, TY, LX, LY, VISC, RHS>::NT)
-stage2d_kernel(StageArgs a) {
+stage2d_kernel(StageArgs a0) {
+  StageArgs a;
+  if (!stage_constants(a0, a)) return;
   extern __shared__ double smem[];
   stage_tile<TX, TY, LX, LY, VISC, RHS>(a, blockIdx.x, blockIdx.y, smem);
 }
@@ -223,7 +280,9 @@ stage2d_kernel(StageArgs a) {
 // WENO5 internals of the stage go to a.wsave for the reverse pass
 template <int TX, int TY, int LX, int LY, bool VISC, bool RHS, bool SAVE>
 __global__ void __launch_bounds__(Stage2DC<TX, TY, LX, LY, VISC>::NT, SAVE ? 3 : 1)
-stage2dc_kernel(StageArgs a, int ntx, int ntiles) {
+stage2dc_kernel(StageArgs a0, int ntx, int ntiles) {
+  StageArgs a;
+  if (!stage_constants(a0, a)) return;
   extern __shared__ double smem[];
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     stage_tile_c<TX, TY, LX, LY, VISC, RHS, false, SAVE>(a, t % ntx, t / ntx, smem);
@@ -234,7 +293,9 @@ stage2dc_kernel(StageArgs a, int ntx, int ntiles) {
 // the same with the tile staged by TMA (tensor map of the stage input as a grid constant)
 template <int TX, int TY, int LX, int LY, bool VISC, bool RHS, bool SAVE>
 __global__ void __launch_bounds__(Stage2DC<TX, TY, LX, LY, VISC, true>::NT, SAVE ? 3 : 1)
-stage2dc_tma_kernel(StageArgs a, int ntx, int ntiles, const __grid_constant__ TensorMap128 tmap) {
+stage2dc_tma_kernel(StageArgs a0, int ntx, int ntiles, const __grid_constant__ TensorMap128 tmap) {
+  StageArgs a;
+  if (!stage_constants(a0, a)) return;
   extern __shared__ __align__(128) double smem[];
   __shared__ __align__(8) unsigned long long bar;
   if (threadIdx.x == 0) mbar_init(&bar);
@@ -247,7 +308,9 @@ stage2dc_tma_kernel(StageArgs a, int ntx, int ntiles, const __grid_constant__ Te
 }
 
 template <int TX, int LX, bool VISC, bool RHS>
-__global__ void __launch_bounds__(TX / LX) stage1d_kernel(StageArgs a) {
+__global__ void __launch_bounds__(TX / LX) stage1d_kernel(StageArgs a0) {
+  StageArgs a;
+  if (!stage_constants(a0, a)) return;
   constexpr int NPL = VISC ? 5 : 4;
   constexpr int PS = TX + 6;
   constexpr int NT = TX / LX;
@@ -441,6 +504,14 @@ cudaError_t launch_rows_unpack(double* U, int nx, int ny, int row0, int nrows, c
 cudaError_t launch_prim_to_cons(const double* W, double* U, long long n, double gamma, cudaStream_t s) {
   const int bs = 256;
   prim_to_cons_kernel<<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>(W, U, n, 1.0 / (gamma - 1.0));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cfl_dt(const unsigned long long* red, double cfl, double dx, double dy, double nu, double mu,
+                          double lim, double hmin, double* t, double t_end, double* dtc, double* dt_log, int k,
+                          int* err, cudaStream_t s) {
+  cfl_dt_kernel<<<1, 1, 0, s>>>(red, cfl, dx, dy, nu, mu > 0.0 ? 1 : 0, mu, lim, hmin, t, t_end, dtc, dt_log, k,
+                                err);
   return cudaGetLastError();
 }
 

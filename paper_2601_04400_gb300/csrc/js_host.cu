@@ -40,6 +40,7 @@ struct js_ctx {
   int* err = nullptr;
   unsigned long long* red = nullptr;
   double* cfl_bmax = nullptr;  // per-block scratch of the CFL reduction
+  double* dtc = nullptr;       // stage constants of the device step size (js_step_cfl)
   BcArgs bc;
   // transposed IB tables
   int n_src = 0;
@@ -50,7 +51,9 @@ struct js_ctx {
   // adjoint workspace (allocated by the first vjp call)
   bool adj_ready = false;
   double* Q = nullptr;       // 5 planes
-  double* Qb = nullptr;      // 5 planes
+  double* fcell = nullptr;   // 24 saved planes: per-face adjoints for the cells of the face
+  double* wrev = nullptr;    // pass-2 segment slots (js::adj_wrev_doubles)
+  double* ppart = nullptr;   // block partials of the parameter gradient (js::adj_ppart_doubles)
   double* lam = nullptr;     // 4 planes
   double* P0 = nullptr;      // 4 planes (stage adjoint ping)
   double* P1 = nullptr;      // 4 planes (pong)
@@ -58,7 +61,7 @@ struct js_ctx {
   double* wsave = nullptr;   // 56 planes
   double* wsave_fwd = nullptr;  // 2 x 56 planes: internals stored by the forward stages 1, 2
   double* fadj = nullptr;    // 16 planes
-  double* inflow_acc = nullptr;   // 16
+  double* inflow_part = nullptr;  // [4 sides][max(nx + 6, ny)][4] inflow halo adjoint partials
   double* inflow_prim = nullptr;  // 16
   double* inflow_host = nullptr;  // 16, pinned
   bool inflow_dirty = true;       // inflow_prim to be uploaded
@@ -76,6 +79,8 @@ struct js_ctx {
   bool nn_keep_failed = false;
   double* nn_partial = nullptr;
   int variant = 0;  // stage-kernel tile shape (js_set_tuning)
+  int arith = JS_ARITH_FAST;  // js_set_arith
+  js::IeeeBufs ieee = {nullptr, nullptr, nullptr};  // workspace of JS_ARITH_IEEE
   std::vector<std::pair<const double*, js::TensorMap128>> tmaps;  // TMA maps of stage inputs
   // tape: per slot the three filled stage states of one recorded step and, when recording
   // internals (2D), the WENO5 internals of its three stages
@@ -296,8 +301,11 @@ StageArgs base_args(const js_ctx* c) {
   return a;
 }
 
-int fill_halos(js_ctx* c, double* X) {
-  JS_CUDA(js::launch_ib_fill(X, c->lay, ib_args(c), c->p.gamma, c->p.wall, c->stream));
+int fill_halos(js_ctx* c, double* X, bool ieee = false) {
+  if (ieee)
+    JS_CUDA(js::launch_ieee_ib_fill(X, c->lay, ib_args(c), c->p.gamma, c->p.wall, c->stream));
+  else
+    JS_CUDA(js::launch_ib_fill(X, c->lay, ib_args(c), c->p.gamma, c->p.wall, c->stream));
   JS_CUDA(js::launch_bc_fill(X, c->lay, c->bc, c->stream));
   c->launches += (c->n_ghost > 0) ? 2 : 1;
   return JS_OK;
@@ -414,6 +422,16 @@ int stage(js_ctx* c, const StageArgs& a, bool visc, bool rhs) {
   return nn_after(c, a, rhs);
 }
 
+// a forward stage (or the RHS) of js_rhs / js_step / js_step_stage in the context's arithmetic
+// mode: the fused stage kernel, or the IEEE-order kernels (stage k of step size dt)
+int stage_fwd(js_ctx* c, const StageArgs& a, bool rhs, double dt, int k) {
+  if (c->arith != JS_ARITH_IEEE) return stage(c, a, c->p.mu > 0.0, rhs);
+  if (c->nn_on) return JS_ERR_ARG;
+  JS_CUDA(js::launch_ieee_stage(a, c->ieee, dt, k, rhs, c->p.mu, c->p.Pr, c->p.nu, c->g.dx, c->g.dy, c->stream));
+  c->launches += (c->g.ny > 1) ? 4 : 3;
+  return JS_OK;
+}
+
 }  // namespace
 
 // batched kernel description of a context (used by js_batch.cu)
@@ -465,16 +483,17 @@ void js_destroy(js_ctx* c) {
   cudaFree(c->N); cudaFree(c->A); cudaFree(c->B); cudaFree(c->acc); cudaFree(c->acc2);
   cudaFree(c->tag);
   cudaFree(c->ib_dst); cudaFree(c->ib_src); cudaFree(c->ib_w); cudaFree(c->ib_nrm);
-  cudaFree(c->err); cudaFree(c->red); cudaFree(c->cfl_bmax);
+  cudaFree(c->err); cudaFree(c->red); cudaFree(c->cfl_bmax); cudaFree(c->dtc);
+  cudaFree(c->ieee.Q); cudaFree(c->ieee.F); cudaFree(c->ieee.G);
   cudaFree(c->ibt_cell); cudaFree(c->ibt_ptr); cudaFree(c->ibt_ghost); cudaFree(c->ibt_w);
-  cudaFree(c->Q); cudaFree(c->Qb); cudaFree(c->lam); cudaFree(c->P0); cudaFree(c->P1); cudaFree(c->Uacc);
+  cudaFree(c->Q); cudaFree(c->fcell); cudaFree(c->wrev); cudaFree(c->ppart); cudaFree(c->lam); cudaFree(c->P0); cudaFree(c->P1); cudaFree(c->Uacc);
   cudaFree(c->wsave); cudaFree(c->wsave_fwd); cudaFree(c->fadj);
   if (c->inflow_host) cudaFreeHost(c->inflow_host);
   cudaFree(c->nnQ); cudaFree(c->nn_partial); cudaFree(c->nn_wsave);
   for (void* b : c->nn_buf) cudaFree(b);
   for (void* b : c->nn_bf16) cudaFree(b);
   for (void* b : c->nn_keep) cudaFree(b);
-  cudaFree(c->inflow_acc); cudaFree(c->inflow_prim); cudaFree(c->qIb);
+  cudaFree(c->inflow_part); cudaFree(c->inflow_prim); cudaFree(c->qIb);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
   for (double* t : c->tape) cudaFree(t);
   for (double* t : c->tape_w) cudaFree(t);
@@ -522,7 +541,8 @@ int create_ctx(const js_grid* grid, const js_params* params, const js_boundary* 
       cudaMalloc(&c->acc, sizeof(double) * 4 * (size_t)grid->nx * grid->ny) != cudaSuccess ||
       cudaMalloc(&c->acc2, sizeof(double) * 4 * (size_t)grid->nx * grid->ny) != cudaSuccess ||
       cudaMalloc(&c->red, 4 * sizeof(unsigned long long)) != cudaSuccess ||
-      cudaMalloc(&c->cfl_bmax, sizeof(double) * js::CFL_MAX_BLOCKS) != cudaSuccess) {
+      cudaMalloc(&c->cfl_bmax, sizeof(double) * js::CFL_MAX_BLOCKS) != cudaSuccess ||
+      cudaMalloc(&c->dtc, sizeof(double) * js::DTC_N) != cudaSuccess) {
     js_destroy(c);
     return JS_ERR_NOMEM;
   }
@@ -650,7 +670,7 @@ int js_rhs(js_ctx* c, const double* U, double* dUdt) {
   if (!c || !U || !dUdt || U == dUdt) return JS_ERR_ARG;
   JS_CUDA(js::launch_pack(U, c->N, c->lay, c->stream));
   ++c->launches;
-  int rc = fill_halos(c, c->N);
+  int rc = fill_halos(c, c->N, c->arith == JS_ARITH_IEEE);
   if (rc) return rc;
   StageArgs a = base_args(c);
   a.Uin = c->N;
@@ -663,7 +683,7 @@ int js_rhs(js_ctx* c, const double* U, double* dUdt) {
   a.rk_a = 0.0;
   a.rk_b = 1.0;
   a.use_un = 0;
-  return stage(c, a, c->p.mu > 0.0, true);
+  return stage_fwd(c, a, true, 0.0, 0);
 }
 
 int js_max_dt(js_ctx* c, const double* U, double cfl, double* dt_out) {
@@ -704,7 +724,7 @@ int js_step(js_ctx* c, double* U, double dt, int n_steps) {
   const double rb[3] = {1.0, 0.25, 2.0 / 3.0};
   for (int k = 0; k < n_steps; ++k) {
     for (int s = 0; s < 3; ++s) {
-      int rc = fill_halos(c, in[s]);
+      int rc = fill_halos(c, in[s], c->arith == JS_ARITH_IEEE);
       if (rc) return rc;
       a.Uin = in[s];
       a.Un = c->N;
@@ -712,12 +732,48 @@ int js_step(js_ctx* c, double* U, double dt, int n_steps) {
       a.rk_a = ra[s];
       a.rk_b = rb[s];
       a.use_un = (s > 0) ? 1 : 0;
-      rc = stage(c, a, visc, false);
+      rc = (c->arith == JS_ARITH_IEEE) ? stage_fwd(c, a, false, dt, s) : stage(c, a, visc, false);
       if (rc) return rc;
     }
   }
   JS_CUDA(js::launch_unpack(c->N, U, c->lay, c->stream));
   c->launches += 2;  // pack + unpack
+  return JS_OK;
+}
+
+int js_step_cfl(js_ctx* c, double* U, double cfl, int n_steps, double* t_dev, double t_end, double* dt_log) {
+  if (!c || !U || n_steps < 0 || !(cfl > 0.0) || c->nn_on) return JS_ERR_ARG;
+  const bool ieee = c->arith == JS_ARITH_IEEE;
+  const bool visc = c->p.mu > 0.0;
+  const double hmin = (c->g.ny > 1) ? (c->g.dx < c->g.dy ? c->g.dx : c->g.dy) : c->g.dx;
+  const double lim = visc ? ((4.0 / 3.0 < c->p.gamma / c->p.Pr) ? c->p.gamma / c->p.Pr : 4.0 / 3.0) : 0.0;
+  double* in[3] = {c->N, c->A, c->B};
+  double* outp[3] = {c->A, c->B, c->N};
+  const double ra[3] = {0.0, 0.75, 1.0 / 3.0};
+  const double rb[3] = {1.0, 0.25, 2.0 / 3.0};
+  StageArgs a = base_args(c);
+  a.dtc = c->dtc;
+  for (int k = 0; k < n_steps; ++k) {
+    JS_CUDA(js::launch_cfl(U, c->lay, c->tag, c->p.gamma, c->g.dx, c->g.dy, c->red, c->cfl_bmax, c->stream));
+    JS_CUDA(js::launch_cfl_dt(c->red, cfl, c->g.dx, c->g.dy, c->p.nu, c->p.mu, lim, hmin, t_dev, t_end, c->dtc,
+                              dt_log, k, c->err, c->stream));
+    JS_CUDA(js::launch_pack(U, c->N, c->lay, c->stream));
+    c->launches += 5;
+    for (int s = 0; s < 3; ++s) {
+      int rc = fill_halos(c, in[s], ieee);
+      if (rc) return rc;
+      a.Uin = in[s];
+      a.Un = c->N;
+      a.Uout = outp[s];
+      a.rk_a = ra[s];
+      a.rk_b = rb[s];
+      a.use_un = (s > 0) ? 1 : 0;
+      rc = ieee ? stage_fwd(c, a, false, 0.0, s) : stage(c, a, visc, false);
+      if (rc) return rc;
+    }
+    JS_CUDA(js::launch_unpack(c->N, U, c->lay, c->stream));
+    ++c->launches;
+  }
   return JS_OK;
 }
 
@@ -750,7 +806,7 @@ int js_step_stage(js_ctx* c, const double* U_n, const double* U_in, double* U_ou
   a.avy = dt * c->p.nu / (c->g.dy * c->g.dy);
   const double ra[3] = {0.0, 0.75, 1.0 / 3.0};
   const double rb[3] = {1.0, 0.25, 2.0 / 3.0};
-  int rc = fill_halos(c, X);
+  int rc = fill_halos(c, X, !keep && c->arith == JS_ARITH_IEEE);
   if (rc) return rc;
   a.Uin = X;
   a.Un = c->N;
@@ -759,7 +815,7 @@ int js_step_stage(js_ctx* c, const double* U_n, const double* U_in, double* U_ou
   a.rk_b = rb[stage_k];
   a.use_un = (stage_k > 0) ? 1 : 0;
   if (keep) rc = stage_save(c, a, c->p.mu > 0.0, c->wsave_fwd + 56 * (size_t)saved_plane(c) * stage_k);
-  else rc = stage(c, a, c->p.mu > 0.0, false);
+  else rc = stage_fwd(c, a, false, dt, stage_k);
   if (rc) return rc;
   if (stage_k < 2) c->stage_kept[stage_k] = keep;
   JS_CUDA(js::launch_unpack(c->B, U_out, c->lay, c->stream));
@@ -773,7 +829,7 @@ int adj_reserve(js_ctx* c) {
   if (c->adj_ready) return JS_OK;
   const size_t pl = sizeof(double) * (size_t)c->lay.plane;
   struct { double** p; size_t planes; } bufs[] = {
-      {&c->Q, 5}, {&c->Qb, 5}, {&c->lam, 4}, {&c->P0, 4}, {&c->P1, 4}, {&c->Uacc, 4}};
+      {&c->Q, 5}, {&c->lam, 4}, {&c->P0, 4}, {&c->P1, 4}, {&c->Uacc, 4}};
   for (auto& b : bufs) {
     if (cudaMalloc(b.p, b.planes * pl) != cudaSuccess) return JS_ERR_NOMEM;
     JS_CUDA(cudaMemsetAsync(*b.p, 0, b.planes * pl, c->stream));  // ordered with the caller's work
@@ -791,7 +847,13 @@ int adj_reserve(js_ctx* c) {
     }
     JS_CUDA(cudaMemsetAsync(c->wsave_fwd, 0, 2 * 56 * spl, c->stream));
   }
-  if (cudaMalloc(&c->inflow_acc, 16 * sizeof(double)) != cudaSuccess ||
+  const size_t tmax = (size_t)std::max(c->g.nx + 6, c->g.ny);
+  const size_t npp = (size_t)js::adj_ppart_doubles(c->lay, c->n_ghost, c->n_src, js::nn_image_vjp_blocks(c->lay));
+  if (cudaMalloc(&c->fcell, 24 * spl) != cudaSuccess ||
+      cudaMalloc(&c->wrev, sizeof(double) * (size_t)js::adj_wrev_doubles(c->lay)) != cudaSuccess ||
+      cudaMalloc(&c->ppart, sizeof(double) * npp) != cudaSuccess)
+    return JS_ERR_NOMEM;
+  if (cudaMalloc(&c->inflow_part, sizeof(double) * 16 * tmax) != cudaSuccess ||
       cudaMalloc(&c->inflow_prim, 16 * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&c->qIb, sizeof(double) * 4 * (size_t)(c->n_ghost > 0 ? c->n_ghost : 1)) != cudaSuccess)
     return JS_ERR_NOMEM;
@@ -806,7 +868,9 @@ js::AdjArgs adj_args(js_ctx* c, const double* X, double* Ub, double* p_bar) {
   a.X = X;
   a.Q = c->Q;
   a.lam = c->lam;
-  a.Qb = c->Qb;
+  a.fcell = c->fcell;
+  a.wrev = c->wrev;
+  a.pp = c->ppart;
   a.Ub = Ub;
   a.wsave = c->wsave;
   a.fadj = c->fadj;
@@ -855,7 +919,7 @@ int adj_stage(js_ctx* c, const double* X, const double* Unext, double* Ub, doubl
   }
   c->nn.g1 = 1.0 / (c->p.gamma - 1.0);
   JS_CUDA(js::launch_adj_stage(a, c->bc, ib_args(c), ibt_args(c), c->p.wall, Unext, c->Uacc, ra, rb, dt, rhs_mode,
-                               c->inflow_acc, c->inflow_prim, c->qIb, c->stream, &c->launches,
+                               c->inflow_part, c->inflow_prim, c->qIb, c->stream, &c->launches,
                                c->nn_on ? &c->nn : nullptr));
   return JS_OK;
 }
@@ -1130,6 +1194,29 @@ int js_sync_status(js_ctx* c) {
   JS_CUDA(cudaStreamSynchronize(c->stream));
   if (h & js::ERR_TIMEOUT_BIT) return JS_ERR_TIMEOUT;
   if (h & js::ERR_NONPHYSICAL_BIT) return JS_ERR_NONPHYSICAL;
+  return JS_OK;
+}
+
+int js_set_arith(js_ctx* c, int mode) {
+  if (!c || (mode != JS_ARITH_FAST && mode != JS_ARITH_IEEE)) return JS_ERR_ARG;
+  if (mode == JS_ARITH_IEEE && !c->ieee.Q) {
+    const size_t nx = (size_t)c->g.nx, ny = (size_t)c->g.ny;
+    if (cudaMalloc(&c->ieee.Q, sizeof(double) * 4 * (size_t)c->lay.plane) != cudaSuccess ||
+        cudaMalloc(&c->ieee.F, sizeof(double) * 4 * (nx + 1) * ny) != cudaSuccess ||
+        (ny > 1 && cudaMalloc(&c->ieee.G, sizeof(double) * 4 * nx * (ny + 1)) != cudaSuccess)) {
+      cudaFree(c->ieee.Q);
+      cudaFree(c->ieee.F);
+      c->ieee = {nullptr, nullptr, nullptr};
+      return JS_ERR_NOMEM;
+    }
+  }
+  c->arith = mode;
+  return JS_OK;
+}
+
+int js_get_arith(js_ctx* c, int* mode) {
+  if (!c || !mode) return JS_ERR_ARG;
+  *mode = c->arith;
   return JS_OK;
 }
 

@@ -26,7 +26,14 @@ struct StageArgs {
   double* wsave;
   long long splane;
   int tpitch;
+  // device-resident step size (js_step_cfl): when set, cx, cy, avx, avy are read from
+  // dtc[0..3] at kernel start, and dtc[4] == 0 means the step is inactive (skip the stage)
+  const double* dtc;
 };
+
+// the per-step constants of a device step size dt: dtc = {dt/dx, dt/dy, dt nu/dx^2,
+// dt nu/dy^2, active, dt}
+constexpr int DTC_N = 6;
 
 struct BcArgs {
   int kind[4];
@@ -56,7 +63,6 @@ struct AdjArgs {
   const double* X;           // padded filled stage state (4 planes)
   double* Q;                 // padded primitives rho, u, v, p, T (5 planes)
   double* lam;               // padded lambda' (4 planes), zero outside fluid cells
-  double* Qb;                // padded primitive adjoints (5 planes)
   double* Ub;                // padded conserved adjoints of X (4 planes)
   double* wsave;             // WENO internals [dir][var][7] planes of splane doubles
   double* fadj;              // face-state adjoints [dir][left/right][var] planes of splane
@@ -72,7 +78,23 @@ struct AdjArgs {
   double inv_mu, kg, kp;     // 1/mu, -1/(gamma (gamma-1)), -1/Pr
   int visc, has_av, two_d;
   int weno_saved;            // wsave already holds the stage's WENO internals (forward SAVE)
+  // deterministic reverse (no floating-point atomics: every sum in a fixed order)
+  double* fcell;             // per face [dir][12] planes of splane: adjoints that go straight to
+                             //   the two cells of the face (positivity fallback, viscous terms:
+                             //   left cell rho,u,v,p,T at 0-4, right cell at 5-9, tangential
+                             //   derivative terms at 10-11)
+  double* wrev;              // pass-2 output slots [dir][4][seg][SL][line] (WENO5 reverse)
+  double* pp;                // block partials of pbar[0..3] of the current launch (4 per block)
 };
+
+// pass-2 segment length (cells per thread along a line) and slot length of wrev
+constexpr int ADJ_SEG2 = 8, ADJ_SEG2_1D = 4;
+// doubles of the wrev slots of a grid, and of the parameter-gradient block partials of one
+// reverse stage (bounds; nn_blocks = blocks of the neural image reverse, 0 without it)
+long long adj_wrev_doubles(const Lay& lay);
+long long adj_ppart_doubles(const Lay& lay, int n_ghost, int n_src, long long nn_blocks);
+// blocks of the neural image-reverse kernel for a grid (one partial each)
+long long nn_image_vjp_blocks(const Lay& lay);
 
 // ---------------------------------------------------------------------------------------
 // neural flux (Sec. 2.3): three 3x3 convolution layers 4 -> 16 -> 32 -> 4 (ReLU, ReLU, tanh)
@@ -132,9 +154,10 @@ cudaError_t nn_eval_vjp(const NnArgs& n, const double* X, int H, int W, const do
 cudaError_t launch_block_average(const double* U, int nx, int ny, int fx, int fy, double* out, cudaStream_t s);
 
 // nn: the neural flux's reverse (run between pass 1 and pass 2) or nullptr
+// inflow_part: [4 sides][max(nx + 6, ny)][4] partial sums of the inflow halo adjoints
 cudaError_t launch_adj_stage(const AdjArgs& a, const BcArgs& bc, const IbArgs& ib, const IbTArgs& ibt, int wall,
                              const double* Unext, double* Uacc, double ra, double rb, double dt, bool rhs_mode,
-                             double* inflow_acc, const double* inflow_prim, double* qIb, cudaStream_t s,
+                             double* inflow_part, const double* inflow_prim, double* qIb, cudaStream_t s,
                              long long* launches, const NnArgs* nn = nullptr);
 cudaError_t launch_adj_unpack(const double* P, const double* P2, double* U, const Lay& lay, cudaStream_t s);
 
@@ -164,6 +187,19 @@ struct alignas(64) TensorMap128 {
 // box of the TMA-staged stage tile (32x32 cells + 3-cell halo, 4 planes)
 constexpr int TMA_TX = 32, TMA_TY = 32;
 
+// IEEE-order arithmetic mode (js_ieee.cu): padded primitives Q (4 planes of lay.plane),
+// x-face fluxes F [4][ny][nx+1], y-face fluxes G [4][ny+1][nx]
+struct IeeeBufs {
+  double* Q;
+  double* F;
+  double* G;
+};
+cudaError_t launch_ieee_ib_fill(double* U, const Lay& lay, const IbArgs& ib, double gamma, int wall, cudaStream_t s);
+// one stage (RHS mode: a.Uout = L(a.Uin) in [4][ny][nx]) from the filled padded input a.Uin
+cudaError_t launch_ieee_stage(const StageArgs& a, const IeeeBufs& b, double dt, int stage, bool rhs, double mu,
+                              double Pr, double nu, double dx, double dy, cudaStream_t s);
+// (a.dtc set: dt = a.dtc[5], and the stage does nothing when a.dtc[4] == 0)
+
 constexpr int STAGE_VARIANTS = 5;
 cudaError_t launch_stage(const StageArgs& a, bool visc, bool rhs, int variant, const TensorMap128* tmap,
                          cudaStream_t s);
@@ -183,6 +219,12 @@ cudaError_t launch_rows_unpack(double* U, int nx, int ny, int row0, int nrows, c
 // CFL reduction of U (user layout): red[0] = bits of the largest rate, red[1] = bits of the
 // smallest density over fluid cells (red: 3 words; bmax: CFL_MAX_BLOCKS doubles of scratch)
 constexpr int CFL_MAX_BLOCKS = 152 * 8;
+// the step size of the reduction in red on the device (js_max_dt's arithmetic; viscous cap when
+// mu > 0 with lim = max(4/3, gamma/Pr), hmin = min(dx, dy) in 2D), clipped to t_end with the
+// running time t (or t == nullptr), into the stage constants dtc[DTC_N] and dt_log[k]
+cudaError_t launch_cfl_dt(const unsigned long long* red, double cfl, double dx, double dy, double nu, double mu,
+                          double lim, double hmin, double* t, double t_end, double* dtc, double* dt_log, int k,
+                          int* err, cudaStream_t s);
 cudaError_t launch_cfl(const double* U, const Lay& lay, const unsigned char* tag, double gamma, double dx,
                        double dy, unsigned long long* red, double* bmax, cudaStream_t s);
 

@@ -988,11 +988,17 @@ __device__ __forceinline__ double nn_warp_sum(double v) {
 template <class T>
 __global__ void __launch_bounds__(256) nn_image_vjp_kernel(NnArgs n, AdjArgs a) {
   __shared__ T sx[4][IT][IT + 1];
-  __shared__ double red[8];
   const int d = blockIdx.z;
   const int H = n.H[d], Wd = n.W[d];
   const int f0 = blockIdx.x * IT, h0 = blockIdx.y * IT;
-  if (f0 >= Wd || h0 >= H) return;  // uniform per block
+  // per-warp partials of pbar[0] (gamma; the other three entries 0), summed with the other
+  // partials of the stage in a fixed order: warp w of block b writes pp[4 (8 b + w) + k]
+  const long long blk = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
+  const long long pw = 4 * (8 * blk + (threadIdx.x >> 5));
+  if (f0 >= Wd || h0 >= H) {  // uniform per block
+    if (a.pp && (threadIdx.x & 31) < 4) a.pp[pw + (threadIdx.x & 31)] = 0.0;
+    return;
+  }
   const long long pix = (long long)H * Wd;
   const T* dX = chan_img<T>(n.G4, 4, d, n.pix0);
   for (int e = threadIdx.x; e < 4 * IT * IT; e += 256) {
@@ -1026,15 +1032,9 @@ __global__ void __launch_bounds__(256) nn_image_vjp_kernel(NnArgs n, AdjArgs a) 
       for (int c = 0; c < 4; ++c) a.fadj[(long long)(fdir + 4 * sd + c) * a.splane + si] += b[c];
     }
   }
-  // one atomic per block: many blocks add to the same entry
   gbar = nn_warp_sum(gbar);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = gbar;
-  __syncthreads();
-  if (threadIdx.x == 0 && a.pbar) {
-    double t = 0.0;
-    for (int k = 0; k < 8; ++k) t += red[k];
-    if (t != 0.0) atomicAdd(a.pbar, t);
-  }
+  const int lane = threadIdx.x & 31;
+  if (a.pp && lane < 4) a.pp[pw + lane] = (lane == 0) ? gbar : 0.0;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1280,6 +1280,17 @@ cudaError_t nn_apply(const NnArgs& n, const StageArgs& a, bool rhs, cudaStream_t
   if (n.fp32) nn_apply_kernel<float><<<grid, 256, 0, s>>>(n, a, rhs ? 1 : 0);
   else nn_apply_kernel<double><<<grid, 256, 0, s>>>(n, a, rhs ? 1 : 0);
   return cudaGetLastError();
+}
+
+long long nn_image_vjp_blocks(const Lay& lay) {
+  NnArgs n;
+  n.nimg = lay.ny > 1 ? 2 : 1;
+  n.H[0] = lay.ny;
+  n.W[0] = lay.nx + 1;
+  n.H[1] = lay.nx;
+  n.W[1] = lay.ny + 1;
+  const dim3 g = image_grid(n);
+  return (long long)g.x * g.y * g.z;
 }
 
 cudaError_t nn_reverse(const NnArgs& n, const AdjArgs& a, cudaStream_t s) {

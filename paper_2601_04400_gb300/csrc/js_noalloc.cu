@@ -30,13 +30,16 @@ static_assert(JS_NOALLOC_MAX_CELLS % kCellsPerBlock == 0, "block size must divid
 static __device__ __align__(256) double g_cfl_scratch[2 * kMaxBlocks + 2];
 
 // rate = (|u| + a)/dx [+ (|v| + a)/dy] of one cell, IEEE-rounded in the same order as the
-// context-based reduction so that both entry points return the same dt.
+// context-based reduction so that both entry points return the same dt.  A non-physical cell
+// (rho or p not positive, or not finite) gets the rate +infinity, so the step size is 0 and
+// the call returns JS_ERR_NONPHYSICAL, as js_max_dt does.
 __device__ __forceinline__ double cell_rate(const double* U, long long n, long long t, double gamma, double dx,
                                             double dy, int two_d, double& r) {
   r = U[t];
   const double u = __ddiv_rn(U[n + t], r), v = __ddiv_rn(U[2 * n + t], r);
   const double ke = __dmul_rn(__dmul_rn(0.5, r), __dadd_rn(__dmul_rn(u, u), __dmul_rn(v, v)));
   const double p = __dmul_rn(gamma - 1.0, __dsub_rn(U[3 * n + t], ke));
+  if (!(r > 0.0) || !(r < INFINITY) || !(p > 0.0) || !(p < INFINITY)) return INFINITY;
   const double a = __dsqrt_rn(__ddiv_rn(__dmul_rn(gamma, p), r));
   double s = __ddiv_rn(__dadd_rn(fabs(u), a), dx);
   if (two_d) s = __dadd_rn(s, __ddiv_rn(__dadd_rn(fabs(v), a), dy));

@@ -196,3 +196,63 @@ def test_reverse_with_forward_stored_weno_internals(B, shape, viscous):
         # summation order of the atomics is the only difference
         assert np.abs(to_host(l) - ref).max() <= 1e-12 * np.abs(ref).max()
         assert np.abs(to_host(p) - pref).max() <= 1e-12 * max(np.abs(pref).max(), 1e-300)
+
+
+# ---------------------------------------------------------------------------------------
+# the reverse pass is deterministic: no floating-point atomics, every sum in a fixed order
+# ---------------------------------------------------------------------------------------
+def _det_cases():
+    out = []
+    p = W.adjoint_case(512)
+    out.append(("adjoint_case_512", p, W.random_state(p, seed=11, amp=0.02), None))
+    p = W.random_periodic(96, 64, seed=4, mu=3e-3, nu=2e-4)
+    out.append(("periodic_ns_av_96x64", p, p.W0, None))
+    p = W.mach5_cylinder(nx=218, ny=97)
+    out.append(("mach5_fallback_218x97", p, p.W0, None))  # positivity fallback faces
+    p = W.random_periodic(40, 33, seed=5).with_(bc=(3, 1, 0, 3), mu=1e-3, inflow=np.array(
+        [[1.1, 0.3, 0.1, 0.9], [1.0, 0.0, 0.0, 1.0], [1.0, 0.0, 0.0, 1.0], [1.2, -0.1, -0.2, 0.8]]))
+    out.append(("mixed_inflow_40x33", p, p.W0, None))
+    p = W.sod(200)
+    out.append(("sod200", p, p.W0, None))
+    p = W.shock_cylinder(nx=128, ny=64)
+    out.append(("cylinder_neural_128x64", p, W.random_state(p, seed=7, amp=0.02), "fp64"))
+    return out
+
+
+DET = _det_cases()
+
+
+@pytest.mark.parametrize("name,prob,Wp,nn", DET, ids=[c[0] for c in DET])
+def test_reverse_step_is_bitwise_reproducible(B, name, prob, Wp, nn):
+    """js_step_vjp twice (and the taped reverse twice) on the same inputs: lambda_n and p_bar
+    equal bit for bit."""
+    import torch
+    s = B.Solver.from_problem(prob)
+    U = to_dev(O.prim_to_cons(prob, Wp))
+    if nn:
+        from paper_2601_04400_gb300 import neural as NN
+        w = NN.init_weights(0, zero_last=False) * 0.5
+        wb = torch.zeros_like(w)
+        s.set_neural(w, NN.frame_norm(U, scale=0.1), w_bar=wb, precision=nn)
+    dt = 0.5 * s.max_dt(U, prob.cfl)
+    lam = to_dev(W.uniform_normal(U.shape, seed=3))
+    outs = []
+    for _ in range(2):
+        pb = torch.zeros(20, dtype=torch.float64, device="cuda")
+        ln, _ = s.step_vjp(U, dt, lam, p_bar=pb)
+        outs.append((to_host(ln), to_host(pb)))
+    assert s.status() == 0
+    assert outs[0][0].tobytes() == outs[1][0].tobytes()
+    assert outs[0][1].tobytes() == outs[1][1].tobytes()
+    assert np.abs(outs[0][1]).max() > 0
+    if not nn:
+        s.tape_reserve(1, weno=prob.ny > 1)
+        tap = []
+        for _ in range(2):
+            Ut = U.clone()
+            s.step_taped(Ut, dt, 0)
+            pb = torch.zeros(20, dtype=torch.float64, device="cuda")
+            ln, _ = s.step_vjp_taped(0, dt, lam, p_bar=pb)
+            tap.append((to_host(ln), to_host(pb)))
+        assert tap[0][0].tobytes() == tap[1][0].tobytes() and tap[0][1].tobytes() == tap[1][1].tobytes()
+    s.close()

@@ -1,13 +1,13 @@
 """js_max_dt_noalloc -- the CFL time step for callers that cannot allocate device memory
 (for example a host application that owns every device allocation through its own pool) --
-returns what the context-based js_max_dt returns.  Its scratch is a file-scope device array
+returns what the context-based js_max_dt returns, bit for bit, and rejects the same
+non-physical states.  Its scratch is a file-scope device array
 shared by all calls, so two calls in a row must not see each other's partial results.
 Collected last, so that a run stopping at the first failure has run every other test."""
 import numpy as np
 import pytest
 
 from paper_2601_04400_gb300 import workloads as W
-from jsutil import TOL
 
 pytestmark = pytest.mark.gpu
 
@@ -43,7 +43,7 @@ def test_noalloc_cfl_matches_js_max_dt_on_consecutive_calls():
         for U in states:
             ref = s.max_dt(U, prob.cfl)
             dt = B.js_max_dt_noalloc(g, p, U, tag_dev, prob.cfl)
-            assert abs(dt - ref) <= TOL * ref
+            assert dt == ref
             got.append(dt)
         assert got[0] != got[1]  # the two calls reduced different states
         s.close()
@@ -57,3 +57,23 @@ def test_noalloc_cfl_rejects_grids_beyond_the_static_scratch():
     with pytest.raises(B.JsError) as e:
         B.js_max_dt_noalloc(g, p, U, None, 0.5)
     assert e.value.code == B.JS_ERR_ARG
+
+
+def test_noalloc_cfl_rejects_non_physical_states_like_js_max_dt():
+    torch, B = _setup()
+    prob = W.shock_cylinder(nx=256, ny=128)
+    s, (U1, _), tag_dev, g, p = _case(torch, B, prob, 3)
+    n, tag = s.ib_info()
+    j, i = np.argwhere(tag == 0)[1234]
+    for bad in (-0.25, float("nan")):
+        U = U1.clone()
+        U[0, j, i] = bad
+        codes = []
+        for call in (lambda: s.max_dt(U, prob.cfl), lambda: B.js_max_dt_noalloc(g, p, U, tag_dev, prob.cfl)):
+            with pytest.raises(B.JsError) as e:
+                call()
+            codes.append(e.value.code)
+        assert codes == [B.JS_ERR_NONPHYSICAL] * 2
+    # after the rejected calls the shared scratch still gives the right answer
+    assert B.js_max_dt_noalloc(g, p, U1, tag_dev, prob.cfl) == s.max_dt(U1, prob.cfl)
+    s.close()
