@@ -427,6 +427,8 @@ def run_batched(args):
         s.close()
     cells = sum(p.cells for p in mine)
     batch = B.Batch(mine, stream=stream)
+    from paper_2601_04400_gb300 import tuning
+    tuned = tuning.autotune_batch(batch, mine, states)  # blocks per SM and schedule (identical results)
     work = [U.clone() for U in states]
     batch.set_states(work)
     batch.step(0.5, args.warmup)
@@ -468,22 +470,42 @@ def run_batched(args):
         dist.all_reduce(tt[:2], op=dist.ReduceOp.MAX)
         dist.all_reduce(tt[2:], op=dist.ReduceOp.SUM)
         t_batch, t_e2e, cells = float(tt[0]), float(tt[1]), int(tt[2])
-    # one at a time: each instance its own context, js_max_dt + js_step per step
+    # one at a time: each instance its own context and its own device CFL steps (js_step_cfl:
+    # no host round trip), instance after instance; and the same launches captured into one
+    # CUDA graph per step of all instances, replayed
     solvers = [B.Solver.from_problem(p, stream=stream) for p in mine]
     seq = [U.clone() for U in states]
     for s, U in zip(solvers, seq):
-        for _ in range(args.warmup):
-            s.step(U, s.max_dt(U, 0.5), 1)
+        s.step_cfl(U, 0.5, args.warmup)
     torch.cuda.synchronize()
     e0.record(stream)
     for s, U in zip(solvers, seq):
-        for _ in range(args.steps):
-            s.step(U, s.max_dt(U, 0.5), 1)
+        s.step_cfl(U, 0.5, args.steps)
     e1.record(stream)
     e1.synchronize()
     t_seq = e0.elapsed_time(e1)
-    # reverse of one batched step (js_batch_step_vjp: every instance's js_step_vjp, spread
-    # over a few streams) against one batched forward step
+    gseq = [U.clone() for U in states]
+    side = torch.cuda.Stream()  # a capture needs a stream of its own
+    torch.cuda.synchronize()
+    for s in solvers:
+        s.set_stream(side)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(graph, stream=side):
+            for s, U in zip(solvers, gseq):
+                s.step_cfl(U, 0.5, 1)
+        torch.cuda.synchronize()
+        e0.record(side)
+        for _ in range(args.steps):
+            graph.replay()
+        e1.record(side)
+        e1.synchronize()
+    t_graph = e0.elapsed_time(e1)
+    for s in solvers:
+        s.set_stream(stream)
+    ok = ok and all(s.status() == 0 for s in solvers)
+    # reverse of one batched step (js_batch_step_vjp: one persistent launch over all
+    # instances) against one batched forward step
     dts = [s.max_dt(U, 0.5) for s, U in zip(solvers, states)]
     lams = [torch.randn_like(U) for U in states]
     outs = [torch.empty_like(U) for U in states]
@@ -497,6 +519,37 @@ def run_batched(args):
     e1.synchronize()
     t_vjp = e0.elapsed_time(e1) / reps
     ok = ok and batch.status() == 0
+    # the whole rollout: n_ro CFL steps forward (one launch, step sizes logged), then its
+    # reverse with sqrt(N) checkpoints (js_batch_rollout_vjp); the first reverse call
+    # allocates its workspace and is not timed
+    n_ro = args.rollout_steps
+    roll = None
+    if n_ro > 0:
+        fwd = [U.clone() for U in states]
+        batch.set_states(fwd)
+        log = torch.zeros((n_ro, len(mine)), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        e0.record(stream)
+        batch.step(0.5, n_ro, dt_log=log)
+        e1.record(stream)
+        e1.synchronize()
+        t_ro_f = e0.elapsed_time(e1)
+        batch.set_states([U.clone() for U in states])
+        lam_r = [torch.randn_like(U) for U in states]
+        batch.rollout_vjp(log, lam_r)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        batch.rollout_vjp(log, lam_r)
+        e1.record(stream)
+        e1.synchronize()
+        t_ro_b = e0.elapsed_time(e1)
+        ok = ok and batch.status() == 0
+        ck = int(round(n_ro ** 0.5))
+        roll = {"steps": n_ro, "checkpoint_every": ck, "ms_forward": t_ro_f, "ms_reverse": t_ro_b,
+                "ratio": t_ro_b / t_ro_f,
+                "note": "js_batch_rollout_vjp (forward to the checkpoints, then per segment: re-run "
+                        "keeping its states + one persistent reverse launch per step) / the batched "
+                        "forward run of the same steps (one launch, device CFL)"}
     info = batch.info()
     if rank == 0:
         print(json.dumps({
@@ -506,7 +559,9 @@ def run_batched(args):
             "data": "synthetic", "status_ok": ok,
             "config": {"workload": "%d viscous shock-cylinder instances (seed 0: Mach U[1.5,3], radius U[0.3,0.7], "
                                    "nx 128..512, ny 128..256), per-instance device CFL 0.5" % len(mine),
-                       "cells": cells, "persistent_blocks": info["blocks"], "tiles": info["tiles"]},
+                       "cells": cells, "persistent_blocks": info["blocks"], "tiles": info["tiles"],
+                       "tuning": {"blocks_per_sm": batch.tuning()[0], "schedule": batch.tuning()[2],
+                                  "timed": {"%d,%d" % k: v for k, v in tuned.items()}}},
             "e2e": {"value": cells * args.steps / (t_e2e * 1e-3), "unit": "cell-updates/s",
                     "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes},
             "roofline": {"bound": "alu", "kernel": "batch_kernel (persistent: CFL, IB and halo fills, stage tiles)",
@@ -518,12 +573,19 @@ def run_batched(args):
                          "traffic": None, "flops_per_cell_stage": FLOPS_PER_CELL_STAGE["shock_cylinder"]},
             "gpu_launches": 1, "clocks": sampler.summary(),
             "one_at_a_time": {"value": local_cells * args.steps / (t_seq * 1e-3), "ms_per_step": t_seq / args.steps,
-                              "how": "rank 0's instances, each: js_max_dt (synchronising) + js_step, one step "
-                                     "at a time"},
+                              "how": "rank 0's instances one after another, each js_step_cfl for all steps "
+                                     "(device CFL, no host round trip)"},
+            "one_at_a_time_graph": {"value": local_cells * args.steps / (t_graph * 1e-3),
+                                    "ms_per_step": t_graph / args.steps,
+                                    "how": "one CUDA graph holding one js_step_cfl step of every instance, "
+                                           "replayed once per step"},
             "speedup_vs_one_at_a_time": t_seq / t_batch,
+            "speedup_vs_graph": t_graph / t_batch,
             "adjoint": {"ms_per_step_vjp": t_vjp, "ratio": t_vjp / (t_batch / args.steps),
-                        "note": "js_batch_step_vjp (each instance's js_step_vjp, recomputing its stage "
-                                "states) / one batched forward step, rank 0's instances"}}), flush=True)
+                        "note": "js_batch_step_vjp (one persistent launch: recompute of the stage states "
+                                "and the reverse of the 3 stages of every instance) / one batched forward "
+                                "step, rank 0's instances"},
+            "rollout": roll}), flush=True)
     if dist is not None:
         dist.destroy_process_group()
 
@@ -627,6 +689,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="shock_cylinder", choices=["riemann2d", "shock_cylinder", "mach5_cylinder", "batched"])
     ap.add_argument("--instances", type=int, default=256)
+    ap.add_argument("--rollout-steps", type=int, default=60,
+                    help="batched workload: steps of the rollout whose checkpointed reverse is timed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--neural", action="store_true", help="also time steps with the neural flux")

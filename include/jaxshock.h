@@ -306,15 +306,41 @@ int js_batch_set_states(js_batch* b, double* const* U);
  * into a CUDA graph. */
 int js_batch_step(js_batch* b, double cfl, int n_steps, double* t_dev, double* dt_log);
 
-/* Reverse of one batched step (the gradient chain rule of Sec. 2 per instance): for every
- * instance k, lam_n[k] = (dU_{n+1}/dU_n)^T lam_np1[k] for the step of size dt[k] taken from
- * U_n[k], and p_bar[k] += (dU_{n+1}/dtheta_k)^T lam_np1[k] (JS_NPARAM doubles each; p_bar or
- * an entry may be NULL).  dt: host array of `count` step sizes (e.g. a row of the dt log,
- * which treats each CFL step size as fixed).  U_n, lam_np1, lam_n, p_bar: host arrays of
- * device pointers.  Enqueued on the batch's stream; the first call allocates each instance's
- * adjoint workspace. */
+/* Reverse of one batched step (the gradient chain rule of Sec. 2 per instance) in ONE
+ * persistent cooperative launch over all instances: for every instance k,
+ * lam_n[k] = (dU_{n+1}/dU_n)^T lam_np1[k] for the step of size dt[k] taken from U_n[k]
+ * (the same values as js_step_vjp, bit for bit), and p_bar[k] += (dU_{n+1}/dtheta_k)^T
+ * lam_np1[k] (JS_NPARAM doubles each, summed in a fixed order; p_bar or an entry may be NULL).
+ * dt: host array of `count` step sizes (e.g. a row of the dt log, which treats each CFL step
+ * size as fixed).  U_n, lam_np1, lam_n, p_bar: host arrays of device pointers; lam_n[k] may
+ * alias lam_np1[k].  The first call allocates each instance's reverse workspace; every call
+ * copies its pointer table to the device and synchronises the stream before returning (use
+ * js_batch_rollout_vjp inside a stream capture). */
 int js_batch_step_vjp(js_batch* b, double* const* U_n, const double* dt, double* const* lam_np1,
                       double* const* lam_n, double* const* p_bar);
+
+/* Advance every registered state n_steps SSP-RK3 steps of the given sizes dt[step][count]
+ * (device) instead of CFL step sizes, e.g. to replay a run logged by js_batch_step.  One launch;
+ * asynchronous; allocates nothing. */
+int js_batch_step_fixed(js_batch* b, int n_steps, const double* dt);
+
+/* Reverse of a batched rollout of n_steps steps (the chain rule of Sec. 2 through the whole
+ * run): the instances start from the registered states (js_batch_set_states; left unchanged)
+ * and take the step sizes dt_log[step][count] (device; e.g. logged by js_batch_step, each CFL
+ * step size treated as fixed).
+ *   lam   : host array of `count` device pointers; in: dL/dU_{n_steps}, out: dL/dU_0
+ *   p_bar : host array of device pointers (JS_NPARAM doubles each, accumulated) or NULL
+ *   ckpt  : checkpoint spacing (<= 0: the integer nearest sqrt(n_steps)): the forward keeps the
+ *           state after every ckpt-th step; then, from the last segment back, each segment is
+ *           re-run keeping its states and reversed step by step by the persistent reverse
+ *           launch of js_batch_step_vjp.
+ * Workspace: ceil(n_steps/ckpt) + ckpt + 1 states per instance and the reverse workspace,
+ * allocated by the first call for these n_steps and ckpt (synchronises; make it before any
+ * stream capture).  Later calls with the same n_steps, ckpt, lam and p_bar pointers enqueue
+ * only kernels (one launch per copy, segment re-run and reverse step) and can be captured into
+ * a CUDA graph.  Asynchronous otherwise. */
+int js_batch_rollout_vjp(js_batch* b, int n_steps, const double* dt_log, int ckpt, double* const* lam,
+                         double* const* p_bar);
 
 /* Read and clear the batch's device error flag (synchronises): JS_OK, JS_ERR_NONPHYSICAL,
  * JS_ERR_TIMEOUT. */
@@ -322,6 +348,17 @@ int js_batch_sync_status(js_batch* b);
 
 /* Launch shape and size: resident blocks of the persistent kernel, 32x16 tiles, cells. */
 int js_batch_info(js_batch* b, int* blocks, int* tiles, long long* cells);
+
+/* Launch shape and schedule of the forward launch (js_batch_step, js_batch_step_fixed and the
+ * rollout's forward runs): blocks_per_sm resident blocks on every SM (0 = the most that fit),
+ * and the order in which the blocks take the tiles of all instances: 0 instance by instance,
+ * 1 interleaved (tile j of every instance, then tile j + 1), 2 the largest instances first.
+ * Results are identical for every choice; only speed differs (the Python autotuner times them
+ * and caches the choice per mix of instances).  Schedules 1 and 2 upload a tile table
+ * (synchronises: before any stream capture).  js_batch_get_tuning reports the current choice,
+ * the most blocks per SM and the number of schedules. */
+int js_batch_set_tuning(js_batch* b, int blocks_per_sm, int schedule);
+int js_batch_get_tuning(js_batch* b, int* blocks_per_sm, int* max_blocks_per_sm, int* schedule, int* n_schedules);
 
 /* The context of instance k (owned by the batch; do not destroy it), e.g. for js_step_vjp. */
 js_ctx* js_batch_instance(js_batch* b, int k);

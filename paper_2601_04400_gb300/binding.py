@@ -91,6 +91,10 @@ SIGNATURES = {
     "js_batch_set_states": (_I, [_P, C.POINTER(_P)]),
     "js_batch_step": (_I, [_P, _D, _I, _P, _P]),
     "js_batch_step_vjp": (_I, [_P, C.POINTER(_P), C.POINTER(_D), C.POINTER(_P), C.POINTER(_P), C.POINTER(_P)]),
+    "js_batch_step_fixed": (_I, [_P, _I, _P]),
+    "js_batch_set_tuning": (_I, [_P, _I, _I]),
+    "js_batch_get_tuning": (_I, [_P, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
+    "js_batch_rollout_vjp": (_I, [_P, _I, _P, _I, C.POINTER(_P), C.POINTER(_P)]),
     "js_batch_sync_status": (_I, [_P]),
     "js_batch_info": (_I, [_P, C.POINTER(_I), C.POINTER(_I), C.POINTER(C.c_longlong)]),
     "js_batch_instance": (_P, [_P, _I]),
@@ -534,6 +538,31 @@ class Batch:
         dt = (C.c_double * n)(*[float(x) for x in dts])
         pb = arr(p_bar) if p_bar is not None else None
         _check(lib().js_batch_step_vjp(self.handle, arr(U_n), dt, arr(lam_np1), arr(lam_n), pb), "js_batch_step_vjp")
+
+    def set_tuning(self, blocks_per_sm=0, schedule=0):
+        _check(lib().js_batch_set_tuning(self.handle, int(blocks_per_sm), int(schedule)), "js_batch_set_tuning")
+
+    def tuning(self):
+        """(blocks per SM, most blocks per SM, schedule, number of schedules)"""
+        v = [C.c_int(0) for _ in range(4)]
+        _check(lib().js_batch_get_tuning(self.handle, *[C.byref(x) for x in v]), "js_batch_get_tuning")
+        return tuple(x.value for x in v)
+
+    def step_fixed(self, dts):
+        """Advance every registered state len(dts) steps of the given sizes: dts float64 CUDA
+        tensor [n_steps, count]."""
+        _check(lib().js_batch_step_fixed(self.handle, int(dts.shape[0]), _ptr(dts)), "js_batch_step_fixed")
+
+    def rollout_vjp(self, dt_log, lam, p_bar=None, ckpt=0):
+        """Reverse of the rollout from the registered states with the step sizes dt_log
+        (float64 CUDA tensor [n_steps, count]); lam: per-instance tensors, dL/dU_N in, dL/dU_0
+        out; p_bar: per-instance JS_NPARAM tensors (accumulated) or None; ckpt: checkpoint
+        spacing (0: about sqrt(n_steps))."""
+        n = self.count
+        arr = lambda ts: (C.c_void_p * n)(*[_ptr(t).value for t in ts])
+        pb = arr(p_bar) if p_bar is not None else None
+        _check(lib().js_batch_rollout_vjp(self.handle, int(dt_log.shape[0]), _ptr(dt_log), int(ckpt), arr(lam), pb),
+               "js_batch_rollout_vjp")
 
     def status(self):
         return lib().js_batch_sync_status(self.handle)

@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "jaxshock.h"
+#include "js_adjoint_body.cuh"
 #include "js_fill.cuh"
 #include "js_internal.h"
 #include "js_stage.cuh"
@@ -50,6 +51,10 @@ struct BatchArgs {
   int n_steps;
   int extra_arrivals;         // > 0 only to exercise the barrier timeout
   long long budget;           // barrier wait budget in clock cycles
+  const double* dt_in;        // [n_steps][count] given step sizes (no CFL reduction), or nullptr
+  double* const* ustate;      // [count] states advanced instead of the registered ones, or nullptr
+  double* const* save;        // [n_steps][count] states after each step, or nullptr
+  const int* order;           // schedule: queue position -> tile number (ntiles), or nullptr
 };
 
 // ---------------------------------------------------------------------------------------
@@ -71,26 +76,26 @@ __device__ __forceinline__ int find_inst64(const long long* pre, int count, long
 }
 
 // grid barrier with a bounded wait; returns false when the launch must stop
-__device__ bool grid_sync(const BatchArgs& b) {
+__device__ bool grid_sync_on(unsigned* bar, int* err, int extra_arrivals, long long budget) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    volatile unsigned* vgen = b.bar + 1;
+    volatile unsigned* vgen = bar + 1;
     const unsigned g = *vgen;
     __threadfence();
-    const unsigned target = gridDim.x + (unsigned)b.extra_arrivals;
-    const unsigned arrived = atomicAdd(b.bar, 1u) + 1u;
+    const unsigned target = gridDim.x + (unsigned)extra_arrivals;
+    const unsigned arrived = atomicAdd(bar, 1u) + 1u;
     if (arrived == target) {
-      b.bar[0] = 0u;
+      bar[0] = 0u;
       __threadfence();
-      atomicAdd(b.bar + 1, 1u);
+      atomicAdd(bar + 1, 1u);
     } else {
       const long long t0 = clock64();
       while (*vgen == g) {
-        if (*(volatile int*)b.err & ERR_TIMEOUT_BIT) { ok = 0; break; }
-        if (clock64() - t0 > b.budget) {
-          atomicOr(b.err, ERR_TIMEOUT_BIT);
+        if (*(volatile int*)err & ERR_TIMEOUT_BIT) { ok = 0; break; }
+        if (clock64() - t0 > budget) {
+          atomicOr(err, ERR_TIMEOUT_BIT);
           ok = 0;
           break;
         }
@@ -102,6 +107,9 @@ __device__ bool grid_sync(const BatchArgs& b) {
   }
   __syncthreads();
   return s_ok != 0;
+}
+__device__ __forceinline__ bool grid_sync(const BatchArgs& b) {
+  return grid_sync_on(b.bar, b.err, b.extra_arrivals, b.budget);
 }
 
 __device__ __forceinline__ double inst_dt(const InstDesc& d, const unsigned long long* red, double cfl) {
@@ -123,9 +131,11 @@ __global__ void __launch_bounds__(BNT) batch_kernel(BatchArgs b) {
   const int tid = threadIdx.x, lane = threadIdx.x & 31;
   // ---- pack user states; reset both reduction buffers
   for (int it = blockIdx.x; it < ntiles; it += gridDim.x) {
-    const int k = find_inst(b.tile0, b.count, it);
+    const int q = b.order ? b.order[it] : it;
+    const int k = find_inst(b.tile0, b.count, q);
     const InstDesc& d = b.inst[k];
-    const int t = it - b.tile0[k];
+    const double* Uk = b.ustate ? b.ustate[k] : d.U;
+    const int t = q - b.tile0[k];
     const int i0 = (t % d.ntx) * BTX, j0 = (t / d.ntx) * BTY;
     const long long n = (long long)d.lay.nx * d.lay.ny;
     for (int e = tid; e < BTX * BTY; e += BNT) {
@@ -133,7 +143,7 @@ __global__ void __launch_bounds__(BNT) batch_kernel(BatchArgs b) {
       if (i >= d.lay.nx || j >= d.lay.ny) continue;
       const long long o = (long long)j * d.lay.nx + i, p = d.lay.idx(i, j);
 #pragma unroll
-      for (int c = 0; c < 4; ++c) d.N[c * d.lay.plane + p] = d.U[c * n + o];
+      for (int c = 0; c < 4; ++c) d.N[c * d.lay.plane + p] = Uk[c * n + o];
     }
   }
   if (blockIdx.x == 0)
@@ -145,11 +155,12 @@ __global__ void __launch_bounds__(BNT) batch_kernel(BatchArgs b) {
   for (int step = 0; step < b.n_steps; ++step) {
     const int par = step & 1;
     unsigned long long* red = b.red + 2 * (long long)b.count * par;
-    // ---- CFL reduction over fluid cells, per instance
-    for (int it = blockIdx.x; it < ntiles; it += gridDim.x) {
-      const int k = find_inst(b.tile0, b.count, it);
+    // ---- CFL reduction over fluid cells, per instance (skipped with given step sizes)
+    for (int it = blockIdx.x; it < (b.dt_in ? 0 : ntiles); it += gridDim.x) {
+      const int q = b.order ? b.order[it] : it;
+    const int k = find_inst(b.tile0, b.count, q);
       const InstDesc& d = b.inst[k];
-      const int t = it - b.tile0[k];
+      const int t = q - b.tile0[k];
       const int i0 = (t % d.ntx) * BTX, j0 = (t / d.ntx) * BTY;
       double rate = 0.0, rmin = __longlong_as_double(0x7ff0000000000000LL);
       for (int e = tid; e < BTX * BTY; e += BNT) {
@@ -171,14 +182,14 @@ __global__ void __launch_bounds__(BNT) batch_kernel(BatchArgs b) {
         atomicMin(red + 2 * k + 1, (unsigned long long)__double_as_longlong(rmin));
       }
     }
-    if (!grid_sync(b)) return;
+    if (!b.dt_in && !grid_sync(b)) return;
     if (blockIdx.x == 0) {
       // the other parity was last read in the previous step: reset it for the next one
       unsigned long long* nxt = b.red + 2 * (long long)b.count * (par ^ 1);
       for (int k = tid; k < b.count; k += BNT) {
         nxt[2 * k] = 0ULL;
         nxt[2 * k + 1] = 0x7ff0000000000000ULL;
-        const double dtk = inst_dt(b.inst[k], red + 2 * k, b.cfl);
+        const double dtk = b.dt_in ? b.dt_in[(long long)step * b.count + k] : inst_dt(b.inst[k], red + 2 * k, b.cfl);
         // a non-physical fluid cell has an infinite rate (cfl_rate): dt = 0
         if (!(dtk > 0.0) || !(dtk < CUDART_INF)) atomicOr(b.err, ERR_NONPHYSICAL_BIT);
         if (b.t) b.t[k] += dtk;
@@ -204,10 +215,11 @@ __global__ void __launch_bounds__(BNT) batch_kernel(BatchArgs b) {
       if (!grid_sync(b)) return;
       // ---- stage tiles
       for (int it = blockIdx.x; it < ntiles; it += gridDim.x) {
-        const int k = find_inst(b.tile0, b.count, it);
+        const int q = b.order ? b.order[it] : it;
+    const int k = find_inst(b.tile0, b.count, q);
         const InstDesc& d = b.inst[k];
-        const int t = it - b.tile0[k];
-        const double dt = inst_dt(d, red + 2 * k, b.cfl);
+        const int t = q - b.tile0[k];
+        const double dt = b.dt_in ? b.dt_in[(long long)step * b.count + k] : inst_dt(d, red + 2 * k, b.cfl);
         StageArgs a;
         a.Uin = (s == 0) ? d.N : ((s == 1) ? d.A : d.B);
         a.Un = d.N;
@@ -237,12 +249,34 @@ __global__ void __launch_bounds__(BNT) batch_kernel(BatchArgs b) {
       }
       if (!grid_sync(b)) return;
     }
+    if (b.save) {
+      // the state after this step (ghost cells included), before the next step refills them
+      for (int it = blockIdx.x; it < ntiles; it += gridDim.x) {
+        const int q = b.order ? b.order[it] : it;
+    const int k = find_inst(b.tile0, b.count, q);
+        const InstDesc& d = b.inst[k];
+        double* S = b.save[(long long)step * b.count + k];
+        const int t = q - b.tile0[k];
+        const int i0 = (t % d.ntx) * BTX, j0 = (t / d.ntx) * BTY;
+        const long long n = (long long)d.lay.nx * d.lay.ny;
+        for (int e = tid; e < BTX * BTY; e += BNT) {
+          const int i = i0 + (e % BTX), j = j0 + (e / BTX);
+          if (i >= d.lay.nx || j >= d.lay.ny) continue;
+          const long long o = (long long)j * d.lay.nx + i, p = d.lay.idx(i, j);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) S[c * n + o] = d.N[c * d.lay.plane + p];
+        }
+      }
+      if (!grid_sync(b)) return;
+    }
   }
   // ---- unpack
   for (int it = blockIdx.x; it < ntiles; it += gridDim.x) {
-    const int k = find_inst(b.tile0, b.count, it);
+    const int q = b.order ? b.order[it] : it;
+    const int k = find_inst(b.tile0, b.count, q);
     const InstDesc& d = b.inst[k];
-    const int t = it - b.tile0[k];
+    double* Uk = b.ustate ? b.ustate[k] : d.U;
+    const int t = q - b.tile0[k];
     const int i0 = (t % d.ntx) * BTX, j0 = (t / d.ntx) * BTY;
     const long long n = (long long)d.lay.nx * d.lay.ny;
     for (int e = tid; e < BTX * BTY; e += BNT) {
@@ -250,8 +284,302 @@ __global__ void __launch_bounds__(BNT) batch_kernel(BatchArgs b) {
       if (i >= d.lay.nx || j >= d.lay.ny) continue;
       const long long o = (long long)j * d.lay.nx + i, p = d.lay.idx(i, j);
 #pragma unroll
-      for (int c = 0; c < 4; ++c) d.U[c * n + o] = d.N[c * d.lay.plane + p];
+      for (int c = 0; c < 4; ++c) Uk[c * n + o] = d.N[c * d.lay.plane + p];
     }
+  }
+}
+
+// =======================================================================================
+// persistent batched reverse: one launch reverses one SSP-RK3 step of every instance (the
+// gradient chain rule of Sec. 2 per instance) -- the per-grid js_step_vjp's phases, each run
+// over the work items of all instances, separated by grid barriers:
+//   pack U_n, lambda_{n+1}; zero Uacc
+//   forward recompute, stages 0 and 1: IB fill | halo fill | stage tiles (storing their WENO5
+//   internals); IB and halo fill of the stage-2 input
+//   reverse, stages 2, 1, 0: seed + primitives (+ the previous stage's parameter-gradient
+//   reduction) | pass 1 | pass 2 | primitive reverse | transposed y halos | transposed x halos |
+//   inflow gradient + transposed IB ghosts | transposed IB sources
+//   unpack lambda_n (+ the last reduction)
+// The device bodies are those of the per-grid launches (js_adjoint_body.cuh, js_stage.cuh,
+// js_fill.cuh) on the same elements in the same order, so lambda_n equals js_step_vjp's bit for
+// bit; the parameter gradient is reduced in a fixed order too (its partial sums are grouped
+// by 128-thread blocks here, so it agrees with js_step_vjp's to rounding).
+// Work items of every instance are padded to whole warps, so a warp never spans two instances.
+// =======================================================================================
+enum RevKind { RK_PLANE = 0, RK_USER4, RK_GHOST, RK_HALO, RK_P1RE, RK_P1SV, RK_P2, RK_BCTY, RK_BCTX, RK_SRC, RK_N };
+
+struct RevCall {
+  const double* const* Un;    // [count] user states U_n
+  const double* const* lam1;  // [count] lambda_{n+1}
+  double* const* lam0;        // [count] lambda_n (may alias lam1)
+  double* const* pbar;        // [count] parameter gradients (entries may be null) or null
+  const double* dt;           // [count] step sizes
+};
+
+struct BatchRevArgs {
+  const InstDesc* inst;
+  const InstRev* rev;
+  int count;
+  const long long* pre;       // [RK_N][count + 1] prefix sums of the padded item counts
+  const int* tile0;
+  RevCall call;
+  unsigned* bar;
+  int* err;
+  long long budget;
+};
+
+// every item g of kind K over all instances: f(k, local) with k = -1 past the end (whole
+// warps, so warp-collective bodies see all 32 lanes)
+template <class F>
+__device__ __forceinline__ void rev_items(const BatchRevArgs& b, int kind, F f) {
+  const long long* pre = b.pre + (long long)kind * (b.count + 1);
+  const long long total = pre[b.count];
+  for (long long base = (long long)blockIdx.x * BNT; base < total; base += (long long)gridDim.x * BNT) {
+    const long long g = base + threadIdx.x;
+    int k = -1;
+    long long local = 0;
+    if (g < total) {
+      k = find_inst64(pre, b.count, g);
+      local = g - pre[k];
+    }
+    f(k, local);
+  }
+}
+
+__device__ __forceinline__ AdjArgs rev_adj(const InstRev& r, const InstDesc& d, int s, const RevCall& call, int k,
+                                           double* dst, bool with_pbar) {
+  AdjArgs a = r.a;
+  a.X = (s == 0) ? d.N : ((s == 1) ? d.A : d.B);
+  a.Ub = dst;
+  a.pbar = with_pbar && call.pbar ? call.pbar[k] : nullptr;
+  a.pp = a.pbar ? r.ppart : nullptr;
+  if (s < 2) {
+    a.wsave = r.wfwd + (long long)56 * s * r.a.splane;
+    a.weno_saved = 1;
+  } else {
+    a.wsave = r.wsave_own;
+    a.weno_saved = 0;
+  }
+  return a;
+}
+
+// the parameter-gradient slot ranges of reverse stage s of one instance, summed into its pbar
+__device__ __forceinline__ void rev_reduce(const InstRev& r, int s, double* pbar) {
+  const long long off[4] = {0, r.off_prim, r.off_g, r.off_s};
+  const long long cnt[4] = {s < 2 ? r.w1_sv : r.w1_re, r.w_prim, r.w_g, r.w_s};
+  adj_pbar_reduce_block(r.ppart, off, cnt, 4, pbar);
+}
+
+__global__ void __launch_bounds__(BNT) batch_vjp_kernel(BatchRevArgs b) {
+  extern __shared__ double smem[];
+  const RevCall& call = b.call;
+  // ---- pack U_n -> N and lambda_{n+1} -> P0; Uacc = 0
+  rev_items(b, RK_USER4, [&](int k, long long t) {
+    if (k < 0) return;
+    const InstDesc& d = b.inst[k];
+    const long long n = (long long)d.lay.nx * d.lay.ny;
+    if (t >= 4 * n) return;
+    const int c = (int)(t / n);
+    const long long o = t % n;
+    const long long p = c * d.lay.plane + d.lay.idx((int)(o % d.lay.nx), (int)(o / d.lay.nx));
+    d.N[p] = call.Un[k][t];
+    b.rev[k].P0[p] = call.lam1[k][t];
+  });
+  rev_items(b, RK_PLANE, [&](int k, long long t) {
+    if (k < 0 || t >= b.inst[k].lay.plane) return;
+    const InstDesc& d = b.inst[k];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) b.rev[k].Uacc[c * d.lay.plane + t] = 0.0;
+  });
+  if (!grid_sync_on(b.bar, b.err, 0, b.budget)) return;
+  // ---- forward recompute of the stage inputs X0 = N, X1 = A, X2 = B
+  for (int s = 0; s < 3; ++s) {
+    rev_items(b, RK_GHOST, [&](int k, long long g) {
+      if (k < 0) return;
+      const InstDesc& d = b.inst[k];
+      if (g >= d.ib.n) return;
+      double* X = (s == 0) ? d.N : ((s == 1) ? d.A : d.B);
+      ib_fill_one(X, d.lay, d.ib, d.gamma, d.wall, (int)g);
+    });
+    if (!grid_sync_on(b.bar, b.err, 0, b.budget)) return;
+    rev_items(b, RK_HALO, [&](int k, long long h) {
+      if (k < 0) return;
+      const InstDesc& d = b.inst[k];
+      if (h >= halo_count(d.lay)) return;
+      double* X = (s == 0) ? d.N : ((s == 1) ? d.A : d.B);
+      bc_fill_one(X, d.lay, d.bc, h);
+    });
+    if (!grid_sync_on(b.bar, b.err, 0, b.budget)) return;
+    if (s == 2) break;
+    for (int it = blockIdx.x; it < b.tile0[b.count]; it += gridDim.x) {
+      const int k = find_inst(b.tile0, b.count, it);
+      const InstDesc& d = b.inst[k];
+      const InstRev& r = b.rev[k];
+      const int t = it - b.tile0[k];
+      const double dt = call.dt[k];
+      StageArgs a;
+      a.Uin = (s == 0) ? d.N : d.A;
+      a.Un = d.N;
+      a.Uout = (s == 0) ? d.A : d.B;
+      a.tag = d.tag;
+      a.acc = d.acc;
+      a.acc2 = d.acc2;
+      a.err = b.err;
+      a.lay = d.lay;
+      a.gamma = d.gamma;
+      a.gm1 = d.gamma - 1.0;
+      a.g1 = 1.0 / (d.gamma - 1.0);
+      a.cx = dt / d.dx;
+      a.cy = dt / d.dy;
+      a.rk_a = (s == 0) ? 0.0 : 0.75;
+      a.rk_b = (s == 0) ? 1.0 : 0.25;
+      a.avx = dt * d.nu / (d.dx * d.dx);
+      a.avy = dt * d.nu / (d.dy * d.dy);
+      a.vx = d.vx;
+      a.vy = d.vy;
+      a.use_un = (s > 0) ? 1 : 0;
+      a.has_av = d.has_av;
+      a.wsave = r.wfwd + (long long)56 * s * r.a.splane;
+      a.splane = r.a.splane;
+      a.tpitch = r.a.tpitch;
+      a.dtc = nullptr;
+      if (d.visc) stage_tile_c<BTX, BTY, BLX, BLY, true, false, false, true>(a, t % d.ntx, t / d.ntx, smem);
+      else stage_tile_c<BTX, BTY, BLX, BLY, false, false, false, true>(a, t % d.ntx, t / d.ntx, smem);
+      __syncthreads();  // the next tile reuses shared memory
+    }
+    if (!grid_sync_on(b.bar, b.err, 0, b.budget)) return;
+  }
+  // ---- reverse through the stages 2, 1, 0: P0 -> P1 -> P0 -> P1
+  const double ra[3] = {0.0, 0.75, 1.0 / 3.0};
+  const double rb[3] = {1.0, 0.25, 2.0 / 3.0};
+  for (int s = 2; s >= 0; --s) {
+    const bool even = (s == 2) || (s == 0);  // src = P0 for stages 2 and 0
+    // seed + primitives; the parameter-gradient partials of stage s+1 are reduced meanwhile
+    rev_items(b, RK_PLANE, [&](int k, long long t) {
+      if (k < 0) return;
+      const InstDesc& d = b.inst[k];
+      const InstRev& r = b.rev[k];
+      if (t >= d.lay.plane) return;
+      const AdjArgs a = rev_adj(r, d, s, call, k, even ? r.P1 : r.P0, false);
+      adj_seed_one(a, t, even ? r.P0 : r.P1, r.Uacc, ra[s], rb[s], call.dt[k], 0);
+      adj_prims_one(a, t);
+    });
+    if (s < 2 && call.pbar)
+      for (int k = blockIdx.x; k < b.count; k += gridDim.x)
+        if (call.pbar[k]) rev_reduce(b.rev[k], s + 1, call.pbar[k]);
+    if (!grid_sync_on(b.bar, b.err, 0, b.budget)) return;
+    // pass 1 (x lines, then y lines from the 32-aligned offset xpad)
+    rev_items(b, s < 2 ? RK_P1SV : RK_P1RE, [&](int k, long long item) {
+      if (k < 0) return;  // whole warps past the end: nothing to do, no partials
+      const InstDesc& d = b.inst[k];
+      const InstRev& r = b.rev[k];
+      const AdjArgs a = rev_adj(r, d, s, call, k, even ? r.P1 : r.P0, true);
+      const long long xpad = s < 2 ? r.xpad_sv : r.xpad_re;
+      const int seg = s < 2 ? r.seg1_sv : r.seg1_re;
+      if (item < xpad) {
+        if (d.visc) {
+          if (s < 2) pass1_body<0, true, true, true>(a, seg, item, 0);
+          else pass1_body<0, true, true, false>(a, seg, item, 0);
+        } else {
+          if (s < 2) pass1_body<0, false, false, true>(a, seg, item, 0);
+          else pass1_body<0, false, false, false>(a, seg, item, 0);
+        }
+      } else {
+        if (d.visc) {
+          if (s < 2) pass1_body<1, true, true, true>(a, seg, item - xpad, xpad >> 5);
+          else pass1_body<1, true, true, false>(a, seg, item - xpad, xpad >> 5);
+        } else {
+          if (s < 2) pass1_body<1, false, false, true>(a, seg, item - xpad, xpad >> 5);
+          else pass1_body<1, false, false, false>(a, seg, item - xpad, xpad >> 5);
+        }
+      }
+    });
+    if (!grid_sync_on(b.bar, b.err, 0, b.budget)) return;
+    rev_items(b, RK_P2, [&](int k, long long item) {
+      if (k < 0) return;
+      const InstDesc& d = b.inst[k];
+      const InstRev& r = b.rev[k];
+      const AdjArgs a = rev_adj(r, d, s, call, k, even ? r.P1 : r.P0, false);
+      if (item < r.xpad_p2) pass2_body<0>(a, r.seg2, item);
+      else pass2_body<1>(a, r.seg2, item - r.xpad_p2);
+    });
+    if (!grid_sync_on(b.bar, b.err, 0, b.budget)) return;
+    rev_items(b, RK_PLANE, [&](int k, long long t) {
+      if (k < 0) return;
+      const InstDesc& d = b.inst[k];
+      const InstRev& r = b.rev[k];
+      const AdjArgs a = rev_adj(r, d, s, call, k, even ? r.P1 : r.P0, true);
+      double gb = 0.0, nb = 0.0;
+      if (d.visc) adj_primvjp_one<true>(a, t, r.seg2, gb, nb);
+      else adj_primvjp_one<false>(a, t, r.seg2, gb, nb);
+      warp_partials(a.pp, r.off_prim + (t >> 5), gb, 0.0, 0.0, nb);
+    });
+    if (!grid_sync_on(b.bar, b.err, 0, b.budget)) return;
+    rev_items(b, RK_BCTY, [&](int k, long long t) {
+      if (k < 0) return;
+      const InstDesc& d = b.inst[k];
+      const InstRev& r = b.rev[k];
+      const AdjArgs a = rev_adj(r, d, s, call, k, even ? r.P1 : r.P0, false);
+      adj_bcT_one(a, d.bc, 1, r.inflow_part, r.tmax, t);
+    });
+    if (!grid_sync_on(b.bar, b.err, 0, b.budget)) return;
+    rev_items(b, RK_BCTX, [&](int k, long long t) {
+      if (k < 0) return;
+      const InstDesc& d = b.inst[k];
+      const InstRev& r = b.rev[k];
+      const AdjArgs a = rev_adj(r, d, s, call, k, even ? r.P1 : r.P0, false);
+      adj_bcT_one(a, d.bc, 0, r.inflow_part, r.tmax, t);
+    });
+    if (!grid_sync_on(b.bar, b.err, 0, b.budget)) return;
+    // inflow-state gradient (one block per instance) and the transposed IB ghosts
+    for (int k = blockIdx.x; k < b.count; k += gridDim.x) {
+      const InstDesc& d = b.inst[k];
+      const InstRev& r = b.rev[k];
+      const AdjArgs a = rev_adj(r, d, s, call, k, even ? r.P1 : r.P0, true);
+      adj_inflow_block(a, d.bc, r.inflow_part, r.tmax, r.inflow_prim);
+    }
+    rev_items(b, RK_GHOST, [&](int k, long long g) {
+      if (k < 0) return;
+      const InstDesc& d = b.inst[k];
+      const InstRev& r = b.rev[k];
+      const AdjArgs a = rev_adj(r, d, s, call, k, even ? r.P1 : r.P0, true);
+      double gb = 0.0;
+      adj_ib_ghost_one(a, d.ib, d.wall, r.qIb, (int)g, gb);
+      warp_partials(a.pp, r.off_g + (g >> 5), gb, 0.0, 0.0, 0.0);
+    });
+    if (!grid_sync_on(b.bar, b.err, 0, b.budget)) return;
+    rev_items(b, RK_SRC, [&](int k, long long q) {
+      if (k < 0) return;
+      const InstDesc& d = b.inst[k];
+      const InstRev& r = b.rev[k];
+      const AdjArgs a = rev_adj(r, d, s, call, k, even ? r.P1 : r.P0, true);
+      double gb = 0.0;
+      adj_ib_src_one(a, r.ibt, r.qIb, (int)q, gb);
+      warp_partials(a.pp, r.off_s + (q >> 5), gb, 0.0, 0.0, 0.0);
+    });
+    if (!grid_sync_on(b.bar, b.err, 0, b.budget)) return;
+  }
+  // ---- lambda_n = P1 + Uacc (stage 0 wrote P1); the last stage's parameter gradient
+  rev_items(b, RK_USER4, [&](int k, long long t) {
+    if (k < 0) return;
+    const InstDesc& d = b.inst[k];
+    if (t >= 4LL * d.lay.nx * d.lay.ny) return;
+    adj_unpack_add_one(b.rev[k].P1, b.rev[k].Uacc, call.lam0[k], d.lay, t);
+  });
+  if (call.pbar)
+    for (int k = blockIdx.x; k < b.count; k += gridDim.x)
+      if (call.pbar[k]) rev_reduce(b.rev[k], 0, call.pbar[k]);
+}
+
+// one launch copying every instance's state: dst[k][i] = src[k][i], i < pre[k+1] - pre[k]
+__global__ void batch_copy_kernel(const double* const* src, double* const* dst, const long long* __restrict__ pre,
+                                  int count) {
+  const long long total = pre[count];
+  for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+       g += (long long)gridDim.x * blockDim.x) {
+    const int k = find_inst64(pre, count, g);
+    const long long i = g - pre[k];
+    dst[k][i] = src[k][i];
   }
 }
 
@@ -274,20 +602,128 @@ struct js_batch {
   unsigned long long* d_red = nullptr;
   unsigned* d_bar = nullptr;
   int* d_err = nullptr;
-  int blocks = 0;
+  int blocks = 0;          // persistent blocks of the forward launch (tuning: blocks per SM x SMs)
+  int sms = 0, per_sm = 0;  // SMs and the forward kernel's resident blocks per SM
+  int schedule = 0;        // tile order of the forward launch (js_batch_set_tuning)
+  int* d_order = nullptr;  // its queue -> tile table (schedules 1 and 2)
   int ntiles = 0;
   long long cells = 0;
   bool states_set = false;
-  // reverse: instances spread over a few streams (each has its own workspace)
-  std::vector<cudaStream_t> rstreams;
-  std::vector<cudaEvent_t> revents;  // [0]: fork from the batch stream, [1..]: joins
+  // persistent reverse (prepared by the first reverse call)
+  bool rev_ready = false;
+  js::InstRev* d_rev = nullptr;
+  long long* d_pre = nullptr;   // [RK_N][count + 1]
+  int rev_blocks = 0;
+  void** d_tab = nullptr;       // call table of js_batch_step_vjp: U_n, lam_np1, lam_n, p_bar x count
+  double* d_dt = nullptr;       // its step sizes
+  // checkpointed rollout reverse (js_batch_rollout_vjp)
+  int ro_steps = 0, ro_ckpt = 0, ro_nck = 0;
+  std::vector<double*> ro_buf;  // per instance: nck checkpoints, ckpt segment states, 1 working state
+  void** d_ro = nullptr;        // device tables: U, cp[nck], seg[ckpt], work, lam, p_bar (x count each)
+  long long* d_spre = nullptr;  // prefix sums of the state sizes (4 nx ny)
+  std::vector<void*> ro_lam, ro_pbar;  // the lam / p_bar pointers the tables hold
 };
 
 // accessors of a context's internals (defined in js_host.cu)
 void js_internal_desc(js_ctx* c, js::InstDesc* d);
+int js_internal_rev_desc(js_ctx* c, js::InstRev* d);
 
 namespace {
 size_t batch_smem() { return js::BStageV::SMEM > js::BStageE::SMEM ? js::BStageV::SMEM : js::BStageE::SMEM; }
+}  // namespace
+
+namespace {
+
+long long round32(long long n) { return (n + 31) / 32 * 32; }
+
+// line items of pass 1 / pass 2 in one direction (dir 0: rows): lines x segments
+long long line_items_of(const js::Lay& L, int dir, int extra, int seg) {
+  const int nline = (dir == 0) ? L.ny : L.nx;
+  const int ncell = (dir == 0) ? L.nx : L.ny;
+  return (long long)nline * ((ncell + extra + seg - 1) / seg);
+}
+
+// the reverse descriptors and per-kind item prefix sums of the batch (first reverse call:
+// allocates each instance's reverse workspace; call before any stream capture)
+int rev_prepare(js_batch* b) {
+  if (b->rev_ready) return JS_OK;
+  const int n = b->count;
+  std::vector<js::InstRev> rev(n);
+  std::vector<long long> pre((size_t)js::RK_N * (n + 1), 0);
+  for (int k = 0; k < n; ++k) {
+    js::InstRev& r = rev[k];
+    const int rc = js_internal_rev_desc(b->ctx[k], &r);
+    if (rc) return rc;
+    const js::InstDesc& d = b->desc[k];
+    const js::Lay& L = d.lay;
+    r.seg1_re = 16;  // the per-grid pass 1: recomputed WENO5 (2D), stored internals
+    r.seg1_sv = 8;
+    r.seg2 = js::ADJ_SEG2;
+    const long long x_re = line_items_of(L, 0, 1, r.seg1_re), y_re = line_items_of(L, 1, 1, r.seg1_re);
+    const long long x_sv = line_items_of(L, 0, 1, r.seg1_sv), y_sv = line_items_of(L, 1, 1, r.seg1_sv);
+    const long long x_p2 = line_items_of(L, 0, 2, r.seg2), y_p2 = line_items_of(L, 1, 2, r.seg2);
+    r.xpad_re = round32(x_re);
+    r.xpad_sv = round32(x_sv);
+    r.xpad_p2 = round32(x_p2);
+    r.w1_re = (r.xpad_re + round32(y_re)) / 32;
+    r.w1_sv = (r.xpad_sv + round32(y_sv)) / 32;
+    r.off_prim = std::max(r.w1_re, r.w1_sv);
+    r.w_prim = round32(L.plane) / 32;
+    r.off_g = r.off_prim + r.w_prim;
+    r.w_g = round32(d.ib.n) / 32;
+    r.off_s = r.off_g + r.w_g;
+    r.w_s = round32(r.ibt.nsrc) / 32;
+    const long long cnt[js::RK_N] = {
+        round32(L.plane), round32(4LL * L.nx * L.ny), round32(d.ib.n), round32(js::halo_count(L)),
+        r.xpad_re + round32(y_re), r.xpad_sv + round32(y_sv), r.xpad_p2 + round32(y_p2),
+        round32(6LL * (L.nx + 6)), round32(6LL * L.ny), round32(r.ibt.nsrc)};
+    for (int q = 0; q < js::RK_N; ++q) pre[(size_t)q * (n + 1) + k + 1] = pre[(size_t)q * (n + 1) + k] + cnt[q];
+  }
+  const size_t smem = batch_smem();
+  if (cudaFuncSetAttribute(js::batch_vjp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return JS_ERR_CUDA;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, js::batch_vjp_kernel, js::BNT, smem);
+  if (per_sm < 1) return JS_ERR_CUDA;
+  b->rev_blocks = sms * per_sm;
+  if (cudaMalloc(&b->d_rev, sizeof(js::InstRev) * n) != cudaSuccess ||
+      cudaMalloc(&b->d_pre, sizeof(long long) * pre.size()) != cudaSuccess ||
+      cudaMalloc(&b->d_tab, sizeof(void*) * 4 * n) != cudaSuccess ||
+      cudaMalloc(&b->d_dt, sizeof(double) * n) != cudaSuccess)
+    return JS_ERR_NOMEM;
+  if (cudaMemcpy(b->d_rev, rev.data(), sizeof(js::InstRev) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->d_pre, pre.data(), sizeof(long long) * pre.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaDeviceSynchronize() != cudaSuccess)
+    return JS_ERR_CUDA;
+  b->rev_ready = true;
+  return JS_OK;
+}
+
+// one persistent cooperative launch reversing one step of every instance
+int rev_launch(js_batch* b, const js::RevCall& call) {
+  js::BatchRevArgs a;
+  a.inst = b->d_desc;
+  a.rev = b->d_rev;
+  a.count = b->count;
+  a.pre = b->d_pre;
+  a.tile0 = b->d_tile0;
+  a.call = call;
+  a.bar = b->d_bar;
+  a.err = b->d_err;
+  int dev = 0, khz = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
+  a.budget = (long long)(2.0 * (khz > 0 ? khz : 2000000) * 1e3);  // 2 s of SM clock cycles
+  void* args[] = {&a};
+  if (cudaLaunchCooperativeKernel((void*)js::batch_vjp_kernel, dim3(b->rev_blocks), dim3(js::BNT), args,
+                                  batch_smem(), b->stream) != cudaSuccess)
+    return JS_ERR_CUDA;
+  return JS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -295,8 +731,9 @@ extern "C" {
 void js_batch_destroy(js_batch* b) {
   if (!b) return;
   if (b->stream) cudaStreamSynchronize(b->stream); else cudaDeviceSynchronize();
-  for (cudaStream_t r : b->rstreams) cudaStreamDestroy(r);
-  for (cudaEvent_t e : b->revents) cudaEventDestroy(e);
+  cudaFree(b->d_rev); cudaFree(b->d_pre); cudaFree(b->d_tab); cudaFree(b->d_dt); cudaFree(b->d_order);
+  for (double* p : b->ro_buf) cudaFree(p);
+  cudaFree(b->d_ro); cudaFree(b->d_spre);
   for (js_ctx* c : b->ctx) js_destroy(c);
   cudaFree(b->d_desc); cudaFree(b->d_tile0); cudaFree(b->d_ghost0); cudaFree(b->d_halo0);
   cudaFree(b->d_red); cudaFree(b->d_bar); cudaFree(b->d_err);
@@ -341,6 +778,8 @@ int js_batch_create(int count, const js_grid* grids, const js_params* params, co
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, js::batch_kernel, js::BNT, smem);
   if (!coop || per_sm < 1) { js_batch_destroy(b); return JS_ERR_CUDA; }
+  b->sms = sms;
+  b->per_sm = per_sm;
   b->blocks = sms * per_sm;
   if (cudaMalloc(&b->d_desc, sizeof(InstDesc) * count) != cudaSuccess ||
       cudaMalloc(&b->d_tile0, sizeof(int) * (count + 1)) != cudaSuccess ||
@@ -380,8 +819,13 @@ int js_batch_set_states(js_batch* b, double* const* U) {
 }
 
 static int batch_launch(js_batch* b, double cfl, int n_steps, double* t_dev, double* dt_log, int extra,
-                        double budget_s) {
+                        double budget_s, const double* dt_in = nullptr, double* const* ustate = nullptr,
+                        double* const* save = nullptr) {
   js::BatchArgs a;
+  a.dt_in = dt_in;
+  a.ustate = ustate;
+  a.save = save;
+  a.order = b->schedule ? b->d_order : nullptr;
   a.inst = b->d_desc;
   a.count = b->count;
   a.tile0 = b->d_tile0;
@@ -413,36 +857,144 @@ int js_batch_step(js_batch* b, double cfl, int n_steps, double* t_dev, double* d
 int js_batch_step_vjp(js_batch* b, double* const* U_n, const double* dt, double* const* lam_np1,
                       double* const* lam_n, double* const* p_bar) {
   if (!b || !U_n || !dt || !lam_np1 || !lam_n) return JS_ERR_ARG;
-  // the instances are independent: up to kRevStreams of them run at once, each on its own
-  // stream forked from and joined back to the batch stream
-  constexpr int kRevStreams = 8;
-  const int ns = b->count < kRevStreams ? b->count : kRevStreams;
-  while ((int)b->rstreams.size() < ns) {
-    cudaStream_t r;
-    if (cudaStreamCreateWithFlags(&r, cudaStreamNonBlocking) != cudaSuccess) return JS_ERR_CUDA;
-    b->rstreams.push_back(r);
+  for (int k = 0; k < b->count; ++k)
+    if (!U_n[k] || !lam_np1[k] || !lam_n[k] || !(dt[k] > 0.0)) return JS_ERR_ARG;
+  int rc = rev_prepare(b);
+  if (rc) return rc;
+  // the call table: pointers and step sizes of this call (copied before the call returns)
+  std::vector<void*> tab(4 * (size_t)b->count);
+  for (int k = 0; k < b->count; ++k) {
+    tab[k] = U_n[k];
+    tab[b->count + k] = lam_np1[k];
+    tab[2 * b->count + k] = lam_n[k];
+    tab[3 * b->count + k] = p_bar ? p_bar[k] : nullptr;
   }
-  while ((int)b->revents.size() < ns + 1) {
-    cudaEvent_t e;
-    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return JS_ERR_CUDA;
-    b->revents.push_back(e);
+  if (cudaMemcpyAsync(b->d_tab, tab.data(), sizeof(void*) * tab.size(), cudaMemcpyHostToDevice, b->stream) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(b->d_dt, dt, sizeof(double) * b->count, cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
+      cudaStreamSynchronize(b->stream) != cudaSuccess)  // the host arrays may change after the call
+    return JS_ERR_CUDA;
+  js::RevCall call;
+  call.Un = reinterpret_cast<const double* const*>(b->d_tab);
+  call.lam1 = reinterpret_cast<const double* const*>(b->d_tab + b->count);
+  call.lam0 = reinterpret_cast<double* const*>(b->d_tab + 2 * b->count);
+  call.pbar = p_bar ? reinterpret_cast<double* const*>(b->d_tab + 3 * b->count) : nullptr;
+  call.dt = b->d_dt;
+  return rev_launch(b, call);
+}
+
+int js_batch_step_fixed(js_batch* b, int n_steps, const double* dt) {
+  if (!b || !b->states_set || n_steps < 0 || (n_steps > 0 && !dt)) return JS_ERR_ARG;
+  return batch_launch(b, 0.5, n_steps, nullptr, nullptr, 0, 2.0, dt);
+}
+
+namespace {
+// one launch copying the states of table src into those of table dst (device tables of count
+// pointers)
+int batch_copy(js_batch* b, void* const* src, void* const* dst) {
+  js::batch_copy_kernel<<<4 * 152, 256, 0, b->stream>>>(reinterpret_cast<const double* const*>(src),
+                                                        reinterpret_cast<double* const*>(dst), b->d_spre, b->count);
+  return cudaGetLastError() == cudaSuccess ? JS_OK : JS_ERR_CUDA;
+}
+
+// the rollout workspace for (n_steps, ckpt): checkpoint, segment and working states per instance
+// and the device pointer tables (allocates and synchronises: before any stream capture)
+int rollout_prepare(js_batch* b, int n_steps, int ckpt) {
+  const int n = b->count;
+  const int nck = (n_steps + ckpt - 1) / ckpt;
+  if (b->ro_steps == n_steps && b->ro_ckpt == ckpt && b->d_ro) return JS_OK;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return JS_ERR_CUDA;
+  for (double* p : b->ro_buf) cudaFree(p);
+  b->ro_buf.assign(n, nullptr);
+  cudaFree(b->d_ro);
+  b->d_ro = nullptr;
+  b->ro_steps = b->ro_ckpt = b->ro_nck = 0;
+  b->ro_lam.clear();
+  b->ro_pbar.clear();
+  const int ntab = nck + ckpt + 4;
+  std::vector<void*> tab((size_t)ntab * n, nullptr);
+  std::vector<long long> spre(n + 1, 0);
+  for (int k = 0; k < n; ++k) {
+    const size_t st = 4 * (size_t)b->desc[k].lay.nx * b->desc[k].lay.ny;
+    spre[k + 1] = spre[k] + (long long)st;
+    if (cudaMalloc(&b->ro_buf[k], sizeof(double) * st * (size_t)(nck + ckpt + 1)) != cudaSuccess) return JS_ERR_NOMEM;
+    tab[k] = b->desc[k].U;
+    for (int c = 0; c < nck; ++c) tab[(size_t)(1 + c) * n + k] = b->ro_buf[k] + st * c;
+    for (int j = 0; j < ckpt; ++j) tab[(size_t)(1 + nck + j) * n + k] = b->ro_buf[k] + st * (nck + j);
+    tab[(size_t)(1 + nck + ckpt) * n + k] = b->ro_buf[k] + st * (nck + ckpt);
   }
-  if (cudaEventRecord(b->revents[0], b->stream) != cudaSuccess) return JS_ERR_CUDA;
-  for (int r = 0; r < ns; ++r)
-    if (cudaStreamWaitEvent(b->rstreams[r], b->revents[0], 0) != cudaSuccess) return JS_ERR_CUDA;
-  int rc = JS_OK;
-  for (int k = 0; k < b->count && rc == JS_OK; ++k) {
-    js_ctx* c = b->ctx[k];
-    js_set_stream(c, b->rstreams[k % ns]);
-    rc = js_step_vjp(c, U_n[k], dt[k], lam_np1[k], lam_n[k], p_bar ? p_bar[k] : nullptr);
-  }
-  for (int r = 0; r < ns; ++r) {
-    if (cudaEventRecord(b->revents[r + 1], b->rstreams[r]) != cudaSuccess ||
-        cudaStreamWaitEvent(b->stream, b->revents[r + 1], 0) != cudaSuccess)
+  if (!b->d_spre && cudaMalloc(&b->d_spre, sizeof(long long) * (n + 1)) != cudaSuccess) return JS_ERR_NOMEM;
+  if (cudaMalloc(&b->d_ro, sizeof(void*) * tab.size()) != cudaSuccess) return JS_ERR_NOMEM;
+  if (cudaMemcpy(b->d_ro, tab.data(), sizeof(void*) * tab.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->d_spre, spre.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice) != cudaSuccess)
+    return JS_ERR_CUDA;
+  b->ro_steps = n_steps;
+  b->ro_ckpt = ckpt;
+  b->ro_nck = nck;
+  return JS_OK;
+}
+}  // namespace
+
+int js_batch_rollout_vjp(js_batch* b, int n_steps, const double* dt_log, int ckpt, double* const* lam,
+                         double* const* p_bar) {
+  if (!b || !b->states_set || n_steps < 1 || !dt_log || !lam) return JS_ERR_ARG;
+  for (int k = 0; k < b->count; ++k)
+    if (!lam[k]) return JS_ERR_ARG;
+  if (ckpt <= 0) ckpt = (int)std::lround(std::sqrt((double)n_steps));
+  if (ckpt < 1) ckpt = 1;
+  if (ckpt > n_steps) ckpt = n_steps;
+  int rc = rev_prepare(b);
+  if (rc) return rc;
+  if ((rc = rollout_prepare(b, n_steps, ckpt))) return rc;
+  const int n = b->count, nck = b->ro_nck;
+  void** T = b->d_ro;
+  void** U = T;
+  auto cp = [&](int c) { return T + (size_t)(1 + c) * n; };
+  auto seg = [&](int j) { return T + (size_t)(1 + nck + j) * n; };
+  void** work = T + (size_t)(1 + nck + ckpt) * n;
+  void** lamt = T + (size_t)(2 + nck + ckpt) * n;
+  void** pbt = T + (size_t)(3 + nck + ckpt) * n;
+  // the lam / p_bar pointers of this call (uploaded when they differ from the previous call's)
+  std::vector<void*> hl(lam, lam + n), hp(n, nullptr);
+  if (p_bar)
+    for (int k = 0; k < n; ++k) hp[k] = p_bar[k];
+  if (hl != b->ro_lam || hp != b->ro_pbar) {
+    if (cudaMemcpyAsync(lamt, hl.data(), sizeof(void*) * n, cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
+        cudaMemcpyAsync(pbt, hp.data(), sizeof(void*) * n, cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess)
       return JS_ERR_CUDA;
+    b->ro_lam = hl;
+    b->ro_pbar = hp;
   }
-  for (int k = 0; k < b->count; ++k) js_set_stream(b->ctx[k], b->stream);
-  return rc;
+  // forward: checkpoint c holds the state after c * ckpt steps
+  if ((rc = batch_copy(b, U, cp(0)))) return rc;
+  for (int c = 1; c < nck; ++c) {
+    if ((rc = batch_copy(b, cp(c - 1), cp(c)))) return rc;
+    if ((rc = batch_launch(b, 0.5, ckpt, nullptr, nullptr, 0, 2.0, dt_log + (size_t)(c - 1) * ckpt * n,
+                           reinterpret_cast<double* const*>(cp(c)))))
+      return rc;
+  }
+  // reverse, segment by segment: re-run the segment keeping its states, then reverse its steps
+  for (int c = nck - 1; c >= 0; --c) {
+    const int s0 = c * ckpt, len = std::min(ckpt, n_steps - s0);
+    if ((rc = batch_copy(b, cp(c), seg(0)))) return rc;
+    if (len > 1) {
+      if ((rc = batch_copy(b, cp(c), work))) return rc;
+      if ((rc = batch_launch(b, 0.5, len - 1, nullptr, nullptr, 0, 2.0, dt_log + (size_t)s0 * n,
+                             reinterpret_cast<double* const*>(work), reinterpret_cast<double* const*>(seg(1)))))
+        return rc;
+    }
+    for (int j = len - 1; j >= 0; --j) {
+      js::RevCall call;
+      call.Un = reinterpret_cast<const double* const*>(seg(j));
+      call.lam1 = reinterpret_cast<const double* const*>(lamt);
+      call.lam0 = reinterpret_cast<double* const*>(lamt);
+      call.pbar = p_bar ? reinterpret_cast<double* const*>(pbt) : nullptr;
+      call.dt = dt_log + (size_t)(s0 + j) * n;
+      if ((rc = rev_launch(b, call))) return rc;
+    }
+  }
+  return JS_OK;
 }
 
 int js_batch_test_timeout(js_batch* b, double budget_s) {
@@ -462,6 +1014,49 @@ int js_batch_sync_status(js_batch* b) {
     return JS_ERR_CUDA;
   if (h & js::ERR_TIMEOUT_BIT) return JS_ERR_TIMEOUT;
   if (h & js::ERR_NONPHYSICAL_BIT) return JS_ERR_NONPHYSICAL;
+  return JS_OK;
+}
+
+int js_batch_set_tuning(js_batch* b, int blocks_per_sm, int schedule) {
+  if (!b || blocks_per_sm < 0 || blocks_per_sm > b->per_sm || schedule < 0 || schedule > 2) return JS_ERR_ARG;
+  if (schedule != 0) {
+    // queue position -> tile number
+    std::vector<int> tile0(b->count + 1, 0);
+    for (int k = 0; k < b->count; ++k) tile0[k + 1] = tile0[k] + b->desc[k].ntx * b->desc[k].nty;
+    std::vector<int> order;
+    order.reserve(b->ntiles);
+    if (schedule == 1) {  // interleaved: tile j of every instance, then tile j + 1
+      int most = 0;
+      for (int k = 0; k < b->count; ++k) most = std::max(most, tile0[k + 1] - tile0[k]);
+      for (int j = 0; j < most; ++j)
+        for (int k = 0; k < b->count; ++k)
+          if (tile0[k] + j < tile0[k + 1]) order.push_back(tile0[k] + j);
+    } else {  // the largest instances first, each instance's tiles together
+      std::vector<int> inst(b->count);
+      for (int k = 0; k < b->count; ++k) inst[k] = k;
+      std::stable_sort(inst.begin(), inst.end(), [&](int x, int y) {
+        return tile0[x + 1] - tile0[x] > tile0[y + 1] - tile0[y];
+      });
+      for (int k : inst)
+        for (int t = tile0[k]; t < tile0[k + 1]; ++t) order.push_back(t);
+    }
+    if (!b->d_order && cudaMalloc(&b->d_order, sizeof(int) * b->ntiles) != cudaSuccess) return JS_ERR_NOMEM;
+    if (cudaMemcpyAsync(b->d_order, order.data(), sizeof(int) * b->ntiles, cudaMemcpyHostToDevice, b->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess)
+      return JS_ERR_CUDA;
+  }
+  b->schedule = schedule;
+  b->blocks = b->sms * (blocks_per_sm == 0 ? b->per_sm : blocks_per_sm);
+  return JS_OK;
+}
+
+int js_batch_get_tuning(js_batch* b, int* blocks_per_sm, int* max_blocks_per_sm, int* schedule, int* n_schedules) {
+  if (!b) return JS_ERR_ARG;
+  if (blocks_per_sm) *blocks_per_sm = b->blocks / (b->sms > 0 ? b->sms : 1);
+  if (max_blocks_per_sm) *max_blocks_per_sm = b->per_sm;
+  if (schedule) *schedule = b->schedule;
+  if (n_schedules) *n_schedules = 3;
   return JS_OK;
 }
 

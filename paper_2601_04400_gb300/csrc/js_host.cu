@@ -1365,3 +1365,26 @@ int js_nn_eval_vjp(js_ctx* c, const double* X, int H, int W, const double* GY, d
   JS_CUDA(js::nn_eval_vjp(c->nn, X, H, W, GY, GX, c->stream));
   return JS_OK;
 }
+
+// reverse-pass description of a context for the batched reverse kernel (js_batch.cu): reserves
+// the reverse workspace and uploads the inflow states (synchronises when they changed)
+int js_internal_rev_desc(js_ctx* c, js::InstRev* d) {
+  std::memset(d, 0, sizeof(*d));
+  int rc = adj_reserve(c);
+  if (rc) return rc;
+  if (!c->wsave_fwd) return JS_ERR_NOMEM;
+  if ((rc = upload_inflow(c))) return rc;
+  d->a = adj_args(c, nullptr, nullptr, nullptr);
+  d->ibt = ibt_args(c);
+  d->P0 = c->P0;
+  d->P1 = c->P1;
+  d->Uacc = c->Uacc;
+  d->wsave_own = c->wsave;
+  d->wfwd = c->wsave_fwd;
+  d->inflow_part = c->inflow_part;
+  d->inflow_prim = c->inflow_prim;
+  d->qIb = c->qIb;
+  d->ppart = c->ppart;
+  d->tmax = std::max(c->g.nx + 6, c->g.ny);
+  return JS_OK;
+}

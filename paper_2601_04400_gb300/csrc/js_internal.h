@@ -179,6 +179,28 @@ struct InstDesc {
   int wall, visc, has_av, ntx, nty;
 };
 
+// reverse-pass description of one instance for the persistent batched reverse kernel
+// (js_batch.cu): the context's adjoint arguments and workspace (js_internal_rev_desc) and the
+// instance's work-item counts and parameter-gradient slot offsets (set by js_batch.cu)
+struct InstRev {
+  AdjArgs a;                 // X, Ub, pbar, pp, wsave, weno_saved are set per phase
+  IbTArgs ibt;
+  double* P0;                // adjoint ping-pong states (4 padded planes each)
+  double* P1;
+  double* Uacc;              // U^n part of the step's adjoint (4 padded planes)
+  double* wsave_own;         // WENO5 internals recomputed by pass 1 (stage 2)
+  double* wfwd;              // internals stored by the forward stages 0 and 1 (2 x 56 planes)
+  double* inflow_part;
+  const double* inflow_prim;
+  double* qIb;
+  double* ppart;             // warp partials of the parameter gradient
+  int tmax;                  // max(nx + 6, ny): inflow_part row length
+  int seg1_re, seg1_sv, seg2;  // pass-1 segment lengths (recompute / stored internals), pass 2
+  long long xpad_re, xpad_sv, xpad_p2;  // x-line items of passes 1 and 2, rounded up to 32
+  long long w1_re, w1_sv;    // warp slots of pass 1 (both directions)
+  long long off_prim, w_prim, off_g, w_g, off_s, w_s;  // slots of primvjp, IB ghost, IB source
+};
+
 // opaque 128-byte, 64-byte aligned tensor map (CUtensorMap) for TMA copies
 struct alignas(64) TensorMap128 {
   unsigned long long opaque[16];

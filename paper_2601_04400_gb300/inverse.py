@@ -16,10 +16,30 @@ import torch
 from . import autograd as A
 
 
-def prim_to_cons(W0, gamma):
-    """Conserved state [4, ny, nx] from primitive W0 = (rho, u, v, p), differentiable in gamma."""
-    r, u, v, p = W0[0], W0[1], W0[2], W0[3]
-    return torch.stack([r, r * u, r * v, p / (gamma - 1.0) + 0.5 * r * (u * u + v * v)])
+class _PrimToCons(torch.autograd.Function):
+    """U = prim_to_cons(W0) with the library's EOS kernel (js_prim_to_cons) at the solver's
+    gamma; its derivative in gamma is analytic: only E = p/(gamma - 1) + rho |u|^2 / 2 depends
+    on it, dE/dgamma = -p / (gamma - 1)^2.  W0 is data (no gradient)."""
+
+    @staticmethod
+    def forward(ctx, gamma, W0, solver):
+        g = float(gamma)
+        A._apply_theta(solver, torch.cat([gamma.detach().view(1).cpu(), A.theta_of(solver)[1:]]))
+        ctx.save_for_backward(W0[3])
+        ctx.g = g
+        return solver.prim_to_cons(W0)
+
+    @staticmethod
+    def backward(ctx, U_bar):
+        (p,) = ctx.saved_tensors
+        dE = -p / (ctx.g - 1.0) ** 2
+        return (U_bar[3] * dE).sum().to(torch.float64).cpu(), None, None
+
+
+def prim_to_cons(solver, W0, gamma):
+    """Conserved state [4, ny, nx] from primitive W0 = (rho, u, v, p) by the library kernel at
+    gamma (which becomes the solver's gamma), differentiable in gamma."""
+    return _PrimToCons.apply(gamma, W0, solver)
 
 
 def multistep_loss(states, targets, mask=None):
@@ -66,7 +86,7 @@ def fit_gamma(solver, W0, targets, dts, gamma0, iters, lr=0.1, schedule=None, ma
                 grp["lr"] = schedule(k)
         opt.zero_grad()
         theta = torch.cat([g.view(1), theta_rest])
-        U0 = prim_to_cons(W0, g.to(W0.device))
+        U0 = prim_to_cons(solver, W0, g)
         states = A.rollout(solver, U0, theta, dts, outputs=outputs, checkpoint_every=checkpoint_every)
         loss = multistep_loss(states, targets, mask)
         loss.backward()

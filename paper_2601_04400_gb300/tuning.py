@@ -75,3 +75,57 @@ def autotune(solver, U, reps=3, use_cache=True):
     cache[_key(solver)] = {"variant": best, "ms_per_step": times}
     _save(cache)
     return times
+
+
+# ---------------------------------------------------------------------------------------
+# batched path: blocks per SM and tile schedule of the persistent forward launch
+# ---------------------------------------------------------------------------------------
+def batch_key(problems):
+    """The instance mix: grid sizes, physics and immersed bodies of all instances (order-free)."""
+    import hashlib
+    items = sorted("%dx%d|visc=%d|av=%d|ib=%d" % (p.nx, p.ny, int(p.mu > 0), int(p.nu > 0), int(p.sdf is not None))
+                   for p in problems)
+    return "batch|%d|%s" % (len(items), hashlib.sha1("\n".join(items).encode()).hexdigest()[:16])
+
+
+def autotune_batch(batch, problems, states, steps=2, use_cache=True):
+    """Time js_batch_step for every (blocks per SM, schedule) on copies of `states` (which are
+    not advanced) and select the fastest; the choice is cached per instance mix.  Results are
+    identical for every choice.  The batch's registered states are `states` afterwards.
+    Returns {(blocks_per_sm, schedule): ms per step} ({} when the cache had the choice)."""
+    import torch
+    key = batch_key(problems)
+    cache = _load()
+    if use_cache and key in cache:
+        batch.set_tuning(*cache[key]["choice"])
+        batch.set_states(states)
+        return {}
+    _, most, _, nsched = batch.tuning()
+    work = [U.clone() for U in states]
+    batch.set_states(work)
+    stream = torch.cuda.current_stream()
+    times = {}
+    for bps in range(1, most + 1):
+        for sched in range(nsched):
+            batch.set_tuning(bps, sched)
+            for U, U0 in zip(work, states):
+                U.copy_(U0)
+            batch.step(0.5, 1)  # warm-up
+            t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            batch.step(0.5, steps)
+            t1.record(stream)
+            t1.synchronize()
+            times[(bps, sched)] = t0.elapsed_time(t1) / steps
+    if batch.status() != 0:
+        raise RuntimeError("batched tuning run failed")
+    default = (most, 0)
+    best = min(times, key=times.get)
+    if times[best] > 0.98 * times[default]:
+        best = default
+    batch.set_tuning(*best)
+    batch.set_states(states)
+    cache = _load()
+    cache[key] = {"choice": list(best), "ms_per_step": {"%d,%d" % k: v for k, v in times.items()}}
+    _save(cache)
+    return times

@@ -218,4 +218,232 @@ def test_full_batched_configuration(env):
         lhs = np.dot(lam.reshape(-1), Jv.reshape(-1))
         rhs = np.dot(to_host(outs[k]).reshape(-1), v.reshape(-1))
         assert abs(lhs - rhs) <= 1e-12 * np.abs(lam).sum() * np.abs(Jv).max(), k
+    # the whole rollout reversed from step 500 with sqrt(N) checkpoints (the registered states
+    # are the initial ones): <lam_500, J v> from the oracle's forward mode over the 500 logged
+    # steps equals <lam_0, v> on the two smallest instances
+    b.set_states([U.clone() for U in states])
+    lam_T = [torch.tensor(rng.standard_normal(U.shape), device="cuda") for U in states]
+    lam_0 = [l.clone() for l in lam_T]
+    pbs = [torch.zeros(20, dtype=torch.float64, device="cuda") for _ in states]
+    b.rollout_vjp(log, lam_0, pbs)
+    assert b.status() == 0
+    for k in small[:2]:
+        p = probs[k]
+        U0 = O.prim_to_cons(p, p.W0)
+        v = rng.standard_normal(U0.shape) * np.abs(U0).max(axis=(1, 2), keepdims=True) * 1e-3
+        _, Jv = O.step_tangent(p, U0, v, np.zeros(20), dts[:, k])
+        lam = to_host(lam_T[k])
+        lhs = np.dot(lam.reshape(-1), Jv.reshape(-1))
+        rhs = np.dot(to_host(lam_0[k]).reshape(-1), v.reshape(-1))
+        assert abs(lhs - rhs) <= 1e-10 * np.abs(lam).sum() * np.abs(Jv).max(), (k, lhs, rhs)
+    b.close()
+
+
+# ---------------------------------------------------------------------------------------
+# the persistent batched reverse (one launch per reversed step of all instances) and the
+# checkpointed rollout reverse
+# ---------------------------------------------------------------------------------------
+def _mixed_cases():
+    """Uneven grids, viscous and Euler instances, immersed bodies of different sizes."""
+    out = W.batched_cases(3, seed=21, nx_choices=(64, 96, 128), ny_choices=(48, 64))
+    out.append(W.shock_cylinder(nx=80, ny=56, mach=2.4, radius=0.45, viscous=False))
+    out.append(W.shock_cylinder(nx=112, ny=40, mach=1.8, radius=0.35, Re=300.0))
+    return out
+
+
+def _per_instance_vjp(torch, B, p, U, dt, lam):
+    s = B.Solver.from_problem(p)
+    pb = torch.zeros(20, dtype=torch.float64, device="cuda")
+    out, _ = s.step_vjp(U, dt, lam, p_bar=pb)
+    torch.cuda.synchronize()
+    s.close()
+    return out, pb
+
+
+def _rel(a, b):
+    return float((a - b).abs().max() / b.abs().max())
+
+
+def test_persistent_reverse_step_equals_js_step_vjp(env):
+    """lambda_n and p_bar of every instance equal js_step_vjp's to rounding (the same device
+    bodies on the same elements, inlined into one kernel, where the compiler may fuse a
+    different set of products and sums), and a second call reproduces the first bit for bit."""
+    torch, B = env
+    probs = _mixed_cases()
+    states = _states(torch, probs)
+    b = B.Batch(probs)
+    b.set_states([U.clone() for U in states])
+    rng = np.random.default_rng(2)
+    lams = [torch.tensor(rng.standard_normal(U.shape), device="cuda") for U in states]
+    dts = []
+    for p, U in zip(probs, states):
+        s = B.Solver.from_problem(p)
+        dts.append(0.9 * s.max_dt(U, 0.5))
+        s.close()
+    outs = [torch.empty_like(U) for U in states]
+    pbs = [torch.zeros(20, dtype=torch.float64, device="cuda") for _ in states]
+    b.step_vjp(states, dts, lams, outs, pbs)
+    assert b.status() == 0
+    for k, p in enumerate(probs):
+        ref, pref = _per_instance_vjp(torch, B, p, states[k], dts[k], lams[k])
+        print("instance %d: lambda %.2e, p_bar %.2e (relative to the maxima)" % (k, _rel(outs[k], ref),
+                                                                             _rel(pbs[k], pref)))
+        assert _rel(outs[k], ref) < 1e-13, k
+        assert _rel(pbs[k], pref) < 1e-12, k
+    # lam_n may alias lam_np1; the same call again gives the same bits
+    again = [lam.clone() for lam in lams]
+    pb2 = [torch.zeros(20, dtype=torch.float64, device="cuda") for _ in states]
+    b.step_vjp(states, dts, again, again, pb2)
+    assert b.status() == 0
+    for k in range(len(probs)):
+        assert torch.equal(again[k], outs[k]), k
+        assert torch.equal(pb2[k], pbs[k]), k
+    b.close()
+
+
+def test_fixed_step_sizes_replay_per_instance_steps(env):
+    torch, B = env
+    probs = _mixed_cases()
+    states = _states(torch, probs)
+    b = B.Batch(probs)
+    work = [U.clone() for U in states]
+    b.set_states(work)
+    rng = np.random.default_rng(4)
+    dts = torch.zeros((6, len(probs)), dtype=torch.float64, device="cuda")
+    for k, (p, U) in enumerate(zip(probs, states)):
+        s = B.Solver.from_problem(p)
+        dts[:, k] = torch.tensor(s.max_dt(U, 0.5) * rng.uniform(0.5, 0.9, 6))
+        s.close()
+    b.step_fixed(dts)
+    assert b.status() == 0
+    for k, (p, U) in enumerate(zip(probs, states)):
+        s = B.Solver.from_problem(p)
+        V = U.clone()
+        for j in range(6):
+            s.step(V, float(dts[j, k]), 1)
+        assert torch.equal(V, work[k]), k
+        s.close()
+    b.close()
+
+
+def _reference_rollout_reverse(torch, B, p, U0, dts, lam):
+    """Per instance: the forward states by js_step, then js_step_vjp from the last step back."""
+    s = B.Solver.from_problem(p)
+    states = [U0.clone()]
+    for dt in dts:
+        V = states[-1].clone()
+        s.step(V, dt, 1)
+        states.append(V)
+    lam = lam.clone()
+    pb = torch.zeros(20, dtype=torch.float64, device="cuda")
+    for j in range(len(dts) - 1, -1, -1):
+        s.step_vjp(states[j], dts[j], lam, lam_n=lam, p_bar=pb)
+    torch.cuda.synchronize()
+    s.close()
+    return lam, pb
+
+
+@pytest.mark.parametrize("ckpt", [4, 0, 13])
+def test_rollout_reverse_equals_step_by_step_reverse(env, ckpt):
+    """13 steps, checkpoints every ckpt (4: an uneven last segment; 0: about sqrt(13); 13: one
+    segment): dL/dU_0 equals the per-instance step-by-step reverse to rounding, and the same
+    for every checkpoint spacing bit for bit; the registered states are left unchanged."""
+    torch, B = env
+    probs = _mixed_cases()
+    states = _states(torch, probs)
+    b = B.Batch(probs)
+    reg = [U.clone() for U in states]
+    b.set_states(reg)
+    n = 13
+    rng = np.random.default_rng(6)
+    dts = torch.zeros((n, len(probs)), dtype=torch.float64, device="cuda")
+    for k, (p, U) in enumerate(zip(probs, states)):
+        s = B.Solver.from_problem(p)
+        dts[:, k] = torch.tensor(s.max_dt(U, 0.5) * rng.uniform(0.4, 0.8, n))
+        s.close()
+    lams = [torch.tensor(rng.standard_normal(U.shape), device="cuda") for U in states]
+    work = [lam.clone() for lam in lams]
+    pbs = [torch.zeros(20, dtype=torch.float64, device="cuda") for _ in states]
+    b.rollout_vjp(dts, work, pbs, ckpt=ckpt)
+    assert b.status() == 0
+    for k, p in enumerate(probs):
+        assert torch.equal(reg[k], states[k]), k
+        ref, pref = _reference_rollout_reverse(torch, B, p, states[k], dts[:, k].tolist(), lams[k])
+        assert _rel(work[k], ref) < 1e-12, (k, _rel(work[k], ref))
+        assert _rel(pbs[k], pref) < 1e-11, (k, _rel(pbs[k], pref))
+    # another checkpoint spacing: the same segments' states, the same reverse launches
+    other = [lam.clone() for lam in lams]
+    b.rollout_vjp(dts, other, None, ckpt=1 if ckpt != 1 else 2)
+    assert b.status() == 0
+    for k in range(len(probs)):
+        assert torch.equal(other[k], work[k]), k
+    b.close()
+
+
+def test_rollout_reverse_is_graph_capturable(env):
+    torch, B = env
+    probs = _mixed_cases()[:3]
+    states = _states(torch, probs)
+    side = torch.cuda.Stream()
+    n = 9
+    with torch.cuda.stream(side):
+        b = B.Batch(probs, stream=side)
+        b.set_states([U.clone() for U in states])
+        log = torch.zeros((n, len(probs)), dtype=torch.float64, device="cuda")
+        fwd = [U.clone() for U in states]
+        b.set_states(fwd)
+        b.step(0.5, n, dt_log=log)
+        b.set_states([U.clone() for U in states])
+        rng = np.random.default_rng(8)
+        lam0 = [torch.tensor(rng.standard_normal(U.shape), device="cuda") for U in states]
+        eager = [l.clone() for l in lam0]
+        b.rollout_vjp(log, eager, ckpt=3)  # first call: workspace, tables
+        work = [l.clone() for l in lam0]
+        b.rollout_vjp(log, work, ckpt=3)  # same pointers from here on
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=side):
+            b.rollout_vjp(log, work, ckpt=3)
+    torch.cuda.synchronize()
+    for w, l in zip(work, lam0):
+        w.copy_(l)
+    torch.cuda.synchronize()
+    g.replay()
+    torch.cuda.synchronize()
+    assert b.status() == 0
+    for w, e in zip(work, eager):
+        assert torch.equal(w, e)
+    b.close()
+
+
+def test_launch_tuning_keeps_results_and_the_tuner_caches_its_choice(env, tmp_path, monkeypatch):
+    """Every (blocks per SM, schedule) gives the default launch's states bit for bit; the
+    autotuner times them, applies the fastest and finds it in its cache the next time."""
+    torch, B = env
+    from paper_2601_04400_gb300 import tuning
+    monkeypatch.setattr(tuning, "_CACHE", str(tmp_path / "tuning.json"))
+    probs = _mixed_cases()
+    states = _states(torch, probs)
+    b = B.Batch(probs)
+    ref = [U.clone() for U in states]
+    b.set_states(ref)
+    b.step(0.5, 3)
+    _, most, _, nsched = b.tuning()
+    assert most >= 1 and nsched == 3
+    for bps in range(1, most + 1):
+        for sched in range(nsched):
+            b.set_tuning(bps, sched)
+            assert b.tuning()[0] == bps and b.tuning()[2] == sched
+            work = [U.clone() for U in states]
+            b.set_states(work)
+            b.step(0.5, 3)
+            assert b.status() == 0
+            for w, r in zip(work, ref):
+                assert torch.equal(w, r), (bps, sched)
+    times = tuning.autotune_batch(b, probs, states)
+    assert len(times) == most * nsched
+    choice = b.tuning()
+    b.set_tuning(0, 0)
+    assert tuning.autotune_batch(b, probs, states) == {}
+    assert b.tuning() == choice
     b.close()

@@ -86,7 +86,7 @@ def test_multistep_loss_gradient(env, case):
         g = torch.tensor(gm, dtype=torch.float64, requires_grad=grad)
         theta = A.theta_of(s)
         theta = torch.cat([g.view(1), theta[1:]])
-        states = A.rollout(s, I.prim_to_cons(W0, g.to("cuda")), theta, dts[:outputs[-1]], outputs=outputs)
+        states = A.rollout(s, I.prim_to_cons(s, W0, g), theta, dts[:outputs[-1]], outputs=outputs)
         L = I.multistep_loss(states, Td, md)
         if grad:
             L.backward()
@@ -135,3 +135,24 @@ def test_gamma_recovery_cylinder_subdomain_warm_cosine(env):
                     outputs=outputs, betas=(0.9, 0.9), schedule=lambda k: I.warm_cosine(k, 30, 80, 0.05, 5e-4))
     assert abs(h["gamma"][-1] - 2.0) < 5e-3
     assert h["loss"][-1] < 1e-4 * h["loss"][0]
+
+
+def test_initial_state_depends_on_gamma_through_the_energy_only(env):
+    """U0 = js_prim_to_cons(W0) at gamma; dU0/dgamma is -p/(gamma-1)^2 in the energy, 0 elsewhere."""
+    torch, B, I = env
+    p = W.riemann2d(24, ny=16).with_(gamma=1.4)
+    s = B.Solver.from_problem(p)
+    W0 = torch.tensor(np.random.default_rng(1).uniform(0.5, 2.0, (4, 16, 24)), device="cuda")
+    g = torch.tensor(1.4, dtype=torch.float64, requires_grad=True)
+    U = I.prim_to_cons(s, W0, g)
+    r, u, v, pr = W0
+    assert torch.allclose(U[3], pr / 0.4 + 0.5 * r * (u * u + v * v), rtol=1e-15, atol=0)
+    (dg,) = torch.autograd.grad(U[3].sum(), g, retain_graph=True)
+    assert float(dg) == pytest.approx(float((-pr / 0.4 ** 2).sum()), rel=1e-14)
+    (d0,) = torch.autograd.grad(U[:3].sum(), g, allow_unused=True)
+    assert d0 is None or float(d0) == 0.0
+    g2 = torch.tensor(1.6, dtype=torch.float64, requires_grad=True)
+    U2 = I.prim_to_cons(s, W0, g2)
+    assert torch.allclose(U2[3], pr / 0.6 + 0.5 * r * (u * u + v * v), rtol=1e-15, atol=0)
+    assert s._spec["gamma"] == 1.6
+    s.close()

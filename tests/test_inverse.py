@@ -33,13 +33,3 @@ def test_multistep_loss_is_the_mean_of_the_step_losses():
     assert got_all == pytest.approx(((S - T) ** 2).sum() / 5, rel=1e-14)
 
 
-def test_initial_state_depends_on_gamma_through_the_energy_only():
-    W0 = torch.tensor(np.random.default_rng(1).uniform(0.5, 2.0, (4, 2, 3)))
-    g = torch.tensor(1.4, dtype=torch.float64, requires_grad=True)
-    U = I.prim_to_cons(W0, g)
-    r, u, v, p = W0
-    assert torch.allclose(U[3], p / 0.4 + 0.5 * r * (u * u + v * v), rtol=1e-15, atol=0)
-    (dg,) = torch.autograd.grad(U[3].sum(), g, retain_graph=True)
-    assert float(dg) == pytest.approx(float((-p / 0.4 ** 2).sum()), rel=1e-14)
-    (d0,) = torch.autograd.grad(U[:3].sum(), g, allow_unused=True)
-    assert d0 is None or float(d0) == 0.0
