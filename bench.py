@@ -525,19 +525,27 @@ def run_batched(args):
     n_ro = args.rollout_steps
     roll = None
     if n_ro > 0:
-        fwd = [U.clone() for U in states]
-        batch.set_states(fwd)
         log = torch.zeros((n_ro, len(mine)), dtype=torch.float64, device="cuda")
+        lam_r = [torch.randn_like(U) for U in states]
+        # first round: allocates the rollout workspace (not timed)
+        batch.set_states([U.clone() for U in states])
+        batch.rollout_forward(0.5, log)
+        batch.rollout_vjp(log, lam_r)
         torch.cuda.synchronize()
+        # the plain forward run of the same steps: one launch, device CFL
+        batch.set_states([U.clone() for U in states])
         e0.record(stream)
         batch.step(0.5, n_ro, dt_log=log)
         e1.record(stream)
         e1.synchronize()
-        t_ro_f = e0.elapsed_time(e1)
+        t_ro_plain = e0.elapsed_time(e1)
+        # the checkpointed forward and its reverse
         batch.set_states([U.clone() for U in states])
-        lam_r = [torch.randn_like(U) for U in states]
-        batch.rollout_vjp(log, lam_r)
-        torch.cuda.synchronize()
+        e0.record(stream)
+        batch.rollout_forward(0.5, log)
+        e1.record(stream)
+        e1.synchronize()
+        t_ro_f = e0.elapsed_time(e1)
         e0.record(stream)
         batch.rollout_vjp(log, lam_r)
         e1.record(stream)
@@ -545,11 +553,12 @@ def run_batched(args):
         t_ro_b = e0.elapsed_time(e1)
         ok = ok and batch.status() == 0
         ck = int(round(n_ro ** 0.5))
-        roll = {"steps": n_ro, "checkpoint_every": ck, "ms_forward": t_ro_f, "ms_reverse": t_ro_b,
-                "ratio": t_ro_b / t_ro_f,
-                "note": "js_batch_rollout_vjp (forward to the checkpoints, then per segment: re-run "
-                        "keeping its states + one persistent reverse launch per step) / the batched "
-                        "forward run of the same steps (one launch, device CFL)"}
+        roll = {"steps": n_ro, "checkpoint_every": ck, "ms_forward_plain": t_ro_plain,
+                "ms_forward_checkpointed": t_ro_f, "ms_reverse": t_ro_b, "ratio": t_ro_b / t_ro_plain,
+                "note": "ratio: js_batch_rollout_vjp (per segment: re-run keeping its states + one "
+                        "persistent reverse launch per step, from the checkpoints js_batch_rollout_"
+                        "forward kept) / the plain batched forward run of the same steps (one "
+                        "launch, device CFL)"}
     info = batch.info()
     if rank == 0:
         print(json.dumps({

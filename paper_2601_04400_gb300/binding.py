@@ -95,6 +95,7 @@ SIGNATURES = {
     "js_batch_set_tuning": (_I, [_P, _I, _I]),
     "js_batch_get_tuning": (_I, [_P, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
     "js_batch_rollout_vjp": (_I, [_P, _I, _P, _I, C.POINTER(_P), C.POINTER(_P)]),
+    "js_batch_rollout_forward": (_I, [_P, _D, _I, _I, _P]),
     "js_batch_sync_status": (_I, [_P]),
     "js_batch_info": (_I, [_P, C.POINTER(_I), C.POINTER(_I), C.POINTER(C.c_longlong)]),
     "js_batch_instance": (_P, [_P, _I]),
@@ -552,6 +553,12 @@ class Batch:
         """Advance every registered state len(dts) steps of the given sizes: dts float64 CUDA
         tensor [n_steps, count]."""
         _check(lib().js_batch_step_fixed(self.handle, int(dts.shape[0]), _ptr(dts)), "js_batch_step_fixed")
+
+    def rollout_forward(self, cfl, dt_log, ckpt=0):
+        """Advance the registered states dt_log.shape[0] CFL steps, logging the step sizes into
+        dt_log (float64 CUDA tensor [n_steps, count]) and keeping checkpoints for rollout_vjp."""
+        _check(lib().js_batch_rollout_forward(self.handle, float(cfl), int(dt_log.shape[0]), int(ckpt), _ptr(dt_log)),
+               "js_batch_rollout_forward")
 
     def rollout_vjp(self, dt_log, lam, p_bar=None, ckpt=0):
         """Reverse of the rollout from the registered states with the step sizes dt_log

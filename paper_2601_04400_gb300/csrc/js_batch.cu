@@ -622,6 +622,8 @@ struct js_batch {
   void** d_ro = nullptr;        // device tables: U, cp[nck], seg[ckpt], work, lam, p_bar (x count each)
   long long* d_spre = nullptr;  // prefix sums of the state sizes (4 nx ny)
   std::vector<void*> ro_lam, ro_pbar;  // the lam / p_bar pointers the tables hold
+  const double* ro_fwd_log = nullptr;  // dt log of the rollout forward whose checkpoints are kept
+  std::vector<void*> ro_U;             // the registered-state pointers table block 0 holds
 };
 
 // accessors of a context's internals (defined in js_host.cu)
@@ -806,6 +808,7 @@ int js_batch_create(int count, const js_grid* grids, const js_params* params, co
 
 int js_batch_set_states(js_batch* b, double* const* U) {
   if (!b || !U) return JS_ERR_ARG;
+  b->ro_fwd_log = nullptr;
   for (int k = 0; k < b->count; ++k) {
     if (!U[k]) return JS_ERR_ARG;
     b->desc[k].U = U[k];
@@ -821,6 +824,7 @@ int js_batch_set_states(js_batch* b, double* const* U) {
 static int batch_launch(js_batch* b, double cfl, int n_steps, double* t_dev, double* dt_log, int extra,
                         double budget_s, const double* dt_in = nullptr, double* const* ustate = nullptr,
                         double* const* save = nullptr) {
+  if (!ustate) b->ro_fwd_log = nullptr;  // the registered states move: kept checkpoints are stale
   js::BatchArgs a;
   a.dt_in = dt_in;
   a.ustate = ustate;
@@ -902,7 +906,19 @@ int batch_copy(js_batch* b, void* const* src, void* const* dst) {
 int rollout_prepare(js_batch* b, int n_steps, int ckpt) {
   const int n = b->count;
   const int nck = (n_steps + ckpt - 1) / ckpt;
-  if (b->ro_steps == n_steps && b->ro_ckpt == ckpt && b->d_ro) return JS_OK;
+  if (b->ro_steps == n_steps && b->ro_ckpt == ckpt && b->d_ro) {
+    // the registered states' pointers (table block 0) may have changed since
+    bool same = true;
+    for (int k = 0; k < n && same; ++k) same = b->ro_U[k] == (void*)b->desc[k].U;
+    if (same) return JS_OK;
+    for (int k = 0; k < n; ++k) b->ro_U[k] = b->desc[k].U;
+    if (cudaMemcpyAsync(b->d_ro, b->ro_U.data(), sizeof(void*) * n, cudaMemcpyHostToDevice, b->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess)
+      return JS_ERR_CUDA;
+    return JS_OK;
+  }
+  b->ro_fwd_log = nullptr;
   if (cudaStreamSynchronize(b->stream) != cudaSuccess) return JS_ERR_CUDA;
   for (double* p : b->ro_buf) cudaFree(p);
   b->ro_buf.assign(n, nullptr);
@@ -928,12 +944,31 @@ int rollout_prepare(js_batch* b, int n_steps, int ckpt) {
   if (cudaMemcpy(b->d_ro, tab.data(), sizeof(void*) * tab.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(b->d_spre, spre.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice) != cudaSuccess)
     return JS_ERR_CUDA;
+  b->ro_U.assign(tab.begin(), tab.begin() + n);
   b->ro_steps = n_steps;
   b->ro_ckpt = ckpt;
   b->ro_nck = nck;
   return JS_OK;
 }
 }  // namespace
+
+int js_batch_rollout_forward(js_batch* b, double cfl, int n_steps, int ckpt, double* dt_log) {
+  if (!b || !b->states_set || n_steps < 1 || !dt_log || !(cfl > 0.0)) return JS_ERR_ARG;
+  if (ckpt <= 0) ckpt = (int)std::lround(std::sqrt((double)n_steps));
+  if (ckpt < 1) ckpt = 1;
+  if (ckpt > n_steps) ckpt = n_steps;
+  int rc = rollout_prepare(b, n_steps, ckpt);
+  if (rc) return rc;
+  const int n = b->count, nck = b->ro_nck;
+  void** T = b->d_ro;
+  for (int c = 0; c < nck; ++c) {
+    const int len = std::min(ckpt, n_steps - c * ckpt);
+    if ((rc = batch_copy(b, T, T + (size_t)(1 + c) * n))) return rc;
+    if ((rc = batch_launch(b, cfl, len, nullptr, dt_log + (size_t)c * ckpt * n, 0, 2.0))) return rc;
+  }
+  b->ro_fwd_log = dt_log;  // after the launches (which clear it)
+  return JS_OK;
+}
 
 int js_batch_rollout_vjp(js_batch* b, int n_steps, const double* dt_log, int ckpt, double* const* lam,
                          double* const* p_bar) {
@@ -966,13 +1001,16 @@ int js_batch_rollout_vjp(js_batch* b, int n_steps, const double* dt_log, int ckp
     b->ro_lam = hl;
     b->ro_pbar = hp;
   }
-  // forward: checkpoint c holds the state after c * ckpt steps
-  if ((rc = batch_copy(b, U, cp(0)))) return rc;
-  for (int c = 1; c < nck; ++c) {
-    if ((rc = batch_copy(b, cp(c - 1), cp(c)))) return rc;
-    if ((rc = batch_launch(b, 0.5, ckpt, nullptr, nullptr, 0, 2.0, dt_log + (size_t)(c - 1) * ckpt * n,
-                           reinterpret_cast<double* const*>(cp(c)))))
-      return rc;
+  // forward: checkpoint c holds the state after c * ckpt steps (kept by js_batch_rollout_forward
+  // when it ran these steps and nothing moved the registered states since)
+  if (b->ro_fwd_log != dt_log) {
+    if ((rc = batch_copy(b, U, cp(0)))) return rc;
+    for (int c = 1; c < nck; ++c) {
+      if ((rc = batch_copy(b, cp(c - 1), cp(c)))) return rc;
+      if ((rc = batch_launch(b, 0.5, ckpt, nullptr, nullptr, 0, 2.0, dt_log + (size_t)(c - 1) * ckpt * n,
+                             reinterpret_cast<double* const*>(cp(c)))))
+        return rc;
+    }
   }
   // reverse, segment by segment: re-run the segment keeping its states, then reverse its steps
   for (int c = nck - 1; c >= 0; --c) {

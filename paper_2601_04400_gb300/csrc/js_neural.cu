@@ -591,7 +591,7 @@ __global__ void __launch_bounds__(128) nn_conv_tc_kernel(NnArgs n, const void* i
   unsigned char* sA = smem_raw;
   unsigned char* sB = smem_raw + TC_AREGION;
   float* sbias = reinterpret_cast<float*>(sB + 9 * BTAP);
-  __shared__ __align__(8) unsigned long long bar;
+  __shared__ __align__(8) unsigned long long bar[2];
   __shared__ uint32_t tmem_base;
   int nxs[2], nys[2];
   for (int d = 0; d < 2; ++d) {
@@ -602,11 +602,14 @@ __global__ void __launch_bounds__(128) nn_conv_tc_kernel(NnArgs n, const void* i
   if ((int)blockIdx.x >= items) return;  // uniform per block, before any allocation
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(smem_u32(&tmem_base))
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(smem_u32(&tmem_base))
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  if (tid == 0) mbar_init(&bar);
+  if (tid == 0) {
+    mbar_init(&bar[0]);
+    mbar_init(&bar[1]);
+  }
   __nv_bfloat16* B16 = reinterpret_cast<__nv_bfloat16*>(sB);
   for (int k = tid; k < 9 * CIN * N; k += 128) {
     const int tap = k / (CIN * N), r = k % (CIN * N), ci = r / N, co = r % N;
@@ -622,7 +625,7 @@ __global__ void __launch_bounds__(128) nn_conv_tc_kernel(NnArgs n, const void* i
   const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
   constexpr uint32_t idesc = umma_idesc_bf16(TC_M, N);
   constexpr long long kBudget = 2000000000LL;  // about one second of SM clock
-  unsigned phase = 0;
+  unsigned phase0 = 0u, phase1 = 0u;  // mbarrier phases of bar[0], bar[1] (scalars: no local memory)
   bool ok = true;
   for (int it = blockIdx.x; it < items && ok; it += gridDim.x) {
     const int d = (it < items0) ? 0 : 1;
@@ -648,11 +651,10 @@ __global__ void __launch_bounds__(128) nn_conv_tc_kernel(NnArgs n, const void* i
       }
       cp_async_commit();
     };
-    load_row(h0 - 1);
-    load_row(h0);
-    load_row(h0 + 1);
-    for (int h = h0; h < h1; ++h) {
-      cp_async_wait<0>();  // this thread's copies of rows up to h + 1 have landed
+    // MMAs of output row r (input rows r-1 .. r+1 in their ring slots) into accumulator ai
+    // (tensor-memory columns 32 ai ..), completion signalled on bar[ai]
+    auto issue = [&](int r, int ai) {
+      cp_async_wait<0>();  // this thread's copies of the rows issued so far (up to r + 1) have landed
       // shared stores of the generic proxy must be visible to the tensor core (async proxy)
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -662,29 +664,42 @@ __global__ void __launch_bounds__(128) nn_conv_tc_kernel(NnArgs n, const void* i
         int acc = 0;
         for (int tap = 0; tap < 9; ++tap) {
           const int ky = tap / 3, kx = tap % 3;
-          const uint32_t slot = a0 + ((h + ky - 1 + TC_NSLOT) % TC_NSLOT) * SLOT;
+          const uint32_t slot = a0 + ((r + ky - 1 + TC_NSLOT) % TC_NSLOT) * SLOT;
           for (int kc = 0; kc < KG / 2; ++kc) {
             const uint64_t ad = umma_smem_desc(slot + 2 * kc * GSTRIDE + kx * 16, GSTRIDE, 128);
             const uint64_t bd = umma_smem_desc(b0 + tap * BTAP + 2 * kc * N * 16, N * 16, 128);
-            umma_bf16(tmem, ad, bd, idesc, acc);
+            umma_bf16(tmem + (uint32_t)(ai * 32), ad, bd, idesc, acc);
             acc = 1;
           }
         }
-        umma_commit(&bar);
+        umma_commit(&bar[ai]);
       }
-      // row h + 2 into the slot of row h - 2: the MMAs that read it (row h - 1's) have completed
-      if (h + 2 <= h1) load_row(h + 2);
-      // every thread waits (bounded); the outcome is made uniform so that the block leaves the
-      // loop together on a timeout
-      ok = __syncthreads_and(mbar_wait(&bar, phase, kBudget) ? 1 : 0) != 0;
+    };
+    // two accumulators: the MMAs of row h + 1 run while row h's epilogue reads the other one
+    load_row(h0 - 1);
+    load_row(h0);
+    load_row(h0 + 1);
+    if (h0 + 2 <= h1) load_row(h0 + 2);
+    issue(h0, 0);
+    for (int h = h0; h < h1; ++h) {
+      const int ai = (h - h0) & 1;
+      const bool next = h + 1 < h1;
+      if (next) issue(h + 1, ai ^ 1);  // rows h .. h + 2 are in their slots
+      // every thread waits (bounded) for row h's MMAs; the outcome is made uniform so that the
+      // block leaves the loop together on a timeout
+      const unsigned ph = ai ? phase1 : phase0;
+      ok = __syncthreads_and(mbar_wait(&bar[ai], ph, kBudget) ? 1 : 0) != 0;
       if (!ok) {
         if (tid == 0) atomicOr(n.err, ERR_TIMEOUT_BIT);
-        mbar_wait(&bar, phase, kBudget);  // drain before the accumulator is released
+        mbar_wait(&bar[ai], ph, kBudget);  // drain before the accumulators are released
+        if (next) mbar_wait(&bar[ai ^ 1], ai ? phase0 : phase1, kBudget);
         break;
       }
-      phase ^= 1u;
+      if (ai) phase1 ^= 1u; else phase0 ^= 1u;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+      // row h + 3 into the slot of row h - 1, whose last reader (row h's MMAs) has completed
+      if (h + 3 <= h1) load_row(h + 3);
+      const uint32_t taddr = tmem + (uint32_t)(ai * 32) + ((uint32_t)(warp * 32) << 16);
       const int gx = x0 + warp * 32 + lane;
       const long long o = (long long)h * Wd + gx;
 #pragma unroll
@@ -732,7 +747,7 @@ __global__ void __launch_bounds__(128) nn_conv_tc_kernel(NnArgs n, const void* i
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem) : "memory");
 }
 
 // network input from an FP64 image / scaled FP64 output (js_nn_eval)

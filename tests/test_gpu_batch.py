@@ -447,3 +447,37 @@ def test_launch_tuning_keeps_results_and_the_tuner_caches_its_choice(env, tmp_pa
     assert tuning.autotune_batch(b, probs, states) == {}
     assert b.tuning() == choice
     b.close()
+
+
+def test_rollout_forward_keeps_checkpoints_for_the_reverse(env):
+    """js_batch_rollout_forward = js_batch_step with the CFL rule (states and logged step sizes bit
+    for bit); the reverse that follows reuses its checkpoints and equals a reverse that runs its
+    own forward from the initial states."""
+    torch, B = env
+    probs = _mixed_cases()
+    states = _states(torch, probs)
+    n = 11
+    b = B.Batch(probs)
+    plain = [U.clone() for U in states]
+    b.set_states(plain)
+    log_a = torch.zeros((n, len(probs)), dtype=torch.float64, device="cuda")
+    b.step(0.5, n, dt_log=log_a)
+    fwd = [U.clone() for U in states]
+    b.set_states(fwd)
+    log_b = torch.zeros((n, len(probs)), dtype=torch.float64, device="cuda")
+    b.rollout_forward(0.5, log_b, ckpt=3)
+    assert b.status() == 0
+    assert torch.equal(log_a, log_b)
+    for x, y in zip(fwd, plain):
+        assert torch.equal(x, y)
+    rng = np.random.default_rng(12)
+    lam_T = [torch.tensor(rng.standard_normal(U.shape), device="cuda") for U in states]
+    reuse = [l.clone() for l in lam_T]
+    b.rollout_vjp(log_b, reuse, ckpt=3)
+    b.set_states([U.clone() for U in states])
+    fresh = [l.clone() for l in lam_T]
+    b.rollout_vjp(log_b, fresh, ckpt=3)
+    assert b.status() == 0
+    for x, y in zip(reuse, fresh):
+        assert torch.equal(x, y)
+    b.close()
