@@ -40,7 +40,10 @@ NN_FLOPS_PER_CELL_STAGE = 2 * 2 * 6336
 # from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of this bench's default
 # run with the TMA-staged variant 0 and the current kernel; None for other workloads or
 # variants.
-STAGE_TRAFFIC_BYTES = {("shock_cylinder", 0): 288.9e6}
+STAGE_TRAFFIC_BYTES = {("shock_cylinder", 0): 288.9e6, ("riemann2d", 0): 111.2e6}
+# DRAM bytes per step of the persistent batched forward kernel on the 256-instance workload: an
+# ncu capture of one 2-step launch (19.26 GB), scaled by the steps of a launch
+BATCH_TRAFFIC_PER_STEP = 9.63e9
 L2_FLUSH_BYTES = 256 << 20
 METRIC = "FP64 cell-updates/s per RK step on 1 GB300 (% roofline); adjoint/forward time ratio"
 
@@ -579,7 +582,9 @@ def run_batched(args):
                          "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": FLOPS_PER_CELL_STAGE["shock_cylinder"] * 3 * cells * args.steps
                          / (t_batch * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
-                         "traffic": None, "flops_per_cell_stage": FLOPS_PER_CELL_STAGE["shock_cylinder"]},
+                         "traffic": BATCH_TRAFFIC_PER_STEP * args.steps if args.instances == 256 and world == 1
+                         else None,
+                         "flops_per_cell_stage": FLOPS_PER_CELL_STAGE["shock_cylinder"]},
             "gpu_launches": 1, "clocks": sampler.summary(),
             "one_at_a_time": {"value": local_cells * args.steps / (t_seq * 1e-3), "ms_per_step": t_seq / args.steps,
                               "how": "rank 0's instances one after another, each js_step_cfl for all steps "

@@ -523,9 +523,10 @@ __global__ void __launch_bounds__(NTHR) nn_wgrad_f32_kernel(NnArgs n, const void
 // ---------------------------------------------------------------------------------------
 constexpr int TC_M = 128;                 // pixels per block
 constexpr int TC_COLS = TC_M + 2;         // with the halo
-// shared bytes of the input row ring: 4 rows x 130 pixels x 32 channels (the widest input), BF16
+// shared bytes of the input row ring of a layer with CIN input channels: 4 rows x 130 pixels x
+// CIN channels, BF16 (sized per layer, so that the narrower layers fit more blocks per SM)
 constexpr int TC_NSLOT = 4;
-constexpr int TC_AREGION = 4 * TC_NSLOT * TC_COLS * 16;
+__host__ __device__ constexpr int tc_aregion(int cin) { return TC_NSLOT * (cin / 8) * TC_COLS * 16; }
 
 // 16-byte asynchronous global -> shared copy (zero-filled, nothing read, when !valid)
 __device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
@@ -586,10 +587,11 @@ __global__ void __launch_bounds__(128) nn_conv_tc_kernel(NnArgs n, const void* i
   constexpr int GSTRIDE = TC_COLS * 16;      // bytes of one channel group of one row slot
   constexpr int SLOT = KG * GSTRIDE;         // bytes of one input row slot
   constexpr int BTAP = KG * N * 16;          // bytes of one tap of the weights
-  static_assert(TC_NSLOT * SLOT <= TC_AREGION, "row slots");
+  constexpr int AREGION = tc_aregion(CIN);
+  static_assert(TC_NSLOT * SLOT <= AREGION, "row slots");
   extern __shared__ __align__(16) unsigned char smem_raw[];  // 16-byte rows: no swizzle
   unsigned char* sA = smem_raw;
-  unsigned char* sB = smem_raw + TC_AREGION;
+  unsigned char* sB = smem_raw + AREGION;
   float* sbias = reinterpret_cast<float*>(sB + 9 * BTAP);
   __shared__ __align__(8) unsigned long long bar[2];
   __shared__ uint32_t tmem_base;
@@ -1142,7 +1144,7 @@ template <int CIN, int COUT, int ACT, int MODE = 0, int CINR = CIN>
 cudaError_t conv_tc(const NnArgs& n, const void* inh, void* out, int woff, cudaStream_t s, void* outh = nullptr,
                     const void* aprev = nullptr) {
   constexpr int N = (COUT + 15) / 16 * 16;
-  const size_t sm = TC_AREGION + 9 * (CIN / 8) * N * 16 + COUT * sizeof(float);
+  const size_t sm = tc_aregion(CIN) + 9 * (CIN / 8) * N * 16 + COUT * sizeof(float);
   auto k = nn_conv_tc_kernel<CIN, COUT, ACT, MODE, CINR>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
