@@ -244,9 +244,11 @@ def test_full_batched_configuration(env):
 # checkpointed rollout reverse
 # ---------------------------------------------------------------------------------------
 def _mixed_cases():
-    """Uneven grids, viscous and Euler instances, immersed bodies of different sizes."""
+    """Uneven grids, viscous and Euler instances, immersed bodies of different sizes, and one
+    instance without a body (no ghost cells: empty work lists in the IB phases)."""
     out = W.batched_cases(3, seed=21, nx_choices=(64, 96, 128), ny_choices=(48, 64))
     out.append(W.shock_cylinder(nx=80, ny=56, mach=2.4, radius=0.45, viscous=False))
+    out.append(W.riemann2d(48, ny=40))
     out.append(W.shock_cylinder(nx=112, ny=40, mach=1.8, radius=0.35, Re=300.0))
     return out
 
