@@ -141,16 +141,32 @@ __device__ __forceinline__ void cfl_block_reduce(double& rate, double* rmin) {
   }
 }
 
-__global__ void cfl_pass1_kernel(const double* __restrict__ U, long long n, int two_d,
+// the state the reduction reads: the user layout [4][ny][nx] (PADDED false: cell t at t, planes
+// n apart) or a context's padded buffer (cell t = (i, j) at off + j pitch + i, planes `plane` apart)
+struct CflSrc {
+  const double* U;
+  long long plane, off;
+  int nx, pitch;
+};
+template <bool PADDED>
+__device__ __forceinline__ long long cfl_at(const CflSrc& q, long long t) {
+  return PADDED ? q.off + (t / q.nx) * q.pitch + t % q.nx : t;
+}
+
+template <bool PADDED>
+__global__ void cfl_pass1_kernel(CflSrc q, long long n, int two_d,
                                  const unsigned char* __restrict__ tag, double gamma, double dx, double dy,
                                  double idx, double idy, unsigned long long* __restrict__ red,
                                  double* __restrict__ bmax) {
   double rate = 0.0, rmin = __longlong_as_double(0x7ff0000000000000LL);
+  const double* __restrict__ U = q.U;
+  const long long P = q.plane;
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
        t += (long long)gridDim.x * blockDim.x) {
     if (tag && tag[t] != 0) continue;
-    const double r = U[t];
-    rate = fmax(rate, cfl_rate_fast(r, U[n + t], U[2 * n + t], U[3 * n + t], gamma, dx, dy, idx, idy, two_d != 0));
+    const long long e = cfl_at<PADDED>(q, t);
+    const double r = U[e];
+    rate = fmax(rate, cfl_rate_fast(r, U[P + e], U[2 * P + e], U[3 * P + e], gamma, dx, dy, idx, idy, two_d != 0));
     rmin = fmin(rmin, r);
   }
   cfl_block_reduce(rate, &rmin);
@@ -172,13 +188,16 @@ __device__ __forceinline__ bool same_bits(double a, double b) {
 // leaves the IEEE rate to that neighbour (also a candidate, in a block that passes the test):
 // of a uniform run of cells, only the first takes it.  The threads of a warp hold consecutive
 // cells, so the neighbour's state comes from the next lower lane.
-__global__ void cfl_pass2_kernel(const double* __restrict__ U, long long n, int nx, int two_d,
+template <bool PADDED>
+__global__ void cfl_pass2_kernel(CflSrc q, long long n, int nx, int two_d,
                                  const unsigned char* __restrict__ tag, double gamma, double dx, double dy,
                                  double idx, double idy, unsigned long long* __restrict__ red,
                                  const double* __restrict__ bmax) {
   const double thr = __longlong_as_double((long long)red[2]) * (1.0 - CFL_MARGIN);
   if (!(bmax[blockIdx.x] >= thr)) return;  // the same for the whole block
   const int lane = threadIdx.x & 31;
+  const double* __restrict__ U = q.U;
+  const long long P = q.plane;
   const long long stride = (long long)gridDim.x * blockDim.x;
   double rate = 0.0;
   for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x - lane); base < n; base += stride) {
@@ -188,20 +207,22 @@ __global__ void cfl_pass2_kernel(const double* __restrict__ U, long long n, int 
     double r = 0.0, mx = 0.0, my = 0.0, E = 0.0;
     if (in) {
       fl = !(tag && tag[t] != 0);
-      r = U[t];
-      mx = U[n + t];
-      my = U[2 * n + t];
-      E = U[3 * n + t];
+      const long long e = cfl_at<PADDED>(q, t);
+      r = U[e];
+      mx = U[P + e];
+      my = U[2 * P + e];
+      E = U[3 * P + e];
     }
     double rl = __shfl_up_sync(0xffffffffu, r, 1), mxl = __shfl_up_sync(0xffffffffu, mx, 1);
     double myl = __shfl_up_sync(0xffffffffu, my, 1), El = __shfl_up_sync(0xffffffffu, E, 1);
     bool fll = __shfl_up_sync(0xffffffffu, fl ? 1 : 0, 1) != 0;
     if (lane == 0 && in && t > 0) {
       fll = !(tag && tag[t - 1] != 0);
-      rl = U[t - 1];
-      mxl = U[n + t - 1];
-      myl = U[2 * n + t - 1];
-      El = U[3 * n + t - 1];
+      const long long e = cfl_at<PADDED>(q, t - 1);
+      rl = U[e];
+      mxl = U[P + e];
+      myl = U[2 * P + e];
+      El = U[3 * P + e];
     }
     if (in && fl && cfl_rate_fast(r, mx, my, E, gamma, dx, dy, idx, idy, two_d != 0) >= thr) {
       const bool same = (t % nx != 0) && fll && same_bits(r, rl) && same_bits(mx, mxl) && same_bits(my, myl) &&
@@ -516,17 +537,26 @@ cudaError_t launch_cfl_dt(const unsigned long long* red, double cfl, double dx, 
 }
 
 cudaError_t launch_cfl(const double* U, const Lay& lay, const unsigned char* tag, double gamma, double dx,
-                       double dy, unsigned long long* red, double* bmax, cudaStream_t s) {
+                       double dy, unsigned long long* red, double* bmax, cudaStream_t s, bool padded) {
   cfl_init_kernel<<<1, 1, 0, s>>>(red);
   const long long n = (long long)lay.nx * lay.ny;
   const int bs = 256;
   long long blocks = (n + bs - 1) / bs;
   if (blocks > CFL_MAX_BLOCKS) blocks = CFL_MAX_BLOCKS;
   const int two_d = lay.ny > 1 ? 1 : 0;
+  const CflSrc q{U, padded ? lay.plane : n, padded ? lay.idx(0, 0) : 0, lay.nx, padded ? lay.pitch : lay.nx};
   // both passes on the same grid: a block of pass 2 visits the cells its pass-1 maximum covers
-  cfl_pass1_kernel<<<(unsigned)blocks, bs, 0, s>>>(U, n, two_d, tag, gamma, dx, dy, 1.0 / dx, 1.0 / dy, red, bmax);
-  cfl_pass2_kernel<<<(unsigned)blocks, bs, 0, s>>>(U, n, lay.nx, two_d, tag, gamma, dx, dy, 1.0 / dx, 1.0 / dy, red,
-                                                    bmax);
+  if (padded) {
+    cfl_pass1_kernel<true><<<(unsigned)blocks, bs, 0, s>>>(q, n, two_d, tag, gamma, dx, dy, 1.0 / dx, 1.0 / dy, red,
+                                                            bmax);
+    cfl_pass2_kernel<true><<<(unsigned)blocks, bs, 0, s>>>(q, n, lay.nx, two_d, tag, gamma, dx, dy, 1.0 / dx,
+                                                            1.0 / dy, red, bmax);
+  } else {
+    cfl_pass1_kernel<false><<<(unsigned)blocks, bs, 0, s>>>(q, n, two_d, tag, gamma, dx, dy, 1.0 / dx, 1.0 / dy, red,
+                                                             bmax);
+    cfl_pass2_kernel<false><<<(unsigned)blocks, bs, 0, s>>>(q, n, lay.nx, two_d, tag, gamma, dx, dy, 1.0 / dx,
+                                                             1.0 / dy, red, bmax);
+  }
   return cudaGetLastError();
 }
 

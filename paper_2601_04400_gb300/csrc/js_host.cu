@@ -753,12 +753,16 @@ int js_step_cfl(js_ctx* c, double* U, double cfl, int n_steps, double* t_dev, do
   const double rb[3] = {1.0, 0.25, 2.0 / 3.0};
   StageArgs a = base_args(c);
   a.dtc = c->dtc;
+  if (n_steps == 0) return JS_OK;
+  // the state stays in the padded buffer N from the first step to the last
+  JS_CUDA(js::launch_pack(U, c->N, c->lay, c->stream));
+  ++c->launches;
   for (int k = 0; k < n_steps; ++k) {
-    JS_CUDA(js::launch_cfl(U, c->lay, c->tag, c->p.gamma, c->g.dx, c->g.dy, c->red, c->cfl_bmax, c->stream));
+    JS_CUDA(js::launch_cfl(c->N, c->lay, c->tag, c->p.gamma, c->g.dx, c->g.dy, c->red, c->cfl_bmax, c->stream,
+                           true));
     JS_CUDA(js::launch_cfl_dt(c->red, cfl, c->g.dx, c->g.dy, c->p.nu, c->p.mu, lim, hmin, t_dev, t_end, c->dtc,
                               dt_log, k, c->err, c->stream));
-    JS_CUDA(js::launch_pack(U, c->N, c->lay, c->stream));
-    c->launches += 5;
+    c->launches += 4;
     for (int s = 0; s < 3; ++s) {
       int rc = fill_halos(c, in[s], ieee);
       if (rc) return rc;
@@ -771,9 +775,9 @@ int js_step_cfl(js_ctx* c, double* U, double cfl, int n_steps, double* t_dev, do
       rc = ieee ? stage_fwd(c, a, false, 0.0, s) : stage(c, a, visc, false);
       if (rc) return rc;
     }
-    JS_CUDA(js::launch_unpack(c->N, U, c->lay, c->stream));
-    ++c->launches;
   }
+  JS_CUDA(js::launch_unpack(c->N, U, c->lay, c->stream));
+  ++c->launches;
   return JS_OK;
 }
 

@@ -247,7 +247,8 @@ constexpr int CFL_MAX_BLOCKS = 152 * 8;
 cudaError_t launch_cfl_dt(const unsigned long long* red, double cfl, double dx, double dy, double nu, double mu,
                           double lim, double hmin, double* t, double t_end, double* dtc, double* dt_log, int k,
                           int* err, cudaStream_t s);
+// (padded: U is a context's padded buffer, e.g. the state N between the steps of js_step_cfl)
 cudaError_t launch_cfl(const double* U, const Lay& lay, const unsigned char* tag, double gamma, double dx,
-                       double dy, unsigned long long* red, double* bmax, cudaStream_t s);
+                       double dy, unsigned long long* red, double* bmax, cudaStream_t s, bool padded = false);
 
 }  // namespace js
