@@ -240,7 +240,10 @@ int js_rows_unpack(js_ctx* ctx, double* U, int row0, int nrows, const double* bu
  *   norm   host array mean[4], sd[4] (> 0), scale[4] (copied)
  *   precision  JS_NN_F64 (FP64 network arithmetic), JS_NN_F32 (FP32 on the CUDA cores) or
  *          JS_NN_BF16 (the 16->32 and 32->4 layers of the forward pass on the tensor cores with
- *          BF16 operands and FP32 accumulation, the rest FP32); the solver stays FP64
+ *          BF16 operands and FP32 accumulation, the rest FP32); the solver stays FP64.
+ *          In BF16 precision the stages that no reverse pass reads evaluate the whole network
+ *          in one launch (activations kept on chip); JS_NN_BF16 | JS_NN_LAYERWISE runs its
+ *          three layers as separate launches instead, with bit-identical results
  * Applies to js_rhs, js_step, the taped steps and the reverse calls of this context (not to
  * js_batch_*).  The first call allocates the network workspace (before any stream capture).
  * Returns JS_ERR_ARG for a bad norm or precision, JS_ERR_NOMEM. */
@@ -248,6 +251,7 @@ int js_rows_unpack(js_ctx* ctx, double* U, int row0, int nrows, const double* bu
 #define JS_NN_F64 0
 #define JS_NN_F32 1
 #define JS_NN_BF16 2
+#define JS_NN_LAYERWISE 0x100
 int js_set_neural(js_ctx* ctx, const double* w, double* w_bar, const double* norm, int precision);
 
 /* The network of js_set_neural alone (its parameters, normalisation scale and precision) on one

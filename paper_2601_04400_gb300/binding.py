@@ -20,6 +20,7 @@ JS_TAPE_WENO = 1
 JS_STAGE_INTERNALS = 16
 JS_NN_NPARAM = 6388
 JS_NN_F64, JS_NN_F32, JS_NN_BF16 = 0, 1, 2
+JS_NN_LAYERWISE = 0x100
 
 _lib = None
 
@@ -328,8 +329,10 @@ class Solver:
         """Neural flux on (w: float64 CUDA tensor of JS_NN_NPARAM parameters, kept by
         reference: later updates in place take effect; norm: mean[4], sd[4], scale[4] of the
         frame channels; w_bar: float64 CUDA tensor that reverse calls add the parameter
-        gradient to, or None; precision: "fp64", "fp32" or "bf16" (tensor-core layers);
-        fp32=True is precision="fp32") or off (w = None)."""
+        gradient to, or None; precision: "fp64", "fp32", "bf16" (tensor-core layers; the
+        network in one fused launch where no reverse pass reads its activations) or
+        "bf16-layerwise" (the same results, one launch per layer); fp32=True is
+        precision="fp32") or off (w = None)."""
         if w is None:
             _check(lib().js_set_neural(self.ctx, None, None, None, 0), "js_set_neural")
             self._nn = None
@@ -338,7 +341,8 @@ class Solver:
             raise ValueError("w and w_bar hold %d parameters" % JS_NN_NPARAM)
         nm = np.ascontiguousarray(np.asarray(norm, dtype=np.float64).reshape(12))
         prec = precision or ("fp32" if fp32 else "fp64")
-        code = {"fp64": JS_NN_F64, "fp32": JS_NN_F32, "bf16": JS_NN_BF16}[prec]
+        code = {"fp64": JS_NN_F64, "fp32": JS_NN_F32, "bf16": JS_NN_BF16,
+                "bf16-layerwise": JS_NN_BF16 | JS_NN_LAYERWISE}[prec]
         _check(lib().js_set_neural(self.ctx, _ptr(w), None if w_bar is None else _ptr(w_bar),
                                    nm.ctypes.data_as(C.c_void_p), code), "js_set_neural")
         self._nn = (w, w_bar, nm)  # keep the device buffers alive while the library uses them

@@ -1286,6 +1286,8 @@ int js_set_neural(js_ctx* c, const double* w, double* w_bar, const double* norm,
     c->nn_on = false;
     return JS_OK;
   }
+  const bool layerwise = (precision & JS_NN_LAYERWISE) != 0;
+  precision &= ~JS_NN_LAYERWISE;
   if (!norm || (precision != JS_NN_F64 && precision != JS_NN_F32 && precision != JS_NN_BF16)) return JS_ERR_ARG;
   for (int k = 0; k < 4; ++k)
     if (!(norm[4 + k] > 0.0) || !std::isfinite(norm[k]) || !std::isfinite(norm[8 + k])) return JS_ERR_ARG;
@@ -1330,6 +1332,7 @@ int js_set_neural(js_ctx* c, const double* w, double* w_bar, const double* norm,
   n.A2h = c->nn_bf16[1];
   n.fp32 = (precision != JS_NN_F64) ? 1 : 0;
   n.bf16 = (precision == JS_NN_BF16) ? 1 : 0;
+  n.fused = layerwise ? 0 : 1;
   n.keep = 0;
   n.fwd_ready = 0;
   n.err = c->err;

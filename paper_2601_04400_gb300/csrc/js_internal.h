@@ -135,6 +135,7 @@ struct NnArgs {
   int keep;                   // 1: the FP32 activations A1, A2 are written (a reverse pass reads
                               //   them); 0: BF16 forward-only stages skip them
   int fwd_ready;              // reverse: X, A1, A2, T3 of this stage's forward are in place
+  int fused;                  // BF16 forward-only stages: the whole network in one launch
 };
 
 // forward: images of the stage input (primitives Q, plane qplane) and the network, into T3

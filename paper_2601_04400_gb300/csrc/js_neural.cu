@@ -752,6 +752,241 @@ __global__ void __launch_bounds__(128) nn_conv_tc_kernel(NnArgs n, const void* i
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem) : "memory");
 }
 
+// ---------------------------------------------------------------------------------------
+// The whole network in one launch for forward-only BF16 stages: layer 1 (FP32 on the CUDA
+// cores, the arithmetic of nn_conv_f32_kernel) and layers 2 and 3 (tcgen05, the MMA sequence of
+// nn_conv_tc_kernel), so the results equal the three separate launches bit for bit, while the
+// 16- and 32-channel activations never leave shared memory.
+//
+// A block owns a 128-pixel-wide strip (local pixel p at x = x0 - 2 + p; layer 1 is exact on all
+// 128 pixels, layer 2 on 1..126, layer 3 on 2..125, so a strip yields 124 outputs) and a band of
+// output rows.  Step s of the band computes layer 3 on row s, layer 2 on row s + 2 and layer 1 on
+// row s + 4: each layer reads only rows the step before produced, so one thread issues the
+// MMAs of both tensor-core layers at the start of the step and they run while all threads
+// compute layer 1 on the CUDA cores; then one bounded mbarrier wait and the epilogues.
+//   rings: FP32 input rows (4 slots: rows s+3..s+5 read, row s+6 in flight), layer-1 and
+//   layer-2 rows as BF16 core matrices (3 slots each: a slot is rewritten only after the MMAs
+//   that read it have completed)
+// ---------------------------------------------------------------------------------------
+constexpr int NF_OUT = TC_M - 4;                 // output pixels per strip
+constexpr int NF_XS = 4, NF_AS = 3;              // ring slots
+constexpr int NF_XSLOT = 4 * TC_COLS * 4;        // FP32 input row: 4 channels x 130 pixels
+constexpr int NF_A1G = TC_COLS * 16;             // one 8-channel group of a BF16 row (core matrices)
+constexpr int NF_A1SLOT = 2 * NF_A1G;            // 16 channels
+constexpr int NF_A2SLOT = 4 * NF_A1G;            // 32 channels
+constexpr int NF_B2TAP = 2 * 32 * 16;            // layer-2 weights of one tap: [group 2][co 32][8]
+constexpr int NF_B3TAP = 4 * 16 * 16;            // layer-3 weights of one tap: [group 4][co 16][8]
+constexpr int NF_OFF_A2 = NF_AS * NF_A1SLOT;
+constexpr int NF_OFF_B2 = NF_OFF_A2 + NF_AS * NF_A2SLOT;
+constexpr int NF_OFF_B3 = NF_OFF_B2 + 9 * NF_B2TAP;
+constexpr int NF_OFF_X = NF_OFF_B3 + 9 * NF_B3TAP;
+constexpr int NF_OFF_W1 = NF_OFF_X + NF_XS * NF_XSLOT;
+constexpr int NF_OFF_BIAS = NF_OFF_W1 + 36 * 16 * 4;
+constexpr int NF_SMEM = NF_OFF_BIAS + (16 + 32 + 4) * 4;
+__host__ __device__ constexpr int nf_slot4(int r) { return (r + 16) & 3; }   // rows >= -16
+__host__ __device__ constexpr int nf_slot3(int r) { return (r + 15) % 3; }   // rows >= -15
+
+__global__ void __launch_bounds__(128) nn_net_tc_kernel(NnArgs n, int band) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* sA1 = smem_raw;
+  unsigned char* sA2 = smem_raw + NF_OFF_A2;
+  float* sX = reinterpret_cast<float*>(smem_raw + NF_OFF_X);
+  float* sW1 = reinterpret_cast<float*>(smem_raw + NF_OFF_W1);
+  float* sb1 = reinterpret_cast<float*>(smem_raw + NF_OFF_BIAS);
+  float* sb2 = sb1 + 16;
+  float* sb3 = sb2 + 32;
+  __shared__ __align__(8) unsigned long long bar;
+  __shared__ uint32_t tmem_base;
+  int nxs[2], nys[2];
+  for (int d = 0; d < 2; ++d) {
+    nxs[d] = (d < n.nimg) ? (n.W[d] + NF_OUT - 1) / NF_OUT : 0;
+    nys[d] = (d < n.nimg) ? (n.H[d] + band - 1) / band : 0;
+  }
+  const int items0 = nxs[0] * nys[0];
+  if ((int)blockIdx.x >= items0 + nxs[1] * nys[1]) return;  // uniform per block, before any allocation
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(smem_u32(&tmem_base))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) mbar_init(&bar);
+  // weights: layer 1 FP32 [ci][ky][kx][co]; layers 2 and 3 BF16 per tap [group][co][8 channels]
+  // (converted FP64 -> FP32 -> BF16 as the separate layers do), biases FP32
+  for (int k = tid; k < 16 * 36; k += 128) sW1[(k % 36) * 16 + k / 36] = (float)n.w[NN_OFF1 + k];
+  __nv_bfloat16* B2 = reinterpret_cast<__nv_bfloat16*>(smem_raw + NF_OFF_B2);
+  for (int k = tid; k < 9 * 16 * 32; k += 128) {
+    const int tap = k / (16 * 32), r = k % (16 * 32), ci = r / 32, co = r % 32;
+    B2[tap * (NF_B2TAP / 2) + ((ci >> 3) * 32 + co) * 8 + (ci & 7)] =
+        __float2bfloat16_rn((float)n.w[NN_OFF2 + (co * 16 + ci) * 9 + tap]);
+  }
+  __nv_bfloat16* B3 = reinterpret_cast<__nv_bfloat16*>(smem_raw + NF_OFF_B3);
+  for (int k = tid; k < 9 * 32 * 16; k += 128) {
+    const int tap = k / (32 * 16), r = k % (32 * 16), ci = r / 16, co = r % 16;
+    B3[tap * (NF_B3TAP / 2) + ((ci >> 3) * 16 + co) * 8 + (ci & 7)] =
+        __float2bfloat16_rn(co < 4 ? (float)n.w[NN_OFF3 + (co * 32 + ci) * 9 + tap] : 0.0f);
+  }
+  for (int k = tid; k < 16; k += 128) sb1[k] = (float)n.w[NN_OFF1 + 16 * 36 + k];
+  for (int k = tid; k < 32; k += 128) sb2[k] = (float)n.w[NN_OFF2 + 32 * 144 + k];
+  for (int k = tid; k < 4; k += 128) sb3[k] = (float)n.w[NN_OFF3 + 4 * 288 + k];
+  // the activation rings start zeroed (rows before the band's first valid ones are read only by
+  // outputs that are never stored)
+  for (int k = tid; k < NF_OFF_B2 / 16; k += 128) reinterpret_cast<uint4*>(smem_raw)[k] = make_uint4(0, 0, 0, 0);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  const uint32_t a1 = smem_u32(sA1), a2 = smem_u32(sA2);
+  const uint32_t b2 = smem_u32(smem_raw + NF_OFF_B2), b3 = smem_u32(smem_raw + NF_OFF_B3);
+  constexpr uint32_t idesc2 = umma_idesc_bf16(TC_M, 32), idesc3 = umma_idesc_bf16(TC_M, 16);
+  constexpr long long kBudget = 2000000000LL;  // about one second of SM clock
+
+  const int it = blockIdx.x;
+  const int d = (it < items0) ? 0 : 1;
+  const int il = (d == 0) ? it : it - items0;
+  const int H = n.H[d], Wd = n.W[d];
+  const int x0 = (il % nxs[d]) * NF_OUT, h0 = (il / nxs[d]) * band;
+  const int h1 = (h0 + band < H) ? h0 + band : H;
+  const int xs = x0 - 2;  // image column of local pixel 0
+  const long long pix = (long long)H * Wd;
+  const float* X = chan_img<float>(n.X, 4, d, n.pix0);
+  float* T3 = chan_img<float>(n.T3, 4, d, n.pix0);
+  const int p = tid, xp = xs + p;
+  const bool col_in = xp >= 0 && xp < Wd;
+  // input row r (zeros outside the image): 4 channels x 130 pixels (local -1 .. 128), 4-byte copies
+  auto load_x = [&](int r) {
+    float* slot = sX + nf_slot4(r) * (NF_XSLOT / 4);
+    const bool row_in = r >= 0 && r < H;
+    for (int k = tid; k < 4 * TC_COLS; k += 128) {
+      const int ch = k / TC_COLS, c = k % TC_COLS, gx = xs - 1 + c;
+      const bool inside = row_in && gx >= 0 && gx < Wd;
+      cp_async4(slot + k, inside ? X + ch * pix + (long long)r * Wd + gx : X, inside);
+    }
+    cp_async_commit();
+  };
+  const int s0 = h0 - 6;
+  load_x(s0 + 3);
+  load_x(s0 + 4);
+  load_x(s0 + 5);
+  unsigned phase = 0u;
+  bool ok = true;
+  for (int s = s0; s < h1; ++s) {
+    load_x(s + 6);  // into the slot of row s + 2, whose last reader (layer 1 of row s + 3) is done
+    if (tid == 0) {
+      // layer 2 of row s + 2 from layer-1 rows s + 1 .. s + 3, accumulator columns 0 .. 31
+      for (int tap = 0; tap < 9; ++tap) {
+        const int ky = tap / 3, kx = tap % 3;
+        const uint32_t slot = a1 + nf_slot3(s + 1 + ky) * NF_A1SLOT;
+        umma_bf16(tmem, umma_smem_desc(slot + kx * 16, NF_A1G, 128),
+                  umma_smem_desc(b2 + tap * NF_B2TAP, 32 * 16, 128), idesc2, tap > 0 ? 1 : 0);
+      }
+      // layer 3 of row s from layer-2 rows s - 1 .. s + 1, accumulator columns 32 .. 47
+      for (int tap = 0; tap < 9; ++tap) {
+        const int ky = tap / 3, kx = tap % 3;
+        const uint32_t slot = a2 + nf_slot3(s - 1 + ky) * NF_A2SLOT;
+        for (int kc = 0; kc < 2; ++kc)
+          umma_bf16(tmem + 32, umma_smem_desc(slot + 2 * kc * NF_A1G + kx * 16, NF_A1G, 128),
+                    umma_smem_desc(b3 + tap * NF_B3TAP + 2 * kc * 16 * 16, 16 * 16, 128), idesc3,
+                    (tap > 0 || kc > 0) ? 1 : 0);
+      }
+      umma_commit(&bar);
+    }
+    cp_async_wait<1>();  // this thread's copies of input rows up to s + 5 have landed
+    __syncthreads();
+    // layer 1 of row s + 4 at pixel p (FP32, bias first, then input channel, kernel row, column)
+    const int r1 = s + 4;
+    float acc[16];
+#pragma unroll
+    for (int co = 0; co < 16; ++co) acc[co] = sb1[co];
+#pragma unroll
+    for (int ci = 0; ci < 4; ++ci)
+#pragma unroll
+      for (int ky = 0; ky < 3; ++ky) {
+        const float* row = sX + nf_slot4(r1 - 1 + ky) * (NF_XSLOT / 4) + ci * TC_COLS + p;
+        const float xv[3] = {row[0], row[1], row[2]};
+#pragma unroll
+        for (int kx = 0; kx < 3; ++kx) {
+          const float4* w4 = reinterpret_cast<const float4*>(sW1 + ((ci * 3 + ky) * 3 + kx) * 16);
+#pragma unroll
+          for (int c4 = 0; c4 < 4; ++c4) {
+            const float4 wv = w4[c4];
+            acc[4 * c4 + 0] = fmaf(wv.x, xv[kx], acc[4 * c4 + 0]);
+            acc[4 * c4 + 1] = fmaf(wv.y, xv[kx], acc[4 * c4 + 1]);
+            acc[4 * c4 + 2] = fmaf(wv.z, xv[kx], acc[4 * c4 + 2]);
+            acc[4 * c4 + 3] = fmaf(wv.w, xv[kx], acc[4 * c4 + 3]);
+          }
+        }
+      }
+    // every thread waits (bounded) for the step's MMAs; the outcome is made uniform
+    ok = __syncthreads_and(mbar_wait(&bar, phase, kBudget) ? 1 : 0) != 0;
+    if (!ok) {
+      if (tid == 0) atomicOr(n.err, ERR_TIMEOUT_BIT);
+      mbar_wait(&bar, phase, kBudget);  // drain before the accumulators are released
+      break;
+    }
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // layer 1 of row s + 4 (zero outside the image) into the slot of row s + 1
+    {
+      const bool in = col_in && r1 >= 0 && r1 < H;
+      unsigned char* dst = sA1 + nf_slot3(r1) * NF_A1SLOT + (p + 1) * 16;
+#pragma unroll
+      for (int g = 0; g < 2; ++g) {
+        __align__(16) __nv_bfloat16 v8[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const float v = acc[8 * g + e];
+          v8[e] = __float2bfloat16_rn(in ? (v > 0.0f ? v : 0.0f) : 0.0f);
+        }
+        *reinterpret_cast<uint4*>(dst + g * NF_A1G) = *reinterpret_cast<const uint4*>(v8);
+      }
+    }
+    const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+    // layer 2 of row s + 2 (bias, ReLU, zero outside the image) into the slot of row s - 1
+    {
+      const int r2 = s + 2;
+      const bool in = col_in && r2 >= 0 && r2 < H;
+      uint32_t r[32];
+      tmem_ld16(tl, r);
+      tmem_ld16(tl + 16, r + 16);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      unsigned char* dst = sA2 + nf_slot3(r2) * NF_A2SLOT + (p + 1) * 16;
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        __align__(16) __nv_bfloat16 v8[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const float z = __uint_as_float(r[8 * g + e]) + sb2[8 * g + e];
+          v8[e] = __float2bfloat16_rn(in ? (z > 0.0f ? z : 0.0f) : 0.0f);
+        }
+        *reinterpret_cast<uint4*>(dst + g * NF_A1G) = *reinterpret_cast<const uint4*>(v8);
+      }
+    }
+    // layer 3 of row s (bias, tanh) to the FP32 output
+    {
+      uint32_t r[16];
+      tmem_ld16(tl + 32, r);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (s >= h0 && p >= 2 && p < 2 + NF_OUT && xp < Wd) {
+        const long long o = (long long)s * Wd + xp;
+#pragma unroll
+        for (int co = 0; co < 4; ++co) T3[co * pix + o] = tanhf(__uint_as_float(r[co]) + sb3[co]);
+      }
+    }
+    // the new rows must be visible to the tensor core (async proxy) before the next step's MMAs
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  }
+  cp_async_wait<0>();  // no copy of this block may land after it leaves
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem) : "memory");
+}
+
 // network input from an FP64 image / scaled FP64 output (js_nn_eval)
 template <class T>
 __global__ void nn_load_kernel(const double* __restrict__ Xd, T* __restrict__ X, long long n4) {
@@ -1157,11 +1392,35 @@ cudaError_t conv_tc(const NnArgs& n, const void* inh, void* out, int woff, cudaS
   return cudaGetLastError();
 }
 
+// the fused network kernel: rows per band about one wave of co-resident blocks (shared memory
+// admits three per SM), at least 16 (each band recomputes 6 rows of layers 1 and 2 at its top)
+cudaError_t net_tc(const NnArgs& n, cudaStream_t s) {
+  auto k = nn_net_tc_kernel;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, NF_SMEM);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  long long rows = 0;
+  int hmax = 1;
+  for (int d = 0; d < n.nimg; ++d) {
+    rows += (long long)cdiv(n.W[d], NF_OUT) * n.H[d];
+    hmax = n.H[d] > hmax ? n.H[d] : hmax;
+  }
+  long long band = (rows + 3LL * sms - 1) / (3LL * sms);
+  band = band < 16 ? 16 : (band > hmax ? hmax : band);
+  long long items = 0;
+  for (int d = 0; d < n.nimg; ++d) items += (long long)cdiv(n.W[d], NF_OUT) * ((n.H[d] + band - 1) / band);
+  k<<<(unsigned)items, 128, NF_SMEM, s>>>(n, (int)band);
+  return cudaGetLastError();
+}
+
 // the three layers on n.X -> n.T3
 template <class T>
 cudaError_t layers_t(const NnArgs& n, cudaStream_t s) {
   cudaError_t e;
   const bool tc = std::is_same<T, float>::value && n.bf16;
+  if (tc && !n.keep && n.fused) return net_tc(n, s);
   // (the tensor-core layers read BF16 pixel-major copies written by the layer before them; their
   // FP32 activations are written only for a reverse pass)
   void* a1 = (tc && !n.keep) ? nullptr : n.A1;

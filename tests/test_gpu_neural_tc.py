@@ -232,3 +232,50 @@ def test_nn_eval_vjp_fp64_fp32_and_bf16(env, shape):
     assert dw.max() <= 1e-3 * np.abs(ew).max(), dw.max() / np.abs(ew).max()
     # and against the exact reverse: of the order of BF16 rounding
     assert np.quantile(np.abs(gx - gx_ref), 0.99) <= 5e-2 * np.abs(gx_ref).max()
+
+
+# The fused network kernel (one launch for the three layers of a forward-only BF16 stage) runs the
+# arithmetic of the layer-by-layer launches in the same order: equal bit for bit.  Images with
+# several 124-pixel strips and a ragged one, bands with a ragged last band, a single row, an image
+# narrower than one strip, and the 1024 x 1024 solver at full size.
+FUSED_SHAPES = [(17, 300), (9, 37), (1, 201), (130, 250), (300, 129), (64, 125)]
+
+
+@pytest.mark.parametrize("shape", FUSED_SHAPES)
+def test_fused_network_equals_layerwise_launches(env, shape):
+    torch, B = env
+    w = _params(11)
+    X = np.random.default_rng(12).standard_normal((4,) + shape)
+    s = B.Solver.from_problem(W.random_periodic(256, 200, seed=0))
+    wd = torch.tensor(w, device="cuda")
+    out = {}
+    for prec in ("bf16", "bf16-layerwise"):
+        s.set_neural(wd, NORM, precision=prec)
+        out[prec] = to_host(s.nn_eval(to_dev(X)))
+    assert s.status() == 0
+    assert np.array_equal(out["bf16"], out["bf16-layerwise"])
+    assert np.abs(out["bf16"]).max() > 0
+
+
+@pytest.mark.parametrize("n", [96, 1024])
+def test_fused_network_solver_steps_equal_layerwise(env, n):
+    torch, B = env
+    from paper_2601_04400_gb300 import neural as NN
+    p = W.riemann2d(n)
+    U0 = to_dev(O.prim_to_cons(p, p.W0))
+    # the benchmark's network: He-uniform weights, outputs scaled to a tenth of the states' spread
+    w = NN.init_weights(0, zero_last=False) * 0.5
+    norm = NN.frame_norm(U0, scale=0.1)
+    res = {}
+    for prec in ("bf16", "bf16-layerwise"):
+        s = B.Solver.from_problem(p)
+        dt = s.max_dt(U0, 0.3)
+        s.set_neural(w, norm, precision=prec)
+        U = U0.clone()
+        L = s.rhs(U)
+        s.step(U, dt, 3)
+        res[prec] = (to_host(L), to_host(U), s.status())
+        s.close()
+    assert res["bf16"][2] == 0 and res["bf16-layerwise"][2] == 0, (res["bf16"][2], res["bf16-layerwise"][2])
+    for a, b in zip(res["bf16"][:2], res["bf16-layerwise"][:2]):
+        assert np.array_equal(a, b)
