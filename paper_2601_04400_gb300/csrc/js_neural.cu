@@ -768,6 +768,20 @@ __global__ void __launch_bounds__(128) nn_conv_tc_kernel(NnArgs n, const void* i
 //   layer-2 rows as BF16 core matrices (3 slots each: a slot is rewritten only after the MMAs
 //   that read it have completed)
 // ---------------------------------------------------------------------------------------
+// two FP32 fused multiply-adds in one instruction (each IEEE-rounded, as fmaf)
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b,
+                                                    unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
+  return (unsigned long long)__float_as_uint(lo) | ((unsigned long long)__float_as_uint(hi) << 32);
+}
+__device__ __forceinline__ float2 unpack2(unsigned long long v) {
+  return make_float2(__uint_as_float((unsigned)v), __uint_as_float((unsigned)(v >> 32)));
+}
+
 constexpr int NF_OUT = TC_M - 4;                 // output pixels per strip
 constexpr int NF_XS = 4, NF_AS = 3;              // ring slots
 constexpr int NF_XSLOT = 4 * TC_COLS * 4;        // FP32 input row: 4 channels x 130 pixels
@@ -854,6 +868,7 @@ __global__ void __launch_bounds__(128) nn_net_tc_kernel(NnArgs n, int band) {
   float* T3 = chan_img<float>(n.T3, 4, d, n.pix0);
   const int p = tid, xp = xs + p;
   const bool col_in = xp >= 0 && xp < Wd;
+  const int l0 = 2 * (tid & 63), hc = tid >> 6;  // layer 1: pixels l0, l0 + 1, channel group hc
   // input row r (zeros outside the image): 4 channels x 130 pixels (local -1 .. 128), 4-byte copies
   auto load_x = [&](int r) {
     float* slot = sX + nf_slot4(r) * (NF_XSLOT / 4);
@@ -894,27 +909,32 @@ __global__ void __launch_bounds__(128) nn_net_tc_kernel(NnArgs n, int band) {
     }
     cp_async_wait<1>();  // this thread's copies of input rows up to s + 5 have landed
     __syncthreads();
-    // layer 1 of row s + 4 at pixel p (FP32, bias first, then input channel, kernel row, column)
+    // layer 1 of row s + 4 (FP32, bias first, then input channel, kernel row, column) at pixels
+    // l0, l0 + 1 and channels 8 hc .. 8 hc + 7: packed FMAs on channel pairs, each weight pair
+    // feeding both pixels
     const int r1 = s + 4;
-    float acc[16];
+    unsigned long long acc[2][4];
 #pragma unroll
-    for (int co = 0; co < 16; ++co) acc[co] = sb1[co];
+    for (int j = 0; j < 4; ++j) acc[0][j] = acc[1][j] = pack2(sb1[8 * hc + 2 * j], sb1[8 * hc + 2 * j + 1]);
 #pragma unroll
     for (int ci = 0; ci < 4; ++ci)
 #pragma unroll
       for (int ky = 0; ky < 3; ++ky) {
-        const float* row = sX + nf_slot4(r1 - 1 + ky) * (NF_XSLOT / 4) + ci * TC_COLS + p;
-        const float xv[3] = {row[0], row[1], row[2]};
+        const float* row = sX + nf_slot4(r1 - 1 + ky) * (NF_XSLOT / 4) + ci * TC_COLS + l0;
+        const float2 xa = *reinterpret_cast<const float2*>(row);
+        const float2 xb = *reinterpret_cast<const float2*>(row + 2);
+        const float xv[4] = {xa.x, xa.y, xb.x, xb.y};
 #pragma unroll
         for (int kx = 0; kx < 3; ++kx) {
-          const float4* w4 = reinterpret_cast<const float4*>(sW1 + ((ci * 3 + ky) * 3 + kx) * 16);
+          const float4* w4 = reinterpret_cast<const float4*>(sW1 + ((ci * 3 + ky) * 3 + kx) * 16 + 8 * hc);
+          const float4 wa = w4[0], wb = w4[1];
+          const unsigned long long w2[4] = {pack2(wa.x, wa.y), pack2(wa.z, wa.w), pack2(wb.x, wb.y),
+                                            pack2(wb.z, wb.w)};
+          const unsigned long long x0 = pack2(xv[kx], xv[kx]), x1 = pack2(xv[kx + 1], xv[kx + 1]);
 #pragma unroll
-          for (int c4 = 0; c4 < 4; ++c4) {
-            const float4 wv = w4[c4];
-            acc[4 * c4 + 0] = fmaf(wv.x, xv[kx], acc[4 * c4 + 0]);
-            acc[4 * c4 + 1] = fmaf(wv.y, xv[kx], acc[4 * c4 + 1]);
-            acc[4 * c4 + 2] = fmaf(wv.z, xv[kx], acc[4 * c4 + 2]);
-            acc[4 * c4 + 3] = fmaf(wv.w, xv[kx], acc[4 * c4 + 3]);
+          for (int j = 0; j < 4; ++j) {
+            acc[0][j] = ffma2(w2[j], x0, acc[0][j]);
+            acc[1][j] = ffma2(w2[j], x1, acc[1][j]);
           }
         }
       }
@@ -927,20 +947,21 @@ __global__ void __launch_bounds__(128) nn_net_tc_kernel(NnArgs n, int band) {
     }
     phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // layer 1 of row s + 4 (zero outside the image) into the slot of row s + 1
-    {
-      const bool in = col_in && r1 >= 0 && r1 < H;
-      unsigned char* dst = sA1 + nf_slot3(r1) * NF_A1SLOT + (p + 1) * 16;
+    // layer 1 of row s + 4 (ReLU, zero outside the image) into the slot of row s + 1: channel
+    // group hc of pixels l0 and l0 + 1
 #pragma unroll
-      for (int g = 0; g < 2; ++g) {
-        __align__(16) __nv_bfloat16 v8[8];
+    for (int q = 0; q < 2; ++q) {
+      const int xq = xs + l0 + q;
+      const bool in = xq >= 0 && xq < Wd && r1 >= 0 && r1 < H;
+      __align__(16) __nv_bfloat16 v8[8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const float v = acc[8 * g + e];
-          v8[e] = __float2bfloat16_rn(in ? (v > 0.0f ? v : 0.0f) : 0.0f);
-        }
-        *reinterpret_cast<uint4*>(dst + g * NF_A1G) = *reinterpret_cast<const uint4*>(v8);
+      for (int j = 0; j < 4; ++j) {
+        const float2 v = unpack2(acc[q][j]);
+        v8[2 * j] = __float2bfloat16_rn(in ? (v.x > 0.0f ? v.x : 0.0f) : 0.0f);
+        v8[2 * j + 1] = __float2bfloat16_rn(in ? (v.y > 0.0f ? v.y : 0.0f) : 0.0f);
       }
+      *reinterpret_cast<uint4*>(sA1 + nf_slot3(r1) * NF_A1SLOT + hc * NF_A1G + (l0 + q + 1) * 16) =
+          *reinterpret_cast<const uint4*>(v8);
     }
     const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
     // layer 2 of row s + 2 (bias, ReLU, zero outside the image) into the slot of row s - 1
