@@ -93,6 +93,23 @@ constexpr double K13 = 13.0 / 3.0;
 constexpr double EPS4 = 4.0e-6;
 constexpr double SIXTH = 1.0 / 6.0;
 
+// Network input of one face (neural flux, Sec. 2.3): the mean of its two WENO5 face states
+// (primitive rho, u, v, p in wl / wr; un / ut the planes of the face-normal and tangential
+// velocity) in conserved variables of the face frame, normalised by mean and 1/sd per channel.
+// One definition for every kernel that forms face images, so that they agree bit for bit.
+__device__ __forceinline__ void face_image(const double wl[4], const double wr[4], int un, int ut, double g1,
+                                           const double mean[4], const double inv_sd[4], double m[4]) {
+  const double rL = wl[0], rR = wr[0];
+  const double EL = fma(0.5 * rL, fma(wl[un], wl[un], wl[ut] * wl[ut]), wl[3] * g1);
+  const double ER = fma(0.5 * rR, fma(wr[un], wr[un], wr[ut] * wr[ut]), wr[3] * g1);
+  m[0] = 0.5 * (rL + rR);
+  m[1] = 0.5 * fma(rL, wl[un], rR * wr[un]);
+  m[2] = 0.5 * fma(rL, wl[ut], rR * wr[ut]);
+  m[3] = 0.5 * (EL + ER);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) m[k] = (m[k] - mean[k]) * inv_sd[k];
+}
+
 struct Win {
   double q0, q1;          // q_i, q_{i+1}
   double dm2, dm1, dp1;   // d_{i-3/2}, d_{i-1/2}, d_{i+1/2}

@@ -299,20 +299,20 @@ stage2d_kernel(StageArgs a0) {
 
 // persistent concurrent-sweep stage kernel: blocks stride over the tiles; with SAVE the
 // WENO5 internals of the stage go to a.wsave for the reverse pass
-template <int TX, int TY, int LX, int LY, bool VISC, bool RHS, bool SAVE>
+template <int TX, int TY, int LX, int LY, bool VISC, bool RHS, bool SAVE, bool IMG = false>
 __global__ void __launch_bounds__(Stage2DC<TX, TY, LX, LY, VISC>::NT, SAVE ? 3 : 1)
 stage2dc_kernel(StageArgs a0, int ntx, int ntiles) {
   StageArgs a;
   if (!stage_constants(a0, a)) return;
   extern __shared__ double smem[];
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    stage_tile_c<TX, TY, LX, LY, VISC, RHS, false, SAVE>(a, t % ntx, t / ntx, smem);
+    stage_tile_c<TX, TY, LX, LY, VISC, RHS, false, SAVE, IMG>(a, t % ntx, t / ntx, smem);
     __syncthreads();
   }
 }
 
 // the same with the tile staged by TMA (tensor map of the stage input as a grid constant)
-template <int TX, int TY, int LX, int LY, bool VISC, bool RHS, bool SAVE>
+template <int TX, int TY, int LX, int LY, bool VISC, bool RHS, bool SAVE, bool IMG = false>
 __global__ void __launch_bounds__(Stage2DC<TX, TY, LX, LY, VISC, true>::NT, SAVE ? 3 : 1)
 stage2dc_tma_kernel(StageArgs a0, int ntx, int ntiles, const __grid_constant__ TensorMap128 tmap) {
   StageArgs a;
@@ -323,7 +323,7 @@ stage2dc_tma_kernel(StageArgs a0, int ntx, int ntiles, const __grid_constant__ T
   __syncthreads();
   unsigned phase = 0;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    stage_tile_c<TX, TY, LX, LY, VISC, RHS, true, SAVE>(a, t % ntx, t / ntx, smem, &tmap, &bar, &phase);
+    stage_tile_c<TX, TY, LX, LY, VISC, RHS, true, SAVE, IMG>(a, t % ntx, t / ntx, smem, &tmap, &bar, &phase);
     __syncthreads();
   }
 }
@@ -389,45 +389,47 @@ cudaError_t launch_stage2d(const StageArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int TX, int TY, int LX, int LY, bool VISC, bool RHS, bool SAVE = false>
+template <int TX, int TY, int LX, int LY, bool VISC, bool RHS, bool SAVE = false, bool IMG = false>
 cudaError_t launch_stage2dc(const StageArgs& a, cudaStream_t s) {
   using S = Stage2DC<TX, TY, LX, LY, VISC>;
-  auto k = stage2dc_kernel<TX, TY, LX, LY, VISC, RHS, SAVE>;
+  auto k = stage2dc_kernel<TX, TY, LX, LY, VISC, RHS, SAVE, IMG>;
+  constexpr size_t SM = S::SMEM;
   static int resident = 0;  // blocks resident on the whole GPU
   if (resident == 0) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, S::NT, S::SMEM);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, S::NT, SM);
     if (e != cudaSuccess) return e;
     resident = sms * (per_sm > 0 ? per_sm : 1);
   }
   const int ntx = (a.lay.nx + TX - 1) / TX, nty = (a.lay.ny + TY - 1) / TY;
   const int ntiles = ntx * nty;
-  k<<<ntiles < resident ? ntiles : resident, S::NT, S::SMEM, s>>>(a, ntx, ntiles);
+  k<<<ntiles < resident ? ntiles : resident, S::NT, SM, s>>>(a, ntx, ntiles);
   return cudaGetLastError();
 }
 
-template <int TX, int TY, int LX, int LY, bool VISC, bool RHS, bool SAVE = false>
+template <int TX, int TY, int LX, int LY, bool VISC, bool RHS, bool SAVE = false, bool IMG = false>
 cudaError_t launch_stage2dc_tma(const StageArgs& a, const TensorMap128* tmap, cudaStream_t s) {
   using S = Stage2DC<TX, TY, LX, LY, VISC, true>;
-  auto k = stage2dc_tma_kernel<TX, TY, LX, LY, VISC, RHS, SAVE>;
+  auto k = stage2dc_tma_kernel<TX, TY, LX, LY, VISC, RHS, SAVE, IMG>;
+  constexpr size_t SM = S::SMEM;
   static int resident = 0;
   if (resident == 0) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, S::NT, S::SMEM);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, S::NT, SM);
     if (e != cudaSuccess) return e;
     resident = sms * (per_sm > 0 ? per_sm : 1);
   }
   const int ntx = (a.lay.nx + TX - 1) / TX, nty = (a.lay.ny + TY - 1) / TY;
   const int ntiles = ntx * nty;
-  k<<<ntiles < resident ? ntiles : resident, S::NT, S::SMEM, s>>>(a, ntx, ntiles, *tmap);
+  k<<<ntiles < resident ? ntiles : resident, S::NT, SM, s>>>(a, ntx, ntiles, *tmap);
   return cudaGetLastError();
 }
 
@@ -462,6 +464,15 @@ cudaError_t launch_stage_save(const StageArgs& a, bool visc, const TensorMap128*
                 : launch_stage2dc_tma<32, 32, 16, 16, false, false, true>(a, tmap, s);
   return visc ? launch_stage2dc<32, 32, 16, 16, true, false, true>(a, s)
               : launch_stage2dc<32, 32, 16, 16, false, false, true>(a, s);
+}
+
+cudaError_t launch_stage_img(const StageArgs& a, bool visc, const TensorMap128* tmap, cudaStream_t s) {
+  if (a.lay.ny == 1 || a.img == nullptr) return cudaErrorInvalidValue;
+  if (tmap != nullptr)
+    return visc ? launch_stage2dc_tma<32, 32, 16, 16, true, false, false, true>(a, tmap, s)
+                : launch_stage2dc_tma<32, 32, 16, 16, false, false, false, true>(a, tmap, s);
+  return visc ? launch_stage2dc<32, 32, 16, 16, true, false, false, true>(a, s)
+              : launch_stage2dc<32, 32, 16, 16, false, false, false, true>(a, s);
 }
 
 cudaError_t launch_stage(const StageArgs& a, bool visc, bool rhs, int variant, const TensorMap128* tmap,

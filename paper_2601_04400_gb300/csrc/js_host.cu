@@ -404,9 +404,30 @@ int stage_save(js_ctx* c, StageArgs a, bool visc, double* wsave) {
 }
 
 // fused stage kernel, bracketed by events while profiling
+// stage update that also writes the FP32 face images of the neural flux (FP32 and BF16
+// networks on 2D grids), then the network and its divergence
+int stage_img(js_ctx* c, StageArgs a, bool visc) {
+  a.img = static_cast<float*>(c->nn.X);
+  for (int k = 0; k < 4; ++k) {
+    a.img_mean[k] = c->nn.mean[k];
+    a.img_isd[k] = c->nn.inv_sd[k];
+  }
+  const bool timed = c->profiling && c->ev_used + 2 <= (int)c->ev.size();
+  if (timed) JS_CUDA(cudaEventRecord(c->ev[c->ev_used], c->stream));
+  JS_CUDA(js::launch_stage_img(a, visc, stage_tmap(c, a.Uin), c->stream));
+  if (timed) {
+    JS_CUDA(cudaEventRecord(c->ev[c->ev_used + 1], c->stream));
+    c->ev_used += 2;
+  }
+  JS_CUDA(js::nn_layers(c->nn, c->stream));
+  c->launches += 4;
+  return nn_after(c, a, false);
+}
+
 int stage(js_ctx* c, const StageArgs& a, bool visc, bool rhs) {
-  // with the neural flux on a 2D grid the stage kernel also stores its WENO5 internals and
-  // the network's face images are formed from them
+  // with the neural flux on a 2D grid the stage kernel also forms the network's face images
+  // (FP32 and BF16 networks) or stores the WENO5 internals they are formed from (FP64)
+  if (c->nn_on && !rhs && c->g.ny > 1 && c->nn.fp32) return stage_img(c, a, visc);
   if (c->nn_on && c->nn_wsave && !rhs) return stage_save(c, a, visc, c->nn_wsave);
   int rc = nn_before(c, a);
   if (rc) return rc;

@@ -29,6 +29,10 @@ struct StageArgs {
   // device-resident step size (js_step_cfl): when set, cx, cy, avx, avy are read from
   // dtc[0..3] at kernel start, and dtc[4] == 0 means the step is inactive (skip the stage)
   const double* dtc;
+  // neural flux (kernels instantiated with IMG): the face images of the stage input, FP32
+  // [4][ny][nx+1] (x faces) then [4][nx][ny+1] (y faces), normalised by img_mean / img_isd
+  float* img;
+  double img_mean[4], img_isd[4];
 };
 
 // the per-step constants of a device step size dt: dtc = {dt/dx, dt/dy, dt nu/dx^2,
@@ -142,6 +146,8 @@ struct NnArgs {
 cudaError_t nn_forward(const NnArgs& n, const double* Q, long long qplane, cudaStream_t s);
 // primitive variables of every padded cell of U into Q (4 planes)
 cudaError_t nn_prims(const double* U, double* Q, const Lay& lay, double gamma, cudaStream_t s);
+// the network alone on the face images already in n.X, into T3 (forward)
+cudaError_t nn_layers(const NnArgs& n, cudaStream_t s);
 // stage output (or RHS) minus the divergence of the neural flux held in T3
 cudaError_t nn_apply(const NnArgs& n, const StageArgs& a, bool rhs, cudaStream_t s);
 // reverse: recompute the network on a.Q, seed with the face-flux adjoints of a.lam, back-
@@ -229,6 +235,8 @@ cudaError_t launch_stage(const StageArgs& a, bool visc, bool rhs, int variant, c
 // stage update (not RHS mode) that also stores the WENO5 internals to a.wsave (2D only;
 // 32x32 concurrent tile, TMA-staged when tmap is given)
 cudaError_t launch_stage_save(const StageArgs& a, bool visc, const TensorMap128* tmap, cudaStream_t s);
+// stage update that also writes the neural flux's face images of its input to a.img (2D)
+cudaError_t launch_stage_img(const StageArgs& a, bool visc, const TensorMap128* tmap, cudaStream_t s);
 cudaError_t launch_bc_fill(double* U, const Lay& lay, const BcArgs& bc, cudaStream_t s);
 cudaError_t launch_ib_fill(double* U, const Lay& lay, const IbArgs& ib, double gamma, int wall, cudaStream_t s);
 cudaError_t launch_pack(const double* U, double* P, const Lay& lay, cudaStream_t s);

@@ -131,18 +131,11 @@ __global__ void __launch_bounds__(256) nn_image_kernel(NnArgs n, const double* _
   for (int fl = threadIdx.x / IT; fl < IT; fl += 256 / IT) {
     const int h = h0 + hl, f = f0 + fl;
     if (h >= H || f >= Wd) continue;
-    double wl[4], wr[4];
+    double wl[4], wr[4], m[4];
     face_states_any(n, n.lay, Q, qplane, d, h, f, wl, wr);
-    const double rL = wl[0], rR = wr[0];
-    const double EL = fma(0.5 * rL, fma(wl[un], wl[un], wl[ut] * wl[ut]), wl[3] * n.g1);
-    const double ER = fma(0.5 * rR, fma(wr[un], wr[un], wr[ut] * wr[ut]), wr[3] * n.g1);
-    double m[4];
-    m[0] = 0.5 * (rL + rR);
-    m[1] = 0.5 * fma(rL, wl[un], rR * wr[un]);
-    m[2] = 0.5 * fma(rL, wl[ut], rR * wr[ut]);
-    m[3] = 0.5 * (EL + ER);
+    face_image(wl, wr, un, ut, n.g1, n.mean, n.inv_sd, m);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) sx[k][hl][fl] = (T)((m[k] - n.mean[k]) * n.inv_sd[k]);
+    for (int k = 0; k < 4; ++k) sx[k][hl][fl] = (T)m[k];
   }
   __syncthreads();
   T* X = chan_img<T>(n.X, 4, d, n.pix0);
@@ -1561,6 +1554,10 @@ cudaError_t nn_prims(const double* U, double* Q, const Lay& lay, double gamma, c
 
 cudaError_t nn_forward(const NnArgs& n, const double* Q, long long qplane, cudaStream_t s) {
   return n.fp32 ? forward_t<float>(n, Q, qplane, s) : forward_t<double>(n, Q, qplane, s);
+}
+
+cudaError_t nn_layers(const NnArgs& n, cudaStream_t s) {
+  return n.fp32 ? layers_t<float>(n, s) : layers_t<double>(n, s);
 }
 
 cudaError_t nn_eval(const NnArgs& n, const double* X, int H, int W, double* Y, cudaStream_t s) {

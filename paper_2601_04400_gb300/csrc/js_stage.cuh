@@ -20,14 +20,21 @@ namespace js {
 // emit(k, dF) receives F_{k+1/2} - F_{k-1/2} (conserved order) for output cells k = 0..L-1.
 // keep(k, c, sv), when given, receives the WENO5 internals of variable c at cell k for
 // k = -1 (left-biased side only), 0..L-1 (both sides) and L (right-biased side only).
+// face(k, ql, qr), when given, receives the two WENO5 states (before any positivity fallback)
+// of face k - 1/2 for k = 0..L.
 struct NoKeep {
   __device__ __forceinline__ void operator()(int, int, const double*) const {}
 };
+struct NoFace {
+  __device__ __forceinline__ void operator()(int, const double*, const double*) const {}
+};
 
-template <int DIR, bool VISC, bool HAS_T, int L, class Emit, class Keep = NoKeep>
+template <int DIR, bool VISC, bool HAS_T, int L, class Emit, class Keep = NoKeep, class Face = NoFace>
 __device__ __forceinline__ void sweep_line(const double* __restrict__ sq, int ps, int base, int st, int ts,
-                                           const Gas& g, const ViscC& vc, Emit&& emit, Keep keep = Keep{}) {
+                                           const Gas& g, const ViscC& vc, Emit&& emit, Keep keep = Keep{},
+                                           Face face = Face{}) {
   constexpr bool SV = !std::is_same<Keep, NoKeep>::value;
+  constexpr bool FI = !std::is_same<Face, NoFace>::value;
   constexpr int PN = (DIR == 0) ? 1 : 2;  // plane of the face-normal velocity
   constexpr int PT = (DIR == 0) ? 2 : 1;  // plane of the tangential velocity
   Win w[4];
@@ -73,6 +80,7 @@ __device__ __forceinline__ void sweep_line(const double* __restrict__ sq, int ps
       double ql[4], qr[4];
 #pragma unroll
       for (int c = 0; c < 4; ++c) { ql[c] = prevL[c]; qr[c] = Rf[c]; }
+      if (FI) face(k, ql, qr);
       if (!(ql[0] > 0.0 && ql[3] > 0.0 && qr[0] > 0.0 && qr[3] > 0.0)) {
         // positivity fallback: first-order (cell) states at this face
 #pragma unroll
@@ -353,7 +361,22 @@ __device__ __forceinline__ void keep_internals(const StageArgs& a, int k, int li
   for (int m = 0; m < 7; ++m) dst[m * a.splane] = (m == 3 || m == 4) && !left ? 0.0 : sv[m];
 }
 
-template <int TX, int TY, int LX, int LY, bool VISC, bool RHS, bool TMA = false, bool SAVE = false>
+// face image of the neural flux (IMG: a.img, FP32 [4][ny][nx+1] for x faces then [4][nx][ny+1]
+// for y faces): face f of a line is written by the segment that holds cell f, the line's last
+// face by the segment that ends there
+template <int DIR>
+__device__ __forceinline__ void put_image(const StageArgs& a, int line, int f, const double* ql, const double* qr) {
+  const int nx = a.lay.nx, ny = a.lay.ny;
+  const long long pix0 = (long long)ny * (nx + 1);
+  const long long pix = (DIR == 0) ? pix0 : (long long)nx * (ny + 1);
+  float* X = a.img + (DIR == 0 ? 0LL : 4 * pix0) + (long long)line * ((DIR == 0 ? nx : ny) + 1) + f;
+  double m[4];
+  face_image(ql, qr, DIR == 0 ? 1 : 2, DIR == 0 ? 2 : 1, a.g1, a.img_mean, a.img_isd, m);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) X[k * pix] = (float)m[k];
+}
+
+template <int TX, int TY, int LX, int LY, bool VISC, bool RHS, bool TMA = false, bool SAVE = false, bool IMG = false>
 __device__ __forceinline__ void stage_tile_c(const StageArgs& a, int bx, int by, double* smem,
                                              const void* tmap = nullptr, unsigned long long* bar = nullptr,
                                              unsigned* phase = nullptr) {
@@ -385,6 +408,12 @@ __device__ __forceinline__ void stage_tile_c(const StageArgs& a, int bx, int by,
                                     [&](int k, int c, const double* sv) {
         if (gj < a.lay.ny) keep_internals<0>(a, tx0 + xs + k, gj, c, sv, k < 0 ? -1 : (k == LX ? 1 : 0));
       });
+    } else if constexpr (IMG) {
+      sweep_line<0, VISC, true, LX>(sq, S::PS, (ty + 3) * S::SP + xs + 3, 1, S::SP, g, a.vx, emit, NoKeep{},
+                                    [&](int k, const double* ql, const double* qr) {
+        const int f = tx0 + xs + k;
+        if (gj < a.lay.ny && f <= a.lay.nx && (k < LX || f == a.lay.nx)) put_image<0>(a, gj, f, ql, qr);
+      });
     } else {
       sweep_line<0, VISC, true, LX>(sq, S::PS, (ty + 3) * S::SP + xs + 3, 1, S::SP, g, a.vx, emit);
     }
@@ -404,6 +433,12 @@ __device__ __forceinline__ void stage_tile_c(const StageArgs& a, int bx, int by,
       sweep_line<1, VISC, true, LY>(sq, S::PS, (ys + 3) * S::SP + tx + 3, S::SP, 1, g, a.vy, emit,
                                     [&](int k, int c, const double* sv) {
         if (gi < a.lay.nx) keep_internals<1>(a, ty0 + ys + k, gi, c, sv, k < 0 ? -1 : (k == LY ? 1 : 0));
+      });
+    } else if constexpr (IMG) {
+      sweep_line<1, VISC, true, LY>(sq, S::PS, (ys + 3) * S::SP + tx + 3, S::SP, 1, g, a.vy, emit, NoKeep{},
+                                    [&](int k, const double* ql, const double* qr) {
+        const int f = ty0 + ys + k;
+        if (gi < a.lay.nx && f <= a.lay.ny && (k < LY || f == a.lay.ny)) put_image<1>(a, gi, f, ql, qr);
       });
     } else {
       sweep_line<1, VISC, true, LY>(sq, S::PS, (ys + 3) * S::SP + tx + 3, S::SP, 1, g, a.vy, emit);

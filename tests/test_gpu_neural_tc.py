@@ -279,3 +279,32 @@ def test_fused_network_solver_steps_equal_layerwise(env, n):
     assert res["bf16"][2] == 0 and res["bf16-layerwise"][2] == 0, (res["bf16"][2], res["bf16-layerwise"][2])
     for a, b in zip(res["bf16"][:2], res["bf16-layerwise"][:2]):
         assert np.array_equal(a, b)
+
+
+# Forward stages write the network's face images from the stage kernel's own WENO5 face states;
+# stages that store their WENO5 internals (for a reverse pass) form them in a separate kernel from
+# those internals.  The two routes share the face-image arithmetic: equal stage outputs bit for
+# bit, for Euler and Navier-Stokes stage kernels, on a grid that is not a multiple of the tile.
+@pytest.mark.parametrize("prec", ["bf16", "fp32"])
+@pytest.mark.parametrize("case", ["riemann", "cylinder"])
+def test_stage_kernel_images_equal_image_kernel(env, prec, case):
+    torch, B = env
+    from paper_2601_04400_gb300 import neural as NN
+    if case == "riemann":
+        p = W.riemann2d(70, ny=45)
+    else:
+        p = W.shock_cylinder(nx=70, ny=45, Lx=3.5, Ly=2.25, centre=(1.6, 1.1), radius=0.45, x_shock=0.8,
+                             viscous=True)
+    U0 = to_dev(O.prim_to_cons(p, W.random_state(p, seed=3, amp=0.02)))
+    s = B.Solver.from_problem(p)
+    dt = s.max_dt(U0, 0.3)
+    s.set_neural(NN.init_weights(0, zero_last=False) * 0.5, NN.frame_norm(U0, scale=0.1), precision=prec)
+    out = {}
+    for internals in (False, True):
+        U1, U2 = torch.empty_like(U0), torch.empty_like(U0)
+        s.step_stage(U0, U0, U1, dt, 0, internals=internals)
+        s.step_stage(U0, U1, U2, dt, 1, internals=internals)
+        out[internals] = (to_host(U1), to_host(U2))
+    assert s.status() == 0
+    for a, b in zip(out[False], out[True]):
+        assert np.array_equal(a, b)
