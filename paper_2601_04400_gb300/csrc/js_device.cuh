@@ -95,17 +95,21 @@ constexpr double SIXTH = 1.0 / 6.0;
 
 // Network input of one face (neural flux, Sec. 2.3): the mean of its two WENO5 face states
 // (primitive rho, u, v, p in wl / wr; un / ut the planes of the face-normal and tangential
-// velocity) in conserved variables of the face frame, normalised by mean and 1/sd per channel.
-// One definition for every kernel that forms face images, so that they agree bit for bit.
-__device__ __forceinline__ void face_image(const double wl[4], const double wr[4], int un, int ut, double g1,
-                                           const double mean[4], const double inv_sd[4], double m[4]) {
-  const double rL = wl[0], rR = wr[0];
-  const double EL = fma(0.5 * rL, fma(wl[un], wl[un], wl[ut] * wl[ut]), wl[3] * g1);
-  const double ER = fma(0.5 * rR, fma(wr[un], wr[un], wr[ut] * wr[ut]), wr[3] * g1);
-  m[0] = 0.5 * (rL + rR);
-  m[1] = 0.5 * fma(rL, wl[un], rR * wr[un]);
-  m[2] = 0.5 * fma(rL, wl[ut], rR * wr[ut]);
-  m[3] = 0.5 * (EL + ER);
+// velocity) in conserved variables of the face frame, normalised by mean and 1/sd per channel,
+// in arithmetic R: double for the FP64 network, float for the FP32 and BF16 networks (whose input
+// is FP32: the face states are rounded to FP32 first, sparing the FP64 pipe).  One definition for
+// every kernel that forms face images, so that they agree bit for bit.
+template <class R>
+__device__ __forceinline__ void face_image(const double wl[4], const double wr[4], int un, int ut, R g1,
+                                           const R mean[4], const R inv_sd[4], R m[4]) {
+  const R rL = (R)wl[0], rR = (R)wr[0], nL = (R)wl[un], nR = (R)wr[un], tL = (R)wl[ut], tR = (R)wr[ut];
+  const R pL = (R)wl[3], pR = (R)wr[3], h = (R)0.5;
+  const R EL = fma(h * rL, fma(nL, nL, tL * tL), pL * g1);
+  const R ER = fma(h * rR, fma(nR, nR, tR * tR), pR * g1);
+  m[0] = h * (rL + rR);
+  m[1] = h * fma(rL, nL, rR * nR);
+  m[2] = h * fma(rL, tL, rR * tR);
+  m[3] = h * (EL + ER);
 #pragma unroll
   for (int k = 0; k < 4; ++k) m[k] = (m[k] - mean[k]) * inv_sd[k];
 }

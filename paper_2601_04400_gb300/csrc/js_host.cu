@@ -409,9 +409,10 @@ int stage_save(js_ctx* c, StageArgs a, bool visc, double* wsave) {
 int stage_img(js_ctx* c, StageArgs a, bool visc) {
   a.img = static_cast<float*>(c->nn.X);
   for (int k = 0; k < 4; ++k) {
-    a.img_mean[k] = c->nn.mean[k];
-    a.img_isd[k] = c->nn.inv_sd[k];
+    a.img_mean[k] = (float)c->nn.mean[k];
+    a.img_isd[k] = (float)c->nn.inv_sd[k];
   }
+  a.img_g1 = (float)(1.0 / (c->p.gamma - 1.0));
   const bool timed = c->profiling && c->ev_used + 2 <= (int)c->ev.size();
   if (timed) JS_CUDA(cudaEventRecord(c->ev[c->ev_used], c->stream));
   JS_CUDA(js::launch_stage_img(a, visc, stage_tmap(c, a.Uin), c->stream));

@@ -32,7 +32,7 @@ struct StageArgs {
   // neural flux (kernels instantiated with IMG): the face images of the stage input, FP32
   // [4][ny][nx+1] (x faces) then [4][nx][ny+1] (y faces), normalised by img_mean / img_isd
   float* img;
-  double img_mean[4], img_isd[4];
+  float img_mean[4], img_isd[4], img_g1;
 };
 
 // the per-step constants of a device step size dt: dtc = {dt/dx, dt/dy, dt nu/dx^2,

@@ -128,14 +128,21 @@ __global__ void __launch_bounds__(256) nn_image_kernel(NnArgs n, const double* _
   const long long pix = (long long)H * Wd;
   const int hl = threadIdx.x % IT;
   const int un = (d == 0) ? 1 : 2, ut = (d == 0) ? 2 : 1;
+  T mean[4], isd[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    mean[k] = (T)n.mean[k];
+    isd[k] = (T)n.inv_sd[k];
+  }
   for (int fl = threadIdx.x / IT; fl < IT; fl += 256 / IT) {
     const int h = h0 + hl, f = f0 + fl;
     if (h >= H || f >= Wd) continue;
-    double wl[4], wr[4], m[4];
+    double wl[4], wr[4];
+    T m[4];
     face_states_any(n, n.lay, Q, qplane, d, h, f, wl, wr);
-    face_image(wl, wr, un, ut, n.g1, n.mean, n.inv_sd, m);
+    face_image<T>(wl, wr, un, ut, (T)n.g1, mean, isd, m);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) sx[k][hl][fl] = (T)m[k];
+    for (int k = 0; k < 4; ++k) sx[k][hl][fl] = m[k];
   }
   __syncthreads();
   T* X = chan_img<T>(n.X, 4, d, n.pix0);
@@ -862,15 +869,24 @@ __global__ void __launch_bounds__(128) nn_net_tc_kernel(NnArgs n, int band) {
   const int p = tid, xp = xs + p;
   const bool col_in = xp >= 0 && xp < Wd;
   const int l0 = 2 * (tid & 63), hc = tid >> 6;  // layer 1: pixels l0, l0 + 1, channel group hc
-  // input row r (zeros outside the image): 4 channels x 130 pixels (local -1 .. 128), 4-byte copies
+  // input row r (zeros outside the image): 4 channels x 130 pixels (local -1 .. 128), 4-byte
+  // copies; element tid + 128 i of a row slot is channel / column xofs[i] of the image row
+  constexpr int NXL = (4 * TC_COLS + 127) / 128;
+  long long xofs[NXL];
+  bool xok[NXL];
+#pragma unroll
+  for (int i = 0; i < NXL; ++i) {
+    const int k = tid + 128 * i, ch = k / TC_COLS, gx = xs - 1 + k % TC_COLS;
+    xok[i] = k < 4 * TC_COLS && gx >= 0 && gx < Wd;
+    xofs[i] = ch * pix + gx;
+  }
   auto load_x = [&](int r) {
-    float* slot = sX + nf_slot4(r) * (NF_XSLOT / 4);
+    float* slot = sX + nf_slot4(r) * (NF_XSLOT / 4) + tid;
     const bool row_in = r >= 0 && r < H;
-    for (int k = tid; k < 4 * TC_COLS; k += 128) {
-      const int ch = k / TC_COLS, c = k % TC_COLS, gx = xs - 1 + c;
-      const bool inside = row_in && gx >= 0 && gx < Wd;
-      cp_async4(slot + k, inside ? X + ch * pix + (long long)r * Wd + gx : X, inside);
-    }
+    const float* Xr = X + (long long)r * Wd;
+#pragma unroll
+    for (int i = 0; i < NXL; ++i)
+      if (tid + 128 * i < 4 * TC_COLS) cp_async4(slot + 128 * i, row_in && xok[i] ? Xr + xofs[i] : X, row_in && xok[i]);
     cp_async_commit();
   };
   const int s0 = h0 - 6;
@@ -1065,6 +1081,8 @@ __global__ void __launch_bounds__(256) nn_apply_kernel(NnArgs n, StageArgs a, in
   const long long px = (long long)n.H[0] * n.W[0];
   const double fac = (!rhs && a.use_un) ? a.rk_b : 1.0;
   const int ky_of[4] = {0, 2, 1, 3};  // frame channel of each conserved component, y faces
+  const float cxf = (float)a.cx, cyf = (float)a.cy;
+  const float scf[4] = {(float)n.scale[0], (float)n.scale[1], (float)n.scale[2], (float)n.scale[3]};
   const int il = threadIdx.x % IT;
   for (int jl = threadIdx.x / IT; jl < IT; jl += 256 / IT) {
     const int i = i0 + il, j = j0 + jl;
@@ -1074,10 +1092,21 @@ __global__ void __launch_bounds__(256) nn_apply_kernel(NnArgs n, StageArgs a, in
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       const long long ox = (long long)j * n.W[0] + i;
-      double corr = a.cx * (n.scale[c] * ((double)Fx[c * px + ox + 1] - (double)Fx[c * px + ox]));
-      if (two) {
-        const int k = ky_of[c];
-        corr = fma(a.cy, n.scale[k] * ((double)sy[k][il][jl + 1] - (double)sy[k][il][jl]), corr);
+      double corr;
+      if (std::is_same<T, float>::value) {
+        // FP32 network: its flux divergence in FP32 (the FP64 pipe only adds it to the state)
+        float cf = cxf * (scf[c] * (Fx[c * px + ox + 1] - Fx[c * px + ox]));
+        if (two) {
+          const int k = ky_of[c];
+          cf = fmaf(cyf, scf[k] * (sy[k][il][jl + 1] - sy[k][il][jl]), cf);
+        }
+        corr = (double)cf;
+      } else {
+        corr = a.cx * (n.scale[c] * ((double)Fx[c * px + ox + 1] - (double)Fx[c * px + ox]));
+        if (two) {
+          const int k = ky_of[c];
+          corr = fma(a.cy, n.scale[k] * ((double)sy[k][il][jl + 1] - (double)sy[k][il][jl]), corr);
+        }
       }
       if (rhs) a.Uout[c * ncell + o] -= corr;
       else a.Uout[c * L.plane + L.idx(i, j)] -= fac * corr;

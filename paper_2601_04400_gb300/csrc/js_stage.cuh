@@ -370,10 +370,10 @@ __device__ __forceinline__ void put_image(const StageArgs& a, int line, int f, c
   const long long pix0 = (long long)ny * (nx + 1);
   const long long pix = (DIR == 0) ? pix0 : (long long)nx * (ny + 1);
   float* X = a.img + (DIR == 0 ? 0LL : 4 * pix0) + (long long)line * ((DIR == 0 ? nx : ny) + 1) + f;
-  double m[4];
-  face_image(ql, qr, DIR == 0 ? 1 : 2, DIR == 0 ? 2 : 1, a.g1, a.img_mean, a.img_isd, m);
+  float m[4];
+  face_image<float>(ql, qr, DIR == 0 ? 1 : 2, DIR == 0 ? 2 : 1, a.img_g1, a.img_mean, a.img_isd, m);
 #pragma unroll
-  for (int k = 0; k < 4; ++k) X[k * pix] = (float)m[k];
+  for (int k = 0; k < 4; ++k) X[k * pix] = m[k];
 }
 
 template <int TX, int TY, int LX, int LY, bool VISC, bool RHS, bool TMA = false, bool SAVE = false, bool IMG = false>
