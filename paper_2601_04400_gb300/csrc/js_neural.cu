@@ -52,6 +52,17 @@ __device__ __forceinline__ const T* chan_img(const void* base, int C, int d, lon
 __device__ __forceinline__ double act_tanh(double x) { return tanh(x); }
 __device__ __forceinline__ float act_tanh(float x) { return tanhf(x); }
 
+// two floats rounded to BF16 (to nearest even) and packed, lo in the low half; eight of them as
+// one 16-byte value (built in registers, not through a local array)
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(lo)) |
+         ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(hi)) << 16);
+}
+__device__ __forceinline__ uint4 pack_bf16x8(const float v[8]) {
+  return make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
+                    pack_bf16x2(v[6], v[7]));
+}
+
 // WENO5 face states (primitive, before any positivity fallback) of face f of line h in
 // direction d: left-biased from cell f-1, right-biased from cell f (the stage kernel's
 // formulation, so the same values)
@@ -273,10 +284,7 @@ __global__ void __launch_bounds__(NTHR_F) nn_conv_f32_kernel(NnArgs n, const voi
         __nv_bfloat16* Yh = static_cast<__nv_bfloat16*>(outh) + (d == 0 ? 0LL : (long long)COUT * n.pix0);
 #pragma unroll
         for (int c8 = 0; c8 < COUT / 8; ++c8) {
-          __align__(16) __nv_bfloat16 v8[8];
-#pragma unroll
-          for (int e = 0; e < 8; ++e) v8[e] = __float2bfloat16_rn(acc[q][8 * c8 + e]);
-          *reinterpret_cast<uint4*>(Yh + o * COUT + 8 * c8) = *reinterpret_cast<const uint4*>(v8);
+          *reinterpret_cast<uint4*>(Yh + o * COUT + 8 * c8) = pack_bf16x8(&acc[q][8 * c8]);
         }
       }
     }
@@ -732,10 +740,7 @@ __global__ void __launch_bounds__(128) nn_conv_tc_kernel(NnArgs n, const void* i
           if (Yh && c0 + 16 <= COUT) {
 #pragma unroll
             for (int c8 = 0; c8 < 2; ++c8) {
-              __align__(16) __nv_bfloat16 v8[8];
-#pragma unroll
-              for (int e = 0; e < 8; ++e) v8[e] = __float2bfloat16_rn(v[8 * c8 + e]);
-              *reinterpret_cast<uint4*>(Yh + o * COUT + c0 + 8 * c8) = *reinterpret_cast<const uint4*>(v8);
+              *reinterpret_cast<uint4*>(Yh + o * COUT + c0 + 8 * c8) = pack_bf16x8(&v[8 * c8]);
             }
           }
         }
@@ -962,15 +967,15 @@ __global__ void __launch_bounds__(128) nn_net_tc_kernel(NnArgs n, int band) {
     for (int q = 0; q < 2; ++q) {
       const int xq = xs + l0 + q;
       const bool in = xq >= 0 && xq < Wd && r1 >= 0 && r1 < H;
-      __align__(16) __nv_bfloat16 v8[8];
+      float v8[8];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const float2 v = unpack2(acc[q][j]);
-        v8[2 * j] = __float2bfloat16_rn(in ? (v.x > 0.0f ? v.x : 0.0f) : 0.0f);
-        v8[2 * j + 1] = __float2bfloat16_rn(in ? (v.y > 0.0f ? v.y : 0.0f) : 0.0f);
+        v8[2 * j] = in ? (v.x > 0.0f ? v.x : 0.0f) : 0.0f;
+        v8[2 * j + 1] = in ? (v.y > 0.0f ? v.y : 0.0f) : 0.0f;
       }
       *reinterpret_cast<uint4*>(sA1 + nf_slot3(r1) * NF_A1SLOT + hc * NF_A1G + (l0 + q + 1) * 16) =
-          *reinterpret_cast<const uint4*>(v8);
+          pack_bf16x8(v8);
     }
     const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
     // layer 2 of row s + 2 (bias, ReLU, zero outside the image) into the slot of row s - 1
@@ -984,13 +989,13 @@ __global__ void __launch_bounds__(128) nn_net_tc_kernel(NnArgs n, int band) {
       unsigned char* dst = sA2 + nf_slot3(r2) * NF_A2SLOT + (p + 1) * 16;
 #pragma unroll
       for (int g = 0; g < 4; ++g) {
-        __align__(16) __nv_bfloat16 v8[8];
+        float v8[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
           const float z = __uint_as_float(r[8 * g + e]) + sb2[8 * g + e];
-          v8[e] = __float2bfloat16_rn(in ? (z > 0.0f ? z : 0.0f) : 0.0f);
+          v8[e] = in ? (z > 0.0f ? z : 0.0f) : 0.0f;
         }
-        *reinterpret_cast<uint4*>(dst + g * NF_A1G) = *reinterpret_cast<const uint4*>(v8);
+        *reinterpret_cast<uint4*>(dst + g * NF_A1G) = pack_bf16x8(v8);
       }
     }
     // layer 3 of row s (bias, tanh) to the FP32 output
@@ -1043,11 +1048,11 @@ __global__ void nn_seed_eval_kernel(NnArgs n, const double* __restrict__ GY, lon
     g[k * pix + p] = (T)(GY[k * pix + p] * n.scale[k] * (1.0 - t * t));
   }
   if (gh) {
-    __align__(16) __nv_bfloat16 v8[8];
+    float v8[8];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) v8[e] = __float2bfloat16_rn(e < 4 ? (float)g[e * pix + p] : 0.0f);
+    for (int e = 0; e < 8; ++e) v8[e] = e < 4 ? (float)g[e * pix + p] : 0.0f;
     uint4* dst = reinterpret_cast<uint4*>(gh + p * 16);
-    dst[0] = *reinterpret_cast<const uint4*>(v8);
+    dst[0] = pack_bf16x8(v8);
     dst[1] = make_uint4(0u, 0u, 0u, 0u);
   }
 }
@@ -1142,11 +1147,11 @@ __global__ void nn_seed_kernel(NnArgs n, AdjArgs a, __nv_bfloat16* gh) {
     g[k * pix + p] = (T)(Fb * n.scale[k] * (1.0 - t * t));
   }
   if (gh) {
-    __align__(16) __nv_bfloat16 v8[8];
+    float v8[8];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) v8[e] = __float2bfloat16_rn(e < 4 ? (float)g[e * pix + p] : 0.0f);
+    for (int e = 0; e < 8; ++e) v8[e] = e < 4 ? (float)g[e * pix + p] : 0.0f;
     uint4* dst = reinterpret_cast<uint4*>(gh + (d == 0 ? 0LL : 16LL * n.pix0) + p * 16);
-    dst[0] = *reinterpret_cast<const uint4*>(v8);
+    dst[0] = pack_bf16x8(v8);
     dst[1] = make_uint4(0u, 0u, 0u, 0u);
   }
 }
