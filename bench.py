@@ -335,8 +335,8 @@ def run_ours(args):
         neural = {"flops_per_cell_stage_network": NN_FLOPS_PER_CELL_STAGE,
                   "note": "network forward per stage: 2 face images (x faces, y faces) x 6336 multiply-adds "
                           "per face; ms per SSP-RK3 step with the network on, and the reverse step "
-                          "(js_step_vjp with the weight gradient); bf16: layers 2-3 of the forward on the "
-                          "tensor cores, the rest FP32, the forward-only stages' network in one fused launch; "
+                          "(js_step_vjp with the weight gradient); bf16: the forward's three layers on the "
+                          "tensor cores (BF16 operands, FP32 accumulation), the forward-only stages' network in one fused launch; "
                           "bf16-layerwise: the same arithmetic and results, one launch per layer"}
         for name in ("bf16", "bf16-layerwise", "fp32", "fp64"):
             solver.set_neural(w, norm, w_bar=wb, precision=name)

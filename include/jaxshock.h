@@ -239,8 +239,11 @@ int js_rows_unpack(js_ctx* ctx, double* U, int row0, int nrows, const double* bu
  *          order: reproducible)
  *   norm   host array mean[4], sd[4] (> 0), scale[4] (copied)
  *   precision  JS_NN_F64 (FP64 network arithmetic), JS_NN_F32 (FP32 on the CUDA cores) or
- *          JS_NN_BF16 (the 16->32 and 32->4 layers of the forward pass on the tensor cores with
- *          BF16 operands and FP32 accumulation, the rest FP32); the solver stays FP64.
+ *          JS_NN_BF16 (the three layers of the forward pass on the tensor cores with BF16
+ *          operands and FP32 accumulation; in the reverse the data gradients of layers 3 and 2
+ *          likewise, the first layer's data gradient and all weight gradients FP32); the solver
+ *          stays FP64 (with FP32 and BF16 networks the face images and the network's flux
+ *          divergence are formed in FP32 and added to the FP64 state).
  *          In BF16 precision the stages that no reverse pass reads evaluate the whole network
  *          in one launch (activations kept on chip); JS_NN_BF16 | JS_NN_LAYERWISE runs its
  *          three layers as separate launches instead, with bit-identical results

@@ -21,7 +21,8 @@
 //
 // Arithmetic type T: double (FP64, the oracle's precision) or float (FP32 on the CUDA
 // cores; the network is a dense contraction of 6336 multiply-adds per face, which FP64
-// would make about 20x the cost of the FP64 solver it corrects).
+// would make about 20x the cost of the FP64 solver it corrects).  BF16 precision (float
+// buffers): the forward's three layers on the tensor cores, BF16 operands, FP32 accumulation.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -584,12 +585,12 @@ constexpr int TC_ROWS = 16;
 // gradient, the same implicit GEMM over the output gradient with the weights transposed and
 // flipped, gin[ci] = sum over taps and co of w[co][ci][2-ky][2-kx] gout[co](pixel + (ky-1, kx-1)),
 // times the ReLU mask (aprev > 0) of the layer below for ACT 1.  CINR <= CIN: channels present
-// in the input (the rest are zero padding up to the MMA's K of 16).
+// in the input (the rest are zero padding up to the MMA's K of 16; the first layer's 4).
 template <int CIN, int COUT, int ACT, int MODE = 0, int CINR = CIN>
 __global__ void __launch_bounds__(128) nn_conv_tc_kernel(NnArgs n, const void* inh, void* out, int woff,
                                                          void* outh, const void* aprev) {
   static_assert(CIN % 16 == 0, "input channels in groups of 16 (K of one MMA)");
-  static_assert(CINR <= CIN && (MODE == 1 || CINR == CIN), "padding only in the data gradient");
+  static_assert(CINR <= CIN, "present channels within the padded ones");
   constexpr int N = (COUT + 15) / 16 * 16;   // MMA N (multiple of 16 for M = 128)
   constexpr int KG = CIN / 8;                // 8-channel groups
   constexpr int GSTRIDE = TC_COLS * 16;      // bytes of one channel group of one row slot
@@ -625,11 +626,11 @@ __global__ void __launch_bounds__(128) nn_conv_tc_kernel(NnArgs n, const void* i
     const int tap = k / (CIN * N), r = k % (CIN * N), ci = r / N, co = r % N;
     float v = 0.0f;
     if (co < COUT && ci < CINR)
-      v = (MODE == 0) ? (float)n.w[woff + (co * CIN + ci) * 9 + tap] : (float)n.w[woff + (ci * COUT + co) * 9 + 8 - tap];
+      v = (MODE == 0) ? (float)n.w[woff + (co * CINR + ci) * 9 + tap] : (float)n.w[woff + (ci * COUT + co) * 9 + 8 - tap];
     B16[tap * (BTAP / 2) + ((ci >> 3) * N + co) * 8 + (ci & 7)] = __float2bfloat16_rn(v);
   }
   if (MODE == 0)
-    for (int k = tid; k < COUT; k += 128) sbias[k] = (float)n.w[woff + COUT * CIN * 9 + k];
+    for (int k = tid; k < COUT; k += 128) sbias[k] = (float)n.w[woff + COUT * CINR * 9 + k];
   __syncthreads();
   const uint32_t tmem = tmem_base;
   const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
@@ -758,59 +759,47 @@ __global__ void __launch_bounds__(128) nn_conv_tc_kernel(NnArgs n, const void* i
 }
 
 // ---------------------------------------------------------------------------------------
-// The whole network in one launch for forward-only BF16 stages: layer 1 (FP32 on the CUDA
-// cores, the arithmetic of nn_conv_f32_kernel) and layers 2 and 3 (tcgen05, the MMA sequence of
-// nn_conv_tc_kernel), so the results equal the three separate launches bit for bit, while the
+// The whole network in one launch for forward-only BF16 stages: all three layers as tcgen05
+// implicit GEMMs with the MMA sequences of nn_conv_tc_kernel (layer 1's 4 input channels padded
+// to the MMA's K of 16), so the results equal the three separate launches bit for bit, while the
 // 16- and 32-channel activations never leave shared memory.
 //
 // A block owns a 128-pixel-wide strip (local pixel p at x = x0 - 2 + p; layer 1 is exact on all
 // 128 pixels, layer 2 on 1..126, layer 3 on 2..125, so a strip yields 124 outputs) and a band of
 // output rows.  Step s of the band computes layer 3 on row s, layer 2 on row s + 2 and layer 1 on
-// row s + 4: each layer reads only rows the step before produced, so one thread issues the
-// MMAs of both tensor-core layers at the start of the step and they run while all threads
-// compute layer 1 on the CUDA cores; then one bounded mbarrier wait and the epilogues.
-//   rings: FP32 input rows (4 slots: rows s+3..s+5 read, row s+6 in flight), layer-1 and
-//   layer-2 rows as BF16 core matrices (3 slots each: a slot is rewritten only after the MMAs
-//   that read it have completed)
+// row s + 4: each layer reads only rows the step before produced, so one thread issues the 36
+// MMAs of the step at its start, one bounded mbarrier wait later the epilogues write the new
+// rows.  Rings (a slot is rewritten only after the MMAs that read it have completed):
+//   FP32 input rows, 2 staging slots (row s + 6 to convert, row s + 7 in flight);
+//   BF16 input rows s + 3 .. s + 5 (3 slots, 8-channel core matrices: 4 channels and 4 zeros;
+//   the MMA's second K group points at a zero region), layer-1 and layer-2 rows (3 slots each).
 // ---------------------------------------------------------------------------------------
-// two FP32 fused multiply-adds in one instruction (each IEEE-rounded, as fmaf)
-__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b,
-                                                    unsigned long long c) {
-  unsigned long long d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-__device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
-  return (unsigned long long)__float_as_uint(lo) | ((unsigned long long)__float_as_uint(hi) << 32);
-}
-__device__ __forceinline__ float2 unpack2(unsigned long long v) {
-  return make_float2(__uint_as_float((unsigned)v), __uint_as_float((unsigned)(v >> 32)));
-}
-
 constexpr int NF_OUT = TC_M - 4;                 // output pixels per strip
-constexpr int NF_XS = 4, NF_AS = 3;              // ring slots
-constexpr int NF_XSLOT = 4 * TC_COLS * 4;        // FP32 input row: 4 channels x 130 pixels
-constexpr int NF_A1G = TC_COLS * 16;             // one 8-channel group of a BF16 row (core matrices)
-constexpr int NF_A1SLOT = 2 * NF_A1G;            // 16 channels
-constexpr int NF_A2SLOT = 4 * NF_A1G;            // 32 channels
+constexpr int NF_AS = 3;                         // ring slots
+constexpr int NF_G = TC_COLS * 16;               // one 8-channel group of a BF16 row (core matrices)
+constexpr int NF_A1SLOT = 2 * NF_G;              // 16 channels
+constexpr int NF_A2SLOT = 4 * NF_G;              // 32 channels
+constexpr int NF_XF = 4 * TC_COLS;               // floats of an FP32 input row: 4 channels x 130 pixels
+constexpr int NF_B1TAP = 2 * 16 * 16;            // layer-1 weights of one tap: [group 2][co 16][8]
 constexpr int NF_B2TAP = 2 * 32 * 16;            // layer-2 weights of one tap: [group 2][co 32][8]
 constexpr int NF_B3TAP = 4 * 16 * 16;            // layer-3 weights of one tap: [group 4][co 16][8]
 constexpr int NF_OFF_A2 = NF_AS * NF_A1SLOT;
-constexpr int NF_OFF_B2 = NF_OFF_A2 + NF_AS * NF_A2SLOT;
+constexpr int NF_OFF_X = NF_OFF_A2 + NF_AS * NF_A2SLOT;   // BF16 input rows, then the zero group
+constexpr int NF_OFF_Z = NF_OFF_X + NF_AS * NF_G;
+constexpr int NF_OFF_B1 = NF_OFF_Z + NF_G;
+constexpr int NF_OFF_B2 = NF_OFF_B1 + 9 * NF_B1TAP;
 constexpr int NF_OFF_B3 = NF_OFF_B2 + 9 * NF_B2TAP;
-constexpr int NF_OFF_X = NF_OFF_B3 + 9 * NF_B3TAP;
-constexpr int NF_OFF_W1 = NF_OFF_X + NF_XS * NF_XSLOT;
-constexpr int NF_OFF_BIAS = NF_OFF_W1 + 36 * 16 * 4;
+constexpr int NF_OFF_XF = NF_OFF_B3 + 9 * NF_B3TAP;
+constexpr int NF_OFF_BIAS = NF_OFF_XF + 2 * NF_XF * 4;
 constexpr int NF_SMEM = NF_OFF_BIAS + (16 + 32 + 4) * 4;
-__host__ __device__ constexpr int nf_slot4(int r) { return (r + 16) & 3; }   // rows >= -16
 __host__ __device__ constexpr int nf_slot3(int r) { return (r + 15) % 3; }   // rows >= -15
 
 __global__ void __launch_bounds__(128) nn_net_tc_kernel(NnArgs n, int band) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* sA1 = smem_raw;
   unsigned char* sA2 = smem_raw + NF_OFF_A2;
-  float* sX = reinterpret_cast<float*>(smem_raw + NF_OFF_X);
-  float* sW1 = reinterpret_cast<float*>(smem_raw + NF_OFF_W1);
+  unsigned char* sX = smem_raw + NF_OFF_X;
+  float* sXf = reinterpret_cast<float*>(smem_raw + NF_OFF_XF);
   float* sb1 = reinterpret_cast<float*>(smem_raw + NF_OFF_BIAS);
   float* sb2 = sb1 + 16;
   float* sb3 = sb2 + 32;
@@ -830,9 +819,14 @@ __global__ void __launch_bounds__(128) nn_net_tc_kernel(NnArgs n, int band) {
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) mbar_init(&bar);
-  // weights: layer 1 FP32 [ci][ky][kx][co]; layers 2 and 3 BF16 per tap [group][co][8 channels]
-  // (converted FP64 -> FP32 -> BF16 as the separate layers do), biases FP32
-  for (int k = tid; k < 16 * 36; k += 128) sW1[(k % 36) * 16 + k / 36] = (float)n.w[NN_OFF1 + k];
+  // weights per tap as [group][co][8 channels], converted FP64 -> FP32 -> BF16 as the separate
+  // layers do (zeros beyond the real channels); biases FP32
+  __nv_bfloat16* B1 = reinterpret_cast<__nv_bfloat16*>(smem_raw + NF_OFF_B1);
+  for (int k = tid; k < 9 * 16 * 16; k += 128) {
+    const int tap = k / (16 * 16), r = k % (16 * 16), ci = r / 16, co = r % 16;
+    B1[tap * (NF_B1TAP / 2) + ((ci >> 3) * 16 + co) * 8 + (ci & 7)] =
+        __float2bfloat16_rn(ci < 4 ? (float)n.w[NN_OFF1 + (co * 4 + ci) * 9 + tap] : 0.0f);
+  }
   __nv_bfloat16* B2 = reinterpret_cast<__nv_bfloat16*>(smem_raw + NF_OFF_B2);
   for (int k = tid; k < 9 * 16 * 32; k += 128) {
     const int tap = k / (16 * 32), r = k % (16 * 32), ci = r / 32, co = r % 32;
@@ -848,18 +842,9 @@ __global__ void __launch_bounds__(128) nn_net_tc_kernel(NnArgs n, int band) {
   for (int k = tid; k < 16; k += 128) sb1[k] = (float)n.w[NN_OFF1 + 16 * 36 + k];
   for (int k = tid; k < 32; k += 128) sb2[k] = (float)n.w[NN_OFF2 + 32 * 144 + k];
   for (int k = tid; k < 4; k += 128) sb3[k] = (float)n.w[NN_OFF3 + 4 * 288 + k];
-  // the activation rings start zeroed (rows before the band's first valid ones are read only by
-  // outputs that are never stored)
-  for (int k = tid; k < NF_OFF_B2 / 16; k += 128) reinterpret_cast<uint4*>(smem_raw)[k] = make_uint4(0, 0, 0, 0);
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t tmem = tmem_base;
-  const uint32_t a1 = smem_u32(sA1), a2 = smem_u32(sA2);
-  const uint32_t b2 = smem_u32(smem_raw + NF_OFF_B2), b3 = smem_u32(smem_raw + NF_OFF_B3);
-  constexpr uint32_t idesc2 = umma_idesc_bf16(TC_M, 32), idesc3 = umma_idesc_bf16(TC_M, 16);
-  constexpr long long kBudget = 2000000000LL;  // about one second of SM clock
+  // the rings and the zero group start zeroed (rows before the band's first valid ones are read
+  // only by outputs that are never stored)
+  for (int k = tid; k < NF_OFF_B1 / 16; k += 128) reinterpret_cast<uint4*>(smem_raw)[k] = make_uint4(0, 0, 0, 0);
 
   const int it = blockIdx.x;
   const int d = (it < items0) ? 0 : 1;
@@ -873,86 +858,89 @@ __global__ void __launch_bounds__(128) nn_net_tc_kernel(NnArgs n, int band) {
   float* T3 = chan_img<float>(n.T3, 4, d, n.pix0);
   const int p = tid, xp = xs + p;
   const bool col_in = xp >= 0 && xp < Wd;
-  const int l0 = 2 * (tid & 63), hc = tid >> 6;  // layer 1: pixels l0, l0 + 1, channel group hc
-  // input row r (zeros outside the image): 4 channels x 130 pixels (local -1 .. 128), 4-byte
-  // copies; element tid + 128 i of a row slot is channel / column xofs[i] of the image row
-  constexpr int NXL = (4 * TC_COLS + 127) / 128;
+  // FP32 input row r (zeros outside the image): 4 channels x 130 pixels (local -1 .. 128), 4-byte
+  // copies into staging slot r & 1; element tid + 128 i of a slot is channel / column xofs[i]
+  constexpr int NXL = (NF_XF + 127) / 128;
   long long xofs[NXL];
   bool xok[NXL];
 #pragma unroll
   for (int i = 0; i < NXL; ++i) {
     const int k = tid + 128 * i, ch = k / TC_COLS, gx = xs - 1 + k % TC_COLS;
-    xok[i] = k < 4 * TC_COLS && gx >= 0 && gx < Wd;
+    xok[i] = k < NF_XF && gx >= 0 && gx < Wd;
     xofs[i] = ch * pix + gx;
   }
   auto load_x = [&](int r) {
-    float* slot = sX + nf_slot4(r) * (NF_XSLOT / 4) + tid;
+    float* slot = sXf + (r & 1) * NF_XF + tid;
     const bool row_in = r >= 0 && r < H;
     const float* Xr = X + (long long)r * Wd;
 #pragma unroll
     for (int i = 0; i < NXL; ++i)
-      if (tid + 128 * i < 4 * TC_COLS) cp_async4(slot + 128 * i, row_in && xok[i] ? Xr + xofs[i] : X, row_in && xok[i]);
+      if (tid + 128 * i < NF_XF) cp_async4(slot + 128 * i, row_in && xok[i] ? Xr + xofs[i] : X, row_in && xok[i]);
     cp_async_commit();
   };
+  // staged FP32 row r to its BF16 ring slot: per pixel one 16-byte core-matrix row (4 channels
+  // rounded to BF16, 4 zeros)
+  auto convert_x = [&](int r) {
+    const float* src = sXf + (r & 1) * NF_XF;
+    unsigned char* dst = sX + nf_slot3(r) * NF_G;
+    for (int c = tid; c < TC_COLS; c += 128)
+      *reinterpret_cast<uint4*>(dst + c * 16) =
+          make_uint4(pack_bf16x2(src[c], src[TC_COLS + c]), pack_bf16x2(src[2 * TC_COLS + c], src[3 * TC_COLS + c]),
+                     0u, 0u);
+  };
   const int s0 = h0 - 6;
-  load_x(s0 + 3);
-  load_x(s0 + 4);
-  load_x(s0 + 5);
+  // prologue: input rows s0 + 3 .. s0 + 5 into the BF16 ring, row s0 + 6 staged
+  for (int r = s0 + 3; r <= s0 + 5; ++r) {
+    load_x(r);
+    cp_async_wait<0>();
+    __syncthreads();
+    convert_x(r);
+    __syncthreads();
+  }
+  load_x(s0 + 6);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  const uint32_t a1 = smem_u32(sA1), a2 = smem_u32(sA2), ax = smem_u32(sX);
+  const uint32_t b1 = smem_u32(smem_raw + NF_OFF_B1), b2 = smem_u32(smem_raw + NF_OFF_B2),
+                 b3 = smem_u32(smem_raw + NF_OFF_B3);
+  constexpr uint32_t idesc16 = umma_idesc_bf16(TC_M, 16), idesc32 = umma_idesc_bf16(TC_M, 32);
+  constexpr long long kBudget = 2000000000LL;  // about one second of SM clock
   unsigned phase = 0u;
   bool ok = true;
   for (int s = s0; s < h1; ++s) {
-    load_x(s + 6);  // into the slot of row s + 2, whose last reader (layer 1 of row s + 3) is done
+    load_x(s + 7);  // into the staging slot of row s + 5, converted in the step before
     if (tid == 0) {
+      // layer 1 of row s + 4 from input rows s + 3 .. s + 5, accumulator columns 48 .. 63 (the
+      // second K group of the A operand is the zero group: LBO from the row's slot to it)
+      for (int tap = 0; tap < 9; ++tap) {
+        const int ky = tap / 3, kx = tap % 3, sl = nf_slot3(s + 3 + ky);
+        umma_bf16(tmem + 48, umma_smem_desc(ax + sl * NF_G + kx * 16, (NF_AS - sl) * NF_G, 128),
+                  umma_smem_desc(b1 + tap * NF_B1TAP, 16 * 16, 128), idesc16, tap > 0 ? 1 : 0);
+      }
       // layer 2 of row s + 2 from layer-1 rows s + 1 .. s + 3, accumulator columns 0 .. 31
       for (int tap = 0; tap < 9; ++tap) {
         const int ky = tap / 3, kx = tap % 3;
         const uint32_t slot = a1 + nf_slot3(s + 1 + ky) * NF_A1SLOT;
-        umma_bf16(tmem, umma_smem_desc(slot + kx * 16, NF_A1G, 128),
-                  umma_smem_desc(b2 + tap * NF_B2TAP, 32 * 16, 128), idesc2, tap > 0 ? 1 : 0);
+        umma_bf16(tmem, umma_smem_desc(slot + kx * 16, NF_G, 128),
+                  umma_smem_desc(b2 + tap * NF_B2TAP, 32 * 16, 128), idesc32, tap > 0 ? 1 : 0);
       }
       // layer 3 of row s from layer-2 rows s - 1 .. s + 1, accumulator columns 32 .. 47
       for (int tap = 0; tap < 9; ++tap) {
         const int ky = tap / 3, kx = tap % 3;
         const uint32_t slot = a2 + nf_slot3(s - 1 + ky) * NF_A2SLOT;
         for (int kc = 0; kc < 2; ++kc)
-          umma_bf16(tmem + 32, umma_smem_desc(slot + 2 * kc * NF_A1G + kx * 16, NF_A1G, 128),
-                    umma_smem_desc(b3 + tap * NF_B3TAP + 2 * kc * 16 * 16, 16 * 16, 128), idesc3,
+          umma_bf16(tmem + 32, umma_smem_desc(slot + 2 * kc * NF_G + kx * 16, NF_G, 128),
+                    umma_smem_desc(b3 + tap * NF_B3TAP + 2 * kc * 16 * 16, 16 * 16, 128), idesc16,
                     (tap > 0 || kc > 0) ? 1 : 0);
       }
       umma_commit(&bar);
     }
-    cp_async_wait<1>();  // this thread's copies of input rows up to s + 5 have landed
-    __syncthreads();
-    // layer 1 of row s + 4 (FP32, bias first, then input channel, kernel row, column) at pixels
-    // l0, l0 + 1 and channels 8 hc .. 8 hc + 7: packed FMAs on channel pairs, each weight pair
-    // feeding both pixels
-    const int r1 = s + 4;
-    unsigned long long acc[2][4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[0][j] = acc[1][j] = pack2(sb1[8 * hc + 2 * j], sb1[8 * hc + 2 * j + 1]);
-#pragma unroll
-    for (int ci = 0; ci < 4; ++ci)
-#pragma unroll
-      for (int ky = 0; ky < 3; ++ky) {
-        const float* row = sX + nf_slot4(r1 - 1 + ky) * (NF_XSLOT / 4) + ci * TC_COLS + l0;
-        const float2 xa = *reinterpret_cast<const float2*>(row);
-        const float2 xb = *reinterpret_cast<const float2*>(row + 2);
-        const float xv[4] = {xa.x, xa.y, xb.x, xb.y};
-#pragma unroll
-        for (int kx = 0; kx < 3; ++kx) {
-          const float4* w4 = reinterpret_cast<const float4*>(sW1 + ((ci * 3 + ky) * 3 + kx) * 16 + 8 * hc);
-          const float4 wa = w4[0], wb = w4[1];
-          const unsigned long long w2[4] = {pack2(wa.x, wa.y), pack2(wa.z, wa.w), pack2(wb.x, wb.y),
-                                            pack2(wb.z, wb.w)};
-          const unsigned long long x0 = pack2(xv[kx], xv[kx]), x1 = pack2(xv[kx + 1], xv[kx + 1]);
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            acc[0][j] = ffma2(w2[j], x0, acc[0][j]);
-            acc[1][j] = ffma2(w2[j], x1, acc[1][j]);
-          }
-        }
-      }
-    // every thread waits (bounded) for the step's MMAs; the outcome is made uniform
+    cp_async_wait<1>();  // this thread's copies of input row s + 6 have landed
+    // every thread waits (bounded) for the step's MMAs; the outcome is made uniform (and the
+    // barrier makes every thread's staged copies visible)
     ok = __syncthreads_and(mbar_wait(&bar, phase, kBudget) ? 1 : 0) != 0;
     if (!ok) {
       if (tid == 0) atomicOr(n.err, ERR_TIMEOUT_BIT);
@@ -961,23 +949,27 @@ __global__ void __launch_bounds__(128) nn_net_tc_kernel(NnArgs n, int band) {
     }
     phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // layer 1 of row s + 4 (ReLU, zero outside the image) into the slot of row s + 1: channel
-    // group hc of pixels l0 and l0 + 1
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const int xq = xs + l0 + q;
-      const bool in = xq >= 0 && xq < Wd && r1 >= 0 && r1 < H;
-      float v8[8];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const float2 v = unpack2(acc[q][j]);
-        v8[2 * j] = in ? (v.x > 0.0f ? v.x : 0.0f) : 0.0f;
-        v8[2 * j + 1] = in ? (v.y > 0.0f ? v.y : 0.0f) : 0.0f;
-      }
-      *reinterpret_cast<uint4*>(sA1 + nf_slot3(r1) * NF_A1SLOT + hc * NF_A1G + (l0 + q + 1) * 16) =
-          pack_bf16x8(v8);
-    }
+    convert_x(s + 6);  // into the slot of row s + 3, whose last reader (layer 1 of row s + 4) is done
     const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+    // layer 1 of row s + 4 (bias, ReLU, zero outside the image) into the slot of row s + 1
+    {
+      const int r1 = s + 4;
+      const bool in = col_in && r1 >= 0 && r1 < H;
+      uint32_t r[16];
+      tmem_ld16(tl + 48, r);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      unsigned char* dst = sA1 + nf_slot3(r1) * NF_A1SLOT + (p + 1) * 16;
+#pragma unroll
+      for (int g = 0; g < 2; ++g) {
+        float v8[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const float z = __uint_as_float(r[8 * g + e]) + sb1[8 * g + e];
+          v8[e] = in ? (z > 0.0f ? z : 0.0f) : 0.0f;
+        }
+        *reinterpret_cast<uint4*>(dst + g * NF_G) = pack_bf16x8(v8);
+      }
+    }
     // layer 2 of row s + 2 (bias, ReLU, zero outside the image) into the slot of row s - 1
     {
       const int r2 = s + 2;
@@ -995,7 +987,7 @@ __global__ void __launch_bounds__(128) nn_net_tc_kernel(NnArgs n, int band) {
           const float z = __uint_as_float(r[8 * g + e]) + sb2[8 * g + e];
           v8[e] = in ? (z > 0.0f ? z : 0.0f) : 0.0f;
         }
-        *reinterpret_cast<uint4*>(dst + g * NF_A1G) = pack_bf16x8(v8);
+        *reinterpret_cast<uint4*>(dst + g * NF_G) = pack_bf16x8(v8);
       }
     }
     // layer 3 of row s (bias, tanh) to the FP32 output
@@ -1020,6 +1012,20 @@ __global__ void __launch_bounds__(128) nn_net_tc_kernel(NnArgs n, int band) {
   __syncthreads();
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem) : "memory");
+}
+
+// the FP32 network input X (planar, 4 channels) as the first tensor-core layer's input: BF16
+// pixel-major, 16 channels per pixel (4 and 12 zeros)
+__global__ void nn_x16_kernel(NnArgs n, __nv_bfloat16* __restrict__ Xh) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long pix = n.pix0 + (n.nimg > 1 ? (long long)n.H[1] * n.W[1] : 0LL);
+  if (t >= pix) return;
+  const int d = (t < n.pix0) ? 0 : 1;
+  const long long q = (d == 0) ? t : t - n.pix0, pd = (long long)n.H[d] * n.W[d];
+  const float* X = chan_img<float>(n.X, 4, d, n.pix0);
+  uint4* dst = reinterpret_cast<uint4*>(Xh + t * 16);
+  dst[0] = make_uint4(pack_bf16x2(X[q], X[pd + q]), pack_bf16x2(X[2 * pd + q], X[3 * pd + q]), 0u, 0u);
+  dst[1] = make_uint4(0u, 0u, 0u, 0u);
 }
 
 // network input from an FP64 image / scaled FP64 output (js_nn_eval)
@@ -1469,15 +1475,20 @@ cudaError_t layers_t(const NnArgs& n, cudaStream_t s) {
   cudaError_t e;
   const bool tc = std::is_same<T, float>::value && n.bf16;
   if (tc && !n.keep && n.fused) return net_tc(n, s);
-  // (the tensor-core layers read BF16 pixel-major copies written by the layer before them; their
-  // FP32 activations are written only for a reverse pass)
-  void* a1 = (tc && !n.keep) ? nullptr : n.A1;
-  void* a2 = (tc && !n.keep) ? nullptr : n.A2;
-  if ((e = conv<T, 4, 16, 0>(n, n.X, a1, NN_OFF1, s, tc ? n.A1h : nullptr)) != cudaSuccess) return e;
+  // (the tensor-core layers read BF16 pixel-major copies written by the step before them: the
+  // input's into the G16 scratch; their FP32 activations are written only for a reverse pass)
   if (tc) {
+    void* a1 = n.keep ? n.A1 : nullptr;
+    void* a2 = n.keep ? n.A2 : nullptr;
+    const long long pix = n.pix0 + (n.nimg > 1 ? (long long)n.H[1] * n.W[1] : 0LL);
+    __nv_bfloat16* xh = static_cast<__nv_bfloat16*>(n.G16);
+    nn_x16_kernel<<<(unsigned)((pix + 255) / 256), 256, 0, s>>>(n, xh);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = conv_tc<16, 16, 0, 0, 4>(n, xh, a1, NN_OFF1, s, n.A1h)) != cudaSuccess) return e;
     if ((e = conv_tc<16, 32, 0>(n, n.A1h, a2, NN_OFF2, s, n.A2h)) != cudaSuccess) return e;
     return conv_tc<32, 4, 1>(n, n.A2h, n.T3, NN_OFF3, s);
   }
+  if ((e = conv<T, 4, 16, 0>(n, n.X, n.A1, NN_OFF1, s)) != cudaSuccess) return e;
   if ((e = conv<T, 16, 32, 0>(n, n.A1, n.A2, NN_OFF2, s)) != cudaSuccess) return e;
   return conv<T, 32, 4, 1>(n, n.A2, n.T3, NN_OFF3, s);
 }

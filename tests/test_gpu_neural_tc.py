@@ -1,9 +1,9 @@
-"""The neural flux network on the tensor cores (BF16 precision: the 16->32 and 32->4 layers as
-tcgen05 implicit GEMMs, BF16 operands, FP32 accumulation) and js_nn_eval.
+"""The neural flux network on the tensor cores (BF16 precision: the three layers of the forward
+pass as tcgen05 implicit GEMMs, BF16 operands, FP32 accumulation) and js_nn_eval.
 
 * js_nn_eval in FP64 equals the oracle's network; in FP32 within FP32 rounding.
-* BF16: equal to a CPU emulation of the same arithmetic (torch: FP32 first layer, inputs and
-  weights of layers 2 and 3 rounded to BF16, FP32 accumulation): the median difference at
+* BF16: equal to a CPU emulation of the same arithmetic (torch: every layer's inputs and
+  weights rounded to BF16, FP32 accumulation): the median difference at
   FP32 rounding, the 99th percentile within 1e-3 and every output within 1e-2 of the output
   range (a layer input on a BF16 rounding boundary may round the other way); a wrong operand
   layout gives errors of order one everywhere.  Images span several 128-pixel blocks with a
@@ -61,7 +61,7 @@ def _emulate_bf16(torch, w, X, scale):
     w3, b3 = t[5232:6384].view(4, 32, 3, 3), t[6384:]
     bf = lambda a: a.to(torch.bfloat16).to(torch.float32)
     x = torch.tensor(X, dtype=torch.float32)[None]
-    a1 = torch.relu(F.conv2d(x, w1, b1, padding=1))
+    a1 = torch.relu(F.conv2d(bf(x), bf(w1), b1, padding=1))
     a2 = torch.relu(F.conv2d(bf(a1), bf(w2), b2, padding=1))
     z3 = F.conv2d(bf(a2), bf(w3), b3, padding=1)
     return (torch.tensor(scale, dtype=torch.float32)[:, None, None] * torch.tanh(z3[0])).double().numpy()
@@ -186,7 +186,7 @@ def _emulate_bf16_vjp(torch, w, X, GY, scale):
     w1, b1, w2, b2, w3, b3 = _torch_net(torch, w, torch.float32)
     bf = lambda a: a.to(torch.bfloat16).to(torch.float32)
     x = torch.tensor(X, dtype=torch.float32)[None]
-    a1 = torch.relu(F.conv2d(x, w1, b1, padding=1))
+    a1 = torch.relu(F.conv2d(bf(x), bf(w1), b1, padding=1))
     a2 = torch.relu(F.conv2d(bf(a1), bf(w2), b2, padding=1))
     t3 = torch.tanh(F.conv2d(bf(a2), bf(w3), b3, padding=1))
     g4 = (torch.tensor(GY, dtype=torch.float64)[None] * torch.tensor(scale, dtype=torch.float64)[:, None, None]
@@ -230,8 +230,9 @@ def test_nn_eval_vjp_fp64_fp32_and_bf16(env, shape):
     assert d.max() <= 1e-2 * span, d.max() / span
     dw = np.abs(gb - ew)
     assert dw.max() <= 1e-3 * np.abs(ew).max(), dw.max() / np.abs(ew).max()
-    # and against the exact reverse: of the order of BF16 rounding
-    assert np.quantile(np.abs(gx - gx_ref), 0.99) <= 5e-2 * np.abs(gx_ref).max()
+    # and against the exact reverse: of the order of BF16 rounding (every layer's inputs and weights
+    # rounded to BF16 in the forward, whose ReLU masks the reverse applies: a few percent)
+    assert np.quantile(np.abs(gx - gx_ref), 0.99) <= 1e-1 * np.abs(gx_ref).max()
 
 
 # The fused network kernel (one launch for the three layers of a forward-only BF16 stage) runs the
@@ -257,11 +258,11 @@ def test_fused_network_equals_layerwise_launches(env, shape):
     assert np.abs(out["bf16"]).max() > 0
 
 
-@pytest.mark.parametrize("n", [96, 1024])
+@pytest.mark.parametrize("n", [96, 1024, "sod"])
 def test_fused_network_solver_steps_equal_layerwise(env, n):
     torch, B = env
     from paper_2601_04400_gb300 import neural as NN
-    p = W.riemann2d(n)
+    p = W.sod(200) if n == "sod" else W.riemann2d(n)  # sod: one image, one row high
     U0 = to_dev(O.prim_to_cons(p, p.W0))
     # the benchmark's network: He-uniform weights, outputs scaled to a tenth of the states' spread
     w = NN.init_weights(0, zero_last=False) * 0.5
