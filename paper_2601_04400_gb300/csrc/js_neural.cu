@@ -818,7 +818,11 @@ __global__ void __launch_bounds__(128) nn_net_tc_kernel(NnArgs n, int band) {
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  if (tid == 0) mbar_init(&bar);
+  if (tid == 0) {
+    // three arrivals per phase: the threads issuing layer 1, 2 and 3 each commit to it
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 3;" ::"r"(smem_u32(&bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
   // weights per tap as [group][co][8 channels], converted FP64 -> FP32 -> BF16 as the separate
   // layers do (zeros beyond the real channels); biases FP32
   __nv_bfloat16* B1 = reinterpret_cast<__nv_bfloat16*>(smem_raw + NF_OFF_B1);
@@ -903,38 +907,60 @@ __global__ void __launch_bounds__(128) nn_net_tc_kernel(NnArgs n, int band) {
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
-  const uint32_t a1 = smem_u32(sA1), a2 = smem_u32(sA2), ax = smem_u32(sX);
-  const uint32_t b1 = smem_u32(smem_raw + NF_OFF_B1), b2 = smem_u32(smem_raw + NF_OFF_B2),
-                 b3 = smem_u32(smem_raw + NF_OFF_B3);
+  // shared-memory descriptors of the ring slots and weights; a byte offset o (a multiple of 16)
+  // adds o / 16 to a descriptor
+  uint64_t ds0, ds1, ds2, db;  // the three ring slots of the layer this thread issues, its weights
+  if (tid == 64) {  // layer 1: input rows (second K group: the zero region), weights [tap][2][16][8]
+    const uint32_t b = smem_u32(sX);
+    ds0 = umma_smem_desc(b, 3 * NF_G, 128);
+    ds1 = umma_smem_desc(b + NF_G, 2 * NF_G, 128);
+    ds2 = umma_smem_desc(b + 2 * NF_G, NF_G, 128);
+    db = umma_smem_desc(smem_u32(smem_raw + NF_OFF_B1), 16 * 16, 128);
+  } else if (tid == 32) {  // layer 2: layer-1 rows, weights [tap][2][32][8]
+    const uint32_t b = smem_u32(sA1);
+    ds0 = umma_smem_desc(b, NF_G, 128);
+    ds1 = umma_smem_desc(b + NF_A1SLOT, NF_G, 128);
+    ds2 = umma_smem_desc(b + 2 * NF_A1SLOT, NF_G, 128);
+    db = umma_smem_desc(smem_u32(smem_raw + NF_OFF_B2), 32 * 16, 128);
+  } else {  // layer 3: layer-2 rows, weights [tap][4][16][8]
+    const uint32_t b = smem_u32(sA2);
+    ds0 = umma_smem_desc(b, NF_G, 128);
+    ds1 = umma_smem_desc(b + NF_A2SLOT, NF_G, 128);
+    ds2 = umma_smem_desc(b + 2 * NF_A2SLOT, NF_G, 128);
+    db = umma_smem_desc(smem_u32(smem_raw + NF_OFF_B3), 16 * 16, 128);
+  }
+  auto dsl = [&](int r) {  // descriptor of the slot of row r
+    const int sl = nf_slot3(r);
+    return sl == 0 ? ds0 : (sl == 1 ? ds1 : ds2);
+  };
   constexpr uint32_t idesc16 = umma_idesc_bf16(TC_M, 16), idesc32 = umma_idesc_bf16(TC_M, 32);
   constexpr long long kBudget = 2000000000LL;  // about one second of SM clock
   unsigned phase = 0u;
   bool ok = true;
   for (int s = s0; s < h1; ++s) {
     load_x(s + 7);  // into the staging slot of row s + 5, converted in the step before
-    if (tid == 0) {
-      // layer 1 of row s + 4 from input rows s + 3 .. s + 5, accumulator columns 48 .. 63 (the
-      // second K group of the A operand is the zero group: LBO from the row's slot to it)
+    // one thread per layer issues its MMAs (into its own accumulator) and commits to the barrier
+    if (tid == 64) {
+      // layer 1 of row s + 4 from input rows s + 3 .. s + 5, accumulator columns 48 .. 63
       for (int tap = 0; tap < 9; ++tap) {
-        const int ky = tap / 3, kx = tap % 3, sl = nf_slot3(s + 3 + ky);
-        umma_bf16(tmem + 48, umma_smem_desc(ax + sl * NF_G + kx * 16, (NF_AS - sl) * NF_G, 128),
-                  umma_smem_desc(b1 + tap * NF_B1TAP, 16 * 16, 128), idesc16, tap > 0 ? 1 : 0);
+        const int ky = tap / 3, kx = tap % 3;
+        umma_bf16(tmem + 48, dsl(s + 3 + ky) + kx, db + tap * (NF_B1TAP / 16), idesc16, tap > 0 ? 1 : 0);
       }
+      umma_commit(&bar);
+    } else if (tid == 32) {
       // layer 2 of row s + 2 from layer-1 rows s + 1 .. s + 3, accumulator columns 0 .. 31
       for (int tap = 0; tap < 9; ++tap) {
         const int ky = tap / 3, kx = tap % 3;
-        const uint32_t slot = a1 + nf_slot3(s + 1 + ky) * NF_A1SLOT;
-        umma_bf16(tmem, umma_smem_desc(slot + kx * 16, NF_G, 128),
-                  umma_smem_desc(b2 + tap * NF_B2TAP, 32 * 16, 128), idesc32, tap > 0 ? 1 : 0);
+        umma_bf16(tmem, dsl(s + 1 + ky) + kx, db + tap * (NF_B2TAP / 16), idesc32, tap > 0 ? 1 : 0);
       }
+      umma_commit(&bar);
+    } else if (tid == 0) {
       // layer 3 of row s from layer-2 rows s - 1 .. s + 1, accumulator columns 32 .. 47
       for (int tap = 0; tap < 9; ++tap) {
         const int ky = tap / 3, kx = tap % 3;
-        const uint32_t slot = a2 + nf_slot3(s - 1 + ky) * NF_A2SLOT;
         for (int kc = 0; kc < 2; ++kc)
-          umma_bf16(tmem + 32, umma_smem_desc(slot + 2 * kc * NF_G + kx * 16, NF_G, 128),
-                    umma_smem_desc(b3 + tap * NF_B3TAP + 2 * kc * 16 * 16, 16 * 16, 128), idesc16,
-                    (tap > 0 || kc > 0) ? 1 : 0);
+          umma_bf16(tmem + 32, dsl(s - 1 + ky) + (2 * kc * NF_G) / 16 + kx,
+                    db + tap * (NF_B3TAP / 16) + kc * (2 * 16 * 16 / 16), idesc16, (tap > 0 || kc > 0) ? 1 : 0);
       }
       umma_commit(&bar);
     }
