@@ -523,9 +523,10 @@ def run_batched(args):
     e1.synchronize()
     t_vjp = e0.elapsed_time(e1) / reps
     ok = ok and batch.status() == 0
-    # the whole rollout: n_ro CFL steps forward (one launch, step sizes logged), then its
-    # reverse with sqrt(N) checkpoints (js_batch_rollout_vjp); the first reverse call
-    # allocates its workspace and is not timed
+    # the whole rollout: n_ro CFL steps forward (step sizes logged), then its reverse
+    # (js_batch_rollout_vjp) with the library's checkpoint spacing (every state when they fit in
+    # half the free device memory, else sqrt(N)); the first reverse call allocates its
+    # workspace and is not timed
     n_ro = args.rollout_steps
     roll = None
     if n_ro > 0:
@@ -556,13 +557,13 @@ def run_batched(args):
         e1.synchronize()
         t_ro_b = e0.elapsed_time(e1)
         ok = ok and batch.status() == 0
-        ck = int(round(n_ro ** 0.5))
+        ck = batch.rollout_spacing(n_ro)
         roll = {"steps": n_ro, "checkpoint_every": ck, "ms_forward_plain": t_ro_plain,
                 "ms_forward_checkpointed": t_ro_f, "ms_reverse": t_ro_b, "ratio": t_ro_b / t_ro_plain,
                 "note": "ratio: js_batch_rollout_vjp (per segment: re-run keeping its states + one "
                         "persistent reverse launch per step, from the checkpoints js_batch_rollout_"
-                        "forward kept) / the plain batched forward run of the same steps (one "
-                        "launch, device CFL)"}
+                        "forward kept; spacing 1 = every state kept, no re-runs) / the plain batched "
+                        "forward run of the same steps (one launch, device CFL)"}
     info = batch.info()
     if rank == 0:
         print(json.dumps({

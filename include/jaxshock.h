@@ -337,11 +337,11 @@ int js_batch_step_fixed(js_batch* b, int n_steps, const double* dt);
  * step size treated as fixed).
  *   lam   : host array of `count` device pointers; in: dL/dU_{n_steps}, out: dL/dU_0
  *   p_bar : host array of device pointers (JS_NPARAM doubles each, accumulated) or NULL
- *   ckpt  : checkpoint spacing (<= 0: the integer nearest sqrt(n_steps)): the forward keeps the
+ *   ckpt  : checkpoint spacing (<= 0: js_batch_rollout_spacing's choice): the forward keeps the
  *           state after every ckpt-th step (or those of js_batch_rollout_forward are used, see
  *           there); then, from the last segment back, each segment is re-run keeping its
  *           states and reversed step by step by the persistent reverse launch of
- *           js_batch_step_vjp.
+ *           js_batch_step_vjp (spacing 1: every state kept, no re-runs).
  * Workspace: ceil(n_steps/ckpt) + ckpt + 1 states per instance and the reverse workspace,
  * allocated by the first call for these n_steps and ckpt (synchronises; make it before any
  * stream capture).  Later calls with the same n_steps, ckpt, lam and p_bar pointers enqueue
@@ -352,11 +352,18 @@ int js_batch_rollout_vjp(js_batch* b, int n_steps, const double* dt_log, int ckp
 
 /* The forward of a checkpointed rollout: advance the registered states n_steps CFL steps
  * (cfl > 0; each instance's step sizes written to dt_log[step][count], device), keeping the
- * state after every ckpt-th step (ckpt <= 0: about sqrt(n_steps)).  A js_batch_rollout_vjp
+ * state after every ckpt-th step (ckpt <= 0: js_batch_rollout_spacing's choice).  A js_batch_rollout_vjp
  * that follows with the same n_steps, ckpt and dt_log, with no batched step or
  * js_batch_set_states in between, reverses from these checkpoints and skips its own forward
  * pass.  Workspace as js_batch_rollout_vjp's. */
 int js_batch_rollout_forward(js_batch* b, double cfl, int n_steps, int ckpt, double* dt_log);
+
+/* The checkpoint spacing the rollout calls use for n_steps when given ckpt <= 0 (*ckpt, host):
+ * the spacing of the rollout workspace already prepared for n_steps; otherwise 1 (every state
+ * kept: the reverse re-runs nothing) when the n_steps + 2 states of all instances fit in half of
+ * the device memory free now, else the integer nearest sqrt(n_steps).  Synchronous (queries
+ * the free memory); allocates nothing. */
+int js_batch_rollout_spacing(js_batch* b, int n_steps, int* ckpt);
 
 /* Read and clear the batch's device error flag (synchronises): JS_OK, JS_ERR_NONPHYSICAL,
  * JS_ERR_TIMEOUT. */

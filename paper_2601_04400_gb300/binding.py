@@ -97,6 +97,7 @@ SIGNATURES = {
     "js_batch_get_tuning": (_I, [_P, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
     "js_batch_rollout_vjp": (_I, [_P, _I, _P, _I, C.POINTER(_P), C.POINTER(_P)]),
     "js_batch_rollout_forward": (_I, [_P, _D, _I, _I, _P]),
+    "js_batch_rollout_spacing": (_I, [_P, _I, C.POINTER(_I)]),
     "js_batch_sync_status": (_I, [_P]),
     "js_batch_info": (_I, [_P, C.POINTER(_I), C.POINTER(_I), C.POINTER(C.c_longlong)]),
     "js_batch_instance": (_P, [_P, _I]),
@@ -558,6 +559,12 @@ class Batch:
         tensor [n_steps, count]."""
         _check(lib().js_batch_step_fixed(self.handle, int(dts.shape[0]), _ptr(dts)), "js_batch_step_fixed")
 
+    def rollout_spacing(self, n_steps):
+        """The checkpoint spacing rollout_forward / rollout_vjp use for n_steps with ckpt=0."""
+        c = C.c_int(0)
+        _check(lib().js_batch_rollout_spacing(self.handle, int(n_steps), C.byref(c)), "js_batch_rollout_spacing")
+        return c.value
+
     def rollout_forward(self, cfl, dt_log, ckpt=0):
         """Advance the registered states dt_log.shape[0] CFL steps, logging the step sizes into
         dt_log (float64 CUDA tensor [n_steps, count]) and keeping checkpoints for rollout_vjp."""
@@ -568,7 +575,7 @@ class Batch:
         """Reverse of the rollout from the registered states with the step sizes dt_log
         (float64 CUDA tensor [n_steps, count]); lam: per-instance tensors, dL/dU_N in, dL/dU_0
         out; p_bar: per-instance JS_NPARAM tensors (accumulated) or None; ckpt: checkpoint
-        spacing (0: about sqrt(n_steps))."""
+        spacing (0: rollout_spacing's choice)."""
         n = self.count
         arr = lambda ts: (C.c_void_p * n)(*[_ptr(t).value for t in ts])
         pb = arr(p_bar) if p_bar is not None else None

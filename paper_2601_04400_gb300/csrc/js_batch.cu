@@ -950,13 +950,35 @@ int rollout_prepare(js_batch* b, int n_steps, int ckpt) {
   b->ro_nck = nck;
   return JS_OK;
 }
+// checkpoint spacing of a rollout of n_steps when the caller leaves it to the library (ckpt <= 0):
+// the spacing of the workspace already prepared for n_steps; else every state (spacing 1: no
+// segment re-runs in the reverse) when the n_steps + 2 states of all instances take at most half
+// of the free device memory; else the integer nearest sqrt(n_steps)
+int default_spacing(js_batch* b, int n_steps) {
+  if (b->d_ro && b->ro_steps == n_steps) return b->ro_ckpt;
+  double bytes = 0.0;
+  for (int k = 0; k < b->count; ++k) bytes += 32.0 * (double)b->desc[k].lay.nx * b->desc[k].lay.ny;
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && (double)(n_steps + 2) * bytes <= 0.5 * (double)fr) return 1;
+  return (int)std::lround(std::sqrt((double)n_steps));
+}
+
+int spacing(js_batch* b, int n_steps, int ckpt) {
+  if (ckpt <= 0) ckpt = default_spacing(b, n_steps);
+  if (ckpt < 1) ckpt = 1;
+  return ckpt > n_steps ? n_steps : ckpt;
+}
 }  // namespace
+
+int js_batch_rollout_spacing(js_batch* b, int n_steps, int* ckpt) {
+  if (!b || !b->states_set || n_steps < 1 || !ckpt) return JS_ERR_ARG;
+  *ckpt = spacing(b, n_steps, 0);
+  return JS_OK;
+}
 
 int js_batch_rollout_forward(js_batch* b, double cfl, int n_steps, int ckpt, double* dt_log) {
   if (!b || !b->states_set || n_steps < 1 || !dt_log || !(cfl > 0.0)) return JS_ERR_ARG;
-  if (ckpt <= 0) ckpt = (int)std::lround(std::sqrt((double)n_steps));
-  if (ckpt < 1) ckpt = 1;
-  if (ckpt > n_steps) ckpt = n_steps;
+  ckpt = spacing(b, n_steps, ckpt);
   int rc = rollout_prepare(b, n_steps, ckpt);
   if (rc) return rc;
   const int n = b->count, nck = b->ro_nck;
@@ -975,9 +997,7 @@ int js_batch_rollout_vjp(js_batch* b, int n_steps, const double* dt_log, int ckp
   if (!b || !b->states_set || n_steps < 1 || !dt_log || !lam) return JS_ERR_ARG;
   for (int k = 0; k < b->count; ++k)
     if (!lam[k]) return JS_ERR_ARG;
-  if (ckpt <= 0) ckpt = (int)std::lround(std::sqrt((double)n_steps));
-  if (ckpt < 1) ckpt = 1;
-  if (ckpt > n_steps) ckpt = n_steps;
+  ckpt = spacing(b, n_steps, ckpt);
   int rc = rev_prepare(b);
   if (rc) return rc;
   if ((rc = rollout_prepare(b, n_steps, ckpt))) return rc;

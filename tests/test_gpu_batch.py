@@ -347,9 +347,10 @@ def _reference_rollout_reverse(torch, B, p, U0, dts, lam):
 
 @pytest.mark.parametrize("ckpt", [4, 0, 13])
 def test_rollout_reverse_equals_step_by_step_reverse(env, ckpt):
-    """13 steps, checkpoints every ckpt (4: an uneven last segment; 0: about sqrt(13); 13: one
-    segment): dL/dU_0 equals the per-instance step-by-step reverse to rounding, and the same
-    for every checkpoint spacing bit for bit; the registered states are left unchanged."""
+    """13 steps, checkpoints every ckpt (4: an uneven last segment; 0: the library's choice,
+    every state for a batch this small; 13: one segment): dL/dU_0 equals the per-instance
+    step-by-step reverse to rounding, and the same for every checkpoint spacing bit for bit;
+    the registered states are left unchanged."""
     torch, B = env
     probs = _mixed_cases()
     states = _states(torch, probs)
@@ -379,6 +380,22 @@ def test_rollout_reverse_equals_step_by_step_reverse(env, ckpt):
     assert b.status() == 0
     for k in range(len(probs)):
         assert torch.equal(other[k], work[k]), k
+    b.close()
+
+
+def test_rollout_default_spacing(env):
+    """With ckpt = 0 the rollout keeps every state when they fit in half the free memory (this
+    batch's 15 states do), and reuses the spacing of a workspace already prepared for the same
+    step count; the square-root spacing otherwise."""
+    torch, B = env
+    probs = _mixed_cases()
+    states = _states(torch, probs)
+    b = B.Batch(probs)
+    b.set_states([U.clone() for U in states])
+    assert b.rollout_spacing(13) == 1
+    dts = torch.zeros((13, len(probs)), dtype=torch.float64, device="cuda")
+    b.rollout_forward(0.5, dts, ckpt=4)
+    assert b.rollout_spacing(13) == 4 and b.rollout_spacing(12) == 1
     b.close()
 
 
