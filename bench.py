@@ -560,10 +560,11 @@ def run_batched(args):
         ck = batch.rollout_spacing(n_ro)
         roll = {"steps": n_ro, "checkpoint_every": ck, "ms_forward_plain": t_ro_plain,
                 "ms_forward_checkpointed": t_ro_f, "ms_reverse": t_ro_b, "ratio": t_ro_b / t_ro_plain,
-                "note": "ratio: js_batch_rollout_vjp (per segment: re-run keeping its states + one "
-                        "persistent reverse launch per step, from the checkpoints js_batch_rollout_"
-                        "forward kept; spacing 1 = every state kept, no re-runs) / the plain batched "
-                        "forward run of the same steps (one launch, device CFL)"}
+                "note": "ratio: js_batch_rollout_vjp (per segment: re-run keeping its states and stage "
+                        "states + one persistent reverse launch per step taking the stage states as given, "
+                        "from the checkpoints js_batch_rollout_forward kept; spacing 1 = every state and "
+                        "stage state kept by the forward, no re-runs) / the plain batched forward run of "
+                        "the same steps (one launch, device CFL)"}
     info = batch.info()
     if rank == 0:
         print(json.dumps({

@@ -340,9 +340,12 @@ int js_batch_step_fixed(js_batch* b, int n_steps, const double* dt);
  *   ckpt  : checkpoint spacing (<= 0: js_batch_rollout_spacing's choice): the forward keeps the
  *           state after every ckpt-th step (or those of js_batch_rollout_forward are used, see
  *           there); then, from the last segment back, each segment is re-run keeping its
- *           states and reversed step by step by the persistent reverse launch of
- *           js_batch_step_vjp (spacing 1: every state kept, no re-runs).
- * Workspace: ceil(n_steps/ckpt) + ckpt + 1 states per instance and the reverse workspace,
+ *           states and its steps' stage states U1, U2, and reversed step by step by the
+ *           persistent reverse launch of js_batch_step_vjp, which takes the stage states as
+ *           given instead of recomputing them.  Spacing 1: the forward keeps every state and
+ *           stage state, nothing is re-run.
+ * Workspace: ceil(n_steps/ckpt) + 3 ckpt + 2 states per instance (3 n_steps + 3 with spacing
+ * 1) and the reverse workspace,
  * allocated by the first call for these n_steps and ckpt (synchronises; make it before any
  * stream capture).  Later calls with the same n_steps, ckpt, lam and p_bar pointers enqueue
  * only kernels (one launch per copy, segment re-run and reverse step) and can be captured into
@@ -360,8 +363,9 @@ int js_batch_rollout_forward(js_batch* b, double cfl, int n_steps, int ckpt, dou
 
 /* The checkpoint spacing the rollout calls use for n_steps when given ckpt <= 0 (*ckpt, host):
  * the spacing of the rollout workspace already prepared for n_steps; otherwise 1 (every state
- * kept: the reverse re-runs nothing) when the n_steps + 2 states of all instances fit in half of
- * the device memory free now, else the integer nearest sqrt(n_steps).  Synchronous (queries
+ * and stage state kept: the reverse re-runs nothing) when that workspace (3 n_steps + 3 states of
+ * all instances) fits in half of the device memory free now, else the integer nearest
+ * sqrt(n_steps).  Synchronous (queries
  * the free memory); allocates nothing. */
 int js_batch_rollout_spacing(js_batch* b, int n_steps, int* ckpt);
 

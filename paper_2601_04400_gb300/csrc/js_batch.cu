@@ -54,6 +54,8 @@ struct BatchArgs {
   const double* dt_in;        // [n_steps][count] given step sizes (no CFL reduction), or nullptr
   double* const* ustate;      // [count] states advanced instead of the registered ones, or nullptr
   double* const* save;        // [n_steps][count] states after each step, or nullptr
+  double* const* save1;       // [n_steps][count] stage states U1, U2 of each step (after stages
+  double* const* save2;       //   1 and 2), or nullptr
   const int* order;           // schedule: queue position -> tile number (ntiles), or nullptr
 };
 
@@ -249,13 +251,18 @@ __global__ void __launch_bounds__(BNT) batch_kernel(BatchArgs b) {
       }
       if (!grid_sync(b)) return;
     }
-    if (b.save) {
-      // the state after this step (ghost cells included), before the next step refills them
+    if (b.save || b.save1) {
+      // the state after this step (ghost cells included), before the next step refills them,
+      // and the stage states A, B of this step (their ghost cells were refilled from fluid
+      // cells, which a reverse pass that fills them again reproduces)
       for (int it = blockIdx.x; it < ntiles; it += gridDim.x) {
         const int q = b.order ? b.order[it] : it;
-    const int k = find_inst(b.tile0, b.count, q);
+        const int k = find_inst(b.tile0, b.count, q);
         const InstDesc& d = b.inst[k];
-        double* S = b.save[(long long)step * b.count + k];
+        const long long row = (long long)step * b.count + k;
+        double* S = b.save ? b.save[row] : nullptr;
+        double* S1 = b.save1 ? b.save1[row] : nullptr;
+        double* S2 = b.save1 ? b.save2[row] : nullptr;
         const int t = q - b.tile0[k];
         const int i0 = (t % d.ntx) * BTX, j0 = (t / d.ntx) * BTY;
         const long long n = (long long)d.lay.nx * d.lay.ny;
@@ -264,7 +271,13 @@ __global__ void __launch_bounds__(BNT) batch_kernel(BatchArgs b) {
           if (i >= d.lay.nx || j >= d.lay.ny) continue;
           const long long o = (long long)j * d.lay.nx + i, p = d.lay.idx(i, j);
 #pragma unroll
-          for (int c = 0; c < 4; ++c) S[c * n + o] = d.N[c * d.lay.plane + p];
+          for (int c = 0; c < 4; ++c) {
+            if (S) S[c * n + o] = d.N[c * d.lay.plane + p];
+            if (S1) {
+              S1[c * n + o] = d.A[c * d.lay.plane + p];
+              S2[c * n + o] = d.B[c * d.lay.plane + p];
+            }
+          }
         }
       }
       if (!grid_sync(b)) return;
@@ -314,6 +327,10 @@ struct RevCall {
   double* const* lam0;        // [count] lambda_n (may alias lam1)
   double* const* pbar;        // [count] parameter gradients (entries may be null) or null
   const double* dt;           // [count] step sizes
+  // [count] the step's stage states U1, U2 (user layout, e.g. kept by a rollout's forward), or
+  // null: the reverse recomputes them (storing their WENO5 internals for pass 1 of stages 1, 0)
+  const double* const* U1;
+  const double* const* U2;
 };
 
 struct BatchRevArgs {
@@ -346,6 +363,10 @@ __device__ __forceinline__ void rev_items(const BatchRevArgs& b, int kind, F f) 
   }
 }
 
+// pass 1 of reverse stage s reads the WENO5 internals stored by the forward recompute (stages
+// 1, 0 when the reverse recomputes the stage states) or recomputes them
+__device__ __forceinline__ bool rev_saved(const RevCall& call, int s) { return s < 2 && call.U1 == nullptr; }
+
 __device__ __forceinline__ AdjArgs rev_adj(const InstRev& r, const InstDesc& d, int s, const RevCall& call, int k,
                                            double* dst, bool with_pbar) {
   AdjArgs a = r.a;
@@ -353,7 +374,7 @@ __device__ __forceinline__ AdjArgs rev_adj(const InstRev& r, const InstDesc& d, 
   a.Ub = dst;
   a.pbar = with_pbar && call.pbar ? call.pbar[k] : nullptr;
   a.pp = a.pbar ? r.ppart : nullptr;
-  if (s < 2) {
+  if (rev_saved(call, s)) {
     a.wsave = r.wfwd + (long long)56 * s * r.a.splane;
     a.weno_saved = 1;
   } else {
@@ -364,9 +385,9 @@ __device__ __forceinline__ AdjArgs rev_adj(const InstRev& r, const InstDesc& d, 
 }
 
 // the parameter-gradient slot ranges of reverse stage s of one instance, summed into its pbar
-__device__ __forceinline__ void rev_reduce(const InstRev& r, int s, double* pbar) {
+__device__ __forceinline__ void rev_reduce(const InstRev& r, bool saved, double* pbar) {
   const long long off[4] = {0, r.off_prim, r.off_g, r.off_s};
-  const long long cnt[4] = {s < 2 ? r.w1_sv : r.w1_re, r.w_prim, r.w_g, r.w_s};
+  const long long cnt[4] = {saved ? r.w1_sv : r.w1_re, r.w_prim, r.w_g, r.w_s};
   adj_pbar_reduce_block(r.ppart, off, cnt, 4, pbar);
 }
 
@@ -384,6 +405,10 @@ __global__ void __launch_bounds__(BNT) batch_vjp_kernel(BatchRevArgs b) {
     const long long p = c * d.lay.plane + d.lay.idx((int)(o % d.lay.nx), (int)(o / d.lay.nx));
     d.N[p] = call.Un[k][t];
     b.rev[k].P0[p] = call.lam1[k][t];
+    if (call.U1) {
+      d.A[p] = call.U1[k][t];
+      d.B[p] = call.U2[k][t];
+    }
   });
   rev_items(b, RK_PLANE, [&](int k, long long t) {
     if (k < 0 || t >= b.inst[k].lay.plane) return;
@@ -411,6 +436,7 @@ __global__ void __launch_bounds__(BNT) batch_vjp_kernel(BatchRevArgs b) {
     });
     if (!grid_sync_on(b.bar, b.err, 0, b.budget)) return;
     if (s == 2) break;
+    if (call.U1) continue;  // the stage states were given: only their ghosts and halos are filled
     for (int it = blockIdx.x; it < b.tile0[b.count]; it += gridDim.x) {
       const int k = find_inst(b.tile0, b.count, it);
       const InstDesc& d = b.inst[k];
@@ -466,30 +492,31 @@ __global__ void __launch_bounds__(BNT) batch_vjp_kernel(BatchRevArgs b) {
     });
     if (s < 2 && call.pbar)
       for (int k = blockIdx.x; k < b.count; k += gridDim.x)
-        if (call.pbar[k]) rev_reduce(b.rev[k], s + 1, call.pbar[k]);
+        if (call.pbar[k]) rev_reduce(b.rev[k], rev_saved(call, s + 1), call.pbar[k]);
     if (!grid_sync_on(b.bar, b.err, 0, b.budget)) return;
     // pass 1 (x lines, then y lines from the 32-aligned offset xpad)
-    rev_items(b, s < 2 ? RK_P1SV : RK_P1RE, [&](int k, long long item) {
+    const bool sv = rev_saved(call, s);
+    rev_items(b, sv ? RK_P1SV : RK_P1RE, [&](int k, long long item) {
       if (k < 0) return;  // whole warps past the end: nothing to do, no partials
       const InstDesc& d = b.inst[k];
       const InstRev& r = b.rev[k];
       const AdjArgs a = rev_adj(r, d, s, call, k, even ? r.P1 : r.P0, true);
-      const long long xpad = s < 2 ? r.xpad_sv : r.xpad_re;
-      const int seg = s < 2 ? r.seg1_sv : r.seg1_re;
+      const long long xpad = sv ? r.xpad_sv : r.xpad_re;
+      const int seg = sv ? r.seg1_sv : r.seg1_re;
       if (item < xpad) {
         if (d.visc) {
-          if (s < 2) pass1_body<0, true, true, true>(a, seg, item, 0);
+          if (sv) pass1_body<0, true, true, true>(a, seg, item, 0);
           else pass1_body<0, true, true, false>(a, seg, item, 0);
         } else {
-          if (s < 2) pass1_body<0, false, false, true>(a, seg, item, 0);
+          if (sv) pass1_body<0, false, false, true>(a, seg, item, 0);
           else pass1_body<0, false, false, false>(a, seg, item, 0);
         }
       } else {
         if (d.visc) {
-          if (s < 2) pass1_body<1, true, true, true>(a, seg, item - xpad, xpad >> 5);
+          if (sv) pass1_body<1, true, true, true>(a, seg, item - xpad, xpad >> 5);
           else pass1_body<1, true, true, false>(a, seg, item - xpad, xpad >> 5);
         } else {
-          if (s < 2) pass1_body<1, false, false, true>(a, seg, item - xpad, xpad >> 5);
+          if (sv) pass1_body<1, false, false, true>(a, seg, item - xpad, xpad >> 5);
           else pass1_body<1, false, false, false>(a, seg, item - xpad, xpad >> 5);
         }
       }
@@ -568,7 +595,7 @@ __global__ void __launch_bounds__(BNT) batch_vjp_kernel(BatchRevArgs b) {
   });
   if (call.pbar)
     for (int k = blockIdx.x; k < b.count; k += gridDim.x)
-      if (call.pbar[k]) rev_reduce(b.rev[k], 0, call.pbar[k]);
+      if (call.pbar[k]) rev_reduce(b.rev[k], rev_saved(call, 0), call.pbar[k]);
 }
 
 // one launch copying every instance's state: dst[k][i] = src[k][i], i < pre[k+1] - pre[k]
@@ -823,12 +850,15 @@ int js_batch_set_states(js_batch* b, double* const* U) {
 
 static int batch_launch(js_batch* b, double cfl, int n_steps, double* t_dev, double* dt_log, int extra,
                         double budget_s, const double* dt_in = nullptr, double* const* ustate = nullptr,
-                        double* const* save = nullptr) {
+                        double* const* save = nullptr, double* const* save1 = nullptr,
+                        double* const* save2 = nullptr) {
   if (!ustate) b->ro_fwd_log = nullptr;  // the registered states move: kept checkpoints are stale
   js::BatchArgs a;
   a.dt_in = dt_in;
   a.ustate = ustate;
   a.save = save;
+  a.save1 = save1;
+  a.save2 = save2;
   a.order = b->schedule ? b->d_order : nullptr;
   a.inst = b->d_desc;
   a.count = b->count;
@@ -884,6 +914,7 @@ int js_batch_step_vjp(js_batch* b, double* const* U_n, const double* dt, double*
   call.lam0 = reinterpret_cast<double* const*>(b->d_tab + 2 * b->count);
   call.pbar = p_bar ? reinterpret_cast<double* const*>(b->d_tab + 3 * b->count) : nullptr;
   call.dt = b->d_dt;
+  call.U1 = call.U2 = nullptr;  // the reverse recomputes the stage states
   return rev_launch(b, call);
 }
 
@@ -901,11 +932,34 @@ int batch_copy(js_batch* b, void* const* src, void* const* dst) {
   return cudaGetLastError() == cudaSuccess ? JS_OK : JS_ERR_CUDA;
 }
 
-// the rollout workspace for (n_steps, ckpt): checkpoint, segment and working states per instance
-// and the device pointer tables (allocates and synchronises: before any stream capture)
+// Rollout workspace for (n_steps, ckpt), per instance: nck checkpoints (the state after every
+// ckpt-th step), the segment states U (ckpt + 1: a re-run saves the state after each of its
+// steps), the stage states U1, U2 of m steps (m = ckpt; with ckpt = 1 every step's, which the
+// forward keeps) and one working state; and the device pointer tables, one block of `count`
+// pointers each (allocates and synchronises: before any stream capture)
+struct RoLayout {
+  int nck, ckpt, m;
+  size_t cp(int c) const { return 1 + (size_t)c; }
+  size_t segU(int j) const { return 1 + (size_t)nck + j; }
+  size_t segU1(int j) const { return 1 + (size_t)nck + ckpt + 1 + j; }
+  size_t segU2(int j) const { return 1 + (size_t)nck + ckpt + 1 + m + j; }
+  size_t work() const { return 1 + (size_t)nck + ckpt + 1 + 2 * (size_t)m; }
+  size_t lam() const { return work() + 1; }
+  size_t pbar() const { return work() + 2; }
+  size_t blocks() const { return work() + 3; }
+  size_t states() const { return (size_t)nck + ckpt + 1 + 2 * (size_t)m + 1; }
+};
+RoLayout ro_layout(int n_steps, int ckpt) {
+  RoLayout L;
+  L.nck = (n_steps + ckpt - 1) / ckpt;
+  L.ckpt = ckpt;
+  L.m = (ckpt == 1) ? n_steps : ckpt;
+  return L;
+}
+
 int rollout_prepare(js_batch* b, int n_steps, int ckpt) {
   const int n = b->count;
-  const int nck = (n_steps + ckpt - 1) / ckpt;
+  const RoLayout L = ro_layout(n_steps, ckpt);
   if (b->ro_steps == n_steps && b->ro_ckpt == ckpt && b->d_ro) {
     // the registered states' pointers (table block 0) may have changed since
     bool same = true;
@@ -927,17 +981,19 @@ int rollout_prepare(js_batch* b, int n_steps, int ckpt) {
   b->ro_steps = b->ro_ckpt = b->ro_nck = 0;
   b->ro_lam.clear();
   b->ro_pbar.clear();
-  const int ntab = nck + ckpt + 4;
-  std::vector<void*> tab((size_t)ntab * n, nullptr);
+  std::vector<void*> tab(L.blocks() * n, nullptr);
   std::vector<long long> spre(n + 1, 0);
   for (int k = 0; k < n; ++k) {
     const size_t st = 4 * (size_t)b->desc[k].lay.nx * b->desc[k].lay.ny;
     spre[k + 1] = spre[k] + (long long)st;
-    if (cudaMalloc(&b->ro_buf[k], sizeof(double) * st * (size_t)(nck + ckpt + 1)) != cudaSuccess) return JS_ERR_NOMEM;
+    if (cudaMalloc(&b->ro_buf[k], sizeof(double) * st * L.states()) != cudaSuccess) return JS_ERR_NOMEM;
+    double* q = b->ro_buf[k];
     tab[k] = b->desc[k].U;
-    for (int c = 0; c < nck; ++c) tab[(size_t)(1 + c) * n + k] = b->ro_buf[k] + st * c;
-    for (int j = 0; j < ckpt; ++j) tab[(size_t)(1 + nck + j) * n + k] = b->ro_buf[k] + st * (nck + j);
-    tab[(size_t)(1 + nck + ckpt) * n + k] = b->ro_buf[k] + st * (nck + ckpt);
+    for (int c = 0; c < L.nck; ++c, q += st) tab[L.cp(c) * n + k] = q;
+    for (int j = 0; j <= ckpt; ++j, q += st) tab[L.segU(j) * n + k] = q;
+    for (int j = 0; j < L.m; ++j, q += st) tab[L.segU1(j) * n + k] = q;
+    for (int j = 0; j < L.m; ++j, q += st) tab[L.segU2(j) * n + k] = q;
+    tab[L.work() * n + k] = q;
   }
   if (!b->d_spre && cudaMalloc(&b->d_spre, sizeof(long long) * (n + 1)) != cudaSuccess) return JS_ERR_NOMEM;
   if (cudaMalloc(&b->d_ro, sizeof(void*) * tab.size()) != cudaSuccess) return JS_ERR_NOMEM;
@@ -947,19 +1003,21 @@ int rollout_prepare(js_batch* b, int n_steps, int ckpt) {
   b->ro_U.assign(tab.begin(), tab.begin() + n);
   b->ro_steps = n_steps;
   b->ro_ckpt = ckpt;
-  b->ro_nck = nck;
+  b->ro_nck = L.nck;
   return JS_OK;
 }
+
 // checkpoint spacing of a rollout of n_steps when the caller leaves it to the library (ckpt <= 0):
-// the spacing of the workspace already prepared for n_steps; else every state (spacing 1: no
-// segment re-runs in the reverse) when the n_steps + 2 states of all instances take at most half
-// of the free device memory; else the integer nearest sqrt(n_steps)
+// the spacing of the workspace already prepared for n_steps; else 1 (every state and stage state
+// kept: the reverse re-runs nothing) when that workspace takes at most half of the free device
+// memory; else the integer nearest sqrt(n_steps)
 int default_spacing(js_batch* b, int n_steps) {
   if (b->d_ro && b->ro_steps == n_steps) return b->ro_ckpt;
   double bytes = 0.0;
   for (int k = 0; k < b->count; ++k) bytes += 32.0 * (double)b->desc[k].lay.nx * b->desc[k].lay.ny;
   size_t fr = 0, tot = 0;
-  if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && (double)(n_steps + 2) * bytes <= 0.5 * (double)fr) return 1;
+  if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && (double)ro_layout(n_steps, 1).states() * bytes <= 0.5 * (double)fr)
+    return 1;
   return (int)std::lround(std::sqrt((double)n_steps));
 }
 
@@ -981,12 +1039,17 @@ int js_batch_rollout_forward(js_batch* b, double cfl, int n_steps, int ckpt, dou
   ckpt = spacing(b, n_steps, ckpt);
   int rc = rollout_prepare(b, n_steps, ckpt);
   if (rc) return rc;
-  const int n = b->count, nck = b->ro_nck;
+  const int n = b->count;
+  const RoLayout L = ro_layout(n_steps, ckpt);
   void** T = b->d_ro;
-  for (int c = 0; c < nck; ++c) {
+  auto tab = [&](size_t blk) { return reinterpret_cast<double* const*>(T + blk * n); };
+  for (int c = 0; c < L.nck; ++c) {
     const int len = std::min(ckpt, n_steps - c * ckpt);
-    if ((rc = batch_copy(b, T, T + (size_t)(1 + c) * n))) return rc;
-    if ((rc = batch_launch(b, cfl, len, nullptr, dt_log + (size_t)c * ckpt * n, 0, 2.0))) return rc;
+    if ((rc = batch_copy(b, T, T + L.cp(c) * n))) return rc;
+    // with every state kept, the step's stage states too
+    if ((rc = batch_launch(b, cfl, len, nullptr, dt_log + (size_t)c * ckpt * n, 0, 2.0, nullptr, nullptr, nullptr,
+                           ckpt == 1 ? tab(L.segU1(c)) : nullptr, ckpt == 1 ? tab(L.segU2(c)) : nullptr)))
+      return rc;
   }
   b->ro_fwd_log = dt_log;  // after the launches (which clear it)
   return JS_OK;
@@ -1001,53 +1064,67 @@ int js_batch_rollout_vjp(js_batch* b, int n_steps, const double* dt_log, int ckp
   int rc = rev_prepare(b);
   if (rc) return rc;
   if ((rc = rollout_prepare(b, n_steps, ckpt))) return rc;
-  const int n = b->count, nck = b->ro_nck;
+  const int n = b->count;
+  const RoLayout L = ro_layout(n_steps, ckpt);
   void** T = b->d_ro;
-  void** U = T;
-  auto cp = [&](int c) { return T + (size_t)(1 + c) * n; };
-  auto seg = [&](int j) { return T + (size_t)(1 + nck + j) * n; };
-  void** work = T + (size_t)(1 + nck + ckpt) * n;
-  void** lamt = T + (size_t)(2 + nck + ckpt) * n;
-  void** pbt = T + (size_t)(3 + nck + ckpt) * n;
+  auto blk = [&](size_t i) { return T + i * n; };
+  auto tab = [&](size_t i) { return reinterpret_cast<double* const*>(T + i * n); };
+  auto ctab = [&](size_t i) { return reinterpret_cast<const double* const*>(T + i * n); };
+  void** work = blk(L.work());
   // the lam / p_bar pointers of this call (uploaded when they differ from the previous call's)
   std::vector<void*> hl(lam, lam + n), hp(n, nullptr);
   if (p_bar)
     for (int k = 0; k < n; ++k) hp[k] = p_bar[k];
   if (hl != b->ro_lam || hp != b->ro_pbar) {
-    if (cudaMemcpyAsync(lamt, hl.data(), sizeof(void*) * n, cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
-        cudaMemcpyAsync(pbt, hp.data(), sizeof(void*) * n, cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
+    if (cudaMemcpyAsync(blk(L.lam()), hl.data(), sizeof(void*) * n, cudaMemcpyHostToDevice, b->stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(blk(L.pbar()), hp.data(), sizeof(void*) * n, cudaMemcpyHostToDevice, b->stream) !=
+            cudaSuccess ||
         cudaStreamSynchronize(b->stream) != cudaSuccess)
       return JS_ERR_CUDA;
     b->ro_lam = hl;
     b->ro_pbar = hp;
   }
   // forward: checkpoint c holds the state after c * ckpt steps (kept by js_batch_rollout_forward
-  // when it ran these steps and nothing moved the registered states since)
+  // when it ran these steps and nothing moved the registered states since); with ckpt = 1 every
+  // step's stage states as well
   if (b->ro_fwd_log != dt_log) {
-    if ((rc = batch_copy(b, U, cp(0)))) return rc;
-    for (int c = 1; c < nck; ++c) {
-      if ((rc = batch_copy(b, cp(c - 1), cp(c)))) return rc;
-      if ((rc = batch_launch(b, 0.5, ckpt, nullptr, nullptr, 0, 2.0, dt_log + (size_t)(c - 1) * ckpt * n,
-                             reinterpret_cast<double* const*>(cp(c)))))
-        return rc;
+    if (ckpt == 1) {
+      if ((rc = batch_copy(b, T, work))) return rc;
+      for (int c = 0; c < n_steps; ++c) {
+        if ((rc = batch_copy(b, work, blk(L.cp(c))))) return rc;
+        if ((rc = batch_launch(b, 0.5, 1, nullptr, nullptr, 0, 2.0, dt_log + (size_t)c * n, tab(L.work()), nullptr,
+                               tab(L.segU1(c)), tab(L.segU2(c)))))
+          return rc;
+      }
+    } else {
+      if ((rc = batch_copy(b, T, blk(L.cp(0))))) return rc;
+      for (int c = 1; c < L.nck; ++c) {
+        if ((rc = batch_copy(b, blk(L.cp(c - 1)), blk(L.cp(c))))) return rc;
+        if ((rc = batch_launch(b, 0.5, ckpt, nullptr, nullptr, 0, 2.0, dt_log + (size_t)(c - 1) * ckpt * n,
+                               tab(L.cp(c)))))
+          return rc;
+      }
     }
   }
-  // reverse, segment by segment: re-run the segment keeping its states, then reverse its steps
-  for (int c = nck - 1; c >= 0; --c) {
+  // reverse, segment by segment: re-run the segment keeping its states and stage states (not
+  // needed with ckpt = 1), then reverse its steps from the last one
+  for (int c = L.nck - 1; c >= 0; --c) {
     const int s0 = c * ckpt, len = std::min(ckpt, n_steps - s0);
-    if ((rc = batch_copy(b, cp(c), seg(0)))) return rc;
-    if (len > 1) {
-      if ((rc = batch_copy(b, cp(c), work))) return rc;
-      if ((rc = batch_launch(b, 0.5, len - 1, nullptr, nullptr, 0, 2.0, dt_log + (size_t)s0 * n,
-                             reinterpret_cast<double* const*>(work), reinterpret_cast<double* const*>(seg(1)))))
+    if (ckpt > 1) {
+      if ((rc = batch_copy(b, blk(L.cp(c)), work))) return rc;
+      if ((rc = batch_launch(b, 0.5, len, nullptr, nullptr, 0, 2.0, dt_log + (size_t)s0 * n, tab(L.work()),
+                             tab(L.segU(1)), tab(L.segU1(0)), tab(L.segU2(0)))))
         return rc;
     }
     for (int j = len - 1; j >= 0; --j) {
       js::RevCall call;
-      call.Un = reinterpret_cast<const double* const*>(seg(j));
-      call.lam1 = reinterpret_cast<const double* const*>(lamt);
-      call.lam0 = reinterpret_cast<double* const*>(lamt);
-      call.pbar = p_bar ? reinterpret_cast<double* const*>(pbt) : nullptr;
+      call.Un = ctab(j == 0 ? L.cp(c) : L.segU(j));
+      call.U1 = ctab(ckpt == 1 ? L.segU1(c) : L.segU1(j));
+      call.U2 = ctab(ckpt == 1 ? L.segU2(c) : L.segU2(j));
+      call.lam1 = ctab(L.lam());
+      call.lam0 = tab(L.lam());
+      call.pbar = p_bar ? tab(L.pbar()) : nullptr;
       call.dt = dt_log + (size_t)(s0 + j) * n;
       if ((rc = rev_launch(b, call))) return rc;
     }
