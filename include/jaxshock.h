@@ -240,8 +240,8 @@ int js_rows_unpack(js_ctx* ctx, double* U, int row0, int nrows, const double* bu
  *   norm   host array mean[4], sd[4] (> 0), scale[4] (copied)
  *   precision  JS_NN_F64 (FP64 network arithmetic), JS_NN_F32 (FP32 on the CUDA cores) or
  *          JS_NN_BF16 (the three layers of the forward pass on the tensor cores with BF16
- *          operands and FP32 accumulation; in the reverse the data gradients of layers 3 and 2
- *          likewise, the first layer's data gradient and all weight gradients FP32); the solver
+ *          operands and FP32 accumulation; in the reverse the data and weight gradients of
+ *          layers 3 and 2 likewise, the first layer's FP32); the solver
  *          stays FP64 (with FP32 and BF16 networks the face images and the network's flux
  *          divergence are formed in FP32 and added to the FP64 state).
  *          In BF16 precision the stages that no reverse pass reads evaluate the whole network
@@ -266,8 +266,8 @@ int js_nn_eval(js_ctx* ctx, const double* X, int H, int W, double* Y);
 /* Reverse of js_nn_eval on the same image (the network's forward is recomputed):
  *   GX     = (dY/dX)^T GY          (overwritten), device [4][H][W] FP64
  *   w_bar += (dY/dw)^T GY          (the w_bar of js_set_neural, when one was given)
- * In BF16 precision the data gradients of layers 3 and 2 run on the tensor cores with BF16
- * output gradients; weight gradients and the first layer are FP32.  GX may alias X or GY.
+ * In BF16 precision the data and weight gradients of layers 3 and 2 run on the tensor cores
+ * (BF16 operands, FP32 accumulation); the first layer's are FP32.  GX may alias X or GY.
  * Errors as js_nn_eval.  Asynchronous. */
 int js_nn_eval_vjp(js_ctx* ctx, const double* X, int H, int W, const double* GY, double* GX);
 

@@ -1040,6 +1040,243 @@ __global__ void __launch_bounds__(128) nn_net_tc_kernel(NnArgs n, int band) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem) : "memory");
 }
 
+// ---------------------------------------------------------------------------------------
+// BF16 weight gradient of one layer on the tensor cores (the BF16 reverse):
+//   dW[co][ci][ky][kx] = sum over pixels q of G[co](q) A[ci](q + (ky-1, kx-1)),  db[co] = sum G[co]
+// with G (the layer's output gradient) and A (its input) rounded to BF16, FP32 accumulation.
+// Per chunk of WC = 64 pixels of image row y (x0 .. x0+63), one implicit GEMM with K = the chunk's
+// pixels:  D[(ky, co)][(kx, ci)] += sum_x G[co](y+1-ky, x) A[ci](y, x+kx-1)  — which is dW once
+// summed over every row y, the shift of a tap split between the two operands: the A operand holds
+// the three G rows y+1, y, y-1 (channels padded to 8), the B operand three x-shifted copies of A's
+// row y and a row of ones (D's ones column on the unshifted G rows is db).  M = 128 (rows beyond
+// 3 x COUTP ignored), N = NB = 3 CIN + 1 rounded up to 16, one tcgen05.mma per 16 pixels into a
+// TMEM accumulator that holds the block's sum over all its chunks.
+// A block walks work items of a 64-pixel column strip and a band of rows; the FP32 rows arrive by
+// 4-byte cp.async into rings (G rows y-1 .. y+1 read, y+2 in flight; A row y read, y+1 in flight;
+// channel strides padded against shared-memory bank conflicts),
+// and each chunk's BF16 operands are built from them into one of two buffers, the next chunk's
+// while the MMAs read the current one.  Each block writes its sums to partial[block] (all the
+// layer's parameters; zeros when it had no chunk), reduced in a fixed order afterwards.
+// ---------------------------------------------------------------------------------------
+constexpr int WC = 64;            // pixels per chunk (the GEMM's K per chunk)
+constexpr int WKG = WC / 8;       // 8-pixel core-matrix columns per chunk
+constexpr int WBAND = 16;         // rows per work item
+constexpr int WNT = 256;          // threads per block
+constexpr int WGS = WC + 4;       // floats per channel of a staged G row (padded: no bank conflicts)
+constexpr int WAS = WC + 3;       // floats per channel of a staged A row (1-pixel halo, odd stride)
+template <int CIN, int COUT>
+struct WgTc {
+  static constexpr int COUTP = (COUT + 7) / 8 * 8;          // G channels per row, padded
+  static constexpr int NB = (3 * CIN + 1 + 15) / 16 * 16;   // MMA N
+  static constexpr int ABYTES = 128 * WC * 2;               // A operand: 128 rows x WC pixels, BF16
+  static constexpr int BBYTES = NB * WC * 2;
+  static constexpr int BUF = ABYTES + BBYTES;
+  static constexpr int GROW = COUT * WGS;                   // floats of a staged G row
+  static constexpr int AROW = CIN * WAS;                    // floats of a staged A row
+  static constexpr int OFF_G = 2 * BUF;                     // G ring (4 rows), then A ring (2 rows)
+  static constexpr int OFF_A = OFF_G + 4 * GROW * 4;
+  static constexpr int SMEM = OFF_A + 2 * AROW * 4;
+  static_assert(3 * COUTP <= 128 && NB <= 256, "one MMA tile");
+};
+
+// 8 floats -> one 16-byte core-matrix row of 8 BF16 values
+__device__ __forceinline__ uint4 bf16x8(const float v[8]) { return pack_bf16x8(v); }
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(WNT) nn_wgrad_tc_kernel(NnArgs n, const float* __restrict__ gout,
+                                                          const float* __restrict__ ain, int woff) {
+  using P = WgTc<CIN, COUT>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) unsigned long long bar[2];
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(smem_u32(&tmem_base))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    mbar_init(&bar[0]);
+    mbar_init(&bar[1]);
+  }
+  // both operand buffers zeroed, then the constant rows of B: the ones row (n = 3 CIN); the
+  // padding rows and the A rows beyond 3 COUTP stay zero
+  for (int k = tid; k < 2 * P::BUF / 16; k += WNT) reinterpret_cast<uint4*>(smem_raw)[k] = make_uint4(0, 0, 0, 0);
+  __syncthreads();
+  for (int u = tid; u < 2 * WKG; u += WNT) {
+    const int buf = u / WKG, kg = u % WKG, nrow = 3 * CIN;
+    const float one[8] = {1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f};
+    *reinterpret_cast<uint4*>(smem_raw + buf * P::BUF + P::ABYTES + ((nrow >> 3) * WKG + kg) * 128 + (nrow & 7) * 16) =
+        bf16x8(one);
+  }
+  float* sG = reinterpret_cast<float*>(smem_raw + P::OFF_G);
+  float* sAr = reinterpret_cast<float*>(smem_raw + P::OFF_A);
+  // work items: image d, 64-pixel column strip, band of WBAND rows
+  int nsx[2], nit[2];
+  for (int d = 0; d < 2; ++d) {
+    nsx[d] = (d < n.nimg) ? (n.W[d] + WC - 1) / WC : 0;
+    nit[d] = (d < n.nimg) ? nsx[d] * ((n.H[d] + WBAND - 1) / WBAND) : 0;
+  }
+  const int items = nit[0] + nit[1];
+  // FP32 rows of the item's strip into the rings (zeros outside the image), 4-byte copies: G row
+  // rg as [co][64] (element: channel, pixel x0 + tid % 64), A row ra as [ci][66] (pixels x0 - 1 ..
+  // x0 + 64)
+  auto load_g = [&](int d, int x0, int rg) {
+    const int H = n.H[d], Wd = n.W[d];
+    const long long pix = (long long)H * Wd;
+    const float* G = gout + (d == 0 ? 0LL : (long long)COUT * n.pix0);
+    float* dst = sG + ((rg + 8) & 3) * P::GROW;
+    const int x = x0 + (tid & 63);
+    const bool in = rg >= 0 && rg < H && x < Wd;
+    for (int co = tid >> 6; co < COUT; co += WNT / 64)
+      cp_async4(dst + co * WGS + (tid & 63), in ? G + co * pix + (long long)rg * Wd + x : G, in);
+  };
+  auto load_a = [&](int d, int x0, int ra) {
+    const int H = n.H[d], Wd = n.W[d];
+    const long long pix = (long long)H * Wd;
+    const float* A = ain + (d == 0 ? 0LL : (long long)CIN * n.pix0);
+    float* dst = sAr + (ra & 1) * P::AROW;
+    for (int k = tid; k < CIN * (WC + 2); k += WNT) {
+      const int ci = k / (WC + 2), xx = k % (WC + 2), x = x0 - 1 + xx;
+      const bool in = ra < H && x >= 0 && x < Wd;
+      cp_async4(dst + ci * WAS + xx, in ? A + ci * pix + (long long)ra * Wd + x : A, in);
+    }
+  };
+  // the BF16 operands of chunk (row y) into buffer b; unit u = (8-row group, pixel column, row
+  // in group) at shared-memory offset 16 u (consecutive threads: consecutive 16-byte rows)
+  auto build = [&](int y, int b) {
+    unsigned char* sA = smem_raw + b * P::BUF;
+    unsigned char* sB = sA + P::ABYTES;
+    constexpr int AU = 3 * P::COUTP * WKG;
+    for (int u = tid; u < AU; u += WNT) {
+      const int kg = (u >> 3) % WKG, m = ((u >> 3) / WKG) * 8 + (u & 7);
+      const int ky = m / P::COUTP, co = m % P::COUTP;
+      if (co >= COUT) continue;  // padding rows stay zero
+      const float4* src = reinterpret_cast<const float4*>(sG + ((y + 1 - ky + 8) & 3) * P::GROW + co * WGS + kg * 8);
+      const float4 p = src[0], q = src[1];
+      const float v[8] = {p.x, p.y, p.z, p.w, q.x, q.y, q.z, q.w};
+      *reinterpret_cast<uint4*>(sA + 16 * u) = bf16x8(v);
+    }
+    constexpr int BU = (3 * CIN + 7) / 8 * 8 * WKG;
+    for (int u = tid; u < BU; u += WNT) {
+      const int kg = (u >> 3) % WKG, nr = ((u >> 3) / WKG) * 8 + (u & 7);
+      if (nr >= 3 * CIN) continue;  // the ones row and padding are constant
+      const int kx = nr / CIN, ci = nr % CIN;
+      const float* src = sAr + (y & 1) * P::AROW + ci * WAS + kg * 8 + kx;
+      float v[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v[e] = src[e];
+      *reinterpret_cast<uint4*>(sB + 16 * u) = bf16x8(v);
+    }
+  };
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  constexpr uint32_t idesc = umma_idesc_bf16(128, P::NB);
+  constexpr long long kBudget = 2000000000LL;  // about one second of SM clock
+  unsigned phase0 = 0u, phase1 = 0u;
+  bool pend0 = false, pend1 = false;  // MMAs committed to bar[b] and not yet waited for
+  bool ok = true;
+  int nmma = 0, chunk = 0;
+  // a bounded wait, uniform across the block, for the MMAs committed to bar[b]
+  auto wait_buf = [&](int b) {
+    const unsigned ph = b ? phase1 : phase0;
+    ok = __syncthreads_and(mbar_wait(&bar[b], ph, kBudget) ? 1 : 0) != 0;
+    if (!ok) {
+      if (tid == 0) atomicOr(n.err, ERR_TIMEOUT_BIT);
+      mbar_wait(&bar[b], ph, kBudget);  // drain before the accumulator is released
+    }
+    if (b) {
+      phase1 ^= 1u;
+      pend1 = false;
+    } else {
+      phase0 ^= 1u;
+      pend0 = false;
+    }
+  };
+  for (int it = blockIdx.x; it < items && ok; it += gridDim.x) {
+    const int d = (it < nit[0]) ? 0 : 1;
+    const int il = (d == 0) ? it : it - nit[0];
+    const int H = n.H[d];
+    const int x0 = (il % nsx[d]) * WC, h0 = (il / nsx[d]) * WBAND;
+    const int h1 = (h0 + WBAND < H) ? h0 + WBAND : H;
+    // prologue: G rows h0 - 1 .. h0 + 1 and A row h0
+    load_g(d, x0, h0 - 1);
+    load_g(d, x0, h0);
+    load_g(d, x0, h0 + 1);
+    load_a(d, x0, h0);
+    cp_async_commit();
+    for (int y = h0; y < h1; ++y, ++chunk) {
+      const int b = chunk & 1;
+      // the next row's copies: G row y + 2 into the slot of row y - 2, A row y + 1 into the slot of
+      // row y - 1, whose last readers (the chunk of row y - 1) passed the barrier before its MMAs
+      load_g(d, x0, y + 2);
+      load_a(d, x0, y + 1);
+      cp_async_commit();
+      if (b ? pend1 : pend0) {
+        wait_buf(b);  // the MMAs of two chunks ago read this buffer
+        if (!ok) break;
+      }
+      cp_async_wait<1>();  // this thread's copies of G rows up to y + 1 and A row y have landed
+      __syncthreads();
+      build(y, b);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (tid == 0) {
+        const uint32_t a0 = smem_u32(smem_raw + b * P::BUF), b0 = a0 + P::ABYTES;
+        for (int j = 0; j < WKG / 2; ++j)  // 16 pixels (two core-matrix columns) per MMA
+          umma_bf16(tmem, umma_smem_desc(a0 + 2 * j * 128, 128, WKG * 128),
+                    umma_smem_desc(b0 + 2 * j * 128, 128, WKG * 128), idesc, (nmma + j) > 0 ? 1 : 0);
+        umma_commit(&bar[b]);
+      }
+      nmma += WKG / 2;  // every thread counts the MMAs issued
+      if (b) pend1 = true; else pend0 = true;
+    }
+    // the item's last copies (rows past the band) land before the rings are refilled
+    cp_async_wait<0>();
+    __syncthreads();
+  }
+  cp_async_wait<0>();
+  if (ok && pend0) wait_buf(0);
+  if (ok && pend1) wait_buf(1);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  // epilogue (warps 0-3, one accumulator lane each): lane m = row (ky, co); columns (kx, ci) and
+  // the ones column
+  const int m = tid;
+  const int ky = m / P::COUTP, co = m % P::COUTP;
+  const bool real = warp < 4 && ky < 3 && co < COUT;
+  double* part = n.partial + (long long)blockIdx.x * NN_NPARAM + woff;
+  const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll
+  for (int c0 = 0; c0 < P::NB; c0 += 16) {
+    if (warp >= 4) break;  // warp-uniform
+    uint32_t r[16];
+    tmem_ld16(tl + c0, r);
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    if (real && ok) {
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        const int nc = c0 + e;
+        const double v = (nmma > 0) ? (double)__uint_as_float(r[e]) : 0.0;
+        if (nc < 3 * CIN) {
+          const int kx = nc / CIN, ci = nc % CIN;
+          part[(co * CIN + ci) * 9 + ky * 3 + kx] = v;
+        } else if (nc == 3 * CIN && ky == 1) {
+          part[COUT * CIN * 9 + co] = v;
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem) : "memory");
+}
+
 // the FP32 network input X (planar, 4 channels) as the first tensor-core layer's input: BF16
 // pixel-major, 16 channels per pixel (4 and 12 zeros)
 __global__ void nn_x16_kernel(NnArgs n, __nv_bfloat16* __restrict__ Xh) {
@@ -1436,8 +1673,22 @@ cudaError_t dgrad(const NnArgs& n, const void* gout, const void* aprev, void* gi
   return cudaGetLastError();
 }
 
+// BF16 weight gradient on the tensor cores: one block per weight-gradient partial sum
+template <int CIN, int COUT>
+cudaError_t wgrad_tc(const NnArgs& n, const void* gout, const void* ain, int woff, cudaStream_t s) {
+  using P = WgTc<CIN, COUT>;
+  auto k = nn_wgrad_tc_kernel<CIN, COUT>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, P::SMEM);
+  if (e != cudaSuccess) return e;
+  k<<<n.nwblk, WNT, P::SMEM, s>>>(n, static_cast<const float*>(gout), static_cast<const float*>(ain), woff);
+  return cudaGetLastError();
+}
+
 template <class T, int CIN, int COUT>
 cudaError_t wgrad(const NnArgs& n, const void* gout, const void* ain, int woff, cudaStream_t s) {
+  // BF16 precision: layers 2 and 3 on the tensor cores (the first layer's 4 input channels leave
+  // its tensor-core form slower than the FP32 kernel)
+  if (std::is_same<T, float>::value && n.bf16 && CIN >= 16) return wgrad_tc<CIN, COUT>(n, gout, ain, woff, s);
   if (std::is_same<T, float>::value) {
     const size_t tiles = 2 * wgrad_tile_floats<CIN, COUT>(), sums = WG_UNITS * 12 + NTHR;
     const size_t sm = sizeof(float) * (tiles > sums ? tiles : sums);

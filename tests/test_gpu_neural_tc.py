@@ -13,7 +13,8 @@ pass as tcgen05 implicit GEMMs, BF16 operands, FP32 accumulation) and js_nn_eval
 * js_nn_eval_vjp (the network's reverse alone): FP64 equal to torch's float64 autograd of the
   same network (itself pinned to the oracle's network on the CPU) to 1e-12, FP32 within FP32
   rounding; BF16 (data gradients of layers 3 and 2 on the tensor cores from BF16 copies of
-  the output gradients, padded from 4 to 16 channels for layer 3; weight gradients FP32)
+  the output gradients, padded from 4 to 16 channels for layer 3; weight gradients of layers 3
+  and 2 on the tensor cores from BF16-rounded output gradients and layer inputs, layer 1's FP32)
   equal to a CPU emulation of that arithmetic with the same bounds as the forward (a
   transposed or unflipped weight layout gives errors of order one).
 * The solver's reverse in BF16 mode against its FP32 mode (which the oracle pins): the
@@ -194,11 +195,13 @@ def _emulate_bf16_vjp(torch, w, X, GY, scale):
     g32 = conv2d_input(a2.shape, bf(w3), bf(g4), padding=1) * (a2 > 0)
     g16 = conv2d_input(a1.shape, bf(w2), bf(g32), padding=1) * (a1 > 0)
     gx = conv2d_input(x.shape, w1, g16, padding=1)
-    dw3 = conv2d_weight(a2, w3.shape, g4, padding=1)
-    dw2 = conv2d_weight(a1, w2.shape, g32, padding=1)
+    # weight gradients of layers 3 and 2 on the tensor cores (output gradients and layer inputs
+    # rounded to BF16), layer 1's in FP32
+    dw3 = conv2d_weight(bf(a2), w3.shape, bf(g4), padding=1)
+    dw2 = conv2d_weight(bf(a1), w2.shape, bf(g32), padding=1)
     dw1 = conv2d_weight(x, w1.shape, g16, padding=1)
-    return gx[0].double().numpy(), _grads_flat(dw1, g16.sum((0, 2, 3)), dw2, g32.sum((0, 2, 3)), dw3,
-                                               g4.sum((0, 2, 3)))
+    return gx[0].double().numpy(), _grads_flat(dw1, g16.sum((0, 2, 3)), dw2, bf(g32).sum((0, 2, 3)), dw3,
+                                               bf(g4).sum((0, 2, 3)))
 
 
 @pytest.mark.parametrize("shape", SHAPES)
