@@ -9,6 +9,7 @@ the largest single-GPU configuration: the viscous Mach-2 shock over the immersed
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload shock_cylinder|riemann2d|...]
     python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
     python bench.py --workload mach5_cylinder --to-end   # one whole run to the end time
+    python bench.py --to-end                             # the cylinder case's 2000 steps, per 250
     python bench.py --slabs 2,4 --steps 20               # the y-slab decomposition on one GPU
 
 Prints ONE JSON line (rank 0).  `value` is cell-updates/s with the state resident in HBM;
@@ -39,8 +40,8 @@ NN_FLOPS_PER_CELL_STAGE = 2 * 2 * 6336
 # DRAM bytes (read + write) per stage-kernel launch, mean of the three stages of one step,
 # from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of this bench's default
 # run with the TMA-staged variant 0 and the current kernel; None for other workloads or
-# variants.
-STAGE_TRAFFIC_BYTES = {("shock_cylinder", 0): 288.9e6, ("riemann2d", 0): 111.2e6}
+# variants (and for workloads whose capture predates the current kernel).
+STAGE_TRAFFIC_BYTES = {("shock_cylinder", 0): 291.0e6}
 # DRAM bytes per step of the persistent batched forward kernel on the 256-instance workload: an
 # ncu capture of one 2-step launch (19.26 GB), scaled by the steps of a launch
 BATCH_TRAFFIC_PER_STEP = 9.63e9
@@ -320,6 +321,13 @@ def run_ours(args):
                        "by js_step_taped) / js_step; ratio_rollout_backward: (js_step_taped + "
                        "js_step_vjp_taped) / js_step, the backward cost per step of a checkpointed rollout"}
 
+    # ---- the workload's whole run (step-count workloads): every part of it, not only the start ----
+    run = None
+    if prob.n_steps and not args.no_whole_run:
+        run = whole_run(prob, solver, U0.clone(), stream)
+        run["note"] = ("the configuration's whole run from t = 0 (js_step_cfl in chunks of 250 steps, CUDA "
+                       "events); `value` times the steps right after the initial condition")
+
     # ---- neural flux (Sec. 2.3): step and reverse step with the network, FP32 and FP64 -----
     neural = None
     if args.neural:
@@ -396,6 +404,7 @@ def run_ours(args):
                     "d2h_bytes_per_step": state_bytes},
             "adjoint_forward_ratio": None if adj is None else adj["ratio"],
             "adjoint": adj,
+            "whole_run": run,
             "neural": neural,
             "gpu_launches": launches,
             "clocks": sampler.summary(),
@@ -619,11 +628,11 @@ def run_to_end(args):
     from paper_2601_04400_gb300 import binding as B
     B.lib()
     prob, desc = workload(args.workload)
-    if prob.t_end is None:
-        raise SystemExit("workload %s has no end time" % args.workload)
     stream = torch.cuda.current_stream()
     solver = B.Solver.from_problem(prob, stream=stream)
     U = solver.prim_to_cons(torch.tensor(prob.W0, dtype=torch.float64, device="cuda"))
+    if prob.t_end is None:
+        return run_steps_to_end(args, prob, desc, solver, U, stream)
     outputs = sorted(set([t for t in (0.3, 1.0) if t < prob.t_end] + [prob.t_end]))
     rho_far = float(np.min(prob.W0[0]))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -655,6 +664,40 @@ def run_to_end(args):
                       "cells": cells, "seconds": gpu_s, "wall_seconds": wall,
                       "cell_updates_per_s": cells * steps / gpu_s, "dtype": "f64", "status_ok": status == 0,
                       "outputs": snaps}), flush=True)
+
+
+def whole_run(prob, solver, U, stream, chunk=250):
+    """The whole run of a workload defined by its step count (the viscous shock-cylinder case:
+    2000 CFL steps from t = 0) with device-computed step sizes (js_step_cfl, no host round trip),
+    in chunks timed with CUDA events: the throughput of every part of the run, from the quiescent
+    start to the developed wake.  U is advanced in place."""
+    import torch
+    ev = []
+    t = torch.zeros(1, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    done = 0
+    while done < prob.n_steps:
+        n = min(chunk, prob.n_steps - done)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        solver.step_cfl(U, prob.cfl, n, t=t)
+        b.record(stream)
+        ev.append((done, n, a, b))
+        done += n
+    torch.cuda.synchronize()
+    solver.check()
+    cells = prob.nx * prob.ny
+    gpu_s = sum(a.elapsed_time(b) for _, _, a, b in ev) * 1e-3
+    return {"steps": prob.n_steps, "t_final": float(t), "seconds": gpu_s,
+            "cell_updates_per_s": cells * prob.n_steps / gpu_s,
+            "chunks": [{"first_step": d, "steps": n, "ms_per_step": a.elapsed_time(b) / n} for d, n, a, b in ev]}
+
+
+def run_steps_to_end(args, prob, desc, solver, U, stream):
+    """--to-end for a workload defined by its step count: one whole run, timed in chunks."""
+    r = whole_run(prob, solver, U, stream)
+    print(json.dumps({"mode": "run_n_steps", "workload": desc, "cells": prob.nx * prob.ny, "dtype": "f64", **r}),
+          flush=True)
 
 
 def run_slabs(args):
@@ -711,9 +754,12 @@ def main():
                     help="batched workload: steps of the rollout whose checkpointed reverse is timed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-whole-run", action="store_true",
+                    help="skip the timing of the workload's whole run (step-count workloads)")
     ap.add_argument("--neural", action="store_true", help="also time steps with the neural flux")
     ap.add_argument("--to-end", action="store_true",
-                    help="one whole run of the workload to its end time (CFL steps), timed as an application")
+                    help="one whole run of the workload to its end time or step count (CFL steps), timed "
+                         "as an application")
     ap.add_argument("--slabs", default=None,
                     help="comma-separated slab counts: time the y-slab decomposition held by this process")
     ap.add_argument("--overlap", type=int, default=3, help="overlap rows of the slabs (--slabs)")

@@ -251,7 +251,26 @@ __device__ __forceinline__ void hllc_vjp(const Face4& L, const Face4& R, const G
     }
     bss += bs2;
   };
-  if (ss == 0.0) {
+  if (ss == 0.0 && sL < 0.0 && sR > 0.0) {
+    // Reverse of the s* = 0 closed form of the forward flux: at s* = 0 (spm = s on both sides)
+    // the derivatives of a branch's star flux F_K + s_K (U*_K - U_K) reduce to
+    //   dF0 = (m/s) ds*,   dF1 = -u d drho + rho (2u - s) du + dp - rho u ds + m ds*,
+    //   dF2 = (m ut/s) ds*,   dF3 = (d (E + p)/s - m u) ds*      (d = s - u, m = rho d),
+    // with d and m already substituted (no separate d, m adjoints) and no gamma dependence
+    // (dF/dE = 0 there); each branch carries half of the face's flux adjoint.
+    auto side0 = [&](const Face4& Q, double s, double d, double m, Face4& bQ, double& bsK) {
+      const double f1 = 0.5 * Fb[1];
+      const double is = recip(s);
+      const double E = fma(0.5 * Q.r, fma(Q.un, Q.un, Q.ut * Q.ut), Q.p * g.g1);
+      bss += 0.5 * (fma(fma(Fb[2], Q.ut, Fb[0]), m * is, Fb[1] * m) + Fb[3] * fma(d * (E + Q.p), is, -m * Q.un));
+      bQ.r -= f1 * Q.un * d;
+      bQ.un += f1 * Q.r * (2.0 * Q.un - s);
+      bQ.p += f1;
+      bsK -= f1 * Q.r * Q.un;
+    };
+    side0(L, sL, dL, mL, bL, bsL);
+    side0(R, sR, dR, mR, bR, bsR);
+  } else if (ss == 0.0) {
     side(true, 0.5);
     side(false, 0.5);
   } else {

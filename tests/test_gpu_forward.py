@@ -35,6 +35,10 @@ def _cases():
     out.append(("cylinder_ns_100x52", p, W.random_state(p, seed=2, amp=0.02)))
     p = W.shock_cylinder(nx=64, ny=40, mach=2.5, viscous=False)
     out.append(("cylinder_euler_64x40", p, W.random_state(p, seed=5, amp=0.05)))
+    # the unperturbed initial condition: the quiescent gas ahead of the shock gives contact
+    # speed s* = 0 exactly at most faces (the two-branch average of the HLLC flux)
+    p = W.shock_cylinder(nx=100, ny=52, mach=2.0, Re=500.0)
+    out.append(("cylinder_ns_initial_100x52", p, p.W0))
     p = W.random_periodic(33, 38, seed=9).with_(bc=(1, 3, 3, 1), inflow=np.array(
         [[1.1, 0.2, 0.1, 0.9], [0.9, -0.1, 0.0, 1.1], [1.0, 0.05, 0.3, 1.0], [1.2, 0.0, -0.2, 0.8]]))
     out.append(("mixed_bc_33x38", p, p.W0))
