@@ -221,6 +221,28 @@ def test_hllc_preserves_stationary_contact():
     assert np.array_equal(F, np.array([0.0, 2.0, 0.0, 0.0]))
 
 
+def test_hllc_average_at_zero_contact_speed_is_the_star_pressure_flux():
+    """At s* = 0 (reading O4: the average of both branches) with sL < 0 < sR, each branch's
+    star flux F_K + s_K (U*_K - U_K) reduces to (0, p_K - m_K u_K, 0, 0), m_K = rho_K (s_K -
+    u_K).  Symmetric collisions and expansions (normal velocities +w | -w, equal rho and p,
+    different tangential velocities) give s* = 0 exactly with u != 0; the oracle's two-branch
+    average must equal that closed form, which the fast GPU kernels evaluate instead of the
+    branches.  Using F_K without the star correction (spm = 0), a sign slip in the star energy
+    or star momentum, or the wrong wave speed in a branch breaks it."""
+    rng = np.random.default_rng(11)
+    for _ in range(200):
+        g = rng.uniform(1.1, 1.8)
+        r, p, w = rng.uniform(0.2, 3.0), rng.uniform(0.2, 3.0), rng.uniform(-1.5, 1.5)
+        qL = np.array([r, w, rng.uniform(-1, 1), p])
+        qR = np.array([r, -w, rng.uniform(-1, 1), p])
+        F, d = O.hllc(qL, qR, g)
+        assert d["ss"] == 0.0 and d["sL"] < 0.0 < d["sR"]
+        mL, mR = r * (d["sL"] - w), r * (d["sR"] + w)
+        pstar = 0.5 * ((p - mL * w) + (p + mR * w))
+        scale = p + r * (abs(w) + np.sqrt(g * p / r)) ** 2
+        assert np.abs(F - np.array([0.0, pstar, 0.0, 0.0])).max() <= 1e-13 * scale
+
+
 # ---------------------------------------------------------------------------------------
 # solver-level invariants
 # ---------------------------------------------------------------------------------------
