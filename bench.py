@@ -518,20 +518,28 @@ def run_batched(args):
     for s in solvers:
         s.set_stream(stream)
     ok = ok and all(s.status() == 0 for s in solvers)
-    # reverse of one batched step (js_batch_step_vjp: one persistent launch over all
-    # instances) against one batched forward step
+    # reverse of one batched step (js_batch_step_vjp over all instances) against one batched
+    # forward step, in both launch forms (one persistent launch; one launch per phase); the tuner
+    # keeps the faster for the rollout below
     dts = [s.max_dt(U, 0.5) for s, U in zip(solvers, states)]
     lams = [torch.randn_like(U) for U in states]
     outs = [torch.empty_like(U) for U in states]
-    batch.step_vjp(states, dts, lams, outs)
-    torch.cuda.synchronize()
+    rev_tuned = tuning.autotune_batch_reverse(batch, mine, states, dts)
+    t_vjp_form = {}
+    choice = batch.reverse_launch()
     reps = 3
-    e0.record(stream)
-    for _ in range(reps):
+    for split in (0, 1):
+        batch.set_reverse_launch(split)
         batch.step_vjp(states, dts, lams, outs)
-    e1.record(stream)
-    e1.synchronize()
-    t_vjp = e0.elapsed_time(e1) / reps
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            batch.step_vjp(states, dts, lams, outs)
+        e1.record(stream)
+        e1.synchronize()
+        t_vjp_form[split] = e0.elapsed_time(e1) / reps
+    batch.set_reverse_launch(choice)
+    t_vjp = t_vjp_form[choice]
     ok = ok and batch.status() == 0
     # the whole rollout: n_ro CFL steps forward (step sizes logged), then its reverse
     # (js_batch_rollout_vjp) with the library's checkpoint spacing (every state when they fit in
@@ -571,7 +579,7 @@ def run_batched(args):
         roll = {"steps": n_ro, "checkpoint_every": ck, "ms_forward_plain": t_ro_plain,
                 "ms_forward_checkpointed": t_ro_f, "ms_reverse": t_ro_b, "ratio": t_ro_b / t_ro_plain,
                 "note": "ratio: js_batch_rollout_vjp (per segment: re-run keeping its states and stage "
-                        "states + one persistent reverse launch per step taking the stage states as given, "
+                        "states + the reverse of each step (the chosen launch form) taking the stage states as given, "
                         "from the checkpoints js_batch_rollout_forward kept; spacing 1 = every state and "
                         "stage state kept by the forward, no re-runs) / the plain batched forward run of "
                         "the same steps (one launch, device CFL)"}
@@ -609,9 +617,12 @@ def run_batched(args):
             "speedup_vs_one_at_a_time": t_seq / t_batch,
             "speedup_vs_graph": t_graph / t_batch,
             "adjoint": {"ms_per_step_vjp": t_vjp, "ratio": t_vjp / (t_batch / args.steps),
-                        "note": "js_batch_step_vjp (one persistent launch: recompute of the stage states "
-                                "and the reverse of the 3 stages of every instance) / one batched forward "
-                                "step, rank 0's instances"},
+                        "launch": "one launch per phase" if choice else "one persistent launch",
+                        "ms_per_step_vjp_persistent": t_vjp_form[0], "ms_per_step_vjp_split": t_vjp_form[1],
+                        "tuner_timed": {str(k): v for k, v in rev_tuned.items()},
+                        "note": "js_batch_step_vjp (recompute of the stage states and the reverse of the 3 "
+                                "stages of every instance; the launch form the tuner chose) / one batched "
+                                "forward step, rank 0's instances"},
             "rollout": roll}), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -387,6 +387,21 @@ int js_batch_info(js_batch* b, int* blocks, int* tiles, long long* cells);
 int js_batch_set_tuning(js_batch* b, int blocks_per_sm, int schedule);
 int js_batch_get_tuning(js_batch* b, int* blocks_per_sm, int* max_blocks_per_sm, int* schedule, int* n_schedules);
 
+/* Launch form of the batched reverse step (js_batch_step_vjp and every reverse step of
+ * js_batch_rollout_vjp; the gradient chain rule of Sec. 2 applied to each instance):
+ *   split = 0 (default): ONE persistent cooperative launch per reverse step, its phases (pack,
+ *     forward recompute, then per stage: seed + primitives, pass 1, pass 2, primitive reverse,
+ *     transposed halos, inflow gradient and IB ghosts, IB sources; unpack) separated by
+ *     bounded grid barriers, every phase at the register allocation of the heaviest one;
+ *   split = 1: one ordinary launch per phase (up to 34 per reverse step), in the same order on
+ *     the batch's stream, each phase kernel at its own occupancy.
+ * Both run the same device code on the same work items in the same order: lambda and the
+ * parameter gradient are identical bit for bit.  Both can be captured in a CUDA graph.
+ * Synchronises the batch's stream (call before any stream capture).  Errors: JS_ERR_ARG for a
+ * split value other than 0 or 1. */
+int js_batch_set_reverse_launch(js_batch* b, int split);
+int js_batch_get_reverse_launch(js_batch* b, int* split);
+
 /* The context of instance k (owned by the batch; do not destroy it), e.g. for js_step_vjp. */
 js_ctx* js_batch_instance(js_batch* b, int k);
 

@@ -95,6 +95,8 @@ SIGNATURES = {
     "js_batch_step_fixed": (_I, [_P, _I, _P]),
     "js_batch_set_tuning": (_I, [_P, _I, _I]),
     "js_batch_get_tuning": (_I, [_P, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
+    "js_batch_set_reverse_launch": (_I, [_P, _I]),
+    "js_batch_get_reverse_launch": (_I, [_P, C.POINTER(_I)]),
     "js_batch_rollout_vjp": (_I, [_P, _I, _P, _I, C.POINTER(_P), C.POINTER(_P)]),
     "js_batch_rollout_forward": (_I, [_P, _D, _I, _I, _P]),
     "js_batch_rollout_spacing": (_I, [_P, _I, C.POINTER(_I)]),
@@ -553,6 +555,16 @@ class Batch:
         v = [C.c_int(0) for _ in range(4)]
         _check(lib().js_batch_get_tuning(self.handle, *[C.byref(x) for x in v]), "js_batch_get_tuning")
         return tuple(x.value for x in v)
+
+    def set_reverse_launch(self, split):
+        """Launch form of the batched reverse step: 0 one persistent launch, 1 one launch per
+        phase (identical results)."""
+        _check(lib().js_batch_set_reverse_launch(self.handle, int(split)), "js_batch_set_reverse_launch")
+
+    def reverse_launch(self):
+        v = C.c_int(0)
+        _check(lib().js_batch_get_reverse_launch(self.handle, C.byref(v)), "js_batch_get_reverse_launch")
+        return v.value
 
     def step_fixed(self, dts):
         """Advance every registered state len(dts) steps of the given sizes: dts float64 CUDA

@@ -391,34 +391,96 @@ __device__ __forceinline__ void rev_reduce(const InstRev& r, bool saved, double*
   adj_pbar_reduce_block(r.ppart, off, cnt, 4, pbar);
 }
 
-__global__ void __launch_bounds__(BNT) batch_vjp_kernel(BatchRevArgs b) {
-  extern __shared__ double smem[];
+// The phases of one batched reverse step.  Each runs over the work items of all instances with
+// grid-stride loops, so it is correct for any grid; the persistent kernel runs them in order
+// with grid barriers between them, the split launch as one kernel per phase (each with its own
+// register allocation and occupancy).
+enum RevPhase {
+  RP_PACK = 0,      // pack U_n, lambda_{n+1} (and given stage states); Uacc = 0
+  RP_GHOST,         // IB fill of stage input s
+  RP_HALO,          // halo fill of stage input s
+  RP_STAGE,         // forward recompute of stage s (0, 1), storing its WENO5 internals
+  RP_SEED,          // reverse stage s: seed + primitives (+ reduction of stage s+1's partials)
+  RP_PASS1,         // pass 1 (x lines, then y lines)
+  RP_PASS2,         // pass 2
+  RP_PRIMVJP,       // primitive reverse
+  RP_BCTY,          // transposed y halos
+  RP_BCTX,          // transposed x halos
+  RP_INFLOW_GHOST,  // inflow-state gradient + transposed IB ghosts
+  RP_SRC,           // transposed IB sources
+  RP_UNPACK,        // lambda_n = P1 + Uacc; the last stage's parameter gradient
+  RP_N
+};
+
+// pass 1 of reverse stage s (x lines, then y lines from the 32-aligned offset xpad).  SVM 0:
+// WENO5 internals stored or recomputed as the call decides (rev_saved), 1: stored, 2:
+// recomputed; VM 0: every instance, 1: the viscous instances only, 2: the inviscid ones only --
+// the split launch fixes both on the host, so that each kernel holds only the pass-1 variant it
+// runs (and its register allocation is that variant's).
+template <int SVM, int VM = 0>
+__device__ __forceinline__ void rev_pass1(const BatchRevArgs& b, int s) {
   const RevCall& call = b.call;
-  // ---- pack U_n -> N and lambda_{n+1} -> P0; Uacc = 0
-  rev_items(b, RK_USER4, [&](int k, long long t) {
-    if (k < 0) return;
+  const bool even = (s == 2) || (s == 0);
+  const bool sv = (SVM == 0) ? rev_saved(call, s) : (SVM == 1);
+  rev_items(b, sv ? RK_P1SV : RK_P1RE, [&](int k, long long item) {
+    if (k < 0) return;  // whole warps past the end: nothing to do, no partials
     const InstDesc& d = b.inst[k];
-    const long long n = (long long)d.lay.nx * d.lay.ny;
-    if (t >= 4 * n) return;
-    const int c = (int)(t / n);
-    const long long o = t % n;
-    const long long p = c * d.lay.plane + d.lay.idx((int)(o % d.lay.nx), (int)(o / d.lay.nx));
-    d.N[p] = call.Un[k][t];
-    b.rev[k].P0[p] = call.lam1[k][t];
-    if (call.U1) {
-      d.A[p] = call.U1[k][t];
-      d.B[p] = call.U2[k][t];
+    if ((VM == 1 && !d.visc) || (VM == 2 && d.visc)) return;  // the other kernel's instance
+    const InstRev& r = b.rev[k];
+    const AdjArgs a = rev_adj(r, d, s, call, k, even ? r.P1 : r.P0, true);
+    const long long xpad = sv ? r.xpad_sv : r.xpad_re;
+    const int seg = sv ? r.seg1_sv : r.seg1_re;
+    const int dir = item < xpad ? 0 : 1;
+    const long long it = dir == 0 ? item : item - xpad;
+    const long long wofs = dir == 0 ? 0 : (xpad >> 5);
+    const bool visc = (VM == 0) ? d.visc : (VM == 1);
+    if (SVM != 2 && sv) {
+      if (VM != 2 && visc) {
+        if (dir == 0) pass1_body<0, true, true, true>(a, seg, it, wofs);
+        else pass1_body<1, true, true, true>(a, seg, it, wofs);
+      } else if (VM != 1) {
+        if (dir == 0) pass1_body<0, false, false, true>(a, seg, it, wofs);
+        else pass1_body<1, false, false, true>(a, seg, it, wofs);
+      }
+    } else if (SVM != 1) {
+      if (VM != 2 && visc) {
+        if (dir == 0) pass1_body<0, true, true, false>(a, seg, it, wofs);
+        else pass1_body<1, true, true, false>(a, seg, it, wofs);
+      } else if (VM != 1) {
+        if (dir == 0) pass1_body<0, false, false, false>(a, seg, it, wofs);
+        else pass1_body<1, false, false, false>(a, seg, it, wofs);
+      }
     }
   });
-  rev_items(b, RK_PLANE, [&](int k, long long t) {
-    if (k < 0 || t >= b.inst[k].lay.plane) return;
-    const InstDesc& d = b.inst[k];
+}
+
+template <int PH>
+__device__ __forceinline__ void rev_phase(const BatchRevArgs& b, int s, double* smem) {
+  const RevCall& call = b.call;
+  const bool even = (s == 2) || (s == 0);  // reverse stages 2 and 0 read P0, write P1
+  if constexpr (PH == RP_PACK) {
+    rev_items(b, RK_USER4, [&](int k, long long t) {
+      if (k < 0) return;
+      const InstDesc& d = b.inst[k];
+      const long long n = (long long)d.lay.nx * d.lay.ny;
+      if (t >= 4 * n) return;
+      const int c = (int)(t / n);
+      const long long o = t % n;
+      const long long p = c * d.lay.plane + d.lay.idx((int)(o % d.lay.nx), (int)(o / d.lay.nx));
+      d.N[p] = call.Un[k][t];
+      b.rev[k].P0[p] = call.lam1[k][t];
+      if (call.U1) {
+        d.A[p] = call.U1[k][t];
+        d.B[p] = call.U2[k][t];
+      }
+    });
+    rev_items(b, RK_PLANE, [&](int k, long long t) {
+      if (k < 0 || t >= b.inst[k].lay.plane) return;
+      const InstDesc& d = b.inst[k];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) b.rev[k].Uacc[c * d.lay.plane + t] = 0.0;
-  });
-  if (!grid_sync_on(b.bar, b.err, 0, b.budget)) return;
-  // ---- forward recompute of the stage inputs X0 = N, X1 = A, X2 = B
-  for (int s = 0; s < 3; ++s) {
+      for (int c = 0; c < 4; ++c) b.rev[k].Uacc[c * d.lay.plane + t] = 0.0;
+    });
+  } else if constexpr (PH == RP_GHOST) {
     rev_items(b, RK_GHOST, [&](int k, long long g) {
       if (k < 0) return;
       const InstDesc& d = b.inst[k];
@@ -426,7 +488,7 @@ __global__ void __launch_bounds__(BNT) batch_vjp_kernel(BatchRevArgs b) {
       double* X = (s == 0) ? d.N : ((s == 1) ? d.A : d.B);
       ib_fill_one(X, d.lay, d.ib, d.gamma, d.wall, (int)g);
     });
-    if (!grid_sync_on(b.bar, b.err, 0, b.budget)) return;
+  } else if constexpr (PH == RP_HALO) {
     rev_items(b, RK_HALO, [&](int k, long long h) {
       if (k < 0) return;
       const InstDesc& d = b.inst[k];
@@ -434,9 +496,7 @@ __global__ void __launch_bounds__(BNT) batch_vjp_kernel(BatchRevArgs b) {
       double* X = (s == 0) ? d.N : ((s == 1) ? d.A : d.B);
       bc_fill_one(X, d.lay, d.bc, h);
     });
-    if (!grid_sync_on(b.bar, b.err, 0, b.budget)) return;
-    if (s == 2) break;
-    if (call.U1) continue;  // the stage states were given: only their ghosts and halos are filled
+  } else if constexpr (PH == RP_STAGE) {
     for (int it = blockIdx.x; it < b.tile0[b.count]; it += gridDim.x) {
       const int k = find_inst(b.tile0, b.count, it);
       const InstDesc& d = b.inst[k];
@@ -473,13 +533,9 @@ __global__ void __launch_bounds__(BNT) batch_vjp_kernel(BatchRevArgs b) {
       else stage_tile_c<BTX, BTY, BLX, BLY, false, false, false, true>(a, t % d.ntx, t / d.ntx, smem);
       __syncthreads();  // the next tile reuses shared memory
     }
-    if (!grid_sync_on(b.bar, b.err, 0, b.budget)) return;
-  }
-  // ---- reverse through the stages 2, 1, 0: P0 -> P1 -> P0 -> P1
-  const double ra[3] = {0.0, 0.75, 1.0 / 3.0};
-  const double rb[3] = {1.0, 0.25, 2.0 / 3.0};
-  for (int s = 2; s >= 0; --s) {
-    const bool even = (s == 2) || (s == 0);  // src = P0 for stages 2 and 0
+  } else if constexpr (PH == RP_SEED) {
+    const double ra[3] = {0.0, 0.75, 1.0 / 3.0};
+    const double rb[3] = {1.0, 0.25, 2.0 / 3.0};
     // seed + primitives; the parameter-gradient partials of stage s+1 are reduced meanwhile
     rev_items(b, RK_PLANE, [&](int k, long long t) {
       if (k < 0) return;
@@ -493,35 +549,9 @@ __global__ void __launch_bounds__(BNT) batch_vjp_kernel(BatchRevArgs b) {
     if (s < 2 && call.pbar)
       for (int k = blockIdx.x; k < b.count; k += gridDim.x)
         if (call.pbar[k]) rev_reduce(b.rev[k], rev_saved(call, s + 1), call.pbar[k]);
-    if (!grid_sync_on(b.bar, b.err, 0, b.budget)) return;
-    // pass 1 (x lines, then y lines from the 32-aligned offset xpad)
-    const bool sv = rev_saved(call, s);
-    rev_items(b, sv ? RK_P1SV : RK_P1RE, [&](int k, long long item) {
-      if (k < 0) return;  // whole warps past the end: nothing to do, no partials
-      const InstDesc& d = b.inst[k];
-      const InstRev& r = b.rev[k];
-      const AdjArgs a = rev_adj(r, d, s, call, k, even ? r.P1 : r.P0, true);
-      const long long xpad = sv ? r.xpad_sv : r.xpad_re;
-      const int seg = sv ? r.seg1_sv : r.seg1_re;
-      if (item < xpad) {
-        if (d.visc) {
-          if (sv) pass1_body<0, true, true, true>(a, seg, item, 0);
-          else pass1_body<0, true, true, false>(a, seg, item, 0);
-        } else {
-          if (sv) pass1_body<0, false, false, true>(a, seg, item, 0);
-          else pass1_body<0, false, false, false>(a, seg, item, 0);
-        }
-      } else {
-        if (d.visc) {
-          if (sv) pass1_body<1, true, true, true>(a, seg, item - xpad, xpad >> 5);
-          else pass1_body<1, true, true, false>(a, seg, item - xpad, xpad >> 5);
-        } else {
-          if (sv) pass1_body<1, false, false, true>(a, seg, item - xpad, xpad >> 5);
-          else pass1_body<1, false, false, false>(a, seg, item - xpad, xpad >> 5);
-        }
-      }
-    });
-    if (!grid_sync_on(b.bar, b.err, 0, b.budget)) return;
+  } else if constexpr (PH == RP_PASS1) {
+    rev_pass1<0>(b, s);
+  } else if constexpr (PH == RP_PASS2) {
     rev_items(b, RK_P2, [&](int k, long long item) {
       if (k < 0) return;
       const InstDesc& d = b.inst[k];
@@ -530,7 +560,7 @@ __global__ void __launch_bounds__(BNT) batch_vjp_kernel(BatchRevArgs b) {
       if (item < r.xpad_p2) pass2_body<0>(a, r.seg2, item);
       else pass2_body<1>(a, r.seg2, item - r.xpad_p2);
     });
-    if (!grid_sync_on(b.bar, b.err, 0, b.budget)) return;
+  } else if constexpr (PH == RP_PRIMVJP) {
     rev_items(b, RK_PLANE, [&](int k, long long t) {
       if (k < 0) return;
       const InstDesc& d = b.inst[k];
@@ -541,23 +571,15 @@ __global__ void __launch_bounds__(BNT) batch_vjp_kernel(BatchRevArgs b) {
       else adj_primvjp_one<false>(a, t, r.seg2, gb, nb);
       warp_partials(a.pp, r.off_prim + (t >> 5), gb, 0.0, 0.0, nb);
     });
-    if (!grid_sync_on(b.bar, b.err, 0, b.budget)) return;
-    rev_items(b, RK_BCTY, [&](int k, long long t) {
+  } else if constexpr (PH == RP_BCTY || PH == RP_BCTX) {
+    rev_items(b, PH == RP_BCTY ? RK_BCTY : RK_BCTX, [&](int k, long long t) {
       if (k < 0) return;
       const InstDesc& d = b.inst[k];
       const InstRev& r = b.rev[k];
       const AdjArgs a = rev_adj(r, d, s, call, k, even ? r.P1 : r.P0, false);
-      adj_bcT_one(a, d.bc, 1, r.inflow_part, r.tmax, t);
+      adj_bcT_one(a, d.bc, PH == RP_BCTY ? 1 : 0, r.inflow_part, r.tmax, t);
     });
-    if (!grid_sync_on(b.bar, b.err, 0, b.budget)) return;
-    rev_items(b, RK_BCTX, [&](int k, long long t) {
-      if (k < 0) return;
-      const InstDesc& d = b.inst[k];
-      const InstRev& r = b.rev[k];
-      const AdjArgs a = rev_adj(r, d, s, call, k, even ? r.P1 : r.P0, false);
-      adj_bcT_one(a, d.bc, 0, r.inflow_part, r.tmax, t);
-    });
-    if (!grid_sync_on(b.bar, b.err, 0, b.budget)) return;
+  } else if constexpr (PH == RP_INFLOW_GHOST) {
     // inflow-state gradient (one block per instance) and the transposed IB ghosts
     for (int k = blockIdx.x; k < b.count; k += gridDim.x) {
       const InstDesc& d = b.inst[k];
@@ -574,7 +596,7 @@ __global__ void __launch_bounds__(BNT) batch_vjp_kernel(BatchRevArgs b) {
       adj_ib_ghost_one(a, d.ib, d.wall, r.qIb, (int)g, gb);
       warp_partials(a.pp, r.off_g + (g >> 5), gb, 0.0, 0.0, 0.0);
     });
-    if (!grid_sync_on(b.bar, b.err, 0, b.budget)) return;
+  } else if constexpr (PH == RP_SRC) {
     rev_items(b, RK_SRC, [&](int k, long long q) {
       if (k < 0) return;
       const InstDesc& d = b.inst[k];
@@ -584,18 +606,67 @@ __global__ void __launch_bounds__(BNT) batch_vjp_kernel(BatchRevArgs b) {
       adj_ib_src_one(a, r.ibt, r.qIb, (int)q, gb);
       warp_partials(a.pp, r.off_s + (q >> 5), gb, 0.0, 0.0, 0.0);
     });
+  } else if constexpr (PH == RP_UNPACK) {
+    // lambda_n = P1 + Uacc (stage 0 wrote P1); the last stage's parameter gradient
+    rev_items(b, RK_USER4, [&](int k, long long t) {
+      if (k < 0) return;
+      const InstDesc& d = b.inst[k];
+      if (t >= 4LL * d.lay.nx * d.lay.ny) return;
+      adj_unpack_add_one(b.rev[k].P1, b.rev[k].Uacc, call.lam0[k], d.lay, t);
+    });
+    if (call.pbar)
+      for (int k = blockIdx.x; k < b.count; k += gridDim.x)
+        if (call.pbar[k]) rev_reduce(b.rev[k], rev_saved(call, 0), call.pbar[k]);
+  }
+}
+
+__global__ void __launch_bounds__(BNT) batch_vjp_kernel(BatchRevArgs b) {
+  extern __shared__ double smem[];
+  rev_phase<RP_PACK>(b, 0, smem);
+  if (!grid_sync_on(b.bar, b.err, 0, b.budget)) return;
+  // ---- forward recompute of the stage inputs X0 = N, X1 = A, X2 = B
+  for (int s = 0; s < 3; ++s) {
+    rev_phase<RP_GHOST>(b, s, smem);
+    if (!grid_sync_on(b.bar, b.err, 0, b.budget)) return;
+    rev_phase<RP_HALO>(b, s, smem);
+    if (!grid_sync_on(b.bar, b.err, 0, b.budget)) return;
+    if (s == 2) break;
+    if (b.call.U1) continue;  // the stage states were given: only their ghosts and halos are filled
+    rev_phase<RP_STAGE>(b, s, smem);
     if (!grid_sync_on(b.bar, b.err, 0, b.budget)) return;
   }
-  // ---- lambda_n = P1 + Uacc (stage 0 wrote P1); the last stage's parameter gradient
-  rev_items(b, RK_USER4, [&](int k, long long t) {
-    if (k < 0) return;
-    const InstDesc& d = b.inst[k];
-    if (t >= 4LL * d.lay.nx * d.lay.ny) return;
-    adj_unpack_add_one(b.rev[k].P1, b.rev[k].Uacc, call.lam0[k], d.lay, t);
-  });
-  if (call.pbar)
-    for (int k = blockIdx.x; k < b.count; k += gridDim.x)
-      if (call.pbar[k]) rev_reduce(b.rev[k], rev_saved(call, 0), call.pbar[k]);
+  // ---- reverse through the stages 2, 1, 0: P0 -> P1 -> P0 -> P1
+  for (int s = 2; s >= 0; --s) {
+    rev_phase<RP_SEED>(b, s, smem);
+    if (!grid_sync_on(b.bar, b.err, 0, b.budget)) return;
+    rev_phase<RP_PASS1>(b, s, smem);
+    if (!grid_sync_on(b.bar, b.err, 0, b.budget)) return;
+    rev_phase<RP_PASS2>(b, s, smem);
+    if (!grid_sync_on(b.bar, b.err, 0, b.budget)) return;
+    rev_phase<RP_PRIMVJP>(b, s, smem);
+    if (!grid_sync_on(b.bar, b.err, 0, b.budget)) return;
+    rev_phase<RP_BCTY>(b, s, smem);
+    if (!grid_sync_on(b.bar, b.err, 0, b.budget)) return;
+    rev_phase<RP_BCTX>(b, s, smem);
+    if (!grid_sync_on(b.bar, b.err, 0, b.budget)) return;
+    rev_phase<RP_INFLOW_GHOST>(b, s, smem);
+    if (!grid_sync_on(b.bar, b.err, 0, b.budget)) return;
+    rev_phase<RP_SRC>(b, s, smem);
+    if (!grid_sync_on(b.bar, b.err, 0, b.budget)) return;
+  }
+  rev_phase<RP_UNPACK>(b, 0, smem);
+}
+
+// one phase of the reverse step as a kernel of its own (split launch); pass 1 has one kernel
+// per WENO5-internals mode
+template <int PH>
+__global__ void __launch_bounds__(BNT) batch_vjp_phase_kernel(BatchRevArgs b, int s) {
+  extern __shared__ double smem[];
+  rev_phase<PH>(b, s, smem);
+}
+template <bool SV, bool VISC>
+__global__ void __launch_bounds__(BNT) batch_vjp_pass1_kernel(BatchRevArgs b, int s) {
+  rev_pass1<SV ? 1 : 2, VISC ? 1 : 2>(b, s);
 }
 
 // one launch copying every instance's state: dst[k][i] = src[k][i], i < pre[k+1] - pre[k]
@@ -641,6 +712,10 @@ struct js_batch {
   js::InstRev* d_rev = nullptr;
   long long* d_pre = nullptr;   // [RK_N][count + 1]
   int rev_blocks = 0;
+  int rev_split = 0;                  // 1: one launch per phase (js_batch_set_reverse_launch)
+  int rev_pblocks[js::RP_N] = {};     // grid of each phase kernel of the split launch
+  int rev_p1blocks[2][2] = {};        // grid of its pass-1 kernels [stored internals][viscous]
+  bool has_visc = false, has_inv = false;  // the batch holds viscous / inviscid instances
   void** d_tab = nullptr;       // call table of js_batch_step_vjp: U_n, lam_np1, lam_n, p_bar x count
   double* d_dt = nullptr;       // its step sizes
   // checkpointed rollout reverse (js_batch_rollout_vjp)
@@ -718,6 +793,38 @@ int rev_prepare(js_batch* b) {
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, js::batch_vjp_kernel, js::BNT, smem);
   if (per_sm < 1) return JS_ERR_CUDA;
   b->rev_blocks = sms * per_sm;
+  // the split launch: each phase kernel's own resident blocks per SM
+  if (cudaFuncSetAttribute(js::batch_vjp_phase_kernel<js::RP_STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess)
+    return JS_ERR_CUDA;
+  const void* kern[js::RP_N] = {
+      (const void*)js::batch_vjp_phase_kernel<js::RP_PACK>, (const void*)js::batch_vjp_phase_kernel<js::RP_GHOST>,
+      (const void*)js::batch_vjp_phase_kernel<js::RP_HALO>, (const void*)js::batch_vjp_phase_kernel<js::RP_STAGE>,
+      (const void*)js::batch_vjp_phase_kernel<js::RP_SEED>, (const void*)js::batch_vjp_phase_kernel<js::RP_PASS1>,
+      (const void*)js::batch_vjp_phase_kernel<js::RP_PASS2>, (const void*)js::batch_vjp_phase_kernel<js::RP_PRIMVJP>,
+      (const void*)js::batch_vjp_phase_kernel<js::RP_BCTY>, (const void*)js::batch_vjp_phase_kernel<js::RP_BCTX>,
+      (const void*)js::batch_vjp_phase_kernel<js::RP_INFLOW_GHOST>,
+      (const void*)js::batch_vjp_phase_kernel<js::RP_SRC>, (const void*)js::batch_vjp_phase_kernel<js::RP_UNPACK>};
+  for (int ph = 0; ph < js::RP_N; ++ph) {
+    int ps = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, kern[ph], js::BNT, ph == js::RP_STAGE ? smem : 0) !=
+            cudaSuccess ||
+        ps < 1)
+      return JS_ERR_CUDA;
+    b->rev_pblocks[ph] = sms * ps;
+  }
+  const void* p1[2][2] = {
+      {(const void*)js::batch_vjp_pass1_kernel<false, false>, (const void*)js::batch_vjp_pass1_kernel<false, true>},
+      {(const void*)js::batch_vjp_pass1_kernel<true, false>, (const void*)js::batch_vjp_pass1_kernel<true, true>}};
+  for (int sv = 0; sv < 2; ++sv)
+    for (int v = 0; v < 2; ++v) {
+      int ps = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, p1[sv][v], js::BNT, 0) != cudaSuccess || ps < 1)
+        return JS_ERR_CUDA;
+      b->rev_p1blocks[sv][v] = sms * ps;
+    }
+  b->has_visc = b->has_inv = false;
+  for (int k = 0; k < n; ++k) (b->desc[k].visc ? b->has_visc : b->has_inv) = true;
   if (cudaMalloc(&b->d_rev, sizeof(js::InstRev) * n) != cudaSuccess ||
       cudaMalloc(&b->d_pre, sizeof(long long) * pre.size()) != cudaSuccess ||
       cudaMalloc(&b->d_tab, sizeof(void*) * 4 * n) != cudaSuccess ||
@@ -746,6 +853,50 @@ int rev_launch(js_batch* b, const js::RevCall& call) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
   a.budget = (long long)(2.0 * (khz > 0 ? khz : 2000000) * 1e3);  // 2 s of SM clock cycles
+  if (b->rev_split) {
+    // one launch per phase, in the persistent kernel's order; kernel boundaries take the place
+    // of its grid barriers
+    bool ok = true;
+    auto run = [&](auto kernel, int ph, int s) {
+      if (!ok) return;
+      kernel<<<b->rev_pblocks[ph], js::BNT, ph == js::RP_STAGE ? batch_smem() : 0, b->stream>>>(a, s);
+      ok = cudaGetLastError() == cudaSuccess;
+    };
+    run(js::batch_vjp_phase_kernel<js::RP_PACK>, js::RP_PACK, 0);
+    for (int s = 0; s < 3; ++s) {
+      run(js::batch_vjp_phase_kernel<js::RP_GHOST>, js::RP_GHOST, s);
+      run(js::batch_vjp_phase_kernel<js::RP_HALO>, js::RP_HALO, s);
+      if (s == 2) break;
+      if (call.U1) continue;
+      run(js::batch_vjp_phase_kernel<js::RP_STAGE>, js::RP_STAGE, s);
+    }
+    for (int s = 2; s >= 0; --s) {
+      run(js::batch_vjp_phase_kernel<js::RP_SEED>, js::RP_SEED, s);
+      if (ok) {
+        // pass 1 reads the WENO5 internals stored by the forward recompute of stages 0 and 1
+        // when the stage states were not given (the device's rev_saved)
+        // (one kernel for the viscous instances, one for the inviscid ones)
+        const bool sv = s < 2 && call.U1 == nullptr;
+        cudaStream_t st = b->stream;
+        if (sv) {
+          if (b->has_visc) js::batch_vjp_pass1_kernel<true, true><<<b->rev_p1blocks[1][1], js::BNT, 0, st>>>(a, s);
+          if (b->has_inv) js::batch_vjp_pass1_kernel<true, false><<<b->rev_p1blocks[1][0], js::BNT, 0, st>>>(a, s);
+        } else {
+          if (b->has_visc) js::batch_vjp_pass1_kernel<false, true><<<b->rev_p1blocks[0][1], js::BNT, 0, st>>>(a, s);
+          if (b->has_inv) js::batch_vjp_pass1_kernel<false, false><<<b->rev_p1blocks[0][0], js::BNT, 0, st>>>(a, s);
+        }
+        ok = cudaGetLastError() == cudaSuccess;
+      }
+      run(js::batch_vjp_phase_kernel<js::RP_PASS2>, js::RP_PASS2, s);
+      run(js::batch_vjp_phase_kernel<js::RP_PRIMVJP>, js::RP_PRIMVJP, s);
+      run(js::batch_vjp_phase_kernel<js::RP_BCTY>, js::RP_BCTY, s);
+      run(js::batch_vjp_phase_kernel<js::RP_BCTX>, js::RP_BCTX, s);
+      run(js::batch_vjp_phase_kernel<js::RP_INFLOW_GHOST>, js::RP_INFLOW_GHOST, s);
+      run(js::batch_vjp_phase_kernel<js::RP_SRC>, js::RP_SRC, s);
+    }
+    run(js::batch_vjp_phase_kernel<js::RP_UNPACK>, js::RP_UNPACK, 0);
+    return ok ? JS_OK : JS_ERR_CUDA;
+  }
   void* args[] = {&a};
   if (cudaLaunchCooperativeKernel((void*)js::batch_vjp_kernel, dim3(b->rev_blocks), dim3(js::BNT), args,
                                   batch_smem(), b->stream) != cudaSuccess)
@@ -1183,6 +1334,19 @@ int js_batch_set_tuning(js_batch* b, int blocks_per_sm, int schedule) {
   }
   b->schedule = schedule;
   b->blocks = b->sms * (blocks_per_sm == 0 ? b->per_sm : blocks_per_sm);
+  return JS_OK;
+}
+
+int js_batch_set_reverse_launch(js_batch* b, int split) {
+  if (!b || (split != 0 && split != 1)) return JS_ERR_ARG;
+  if (b->stream) cudaStreamSynchronize(b->stream); else cudaDeviceSynchronize();
+  b->rev_split = split;
+  return JS_OK;
+}
+
+int js_batch_get_reverse_launch(js_batch* b, int* split) {
+  if (!b || !split) return JS_ERR_ARG;
+  *split = b->rev_split;
   return JS_OK;
 }
 

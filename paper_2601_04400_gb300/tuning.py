@@ -1,4 +1,4 @@
-"""Autotuner of the fused stage kernel's tile shape.
+"""Autotuners of the fused stage kernel's tile shape and of the batched launches.
 
 Every variant computes identical results; only speed differs.  `autotune` times a few
 js_step calls per variant with CUDA events on the solver's stream, selects the fastest and
@@ -127,5 +127,40 @@ def autotune_batch(batch, problems, states, steps=2, use_cache=True):
     batch.set_states(states)
     cache = _load()
     cache[key] = {"choice": list(best), "ms_per_step": {"%d,%d" % k: v for k, v in times.items()}}
+    _save(cache)
+    return times
+
+
+def autotune_batch_reverse(batch, problems, states, dts, reps=2, use_cache=True):
+    """Time js_batch_step_vjp (one reverse step of every instance from `states` with step sizes
+    `dts`) in both launch forms -- one persistent launch, one launch per phase -- and select the
+    faster; the choice is cached per instance mix.  Results are identical for both forms.
+    Returns {split: ms per reverse step} ({} when the cache had the choice)."""
+    import torch
+    key = batch_key(problems) + "|reverse"
+    cache = _load()
+    if use_cache and key in cache:
+        batch.set_reverse_launch(cache[key]["split"])
+        return {}
+    lam = [torch.randn_like(U) for U in states]
+    out = [torch.empty_like(U) for U in states]
+    stream = torch.cuda.current_stream()
+    times = {}
+    for split in (0, 1):
+        batch.set_reverse_launch(split)
+        batch.step_vjp(states, dts, lam, out)  # warm-up (the first call prepares the workspace)
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(reps):
+            batch.step_vjp(states, dts, lam, out)
+        t1.record(stream)
+        t1.synchronize()
+        times[split] = t0.elapsed_time(t1) / reps
+    if batch.status() != 0:
+        raise RuntimeError("batched reverse tuning run failed")
+    best = 1 if times[1] < 0.98 * times[0] else 0
+    batch.set_reverse_launch(best)
+    cache = _load()
+    cache[key] = {"split": best, "ms_per_reverse_step": {str(k): v for k, v in times.items()}}
     _save(cache)
     return times

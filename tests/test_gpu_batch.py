@@ -303,6 +303,59 @@ def test_persistent_reverse_step_equals_js_step_vjp(env):
     b.close()
 
 
+def test_split_reverse_launch_equals_the_persistent_launch(env):
+    """One launch per phase (js_batch_set_reverse_launch(b, 1)) runs the persistent kernel's
+    device code on the same work items in the same order: lambda_n and p_bar equal the
+    persistent launch's to rounding (separately compiled kernels may contract a different set of
+    products into fused multiply-adds) and repeat bit for bit; a rollout reverse with the split
+    launch (stage states given) equals the per-instance step-by-step reverse."""
+    torch, B = env
+    probs = _mixed_cases()
+    states = _states(torch, probs)
+    b = B.Batch(probs)
+    b.set_states([U.clone() for U in states])
+    assert b.reverse_launch() == 0
+    with pytest.raises(B.JsError):
+        b.set_reverse_launch(2)
+    rng = np.random.default_rng(12)
+    lams = [torch.tensor(rng.standard_normal(U.shape), device="cuda") for U in states]
+    dts = []
+    for p, U in zip(probs, states):
+        s = B.Solver.from_problem(p)
+        dts.append(0.9 * s.max_dt(U, 0.5))
+        s.close()
+    res = {}
+    for split in (0, 1, 1):
+        b.set_reverse_launch(split)
+        assert b.reverse_launch() == split
+        outs = [torch.empty_like(U) for U in states]
+        pbs = [torch.zeros(20, dtype=torch.float64, device="cuda") for _ in states]
+        b.step_vjp(states, dts, lams, outs, pbs)
+        assert b.status() == 0
+        if split in res:  # the second split call: the same bits
+            for k in range(len(probs)):
+                assert torch.equal(outs[k], res[split][0][k]), k
+                assert torch.equal(pbs[k], res[split][1][k]), k
+        res[split] = (outs, pbs)
+    for k in range(len(probs)):
+        assert _rel(res[1][0][k], res[0][0][k]) < 1e-13, k
+        assert _rel(res[1][1][k], res[0][1][k]) < 1e-12, k
+    # rollout reverse (stage states given to the reverse launches) with the split launch
+    n = 7
+    log = torch.zeros((n, len(probs)), dtype=torch.float64, device="cuda")
+    for k, (p, U) in enumerate(zip(probs, states)):
+        log[:, k] = torch.tensor(dts[k] * rng.uniform(0.5, 0.9, n))
+    work = [lam.clone() for lam in lams]
+    pbs = [torch.zeros(20, dtype=torch.float64, device="cuda") for _ in states]
+    b.rollout_vjp(log, work, pbs, ckpt=3)
+    assert b.status() == 0
+    for k, p in enumerate(probs):
+        ref, pref = _reference_rollout_reverse(torch, B, p, states[k], log[:, k].tolist(), lams[k])
+        assert _rel(work[k], ref) < 1e-12, (k, _rel(work[k], ref))
+        assert _rel(pbs[k], pref) < 1e-11, (k, _rel(pbs[k], pref))
+    b.close()
+
+
 def test_fixed_step_sizes_replay_per_instance_steps(env):
     torch, B = env
     probs = _mixed_cases()
@@ -399,7 +452,8 @@ def test_rollout_default_spacing(env):
     b.close()
 
 
-def test_rollout_reverse_is_graph_capturable(env):
+@pytest.mark.parametrize("split", [0, 1])
+def test_rollout_reverse_is_graph_capturable(env, split):
     torch, B = env
     probs = _mixed_cases()[:3]
     states = _states(torch, probs)
@@ -407,6 +461,7 @@ def test_rollout_reverse_is_graph_capturable(env):
     n = 9
     with torch.cuda.stream(side):
         b = B.Batch(probs, stream=side)
+        b.set_reverse_launch(split)
         b.set_states([U.clone() for U in states])
         log = torch.zeros((n, len(probs)), dtype=torch.float64, device="cuda")
         fwd = [U.clone() for U in states]
