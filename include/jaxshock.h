@@ -393,10 +393,13 @@ int js_batch_get_tuning(js_batch* b, int* blocks_per_sm, int* max_blocks_per_sm,
  *     forward recompute, then per stage: seed + primitives, pass 1, pass 2, primitive reverse,
  *     transposed halos, inflow gradient and IB ghosts, IB sources; unpack) separated by
  *     bounded grid barriers, every phase at the register allocation of the heaviest one;
- *   split = 1: one ordinary launch per phase (up to 34 per reverse step), in the same order on
- *     the batch's stream, each phase kernel at its own occupancy.
+ *   split = 1: one ordinary launch per phase (34 per reverse step; 37 when the batch mixes
+ *     viscous and inviscid instances), in the same order on the batch's stream, each phase
+ *     kernel at its own occupancy.
  * Both run the same device code on the same work items in the same order: lambda and the
- * parameter gradient are identical bit for bit.  Both can be captured in a CUDA graph.
+ * parameter gradient agree to rounding (separately compiled kernels may contract different
+ * products into fused multiply-adds), and each form repeats its own results bit for bit.
+ * Both can be captured in a CUDA graph.
  * Synchronises the batch's stream (call before any stream capture).  Errors: JS_ERR_ARG for a
  * split value other than 0 or 1. */
 int js_batch_set_reverse_launch(js_batch* b, int split);
