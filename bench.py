@@ -44,7 +44,7 @@ NN_FLOPS_PER_CELL_STAGE = 2 * 2 * 6336
 STAGE_TRAFFIC_BYTES = {("shock_cylinder", 0): 291.0e6}
 # DRAM bytes per step of the persistent batched forward kernel on the 256-instance workload: an
 # ncu capture of one 2-step launch (19.26 GB), scaled by the steps of a launch
-BATCH_TRAFFIC_PER_STEP = 9.63e9
+BATCH_TRAFFIC_PER_STEP = 9.64e9
 L2_FLUSH_BYTES = 256 << 20
 METRIC = "FP64 cell-updates/s per RK step on 1 GB300 (% roofline); adjoint/forward time ratio"
 
