@@ -43,7 +43,7 @@ NN_FLOPS_PER_CELL_STAGE = 2 * 2 * 6336
 # variants (and for workloads whose capture predates the current kernel).
 STAGE_TRAFFIC_BYTES = {("shock_cylinder", 0): 291.0e6}
 # DRAM bytes per step of the persistent batched forward kernel on the 256-instance workload: an
-# ncu capture of one 2-step launch (19.26 GB), scaled by the steps of a launch
+# ncu capture of one 2-step launch of the current kernel (19.27 GB), scaled by the steps of a launch
 BATCH_TRAFFIC_PER_STEP = 9.64e9
 L2_FLUSH_BYTES = 256 << 20
 METRIC = "FP64 cell-updates/s per RK step on 1 GB300 (% roofline); adjoint/forward time ratio"
