@@ -41,7 +41,7 @@ NN_FLOPS_PER_CELL_STAGE = 2 * 2 * 6336
 # from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of this bench's default
 # run with the TMA-staged variant 0 and the current kernel; None for other workloads or
 # variants (and for workloads whose capture predates the current kernel).
-STAGE_TRAFFIC_BYTES = {("shock_cylinder", 0): 291.0e6}
+STAGE_TRAFFIC_BYTES = {("shock_cylinder", 0): 291.0e6, ("riemann2d", 0): 108.0e6}
 # DRAM bytes per step of the persistent batched forward kernel on the 256-instance workload: an
 # ncu capture of one 2-step launch of the current kernel (19.27 GB), scaled by the steps of a launch
 BATCH_TRAFFIC_PER_STEP = 9.64e9
